@@ -1,0 +1,224 @@
+"""FP64 CPU oracle for the Cartesian FMM operators (arXiv:1811.06332).
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow restatement of the
+paper's equations against which the CUDA library is checked.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference leg may
+import it; the library under ``paper_1811_06332_gb300/`` never does, and the
+two share no code.
+
+Every function here marshals numpy arrays into ``fmm_oracle.c``; the arithmetic
+is all in that C file, each routine citing the equation it restates:
+
+* ``dtensor``      -- Eq. traceless grad + Eq. Detracer3 (App. A)
+* ``detracer_T``   -- Eq. Detracer (App. A); ``detracer_D`` = T/(2n-1)!!
+* ``p2m``          -- Eq. P2M (Sec. 2.1), sign (-r_a)^n as in App. B
+* ``m2m``          -- Eq. M2M / M2M part 2 (Sec. 2.1)
+* ``m2l``          -- Eq. M2L (Sec. 2.1)
+* ``l2l``          -- Eq. L2L (Sec. 2.1)
+* ``l2p``          -- Eq. L2P (Sec. 2.1)
+* ``direct``       -- Eq. PhiAB (App. B), O(N^2)
+* ``fmm_uniform``  -- App. C on a uniform octree with the standard
+                      (Chebyshev distance >= 2) separation criterion
+
+Parity status: every function is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_*.py`` (closed forms, finite differences, identities,
+the paper's worked example and storage table, direct sums).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+SYM = 0
+TRACELESS = 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_ncoef.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc_ncoef.restype = ctypes.c_int
+        L.orc_indices.argtypes = [ctypes.c_int, ctypes.c_int, _ip]
+        L.orc_indices.restype = ctypes.c_int
+        L.orc_expand_traceless.argtypes = [ctypes.c_int, _dp, _dp]
+        L.orc_detracer_T.argtypes = [ctypes.c_int, _dp, _dp]
+        L.orc_detracer_D.argtypes = [ctypes.c_int, _dp, _dp]
+        L.orc_dtensor.argtypes = [ctypes.c_int, _dp, _dp]
+        L.orc_dtensor_batch.argtypes = [ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp]
+        L.orc_p2m.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_m2m.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.orc_m2l.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.orc_m2l_D.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.orc_m2l_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp,
+                                    _dp, ctypes.c_int]
+        L.orc_l2l.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.orc_l2p.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.orc_direct.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int64, _i64p,
+                                 _dp, _dp, _dp, _dp]
+        L.orc_fmm_uniform.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int64, _i64p, _dp, _dp, _dp, _dp]
+        L.orc_fmm_uniform.restype = ctypes.c_int
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], (a.dtype, a.flags)
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def ncoef(p: int, basis: int) -> int:
+    return lib().orc_ncoef(p, basis)
+
+
+def indices(p: int, basis: int) -> np.ndarray:
+    """Multi-indices (ncoef, 3) in storage order."""
+    nc = ncoef(p, basis)
+    out = np.zeros((nc, 3), dtype=np.int32)
+    lib().orc_indices(p, basis, out.ctypes.data_as(_ip))
+    return out
+
+
+def expand_traceless(p: int, A: np.ndarray) -> np.ndarray:
+    A = _f64(A)
+    out = np.zeros(ncoef(p, SYM))
+    lib().orc_expand_traceless(p, _d(A), _d(out))
+    return out
+
+
+def detracer_T(n: int, A: np.ndarray) -> np.ndarray:
+    A = _f64(A)
+    out = np.zeros((n + 1) * (n + 2) // 2)
+    lib().orc_detracer_T(n, _d(A), _d(out))
+    return out
+
+
+def detracer_D(n: int, A: np.ndarray) -> np.ndarray:
+    A = _f64(A)
+    out = np.zeros((n + 1) * (n + 2) // 2)
+    lib().orc_detracer_D(n, _d(A), _d(out))
+    return out
+
+
+def dtensor(p: int, r) -> np.ndarray:
+    r = _f64(r)
+    out = np.zeros(ncoef(p, SYM))
+    lib().orc_dtensor(p, _d(r), _d(out))
+    return out
+
+
+def dtensor_batch(p: int, r: np.ndarray) -> np.ndarray:
+    """r: (3, n) -> D: (ns, n)."""
+    r = _f64(r)
+    n = r.shape[1]
+    out = np.zeros((ncoef(p, SYM), n))
+    rx, ry, rz = _f64(r[0]), _f64(r[1]), _f64(r[2])
+    lib().orc_dtensor_batch(p, n, _d(rx), _d(ry), _d(rz), _d(out))
+    return out
+
+
+def p2m(p: int, basis: int, x, y, z, q, zc) -> np.ndarray:
+    x, y, z, q, zc = (_f64(v) for v in (x, y, z, q, zc))
+    out = np.zeros(ncoef(p, basis))
+    lib().orc_p2m(p, basis, len(x), _d(x), _d(y), _d(z), _d(q), _d(zc), _d(out))
+    return out
+
+
+def m2m(p: int, basis: int, M: np.ndarray, delta) -> np.ndarray:
+    M, delta = _f64(M), _f64(delta)
+    out = np.zeros(ncoef(p, basis))
+    lib().orc_m2m(p, basis, _d(M), _d(delta), _d(out))
+    return out
+
+
+def m2l(p: int, basis: int, M: np.ndarray, r) -> np.ndarray:
+    M, r = _f64(M), _f64(r)
+    out = np.zeros(ncoef(p, basis))
+    lib().orc_m2l(p, basis, _d(M), _d(r), _d(out))
+    return out
+
+
+def m2l_D(p: int, basis: int, M: np.ndarray, D: np.ndarray) -> np.ndarray:
+    M, D = _f64(M), _f64(D)
+    out = np.zeros(ncoef(p, basis))
+    lib().orc_m2l_D(p, basis, _d(M), _d(D), _d(out))
+    return out
+
+
+def m2l_batch(p: int, basis: int, M: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """M: (ncoef, n), r: (3, n) -> L: (ncoef, n)."""
+    M = _f64(M)
+    n = M.shape[1]
+    rx, ry, rz = _f64(r[0]), _f64(r[1]), _f64(r[2])
+    out = np.zeros((ncoef(p, basis), n))
+    lib().orc_m2l_batch(p, basis, n, _d(M), _d(rx), _d(ry), _d(rz), _d(out), 0)
+    return out
+
+
+def l2l(p: int, basis: int, L: np.ndarray, delta) -> np.ndarray:
+    L, delta = _f64(L), _f64(delta)
+    out = np.zeros(ncoef(p, basis))
+    lib().orc_l2l(p, basis, _d(L), _d(delta), _d(out))
+    return out
+
+
+def l2p(p: int, basis: int, L: np.ndarray, rb) -> np.ndarray:
+    """Returns [Phi, dPhi/dx, dPhi/dy, dPhi/dz] (paper's positive sign)."""
+    L, rb = _f64(L), _f64(rb)
+    out = np.zeros(4)
+    lib().orc_l2p(p, basis, _d(L), _d(rb), _d(out))
+    return out
+
+
+def direct(x, y, z, q, targets=None):
+    """O(N^2) FP64 sum: pot = -sum q/r, acc = sum q (x_j - x_i)/r^3."""
+    x, y, z, q = (_f64(v) for v in (x, y, z, q))
+    n = len(x)
+    if targets is None:
+        nt, tp = n, None
+    else:
+        targets = np.ascontiguousarray(targets, dtype=np.int64)
+        nt, tp = len(targets), targets.ctypes.data_as(_i64p)
+    pot, ax, ay, az = (np.zeros(nt) for _ in range(4))
+    lib().orc_direct(n, _d(x), _d(y), _d(z), _d(q), nt, tp, _d(pot), _d(ax), _d(ay), _d(az))
+    return pot, np.stack([ax, ay, az])
+
+
+def fmm_uniform(x, y, z, q, depth: int, p: int, basis: int, sample=None):
+    """Uniform-octree FMM (App. C); returns pot (n,) and acc (3, n).
+
+    With ``sample`` (int64 indices) only those particles are evaluated."""
+    x, y, z, q = (_f64(v) for v in (x, y, z, q))
+    n = len(x)
+    if sample is None:
+        ns, sp, nout = -1, None, n
+    else:
+        sample = np.ascontiguousarray(sample, dtype=np.int64)
+        ns, sp, nout = len(sample), sample.ctypes.data_as(_i64p), len(sample)
+    pot, ax, ay, az = (np.zeros(nout) for _ in range(4))
+    rc = lib().orc_fmm_uniform(n, _d(x), _d(y), _d(z), _d(q), depth, p, basis, ns, sp,
+                               _d(pot), _d(ax), _d(ay), _d(az))
+    if rc != 0:
+        raise ValueError("orc_fmm_uniform rejected its arguments")
+    return pot, np.stack([ax, ay, az])

@@ -1,0 +1,656 @@
+/*
+ * fmm_oracle.c -- plain FP64 CPU oracle for the Cartesian FMM operators of
+ * Coles & Bieri, "An Optimizing Symbolic Algebra Approach for Generating Fast
+ * Multipole Method Operators" (arXiv:1811.06332).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * restatement of the paper's equations against which the CUDA library is
+ * checked.  Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference leg may load it.  The CUDA library never links, includes or calls
+ * anything here, and nothing here is shared with it.
+ *
+ * Conventions (each one a reading of the paper, listed again in the design doc):
+ *  - multi-index notation of App. D: n = (nx,ny,nz), |n| = nx+ny+nz,
+ *    n! = nx! ny! nz!, r^n = x^nx y^ny z^nz; a negative component makes the
+ *    whole term zero.
+ *  - symmetric ("totally symmetric", compressed) storage, App. A: ranks 0..p
+ *    concatenated; inside rank j the (j+1)(j+2)/2 components are ordered by
+ *    descending nx, then descending ny.
+ *  - traceless storage (Sec. 2.1 / App. B: only independent components are
+ *    kept): inside rank j the 2j+1 components with nz <= 1, ordered
+ *    (j,0,0),(j-1,1,0),...,(0,j,0),(j-1,0,1),...,(0,j-1,1).  Dependent
+ *    components come from the trace condition A_{k+2ez} = -A_{k+2ex} - A_{k+2ey}.
+ *  - normalisation of the main text (Sec. 2.1): M_n = sum_a q_a (-r_a)^n,
+ *    M2L with 1/m!, L2L with delta^k/k!, L2P reads L_n at the particle.
+ *  - the P2M sign printed as "-r_a^n" is read as (-r_a)^n (App. B, Eq.
+ *    multipole v1 carries (-1)^n r_a^n).
+ *  - output sign: pot = -Phi_paper (astrophysical sign, Sec. 2.1 last
+ *    paragraph), acc = +grad Phi_paper = sum_j q_j (x_j - x_i)/|x_j - x_i|^3.
+ *  - self-interaction excluded, no softening, coincident pairs skipped.
+ *
+ * Everything is double precision and straightforward loops; OpenMP is used
+ * only to spread independent targets over host cores.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PMAX 12
+#define NS_MAX 455 /* C(12+3,3) */
+#define NT_MAX 169 /* (12+1)^2  */
+
+/* ------------------------------------------------------------------------ */
+/* Multi-index tables (App. D; storage sizes of the table in App. E)         */
+/* ------------------------------------------------------------------------ */
+static int g_init = 0;
+static int g_sym[NS_MAX][3];                       /* sym index -> n     */
+static int g_tl[NT_MAX][3];                        /* tl index  -> n     */
+static int g_pos_sym[ORC_PMAX + 1][ORC_PMAX + 1][ORC_PMAX + 1];
+static int g_pos_tl[ORC_PMAX + 1][ORC_PMAX + 1][ORC_PMAX + 1];
+static double g_fact[4 * ORC_PMAX + 4];
+
+__attribute__((constructor)) static void orc_init(void) {
+    if (g_init) return;
+    int c = 0;
+    for (int j = 0; j <= ORC_PMAX; ++j)
+        for (int nx = j; nx >= 0; --nx)
+            for (int ny = j - nx; ny >= 0; --ny) {
+                int nz = j - nx - ny;
+                g_sym[c][0] = nx; g_sym[c][1] = ny; g_sym[c][2] = nz;
+                g_pos_sym[nx][ny][nz] = c;
+                ++c;
+            }
+    for (int a = 0; a <= ORC_PMAX; ++a)
+        for (int b = 0; b <= ORC_PMAX; ++b)
+            for (int d = 0; d <= ORC_PMAX; ++d) g_pos_tl[a][b][d] = -1;
+    c = 0;
+    for (int j = 0; j <= ORC_PMAX; ++j) {
+        for (int ny = 0; ny <= j; ++ny) {           /* nz = 0 */
+            g_tl[c][0] = j - ny; g_tl[c][1] = ny; g_tl[c][2] = 0;
+            g_pos_tl[j - ny][ny][0] = c; ++c;
+        }
+        for (int ny = 0; ny <= j - 1; ++ny) {       /* nz = 1 */
+            g_tl[c][0] = j - 1 - ny; g_tl[c][1] = ny; g_tl[c][2] = 1;
+            g_pos_tl[j - 1 - ny][ny][1] = c; ++c;
+        }
+    }
+    g_fact[0] = 1.0;
+    for (int i = 1; i < 4 * ORC_PMAX + 4; ++i) g_fact[i] = g_fact[i - 1] * i;
+    g_init = 1;
+}
+
+int orc_pmax(void) { return ORC_PMAX; }
+int orc_ncoef_sym(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+int orc_ncoef_tl(int p) { return (p + 1) * (p + 1); }
+int orc_ncoef(int p, int basis) { return basis ? orc_ncoef_tl(p) : orc_ncoef_sym(p); }
+
+/* Copies the multi-indices of the storage order into out[3*ncoef]. */
+int orc_indices(int p, int basis, int* out) {
+    orc_init();
+    if (p < 0 || p > ORC_PMAX) return -1;
+    int nc = orc_ncoef(p, basis);
+    for (int i = 0; i < nc; ++i)
+        for (int d = 0; d < 3; ++d) out[3 * i + d] = basis ? g_tl[i][d] : g_sym[i][d];
+    return nc;
+}
+
+static double mfact(int nx, int ny, int nz) { return g_fact[nx] * g_fact[ny] * g_fact[nz]; }
+
+/* (2k-1)!! for k >= 0, with (-1)!! = 1 */
+static double dfact_odd(int k) {
+    double v = 1.0;
+    for (int i = 2 * k - 1; i > 1; i -= 2) v *= i;
+    return v;
+}
+
+static double ipow(double x, int e) {
+    double v = 1.0;
+    for (int i = 0; i < e; ++i) v *= x;
+    return v;
+}
+
+/* f_{n,m} of Eq. Detracer (App. A):
+ * (-1)^|m| (2|n|-2|m|-1)!! n! / (2^|m| m! (n-2m)!)  for m <= floor(n/2). */
+static double f_nm(const int n[3], const int m[3]) {
+    int nn = n[0] + n[1] + n[2], mm = m[0] + m[1] + m[2];
+    double v = dfact_odd(nn - mm) * mfact(n[0], n[1], n[2]) /
+               (ldexp(1.0, mm) * mfact(m[0], m[1], m[2]) *
+                mfact(n[0] - 2 * m[0], n[1] - 2 * m[1], n[2] - 2 * m[2]));
+    return (mm & 1) ? -v : v;
+}
+
+/* Expands traceless storage into full symmetric storage, ranks 0..p, using
+ * the trace condition (App. B: dependent elements are rebuilt from the trace,
+ * e.g. A_zz = -A_xx - A_yy).  Symmetric order visits both right-hand sides
+ * before the left-hand side. */
+static void tl_to_sym(int p, const double* Atl, double* A) {
+    int ns = orc_ncoef_sym(p);
+    for (int i = 0; i < ns; ++i) {
+        int nx = g_sym[i][0], ny = g_sym[i][1], nz = g_sym[i][2];
+        if (nz <= 1)
+            A[i] = Atl[g_pos_tl[nx][ny][nz]];
+        else
+            A[i] = -A[g_pos_sym[nx + 2][ny][nz - 2]] - A[g_pos_sym[nx][ny + 2][nz - 2]];
+    }
+}
+
+/* Public version for tests. */
+void orc_expand_traceless(int p, const double* Atl, double* A) {
+    orc_init();
+    tl_to_sym(p, Atl, A);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Detracer (Eq. Detracer, App. A)                                           */
+/* ------------------------------------------------------------------------ */
+/* T[A]_n = sum_{m <= floor(n/2)} f_{n,m} A^{(n:|m|)}_{n-2m},
+ * A^{(n:mm)}_k = sum_{|k'|=mm} (mm!/k'!) A_{k+2k'} (m-fold trace).
+ * A and out are full symmetric rank-nrank blocks (the rank-nrank slice of the
+ * symmetric storage order). */
+void orc_detracer_T(int nrank, const double* A, double* out) {
+    orc_init();
+    int off = orc_ncoef_sym(nrank - 1); /* 0 for nrank == 0 */
+    int cnt = (nrank + 1) * (nrank + 2) / 2;
+    for (int i = 0; i < cnt; ++i) {
+        const int* n = g_sym[off + i];
+        double s = 0.0;
+        for (int mx = 0; mx <= n[0] / 2; ++mx)
+            for (int my = 0; my <= n[1] / 2; ++my)
+                for (int mz = 0; mz <= n[2] / 2; ++mz) {
+                    int m[3] = {mx, my, mz};
+                    int mm = mx + my + mz;
+                    double tr = 0.0;
+                    for (int kx = mm; kx >= 0; --kx)
+                        for (int ky = mm - kx; ky >= 0; --ky) {
+                            int kz = mm - kx - ky;
+                            int ix = n[0] - 2 * mx + 2 * kx;
+                            int iy = n[1] - 2 * my + 2 * ky;
+                            int iz = n[2] - 2 * mz + 2 * kz;
+                            tr += g_fact[mm] / mfact(kx, ky, kz) *
+                                  A[g_pos_sym[ix][iy][iz] - off];
+                        }
+                    s += f_nm(n, m) * tr;
+                }
+        out[i] = s;
+    }
+}
+
+/* D[A] = T[A] / (2n-1)!!  (App. A, the idempotent detracer). */
+void orc_detracer_D(int nrank, const double* A, double* out) {
+    orc_detracer_T(nrank, A, out);
+    double s = 1.0 / dfact_odd(nrank);
+    int cnt = (nrank + 1) * (nrank + 2) / 2;
+    for (int i = 0; i < cnt; ++i) out[i] *= s;
+}
+
+/* Applies D[] rank by rank to a full symmetric polytensor (ranks 0..p). */
+static void detrace_polytensor(int p, const double* A, double* out) {
+    for (int j = 0; j <= p; ++j) {
+        int off = orc_ncoef_sym(j - 1);
+        orc_detracer_D(j, A + off, out + off);
+    }
+}
+
+/* Writes (basis 1) the independent components of a full symmetric
+ * polytensor, or (basis 0) all of them, adding into dst. */
+static void add_out(int p, int basis, const double* Afull, double* dst) {
+    if (!basis) {
+        int ns = orc_ncoef_sym(p);
+        for (int i = 0; i < ns; ++i) dst[i] += Afull[i];
+    } else {
+        int nt = orc_ncoef_tl(p);
+        for (int i = 0; i < nt; ++i) dst[i] += Afull[g_pos_sym[g_tl[i][0]][g_tl[i][1]][g_tl[i][2]]];
+    }
+}
+
+static void to_full(int p, int basis, const double* A, double* Afull) {
+    if (basis)
+        tl_to_sym(p, A, Afull);
+    else
+        memcpy(Afull, A, sizeof(double) * orc_ncoef_sym(p));
+}
+
+/* ------------------------------------------------------------------------ */
+/* D-tensor: traceless gradient of 1/r (Eq. traceless grad and Eq.          */
+/* Detracer3, App. A):                                                       */
+/*   D_n(r) = grad^n r^{-1} = (-1)^|n| r^{-2|n|-1} T[r^n]_n,                 */
+/*   T[r^n]_n = sum_{m <= floor(n/2)} f_{n,m} r^{2|m|} r^{n-2m}.             */
+/* ------------------------------------------------------------------------ */
+void orc_dtensor(int p, const double r[3], double* D) {
+    orc_init();
+    double x = r[0], y = r[1], z = r[2];
+    double r2 = x * x + y * y + z * z;
+    double rn = sqrt(r2);
+    int ns = orc_ncoef_sym(p);
+    for (int i = 0; i < ns; ++i) {
+        const int* n = g_sym[i];
+        int nn = n[0] + n[1] + n[2];
+        double s = 0.0;
+        for (int mx = 0; mx <= n[0] / 2; ++mx)
+            for (int my = 0; my <= n[1] / 2; ++my)
+                for (int mz = 0; mz <= n[2] / 2; ++mz) {
+                    int m[3] = {mx, my, mz};
+                    int mm = mx + my + mz;
+                    s += f_nm(n, m) * ipow(r2, mm) * ipow(x, n[0] - 2 * mx) *
+                         ipow(y, n[1] - 2 * my) * ipow(z, n[2] - 2 * mz);
+                }
+        double pre = pow(rn, -(2.0 * nn + 1.0));
+        D[i] = ((nn & 1) ? -pre : pre) * s;
+    }
+}
+
+void orc_dtensor_batch(int p, int64_t n, const double* rx, const double* ry,
+                       const double* rz, double* D /* [ns][n] */) {
+    orc_init();
+    int ns = orc_ncoef_sym(p);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < n; ++t) {
+        double r[3] = {rx[t], ry[t], rz[t]}, d[NS_MAX];
+        orc_dtensor(p, r, d);
+        for (int i = 0; i < ns; ++i) D[(int64_t)i * n + t] = d[i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* P2M (Eq. P2M, Sec. 2.1; App. B Eq. multipole v1 for the sign):            */
+/*   M_n = sum_a q_a (-r_a)^n,  r_a = x_a - z_A;   traceless: Mbar = D[M].    */
+/* M is added into (accumulate).                                             */
+/* ------------------------------------------------------------------------ */
+void orc_p2m(int p, int basis, int64_t na, const double* x, const double* y,
+             const double* z, const double* q, const double zc[3], double* M) {
+    orc_init();
+    int ns = orc_ncoef_sym(p);
+    double Ms[NS_MAX];
+    for (int i = 0; i < ns; ++i) Ms[i] = 0.0;
+    for (int64_t a = 0; a < na; ++a) {
+        double ra[3] = {x[a] - zc[0], y[a] - zc[1], z[a] - zc[2]};
+        for (int i = 0; i < ns; ++i) {
+            const int* n = g_sym[i];
+            Ms[i] += q[a] * ipow(-ra[0], n[0]) * ipow(-ra[1], n[1]) * ipow(-ra[2], n[2]);
+        }
+    }
+    if (basis) {
+        double Mt[NS_MAX];
+        detrace_polytensor(p, Ms, Mt);
+        add_out(p, basis, Mt, M);
+    } else {
+        add_out(p, basis, Ms, M);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* M2M (Eq. M2M and Eq. M2M part 2, Sec. 2.1):                               */
+/*   M'_n(z' = z - delta) = sum_{k <= n} n!/(k!(n-k)!) (-delta)^{n-k} M_k(z)  */
+/*   traceless: Mbar(z') = D[M'].   Result is added into Mp.                  */
+/* ------------------------------------------------------------------------ */
+void orc_m2m(int p, int basis, const double* Mc, const double delta[3], double* Mp) {
+    orc_init();
+    int ns = orc_ncoef_sym(p);
+    double Ms[NS_MAX], Mn[NS_MAX];
+    to_full(p, basis, Mc, Ms);
+    double md[3] = {-delta[0], -delta[1], -delta[2]};
+    for (int i = 0; i < ns; ++i) {
+        const int* n = g_sym[i];
+        double s = 0.0;
+        for (int kx = 0; kx <= n[0]; ++kx)
+            for (int ky = 0; ky <= n[1]; ++ky)
+                for (int kz = 0; kz <= n[2]; ++kz) {
+                    double binom = mfact(n[0], n[1], n[2]) /
+                                   (mfact(kx, ky, kz) * mfact(n[0] - kx, n[1] - ky, n[2] - kz));
+                    s += binom * ipow(md[0], n[0] - kx) * ipow(md[1], n[1] - ky) *
+                         ipow(md[2], n[2] - kz) * Ms[g_pos_sym[kx][ky][kz]];
+                }
+        Mn[i] = s;
+    }
+    if (basis) {
+        double Mt[NS_MAX];
+        detrace_polytensor(p, Mn, Mt);
+        add_out(p, basis, Mt, Mp);
+    } else {
+        add_out(p, basis, Mn, Mp);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* M2L (Eq. M2L, Sec. 2.1):                                                  */
+/*   L_n(z' = z + r) += sum_{|m| <= p-|n|} (1/m!) M_m(z) D_{n+m}(r)           */
+/* D is the full symmetric D-tensor up to rank p (orc_dtensor).              */
+/* ------------------------------------------------------------------------ */
+void orc_m2l_D(int p, int basis, const double* M, const double* D, double* L) {
+    orc_init();
+    int ns = orc_ncoef_sym(p);
+    double Ms[NS_MAX], Ls[NS_MAX];
+    to_full(p, basis, M, Ms);
+    for (int i = 0; i < ns; ++i) {
+        const int* n = g_sym[i];
+        int nn = n[0] + n[1] + n[2];
+        double s = 0.0;
+        if (basis && n[2] >= 2) { Ls[i] = 0.0; continue; } /* dependent output */
+        int nm = orc_ncoef_sym(p - nn);
+        for (int k = 0; k < nm; ++k) {
+            const int* m = g_sym[k];
+            s += Ms[k] / mfact(m[0], m[1], m[2]) *
+                 D[g_pos_sym[n[0] + m[0]][n[1] + m[1]][n[2] + m[2]]];
+        }
+        Ls[i] = s;
+    }
+    add_out(p, basis, Ls, L);
+}
+
+void orc_m2l(int p, int basis, const double* M, const double r[3], double* L) {
+    double D[NS_MAX];
+    orc_dtensor(p, r, D);
+    orc_m2l_D(p, basis, M, D, L);
+}
+
+/* Batched M2L over independent pairs: M [ncoef][n], offsets r [3][n] (SoA),
+ * L [ncoef][n] accumulated (or overwritten when accumulate == 0). */
+void orc_m2l_batch(int p, int basis, int64_t n, const double* M, const double* rx,
+                   const double* ry, const double* rz, double* L, int accumulate) {
+    orc_init();
+    int nc = orc_ncoef(p, basis);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < n; ++t) {
+        double m[NS_MAX], l[NS_MAX], r[3] = {rx[t], ry[t], rz[t]};
+        for (int i = 0; i < nc; ++i) {
+            m[i] = M[(int64_t)i * n + t];
+            l[i] = accumulate ? L[(int64_t)i * n + t] : 0.0;
+        }
+        orc_m2l(p, basis, m, r, l);
+        for (int i = 0; i < nc; ++i) L[(int64_t)i * n + t] = l[i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* L2L (Eq. L2L, Sec. 2.1):                                                  */
+/*   L_n(z' = z + delta) += sum_{|k| <= p-|n|} delta^k/k! L_{n+k}(z)          */
+/* ------------------------------------------------------------------------ */
+void orc_l2l(int p, int basis, const double* Lp, const double delta[3], double* Lc) {
+    orc_init();
+    int ns = orc_ncoef_sym(p);
+    double Ls[NS_MAX], Ln[NS_MAX];
+    to_full(p, basis, Lp, Ls);
+    for (int i = 0; i < ns; ++i) {
+        const int* n = g_sym[i];
+        int nn = n[0] + n[1] + n[2];
+        int nk = orc_ncoef_sym(p - nn);
+        double s = 0.0;
+        for (int k = 0; k < nk; ++k) {
+            const int* kk = g_sym[k];
+            s += ipow(delta[0], kk[0]) * ipow(delta[1], kk[1]) * ipow(delta[2], kk[2]) /
+                 mfact(kk[0], kk[1], kk[2]) *
+                 Ls[g_pos_sym[n[0] + kk[0]][n[1] + kk[1]][n[2] + kk[2]]];
+        }
+        Ln[i] = s;
+    }
+    add_out(p, basis, Ln, Lc);
+}
+
+/* ------------------------------------------------------------------------ */
+/* L2P (Eq. L2P, Sec. 2.1): shift L to the particle (delta = r_b) and read   */
+/* the rank-0 and rank-1 components:                                         */
+/*   Phi = sum_{|k|<=p} r_b^k/k! L_k,  dPhi/dx_i = sum_{|k|<=p-1} r_b^k/k! L_{k+e_i}. */
+/* out[0] = Phi, out[1..3] = grad Phi (paper's positive-potential sign).     */
+/* ------------------------------------------------------------------------ */
+void orc_l2p(int p, int basis, const double* L, const double rb[3], double out[4]) {
+    orc_init();
+    double Ls[NS_MAX];
+    to_full(p, basis, L, Ls);
+    int ns = orc_ncoef_sym(p);
+    double phi = 0.0, g[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < ns; ++k) {
+        const int* kk = g_sym[k];
+        int nk = kk[0] + kk[1] + kk[2];
+        double w = ipow(rb[0], kk[0]) * ipow(rb[1], kk[1]) * ipow(rb[2], kk[2]) /
+                   mfact(kk[0], kk[1], kk[2]);
+        phi += w * Ls[k];
+        if (nk <= p - 1) {
+            g[0] += w * Ls[g_pos_sym[kk[0] + 1][kk[1]][kk[2]]];
+            g[1] += w * Ls[g_pos_sym[kk[0]][kk[1] + 1][kk[2]]];
+            g[2] += w * Ls[g_pos_sym[kk[0]][kk[1]][kk[2] + 1]];
+        }
+    }
+    out[0] = phi; out[1] = g[0]; out[2] = g[1]; out[3] = g[2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct sum (Eq. PhiAB, App. B) with the output sign convention above.     */
+/* targets == NULL means every particle; otherwise nt indices.               */
+/* ------------------------------------------------------------------------ */
+void orc_direct(int64_t n, const double* x, const double* y, const double* z,
+                const double* q, int64_t nt, const int64_t* targets, double* pot,
+                double* ax, double* ay, double* az) {
+    int64_t cnt = targets ? nt : n;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < cnt; ++t) {
+        int64_t i = targets ? targets[t] : t;
+        double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == 0.0) continue;
+            double ir = 1.0 / sqrt(r2);
+            double ir3 = ir * ir * ir;
+            ph += q[j] * ir;
+            gx += q[j] * dx * ir3; gy += q[j] * dy * ir3; gz += q[j] * dz * ir3;
+        }
+        pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uniform-octree FMM (App. C, with the octree and "standard" separation     */
+/* criterion of the uniform workloads): leaves at level `depth` of the unit   */
+/* cube [0,1)^3, leaf of a particle i_d = min(floor(x_d 2^depth), 2^depth-1).  */
+/* Same-level cells are well separated when their Chebyshev index distance   */
+/* is >= 2; the interaction list of a cell is the children of its parent's  */
+/* neighbours (parent included) that are not adjacent to it; M2L runs at     */
+/* levels 2..depth; adjacent leaves (self included) are summed directly.     */
+/* Expansion centres are geometric cell centres (App. C).                    */
+/* If nsample >= 0 only the particles listed in sample[] are evaluated       */
+/* (outputs have nsample entries, in that order); otherwise all n, in the    */
+/* caller's order.                                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int depth, p, basis, nc;
+    int64_t n;
+    const double *x, *y, *z, *q;
+    int64_t* leaf_start; /* [nleaf+1] */
+    int64_t* order;      /* particles sorted by leaf, stable */
+    double** M;          /* per level, [ncell][nc] */
+    double** L;
+} uni_t;
+
+static inline int64_t cell_id(int l, int ix, int iy, int iz) {
+    int64_t s = (int64_t)1 << l;
+    return ((int64_t)iz * s + iy) * s + ix;
+}
+
+static void cell_centre(int l, int ix, int iy, int iz, double c[3]) {
+    double h = ldexp(1.0, -l);
+    c[0] = (ix + 0.5) * h; c[1] = (iy + 0.5) * h; c[2] = (iz + 0.5) * h;
+}
+
+static int leaf_coord(double v, int side) {
+    int i = (int)floor(v * side);
+    if (i < 0) i = 0;
+    if (i > side - 1) i = side - 1;
+    return i;
+}
+
+int orc_fmm_uniform(int64_t n, const double* x, const double* y, const double* z,
+                    const double* q, int depth, int p, int basis, int64_t nsample,
+                    const int64_t* sample, double* pot, double* ax, double* ay,
+                    double* az) {
+    orc_init();
+    if (p < 0 || p > ORC_PMAX || depth < 0 || depth > 10) return -1;
+    int side = 1 << depth;
+    int64_t nleaf = (int64_t)side * side * side;
+    int nc = orc_ncoef(p, basis);
+    uni_t U;
+    U.depth = depth; U.p = p; U.basis = basis; U.nc = nc; U.n = n;
+    U.x = x; U.y = y; U.z = z; U.q = q;
+
+    /* leaf assignment and stable bucket sort */
+    int64_t* leaf = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    U.leaf_start = (int64_t*)calloc(nleaf + 1, sizeof(int64_t));
+    U.order = (int64_t*)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        leaf[i] = cell_id(depth, leaf_coord(x[i], side), leaf_coord(y[i], side),
+                          leaf_coord(z[i], side));
+        U.leaf_start[leaf[i] + 1]++;
+    }
+    for (int64_t c = 0; c < nleaf; ++c) U.leaf_start[c + 1] += U.leaf_start[c];
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * nleaf);
+        memcpy(fill, U.leaf_start, sizeof(int64_t) * nleaf);
+        for (int64_t i = 0; i < n; ++i) U.order[fill[leaf[i]]++] = i;
+        free(fill);
+    }
+
+    /* which leaves / cells are needed (sampled mode) */
+    char** need = (char**)malloc(sizeof(char*) * (depth + 1));
+    for (int l = 0; l <= depth; ++l) {
+        int64_t nce = (int64_t)1 << (3 * l);
+        need[l] = (char*)calloc(nce, 1);
+    }
+    int64_t ntarg = nsample >= 0 ? nsample : n;
+    for (int64_t t = 0; t < ntarg; ++t) {
+        int64_t i = nsample >= 0 ? sample[t] : t;
+        int ix = leaf_coord(x[i], side), iy = leaf_coord(y[i], side), iz = leaf_coord(z[i], side);
+        for (int l = depth; l >= 0; --l) {
+            need[l][cell_id(l, ix, iy, iz)] = 1;
+            ix >>= 1; iy >>= 1; iz >>= 1;
+        }
+    }
+
+    /* upward pass: P2M at leaves, M2M bottom-up (App. C) */
+    U.M = (double**)malloc(sizeof(double*) * (depth + 1));
+    U.L = (double**)malloc(sizeof(double*) * (depth + 1));
+    for (int l = 0; l <= depth; ++l) {
+        int64_t nce = (int64_t)1 << (3 * l);
+        U.M[l] = (double*)calloc(nce * nc, sizeof(double));
+        U.L[l] = (double*)calloc(nce * nc, sizeof(double));
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < nleaf; ++c) {
+        int64_t b = U.leaf_start[c], e = U.leaf_start[c + 1];
+        if (b == e) continue;
+        int ix = (int)(c % side), iy = (int)((c / side) % side), iz = (int)(c / ((int64_t)side * side));
+        double zc[3];
+        cell_centre(depth, ix, iy, iz, zc);
+        int64_t cnt = e - b;
+        double* buf = (double*)malloc(sizeof(double) * 4 * cnt);
+        for (int64_t a = 0; a < cnt; ++a) {
+            int64_t i = U.order[b + a];
+            buf[a] = x[i]; buf[cnt + a] = y[i]; buf[2 * cnt + a] = z[i]; buf[3 * cnt + a] = q[i];
+        }
+        orc_p2m(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, buf + 3 * cnt, zc, U.M[depth] + c * nc);
+        free(buf);
+    }
+    for (int l = depth - 1; l >= 0; --l) {
+        int s = 1 << l;
+        int64_t nce = (int64_t)s * s * s;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t c = 0; c < nce; ++c) {
+            int ix = (int)(c % s), iy = (int)((c / s) % s), iz = (int)(c / ((int64_t)s * s));
+            double zp[3];
+            cell_centre(l, ix, iy, iz, zp);
+            for (int ch = 0; ch < 8; ++ch) {
+                int cx = 2 * ix + (ch & 1), cy = 2 * iy + ((ch >> 1) & 1), cz = 2 * iz + (ch >> 2);
+                double zch[3], d[3];
+                cell_centre(l + 1, cx, cy, cz, zch);
+                d[0] = zch[0] - zp[0]; d[1] = zch[1] - zp[1]; d[2] = zch[2] - zp[2];
+                orc_m2m(p, basis, U.M[l + 1] + cell_id(l + 1, cx, cy, cz) * nc, d, U.M[l] + c * nc);
+            }
+        }
+    }
+
+    /* interaction phase: M2L over the interaction lists at levels 2..depth */
+    for (int l = 2; l <= depth; ++l) {
+        int s = 1 << l;
+        int64_t nce = (int64_t)s * s * s;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t c = 0; c < nce; ++c) {
+            if (!need[l][c]) continue;
+            int ix = (int)(c % s), iy = (int)((c / s) % s), iz = (int)(c / ((int64_t)s * s));
+            double zt[3];
+            cell_centre(l, ix, iy, iz, zt);
+            int px = ix >> 1, py = iy >> 1, pz = iz >> 1;
+            for (int jz = 2 * pz - 2; jz <= 2 * pz + 3; ++jz)
+                for (int jy = 2 * py - 2; jy <= 2 * py + 3; ++jy)
+                    for (int jx = 2 * px - 2; jx <= 2 * px + 3; ++jx) {
+                        if (jx < 0 || jy < 0 || jz < 0 || jx >= s || jy >= s || jz >= s) continue;
+                        if (abs(jx - ix) <= 1 && abs(jy - iy) <= 1 && abs(jz - iz) <= 1) continue;
+                        double zs[3], r[3];
+                        cell_centre(l, jx, jy, jz, zs);
+                        r[0] = zt[0] - zs[0]; r[1] = zt[1] - zs[1]; r[2] = zt[2] - zs[2];
+                        orc_m2l(p, basis, U.M[l] + cell_id(l, jx, jy, jz) * nc, r, U.L[l] + c * nc);
+                    }
+        }
+    }
+
+    /* downward pass: L2L from level 2 to the leaves (App. C) */
+    for (int l = 3; l <= depth; ++l) {
+        int s = 1 << l;
+        int64_t nce = (int64_t)s * s * s;
+#pragma omp parallel for schedule(static)
+        for (int64_t c = 0; c < nce; ++c) {
+            if (!need[l][c]) continue;
+            int ix = (int)(c % s), iy = (int)((c / s) % s), iz = (int)(c / ((int64_t)s * s));
+            double zc[3], zp[3], d[3];
+            cell_centre(l, ix, iy, iz, zc);
+            cell_centre(l - 1, ix >> 1, iy >> 1, iz >> 1, zp);
+            d[0] = zc[0] - zp[0]; d[1] = zc[1] - zp[1]; d[2] = zc[2] - zp[2];
+            orc_l2l(p, basis, U.L[l - 1] + cell_id(l - 1, ix >> 1, iy >> 1, iz >> 1) * nc, d,
+                    U.L[l] + c * nc);
+        }
+    }
+
+    /* evaluation: L2P at leaves plus direct near field over adjacent leaves */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < ntarg; ++t) {
+        int64_t i = nsample >= 0 ? sample[t] : t;
+        int ix = leaf_coord(x[i], side), iy = leaf_coord(y[i], side), iz = leaf_coord(z[i], side);
+        double zc[3], rb[3], o[4] = {0.0, 0.0, 0.0, 0.0};
+        cell_centre(depth, ix, iy, iz, zc);
+        rb[0] = x[i] - zc[0]; rb[1] = y[i] - zc[1]; rb[2] = z[i] - zc[2];
+        if (depth >= 2) orc_l2p(p, basis, U.L[depth] + cell_id(depth, ix, iy, iz) * nc, rb, o);
+        double ph = o[0], gx = o[1], gy = o[2], gz = o[3];
+        for (int jz = iz - 1; jz <= iz + 1; ++jz)
+            for (int jy = iy - 1; jy <= iy + 1; ++jy)
+                for (int jx = ix - 1; jx <= ix + 1; ++jx) {
+                    if (jx < 0 || jy < 0 || jz < 0 || jx >= side || jy >= side || jz >= side) continue;
+                    int64_t lc = cell_id(depth, jx, jy, jz);
+                    for (int64_t a = U.leaf_start[lc]; a < U.leaf_start[lc + 1]; ++a) {
+                        int64_t j = U.order[a];
+                        if (j == i) continue;
+                        double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+                        double r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 == 0.0) continue;
+                        double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
+                        ph += q[j] * ir;
+                        gx += q[j] * dx * ir3; gy += q[j] * dy * ir3; gz += q[j] * dz * ir3;
+                    }
+                }
+        pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
+    }
+
+    for (int l = 0; l <= depth; ++l) { free(U.M[l]); free(U.L[l]); free(need[l]); }
+    free(U.M); free(U.L); free(need);
+    free(leaf); free(U.leaf_start); free(U.order);
+    return 0;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
