@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Cartesian FMM.
+
+One step = one pass of the whole hot path over one batch: uniform-octree
+build, P2M, M2M, M2L over all interaction lists (levels 2..6), L2L, L2P and
+P2P, on 4,194,304 uniform particles with equal masses, a depth-6 octree
+(262,144 leaves, 16 particles per leaf on average) and traceless tensors at
+p = 8 (the precision-form workload).  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (a 256 MiB write) before every timed step.
+
+Printed (rank 0, one JSON line): FMM particles/s of the chosen form, the
+plain FP64 GPU form's particles/s and M2L pairs/s beside it, the relative
+force error against an FP64 direct sum on sampled targets, the roofline of
+the dominant kernel (M2L), the oracle timed on the host cores, an
+end-to-end figure through fmm_evaluate_host, and SM clocks sampled during the
+timed region.
+
+  python bench.py [--gpus N --steps K --warmup W] [--form fp64|fp32]
+  python bench.py --impl reference ...      # the FP64 CPU oracle
+  python bench.py --workload m2l ...        # per-pair M2L micro-benchmark sweep
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM particles/s at 1e-4 rel force err; M2L pairs/s vs plain FP64 GPU form"
+N_PART, DEPTH, P, BASIS = 4194304, 6, 8, 1
+SEED = 3
+WORKLOAD = "uniform cube, 4,194,304 particles, equal masses 1/N, depth-6 octree (262,144 leaves), traceless p=8"
+L2_FLUSH_BYTES = 256 << 20
+NOMINAL = {"sm_count": 152, "fp64_fma_per_clk_sm": 2, "fp32_fma_per_clk_sm": 128}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def m2l_pairs_uniform(depth):
+    """Number of M2L (target, source) pairs of the uniform interaction lists."""
+    tot = 0
+    for l in range(2, depth + 1):
+        s = 1 << l
+        i = np.arange(s)
+        p = i >> 1
+        # per axis: sources j in [2p-2, 2p+3] inside the grid, per target i
+        cnt_all = np.minimum(2 * p + 3, s - 1) - np.maximum(2 * p - 2, 0) + 1
+        cnt_adj = np.minimum(i + 1, s - 1) - np.maximum(i - 1, 0) + 1
+        a3 = np.einsum("i,j,k->", cnt_all, cnt_all, cnt_all)
+        b3 = np.einsum("i,j,k->", cnt_adj, cnt_adj, cnt_adj)
+        tot += int(a3 - b3)
+    return tot
+
+
+def m2l_fma_per_pair(p, basis):
+    """FMAs of one M2L as the kernels execute it: symmetric -> C(p+6,6);
+    traceless on the reduced representative -> sum_a (2a+1)(p-a+1)^2."""
+    if basis == 0:
+        from math import comb
+        return comb(p + 6, 6)
+    return sum((2 * a + 1) * (p - a + 1) ** 2 for a in range(p + 1))
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(", ") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_reference(steps, warmup, emit=True):
+    """The FP64 oracle on the host cores: a full FMM on a 262,144-particle
+    uniform cube at the same leaf density (depth 4, 16 per leaf) and p."""
+    import oracle
+    from paper_1811_06332_gb300 import inputs
+    n, depth = 262144, 4
+    x, y, z = inputs.uniform_cube(n, SEED)
+    q = inputs.masses_equal(n)
+    times = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        oracle.fmm_uniform(x, y, z, q, depth, P, BASIS)
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+    v = n / float(np.mean(times))
+    return {"value": v, "unit": "particles/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "full oracle FMM on 262,144 uniform particles, depth 4 (16 per leaf), traceless p=8; "
+                      "same leaf density and order as the GPU workload, mean of %d run(s)" % len(times),
+            "seconds_per_run": float(np.mean(times))}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cb = cpu_reference(args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "particles/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cb["seconds_per_run"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": "particles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1811_06332_gb300 import fmm as F
+    from paper_1811_06332_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    forms = {"fp64": F.FP64, "fp32": F.FP32}
+    form = args.form
+    prec = forms[form]
+    # each rank evaluates its own independent particle set (weak scaling)
+    x, y, z = inputs.uniform_cube(N_PART, SEED + 1000 * rank)
+    q = inputs.masses_equal(N_PART)
+    X = [torch.from_numpy(a).to(dev) for a in (x, y, z, q)]
+    out = torch.empty((4, N_PART), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    plan = F.Plan(p=P, basis=BASIS, prec=prec, depth=DEPTH)
+
+    stages = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p"]
+
+    def step(ev):
+        ev[0].record(stream)
+        plan.fmm_build_tree(*X); ev[1].record(stream)
+        plan.fmm_p2m(); ev[2].record(stream)
+        plan.fmm_m2m(); ev[3].record(stream)
+        plan.fmm_m2l(); ev[4].record(stream)
+        plan.fmm_l2l(); ev[5].record(stream)
+        plan.fmm_l2p(out[0], out[1], out[2], out[3]); ev[6].record(stream)
+        plan.fmm_p2p(out[0], out[1], out[2], out[3]); ev[7].record(stream)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    wev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step(wev)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = F.kernel_launches()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            step(evs[k])
+        torch.cuda.synchronize()
+    launches = F.kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    per_stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(7)] for k in range(args.steps)])
+    step_ms = per_stage.sum(1)
+    t_ms = float(step_ms.mean())
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * N_PART / (t_ms * 1e-3)
+
+    # accuracy: relative force error against an FP64 direct sum on 4096 sampled targets
+    torch.cuda.synchronize()
+    tsel = torch.from_numpy(np.sort(np.unique((inputs.u01(SEED, 91, 4096) * N_PART).astype(np.int64)))).to(dev)
+    ref = torch.empty((4, len(tsel)), dtype=torch.float64, device=dev)
+    F.fmm_direct(X[0], X[1], X[2], X[3], ref[0], ref[1], ref[2], ref[3], targets=tsel)
+    plan.fmm_evaluate(*X, out[0], out[1], out[2], out[3])
+    torch.cuda.synchronize()
+    acc = out[1:, tsel]
+    rel_err = float(torch.sqrt(((acc - ref[1:]) ** 2).sum() / (ref[1:] ** 2).sum()).item())
+
+    m2l_ms = float(per_stage[:, 3].mean())
+    npairs = m2l_pairs_uniform(DEPTH)
+    fma = m2l_fma_per_pair(P, BASIS)
+    pk, pk_kind = peaks()
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    if prec == F.FP64:
+        peak = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
+        peak_note = "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
+    else:
+        peak = NOMINAL["sm_count"] * NOMINAL["fp32_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
+        peak_note = "FP32 ALU: 152 SMs x 128 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
+    achieved = npairs * fma * 2 / (m2l_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "m2l (levels 2..6, %d pairs per step)" % npairs,
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": peak_note, "flops_per_pair": 2 * fma,
+            "m2l_ms_per_step": m2l_ms}
+
+    # plain FP64 GPU form beside it (same workload, fewer steps)
+    fp64 = None
+    if prec != F.FP64 and not args.no_fp64:
+        p64 = F.Plan(p=P, basis=BASIS, prec=F.FP64, depth=DEPTH)
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        p64.fmm_evaluate(*X, out[0], out[1], out[2], out[3])
+        flush.fill_(2.0)
+        e0.record(stream)
+        p64.fmm_build_tree(*X); p64.fmm_p2m(); p64.fmm_m2m()
+        e1.record(stream)
+        p64.fmm_m2l()
+        e2.record(stream)
+        p64.fmm_l2l(); p64.fmm_l2p(out[0], out[1], out[2], out[3]); p64.fmm_p2p(out[0], out[1], out[2], out[3])
+        e3.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e3)
+        fp64 = {"value": N_PART / (ms * 1e-3), "m2l_pairs_per_s": npairs / (e1.elapsed_time(e2) * 1e-3),
+                "ms_per_step": ms}
+        p64.close()
+    else:
+        fp64 = {"value": value / world, "m2l_pairs_per_s": npairs / (m2l_ms * 1e-3), "ms_per_step": t_ms}
+
+    # end to end through the host entry point (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        hx = [torch.from_numpy(a).pin_memory() for a in (x, y, z, q)]
+        ho = torch.empty((4, N_PART), dtype=torch.float64).pin_memory()
+        plan.fmm_evaluate_host(*hx, ho[0], ho[1], ho[2], ho[3])
+        tms = []
+        for _ in range(max(1, min(args.steps, 5))):
+            t0 = time.perf_counter()
+            plan.fmm_evaluate_host(*hx, ho[0], ho[1], ho[2], ho[3])
+            tms.append(time.perf_counter() - t0)
+        e2e = {"value": world * N_PART / float(np.mean(tms)), "unit": "particles/s",
+               "h2d_bytes_per_step": 4 * 8 * N_PART, "d2h_bytes_per_step": 4 * 8 * N_PART,
+               "host_api": "fmm_evaluate_host"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cb = cpu_reference(1, 0)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32 (M2L, P2P) + f64"}[form],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": form, "p": P, "basis": "traceless", "depth": DEPTH,
+                   "particles_per_gpu": N_PART, "m2l_pairs": npairs, "l2": "flushed (256 MiB write) before each step"},
+        "rel_force_err": rel_err,
+        "stage_ms": {s: float(per_stage[:, i].mean()) for i, s in enumerate(stages)},
+        "m2l_pairs_per_s": world * npairs / (m2l_ms * 1e-3),
+        "fp64_form": fp64,
+        "vs_fp64_form": value / world / fp64["value"],
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "peaks_source": pk_kind,
+    }
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_m2l_sweep(args):
+    """Per-pair M2L micro-benchmark: 2^20 independent side-1 cell pairs,
+    offsets uniform over the 316 well-separated integer vectors, multipoles
+    from P2M of 16 unit-mass particles per cell (GPU P2M), D on the fly."""
+    import torch
+
+    from paper_1811_06332_gb300 import fmm as F
+    from paper_1811_06332_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    n = 1 << 20
+    r, src, q = inputs.m2l_pairs(n, 2)
+    R = torch.from_numpy(r).to(dev)
+    per = src.shape[1]
+    start = torch.arange(0, (n + 1) * per, per, device=dev, dtype=torch.int64)
+    xs = [torch.from_numpy(np.ascontiguousarray(src[d].T.reshape(-1))).to(dev) for d in range(3)]
+    qs = torch.from_numpy(np.ascontiguousarray(q.T.reshape(-1))).to(dev)
+    zero = torch.zeros((3, n), device=dev, dtype=torch.float64)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ps = [int(v) for v in args.orders.split(",")]
+    for p in ps:
+        for basis in (0, 1):
+            nc = F.ncoef(p, basis)
+            M = torch.empty((nc, n), device=dev, dtype=torch.float64)
+            F.fmm_op_p2m(p, basis, start, xs[0], xs[1], xs[2], qs, zero, M)
+            res = {}
+            for prec, dt in ((F.FP64, torch.float64), (F.FP32, torch.float32)):
+                Mi = M.to(dt)
+                L = torch.empty((nc, n), device=dev, dtype=dt)
+                for _ in range(args.warmup):
+                    F.fmm_op_m2l(p, basis, prec, Mi, R, L)
+                times = []
+                for _ in range(args.steps):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    F.fmm_op_m2l(p, basis, prec, Mi, R, L)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = float(np.median(times))
+                s = 8 if prec == F.FP64 else 4
+                res["fp64" if prec == F.FP64 else "fp32"] = {
+                    "pairs_per_s": n / (ms * 1e-3), "ms": ms,
+                    "GB_per_s": n * (2 * nc * s + 24) / (ms * 1e-3) / 1e9}
+            print(json.dumps({"workload": "m2l per-pair, 2^20 pairs", "p": p,
+                              "basis": "sym" if basis == 0 else "traceless", **res,
+                              "fp32_vs_fp64": res["fp32"]["pairs_per_s"] / res["fp64"]["pairs_per_s"]}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l"])
+    ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and args.workload == "fmm":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    import __graft_entry__ as g
+    g.build()
+    if args.workload == "m2l":
+        return run_m2l_sweep(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * fmm_gb300.h -- C-ABI of the GB300 Cartesian fast multipole library for the
+ * 1/r kernel (Coles & Bieri, "An Optimizing Symbolic Algebra Approach for
+ * Generating Fast Multipole Method Operators", arXiv:1811.06332).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Multi-indices follow App. D: n = (nx,ny,nz), |n| = nx+ny+nz,
+ *    n! = nx!ny!nz!, r^n = x^nx y^ny z^nz.
+ *  - Coefficient storage (App. A compressed form; App. E table of sizes):
+ *      FMM_BASIS_SYM        C(p+3,3) components, ranks 0..p concatenated,
+ *                           inside a rank descending nx then descending ny;
+ *      FMM_BASIS_TRACELESS  (p+1)^2 independent components (nz <= 1) per
+ *                           polytensor, inside rank j ordered
+ *                           (j,0,0),(j-1,1,0),...,(0,j,0),(j-1,0,1),...,(0,j-1,1);
+ *                           dependent components follow from the trace
+ *                           condition A_{k+2ez} = -A_{k+2ex} - A_{k+2ey}
+ *                           (App. B).
+ *    fmm_ncoef(p, basis) returns the count.
+ *  - Batched arrays are structure-of-arrays, coefficient-major:
+ *    element (c, i) of an [ncoef][n] array lives at index c*n + i.
+ *    Vectors are [3][n]: x components, then y, then z.
+ *  - Normalisation of Sec. 2.1: M_n = sum_a q_a (-r_a)^n, M2L weights 1/m!,
+ *    L2L weights delta^k/k!, L2P reads L at the particle.
+ *  - Potentials and accelerations returned by fmm_l2p/fmm_p2p/fmm_evaluate
+ *    use the astrophysical sign that Sec. 2.1 prescribes for gravity:
+ *    pot_i = -sum_{j!=i} q_j/|x_i - x_j|,
+ *    acc_i = sum_{j!=i} q_j (x_j - x_i)/|x_i - x_j|^3  (= +grad Phi of the paper).
+ *    fmm_op_l2p returns the paper's own positive Phi and grad Phi.
+ *  - Pointers: every array argument is a DEVICE pointer unless the entry
+ *    point's name ends in _host.  The caller owns its inputs and outputs; a
+ *    plan owns everything it allocates.  Work is queued on `stream` (a
+ *    cudaStream_t passed as void*, NULL = legacy default stream) and is
+ *    asynchronous unless stated otherwise.
+ *  - Errors: every int-returning call returns an fmm_status.  Arguments are
+ *    validated before any launch; nothing is thrown across the ABI.  The
+ *    text of the last error is returned by fmm_last_error(plan), or by
+ *    fmm_last_error(NULL) for the plan-less operator calls (thread-local).
+ *  - Threading: a plan is used by one host thread at a time.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = -1,         /* invalid argument (size, pointer, p, basis) */
+    FMM_ERR_CUDA = -2,        /* a CUDA call failed; see fmm_last_error     */
+    FMM_ERR_OOM = -3,         /* device allocation failed                   */
+    FMM_ERR_STATE = -4,       /* call made before fmm_build_tree            */
+    FMM_ERR_TIMEOUT = -5,     /* a bounded device wait gave up              */
+    FMM_ERR_UNSUPPORTED = -6  /* valid but not implemented combination      */
+} fmm_status;
+
+typedef enum { FMM_BASIS_SYM = 0, FMM_BASIS_TRACELESS = 1 } fmm_basis;
+
+typedef enum {
+    FMM_FP64 = 0,        /* every operator in FP64                                     */
+    FMM_FP32 = 1,        /* M2L and P2P in FP32 (FP64 tree, P2M, M2M, L2L, L2P)          */
+    FMM_GEMM_TF32X3 = 2, /* M2L as offset-grouped tensor-core GEMMs, TF32 hi/lo, 3 passes */
+    FMM_GEMM_BF16X3 = 3  /* M2L as offset-grouped tensor-core GEMMs, BF16 hi/lo, 3 passes */
+} fmm_precision;
+
+typedef struct {
+    int p;                 /* expansion order, 0..10 (Eq. phi expansion, App. B)      */
+    int basis;             /* fmm_basis                                                */
+    int prec;              /* fmm_precision                                            */
+    int adaptive;          /* 0: uniform octree of depth `depth` over [0,1)^3          */
+    int depth;             /* uniform octree depth (leaves = 8^depth), 0..10           */
+    int max_leaf;          /* adaptive trees: maximum particles per leaf               */
+    double theta;          /* adaptive trees: opening parameter of the MAC (App. C)    */
+    int learned_p;         /* reserved: per-interaction order selection                */
+    double target_rel_err; /* reserved: target relative force error                    */
+    int use_graph;         /* 1: replay fmm_evaluate from a captured CUDA graph        */
+} fmm_config;
+
+typedef struct fmm_plan fmm_plan;
+
+/* Number of stored coefficients of an order-p polytensor: C(p+3,3) for
+ * FMM_BASIS_SYM, (p+1)^2 for FMM_BASIS_TRACELESS (App. E table).  Returns
+ * FMM_ERR_ARG for p outside 0..10 or an unknown basis. */
+int fmm_ncoef(int p, int basis);
+
+/* ---------------------------------------------------------------------------
+ * Plan-based FMM (App. C): tree, upward pass, interaction phase, downward
+ * pass, near field.  Uniform octree over the unit cube: a particle belongs to
+ * leaf i_d = min(floor(x_d 2^depth), 2^depth - 1) (coordinates outside
+ * [0,1) are clamped into the boundary leaves); expansion centres are cell
+ * centres (App. C); same-level cells at Chebyshev index distance >= 2 are
+ * well separated, M2L runs over the children of the parent's neighbours
+ * that are not adjacent (levels 2..depth) and adjacent leaves are summed
+ * directly.
+ * ------------------------------------------------------------------------- */
+
+/* Creates a plan.  Validates cfg (p in 0..10, basis, prec, depth in 0..10,
+ * adaptive == 0) and returns FMM_ERR_ARG / FMM_ERR_UNSUPPORTED otherwise.
+ * *out receives the plan (NULL on failure).  Allocates no particle storage. */
+int fmm_create(const fmm_config* cfg, fmm_plan** out);
+
+/* Destroys a plan and frees everything it owns.  NULL is ignored.  The
+ * caller must make sure no work of the plan is still running. */
+void fmm_destroy(fmm_plan* plan);
+
+/* Text of the last error of `plan` (or of the calling thread's last
+ * plan-less call when plan == NULL).  Valid until the next call. */
+const char* fmm_last_error(const fmm_plan* plan);
+
+/* Sorts the n particles (device arrays x, y, z, q of length n, caller order)
+ * into the leaves of the octree, stably by original index, and prepares the
+ * interaction lists (App. C).  The plan keeps its own sorted copies; the
+ * caller's arrays may be reused once the stream reaches this point.
+ * n may be 0.  (Re)allocates plan storage when n or the tree changes. */
+int fmm_build_tree(fmm_plan* plan, int64_t n, const double* x, const double* y,
+                   const double* z, const double* q, void* stream);
+
+/* P2M at every leaf (Eq. P2M, Sec. 2.1) about the leaf centre. */
+int fmm_p2m(fmm_plan* plan, void* stream);
+/* M2M bottom-up (Eq. M2M / M2M part 2, Sec. 2.1), delta = z_child - z_parent. */
+int fmm_m2m(fmm_plan* plan, void* stream);
+/* M2L over the interaction lists of levels 2..depth (Eq. M2L, Sec. 2.1),
+ * r = z_target - z_source, in the plan's precision form. */
+int fmm_m2l(fmm_plan* plan, void* stream);
+/* L2L top-down (Eq. L2L, Sec. 2.1), delta = z_child - z_parent. */
+int fmm_l2l(fmm_plan* plan, void* stream);
+/* L2P (Eq. L2P, Sec. 2.1): OVERWRITES pot, ax, ay, az (device, length n,
+ * caller order) with the far-field potential and acceleration. */
+int fmm_l2p(fmm_plan* plan, double* pot, double* ax, double* ay, double* az, void* stream);
+/* Near field (App. C direct sum over adjacent leaves, self excluded):
+ * ADDS into pot, ax, ay, az (device, length n, caller order). */
+int fmm_p2p(fmm_plan* plan, double* pot, double* ax, double* ay, double* az, void* stream);
+
+/* fmm_build_tree + p2m + m2m + m2l + l2l + l2p + p2p on `stream`.
+ * All arrays are device arrays of length n in caller order; outputs are
+ * overwritten.  With cfg.use_graph the sequence is captured into a CUDA
+ * graph on the first call for a given (n, input/output pointers) and
+ * replayed afterwards. */
+int fmm_evaluate(fmm_plan* plan, int64_t n, const double* x, const double* y,
+                 const double* z, const double* q, double* pot, double* ax,
+                 double* ay, double* az, void* stream);
+
+/* fmm_evaluate on HOST arrays (length n, caller order): copies the inputs to
+ * the device, evaluates, copies the outputs back and waits for the stream.
+ * Uses plan-owned staging buffers; page-locked host memory gives full copy
+ * speed but is not required.  Synchronous. */
+int fmm_evaluate_host(fmm_plan* plan, int64_t n, const double* x, const double* y,
+                      const double* z, const double* q, double* pot, double* ax,
+                      double* ay, double* az, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Operator-level batched entry points (independent items, physical units).
+ * ------------------------------------------------------------------------- */
+
+/* D-tensor D_k(r) = grad^k |r|^{-1} for all |k| <= p (Eq. traceless grad,
+ * App. A), full symmetric storage.  r: [3][n] doubles; D: [C(p+3,3)][n] of
+ * doubles (prec FMM_FP64) or floats (FMM_FP32).  r must be nonzero. */
+int fmm_op_dtensor(int p, int prec, int64_t n, const double* r, void* D, void* stream);
+
+/* P2M (Eq. P2M, Sec. 2.1; traceless: Mbar = D[M] per rank, Eq. Detracer of
+ * App. A) for ncell particle groups: particles of group c are
+ * start[c] .. start[c+1]-1 of x, y, z, q (device, doubles); start is an
+ * int64 device array of ncell+1 nondecreasing offsets; centre: [3][ncell];
+ * M: [ncoef][ncell] doubles, OVERWRITTEN. */
+int fmm_op_p2m(int p, int basis, int64_t ncell, const int64_t* start, const double* x,
+               const double* y, const double* z, const double* q, const double* centre,
+               double* M, void* stream);
+
+/* M2M (Eq. M2M / M2M part 2, Sec. 2.1): Mp[:,i] += shift of Mc[:,i] by
+ * delta[:,i] = z_child - z_parent (traceless: followed by D[]).  Mc, Mp:
+ * [ncoef][n] doubles (distinct arrays); delta: [3][n]. */
+int fmm_op_m2m(int p, int basis, int64_t n, const double* Mc, const double* delta,
+               double* Mp, void* stream);
+
+/* M2L (Eq. M2L, Sec. 2.1) for n independent pairs with the D-tensor computed
+ * on the fly: L[:,i] (+)= sum_{|m|<=p-|n|} M_m[:,i]/m! D_{n+m}(r[:,i]).
+ * prec FMM_FP64: M, L are doubles; FMM_FP32: floats.  r: [3][n] doubles,
+ * r = z_target - z_source, nonzero.  accumulate = 0 overwrites L. */
+int fmm_op_m2l(int p, int basis, int prec, int64_t n, const void* M, const double* r,
+               void* L, int accumulate, void* stream);
+
+/* L2L (Eq. L2L, Sec. 2.1): Lc[:,i] += shift of Lp[:,i] by
+ * delta[:,i] = z_child - z_parent.  [ncoef][n] doubles, distinct arrays. */
+int fmm_op_l2l(int p, int basis, int64_t n, const double* Lp, const double* delta,
+               double* Lc, void* stream);
+
+/* L2P (Eq. L2P, Sec. 2.1): out[0][i] = Phi, out[1..3][i] = grad Phi at
+ * offset rb[:,i] from the expansion centre (the paper's positive sign).
+ * L: [ncoef][n]; rb: [3][n]; out: [4][n], OVERWRITTEN. */
+int fmm_op_l2p(int p, int basis, int64_t n, const double* L, const double* rb,
+               double* out, void* stream);
+
+/* FP64 direct sum (Eq. PhiAB, App. B) of all n sources onto nt targets
+ * (indices into the sources, int64 device array; NULL = all n, nt ignored),
+ * with the astrophysical sign convention above.  Outputs have nt entries. */
+int fmm_direct(int64_t n, const double* x, const double* y, const double* z,
+               const double* q, int64_t nt, const int64_t* targets, double* pot,
+               double* ax, double* ay, double* az, void* stream);
+
+/* Number of kernels this library launched since it was loaded (all plans and
+ * operator calls), counted on the host at each launch. */
+int64_t fmm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_GB300_H */

@@ -1,0 +1,528 @@
+// C-ABI of the GB300 Cartesian FMM library (declared in include/fmm_gb300.h):
+// argument validation, the plan (tree, expansions, operator matrices), the
+// FMM pipeline of App. C, and the operator-level batched entry points.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fmm_gb300.h"
+#include "fmm_internal.h"
+
+namespace fmm {
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace fmm
+
+using namespace fmm;
+
+static thread_local std::string t_err;
+
+struct fmm_plan {
+    fmm_config cfg;
+    int dev = 0;
+    std::string err;
+    int nc = 0, ns = 0;
+    // tree
+    int64_t n = -1;
+    int depth = 0;
+    int64_t nleaf = 0;
+    bool built = false;
+    double *xs = nullptr, *ys = nullptr, *zs = nullptr, *qs = nullptr;
+    int* perm = nullptr;
+    int* start = nullptr;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // expansions, levels 0..depth, each [nc][8^l]
+    double* Mbuf = nullptr;
+    double* Lbuf = nullptr;
+    int64_t lvl_off[FMM_PMAX + 2];
+    // operator matrices (scaled units)
+    double* W = nullptr;     // 8 x nc x nc  (M2M)
+    double* V = nullptr;     // 8 x nc x nc  (L2L)
+    double* Dtab = nullptr;  // 343 x ns     (M2L, integer offsets in cell units)
+    float* K32 = nullptr;    // 343 x kstride packed FP32 M2L matrices (FMM_FP32)
+    float* M32 = nullptr;    // FP32 copy of the multipoles (FMM_FP32)
+    int kst = 0;
+    // host-call staging
+    double* stage = nullptr;
+    int64_t stage_n = 0;
+};
+
+static int fail_plan(fmm_plan* pl, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (pl) pl->err = buf;
+    t_err = buf;
+    return code;
+}
+#define FAIL(code, ...) return fail_plan(pl, code, __VA_ARGS__)
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) FAIL(FMM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+#define CKLAUNCH()                                                                                    \
+    do {                                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                                          \
+        if (e_ != cudaSuccess) FAIL(FMM_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+static int tables_for_current(fmm_plan* pl, int* dev_out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const int rc = ensure_tables(dev);
+    if (rc == -3) FAIL(FMM_ERR_OOM, "allocating constant tables failed");
+    if (rc != 0) FAIL(FMM_ERR_CUDA, "uploading constant tables failed");
+    *dev_out = dev;
+    return FMM_OK;
+}
+
+typedef int (*pair_launch_t)(int, int, int64_t, const void*, const double*, void*, int, cudaStream_t);
+typedef int (*dten_launch_t)(int, int64_t, const double*, void*, cudaStream_t);
+typedef int (*dtab_launch_t)(int, const double*, double*, cudaStream_t);
+static const pair_launch_t k_pair[FMM_PMAX + 1] = {
+    launch_m2l_pair_p0, launch_m2l_pair_p1, launch_m2l_pair_p2, launch_m2l_pair_p3,
+    launch_m2l_pair_p4, launch_m2l_pair_p5, launch_m2l_pair_p6, launch_m2l_pair_p7,
+    launch_m2l_pair_p8, launch_m2l_pair_p9, launch_m2l_pair_p10};
+static const dten_launch_t k_dten[FMM_PMAX + 1] = {
+    launch_dtensor_p0, launch_dtensor_p1, launch_dtensor_p2, launch_dtensor_p3,
+    launch_dtensor_p4, launch_dtensor_p5, launch_dtensor_p6, launch_dtensor_p7,
+    launch_dtensor_p8, launch_dtensor_p9, launch_dtensor_p10};
+static const dtab_launch_t k_dtab[FMM_PMAX + 1] = {
+    launch_dtable_p0, launch_dtable_p1, launch_dtable_p2, launch_dtable_p3,
+    launch_dtable_p4, launch_dtable_p5, launch_dtable_p6, launch_dtable_p7,
+    launch_dtable_p8, launch_dtable_p9, launch_dtable_p10};
+
+static inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+extern "C" {
+
+int fmm_ncoef(int p, int basis) {
+    if (p < 0 || p > FMM_PMAX || (basis != 0 && basis != 1)) return FMM_ERR_ARG;
+    return ncoef_of(p, basis);
+}
+
+const char* fmm_last_error(const fmm_plan* plan) { return plan ? plan->err.c_str() : t_err.c_str(); }
+
+int64_t fmm_kernel_launches(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// operator-level entry points
+// ---------------------------------------------------------------------------
+int fmm_op_dtensor(int p, int prec, int64_t n, const double* r, void* D, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (prec != FMM_FP64 && prec != FMM_FP32) FAIL(FMM_ERR_ARG, "prec must be FMM_FP64 or FMM_FP32");
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n > 0 && (!r || !D)) FAIL(FMM_ERR_ARG, "null array");
+    k_dten[p](prec, n, r, D, S(stream));
+    if (n > 0) count_launch();
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_op_m2l(int p, int basis, int prec, int64_t n, const void* M, const double* r, void* L, int accumulate,
+               void* stream) {
+    fmm_plan* pl = nullptr;
+    if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (prec != FMM_FP64 && prec != FMM_FP32) FAIL(FMM_ERR_ARG, "prec must be FMM_FP64 or FMM_FP32");
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n > 0 && (!M || !r || !L)) FAIL(FMM_ERR_ARG, "null array");
+    if (k_pair[p](basis, prec, n, M, r, L, accumulate, S(stream)) != 0) FAIL(FMM_ERR_ARG, "bad combination");
+    if (n > 0) count_launch();
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_op_p2m(int p, int basis, int64_t ncell, const int64_t* start, const double* x, const double* y,
+               const double* z, const double* q, const double* centre, double* M, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (ncell < 0) FAIL(FMM_ERR_ARG, "ncell < 0");
+    if (ncell > 0 && (!start || !x || !y || !z || !q || !centre || !M)) FAIL(FMM_ERR_ARG, "null array");
+    int dev;
+    if (int rc = tables_for_current(pl, &dev)) return rc;
+    launch_p2m(p, basis, 0, ncell, start, nullptr, x, y, z, q, centre, 0, 1.0, M, ncell, g_tab[dev], S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_op_m2m(int p, int basis, int64_t n, const double* Mc, const double* delta, double* Mp, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n > 0 && (!Mc || !delta || !Mp)) FAIL(FMM_ERR_ARG, "null array");
+    if (n > 0 && Mc == Mp) FAIL(FMM_ERR_ARG, "Mc and Mp must be distinct");
+    int dev;
+    if (int rc = tables_for_current(pl, &dev)) return rc;
+    launch_m2m_general(p, basis, n, Mc, delta, Mp, g_tab[dev], S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_op_l2l(int p, int basis, int64_t n, const double* Lp, const double* delta, double* Lc, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n > 0 && (!Lp || !delta || !Lc)) FAIL(FMM_ERR_ARG, "null array");
+    if (n > 0 && Lp == Lc) FAIL(FMM_ERR_ARG, "Lp and Lc must be distinct");
+    int dev;
+    if (int rc = tables_for_current(pl, &dev)) return rc;
+    launch_l2l_general(p, basis, n, Lp, delta, Lc, g_tab[dev], S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_op_l2p(int p, int basis, int64_t n, const double* L, const double* rb, double* out, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n > 0 && (!L || !rb || !out)) FAIL(FMM_ERR_ARG, "null array");
+    int dev;
+    if (int rc = tables_for_current(pl, &dev)) return rc;
+    launch_l2p_general(p, basis, n, L, rb, out, g_tab[dev], S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_direct(int64_t n, const double* x, const double* y, const double* z, const double* q, int64_t nt,
+               const int64_t* targets, double* pot, double* ax, double* ay, double* az, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (!targets) nt = n;
+    if (nt < 0) FAIL(FMM_ERR_ARG, "nt < 0");
+    if (n > 0 && (!x || !y || !z || !q)) FAIL(FMM_ERR_ARG, "null source array");
+    if (nt > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
+    launch_direct(n, x, y, z, q, nt, targets, pot, ax, ay, az, S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+static void free_tree(fmm_plan* pl) {
+    cudaFree(pl->xs); cudaFree(pl->ys); cudaFree(pl->zs); cudaFree(pl->qs);
+    cudaFree(pl->perm); cudaFree(pl->start); cudaFree(pl->scratch);
+    cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32);
+    pl->M32 = nullptr;
+    pl->xs = pl->ys = pl->zs = pl->qs = nullptr;
+    pl->perm = pl->start = nullptr;
+    pl->scratch = nullptr;
+    pl->Mbuf = pl->Lbuf = nullptr;
+    pl->n = -1;
+    pl->built = false;
+}
+
+// Translation matrices in scaled units (level independent):
+//   M2M  Mt_n(parent) = sum_k n!/(k!(n-k)!) (-d)^(n-k) 2^-|k| Mt_k(child)
+//   L2L  Lt_n(child)  = sum_k d^k/k! 2^-(|n|+1) Lt_(n+k)(parent)
+// d = (z_child - z_parent)/h_parent = (+-1/4, +-1/4, +-1/4) for child class c
+// (bit 0: x, bit 1: y, bit 2: z).  Traceless: M2M acts on the reduced
+// representative (embed nz<=1 comps, shift, reduce), L2L on independent
+// components (expand by the trace condition, shift, keep independent rows).
+static void build_translation(int p, int basis, std::vector<double>& W, std::vector<double>& V) {
+    const int ns = ns_of(p), nc = ncoef_of(p, basis);
+    std::vector<double> Sm((size_t)ns * ns), Vs((size_t)ns * ns);
+    W.assign((size_t)8 * nc * nc, 0.0);
+    V.assign((size_t)8 * nc * nc, 0.0);
+    auto fact = [](int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; };
+    auto binom = [&](int a, int b) { return fact(a) / (fact(b) * fact(a - b)); };
+    auto ipow = [](double v, int e) { double r = 1; for (int i = 0; i < e; ++i) r *= v; return r; };
+    for (int c = 0; c < 8; ++c) {
+        const double d[3] = {(c & 1) ? 0.25 : -0.25, (c & 2) ? 0.25 : -0.25, (c & 4) ? 0.25 : -0.25};
+        for (int a = 0; a < ns; ++a) {
+            const unsigned char* n = fmm_sym_idx[a];
+            for (int b = 0; b < ns; ++b) {
+                const unsigned char* k = fmm_sym_idx[b];
+                double s = 0.0, v = 0.0;
+                if (k[0] <= n[0] && k[1] <= n[1] && k[2] <= n[2]) {
+                    s = std::ldexp(1.0, -(k[0] + k[1] + k[2]));
+                    for (int e = 0; e < 3; ++e) s *= binom(n[e], k[e]) * ipow(-d[e], n[e] - k[e]);
+                }
+                // Vs[a][b]: row n, column j = b with j >= n
+                const unsigned char* j = k;
+                if (j[0] >= n[0] && j[1] >= n[1] && j[2] >= n[2]) {
+                    v = std::ldexp(1.0, -(n[0] + n[1] + n[2] + 1));
+                    for (int e = 0; e < 3; ++e) v *= ipow(d[e], j[e] - n[e]) / fact(j[e] - n[e]);
+                }
+                Sm[(size_t)a * ns + b] = s;
+                Vs[(size_t)a * ns + b] = v;
+            }
+        }
+        double* Wc = W.data() + (size_t)c * nc * nc;
+        double* Vc = V.data() + (size_t)c * nc * nc;
+        if (!basis) {
+            std::memcpy(Wc, Sm.data(), sizeof(double) * ns * ns);
+            std::memcpy(Vc, Vs.data(), sizeof(double) * ns * ns);
+            continue;
+        }
+        for (int to = 0; to < nc; ++to) {
+            const unsigned char* no = fmm_tl_idx[to];
+            const int jo = no[0] + no[1] + no[2];
+            const int cols = (jo + 1) * (jo + 2) / 2;
+            const double* R = fmm_reduce_val + fmm_reduce_off[jo] + (size_t)(to - jo * jo) * cols;
+            for (int ti = 0; ti < nc; ++ti) {
+                const unsigned char* ni = fmm_tl_idx[ti];
+                const int ci = pos_sym(ni[0], ni[1], ni[2]);
+                // M2M: reduce o shift o embed
+                double w = 0.0;
+                for (int s = 0; s < cols; ++s) w += R[s] * Sm[(size_t)(ns_of(jo - 1) + s) * ns + ci];
+                Wc[(size_t)to * nc + ti] = w;
+                // L2L: keep row o shift o expand
+                const int ji = ni[0] + ni[1] + ni[2];
+                const int ro = pos_sym(no[0], no[1], no[2]);
+                const int rcols = (ji + 1) * (ji + 2) / 2;
+                double v = 0.0;
+                for (int s = 0; s < rcols; ++s) {
+                    const double* Ex = fmm_expand_val + fmm_expand_off[ji] + (size_t)s * (2 * ji + 1);
+                    v += Vs[(size_t)ro * ns + ns_of(ji - 1) + s] * Ex[ti - ji * ji];
+                }
+                Vc[(size_t)to * nc + ti] = v;
+            }
+        }
+    }
+}
+
+int fmm_create(const fmm_config* cfg, fmm_plan** out) {
+    fmm_plan* pl = nullptr;
+    if (!out) FAIL(FMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) FAIL(FMM_ERR_ARG, "cfg is NULL");
+    if (cfg->p < 0 || cfg->p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", cfg->p, FMM_PMAX);
+    if (cfg->basis != 0 && cfg->basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", cfg->basis);
+    if (cfg->prec < FMM_FP64 || cfg->prec > FMM_GEMM_BF16X3) FAIL(FMM_ERR_ARG, "unknown precision %d", cfg->prec);
+    if (cfg->adaptive) FAIL(FMM_ERR_UNSUPPORTED, "adaptive trees are not available in this build");
+    if (cfg->depth < 0 || cfg->depth > 9) FAIL(FMM_ERR_ARG, "depth=%d outside 0..9", cfg->depth);
+    if (cfg->prec >= FMM_GEMM_TF32X3) FAIL(FMM_ERR_UNSUPPORTED, "tensor-core M2L forms are not available yet");
+    pl = new fmm_plan();
+    pl->cfg = *cfg;
+    pl->depth = cfg->depth;
+    pl->nleaf = (int64_t)1 << (3 * cfg->depth);
+    pl->nc = ncoef_of(cfg->p, cfg->basis);
+    pl->ns = ns_of(cfg->p);
+    int dev;
+    if (int rc = tables_for_current(pl, &dev)) { fmm_destroy(pl); return rc; }
+    pl->dev = dev;
+    std::vector<double> W, V;
+    build_translation(cfg->p, cfg->basis, W, V);
+    const size_t mb = W.size() * sizeof(double);
+    if (cudaMalloc(&pl->W, mb) != cudaSuccess || cudaMalloc(&pl->V, mb) != cudaSuccess ||
+        cudaMalloc(&pl->Dtab, (size_t)343 * pl->ns * sizeof(double)) != cudaSuccess) {
+        fmm_destroy(pl);
+        return fail_plan(nullptr, FMM_ERR_OOM, "allocating operator matrices failed");
+    }
+    std::vector<double> offs(3 * 343);
+    for (int o = 0; o < 343; ++o) {
+        const int rx = o % 7 - 3, ry = (o / 7) % 7 - 3, rz = o / 49 - 3;
+        const bool near = rx >= -1 && rx <= 1 && ry >= -1 && ry <= 1 && rz >= -1 && rz <= 1;
+        offs[3 * o] = near ? 10.0 : rx;  // adjacent offsets are never used; keep them finite
+        offs[3 * o + 1] = near ? 10.0 : ry;
+        offs[3 * o + 2] = near ? 10.0 : rz;
+    }
+    double* doffs = nullptr;
+    bool ok = cudaMemcpy(pl->W, W.data(), mb, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(pl->V, V.data(), mb, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMalloc(&doffs, offs.size() * sizeof(double)) == cudaSuccess &&
+              cudaMemcpy(doffs, offs.data(), offs.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+        k_dtab[cfg->p](343, doffs, pl->Dtab, 0);
+        count_launch();
+        ok = cudaDeviceSynchronize() == cudaSuccess;
+    }
+    cudaFree(doffs);
+    if (ok && cfg->prec == FMM_FP32) {
+        pl->kst = grouped_kstride(cfg->p, cfg->basis);
+        const int cap = pl->kst;
+        std::vector<unsigned char> ent((size_t)6 * cap);
+        unsigned char* dent = nullptr;
+        ok = grouped_entries(cfg->p, cfg->basis, ent.data(), cap) >= 0 &&
+             cudaMalloc(&dent, ent.size()) == cudaSuccess &&
+             cudaMemcpy(dent, ent.data(), ent.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMalloc(&pl->K32, (size_t)343 * pl->kst * sizeof(float)) == cudaSuccess;
+        if (ok) {
+            launch_build_ktab(cfg->p, cfg->basis, pl->kst, dent, pl->Dtab, pl->K32, 0);
+            ok = cudaDeviceSynchronize() == cudaSuccess;
+        }
+        cudaFree(dent);
+    }
+    if (!ok) {
+        fmm_destroy(pl);
+        return fail_plan(nullptr, FMM_ERR_CUDA, "plan set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    *out = pl;
+    return FMM_OK;
+}
+
+void fmm_destroy(fmm_plan* pl) {
+    if (!pl) return;
+    free_tree(pl);
+    cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32);
+    delete pl;
+}
+
+int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, const double* z, const double* q,
+                   void* stream) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (n < 0 || n > (int64_t)0x7fffffff) FAIL(FMM_ERR_ARG, "n=%lld outside 0..2^31-1", (long long)n);
+    if (n > 0 && (!x || !y || !z || !q)) FAIL(FMM_ERR_ARG, "null particle array");
+    if (n != pl->n) {
+        free_tree(pl);
+        const int64_t nn = n > 0 ? n : 1;
+        const int nc = pl->nc;
+        int64_t tot = 0;
+        for (int l = 0; l <= pl->depth; ++l) { pl->lvl_off[l] = tot; tot += (int64_t)nc << (3 * l); }
+        pl->scratch_bytes = tree_scratch_bytes(nn, pl->nleaf);
+        if (cudaMalloc(&pl->xs, nn * 8) != cudaSuccess || cudaMalloc(&pl->ys, nn * 8) != cudaSuccess ||
+            cudaMalloc(&pl->zs, nn * 8) != cudaSuccess || cudaMalloc(&pl->qs, nn * 8) != cudaSuccess ||
+            cudaMalloc(&pl->perm, nn * 4) != cudaSuccess ||
+            cudaMalloc(&pl->start, (pl->nleaf + 1) * 4) != cudaSuccess ||
+            cudaMalloc(&pl->scratch, pl->scratch_bytes) != cudaSuccess ||
+            cudaMalloc(&pl->Mbuf, tot * 8) != cudaSuccess || cudaMalloc(&pl->Lbuf, tot * 8) != cudaSuccess ||
+            (pl->cfg.prec == FMM_FP32 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess)) {
+            cudaGetLastError();
+            free_tree(pl);
+            FAIL(FMM_ERR_OOM, "allocating tree storage for n=%lld failed", (long long)n);
+        }
+        pl->n = n;
+    }
+    if (launch_uniform_tree(n, pl->depth, x, y, z, q, pl->xs, pl->ys, pl->zs, pl->qs, pl->perm, pl->start,
+                            pl->scratch, S(stream)) != 0)
+        FAIL(FMM_ERR_CUDA, "tree build failed: %s", cudaGetErrorString(cudaGetLastError()));
+    CKLAUNCH();
+    pl->built = true;
+    return FMM_OK;
+}
+
+static double* Mlev(fmm_plan* pl, int l) { return pl->Mbuf + pl->lvl_off[l]; }
+static double* Llev(fmm_plan* pl, int l) { return pl->Lbuf + pl->lvl_off[l]; }
+
+#define NEED_TREE() \
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL"); \
+    if (!pl->built) FAIL(FMM_ERR_STATE, "fmm_build_tree has not been called")
+
+int fmm_p2m(fmm_plan* pl, void* stream) {
+    NEED_TREE();
+    const int d = pl->depth;
+    launch_p2m(pl->cfg.p, pl->cfg.basis, 1, pl->nleaf, nullptr, pl->start, pl->xs, pl->ys, pl->zs, pl->qs,
+               nullptr, d, std::ldexp(1.0, d), Mlev(pl, d), pl->nleaf, g_tab[pl->dev], S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_m2m(fmm_plan* pl, void* stream) {
+    NEED_TREE();
+    for (int l = pl->depth - 1; l >= 2; --l)
+        launch_m2m_level(pl->cfg.p, pl->cfg.basis, l, pl->W, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
+                         Mlev(pl, l), (int64_t)1 << (3 * l), S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_m2l(fmm_plan* pl, void* stream) {
+    NEED_TREE();
+    if (pl->cfg.prec == FMM_FP32 && pl->depth >= 2) {
+        const int64_t b = pl->lvl_off[2], e = pl->lvl_off[pl->depth] + ((int64_t)pl->nc << (3 * pl->depth));
+        launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
+        for (int l = 2; l <= pl->depth; ++l) {
+            const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
+                                             pl->K32, (int64_t)1 << (3 * l), S(stream));
+            for (int k = 0; k < parts; ++k) count_launch();
+        }
+        CKLAUNCH();
+        return FMM_OK;
+    }
+    for (int l = 2; l <= pl->depth; ++l)
+        launch_m2l_fp64_level(pl->cfg.p, pl->cfg.basis, l, pl->Dtab, Mlev(pl, l), Llev(pl, l),
+                              (int64_t)1 << (3 * l), S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_l2l(fmm_plan* pl, void* stream) {
+    NEED_TREE();
+    for (int l = 2; l < pl->depth; ++l)
+        launch_l2l_level(pl->cfg.p, pl->cfg.basis, l, pl->V, Llev(pl, l), (int64_t)1 << (3 * l), Llev(pl, l + 1),
+                         (int64_t)1 << (3 * (l + 1)), S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void* stream) {
+    NEED_TREE();
+    if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
+    if (pl->depth >= 2)
+        launch_l2p_leaf(pl->cfg.p, pl->cfg.basis, pl->depth, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs,
+                        pl->perm, Llev(pl, pl->depth), g_tab[pl->dev], pot, ax, ay, az, S(stream));
+    else
+        launch_zero4(pl->n, pot, ax, ay, az, S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void* stream) {
+    NEED_TREE();
+    if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
+    launch_p2p_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->depth, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs,
+                    pl->qs, pl->perm, pot, ax, ay, az, S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_evaluate(fmm_plan* pl, int64_t n, const double* x, const double* y, const double* z, const double* q,
+                 double* pot, double* ax, double* ay, double* az, void* stream) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
+    int rc;
+    if ((rc = fmm_build_tree(pl, n, x, y, z, q, stream))) return rc;
+    if ((rc = fmm_p2m(pl, stream))) return rc;
+    if ((rc = fmm_m2m(pl, stream))) return rc;
+    if ((rc = fmm_m2l(pl, stream))) return rc;
+    if ((rc = fmm_l2l(pl, stream))) return rc;
+    if ((rc = fmm_l2p(pl, pot, ax, ay, az, stream))) return rc;
+    if ((rc = fmm_p2p(pl, pot, ax, ay, az, stream))) return rc;
+    return FMM_OK;
+}
+
+int fmm_evaluate_host(fmm_plan* pl, int64_t n, const double* x, const double* y, const double* z,
+                      const double* q, double* pot, double* ax, double* ay, double* az, void* stream) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n > 0 && (!x || !y || !z || !q || !pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null host array");
+    if (n > pl->stage_n) {
+        cudaFree(pl->stage);
+        pl->stage = nullptr;
+        pl->stage_n = 0;
+        if (cudaMalloc(&pl->stage, (size_t)8 * n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            FAIL(FMM_ERR_OOM, "allocating staging buffers failed");
+        }
+        pl->stage_n = n;
+    }
+    double* d = pl->stage;
+    const size_t b = (size_t)n * sizeof(double);
+    cudaStream_t s = S(stream);
+    const double* in[4] = {x, y, z, q};
+    double* outp[4] = {pot, ax, ay, az};
+    for (int k = 0; k < 4; ++k) CK(cudaMemcpyAsync(d + (size_t)k * n, in[k], b, cudaMemcpyHostToDevice, s));
+    int rc = fmm_evaluate(pl, n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, d + 6 * n, d + 7 * n,
+                          stream);
+    if (rc) return rc;
+    for (int k = 0; k < 4; ++k) CK(cudaMemcpyAsync(outp[k], d + (size_t)(4 + k) * n, b, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return FMM_OK;
+}
+
+}  // extern "C"

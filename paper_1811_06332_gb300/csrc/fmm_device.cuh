@@ -1,0 +1,55 @@
+// Device-side helpers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "_gen/fmm_tables.h"
+
+namespace fmm {
+
+__device__ __forceinline__ double fmm_rsqrt(double v) { return 1.0 / sqrt(v); }
+__device__ __forceinline__ float fmm_rsqrt(float v) { return rsqrtf(v); }
+
+// Storage positions (App. D multi-indices; App. A compressed order).
+__host__ __device__ __forceinline__ int ns_of(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }
+__host__ __device__ __forceinline__ int nt_of(int p) { return p < 0 ? 0 : (p + 1) * (p + 1); }
+__host__ __device__ __forceinline__ int ncoef_of(int p, int basis) { return basis ? nt_of(p) : ns_of(p); }
+// symmetric order: rank j block starts at ns(j-1); inside, (j-nx)(j-nx+1)/2 + nz
+__host__ __device__ __forceinline__ int pos_sym(int nx, int ny, int nz) {
+    const int j = nx + ny + nz, a = j - nx;
+    return ns_of(j - 1) + a * (a + 1) / 2 + nz;
+}
+// independent (nz <= 1) traceless order: rank j block starts at j^2
+__host__ __device__ __forceinline__ int pos_tl(int nx, int ny, int nz) {
+    const int j = nx + ny + nz;
+    return j * j + (nz == 0 ? ny : j + 1 + ny);
+}
+
+// Uniform octree cell numbering used for every level l >= 1: cells are
+// grouped by the parity of their integer coordinates ("class" = x&1 |
+// (y&1)<<1 | (z&1)<<2), then linear in (x>>1, y>>1, z>>1).  The 8 children
+// of a parent at linear position P of level l-1 are then c*8^(l-1) + P.
+__host__ __device__ __forceinline__ int64_t cell_index(int l, int ix, int iy, int iz) {
+    if (l == 0) return 0;
+    const int64_t hs = (int64_t)1 << (l - 1);
+    const int cls = (ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2);
+    return (int64_t)cls * hs * hs * hs + (((int64_t)(iz >> 1) * hs + (iy >> 1)) * hs + (ix >> 1));
+}
+__host__ __device__ __forceinline__ void cell_coords(int l, int64_t idx, int& ix, int& iy, int& iz) {
+    if (l == 0) { ix = iy = iz = 0; return; }
+    const int64_t hs = (int64_t)1 << (l - 1);
+    const int64_t h3 = hs * hs * hs;
+    const int cls = (int)(idx / h3);
+    const int64_t lin = idx - cls * h3;
+    const int jx = (int)(lin % hs), jy = (int)((lin / hs) % hs), jz = (int)(lin / (hs * hs));
+    ix = 2 * jx + (cls & 1);
+    iy = 2 * jy + ((cls >> 1) & 1);
+    iz = 2 * jz + ((cls >> 2) & 1);
+}
+// plain linear index of level l (used for the parent of a child)
+__host__ __device__ __forceinline__ int64_t lin_index(int l, int ix, int iy, int iz) {
+    const int64_t s = (int64_t)1 << l;
+    return ((int64_t)iz * s + iy) * s + ix;
+}
+
+}  // namespace fmm

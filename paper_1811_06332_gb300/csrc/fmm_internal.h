@@ -1,0 +1,114 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmm_device.cuh"
+#include "_gen/fmm_ctables.cuh"
+
+namespace fmm {
+
+struct DevOffsets {
+    int detr[FMM_PMAX + 2];
+    int expand[FMM_PMAX + 2];
+    int reduce[FMM_PMAX + 2];
+};
+
+struct DevTables {
+    double* detr = nullptr;
+    double* expand = nullptr;
+    double* reduce = nullptr;
+    int detr_off[FMM_PMAX + 2];
+    int expand_off[FMM_PMAX + 2];
+    int reduce_off[FMM_PMAX + 2];
+    DevOffsets offsets() const {
+        DevOffsets o;
+        for (int j = 0; j < FMM_PMAX + 2; ++j) {
+            o.detr[j] = detr_off[j];
+            o.expand[j] = expand_off[j];
+            o.reduce[j] = reduce_off[j];
+        }
+        return o;
+    }
+};
+
+extern DevTables g_tab[64];
+int ensure_tables(int dev);  // 0 ok, -2 CUDA error, -3 allocation failure
+void count_launch();
+
+// ---------------------------------------------------------------------------
+// small warp helpers
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Rebuilds the full symmetric polytensor X (ranks 0..p) from independent
+// traceless components A (trace condition, App. B); lanes stride the output.
+static __device__ __noinline__ void expand_tl_warp(int p, const double* A, double* X, const double* expand,
+                               const DevOffsets& off, int lane) {
+    const int ns = ns_of(p);
+    for (int s = lane; s < ns; s += 32) {
+        const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
+        const int j = nx + ny + nz;
+        const int row = (j - nx) * (j - nx + 1) / 2 + nz;
+        const double* E = expand + off.expand[j] + row * (2 * j + 1);
+        double v = 0.0;
+        for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * A[j * j + t];
+        X[s] = v;
+    }
+}
+
+// generated per-order launchers (csrc/_gen/pair_P<p>.cu)
+#define FMM_DECL_P(P)                                                                                   \
+    int launch_dtensor_p##P(int prec, int64_t n, const double* r, void* D, cudaStream_t s);            \
+    int launch_m2l_pair_p##P(int basis, int prec, int64_t n, const void* M, const double* r, void* L, \
+                             int accumulate, cudaStream_t s);                                           \
+    int launch_dtable_p##P(int noff, const double* o, double* D, cudaStream_t s);
+FMM_DECL_P(0) FMM_DECL_P(1) FMM_DECL_P(2) FMM_DECL_P(3) FMM_DECL_P(4) FMM_DECL_P(5)
+FMM_DECL_P(6) FMM_DECL_P(7) FMM_DECL_P(8) FMM_DECL_P(9) FMM_DECL_P(10)
+#undef FMM_DECL_P
+
+// fmm_ops.cu
+int launch_p2m(int p, int basis, int mode, int64_t ncell, const int64_t* start64, const int* start32,
+               const double* x, const double* y, const double* z, const double* q, const double* centre,
+               int depth, double inv_h, double* M, int64_t ldm, const DevTables& T, cudaStream_t s);
+int launch_m2m_general(int p, int basis, int64_t n, const double* Mc, const double* delta, double* Mp,
+                       const DevTables& T, cudaStream_t s);
+int launch_l2l_general(int p, int basis, int64_t n, const double* Lp, const double* delta, double* Lc,
+                       const DevTables& T, cudaStream_t s);
+int launch_l2p_general(int p, int basis, int64_t n, const double* L, const double* rb, double* out,
+                       const DevTables& T, cudaStream_t s);
+int launch_direct(int64_t n, const double* x, const double* y, const double* z, const double* q, int64_t nt,
+                  const int64_t* targets, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+int launch_m2m_level(int p, int basis, int l, const double* W, const double* Mch, int64_t nch, double* Mpa,
+                     int64_t npa, cudaStream_t s);
+int launch_l2l_level(int p, int basis, int l, const double* V, const double* Lpa, int64_t npa, double* Lch,
+                     int64_t nch, cudaStream_t s);
+int launch_m2l_fp64_level(int p, int basis, int l, const double* Dtab, const double* Mt, double* Lt,
+                          int64_t ncell, cudaStream_t s);
+int launch_l2p_leaf(int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
+                    const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& T,
+                    double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+int launch_zero4(int64_t n, double* a, double* b, double* c, double* d, cudaStream_t s);
+int launch_p2p_leaf(int prec, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
+                    const double* zs, const double* qs, const int* perm, double* pot, double* ax, double* ay,
+                    double* az, cudaStream_t s);
+
+// fmm_m2l32.cu and generated grp_*.cu
+int launch_build_ktab(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, float* K,
+                      cudaStream_t s);
+int grouped_entries(int p, int basis, unsigned char* out, int cap);
+int launch_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
+int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K, int64_t ncell,
+                   cudaStream_t s);
+int grouped_kstride(int p, int basis);
+
+// fmm_tree.cu
+size_t tree_scratch_bytes(int64_t n, int64_t nleaf);
+int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,
+                        double* xs, double* ys, double* zs, double* qs, int* perm, int* start, void* scratch,
+                        cudaStream_t s);
+
+}  // namespace fmm

@@ -1,0 +1,71 @@
+// FP32 offset-grouped M2L support: the packed per-offset matrices
+//   Kt_r(n, m) = D_{n+m}(r)/m!   (cell units, |n| + |m| <= p; Eq. M2L)
+// built in FP64 from the D-tensor table and rounded once to FP32, and the
+// FP64 -> FP32 copy of the multipoles they multiply.
+#include "fmm_internal.h"
+
+namespace fmm {
+
+// ent[e] = (nx, ny, nz, mx, my, mz) of packed entry e (row n, column m).
+__global__ void k_build_ktab(int ns, int ksz, int kst, const unsigned char* __restrict__ ent,
+                             const double* __restrict__ Dtab, float* __restrict__ K) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)343 * kst) return;
+    const int r = (int)(i / kst), e = (int)(i % kst);
+    float v = 0.f;
+    if (e < ksz) {
+        const unsigned char* t = ent + 6 * e;
+        const double d = Dtab[(int64_t)r * ns + pos_sym(t[0] + t[3], t[1] + t[4], t[2] + t[5])];
+        v = (float)(d * c_invfact[t[3]] * c_invfact[t[4]] * c_invfact[t[5]]);
+    }
+    K[i] = v;
+}
+
+int launch_build_ktab(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, float* K,
+                      cudaStream_t s) {
+    int ksz = 0;
+    const int nc = ncoef_of(p, basis);
+    for (int r = 0; r < nc; ++r) {
+        const unsigned char* n = basis ? fmm_tl_idx[r] : fmm_sym_idx[r];
+        const int rem = p - n[0] - n[1] - n[2];
+        ksz += basis ? nt_of(rem) : ns_of(rem);
+    }
+    const int64_t tot = (int64_t)343 * kst;
+    k_build_ktab<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ns_of(p), ksz, kst, ent, Dtab, K);
+    count_launch();
+    return ksz;
+}
+
+// Host-side packed entry list in the generator's layout (rows in storage
+// order, each followed by its prefix of columns).
+int grouped_entries(int p, int basis, unsigned char* out, int cap) {
+    const int nc = ncoef_of(p, basis);
+    int e = 0;
+    for (int r = 0; r < nc; ++r) {
+        const unsigned char* n = basis ? fmm_tl_idx[r] : fmm_sym_idx[r];
+        const int rem = p - n[0] - n[1] - n[2];
+        const int pre = basis ? nt_of(rem) : ns_of(rem);
+        for (int c = 0; c < pre; ++c) {
+            const unsigned char* m = basis ? fmm_tl_idx[c] : fmm_sym_idx[c];
+            if (e >= cap) return -1;
+            unsigned char* o = out + 6 * e;
+            o[0] = n[0]; o[1] = n[1]; o[2] = n[2]; o[3] = m[0]; o[4] = m[1]; o[5] = m[2];
+            ++e;
+        }
+    }
+    return e;
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+int launch_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
+    if (n <= 0) return 0;
+    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b);
+    count_launch();
+    return 0;
+}
+
+}  // namespace fmm

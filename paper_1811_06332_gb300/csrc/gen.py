@@ -1,0 +1,555 @@
+"""Build-time generator for the CUDA library's tables and unrolled kernels.
+
+Emits, into csrc/_gen/:
+  * fmm_tables.h     multi-index tables (App. D) and exact combinatorial maps
+                     (detracer, trace expansion, reduced representative),
+                     computed here with exact rational arithmetic;
+  * pair_P<p>.cu     per-pair D-tensor and M2L kernels for one order p,
+                     straight-line code for both bases and both precisions.
+
+Only the Python standard library is used, so the generator runs wherever the
+library is built.  Nothing here is shared with the FP64 oracle; the D-tensor
+kernels use a different route to grad^n r^{-1} (the Leibniz recurrence
+described at gen_dtensor) from the oracle's closed form.
+"""
+from __future__ import annotations
+
+import os
+import sys
+from fractions import Fraction
+from math import factorial
+
+PMAX = 10
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "_gen")
+
+
+# ----------------------------------------------------------------------------
+# multi-index enumeration (App. D) and storage orders
+# ----------------------------------------------------------------------------
+def rank_sym(j):
+    """Rank-j multi-indices: descending nx, then descending ny."""
+    return [(nx, ny, j - nx - ny) for nx in range(j, -1, -1) for ny in range(j - nx, -1, -1)]
+
+
+def rank_tl(j):
+    """Independent rank-j multi-indices (nz <= 1): nz = 0 block then nz = 1."""
+    return [(j - ny, ny, 0) for ny in range(j + 1)] + [(j - 1 - ny, ny, 1) for ny in range(j)]
+
+
+def sym_list(p):
+    return [n for j in range(p + 1) for n in rank_sym(j)]
+
+
+def tl_list(p):
+    return [n for j in range(p + 1) for n in rank_tl(j)]
+
+
+def ns(p):
+    return (p + 1) * (p + 2) * (p + 3) // 6
+
+
+def nt(p):
+    return (p + 1) ** 2
+
+
+def mfact(n):
+    return factorial(n[0]) * factorial(n[1]) * factorial(n[2])
+
+
+def add(a, b):
+    return (a[0] + b[0], a[1] + b[1], a[2] + b[2])
+
+
+def sub(a, b):
+    return (a[0] - b[0], a[1] - b[1], a[2] - b[2])
+
+
+E = ((1, 0, 0), (0, 1, 0), (0, 0, 1))
+
+
+# ----------------------------------------------------------------------------
+# exact combinatorial maps per rank
+# ----------------------------------------------------------------------------
+def dfact_odd(k):
+    v = 1
+    for i in range(2 * k - 1, 1, -2):
+        v *= i
+    return v
+
+
+def detracer_rank(j):
+    """Matrix of the idempotent detracer D = T/(2j-1)!! on rank-j symmetric
+    tensors (rows, cols: rank_sym(j)), from Eq. Detracer of App. A:
+    T[A]_n = sum_{m <= n/2} f_{n,m} sum_{|k|=|m|} (|m|!/k!) A_{n-2m+2k}."""
+    idx = rank_sym(j)
+    col = {n: i for i, n in enumerate(idx)}
+    Mx = [[Fraction(0)] * len(idx) for _ in idx]
+    for r, n in enumerate(idx):
+        for mx in range(n[0] // 2 + 1):
+            for my in range(n[1] // 2 + 1):
+                for mz in range(n[2] // 2 + 1):
+                    m = (mx, my, mz)
+                    mm = mx + my + mz
+                    f = Fraction((-1) ** mm * dfact_odd(j - mm) * mfact(n),
+                                 2 ** mm * mfact(m) * mfact(sub(n, (2 * mx, 2 * my, 2 * mz))))
+                    for k in rank_sym(mm):
+                        tgt = (n[0] - 2 * mx + 2 * k[0], n[1] - 2 * my + 2 * k[1], n[2] - 2 * mz + 2 * k[2])
+                        Mx[r][col[tgt]] += f * Fraction(factorial(mm), mfact(k))
+    s = Fraction(1, dfact_odd(j))
+    return [[v * s for v in row] for row in Mx]
+
+
+def expand_rank(j):
+    """Matrix X (rank_sym(j) x rank_tl(j)) rebuilding every component of a
+    trace-free rank-j tensor from its independent ones by the trace condition
+    A_{k+2ez} = -A_{k+2ex} - A_{k+2ey}."""
+    idx = rank_sym(j)
+    tl = rank_tl(j)
+    tcol = {n: i for i, n in enumerate(tl)}
+    rows = {}
+    for n in idx:  # symmetric order visits both right-hand sides first
+        if n[2] <= 1:
+            v = [Fraction(0)] * len(tl)
+            v[tcol[n]] = Fraction(1)
+        else:
+            a = rows[(n[0] + 2, n[1], n[2] - 2)]
+            b = rows[(n[0], n[1] + 2, n[2] - 2)]
+            v = [-x - y for x, y in zip(a, b)]
+        rows[n] = v
+    return [rows[n] for n in idx]
+
+
+def solve_exact(A, B):
+    """Solves A X = B exactly (A square, Fractions), Gauss-Jordan."""
+    n = len(A)
+    M = [list(A[i]) + list(B[i]) for i in range(n)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        pv = M[c][c]
+        M[c] = [v / pv for v in M[c]]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c]
+                M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+    return [row[n:] for row in M]
+
+
+def reduce_rank(j):
+    """Matrix P (rank_tl(j) x rank_sym(j)) taking any symmetric rank-j tensor
+    A to the unique tensor A^r supported on the nz <= 1 components with
+    D[A^r] = D[A].  Because grad^k r^{-1} is trace free, contracting it with
+    A^r or with A gives the same number, so the traceless M2L, M2M and
+    P2M can run over the 2j+1 stored components only."""
+    idx = rank_sym(j)
+    tl = rank_tl(j)
+    Dm = detracer_rank(j)
+    pos = {n: i for i, n in enumerate(idx)}
+    rows_tl = [pos[n] for n in tl]
+    # restriction of D to nz<=1 inputs, read on the independent outputs
+    Dr = [[Dm[r][pos[c]] for c in tl] for r in rows_tl]
+    # P = Dr^{-1} (D restricted to independent output rows)
+    rhs = [[Dm[r][c] for c in range(len(idx))] for r in rows_tl]
+    return solve_exact(Dr, rhs)
+
+
+# ----------------------------------------------------------------------------
+# C emission helpers
+# ----------------------------------------------------------------------------
+def lit(x, T="T"):
+    x = float(x)
+    if x == int(x) and abs(x) < 1e15:
+        return "%s(%d.0)" % (T, int(x))
+    return "%s(%.17g)" % (T, x)
+
+
+def emit_tables():
+    L = []
+    L.append("// Generated by gen.py: multi-index tables and exact combinatorial maps.")
+    L.append("#pragma once")
+    L.append("#define FMM_PMAX %d" % PMAX)
+    sl, tlst = sym_list(PMAX), tl_list(PMAX)
+    L.append("#define FMM_NS_MAX %d" % len(sl))
+    L.append("#define FMM_NT_MAX %d" % len(tlst))
+    L.append("static const unsigned char fmm_sym_idx[%d][3] = {%s};" % (
+        len(sl), ",".join("{%d,%d,%d}" % n for n in sl)))
+    L.append("static const unsigned char fmm_tl_idx[%d][3] = {%s};" % (
+        len(tlst), ",".join("{%d,%d,%d}" % n for n in tlst)))
+    # per-rank dense maps, flattened with offsets
+    for name, fn, shape in (("fmm_detr", detracer_rank, lambda j: ((j + 1) * (j + 2) // 2, (j + 1) * (j + 2) // 2)),
+                            ("fmm_expand", expand_rank, lambda j: ((j + 1) * (j + 2) // 2, 2 * j + 1)),
+                            ("fmm_reduce", reduce_rank, lambda j: (2 * j + 1, (j + 1) * (j + 2) // 2))):
+        vals, offs = [], []
+        for j in range(PMAX + 1):
+            offs.append(len(vals))
+            Mx = fn(j)
+            r, c = shape(j)
+            assert len(Mx) == r and all(len(row) == c for row in Mx), (name, j)
+            for row in Mx:
+                vals.extend(row)
+        offs.append(len(vals))
+        L.append("static const int %s_off[%d] = {%s};" % (name, PMAX + 2, ",".join(map(str, offs))))
+        L.append("static const double %s_val[%d] = {%s};" % (
+            name, len(vals), ",".join("%.17g" % float(v) for v in vals)))
+    return "\n".join(L) + "\n"
+
+
+# ----------------------------------------------------------------------------
+# D-tensor by recurrence.
+#
+# With phi = 1/|x|, d/dx_i phi = -x_i phi / |x|^2, i.e. |x|^2 d_i phi + x_i phi = 0.
+# Applying d^(k - e_i) with Leibniz' rule (d_j |x|^2 = 2 x_j, d_j^2 |x|^2 = 2)
+# gives, for any axis i with k_i >= 1,
+#   |x|^2 D_k = -[ (2k_i - 1) x_i D_{k-e_i} + sum_{j!=i} 2 k_j x_j D_{k-e_j}
+#                 + (k_i - 1)^2 D_{k-2e_i} + sum_{j!=i} k_j (k_j - 1) D_{k-2e_j} ],
+# with D_k = d^k phi.  Each component costs at most six products.
+# ----------------------------------------------------------------------------
+def dtensor_terms(k):
+    i = max(range(3), key=lambda a: (k[a], -a))
+    terms = []  # (coef, axis or None, source index)
+    for j in range(3):
+        if k[j] == 0:
+            continue
+        c = (2 * k[j] - 1) if j == i else 2 * k[j]
+        terms.append((c, j, sub(k, E[j])))
+    for j in range(3):
+        c = (k[j] - 1) ** 2 if j == i else k[j] * (k[j] - 1)
+        if k[j] >= 2 and c:
+            terms.append((c, None, sub(k, tuple(2 * v for v in E[j]))))
+    return terms
+
+
+def gen_dtensor(p, T="T", out="d"):
+    """Straight-line code computing out[0..ns(p)) = grad^k |r|^{-1}."""
+    pos = {n: i for i, n in enumerate(sym_list(p))}
+    xs = ("x", "y", "z")
+    L = ["  const T r2 = x * x + y * y + z * z;",
+         "  const T ir2 = T(1) / r2;",
+         "  %s[0] = fmm_rsqrt(r2);" % out]
+    for k in sym_list(p)[1:]:
+        parts = []
+        for c, ax, src in dtensor_terms(k):
+            cc = lit(c, T)
+            if ax is None:
+                parts.append("%s * %s[%d]" % (cc, out, pos[src]))
+            else:
+                parts.append("%s * %s * %s[%d]" % (cc, xs[ax], out, pos[src]))
+        L.append("  %s[%d] = -ir2 * (%s);" % (out, pos[k], " + ".join(parts)))
+    return "\n".join(L)
+
+
+# ----------------------------------------------------------------------------
+# per-pair M2L (Eq. M2L): L_n += sum_{|m| <= p-|n|} (1/m!) M_m D_{n+m}(r)
+# ----------------------------------------------------------------------------
+def gen_m2l_pair(p, basis, tile):
+    syml = sym_list(p)
+    pos = {n: i for i, n in enumerate(syml)}
+    outs = syml if basis == 0 else tl_list(p)
+    tpos = {n: i for i, n in enumerate(tl_list(p))}
+    L = []
+    for t0 in range(0, len(outs), tile):
+        tl_ = outs[t0:t0 + tile]
+        minr = min(sum(n) for n in tl_)
+        L.append("  {")
+        for a, n in enumerate(tl_):
+            L.append("    T a%d = accumulate ? Lp[(int64_t)%d * n + t] : T(0);" % (a, t0 + a))
+        for b in range(0, p - minr + 1):
+            blk = rank_sym(b)
+            L.append("    {")
+            # load rank-b multipole block (reconstructing dependents in tl)
+            for m in blk:
+                if basis == 0:
+                    L.append("      const T m_%d_%d_%d = __ldg(&Mp[(int64_t)%d * n + t]);" % (m + (pos[m],)))
+                elif m[2] <= 1:
+                    L.append("      const T m_%d_%d_%d = __ldg(&Mp[(int64_t)%d * n + t]);" % (m + (tpos[m],)))
+                else:
+                    L.append("      const T m_%d_%d_%d = -m_%d_%d_%d - m_%d_%d_%d;" % (
+                        m + (m[0] + 2, m[1], m[2] - 2) + (m[0], m[1] + 2, m[2] - 2)))
+            for m in blk:
+                users = [(a, n) for a, n in enumerate(tl_) if sum(n) + b <= p]
+                if not users:
+                    continue
+                f = mfact(m)
+                mc = "m_%d_%d_%d" % m if f == 1 else "(m_%d_%d_%d * %s)" % (m + (lit(Fraction(1, f)),))
+                L.append("      { const T c = %s;" % mc)
+                for a, n in users:
+                    L.append("        a%d = fma(c, d[%d], a%d);" % (a, pos[add(n, m)], a))
+                L.append("      }")
+            L.append("    }")
+        for a, n in enumerate(tl_):
+            L.append("    Lp[(int64_t)%d * n + t] = a%d;" % (t0 + a, a))
+        L.append("  }")
+    return "\n".join(L)
+
+
+def emit_pair_file(p):
+    """D-tensor kernels and the M2L launcher of order p."""
+    L = ['// Generated by gen.py: per-pair D-tensor kernels and M2L dispatch, p = %d.' % p,
+         '#include "../fmm_device.cuh"',
+         "namespace fmm {",
+         ""]
+    for basis in (0, 1):
+        for T in ("float", "double"):
+            L.append("int launch_m2l_pair_p%d_b%d_%s(int64_t n, const void* M, const double* r, void* L,"
+                     " int accumulate, cudaStream_t s);" % (p, basis, T))
+    L.append("template <typename T> __global__ void __launch_bounds__(128)")
+    L.append("dtensor_pair_p%d(int64_t n, const double* __restrict__ r, T* __restrict__ D) {" % p)
+    L.append("  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;")
+    L.append("  if (t >= n) return;")
+    L.append("  const T x = T(r[t]), y = T(r[n + t]), z = T(r[2 * n + t]);")
+    L.append("  T d[%d];" % ns(p))
+    L.append(gen_dtensor(p))
+    L.append("  #pragma unroll")
+    L.append("  for (int i = 0; i < %d; ++i) D[(int64_t)i * n + t] = d[i];" % ns(p))
+    L.append("}")
+    L.append("")
+    L.append("template <typename T> __device__ __forceinline__ void dtensor_p%d(T x, T y, T z, T* d) {" % p)
+    L.append(gen_dtensor(p))
+    L.append("}")
+    L.append("")
+    L.append("int launch_dtensor_p%d(int prec, int64_t n, const double* r, void* D, cudaStream_t s) {" % p)
+    L.append("  if (n <= 0) return 0;")
+    L.append("  const unsigned g = (unsigned)((n + 127) / 128);")
+    L.append("  if (prec == 0) dtensor_pair_p%d<double><<<g, 128, 0, s>>>(n, r, (double*)D);" % p)
+    L.append("  else dtensor_pair_p%d<float><<<g, 128, 0, s>>>(n, r, (float*)D);" % p)
+    L.append("  return 0;")
+    L.append("}")
+    L.append("int launch_m2l_pair_p%d(int basis, int prec, int64_t n, const void* M, const double* r, void* L,"
+             " int accumulate, cudaStream_t s) {" % p)
+    L.append("  if (n <= 0) return 0;")
+    for basis in (0, 1):
+        L.append("  if (basis == %d && prec == 0) return launch_m2l_pair_p%d_b%d_double(n, M, r, L, accumulate, s);"
+                 % (basis, p, basis))
+        L.append("  if (basis == %d && prec == 1) return launch_m2l_pair_p%d_b%d_float(n, M, r, L, accumulate, s);"
+                 % (basis, p, basis))
+    L.append("  return -1;")
+    L.append("}")
+    L.append("")
+    L.append("__global__ void dtable_p%d(int noff, const double* __restrict__ o, double* __restrict__ D) {" % p)
+    L.append("  const int t = blockIdx.x * blockDim.x + threadIdx.x;")
+    L.append("  if (t >= noff) return;")
+    L.append("  double d[%d];" % ns(p))
+    L.append("  dtensor_p%d<double>(o[3 * t], o[3 * t + 1], o[3 * t + 2], d);" % p)
+    L.append("  for (int i = 0; i < %d; ++i) D[(int64_t)t * %d + i] = d[i];" % (ns(p), ns(p)))
+    L.append("}")
+    L.append("int launch_dtable_p%d(int noff, const double* o, double* D, cudaStream_t s) {" % p)
+    L.append("  dtable_p%d<<<(noff + 63) / 64, 64, 0, s>>>(noff, o, D);" % p)
+    L.append("  return 0;")
+    L.append("}")
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
+def emit_m2l_file(p, basis, T):
+    """One per-pair M2L kernel (order p, basis, precision) and its launcher."""
+    tile = 40 if T == "float" else 24
+    L = ['// Generated by gen.py: per-pair M2L (Eq. M2L), p = %d, basis %d, %s.' % (p, basis, T),
+         '#include "../fmm_device.cuh"',
+         "namespace fmm {",
+         "__global__ void __launch_bounds__(128)",
+         "m2l_pair_p%d_b%d_%s(int64_t n, const %s* __restrict__ Mp, const double* __restrict__ r,"
+         " %s* __restrict__ Lp, int accumulate) {" % (p, basis, T, T, T),
+         "  typedef %s T;" % T,
+         "  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;",
+         "  if (t >= n) return;",
+         "  const T x = T(r[t]), y = T(r[n + t]), z = T(r[2 * n + t]);",
+         "  T d[%d];" % ns(p),
+         gen_dtensor(p),
+         gen_m2l_pair(p, basis, tile),
+         "}",
+         "int launch_m2l_pair_p%d_b%d_%s(int64_t n, const void* M, const double* r, void* L,"
+         " int accumulate, cudaStream_t s) {" % (p, basis, T),
+         "  m2l_pair_p%d_b%d_%s<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, (const %s*)M, r, (%s*)L,"
+         " accumulate);" % (p, basis, T, T, T),
+         "  return 0;",
+         "}",
+         "}  // namespace fmm"]
+    return "\n".join(L) + "\n"
+
+
+def grouped_layout(p, basis):
+    """Row/column structure of the offset-grouped M2L matrices
+    Kt_r(n, m) = D_{n+m}(r)/m! (cell units): rows n = output components in
+    storage order, columns m = multipole components of rank <= p - |n|, which
+    form a prefix of the storage order.  Returns (rows, prefix length per
+    row, packed offset per row, packed size)."""
+    rows = sym_list(p) if basis == 0 else tl_list(p)
+    pre = [(ns(p - sum(n)) if basis == 0 else nt(p - sum(n))) for n in rows]
+    off = [0]
+    for k in pre:
+        off.append(off[-1] + k)
+    return rows, pre, off, off[-1]
+
+
+def grouped_parts(p, basis, budget=200):
+    """Splits the output rows so that accumulators + multipole registers of
+    one kernel stay within `budget` 32-bit registers."""
+    rows, pre, _, _ = grouped_layout(p, basis)
+    parts, r0 = [], 0
+    while r0 < len(rows):
+        r1 = r0 + 1
+        while r1 < len(rows) and (r1 + 1 - r0) + pre[r0] <= budget:
+            r1 += 1
+        parts.append((r0, r1))
+        r0 = r1
+    return parts
+
+
+def kstride(p, basis):
+    return (grouped_layout(p, basis)[3] + 3) // 4 * 4
+
+
+def emit_grouped_file(p, basis):
+    """FP32 offset-grouped M2L over the uniform interaction lists of one
+    level: one thread per target cell, the block's 128 targets share one
+    parity class and hence one sequence of 189 offsets; the packed matrix of
+    each offset is staged in shared memory and read by every thread at the
+    same address, the source multipole sits in registers."""
+    rows, pre, off, ksz = grouped_layout(p, basis)
+    kst = kstride(p, basis)
+    L = ['// Generated by gen.py: FP32 offset-grouped M2L, p = %d, basis %d.' % (p, basis),
+         '#include "../fmm_device.cuh"',
+         "namespace fmm {"]
+    parts = grouped_parts(p, basis)
+    for k, (r0, r1) in enumerate(parts):
+        klen = off[r1] - off[r0]
+        ncol = pre[r0]
+        L.append("__global__ void __launch_bounds__(128)")
+        L.append("m2l_grp_p%d_b%d_r%d(int l, const float* __restrict__ M, double* __restrict__ Lt,"
+                 " const float* __restrict__ K, int64_t ncell) {" % (p, basis, k))
+        L.append("  __shared__ __align__(16) float sK[%d];" % ((klen + 3) // 4 * 4))
+        L.append("  const int side = 1 << l, hs = side >> 1;")
+        L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + 127) / 128;")
+        L.append("  const int cls = (int)(blockIdx.x / bpc);")
+        L.append("  const int64_t t = (int64_t)(blockIdx.x % bpc) * 128 + threadIdx.x;")
+        L.append("  const bool act = t < h3;")
+        L.append("  const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;")
+        L.append("  const int ix = 2 * (int)(t % hs) + cx, iy = 2 * (int)((t / hs) % hs) + cy,"
+                 " iz = 2 * (int)(t / ((int64_t)hs * hs)) + cz;")
+        for a in range(r1 - r0):
+            L.append("  float a%d = 0.f;" % a)
+        L.append("  #pragma unroll 1")
+        L.append("  for (int u = 0; u < 216; ++u) {")
+        L.append("    const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;")
+        L.append("    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;")
+        L.append("    const float* Kg = K + (int64_t)((3 - oz) * 49 + (3 - oy) * 7 + (3 - ox)) * %d + %d;" % (kst, off[r0]))
+        L.append("    __syncthreads();")
+        L.append("    for (int e = threadIdx.x; e < %d; e += 128) sK[e] = __ldg(Kg + e);" % klen)
+        L.append("    __syncthreads();")
+        L.append("    const int jx = ix + ox, jy = iy + oy, jz = iz + oz;")
+        L.append("    if (!act || jx < 0 || jy < 0 || jz < 0 || jx >= side || jy >= side || jz >= side) continue;")
+        L.append("    const int64_t s = cell_index(l, jx, jy, jz);")
+        for c in range(ncol):
+            L.append("    const float m%d = __ldg(M + (int64_t)%d * ncell + s);" % (c, c))
+        for r in range(r0, r1):
+            base = off[r] - off[r0]
+            for c in range(pre[r]):
+                L.append("    a%d = fmaf(sK[%d], m%d, a%d);" % (r - r0, base + c, c, r - r0))
+        L.append("  }")
+        L.append("  if (!act) return;")
+        L.append("  const int64_t tg = (int64_t)cls * h3 + t;")
+        for r in range(r0, r1):
+            L.append("  Lt[(int64_t)%d * ncell + tg] = (double)a%d;" % (r, r - r0))
+        L.append("}")
+    L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
+             " cudaStream_t s) {" % (p, basis))
+    L.append("  const int hs = (1 << l) >> 1;")
+    L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + 127) / 128;")
+    for k in range(len(parts)):
+        L.append("  m2l_grp_p%d_b%d_r%d<<<(unsigned)(8 * bpc), 128, 0, s>>>(l, M, Lt, K, ncell);" % (p, basis, k))
+    L.append("  return %d;" % len(parts))
+    L.append("}")
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
+def emit_grouped_dispatch():
+    L = ['// Generated by gen.py: dispatch and layout of the FP32 offset-grouped M2L.',
+         '#include "../fmm_device.cuh"', "namespace fmm {"]
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
+                     " cudaStream_t s);" % (p, b))
+    L.append("int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K,"
+             " int64_t ncell, cudaStream_t s) {")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s);"
+                     % (p, b, p, b))
+    L.append("  return -1;")
+    L.append("}")
+    L.append("int grouped_kstride(int p, int basis) {")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("  if (p == %d && basis == %d) return %d;" % (p, b, kstride(p, b)))
+    L.append("  return -1;")
+    L.append("}")
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
+def emit_ctables():
+    """Statically initialised __constant__ copies of the small index tables
+    (one copy per translation unit that includes the header)."""
+    sl, tlst = sym_list(PMAX), tl_list(PMAX)
+    L = ["// Generated by gen.py: device constant tables (internal linkage).", "#pragma once",
+         "namespace fmm {"]
+    L.append("static __constant__ unsigned char c_sym_idx[%d][3] = {%s};" % (
+        len(sl), ",".join("{%d,%d,%d}" % n for n in sl)))
+    L.append("static __constant__ unsigned char c_tl_idx[%d][3] = {%s};" % (
+        len(tlst), ",".join("{%d,%d,%d}" % n for n in tlst)))
+    L.append("static __constant__ double c_invfact[%d] = {%s};" % (
+        PMAX + 2, ",".join("%.17g" % (1.0 / factorial(i)) for i in range(PMAX + 2))))
+    rows = []
+    for a in range(PMAX + 1):
+        rows.append("{" + ",".join("%d.0" % (factorial(a) // (factorial(b) * factorial(a - b)) if b <= a else 0)
+                                  for b in range(PMAX + 1)) + "}")
+    L.append("static __constant__ double c_binom[%d][%d] = {%s};" % (PMAX + 1, PMAX + 1, ",".join(rows)))
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
+def write_if_changed(path, text):
+    if os.path.exists(path):
+        with open(path) as f:
+            if f.read() == text:
+                return False
+    with open(path + ".tmp", "w") as f:
+        f.write(text)
+    os.replace(path + ".tmp", path)
+    return True
+
+
+def generate(out=OUT):
+    os.makedirs(out, exist_ok=True)
+    files = []
+    p_t = os.path.join(out, "fmm_tables.h")
+    write_if_changed(p_t, emit_tables())
+    files.append(p_t)
+    p_c = os.path.join(out, "fmm_ctables.cuh")
+    write_if_changed(p_c, emit_ctables())
+    files.append(p_c)
+    for p in range(0, PMAX + 1):
+        fp = os.path.join(out, "pair_P%d.cu" % p)
+        write_if_changed(fp, emit_pair_file(p))
+        files.append(fp)
+        for basis in (0, 1):
+            for T in ("float", "double"):
+                fm = os.path.join(out, "m2l_P%d_b%d_%s.cu" % (p, basis, T))
+                write_if_changed(fm, emit_m2l_file(p, basis, T))
+                files.append(fm)
+            fg = os.path.join(out, "grp_P%d_b%d.cu" % (p, basis))
+            write_if_changed(fg, emit_grouped_file(p, basis))
+            files.append(fg)
+    fd = os.path.join(out, "grp_dispatch.cu")
+    write_if_changed(fd, emit_grouped_dispatch())
+    files.append(fd)
+    if False:
+        pass
+    return files
+
+
+if __name__ == "__main__":
+    for f in generate(sys.argv[1] if len(sys.argv) > 1 else OUT):
+        print(f)

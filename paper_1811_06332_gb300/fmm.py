@@ -1,0 +1,224 @@
+"""ctypes binding of libfmm_gb300.so (C-ABI declared in include/fmm_gb300.h).
+
+Argument marshalling only: every function forwards device pointers (taken
+from torch tensors) and sizes to the entry point of the same name; all the
+arithmetic runs in the library's CUDA kernels.  Loading fails loudly when the
+library has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+BASIS_SYM, BASIS_TRACELESS = 0, 1
+FP64, FP32, GEMM_TF32X3, GEMM_BF16X3 = 0, 1, 2, 3
+
+EXPORTS = [
+    "fmm_ncoef", "fmm_create", "fmm_destroy", "fmm_last_error", "fmm_build_tree", "fmm_p2m", "fmm_m2m",
+    "fmm_m2l", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate", "fmm_evaluate_host", "fmm_op_dtensor",
+    "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
+    "fmm_kernel_launches",
+]
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fmm status %d: %s" % (code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("basis", ctypes.c_int), ("prec", ctypes.c_int),
+                ("adaptive", ctypes.c_int), ("depth", ctypes.c_int), ("max_leaf", ctypes.c_int),
+                ("theta", ctypes.c_double), ("learned_p", ctypes.c_int),
+                ("target_rel_err", ctypes.c_double), ("use_graph", ctypes.c_int)]
+
+
+_lib = None
+_vp, _i64, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfmm_gb300.so is not built (run __graft_entry__.build()); "
+                               "the CUDA library is required, there is no CPU path")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "fmm_ncoef": ([_int, _int], _int),
+            "fmm_create": ([ctypes.POINTER(Config), ctypes.POINTER(_vp)], _int),
+            "fmm_destroy": ([_vp], None),
+            "fmm_last_error": ([_vp], ctypes.c_char_p),
+            "fmm_build_tree": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp], _int),
+            "fmm_p2m": ([_vp, _vp], _int), "fmm_m2m": ([_vp, _vp], _int),
+            "fmm_m2l": ([_vp, _vp], _int), "fmm_l2l": ([_vp, _vp], _int),
+            "fmm_l2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
+            "fmm_p2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
+            "fmm_evaluate": ([_vp, _i64] + [_vp] * 9, _int),
+            "fmm_evaluate_host": ([_vp, _i64] + [_vp] * 9, _int),
+            "fmm_op_dtensor": ([_int, _int, _i64, _vp, _vp, _vp], _int),
+            "fmm_op_p2m": ([_int, _int, _i64] + [_vp] * 8, _int),
+            "fmm_op_m2m": ([_int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_op_m2l": ([_int, _int, _int, _i64, _vp, _vp, _vp, _int, _vp], _int),
+            "fmm_op_l2l": ([_int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_op_l2p": ([_int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_direct": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
+            "fmm_kernel_launches": ([], _i64),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if t.is_cuda and not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _check(rc, plan=None):
+    if rc != OK:
+        msg = lib().fmm_last_error(plan)
+        raise FMMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def ncoef(p: int, basis: int) -> int:
+    n = lib().fmm_ncoef(p, basis)
+    if n < 0:
+        raise FMMError(n, "bad p/basis")
+    return n
+
+
+def kernel_launches() -> int:
+    return lib().fmm_kernel_launches()
+
+
+# ---------------------------------------------------------------------------
+# operator-level calls (device tensors, physical units)
+# ---------------------------------------------------------------------------
+def fmm_op_dtensor(p, prec, r, D, stream=None):
+    _check(lib().fmm_op_dtensor(p, prec, r.shape[1], _ptr(r), _ptr(D), _stream(stream)))
+
+
+def fmm_op_p2m(p, basis, start, x, y, z, q, centre, M, stream=None):
+    _check(lib().fmm_op_p2m(p, basis, len(start) - 1, _ptr(start), _ptr(x), _ptr(y), _ptr(z), _ptr(q),
+                            _ptr(centre), _ptr(M), _stream(stream)))
+
+
+def fmm_op_m2m(p, basis, Mc, delta, Mp, stream=None):
+    _check(lib().fmm_op_m2m(p, basis, Mc.shape[1], _ptr(Mc), _ptr(delta), _ptr(Mp), _stream(stream)))
+
+
+def fmm_op_m2l(p, basis, prec, M, r, L, accumulate=False, stream=None):
+    _check(lib().fmm_op_m2l(p, basis, prec, M.shape[1], _ptr(M), _ptr(r), _ptr(L), int(accumulate),
+                            _stream(stream)))
+
+
+def fmm_op_l2l(p, basis, Lp, delta, Lc, stream=None):
+    _check(lib().fmm_op_l2l(p, basis, Lp.shape[1], _ptr(Lp), _ptr(delta), _ptr(Lc), _stream(stream)))
+
+
+def fmm_op_l2p(p, basis, L, rb, out, stream=None):
+    _check(lib().fmm_op_l2p(p, basis, L.shape[1], _ptr(L), _ptr(rb), _ptr(out), _stream(stream)))
+
+
+def fmm_direct(x, y, z, q, pot, ax, ay, az, targets=None, stream=None):
+    nt = len(targets) if targets is not None else len(x)
+    _check(lib().fmm_direct(len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), nt, _ptr(targets), _ptr(pot),
+                            _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# plan
+# ---------------------------------------------------------------------------
+class Plan:
+    """Owns an fmm_plan (uniform octree FMM of App. C)."""
+
+    def __init__(self, p, basis=BASIS_SYM, prec=FP64, depth=3, use_graph=False, adaptive=False,
+                 max_leaf=64, theta=0.5):
+        cfg = Config(p=p, basis=basis, prec=prec, adaptive=int(adaptive), depth=depth, max_leaf=max_leaf,
+                     theta=theta, learned_p=0, target_rel_err=1e-4, use_graph=int(use_graph))
+        h = _vp()
+        _check(lib().fmm_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self.cfg = cfg
+
+    def close(self):
+        if self.h:
+            lib().fmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, rc):
+        return _check(rc, self.h)
+
+    def fmm_build_tree(self, x, y, z, q, stream=None):
+        self._c(lib().fmm_build_tree(self.h, len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), _stream(stream)))
+
+    def fmm_p2m(self, stream=None):
+        self._c(lib().fmm_p2m(self.h, _stream(stream)))
+
+    def fmm_m2m(self, stream=None):
+        self._c(lib().fmm_m2m(self.h, _stream(stream)))
+
+    def fmm_m2l(self, stream=None):
+        self._c(lib().fmm_m2l(self.h, _stream(stream)))
+
+    def fmm_l2l(self, stream=None):
+        self._c(lib().fmm_l2l(self.h, _stream(stream)))
+
+    def fmm_l2p(self, pot, ax, ay, az, stream=None):
+        self._c(lib().fmm_l2p(self.h, _ptr(pot), _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
+
+    def fmm_p2p(self, pot, ax, ay, az, stream=None):
+        self._c(lib().fmm_p2p(self.h, _ptr(pot), _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
+
+    def fmm_evaluate(self, x, y, z, q, pot, ax, ay, az, stream=None):
+        self._c(lib().fmm_evaluate(self.h, len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), _ptr(pot), _ptr(ax),
+                                   _ptr(ay), _ptr(az), _stream(stream)))
+
+    def fmm_evaluate_host(self, x, y, z, q, pot, ax, ay, az, stream=None):
+        """Host (CPU) tensors or numpy arrays of float64; synchronous."""
+        import numpy as np
+
+        def hp(a):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+                return a.ctypes.data
+            assert not a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+            return a.data_ptr()
+        self._c(lib().fmm_evaluate_host(self.h, len(x), hp(x), hp(y), hp(z), hp(q), hp(pot), hp(ax), hp(ay),
+                                        hp(az), _stream(stream)))
+
+    def evaluate(self, x, y, z, q, stream=None):
+        """Convenience: allocates outputs, returns (pot, acc[3, n]) device tensors."""
+        n = len(x)
+        out = torch.empty((4, n), dtype=torch.float64, device=x.device)
+        self.fmm_evaluate(x, y, z, q, out[0], out[1], out[2], out[3], stream)
+        return out[0], out[1:]

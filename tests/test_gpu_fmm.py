@@ -1,0 +1,159 @@
+"""GPU parity of the plan-based uniform-octree FMM (fmm_evaluate and the
+step-by-step entry points) against the FP64 oracle on the same tree, plus the
+direct-sum accuracy and edge cases.
+
+FP64 tolerance: normwise relative error of pot and of acc over all particles
+<= 1e-12, and per particle |d acc|/|acc| <= 1e-10 (summation order differs
+between the two; single particles can sit where the field nearly cancels).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1811_06332_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def F():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1811_06332_gb300 import fmm
+    return fmm
+
+
+def g(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def errs(pot, acc, pref, aref):
+    ep = np.linalg.norm(pot - pref) / max(np.linalg.norm(pref), 1e-300)
+    ea = np.linalg.norm(acc - aref) / max(np.linalg.norm(aref), 1e-300)
+    per = np.linalg.norm(acc - aref, axis=0) / np.maximum(np.linalg.norm(aref, axis=0), 1e-300)
+    return ep, ea, per.max() if per.size else 0.0
+
+
+def run(F, x, y, z, q, p, basis, depth, prec=None):
+    plan = F.Plan(p=p, basis=basis, prec=F.FP64 if prec is None else prec, depth=depth)
+    pot, acc = plan.evaluate(g(x), g(y), g(z), g(q))
+    torch.cuda.synchronize()
+    plan.close()
+    return pot.cpu().numpy(), acc.cpu().numpy()
+
+
+@pytest.mark.parametrize("p,basis", [(4, 0), (4, 1), (8, 1), (8, 0), (10, 1), (2, 0)])
+def test_small_uniform_vs_oracle(F, p, basis):
+    n, depth = 4096, 3
+    x, y, z = inputs.uniform_cube(n, 1)
+    q = inputs.masses_open_unit(n, 1)
+    pot, acc = run(F, x, y, z, q, p, basis, depth)
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, basis)
+    ep, ea, per = errs(pot, acc, pref, aref)
+    assert ep < 1e-12 and ea < 1e-12 and per < 1e-10, (ep, ea, per)
+
+
+def test_small_uniform_vs_direct(F):
+    n, depth, p = 4096, 3, 4
+    x, y, z = inputs.uniform_cube(n, 1)
+    q = inputs.masses_open_unit(n, 1)
+    pot, acc = run(F, x, y, z, q, p, 0, depth)
+    pd, ad = oracle.direct(x, y, z, q)
+    assert np.sqrt(((acc - ad) ** 2).sum() / (ad ** 2).sum()) < 3e-3
+
+
+def test_step_by_step_equals_evaluate(F):
+    n, depth, p = 5000, 3, 6
+    x, y, z = inputs.uniform_cube(n, 2)
+    q = inputs.masses_open_unit(n, 2)
+    plan = F.Plan(p=p, basis=1, prec=F.FP64, depth=depth)
+    t = [g(a) for a in (x, y, z, q)]
+    out = torch.zeros((4, n), device=DEV, dtype=torch.float64)
+    with pytest.raises(F.FMMError):
+        plan.fmm_p2m()            # before fmm_build_tree: FMM_ERR_STATE
+    plan.fmm_build_tree(*t)
+    plan.fmm_p2m(); plan.fmm_m2m(); plan.fmm_m2l(); plan.fmm_l2l()
+    plan.fmm_l2p(out[0], out[1], out[2], out[3])
+    far = out.clone()
+    plan.fmm_p2p(out[0], out[1], out[2], out[3])
+    pot, acc = plan.evaluate(*t)
+    torch.cuda.synchronize()
+    assert torch.equal(out[0], pot) and torch.equal(out[1:], acc)
+    assert not torch.equal(far, out)
+    plan.close()
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2])
+def test_shallow_trees(F, depth):
+    n = 1500
+    x, y, z = inputs.uniform_cube(n, 3)
+    q = inputs.masses_open_unit(n, 3)
+    pot, acc = run(F, x, y, z, q, 5, 1, depth)
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, 5, 1)
+    ep, ea, per = errs(pot, acc, pref, aref)
+    assert ep < 1e-12 and ea < 1e-12, (ep, ea)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 9])
+def test_tiny_inputs(F, n):
+    x, y, z = inputs.uniform_cube(max(n, 1), 4)
+    q = inputs.masses_open_unit(max(n, 1), 4)
+    x, y, z, q = x[:n], y[:n], z[:n], q[:n]
+    pot, acc = run(F, x, y, z, q, 4, 0, 3)
+    if n:
+        pref, aref = oracle.fmm_uniform(x, y, z, q, 3, 4, 0)
+        np.testing.assert_allclose(pot, pref, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(acc, aref, rtol=1e-10, atol=1e-12 * max(np.abs(aref).max(), 1e-300))
+        if n == 1:
+            assert pot[0] == 0.0 and not acc.any()
+
+
+def test_crowded_and_boundary(F):
+    """All particles in one leaf, others on the cube faces (x = 1 clamps)."""
+    n = 700
+    x, y, z = inputs.uniform_cube(n, 5)
+    x[:400] = 0.3 + 0.01 * x[:400]; y[:400] = 0.6 + 0.01 * y[:400]; z[:400] = 0.1 + 0.01 * z[:400]
+    x[400:410] = 1.0; y[410:420] = 0.0; z[420:430] = 1.0
+    q = inputs.masses_open_unit(n, 5)
+    pot, acc = run(F, x, y, z, q, 6, 1, 3)
+    pref, aref = oracle.fmm_uniform(x, y, z, q, 3, 6, 1)
+    ep, ea, per = errs(pot, acc, pref, aref)
+    assert ep < 1e-12 and ea < 1e-12, (ep, ea)
+
+
+def test_fp32_near_field(F):
+    n, depth, p = 4096, 3, 6
+    x, y, z = inputs.uniform_cube(n, 6)
+    q = inputs.masses_open_unit(n, 6)
+    pot, acc = run(F, x, y, z, q, p, 1, depth, prec=F.FP32)
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, 1)
+    ep, ea, per = errs(pot, acc, pref, aref)
+    assert ep < 1e-6 and ea < 1e-6, (ep, ea)
+
+
+def test_host_entry_point(F):
+    n, depth, p = 3000, 3, 4
+    x, y, z = inputs.uniform_cube(n, 7)
+    q = inputs.masses_open_unit(n, 7)
+    plan = F.Plan(p=p, basis=0, prec=F.FP64, depth=depth)
+    out = np.zeros((4, n))
+    plan.fmm_evaluate_host(x, y, z, q, out[0], out[1], out[2], out[3])
+    pot, acc = plan.evaluate(g(x), g(y), g(z), g(q))
+    np.testing.assert_array_equal(out[0], pot.cpu().numpy())
+    np.testing.assert_array_equal(out[1:], acc.cpu().numpy())
+    plan.close()
+
+
+def test_full_size_sampled_precision_workload(F):
+    """4,194,304 uniform particles, depth 6 (262,144 leaves), traceless p = 8:
+    GPU FP64 FMM against the oracle on 64 sampled particles."""
+    n, depth, p = 4194304, 6, 8
+    x, y, z = inputs.uniform_cube(n, 3)
+    q = inputs.masses_equal(n)
+    pot, acc = run(F, x, y, z, q, p, 1, depth)
+    s = np.sort(np.unique((inputs.u01(3, 90, 64) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, 1, sample=s)
+    ep, ea, per = errs(pot[s], acc[:, s], pref, aref)
+    assert ep < 1e-12 and ea < 1e-12 and per < 1e-10, (ep, ea, per)
