@@ -102,7 +102,10 @@ def test_m2l_pair_random(F, p, basis):
     L32 = torch.zeros((nc, n), device=DEV, dtype=torch.float32)
     F.fmm_op_m2l(p, basis, F.FP32, g(M32, torch.float32), g(r), L32)
     den = abs_terms(p, basis, M32.astype(np.float64), r)
-    e = (np.abs(L32.double().cpu().numpy() - ref32) / den).max()
+    num = np.abs(L32.double().cpu().numpy() - ref32)
+    nz = den > 0
+    assert np.all(num[~nz] == 0)        # exactly vanishing components stay zero
+    e = (num[nz] / den[nz]).max()
     assert e < 1e-5, e
 
 
