@@ -2,12 +2,15 @@
 
 Tolerances (normwise relative error per result):
   * FP64 kernels: 1e-12 per item and rank (expansions) or per item (fields);
+    on random-sign coefficients the condition-aware form below, at 1e-12;
   * FP32 D-tensor: 1e-5 for p <= 8 and 5e-5 for p = 9, 10 (normwise per
     rank; the recurrence loses a few bits to cancellation at high rank);
-  * FP32 per-pair M2L: |L_gpu - L_ref| <= 1e-5 x sum_m |M_m/m! D_{n+m}| per
-    component (condition-aware: random-sign coefficients make L_n itself
-    cancel, so a bound relative to |L_n| would measure the input, not the
-    kernel); on physical multipoles also normwise per rank <= 1e-5.
+  * FP32 per-pair M2L: per item and rank, max |L_gpu - L_ref| <= 1e-5 x
+    max sum_m |M_m/m! D_{n+m}| (condition-aware: random-sign coefficients
+    make single L_n cancel, and at symmetric offsets a D component such as
+    3x^2 - r^2 vanishes exactly in the oracle but only to rounding in FP32,
+    so a bound relative to |L_n| would measure the input, not the kernel);
+    on physical multipoles also normwise per rank <= 1e-5.
 """
 import numpy as np
 import pytest
@@ -64,6 +67,17 @@ def abs_terms(p, basis, M, r):
     return out
 
 
+def cond_err(p, basis, got, ref, den):
+    """per item and rank: max |got - ref| / max sum|terms| (condition-aware)."""
+    num = np.abs(got - ref)
+    rank = oracle.indices(p, basis).sum(1)
+    e = 0.0
+    for j in range(p + 1):
+        sel = rank == j
+        e = max(e, float((num[sel].max(0) / den[sel].max(0)).max()))
+    return e
+
+
 def pair_offsets(n, seed):
     r, _, _ = inputs.m2l_pairs(n, seed)
     return r
@@ -90,23 +104,20 @@ def test_m2l_pair_random(F, p, basis):
     r = pair_offsets(n, 20 + p)
     M = inputs.random_coefficients(nc, n, 30 + p)
     ref = oracle.m2l_batch(p, basis, M, r)
+    den = abs_terms(p, basis, M, r)
     L = torch.zeros((nc, n), device=DEV, dtype=torch.float64)
     F.fmm_op_m2l(p, basis, F.FP64, g(M), g(r), L)
-    assert rank_err(L.cpu().numpy(), ref, p, basis) < 1e-12
+    assert cond_err(p, basis, L.cpu().numpy(), ref, den) < 1e-12
     # accumulate mode adds
     F.fmm_op_m2l(p, basis, F.FP64, g(M), g(r), L, accumulate=True)
-    assert rank_err(L.cpu().numpy(), 2 * ref, p, basis) < 1e-12
+    assert cond_err(p, basis, L.cpu().numpy(), 2 * ref, 2 * den) < 1e-12
     # FP32: compare with the oracle run on the float-rounded input
     M32 = M.astype(np.float32)
     ref32 = oracle.m2l_batch(p, basis, M32.astype(np.float64), r)
     L32 = torch.zeros((nc, n), device=DEV, dtype=torch.float32)
     F.fmm_op_m2l(p, basis, F.FP32, g(M32, torch.float32), g(r), L32)
-    den = abs_terms(p, basis, M32.astype(np.float64), r)
-    num = np.abs(L32.double().cpu().numpy() - ref32)
-    nz = den > 0
-    assert np.all(num[~nz] == 0)        # exactly vanishing components stay zero
-    e = (num[nz] / den[nz]).max()
-    assert e < 1e-5, e
+    den32 = abs_terms(p, basis, M32.astype(np.float64), r)
+    assert cond_err(p, basis, L32.double().cpu().numpy(), ref32, den32) < 1e-5
 
 
 @pytest.mark.parametrize("basis", [0, 1])
@@ -178,8 +189,11 @@ def test_p2m_m2m_l2l_l2p(F, p, basis):
     F.fmm_op_l2p(p, basis, Lg, g(delta), out)
     o = out.cpu().numpy()
     assert np.abs(o[0] - ref3[0]).max() <= 1e-12 * np.abs(ref3[0]).max()
-    gerr = np.linalg.norm(o[1:] - ref3[1:], axis=0) / np.linalg.norm(ref3[1:], axis=0)
-    assert gerr.max() < 1e-12
+    gn = np.linalg.norm(ref3[1:], axis=0)
+    dn = np.linalg.norm(o[1:] - ref3[1:], axis=0)
+    assert np.all(dn[gn == 0] == 0)     # empty cells, and p = 0 (no gradient terms)
+    if (gn > 0).any():
+        assert (dn[gn > 0] / gn[gn > 0]).max() < 1e-12
 
 
 def test_direct_sum(F):
