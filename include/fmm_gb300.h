@@ -200,6 +200,41 @@ int fmm_direct(int64_t n, const double* x, const double* y, const double* z,
                const double* q, int64_t nt, const int64_t* targets, double* pot,
                double* ax, double* ay, double* az, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * No-allocation evaluation.  The paper has no counterpart to this entry
+ * point; it exists for callers that must not allocate device memory --
+ * applications that hand all device memory to their own pool allocator up
+ * front, or that cannot afford the device-wide synchronisation which
+ * cudaMalloc/cudaFree may cause in the middle of a time step.
+ *
+ * fmm_evaluate_noalloc computes what fmm_evaluate computes for a plan with
+ * {p, basis, FMM_FP64, uniform octree of depth `depth`} and returns the same
+ * numbers, but it allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.  Its working memory (sorted particles, leaf
+ * ranges, tree-build counters, expansions, translation matrices, tables) is
+ * one fixed __device__ array of FMM_NOALLOC_BYTES_APPROX bytes that every GPU
+ * which loads this library holds until the process exits.  Limits:
+ * 0 <= n <= FMM_NOALLOC_MAX_N, 0 <= p <= FMM_NOALLOC_MAX_P,
+ * 0 <= depth <= FMM_NOALLOC_MAX_DEPTH; larger sizes return FMM_ERR_ARG with
+ * a message, before any work is queued.  x, y, z, q, pot, ax, ay, az are
+ * device arrays of length n in caller order (outputs overwritten).
+ *
+ * The first call on a device does the set-up (finds the array's device
+ * address, uploads constant tables; synchronous), and a call whose (p, basis)
+ * differs from the previous call's on that device rebuilds the translation
+ * matrices (synchronous).  Make the first call before any stream capture.
+ * Every call on a device shares the one array and overwrites what the
+ * previous call left there; calls that overlap on the GPU (different streams
+ * or threads without ordering between them) race and corrupt each other's
+ * results.  Errors: fmm_last_error(NULL). */
+#define FMM_NOALLOC_MAX_N 65536
+#define FMM_NOALLOC_MAX_DEPTH 3
+#define FMM_NOALLOC_MAX_P 6
+#define FMM_NOALLOC_BYTES_APPROX 5300000
+int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, const double* x, const double* y,
+                         const double* z, const double* q, double* pot, double* ax, double* ay,
+                         double* az, void* stream);
+
 /* Number of kernels this library launched since it was loaded (all plans and
  * operator calls), counted on the host at each launch. */
 int64_t fmm_kernel_launches(void);

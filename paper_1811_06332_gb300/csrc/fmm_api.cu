@@ -100,6 +100,9 @@ static const dtab_launch_t k_dtab[FMM_PMAX + 1] = {
     launch_dtable_p4, launch_dtable_p5, launch_dtable_p6, launch_dtable_p7,
     launch_dtable_p8, launch_dtable_p9, launch_dtable_p10};
 
+// Thread-local error text of plan-less calls, also set by fmm_noalloc.cu.
+std::string& fmm_thread_error() { return t_err; }
+
 static inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
 extern "C" {
@@ -233,7 +236,7 @@ static void free_tree(fmm_plan* pl) {
 // (bit 0: x, bit 1: y, bit 2: z).  Traceless: M2M acts on the reduced
 // representative (embed nz<=1 comps, shift, reduce), L2L on independent
 // components (expand by the trace condition, shift, keep independent rows).
-static void build_translation(int p, int basis, std::vector<double>& W, std::vector<double>& V) {
+void build_translation(int p, int basis, std::vector<double>& W, std::vector<double>& V) {
     const int ns = ns_of(p), nc = ncoef_of(p, basis);
     std::vector<double> Sm((size_t)ns * ns), Vs((size_t)ns * ns);
     W.assign((size_t)8 * nc * nc, 0.0);

@@ -105,6 +105,12 @@ int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const fl
                    cudaStream_t s);
 int grouped_kstride(int p, int basis);
 
+// fmm_api.cu: translation matrices of the uniform octree in scaled units
+}  // namespace fmm
+#include <vector>
+extern "C" __attribute__((visibility("hidden"))) void build_translation(int p, int basis, std::vector<double>& W, std::vector<double>& V);
+namespace fmm {
+
 // fmm_tree.cu
 size_t tree_scratch_bytes(int64_t n, int64_t nleaf);
 int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,

@@ -23,7 +23,7 @@ EXPORTS = [
     "fmm_ncoef", "fmm_create", "fmm_destroy", "fmm_last_error", "fmm_build_tree", "fmm_p2m", "fmm_m2m",
     "fmm_m2l", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate", "fmm_evaluate_host", "fmm_op_dtensor",
     "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
-    "fmm_kernel_launches",
+    "fmm_kernel_launches", "fmm_evaluate_noalloc",
 ]
 
 
@@ -71,6 +71,7 @@ def lib():
             "fmm_op_l2p": ([_int, _int, _i64, _vp, _vp, _vp, _vp], _int),
             "fmm_direct": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_kernel_launches": ([], _i64),
+            "fmm_evaluate_noalloc": ([_int, _int, _int, _i64] + [_vp] * 9, _int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
