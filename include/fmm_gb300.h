@@ -61,7 +61,8 @@ typedef enum { FMM_BASIS_SYM = 0, FMM_BASIS_TRACELESS = 1 } fmm_basis;
 
 typedef enum {
     FMM_FP64 = 0,        /* every operator in FP64                                     */
-    FMM_FP32 = 1,        /* M2L and P2P in FP32 (FP64 tree, P2M, M2M, L2L, L2P)          */
+    FMM_FP32 = 1,        /* P2M, M2L, L2P, P2P arithmetic in FP32; D-tensors, M2M, L2L
+                            and every stored expansion in FP64                           */
     FMM_GEMM_TF32X3 = 2, /* M2L as offset-grouped tensor-core GEMMs, TF32 hi/lo, 3 passes */
     FMM_GEMM_BF16X3 = 3  /* M2L as offset-grouped tensor-core GEMMs, BF16 hi/lo, 3 passes */
 } fmm_precision;

@@ -419,8 +419,8 @@ static double* Llev(fmm_plan* pl, int l) { return pl->Lbuf + pl->lvl_off[l]; }
 int fmm_p2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
     const int d = pl->depth;
-    launch_p2m(pl->cfg.p, pl->cfg.basis, 1, pl->nleaf, nullptr, pl->start, pl->xs, pl->ys, pl->zs, pl->qs,
-               nullptr, d, std::ldexp(1.0, d), Mlev(pl, d), pl->nleaf, g_tab[pl->dev], S(stream));
+    launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, d, pl->nleaf, pl->start, pl->xs,
+                    pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream));
     CKLAUNCH();
     return FMM_OK;
 }
@@ -467,8 +467,9 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
     NEED_TREE();
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
     if (pl->depth >= 2)
-        launch_l2p_leaf(pl->cfg.p, pl->cfg.basis, pl->depth, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs,
-                        pl->perm, Llev(pl, pl->depth), g_tab[pl->dev], pot, ax, ay, az, S(stream));
+        launch_l2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, pl->depth, pl->nleaf,
+                         pl->start, pl->xs, pl->ys, pl->zs, pl->perm, Llev(pl, pl->depth), g_tab[pl->dev], pot, ax,
+                         ay, az, S(stream));
     else
         launch_zero4(pl->n, pot, ax, ay, az, S(stream));
     CKLAUNCH();
@@ -478,8 +479,8 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
 int fmm_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void* stream) {
     NEED_TREE();
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
-    launch_p2p_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->depth, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs,
-                    pl->qs, pl->perm, pot, ax, ay, az, S(stream));
+    launch_p2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->depth, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs,
+                     pl->qs, pl->perm, pot, ax, ay, az, S(stream));
     CKLAUNCH();
     return FMM_OK;
 }

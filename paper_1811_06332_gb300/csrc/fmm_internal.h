@@ -96,6 +96,17 @@ int launch_p2p_leaf(int prec, int depth, int64_t nleaf, const int* start, const 
                     const double* zs, const double* qs, const int* perm, double* pot, double* ax, double* ay,
                     double* az, cudaStream_t s);
 
+// fmm_leafops.cu (prec 0: double arithmetic, 1: float arithmetic)
+int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
+                    const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
+                    cudaStream_t s);
+int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
+                     const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
+                     double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
+                     const double* zs, const double* qs, const int* perm, double* pot, double* ax, double* ay,
+                     double* az, cudaStream_t s);
+
 // fmm_m2l32.cu and generated grp_*.cu
 int launch_build_ktab(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, float* K,
                       cudaStream_t s);

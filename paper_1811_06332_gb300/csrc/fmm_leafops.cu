@@ -1,0 +1,329 @@
+// Leaf kernels of the uniform-octree FMM, specialised per order p and per
+// arithmetic type (double for FMM_FP64, float for the reduced-precision
+// forms; expansions are stored in FP64 either way):
+//   P2M (Eq. P2M):   A_m = sum_a q_a (-(x_a - z)/h)^m, then SYM: Mt = A,
+//                    TRACELESS: Mt = reduced representative of D[A];
+//   L2P (Eq. L2P):   Phi = (1/h) sum_k rho^k/k! Lt_k,
+//                    dPhi/dx_i = (1/h^2) sum_k rho^k/k! Lt_{k+e_i};
+//   P2P (near field over adjacent leaves, self excluded).
+#include "fmm_internal.h"
+
+namespace fmm {
+
+// ---------------------------------------------------------------------------
+// P2M: one warp per leaf.  Particles are staged 32 at a time; lane c owns
+// the column (nx, ny) of multi-indices and walks nz upward, multiplying by
+// the particle's z offset, so each particle costs one product per component.
+// ---------------------------------------------------------------------------
+template <int P, typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
+           const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
+           double* __restrict__ M, const double* __restrict__ reduce, DevOffsets off) {
+    constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
+    constexpr int NCOL = (P + 1) * (P + 2) / 2;
+    __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
+    __shared__ double sA[WARPS][NS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * WARPS + w;
+    if (c >= nleaf) return;
+    int ix, iy, iz;
+    cell_coords(depth, c, ix, iy, iz);
+    const double inv_h = (double)(1 << depth), h = 1.0 / inv_h;
+    const double cx = (ix + 0.5) * h, cy = (iy + 0.5) * h, cz = (iz + 0.5) * h;
+    const int b = start[c], e = start[c + 1];
+    // columns of this lane: col = lane + 32*k -> (nx, ny)
+    constexpr int KC = (NCOL + 31) / 32;
+    T acc[KC][P + 1];
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+#pragma unroll
+        for (int j = 0; j <= P; ++j) acc[k][j] = T(0);
+    int cnx[KC], cny[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        int col = lane + 32 * k, nx = 0;
+        while (nx <= P && col >= P + 1 - nx) { col -= P + 1 - nx; ++nx; }
+        cnx[k] = nx;
+        cny[k] = col;
+    }
+    for (int a0 = b; a0 < e; a0 += 32) {
+        const int a = a0 + lane;
+        __syncwarp();
+        if (a < e) {
+            sx[w][lane] = T((cx - xs[a]) * inv_h);   // -(x_a - z)/h
+            sy[w][lane] = T((cy - ys[a]) * inv_h);
+            sz[w][lane] = T((cz - zs[a]) * inv_h);
+            sq[w][lane] = T(qs[a]);
+        }
+        __syncwarp();
+        const int cnt = min(32, e - a0);
+        for (int i = 0; i < cnt; ++i) {
+            const T rx = sx[w][i], ry = sy[w][i], rz = sz[w][i], qa = sq[w][i];
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                if (lane + 32 * k < NCOL) {
+                    T wgt = qa;
+                    for (int t = 0; t < cnx[k]; ++t) wgt *= rx;
+                    for (int t = 0; t < cny[k]; ++t) wgt *= ry;
+                    const int rem = P - cnx[k] - cny[k];
+#pragma unroll
+                    for (int j = 0; j <= P; ++j) {
+                        if (j <= rem) { acc[k][j] += wgt; wgt *= rz; }
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        if (lane + 32 * k < NCOL) {
+            const int rem = P - cnx[k] - cny[k];
+#pragma unroll
+            for (int j = 0; j <= P; ++j)
+                if (j <= rem) sA[w][pos_sym(cnx[k], cny[k], j)] = (double)acc[k][j];
+        }
+    }
+    __syncwarp();
+    if (!basis) {
+        for (int s = lane; s < NS; s += 32) M[(int64_t)s * nleaf + c] = sA[w][s];
+        return;
+    }
+    constexpr int NT = (P + 1) * (P + 1);
+    for (int t = lane; t < NT; t += 32) {
+        const int j = c_tl_idx[t][0] + c_tl_idx[t][1] + c_tl_idx[t][2];
+        const int cols = (j + 1) * (j + 2) / 2;
+        const double* R = reduce + off.reduce[j] + (t - j * j) * cols;
+        const double* As = &sA[w][ns_of(j - 1)];
+        double v = 0.0;
+        for (int s = 0; s < cols; ++s) v += R[s] * As[s];
+        M[(int64_t)t * nleaf + c] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2P: one warp per leaf, lanes over particles.  The expansion (full
+// symmetric, dependent traceless components rebuilt) sits in shared memory
+// and every lane reads the same coefficient at the same time.  Nested sums
+// Phi = sum_kx ax[kx] sum_ky ay[ky] sum_kz az[kz] L[kx,ky,kz].
+// ---------------------------------------------------------------------------
+template <int P, typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
+            const double* __restrict__ ys, const double* __restrict__ zs, const int* __restrict__ perm,
+            const double* __restrict__ Lt, const double* __restrict__ expand, DevOffsets off,
+            double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az) {
+    constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
+    __shared__ double sA[WARPS][NS];
+    __shared__ T sL[WARPS][NS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * WARPS + w;
+    if (c >= nleaf) return;
+    const int b = start[c], e = start[c + 1];
+    if (b == e) return;
+    if (basis) {
+        constexpr int NT = (P + 1) * (P + 1);
+        for (int t = lane; t < NT; t += 32) sA[w][t] = Lt[(int64_t)t * nleaf + c];
+        __syncwarp();
+        for (int s = lane; s < NS; s += 32) {
+            const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
+            const int j = nx + ny + nz;
+            const int row = (j - nx) * (j - nx + 1) / 2 + nz;
+            const double* E = expand + off.expand[j] + row * (2 * j + 1);
+            double v = 0.0;
+            for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][j * j + t];
+            sL[w][s] = T(v);
+        }
+    } else {
+        for (int s = lane; s < NS; s += 32) sL[w][s] = T(Lt[(int64_t)s * nleaf + c]);
+    }
+    __syncwarp();
+    int ix, iy, iz;
+    cell_coords(depth, c, ix, iy, iz);
+    const double inv_h = (double)(1 << depth), h = 1.0 / inv_h;
+    const double cx = (ix + 0.5) * h, cy = (iy + 0.5) * h, cz = (iz + 0.5) * h;
+    const T* L = sL[w];
+    for (int a0 = b; a0 < e; a0 += 32) {
+        const int a = a0 + lane;
+        if (a >= e) break;
+        const T rx = T((xs[a] - cx) * inv_h), ry = T((ys[a] - cy) * inv_h), rz = T((zs[a] - cz) * inv_h);
+        T fx[P + 1], fy[P + 1], fz[P + 1];
+        fx[0] = fy[0] = fz[0] = T(1);
+#pragma unroll
+        for (int k = 1; k <= P; ++k) {
+            fx[k] = fx[k - 1] * rx * T(1.0 / k);
+            fy[k] = fy[k - 1] * ry * T(1.0 / k);
+            fz[k] = fz[k - 1] * rz * T(1.0 / k);
+        }
+        T ph = 0, gx = 0, gy = 0, gz = 0;
+#pragma unroll
+        for (int kx = 0; kx <= P; ++kx) {
+            T sx_p = 0, sx_gx = 0, sx_gy = 0, sx_gz = 0;
+#pragma unroll
+            for (int ky = 0; ky <= P - kx; ++ky) {
+                T s_p = 0, s_gx = 0, s_gy = 0, s_gz = 0;
+#pragma unroll
+                for (int kz = 0; kz <= P - kx - ky; ++kz) {
+                    s_p += fz[kz] * L[pos_sym(kx, ky, kz)];
+                    if (kx + ky + kz < P) {
+                        s_gx += fz[kz] * L[pos_sym(kx + 1, ky, kz)];
+                        s_gy += fz[kz] * L[pos_sym(kx, ky + 1, kz)];
+                        s_gz += fz[kz] * L[pos_sym(kx, ky, kz + 1)];
+                    }
+                }
+                sx_p += fy[ky] * s_p; sx_gx += fy[ky] * s_gx; sx_gy += fy[ky] * s_gy; sx_gz += fy[ky] * s_gz;
+            }
+            ph += fx[kx] * sx_p; gx += fx[kx] * sx_gx; gy += fx[kx] * sx_gy; gz += fx[kx] * sx_gz;
+        }
+        const int o = perm[a];
+        pot[o] = -(double)ph * inv_h;
+        ax[o] = (double)gx * inv_h * inv_h;
+        ay[o] = (double)gy * inv_h * inv_h;
+        az[o] = (double)gz * inv_h * inv_h;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P2P: one warp per target leaf.  Targets of a pass are spread over lane
+// groups (tp = next power of two >= targets, G = 32/tp groups), each group
+// takes every G-th staged source, and the groups are summed by shuffles.
+// ---------------------------------------------------------------------------
+template <typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_p2p_leaf2(int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
+            const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
+            const int* __restrict__ perm, double* __restrict__ pot, double* __restrict__ ax,
+            double* __restrict__ ay, double* __restrict__ az) {
+    __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
+    __shared__ int sid[WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * WARPS + w;
+    if (c >= nleaf) return;
+    const int b = start[c], e = start[c + 1];
+    if (b == e) return;
+    const int side = 1 << depth;
+    int ix, iy, iz;
+    cell_coords(depth, c, ix, iy, iz);
+    const double h = 1.0 / side;
+    const double cx = (ix + 0.5) * h, cy = (iy + 0.5) * h, cz = (iz + 0.5) * h;
+    for (int t0 = b; t0 < e; t0 += 32) {
+        const int tn = min(32, e - t0);
+        int tp = 1;
+        while (tp < tn) tp <<= 1;
+        const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
+        const int ti = t0 + tl;
+        const bool act = tl < tn;
+        const T xi = act ? T(xs[ti] - cx) : T(0), yi = act ? T(ys[ti] - cy) : T(0), zi = act ? T(zs[ti] - cz) : T(0);
+        T ph = 0, gx = 0, gy = 0, gz = 0;
+#pragma unroll 1
+        for (int nb = 0; nb < 27; ++nb) {
+            const int jx = ix - 1 + nb % 3, jy = iy - 1 + (nb / 3) % 3, jz = iz - 1 + nb / 9;
+            if (jx < 0 || jy < 0 || jz < 0 || jx >= side || jy >= side || jz >= side) continue;
+            const int64_t S = cell_index(depth, jx, jy, jz);
+            const int sb = start[S], se = start[S + 1];
+            for (int s0 = sb; s0 < se; s0 += 32) {
+                __syncwarp();
+                const int sj = s0 + lane;
+                if (sj < se) {
+                    sx[w][lane] = T(xs[sj] - cx);
+                    sy[w][lane] = T(ys[sj] - cy);
+                    sz[w][lane] = T(zs[sj] - cz);
+                    sq[w][lane] = T(qs[sj]);
+                    sid[w][lane] = sj;
+                }
+                __syncwarp();
+                const int cnt = min(32, se - s0);
+                if (act) {
+                    for (int k = grp; k < cnt; k += G) {
+                        const T dx = sx[w][k] - xi, dy = sy[w][k] - yi, dz = sz[w][k] - zi;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        if (sid[w][k] == ti || r2 == T(0)) continue;
+                        const T ir = fmm_rsqrt(r2);
+                        const T qir = sq[w][k] * ir;
+                        const T qir3 = qir * ir * ir;
+                        ph += qir;
+                        gx += qir3 * dx; gy += qir3 * dy; gz += qir3 * dz;
+                    }
+                }
+            }
+        }
+        for (int o = tp; o < 32; o <<= 1) {
+            ph += __shfl_xor_sync(0xffffffffu, ph, o);
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+            gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        }
+        if (act && grp == 0) {
+            const int o = perm[ti];
+            pot[o] -= (double)ph;
+            ax[o] += (double)gx;
+            ay[o] += (double)gy;
+            az[o] += (double)gz;
+        }
+    }
+}
+
+template <int P, typename T>
+static void p2m_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
+                       const double* zs, const double* qs, double* M, const DevTables& Tb, cudaStream_t s) {
+    constexpr int W = 4;
+    k_p2m_leaf<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(basis, depth, nleaf, start, xs, ys, zs,
+                                                                           qs, M, Tb.reduce, Tb.offsets());
+}
+template <int P, typename T>
+static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
+                       const double* zs, const int* perm, const double* Lt, const DevTables& Tb, double* pot,
+                       double* ax, double* ay, double* az, cudaStream_t s) {
+    constexpr int W = 4;
+    k_l2p_leaf2<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(
+        basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb.expand, Tb.offsets(), pot, ax, ay, az);
+}
+
+#define FMM_P_SWITCH(P_, CALL) \
+    switch (P_) {              \
+        case 0: CALL(0); break; case 1: CALL(1); break; case 2: CALL(2); break; case 3: CALL(3); break; \
+        case 4: CALL(4); break; case 5: CALL(5); break; case 6: CALL(6); break; case 7: CALL(7); break; \
+        case 8: CALL(8); break; case 9: CALL(9); break; default: CALL(10); break; }
+
+int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
+                    const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
+                    cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+#define C64(P) p2m_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s)
+#define C32(P) p2m_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s)
+    if (prec == 0) { FMM_P_SWITCH(p, C64) } else { FMM_P_SWITCH(p, C32) }
+#undef C64
+#undef C32
+    count_launch();
+    return 0;
+}
+
+int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
+                     const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
+                     double* pot, double* ax, double* ay, double* az, cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+#define C64(P) l2p_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s)
+#define C32(P) l2p_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s)
+    if (prec == 0) { FMM_P_SWITCH(p, C64) } else { FMM_P_SWITCH(p, C32) }
+#undef C64
+#undef C32
+    count_launch();
+    return 0;
+}
+
+int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
+                     const double* zs, const double* qs, const int* perm, double* pot, double* ax, double* ay,
+                     double* az, cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+    constexpr int W = 4;
+    const unsigned g = (unsigned)((nleaf + W - 1) / W);
+    if (prec == 0)
+        k_p2p_leaf2<double, W><<<g, W * 32, 0, s>>>(depth, nleaf, start, xs, ys, zs, qs, perm, pot, ax, ay, az);
+    else
+        k_p2p_leaf2<float, W><<<g, W * 32, 0, s>>>(depth, nleaf, start, xs, ys, zs, qs, perm, pot, ax, ay, az);
+    count_launch();
+    return 0;
+}
+
+}  // namespace fmm
