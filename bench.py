@@ -173,7 +173,7 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    forms = {"fp64": F.FP64, "fp32": F.FP32}
+    forms = {"fp64": F.FP64, "fp32": F.FP32, "bf16x3": F.GEMM_BF16X3}
     form = args.form
     prec = forms[form]
     # each rank evaluates its own independent particle set (weak scaling)
@@ -240,6 +240,12 @@ def run_gpu(args):
     fma = m2l_fma_per_pair(P, BASIS)
     pk, pk_kind = peaks()
     mhz = pk.get("sm_max_mhz", 2070.0)
+    tc = None
+    if prec == F.GEMM_BF16X3:
+        # executed tensor-core work of levels 4..6: per tile of 128 targets and
+        # offset, 3 passes of a 128 x 96 x 96 BF16 product
+        tiles = sum(8 ** (l - 1) // 128 * 8 for l in range(4, DEPTH + 1))
+        tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * 96 * 96}
     if prec == F.FP64:
         peak = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
         peak_note = "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
@@ -251,6 +257,15 @@ def run_gpu(args):
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "peak_source": peak_note, "flops_per_pair": 2 * fma,
             "m2l_ms_per_step": m2l_ms}
+    if tc is not None:
+        bf = pk.get("bf16_tflops", 1900.0)
+        ex = tc["executed_flop_per_step"] / (m2l_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "m2l (tensor cores at levels 4..6; FP32 SIMT at 2..3)",
+                "achieved": ex, "peak": bf, "unit": "TFLOP/s", "frac": ex / bf, "traffic": None,
+                "peak_source": "bf16_tflops of MEASURED_PEAKS.json (%s, burst)" % pk_kind,
+                "executed_flop_per_step": tc["executed_flop_per_step"],
+                "algorithmic_flop_per_step": npairs * 2 * fma,
+                "algorithmic_tflops": achieved, "m2l_ms_per_step": m2l_ms}
 
     # plain FP64 GPU form beside it (same workload, fewer steps)
     fp64 = None
@@ -297,7 +312,9 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32 (M2L, P2P) + f64"}[form],
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32 (P2M, M2L, L2P, P2P) + f64",
+                  "bf16x3": "bf16x3 tensor-core M2L + f32 (P2M, L2P, P2P) + f64"}[form],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": form, "p": P, "basis": "traceless", "depth": DEPTH,
                    "particles_per_gpu": N_PART, "m2l_pairs": npairs, "l2": "flushed (256 MiB write) before each step"},
@@ -378,7 +395,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32", "bf16x3"])
     ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l"])
     ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
     ap.add_argument("--no-cpu", action="store_true")

@@ -47,10 +47,22 @@ struct fmm_plan {
     float* K32 = nullptr;    // 343 x kstride packed FP32 M2L matrices (FMM_FP32)
     float* M32 = nullptr;    // FP32 copy of the multipoles (FMM_FP32)
     int kst = 0;
+    // tensor-core form (FMM_GEMM_BF16X3)
+    void* Kbf = nullptr;                 // 343 x {hi, lo} preformatted matrices
+    void* Mbf = nullptr;                 // per level >= 4: hi then lo operand tiles
+    int64_t mbf_off[FMM_PMAX + 2];       // element offset of level l's hi block
+    std::vector<unsigned char> maps;     // tensor maps, one block per level
+    int* derr = nullptr;                 // device error word (bounded waits)
     // host-call staging
     double* stage = nullptr;
     int64_t stage_n = 0;
 };
+
+static void* tc_maps_at(fmm_plan* pl, int l) {
+    // 64-byte aligned block of the host-side tensor maps of level l
+    uintptr_t b = ((uintptr_t)pl->maps.data() + 63) & ~(uintptr_t)63;
+    return (void*)(b + (size_t)l * tc_maps_bytes());
+}
 
 static int fail_plan(fmm_plan* pl, int code, const char* fmt, ...) {
     char buf[512];
@@ -219,8 +231,9 @@ int fmm_direct(int64_t n, const double* x, const double* y, const double* z, con
 static void free_tree(fmm_plan* pl) {
     cudaFree(pl->xs); cudaFree(pl->ys); cudaFree(pl->zs); cudaFree(pl->qs);
     cudaFree(pl->perm); cudaFree(pl->start); cudaFree(pl->scratch);
-    cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32);
+    cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32); cudaFree(pl->Mbf);
     pl->M32 = nullptr;
+    pl->Mbf = nullptr;
     pl->xs = pl->ys = pl->zs = pl->qs = nullptr;
     pl->perm = pl->start = nullptr;
     pl->scratch = nullptr;
@@ -309,7 +322,9 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     if (cfg->prec < FMM_FP64 || cfg->prec > FMM_GEMM_BF16X3) FAIL(FMM_ERR_ARG, "unknown precision %d", cfg->prec);
     if (cfg->adaptive) FAIL(FMM_ERR_UNSUPPORTED, "adaptive trees are not available in this build");
     if (cfg->depth < 0 || cfg->depth > 9) FAIL(FMM_ERR_ARG, "depth=%d outside 0..9", cfg->depth);
-    if (cfg->prec >= FMM_GEMM_TF32X3) FAIL(FMM_ERR_UNSUPPORTED, "tensor-core M2L forms are not available yet");
+    if (cfg->prec == FMM_GEMM_TF32X3) FAIL(FMM_ERR_UNSUPPORTED, "the TF32x3 tensor-core form is not available yet");
+    if (cfg->prec == FMM_GEMM_BF16X3 && !tc_supported(cfg->p, cfg->basis))
+        FAIL(FMM_ERR_UNSUPPORTED, "the tensor-core form needs the traceless basis and 1 <= p <= 8");
     pl = new fmm_plan();
     pl->cfg = *cfg;
     pl->depth = cfg->depth;
@@ -346,7 +361,12 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
     cudaFree(doffs);
-    if (ok && cfg->prec == FMM_FP32) {
+    if (ok && cfg->prec == FMM_GEMM_BF16X3) {
+        ok = cudaMalloc(&pl->Kbf, tc_b_bytes()) == cudaSuccess && cudaMalloc(&pl->derr, sizeof(int)) == cudaSuccess &&
+             cudaMemset(pl->derr, 0, sizeof(int)) == cudaSuccess && tc_build_b(cfg->p, pl->Dtab, pl->Kbf, 0) == 0 &&
+             cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (ok && (cfg->prec == FMM_FP32 || cfg->prec == FMM_GEMM_BF16X3)) {
         pl->kst = grouped_kstride(cfg->p, cfg->basis);
         const int cap = pl->kst;
         std::vector<unsigned char> ent((size_t)6 * cap);
@@ -373,6 +393,7 @@ void fmm_destroy(fmm_plan* pl) {
     if (!pl) return;
     free_tree(pl);
     cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32);
+    cudaFree(pl->Kbf); cudaFree(pl->derr);
     delete pl;
 }
 
@@ -394,10 +415,31 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             cudaMalloc(&pl->start, (pl->nleaf + 1) * 4) != cudaSuccess ||
             cudaMalloc(&pl->scratch, pl->scratch_bytes) != cudaSuccess ||
             cudaMalloc(&pl->Mbuf, tot * 8) != cudaSuccess || cudaMalloc(&pl->Lbuf, tot * 8) != cudaSuccess ||
-            (pl->cfg.prec == FMM_FP32 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess)) {
+            (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess)) {
             cudaGetLastError();
             free_tree(pl);
             FAIL(FMM_ERR_OOM, "allocating tree storage for n=%lld failed", (long long)n);
+        }
+        if (pl->cfg.prec == FMM_GEMM_BF16X3) {
+            int64_t tb = 0;
+            for (int l = 0; l <= pl->depth; ++l) {
+                pl->mbf_off[l] = tb;
+                if (l >= 4) tb += 2 * (int64_t)tc_m_elems(l);
+            }
+            pl->maps.assign((size_t)(pl->depth + 1) * tc_maps_bytes() + 64, 0);
+            if (tb > 0 && cudaMalloc(&pl->Mbf, tb * 2) != cudaSuccess) {
+                cudaGetLastError();
+                free_tree(pl);
+                FAIL(FMM_ERR_OOM, "allocating tensor-core operands failed");
+            }
+            for (int l = 4; l <= pl->depth; ++l) {
+                char* hi = (char*)pl->Mbf + pl->mbf_off[l] * 2;
+                char* lo = hi + tc_m_elems(l) * 2;
+                if (tc_encode_maps(l, hi, lo, tc_maps_at(pl, l)) != 0) {
+                    free_tree(pl);
+                    FAIL(FMM_ERR_CUDA, "encoding TMA tensor maps failed");
+                }
+            }
         }
         pl->n = n;
     }
@@ -436,6 +478,26 @@ int fmm_m2m(fmm_plan* pl, void* stream) {
 
 int fmm_m2l(fmm_plan* pl, void* stream) {
     NEED_TREE();
+    if (pl->cfg.prec == FMM_GEMM_BF16X3 && pl->depth >= 2) {
+        // levels 2..3 (grids smaller than one 8x4x4 tile) on the FP32 grouped kernel
+        const int lt = pl->depth < 3 ? pl->depth : 3;
+        const int64_t b = pl->lvl_off[2], e = pl->lvl_off[lt] + ((int64_t)pl->nc << (3 * lt));
+        launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
+        for (int l = 2; l <= lt; ++l) {
+            const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
+                                             pl->K32, (int64_t)1 << (3 * l), S(stream));
+            for (int k = 0; k < parts; ++k) count_launch();
+        }
+        for (int l = 4; l <= pl->depth; ++l) {
+            char* hi = (char*)pl->Mbf + pl->mbf_off[l] * 2;
+            char* lo = hi + tc_m_elems(l) * 2;
+            if (tc_m2l_level(pl->cfg.p, l, Mlev(pl, l), hi, lo, tc_maps_at(pl, l), pl->Kbf, Llev(pl, l), pl->derr,
+                             S(stream)) != 0)
+                FAIL(FMM_ERR_CUDA, "tensor-core M2L launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        CKLAUNCH();
+        return FMM_OK;
+    }
     if (pl->cfg.prec == FMM_FP32 && pl->depth >= 2) {
         const int64_t b = pl->lvl_off[2], e = pl->lvl_off[pl->depth] + ((int64_t)pl->nc << (3 * pl->depth));
         launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
@@ -526,6 +588,11 @@ int fmm_evaluate_host(fmm_plan* pl, int64_t n, const double* x, const double* y,
     if (rc) return rc;
     for (int k = 0; k < 4; ++k) CK(cudaMemcpyAsync(outp[k], d + (size_t)(4 + k) * n, b, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (pl->derr) {
+        int herr = 0;
+        CK(cudaMemcpy(&herr, pl->derr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) FAIL(FMM_ERR_TIMEOUT, "a bounded wait in the tensor-core M2L gave up (code %d)", herr);
+    }
     return FMM_OK;
 }
 

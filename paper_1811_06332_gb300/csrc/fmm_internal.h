@@ -122,6 +122,16 @@ int grouped_kstride(int p, int basis);
 extern "C" __attribute__((visibility("hidden"))) void build_translation(int p, int basis, std::vector<double>& W, std::vector<double>& V);
 namespace fmm {
 
+// fmm_m2l_tc.cu (tensor-core offset-grouped M2L, traceless basis)
+int tc_supported(int p, int basis);
+size_t tc_b_bytes();
+size_t tc_m_elems(int l);
+size_t tc_maps_bytes();
+int tc_build_b(int p, const double* Dtab, void* B, cudaStream_t s);
+int tc_encode_maps(int l, void* hi, void* lo, void* out_maps);
+int tc_m2l_level(int p, int l, const double* M, void* hi, void* lo, const void* maps, const void* B, double* Lt,
+                 int* err, cudaStream_t s);
+
 // fmm_tree.cu
 size_t tree_scratch_bytes(int64_t n, int64_t nleaf);
 int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,

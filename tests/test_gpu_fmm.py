@@ -157,3 +157,25 @@ def test_full_size_sampled_precision_workload(F):
     pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, 1, sample=s)
     ep, ea, per = errs(pot[s], acc[:, s], pref, aref)
     assert ep < 1e-12 and ea < 1e-12 and per < 1e-10, (ep, ea, per)
+
+
+@pytest.mark.parametrize("depth,n", [(4, 40000), (5, 131072)])
+def test_tensor_core_form_vs_oracle(F, depth, n):
+    """Offset-grouped tensor-core M2L (BF16 hi/lo, three passes, FP32
+    accumulation in TMEM; levels >= 4), traceless p = 8, against the FP64
+    oracle on 200 sampled particles.  Split BF16 products keep ~16 bits, so
+    the tolerance is 5e-5 normwise on pot and acc."""
+    x, y, z = inputs.uniform_cube(n, 11 + depth)
+    q = inputs.masses_equal(n)
+    pot, acc = run(F, x, y, z, q, 8, 1, depth, prec=F.GEMM_BF16X3)
+    s = np.sort(np.unique((inputs.u01(7, 92, 200) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, 8, 1, sample=s)
+    ep, ea, per = errs(pot[s], acc[:, s], pref, aref)
+    assert ep < 5e-5 and ea < 5e-5, (ep, ea, per)
+
+
+def test_tensor_core_form_rejects_unsupported(F):
+    with pytest.raises(F.FMMError):
+        F.Plan(p=9, basis=1, prec=F.GEMM_BF16X3, depth=4)
+    with pytest.raises(F.FMMError):
+        F.Plan(p=6, basis=0, prec=F.GEMM_BF16X3, depth=4)
