@@ -53,6 +53,10 @@ struct fmm_plan {
     int64_t mbf_off[FMM_PMAX + 2];       // element offset of level l's hi block
     std::vector<unsigned char> maps;     // tensor maps, one block per level
     int* derr = nullptr;                 // device error word (bounded waits)
+    // FP32 forms: positions relative to leaf centres, packed FP32 shifts
+    float4* pos32 = nullptr;
+    float* W32 = nullptr;
+    float* V32 = nullptr;
     // host-call staging
     double* stage = nullptr;
     int64_t stage_n = 0;
@@ -231,7 +235,8 @@ int fmm_direct(int64_t n, const double* x, const double* y, const double* z, con
 static void free_tree(fmm_plan* pl) {
     cudaFree(pl->xs); cudaFree(pl->ys); cudaFree(pl->zs); cudaFree(pl->qs);
     cudaFree(pl->perm); cudaFree(pl->start); cudaFree(pl->scratch);
-    cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32); cudaFree(pl->Mbf);
+    cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32); cudaFree(pl->Mbf); cudaFree(pl->pos32);
+    pl->pos32 = nullptr;
     pl->M32 = nullptr;
     pl->Mbf = nullptr;
     pl->xs = pl->ys = pl->zs = pl->qs = nullptr;
@@ -361,6 +366,28 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
     cudaFree(doffs);
+    if (ok && cfg->prec != FMM_FP64 && shift32_supported(cfg->p, cfg->basis)) {
+        // FP32 shift matrices packed row by row: M2M row n keeps the columns of
+        // rank <= |n| (a prefix), L2L row n those of rank >= |n| (a suffix)
+        const int nc = pl->nc;
+        auto pre = [&](int k) { return k < 0 ? 0 : (cfg->basis ? (k + 1) * (k + 1) : ns_of(k)); };
+        std::vector<float> w32, v32;
+        for (int c = 0; c < 8; ++c) {
+            for (int r = 0; r < nc; ++r) {
+                const unsigned char* n = cfg->basis ? fmm_tl_idx[r] : fmm_sym_idx[r];
+                const int rk = n[0] + n[1] + n[2];
+                for (int k = 0; k < pre(rk); ++k) w32.push_back((float)W[((size_t)c * nc + r) * nc + k]);
+            }
+            for (int r = 0; r < nc; ++r) {
+                const unsigned char* n = cfg->basis ? fmm_tl_idx[r] : fmm_sym_idx[r];
+                const int rk = n[0] + n[1] + n[2];
+                for (int k = pre(rk - 1); k < nc; ++k) v32.push_back((float)V[((size_t)c * nc + r) * nc + k]);
+            }
+        }
+        ok = cudaMalloc(&pl->W32, w32.size() * 4) == cudaSuccess && cudaMalloc(&pl->V32, v32.size() * 4) == cudaSuccess &&
+             cudaMemcpy(pl->W32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(pl->V32, v32.data(), v32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     if (ok && cfg->prec == FMM_GEMM_BF16X3) {
         ok = cudaMalloc(&pl->Kbf, tc_b_bytes()) == cudaSuccess && cudaMalloc(&pl->derr, sizeof(int)) == cudaSuccess &&
              cudaMemset(pl->derr, 0, sizeof(int)) == cudaSuccess && tc_build_b(cfg->p, pl->Dtab, pl->Kbf, 0) == 0 &&
@@ -393,7 +420,7 @@ void fmm_destroy(fmm_plan* pl) {
     if (!pl) return;
     free_tree(pl);
     cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32);
-    cudaFree(pl->Kbf); cudaFree(pl->derr);
+    cudaFree(pl->Kbf); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32);
     delete pl;
 }
 
@@ -415,7 +442,8 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             cudaMalloc(&pl->start, (pl->nleaf + 1) * 4) != cudaSuccess ||
             cudaMalloc(&pl->scratch, pl->scratch_bytes) != cudaSuccess ||
             cudaMalloc(&pl->Mbuf, tot * 8) != cudaSuccess || cudaMalloc(&pl->Lbuf, tot * 8) != cudaSuccess ||
-            (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess)) {
+            (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess) ||
+            (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->pos32, nn * 16) != cudaSuccess)) {
             cudaGetLastError();
             free_tree(pl);
             FAIL(FMM_ERR_OOM, "allocating tree storage for n=%lld failed", (long long)n);
@@ -444,7 +472,7 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
         pl->n = n;
     }
     if (launch_uniform_tree(n, pl->depth, x, y, z, q, pl->xs, pl->ys, pl->zs, pl->qs, pl->perm, pl->start,
-                            pl->scratch, S(stream)) != 0)
+                            pl->scratch, S(stream), pl->pos32) != 0)
         FAIL(FMM_ERR_CUDA, "tree build failed: %s", cudaGetErrorString(cudaGetLastError()));
     CKLAUNCH();
     pl->built = true;
@@ -462,13 +490,22 @@ int fmm_p2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
     const int d = pl->depth;
     launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, d, pl->nleaf, pl->start, pl->xs,
-                    pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream));
+                    pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32);
     CKLAUNCH();
     return FMM_OK;
 }
 
 int fmm_m2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
+    if (pl->W32) {
+        for (int l = pl->depth - 1; l >= 2; --l) {
+            launch_shift32(pl->cfg.p, pl->cfg.basis, 1, l, pl->W32, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
+                           Mlev(pl, l), (int64_t)1 << (3 * l), S(stream));
+            count_launch();
+        }
+        CKLAUNCH();
+        return FMM_OK;
+    }
     for (int l = pl->depth - 1; l >= 2; --l)
         launch_m2m_level(pl->cfg.p, pl->cfg.basis, l, pl->W, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
                          Mlev(pl, l), (int64_t)1 << (3 * l), S(stream));
@@ -518,6 +555,15 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
 
 int fmm_l2l(fmm_plan* pl, void* stream) {
     NEED_TREE();
+    if (pl->V32) {
+        for (int l = 2; l < pl->depth; ++l) {
+            launch_shift32(pl->cfg.p, pl->cfg.basis, 0, l, pl->V32, Llev(pl, l), (int64_t)1 << (3 * l),
+                           Llev(pl, l + 1), (int64_t)1 << (3 * (l + 1)), S(stream));
+            count_launch();
+        }
+        CKLAUNCH();
+        return FMM_OK;
+    }
     for (int l = 2; l < pl->depth; ++l)
         launch_l2l_level(pl->cfg.p, pl->cfg.basis, l, pl->V, Llev(pl, l), (int64_t)1 << (3 * l), Llev(pl, l + 1),
                          (int64_t)1 << (3 * (l + 1)), S(stream));
@@ -531,7 +577,7 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
     if (pl->depth >= 2)
         launch_l2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, pl->depth, pl->nleaf,
                          pl->start, pl->xs, pl->ys, pl->zs, pl->perm, Llev(pl, pl->depth), g_tab[pl->dev], pot, ax,
-                         ay, az, S(stream));
+                         ay, az, S(stream), pl->pos32);
     else
         launch_zero4(pl->n, pot, ax, ay, az, S(stream));
     CKLAUNCH();
@@ -541,8 +587,11 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
 int fmm_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void* stream) {
     NEED_TREE();
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
-    launch_p2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->depth, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs,
-                     pl->qs, pl->perm, pot, ax, ay, az, S(stream));
+    if (pl->pos32)
+        launch_p2p32(pl->depth, pl->nleaf, pl->start, pl->pos32, pl->perm, pot, ax, ay, az, S(stream));
+    else
+        launch_p2p_leaf2(0, pl->depth, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs, pl->qs, pl->perm, pot, ax, ay,
+                         az, S(stream));
     CKLAUNCH();
     return FMM_OK;
 }

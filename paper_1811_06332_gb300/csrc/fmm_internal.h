@@ -99,10 +99,11 @@ int launch_p2p_leaf(int prec, int depth, int64_t nleaf, const int* start, const 
 // fmm_leafops.cu (prec 0: double arithmetic, 1: float arithmetic)
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                     const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
-                    cudaStream_t s);
+                    cudaStream_t s, const float4* pos32 = nullptr);
 int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                      const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
-                     double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+                     double* pot, double* ax, double* ay, double* az, cudaStream_t s,
+                     const float4* pos32 = nullptr);
 int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
                      const double* zs, const double* qs, const int* perm, double* pot, double* ax, double* ay,
                      double* az, cudaStream_t s);
@@ -122,6 +123,13 @@ int grouped_kstride(int p, int basis);
 extern "C" __attribute__((visibility("hidden"))) void build_translation(int p, int basis, std::vector<double>& W, std::vector<double>& V);
 namespace fmm {
 
+// generated shift_*.cu: FP32 level shifts (m2m = 1: M2M, 0: L2L)
+int launch_shift32(int p, int basis, int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,
+                   int64_t ny, cudaStream_t s);
+int shift32_supported(int p, int basis);
+int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm, double* pot,
+                 double* ax, double* ay, double* az, cudaStream_t s);
+
 // fmm_m2l_tc.cu (tensor-core offset-grouped M2L, traceless basis)
 int tc_supported(int p, int basis);
 size_t tc_b_bytes();
@@ -136,6 +144,6 @@ int tc_m2l_level(int p, int l, const double* M, void* hi, void* lo, const void* 
 size_t tree_scratch_bytes(int64_t n, int64_t nleaf);
 int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,
                         double* xs, double* ys, double* zs, double* qs, int* perm, int* start, void* scratch,
-                        cudaStream_t s);
+                        cudaStream_t s, float4* pos32 = nullptr);
 
 }  // namespace fmm

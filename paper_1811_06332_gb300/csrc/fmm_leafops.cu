@@ -19,7 +19,8 @@ template <int P, typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
            const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
-           double* __restrict__ M, const double* __restrict__ reduce, DevOffsets off) {
+           double* __restrict__ M, const double* __restrict__ reduce, DevOffsets off,
+           const float4* __restrict__ pos32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
     __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
@@ -51,10 +52,18 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
         const int a = a0 + lane;
         __syncwarp();
         if (a < e) {
-            sx[w][lane] = T((cx - xs[a]) * inv_h);   // -(x_a - z)/h
-            sy[w][lane] = T((cy - ys[a]) * inv_h);
-            sz[w][lane] = T((cz - zs[a]) * inv_h);
-            sq[w][lane] = T(qs[a]);
+            if (pos32) {   // FP32 offsets from the leaf centre
+                const float4 v = pos32[a];
+                sx[w][lane] = T(-v.x * (float)inv_h);
+                sy[w][lane] = T(-v.y * (float)inv_h);
+                sz[w][lane] = T(-v.z * (float)inv_h);
+                sq[w][lane] = T(v.w);
+            } else {
+                sx[w][lane] = T((cx - xs[a]) * inv_h);   // -(x_a - z)/h
+                sy[w][lane] = T((cy - ys[a]) * inv_h);
+                sz[w][lane] = T((cz - zs[a]) * inv_h);
+                sq[w][lane] = T(qs[a]);
+            }
         }
         __syncwarp();
         const int cnt = min(32, e - a0);
@@ -113,7 +122,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
             const double* __restrict__ ys, const double* __restrict__ zs, const int* __restrict__ perm,
             const double* __restrict__ Lt, const double* __restrict__ expand, DevOffsets off,
-            double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az) {
+            double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az,
+            const float4* __restrict__ pos32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     __shared__ double sA[WARPS][NS];
     __shared__ T sL[WARPS][NS];
@@ -147,7 +157,13 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
     for (int a0 = b; a0 < e; a0 += 32) {
         const int a = a0 + lane;
         if (a >= e) break;
-        const T rx = T((xs[a] - cx) * inv_h), ry = T((ys[a] - cy) * inv_h), rz = T((zs[a] - cz) * inv_h);
+        T rx, ry, rz;
+        if (pos32) {
+            const float4 v = pos32[a];
+            rx = T(v.x * (float)inv_h); ry = T(v.y * (float)inv_h); rz = T(v.z * (float)inv_h);
+        } else {
+            rx = T((xs[a] - cx) * inv_h); ry = T((ys[a] - cy) * inv_h); rz = T((zs[a] - cz) * inv_h);
+        }
         T fx[P + 1], fy[P + 1], fz[P + 1];
         fx[0] = fy[0] = fz[0] = T(1);
 #pragma unroll
@@ -266,18 +282,19 @@ k_p2p_leaf2(int depth, int64_t nleaf, const int* __restrict__ start, const doubl
 
 template <int P, typename T>
 static void p2m_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
-                       const double* zs, const double* qs, double* M, const DevTables& Tb, cudaStream_t s) {
+                       const double* zs, const double* qs, double* M, const DevTables& Tb, cudaStream_t s,
+                       const float4* pos32) {
     constexpr int W = 4;
     k_p2m_leaf<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(basis, depth, nleaf, start, xs, ys, zs,
-                                                                           qs, M, Tb.reduce, Tb.offsets());
+                                                                           qs, M, Tb.reduce, Tb.offsets(), pos32);
 }
 template <int P, typename T>
 static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
                        const double* zs, const int* perm, const double* Lt, const DevTables& Tb, double* pot,
-                       double* ax, double* ay, double* az, cudaStream_t s) {
+                       double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32) {
     constexpr int W = 4;
     k_l2p_leaf2<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(
-        basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb.expand, Tb.offsets(), pot, ax, ay, az);
+        basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb.expand, Tb.offsets(), pot, ax, ay, az, pos32);
 }
 
 #define FMM_P_SWITCH(P_, CALL) \
@@ -288,10 +305,10 @@ static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, co
 
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                     const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
-                    cudaStream_t s) {
+                    cudaStream_t s, const float4* pos32) {
     if (nleaf <= 0) return 0;
-#define C64(P) p2m_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s)
-#define C32(P) p2m_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s)
+#define C64(P) p2m_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, nullptr)
+#define C32(P) p2m_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, pos32)
     if (prec == 0) { FMM_P_SWITCH(p, C64) } else { FMM_P_SWITCH(p, C32) }
 #undef C64
 #undef C32
@@ -301,10 +318,10 @@ int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const 
 
 int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                      const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
-                     double* pot, double* ax, double* ay, double* az, cudaStream_t s) {
+                     double* pot, double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32) {
     if (nleaf <= 0) return 0;
-#define C64(P) l2p_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s)
-#define C32(P) l2p_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s)
+#define C64(P) l2p_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s, nullptr)
+#define C32(P) l2p_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s, pos32)
     if (prec == 0) { FMM_P_SWITCH(p, C64) } else { FMM_P_SWITCH(p, C32) }
 #undef C64
 #undef C32
@@ -322,6 +339,101 @@ int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const
         k_p2p_leaf2<double, W><<<g, W * 32, 0, s>>>(depth, nleaf, start, xs, ys, zs, qs, perm, pot, ax, ay, az);
     else
         k_p2p_leaf2<float, W><<<g, W * 32, 0, s>>>(depth, nleaf, start, xs, ys, zs, qs, perm, pot, ax, ay, az);
+    count_launch();
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 P2P on positions relative to leaf centres: one warp per target leaf,
+// two targets per lane (each staged source is used twice from registers),
+// lane groups split the sources, one 16-byte shared load per source.  The
+// self pair and coincident pairs have r^2 == 0 exactly and are dropped by a
+// select, as the direct sum skips them.
+// ---------------------------------------------------------------------------
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* __restrict__ pos,
+        const int* __restrict__ perm, double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay,
+        double* __restrict__ az) {
+    __shared__ float4 sP[WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * WARPS + w;
+    if (c >= nleaf) return;
+    const int b = start[c], e = start[c + 1];
+    if (b == e) return;
+    const int side = 1 << depth;
+    const float h = 1.0f / (float)side;
+    int ix, iy, iz;
+    cell_coords(depth, c, ix, iy, iz);
+    for (int t0 = b; t0 < e; t0 += 64) {
+        const int tn = min(64, e - t0), half = (tn + 1) >> 1;
+        int tp = 1;
+        while (tp < half) tp <<= 1;
+        const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
+        const int ta = t0 + tl, tb = t0 + tl + tp;
+        const bool va = tl < tn, vb = tl + tp < tn;
+        const float4 pa = va ? pos[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 pb = vb ? pos[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float fa = 0.f, xa = 0.f, ya = 0.f, za = 0.f, fb = 0.f, xb = 0.f, yb = 0.f, zb = 0.f;
+#pragma unroll 1
+        for (int nb = 0; nb < 27; ++nb) {
+            const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+            const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+            if (jx < 0 || jy < 0 || jz < 0 || jx >= side || jy >= side || jz >= side) continue;
+            const int64_t S = cell_index(depth, jx, jy, jz);
+            const int sb = start[S], se = start[S + 1];
+            const float ox = dx * h, oy = dy * h, oz = dz * h;
+            for (int s0 = sb; s0 < se; s0 += 32) {
+                __syncwarp();
+                if (s0 + lane < se) {
+                    const float4 v = pos[s0 + lane];
+                    sP[w][lane] = make_float4(v.x + ox, v.y + oy, v.z + oz, v.w);
+                }
+                __syncwarp();
+                const int cnt = min(32, se - s0);
+                for (int k = grp; k < cnt; k += G) {
+                    const float4 sv = sP[w][k];
+                    {
+                        const float rx = sv.x - pa.x, ry = sv.y - pa.y, rz = sv.z - pa.z;
+                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        const float qir = sv.w * ir, qir3 = qir * ir * ir;
+                        fa += qir; xa = fmaf(qir3, rx, xa); ya = fmaf(qir3, ry, ya); za = fmaf(qir3, rz, za);
+                    }
+                    {
+                        const float rx = sv.x - pb.x, ry = sv.y - pb.y, rz = sv.z - pb.z;
+                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        const float qir = sv.w * ir, qir3 = qir * ir * ir;
+                        fb += qir; xb = fmaf(qir3, rx, xb); yb = fmaf(qir3, ry, yb); zb = fmaf(qir3, rz, zb);
+                    }
+                }
+            }
+        }
+        for (int o = tp; o < 32; o <<= 1) {
+            fa += __shfl_xor_sync(0xffffffffu, fa, o); xa += __shfl_xor_sync(0xffffffffu, xa, o);
+            ya += __shfl_xor_sync(0xffffffffu, ya, o); za += __shfl_xor_sync(0xffffffffu, za, o);
+            fb += __shfl_xor_sync(0xffffffffu, fb, o); xb += __shfl_xor_sync(0xffffffffu, xb, o);
+            yb += __shfl_xor_sync(0xffffffffu, yb, o); zb += __shfl_xor_sync(0xffffffffu, zb, o);
+        }
+        if (grp == 0) {
+            if (va) {
+                const int o = perm[ta];
+                pot[o] -= (double)fa; ax[o] += (double)xa; ay[o] += (double)ya; az[o] += (double)za;
+            }
+            if (vb) {
+                const int o = perm[tb];
+                pot[o] -= (double)fb; ax[o] += (double)xb; ay[o] += (double)yb; az[o] += (double)zb;
+            }
+        }
+    }
+}
+
+int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm, double* pot,
+                 double* ax, double* ay, double* az, cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+    constexpr int W = 4;
+    k_p2p32<W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(depth, nleaf, start, pos, perm, pot, ax, ay, az);
     count_launch();
     return 0;
 }

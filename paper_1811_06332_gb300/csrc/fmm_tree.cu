@@ -123,17 +123,27 @@ __global__ void k_leaf_sort(int64_t nleaf, const int* __restrict__ start, int* _
 __global__ void k_gather(int64_t n, const int* __restrict__ order, const double* __restrict__ x,
                          const double* __restrict__ y, const double* __restrict__ z, const double* __restrict__ q,
                          double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ zs,
-                         double* __restrict__ qs, int* __restrict__ perm) {
+                         double* __restrict__ qs, int* __restrict__ perm, int depth, const int* __restrict__ key,
+                         float4* __restrict__ pos32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = order[i];
-    xs[i] = x[o]; ys[i] = y[o]; zs[i] = z[o]; qs[i] = q[o];
+    const double xo = x[o], yo = y[o], zo = z[o], qo = q[o];
+    xs[i] = xo; ys[i] = yo; zs[i] = zo; qs[i] = qo;
     perm[i] = o;
+    if (pos32) {
+        // FP32 position relative to the centre of the particle's own leaf
+        int ix, iy, iz;
+        cell_coords(depth, key[o], ix, iy, iz);
+        const double h = 1.0 / (double)(1 << depth);
+        pos32[i] = make_float4((float)(xo - (ix + 0.5) * h), (float)(yo - (iy + 0.5) * h),
+                               (float)(zo - (iz + 0.5) * h), (float)qo);
+    }
 }
 
 int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,
                         double* xs, double* ys, double* zs, double* qs, int* perm, int* start, void* scratch,
-                        cudaStream_t s) {
+                        cudaStream_t s, float4* pos32) {
     const int64_t nleaf = (int64_t)1 << (3 * depth);
     char* p = (char*)scratch;
     int* key = (int*)p;   p += align_up(n * 4, 256);
@@ -154,7 +164,8 @@ int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, 
     k_leaf_sort<<<(unsigned)((nleaf + 255) / 256), 256, 0, s>>>(nleaf, start, order);
     count_launch();
     if (n > 0) {
-        k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, order, x, y, z, q, xs, ys, zs, qs, perm);
+        k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, order, x, y, z, q, xs, ys, zs, qs, perm, depth, key,
+                                                             pos32);
         count_launch();
     }
     return 0;

@@ -464,6 +464,137 @@ def emit_grouped_file(p, basis):
     return "\n".join(L) + "\n"
 
 
+def shift_layout(p, basis, upper):
+    """Packed layout of the level-independent shift matrices (scaled units).
+    M2M (upper=False): row n uses columns of rank <= |n| (a prefix);
+    L2L (upper=True): row n uses columns of rank >= |n| (a suffix).
+    Returns (rows, (c0, c1) column range per row, packed offset, size)."""
+    rows = sym_list(p) if basis == 0 else tl_list(p)
+    pre = (lambda k: ns(k)) if basis == 0 else (lambda k: nt(k))
+    nc = len(rows)
+    rng = []
+    for n in rows:
+        a = sum(n)
+        rng.append((pre(a - 1) if a > 0 else 0, nc) if upper else (0, pre(a)))
+    off = [0]
+    for c0, c1 in rng:
+        off.append(off[-1] + c1 - c0)
+    return rows, rng, off, off[-1]
+
+
+def shift32_ok(p, basis):
+    return 2 * (ns(p) if basis == 0 else nt(p)) <= 180
+
+
+def emit_shift_file(p, basis):
+    """FP32 M2M / L2L on one uniform level (scaled units).  M2M: one thread
+    per parent, the eight child matrices staged in shared memory in turn.
+    L2L: one thread per child, all threads of a block in one child class,
+    which selects the matrix.  Expansions stay FP64 in memory; L2L adds its
+    FP32 result into the FP64 local expansion."""
+    L = ['// Generated by gen.py: FP32 level shifts (M2M, L2L), p = %d, basis %d.' % (p, basis),
+         '#include "../fmm_device.cuh"', "namespace fmm {"]
+    nc = ns(p) if basis == 0 else nt(p)
+    if shift32_ok(p, basis):
+        # ---- M2M ----
+        rows, rng, off, sz = shift_layout(p, basis, False)
+        L.append("__global__ void __launch_bounds__(128)")
+        L.append("m2m32_p%d_b%d(int l, const float* __restrict__ W, const double* __restrict__ Mch, int64_t nch,"
+                 " double* __restrict__ Mpa, int64_t npa) {" % (p, basis))
+        L.append("  __shared__ float sW[%d];" % sz)
+        L.append("  const int64_t P = (int64_t)blockIdx.x * 128 + threadIdx.x;")
+        L.append("  const bool act = P < npa;")
+        L.append("  int ix = 0, iy = 0, iz = 0;")
+        L.append("  if (act) cell_coords(l, P, ix, iy, iz);")
+        L.append("  const int64_t lin = lin_index(l, ix, iy, iz), blk = (int64_t)1 << (3 * l);")
+        for r in range(nc):
+            L.append("  float a%d = 0.f;" % r)
+        L.append("  #pragma unroll 1")
+        L.append("  for (int c = 0; c < 8; ++c) {")
+        L.append("    __syncthreads();")
+        L.append("    for (int e = threadIdx.x; e < %d; e += 128) sW[e] = W[c * %d + e];" % (sz, sz))
+        L.append("    __syncthreads();")
+        L.append("    if (!act) continue;")
+        L.append("    const int64_t ch = c * blk + lin;")
+        for k in range(nc):
+            L.append("    const float x%d = (float)Mch[(int64_t)%d * nch + ch];" % (k, k))
+        for r in range(nc):
+            c0, c1 = rng[r]
+            for k in range(c0, c1):
+                L.append("    a%d = fmaf(sW[%d], x%d, a%d);" % (r, off[r] + k - c0, k, r))
+        L.append("  }")
+        L.append("  if (!act) return;")
+        for r in range(nc):
+            L.append("  Mpa[(int64_t)%d * npa + P] = (double)a%d;" % (r, r))
+        L.append("}")
+        # ---- L2L ----
+        rows, rng, off, sz = shift_layout(p, basis, True)
+        L.append("__global__ void __launch_bounds__(128)")
+        L.append("l2l32_p%d_b%d(int l, const float* __restrict__ V, const double* __restrict__ Lpa, int64_t npa,"
+                 " double* __restrict__ Lch, int64_t nch) {" % (p, basis))
+        L.append("  __shared__ float sV[%d];" % sz)
+        L.append("  const int64_t blk = (int64_t)1 << (3 * l), bpc = (blk + 127) / 128;")
+        L.append("  const int c = (int)(blockIdx.x / bpc);")
+        L.append("  const int64_t lin = (int64_t)(blockIdx.x % bpc) * 128 + threadIdx.x;")
+        L.append("  for (int e = threadIdx.x; e < %d; e += 128) sV[e] = V[c * %d + e];" % (sz, sz))
+        L.append("  __syncthreads();")
+        L.append("  if (lin >= blk) return;")
+        L.append("  const int s = 1 << l;")
+        L.append("  const int px = (int)(lin % s), py = (int)((lin / s) % s), pz = (int)(lin / ((int64_t)s * s));")
+        L.append("  const int64_t P = cell_index(l, px, py, pz), C = c * blk + lin;")
+        for k in range(nc):
+            L.append("  const float x%d = (float)Lpa[(int64_t)%d * npa + P];" % (k, k))
+        for r in range(nc):
+            c0, c1 = rng[r]
+            terms = " + ".join([])
+            L.append("  {")
+            L.append("    float a = 0.f;")
+            for k in range(c0, c1):
+                L.append("    a = fmaf(sV[%d], x%d, a);" % (off[r] + k - c0, k))
+            L.append("    Lch[(int64_t)%d * nch + C] += (double)a;" % r)
+            L.append("  }")
+        L.append("}")
+    L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,"
+             " int64_t ny, cudaStream_t s) {" % (p, basis))
+    if shift32_ok(p, basis):
+        L.append("  if (m2m) m2m32_p%d_b%d<<<(unsigned)((ny + 127) / 128), 128, 0, s>>>(l, A, X, nx, Y, ny);"
+                 % (p, basis))
+        L.append("  else l2l32_p%d_b%d<<<(unsigned)(8 * ((((int64_t)1 << (3 * l)) + 127) / 128)), 128, 0, s>>>"
+                 "(l, A, X, nx, Y, ny);" % (p, basis))
+        L.append("  return 0;")
+    else:
+        L.append("  return -1;")
+    L.append("}")
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
+def emit_shift_dispatch():
+    L = ['// Generated by gen.py: dispatch and packed layouts of the FP32 level shifts.',
+         '#include "../fmm_device.cuh"', "namespace fmm {"]
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx,"
+                     " double* Y, int64_t ny, cudaStream_t s);" % (p, b))
+    L.append("int launch_shift32(int p, int basis, int m2m, int l, const float* A, const double* X, int64_t nx,"
+             " double* Y, int64_t ny, cudaStream_t s) {")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("  if (p == %d && basis == %d) return launch_shift32_p%d_b%d(m2m, l, A, X, nx, Y, ny, s);"
+                     % (p, b, p, b))
+    L.append("  return -1;")
+    L.append("}")
+    # packed entry lists (row, column) for host-side packing
+    L.append("int shift32_supported(int p, int basis) {")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("  if (p == %d && basis == %d) return %d;" % (p, b, 1 if shift32_ok(p, b) else 0))
+    L.append("  return 0;")
+    L.append("}")
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
 def emit_grouped_dispatch():
     L = ['// Generated by gen.py: dispatch and layout of the FP32 offset-grouped M2L.',
          '#include "../fmm_device.cuh"', "namespace fmm {"]
@@ -542,6 +673,14 @@ def generate(out=OUT):
             fg = os.path.join(out, "grp_P%d_b%d.cu" % (p, basis))
             write_if_changed(fg, emit_grouped_file(p, basis))
             files.append(fg)
+    for p in range(0, PMAX + 1):
+        for basis in (0, 1):
+            fs = os.path.join(out, "shift_P%d_b%d.cu" % (p, basis))
+            write_if_changed(fs, emit_shift_file(p, basis))
+            files.append(fs)
+    fsd = os.path.join(out, "shift_dispatch.cu")
+    write_if_changed(fsd, emit_shift_dispatch())
+    files.append(fsd)
     fd = os.path.join(out, "grp_dispatch.cu")
     write_if_changed(fd, emit_grouped_dispatch())
     files.append(fd)
