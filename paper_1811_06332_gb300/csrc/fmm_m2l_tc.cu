@@ -15,8 +15,9 @@
 //
 // Roles: warp 0 lane 0 issues copies, warp 1 owns TMEM and lane 0 issues
 // tcgen05.mma, warps 2..5 drain TMEM (each reads its lane quadrant).
-// Stages form a 2-deep mbarrier ring; every wait is bounded and reports a
+// Stages form a 3-deep mbarrier ring; every wait is bounded and reports a
 // timeout through an error word instead of hanging.
+#include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -28,13 +29,26 @@ namespace fmm {
 constexpr int TC_K = 96;                       // padded multipole components (K)
 constexpr int TC_N = 96;                       // padded local components (N)
 constexpr int TC_CH = TC_K / 8;                // 16-byte chunks along K
+constexpr int TC_NCH = TC_N / 16;              // N-chunks of 16 local components
 constexpr int TC_A_BYTES = 128 * TC_K * 2;     // 24576
-constexpr int TC_B_BYTES = TC_N * TC_K * 2;    // 18432
-constexpr int TC_STAGE = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
-constexpr int TC_STAGES = 2;
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE + 1024 + 256;
+constexpr int TC_BMAX = TC_N * TC_K * 2;       // 18432: bound on one packed matrix
+constexpr int TC_STAGES = 3;
 constexpr int TC_TMEM_COLS = 128;
 constexpr long TC_SPIN = 1L << 24;             // bounded waits
+
+// The matrix of one offset is block-triangular in rank (|n| + |m| <= p), so
+// local components are processed in N-chunks of 16: chunk j (rows 16j..16j+15,
+// lowest rank a_j) only multiplies multipole components of rank <= p - a_j,
+// i.e. the first kch[j] K-steps of 16.  Chunk j's packed block holds 16 rows
+// x 16 kch[j] columns in the K-major core-matrix layout (SBO = 256 kch[j]).
+struct TcChunks {
+    int cw;             // chunk width (local components per chunk, N of one MMA)
+    int nch;            // chunks holding real rows
+    int kch[TC_NCH];    // K-steps of chunk j
+    int boff[TC_NCH];   // byte offset of chunk j inside a packed matrix
+    int bbytes;         // bytes of one packed matrix (hi or lo)
+    int nst;            // pipeline stages that fit in shared memory (2 or 3)
+};
 
 struct TcMaps {
     CUtensorMap hi[8];
@@ -80,11 +94,12 @@ __host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N) {
 __device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
 
 __global__ void __launch_bounds__(192, 1)
-k_m2l_tc(const __grid_constant__ TcMaps maps, int l, int nrows, const __nv_bfloat16* __restrict__ Kmat,
-         double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
+k_m2l_tc(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrows,
+         const __nv_bfloat16* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = (uint64_t*)(smem + TC_STAGES * TC_STAGE);
+    const int TC_STAGE = 2 * TC_A_BYTES + 2 * ch.bbytes;   // bbytes is a multiple of 1024
+    uint64_t* bars = (uint64_t*)(smem + ch.nst * TC_STAGE);
     uint64_t* full = bars;                 // [TC_STAGES]
     uint64_t* empty = bars + TC_STAGES;    // [TC_STAGES]
     uint64_t* done = bars + 2 * TC_STAGES;
@@ -99,7 +114,7 @@ k_m2l_tc(const __grid_constant__ TcMaps maps, int l, int nrows, const __nv_bfloa
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < ch.nst; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
         }
@@ -123,8 +138,8 @@ k_m2l_tc(const __grid_constant__ TcMaps maps, int l, int nrows, const __nv_bfloa
         for (int u = 0; u < 216 && ok; ++u) {
             const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;
             if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-            const int s = it % TC_STAGES;
-            const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+            const int s = it % ch.nst;
+            const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
             if (!(ok = mbar_wait(smem_u32(&empty[s]), ph ^ 1u, err, 1))) break;
             const uint32_t fb = smem_u32(&full[s]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(TC_STAGE) : "memory");
@@ -145,49 +160,48 @@ k_m2l_tc(const __grid_constant__ TcMaps maps, int l, int nrows, const __nv_bfloa
                 "l"((uint64_t)ml), "r"(0), "r"(c1), "r"(0), "r"(c3), "r"(c4), "r"(fb)
                 : "memory");
             const int ridx = (3 - oz) * 49 + (3 - oy) * 7 + (3 - ox);   // r = target - source = -o
-            const __nv_bfloat16* kb = Kmat + (int64_t)ridx * 2 * (TC_N * TC_K);
+            const unsigned char* kb = (const unsigned char*)Kmat + (int64_t)ridx * 2 * ch.bbytes;
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                              smem_u32(st + 2 * TC_A_BYTES)),
-                         "l"((uint64_t)kb), "r"(TC_B_BYTES), "r"(fb)
-                         : "memory");
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                             smem_u32(st + 2 * TC_A_BYTES + TC_B_BYTES)),
-                         "l"((uint64_t)(kb + TC_N * TC_K)), "r"(TC_B_BYTES), "r"(fb)
+                         "l"((uint64_t)kb), "r"(2 * ch.bbytes), "r"(fb)
                          : "memory");
             ++it;
         }
         // drain: every issued stage has landed before the CTA may exit
-        const int first = it > TC_STAGES ? it - TC_STAGES : 0;
+        const int first = it > ch.nst ? it - ch.nst : 0;
         for (int k = first; k < it; ++k)
-            mbar_wait(smem_u32(&full[k % TC_STAGES]), (uint32_t)(k / TC_STAGES) & 1u, err, 2);
+            mbar_wait(smem_u32(&full[k % ch.nst]), (uint32_t)(k / ch.nst) & 1u, err, 2);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        constexpr uint32_t idesc = make_idesc_bf16(128, TC_N);
+        const uint32_t idesc = make_idesc_bf16(128, ch.cw);
         int it = 0;
         bool ok = true;
         for (int u = 0; u < 216; ++u) {
             const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;
             if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-            const int s = it % TC_STAGES;
-            const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+            const int s = it % ch.nst;
+            const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
             if (!(ok = mbar_wait(smem_u32(&full[s]), ph, err, 3))) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t base = smem_u32(smem + s * TC_STAGE);
             const uint32_t a_addr[2] = {base, base + TC_A_BYTES};
-            const uint32_t b_addr[2] = {base + 2 * TC_A_BYTES, base + 2 * TC_A_BYTES + TC_B_BYTES};
+            const uint32_t b_addr[2] = {base + 2 * TC_A_BYTES, base + 2 * TC_A_BYTES + ch.bbytes};
+            for (int j = 0; j < ch.nch; ++j) {
+                const uint32_t dcol = tmem + (uint32_t)(ch.cw * j);
+                const uint32_t sbo = 256u * ch.kch[j];
 #pragma unroll
-            for (int pass = 0; pass < 3; ++pass) {
-                const int ia = pass == 2 ? 1 : 0, ib = pass == 1 ? 1 : 0;   // hi.hi, hi.lo, lo.hi
-#pragma unroll
-                for (int ks = 0; ks < TC_K / 16; ++ks) {
-                    const uint64_t ad = make_desc(a_addr[ia] + ks * 256, 128, TC_CH * 128);
-                    const uint64_t bd = make_desc(b_addr[ib] + ks * 256, 128, TC_CH * 128);
-                    const uint32_t acc = (it > 0 || pass > 0 || ks > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                        : "memory");
+                for (int pass = 0; pass < 3; ++pass) {
+                    const int ia = pass == 2 ? 1 : 0, ib = pass == 1 ? 1 : 0;   // hi.hi, hi.lo, lo.hi
+                    for (int ks = 0; ks < ch.kch[j]; ++ks) {
+                        const uint64_t ad = make_desc(a_addr[ia] + ks * 256, 128, TC_CH * 128);
+                        const uint64_t bd = make_desc(b_addr[ib] + ch.boff[j] + ks * 256, 128, sbo);
+                        const uint32_t acc = (it > 0 || pass > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -275,13 +289,18 @@ __global__ void k_tc_split_m(int l, int nc, const double* __restrict__ M, __nv_b
 
 // Kt_r(n, m) = D_{n+m}(r)/m! (traceless basis, reduced multipole columns),
 // zero outside |n| + |m| <= p and in the padding, split into BF16 hi/lo and
-// stored per offset in the K-major no-swizzle core-matrix layout:
-// byte (n/8)*SBO + (m/8)*128 + (n%8)*16 + (m%8)*2 with SBO = 12*128.
-__global__ void k_tc_build_b(int p, int nc, const double* __restrict__ Dtab, __nv_bfloat16* __restrict__ B) {
+// stored per offset as N-chunks: chunk j = rows 16j..16j+15 by 16 kch[j]
+// columns, K-major core-matrix layout, byte (r/8)*256 kch[j] + (m/8)*128 +
+// (r%8)*16 + (m%8)*2 inside the chunk.  One thread per (offset, row, column
+// group of 8).
+__global__ void k_tc_build_b(int p, int nc, const TcChunks ch, const double* __restrict__ Dtab,
+                             __nv_bfloat16* __restrict__ B) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)343 * TC_N * TC_CH) return;
     const int r = (int)(t / (TC_N * TC_CH));
     const int n = (int)((t / TC_CH) % TC_N), c = (int)(t % TC_CH);
+    const int j = n / ch.cw, rr = n % ch.cw;
+    if (j >= ch.nch || c >= 2 * ch.kch[j]) return;
     const int ns = ns_of(p);
     __align__(16) __nv_bfloat16 vh[8], vl[8];
 #pragma unroll
@@ -299,10 +318,10 @@ __global__ void k_tc_build_b(int p, int nc, const double* __restrict__ Dtab, __n
         vh[e] = h;
         vl[e] = __double2bfloat16(v - (double)__bfloat162float(h));
     }
-    const int64_t off = (int64_t)(n / 8) * (TC_CH * 64) + (int64_t)c * 64 + (n % 8) * 8;  // in elements
-    __nv_bfloat16* bh = B + (int64_t)r * 2 * (TC_N * TC_K);
-    *(uint4*)(bh + off) = *(const uint4*)vh;
-    *(uint4*)(bh + TC_N * TC_K + off) = *(const uint4*)vl;
+    const int64_t boff = ch.boff[j] + (rr / 8) * 256 * ch.kch[j] + c * 128 + (rr % 8) * 16;   // bytes
+    unsigned char* bh = (unsigned char*)B + (int64_t)r * 2 * ch.bbytes;
+    *(uint4*)(bh + boff) = *(const uint4*)vh;
+    *(uint4*)(bh + ch.bbytes + boff) = *(const uint4*)vl;
 }
 
 // ---------------------------------------------------------------------------
@@ -311,12 +330,52 @@ __global__ void k_tc_build_b(int p, int nc, const double* __restrict__ Dtab, __n
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 int tc_supported(int p, int basis) { return basis == 1 && p >= 1 && ncoef_of(p, basis) <= TC_K; }
-size_t tc_b_bytes() { return (size_t)343 * 2 * TC_N * TC_K * sizeof(__nv_bfloat16); }
+size_t tc_b_bytes() { return (size_t)343 * 2 * TC_BMAX; }
+
+// Chunk width: the N of one MMA.  Wider chunks issue fewer, larger MMAs;
+// narrower ones skip more of the zero triangle.  FMM_TC_CHUNK (16, 32, 48 or
+// 96) overrides the default for tuning.
+static int tc_chunk_width() {
+    static int cw = 0;
+    if (!cw) {
+        cw = 32;
+        if (const char* e = getenv("FMM_TC_CHUNK")) {
+            const int v = atoi(e);
+            if (v == 16 || v == 32 || v == 48 || v == 96) cw = v;
+        }
+    }
+    return cw;
+}
+
+static TcChunks tc_chunks(int p) {
+    TcChunks c;
+    const int nc = ncoef_of(p, 1);
+    c.cw = tc_chunk_width();
+    c.nch = (nc + c.cw - 1) / c.cw;
+    int off = 0;
+    for (int j = 0; j < TC_NCH; ++j) {
+        c.kch[j] = 0;
+        c.boff[j] = off;
+        if (j < c.nch) {
+            const int r0 = c.cw * j;
+            const int a = fmm_tl_idx[r0][0] + fmm_tl_idx[r0][1] + fmm_tl_idx[r0][2];   // lowest rank in chunk
+            const int cols = (p - a + 1) * (p - a + 1);
+            c.kch[j] = (cols + 15) / 16;
+            off += 32 * c.cw * c.kch[j];
+        }
+    }
+    c.bbytes = (off + 1023) / 1024 * 1024;
+    c.nst = TC_STAGES * (2 * TC_A_BYTES + 2 * c.bbytes) + 1280 <= 227 * 1024 ? TC_STAGES : 2;
+    return c;
+}
+
 size_t tc_m_elems(int l) { return l < 1 ? 0 : ((size_t)8 << (3 * (l - 1))) * TC_K; }
 
 int tc_build_b(int p, const double* Dtab, void* B, cudaStream_t s) {
     const int64_t tot = (int64_t)343 * TC_N * TC_CH;
-    k_tc_build_b<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p, ncoef_of(p, 1), Dtab, (__nv_bfloat16*)B);
+    if (cudaMemsetAsync(B, 0, tc_b_bytes(), s) != cudaSuccess) return -2;
+    k_tc_build_b<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p), Dtab,
+                                                               (__nv_bfloat16*)B);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
@@ -362,15 +421,12 @@ int tc_m2l_level(int p, int l, const double* M, void* hi, void* lo, const void* 
     const int64_t tot = ncell * TC_CH;
     k_tc_split_m<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(l, nc, M, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
     count_launch();
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
-            return -2;
-        attr = true;
-    }
+    const TcChunks ch = tc_chunks(p);
+    const int smem = ch.nst * (2 * TC_A_BYTES + 2 * ch.bbytes) + 1024 + 256;
+    if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return -2;
     const int tpc = (hs / 8) * (hs / 4) * (hs / 4);
-    k_m2l_tc<<<(unsigned)(8 * tpc), 192, TC_SMEM, s>>>(*(const TcMaps*)maps, l, nc, (const __nv_bfloat16*)B, Lt,
-                                                       ncell, err);
+    k_m2l_tc<<<(unsigned)(8 * tpc), 192, smem, s>>>(*(const TcMaps*)maps, ch, l, nc, (const __nv_bfloat16*)B, Lt,
+                                                    ncell, err);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
