@@ -39,6 +39,11 @@ SEED = 3
 WORKLOAD = "uniform cube, 4,194,304 particles, equal masses 1/N, depth-6 octree (262,144 leaves), traceless p=8"
 L2_FLUSH_BYTES = 256 << 20
 NOMINAL = {"sm_count": 152, "fp64_fma_per_clk_sm": 2, "fp32_fma_per_clk_sm": 128}
+# DRAM bytes (read + write) of the M2L kernels per step, from one ncu capture
+# of the level-6 launch (profiles/m2l_*_level6_uniform4M_p8.md) scaled by the
+# cells of all M2L levels; set to None whenever the kernel changes.
+M2L_TRAFFIC = {"fp32": (643.8e6 + 154.9e6) * (299584 / 262144),
+               "bf16x3": (772.4e6 + 174.4e6) * (299520 / 262144)}
 
 
 def peaks():
@@ -255,13 +260,13 @@ def run_gpu(args):
     achieved = npairs * fma * 2 / (m2l_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "m2l (levels 2..6, %d pairs per step)" % npairs,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": peak_note, "flops_per_pair": 2 * fma,
+            "traffic": M2L_TRAFFIC.get(form), "peak_source": peak_note, "flops_per_pair": 2 * fma,
             "m2l_ms_per_step": m2l_ms}
     if tc is not None:
         bf = pk.get("bf16_tflops", 1900.0)
         ex = tc["executed_flop_per_step"] / (m2l_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": "m2l (tensor cores at levels 4..6; FP32 SIMT at 2..3)",
-                "achieved": ex, "peak": bf, "unit": "TFLOP/s", "frac": ex / bf, "traffic": None,
+                "achieved": ex, "peak": bf, "unit": "TFLOP/s", "frac": ex / bf, "traffic": M2L_TRAFFIC.get(form),
                 "peak_source": "bf16_tflops of MEASURED_PEAKS.json (%s, burst)" % pk_kind,
                 "executed_flop_per_step": tc["executed_flop_per_step"],
                 "algorithmic_flop_per_step": npairs * 2 * fma,
