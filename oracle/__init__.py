@@ -19,6 +19,8 @@ is all in that C file, each routine citing the equation it restates:
 * ``direct``       -- Eq. PhiAB (App. B), O(N^2)
 * ``fmm_uniform``  -- App. C on a uniform octree with the standard
                       (Chebyshev distance >= 2) separation criterion
+* ``fmm_adaptive`` -- App. C on an adaptive octree: MAC
+                      theta |z_A - z_B| > r_A + r_B, dual-tree traversal
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (closed forms, finite differences, identities,
@@ -70,6 +72,10 @@ def lib():
         L.orc_fmm_uniform.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int64, _i64p, _dp, _dp, _dp, _dp]
         L.orc_fmm_uniform.restype = ctypes.c_int
+        L.orc_fmm_adaptive.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i64p, _dp, _dp, _dp, _dp,
+                                       _i64p]
+        L.orc_fmm_adaptive.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -222,3 +228,25 @@ def fmm_uniform(x, y, z, q, depth: int, p: int, basis: int, sample=None):
     if rc != 0:
         raise ValueError("orc_fmm_uniform rejected its arguments")
     return pot, np.stack([ax, ay, az])
+
+
+def fmm_adaptive(x, y, z, q, max_leaf: int, theta: float, p: int, basis: int, sample=None):
+    """Adaptive-octree FMM with the dual-tree traversal and MAC of App. C.
+
+    Returns pot (n,), acc (3, n) and stats {nodes, m2l_pairs, p2p_pairs,
+    leaves}; with ``sample`` only those particles are evaluated."""
+    x, y, z, q = (_f64(v) for v in (x, y, z, q))
+    n = len(x)
+    if sample is None:
+        ns, sp, nout = -1, None, n
+    else:
+        sample = np.ascontiguousarray(sample, dtype=np.int64)
+        ns, sp, nout = len(sample), sample.ctypes.data_as(_i64p), len(sample)
+    pot, ax, ay, az = (np.zeros(nout) for _ in range(4))
+    st = np.zeros(5, dtype=np.int64)
+    rc = lib().orc_fmm_adaptive(n, _d(x), _d(y), _d(z), _d(q), max_leaf, float(theta), p, basis, ns, sp,
+                                _d(pot), _d(ax), _d(ay), _d(az), st.ctypes.data_as(_i64p))
+    if rc != 0:
+        raise ValueError("orc_fmm_adaptive rejected its arguments")
+    keys = ("nodes", "m2l_pairs", "p2p_pairs", "leaves", "covered_pairs")
+    return pot, np.stack([ax, ay, az]), dict(zip(keys, st.tolist()))

@@ -654,3 +654,284 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adaptive octree FMM (App. C with an octree): the bounding cube of the      */
+/* data (anchored at the coordinate minima, side = largest extent enlarged by */
+/* 1e-12 relative), Morton keys with 21 bits per axis, particles sorted by    */
+/* (key, index); a cell holding more than max_leaf particles is split into    */
+/* its non-empty octants (children kept in octant order), down to level 21.   */
+/* Expansion centres are geometric cell centres (App. C); the enclosing       */
+/* radius of a leaf is the largest particle distance from its centre, of an   */
+/* inner cell max over children of (|z_child - z| + r_child).                 */
+/* Interaction lists come from a directed dual-tree traversal (App. C, after  */
+/* Dehnen): start from (root, root); a self pair of an inner cell expands to  */
+/* all ordered pairs of its children; a pair (A target, B source) is accepted */
+/* for M2L when theta |z_A - z_B| > r_A + r_B (the MAC), goes to P2P when both */
+/* are leaves, and otherwise the larger cell (by radius; the target on ties)  */
+/* is opened, or the one that is not a leaf.  theta = 0 accepts nothing, so   */
+/* the method reduces to the direct sum.                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int level, ix, iy, iz;
+    int64_t b, e;          /* particle range in sorted order */
+    int64_t child0;        /* first child node, -1 for leaves */
+    int nchild;
+    int64_t parent;
+    double z[3], r;
+} anode_t;
+
+static uint64_t spread21(uint64_t v) {
+    uint64_t r = 0;
+    for (int j = 0; j < 21; ++j) r |= ((v >> j) & 1ull) << (3 * j);
+    return r;
+}
+
+typedef struct { uint64_t key; int64_t idx; } kv_t;
+static int kv_cmp(const void* a, const void* b) {
+    const kv_t* p = (const kv_t*)a;
+    const kv_t* q = (const kv_t*)b;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    return p->idx < q->idx ? -1 : (p->idx > q->idx);
+}
+
+typedef struct { int64_t a, b; } pair_t;
+typedef struct { pair_t* v; int64_t n, cap; } plist_t;
+static void pl_push(plist_t* l, int64_t a, int64_t b) {
+    if (l->n == l->cap) {
+        l->cap = l->cap ? 2 * l->cap : 1024;
+        l->v = (pair_t*)realloc(l->v, sizeof(pair_t) * l->cap);
+    }
+    l->v[l->n].a = a; l->v[l->n].b = b; l->n++;
+}
+
+static double dist3(const double* a, const double* b) {
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                     int max_leaf, double theta, int p, int basis, int64_t nsample, const int64_t* sample,
+                     double* pot, double* ax, double* ay, double* az, int64_t* stats /* [5] or NULL */) {
+    orc_init();
+    if (p < 0 || p > ORC_PMAX || max_leaf < 1 || theta < 0.0 || n < 0) return -1;
+    int64_t ntarg = nsample >= 0 ? nsample : n;
+    if (n == 0) return 0;
+    /* bounding cube */
+    double lo[3] = {x[0], y[0], z[0]}, hi[3] = {x[0], y[0], z[0]};
+    for (int64_t i = 0; i < n; ++i) {
+        const double v[3] = {x[i], y[i], z[i]};
+        for (int d = 0; d < 3; ++d) { if (v[d] < lo[d]) lo[d] = v[d]; if (v[d] > hi[d]) hi[d] = v[d]; }
+    }
+    double side = 0.0;
+    for (int d = 0; d < 3; ++d) if (hi[d] - lo[d] > side) side = hi[d] - lo[d];
+    if (side == 0.0) side = 1.0;
+    side = side * (1.0 + 1e-12);
+    const double scale = 2097152.0 / side; /* 2^21 */
+    kv_t* kv = (kv_t*)malloc(sizeof(kv_t) * n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double v[3] = {x[i], y[i], z[i]};
+        uint64_t key = 0;
+        for (int d = 0; d < 3; ++d) {
+            int64_t c = (int64_t)floor((v[d] - lo[d]) * scale);
+            if (c < 0) c = 0;
+            if (c > 2097151) c = 2097151;
+            key |= spread21((uint64_t)c) << d;
+        }
+        kv[i].key = key; kv[i].idx = i;
+    }
+    qsort(kv, n, sizeof(kv_t), kv_cmp);
+    /* tree, level by level */
+    int64_t cap = 1024, nn = 1;
+    anode_t* nd = (anode_t*)malloc(sizeof(anode_t) * cap);
+    nd[0].level = 0; nd[0].ix = nd[0].iy = nd[0].iz = 0; nd[0].b = 0; nd[0].e = n;
+    nd[0].child0 = -1; nd[0].nchild = 0; nd[0].parent = -1;
+    int64_t lvl_b = 0, lvl_e = 1;
+    while (lvl_b < lvl_e) {
+        for (int64_t c = lvl_b; c < lvl_e; ++c) {
+            if (nd[c].e - nd[c].b <= max_leaf || nd[c].level >= 21) continue;
+            const int L = nd[c].level;
+            const int shift = 3 * (20 - L);
+            nd[c].child0 = nn;
+            int64_t s = nd[c].b;
+            for (int oct = 0; oct < 8; ++oct) {
+                int64_t e = s;
+                while (e < nd[c].e && (int)((kv[e].key >> shift) & 7ull) == oct) ++e;
+                if (e > s) {
+                    if (nn == cap) { cap *= 2; nd = (anode_t*)realloc(nd, sizeof(anode_t) * cap); }
+                    anode_t* ch = &nd[nn++];
+                    ch->level = L + 1;
+                    ch->ix = 2 * nd[c].ix + (oct & 1);
+                    ch->iy = 2 * nd[c].iy + ((oct >> 1) & 1);
+                    ch->iz = 2 * nd[c].iz + ((oct >> 2) & 1);
+                    ch->b = s; ch->e = e; ch->child0 = -1; ch->nchild = 0; ch->parent = c;
+                    nd[c].nchild++;
+                }
+                s = e;
+            }
+        }
+        lvl_b = lvl_e;
+        lvl_e = nn;
+    }
+    /* geometry: centres, radii (children after parents in the array) */
+    for (int64_t c = 0; c < nn; ++c) {
+        const double h = side / (double)(1ull << nd[c].level);
+        nd[c].z[0] = lo[0] + (nd[c].ix + 0.5) * h;
+        nd[c].z[1] = lo[1] + (nd[c].iy + 0.5) * h;
+        nd[c].z[2] = lo[2] + (nd[c].iz + 0.5) * h;
+    }
+    for (int64_t c = nn - 1; c >= 0; --c) {
+        double r = 0.0;
+        if (nd[c].nchild == 0) {
+            for (int64_t a = nd[c].b; a < nd[c].e; ++a) {
+                const int64_t i = kv[a].idx;
+                const double v[3] = {x[i], y[i], z[i]};
+                const double d = dist3(v, nd[c].z);
+                if (d > r) r = d;
+            }
+        } else {
+            for (int k = 0; k < nd[c].nchild; ++k) {
+                const anode_t* ch = &nd[nd[c].child0 + k];
+                const double d = dist3(ch->z, nd[c].z) + ch->r;
+                if (d > r) r = d;
+            }
+        }
+        nd[c].r = r;
+    }
+    /* directed dual traversal */
+    plist_t qa = {0, 0, 0}, qb = {0, 0, 0}, m2l = {0, 0, 0}, p2p = {0, 0, 0};
+    pl_push(&qa, 0, 0);
+    while (qa.n) {
+        qb.n = 0;
+        for (int64_t k = 0; k < qa.n; ++k) {
+            const int64_t A = qa.v[k].a, B = qa.v[k].b;
+            const int la = nd[A].nchild == 0, lb = nd[B].nchild == 0;
+            if (A == B) {
+                if (la) pl_push(&p2p, A, A);
+                else
+                    for (int i = 0; i < nd[A].nchild; ++i)
+                        for (int j = 0; j < nd[A].nchild; ++j) pl_push(&qb, nd[A].child0 + i, nd[A].child0 + j);
+                continue;
+            }
+            if (theta * dist3(nd[A].z, nd[B].z) > nd[A].r + nd[B].r) { pl_push(&m2l, A, B); continue; }
+            if (la && lb) { pl_push(&p2p, A, B); continue; }
+            if (!la && (lb || nd[A].r >= nd[B].r)) {
+                for (int i = 0; i < nd[A].nchild; ++i) pl_push(&qb, nd[A].child0 + i, B);
+            } else {
+                for (int j = 0; j < nd[B].nchild; ++j) pl_push(&qb, A, nd[B].child0 + j);
+            }
+        }
+        plist_t t = qa; qa = qb; qb = t;
+    }
+    if (stats) {
+        /* stats: nodes, M2L pairs, P2P pairs, leaves, and the number of ordered
+           particle pairs the lists cover (n^2 when every pair is covered once) */
+        stats[0] = nn; stats[1] = m2l.n; stats[2] = p2p.n; stats[3] = 0; stats[4] = 0;
+        for (int64_t c = 0; c < nn; ++c) stats[3] += nd[c].nchild == 0;
+        for (int64_t k = 0; k < m2l.n; ++k)
+            stats[4] += (nd[m2l.v[k].a].e - nd[m2l.v[k].a].b) * (nd[m2l.v[k].b].e - nd[m2l.v[k].b].b);
+        for (int64_t k = 0; k < p2p.n; ++k)
+            stats[4] += (nd[p2p.v[k].a].e - nd[p2p.v[k].a].b) * (nd[p2p.v[k].b].e - nd[p2p.v[k].b].b);
+    }
+    /* which nodes feed sampled targets */
+    int64_t* pos_of = (int64_t*)malloc(sizeof(int64_t) * n);   /* sorted position of particle */
+    for (int64_t a = 0; a < n; ++a) pos_of[kv[a].idx] = a;
+    int64_t* leaf_of = (int64_t*)malloc(sizeof(int64_t) * n);   /* leaf of sorted position */
+    for (int64_t c = 0; c < nn; ++c)
+        if (nd[c].nchild == 0)
+            for (int64_t a = nd[c].b; a < nd[c].e; ++a) leaf_of[a] = c;
+    char* need = (char*)calloc(nn, 1);
+    for (int64_t t = 0; t < ntarg; ++t) {
+        int64_t c = leaf_of[pos_of[nsample >= 0 ? sample[t] : t]];
+        while (c >= 0 && !need[c]) { need[c] = 1; c = nd[c].parent; }
+    }
+    /* upward pass */
+    const int nc = orc_ncoef(p, basis);
+    double* M = (double*)calloc((size_t)nn * nc, sizeof(double));
+    double* L = (double*)calloc((size_t)nn * nc, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < nn; ++c) {
+        if (nd[c].nchild) continue;
+        const int64_t cnt = nd[c].e - nd[c].b;
+        double* buf = (double*)malloc(sizeof(double) * 4 * cnt);
+        for (int64_t a = 0; a < cnt; ++a) {
+            const int64_t i = kv[nd[c].b + a].idx;
+            buf[a] = x[i]; buf[cnt + a] = y[i]; buf[2 * cnt + a] = z[i]; buf[3 * cnt + a] = q[i];
+        }
+        orc_p2m(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, buf + 3 * cnt, nd[c].z, M + c * nc);
+        free(buf);
+    }
+    for (int64_t c = nn - 1; c >= 0; --c) {   /* children precede nothing: reverse order is bottom-up */
+        if (!nd[c].nchild) continue;
+        for (int k = 0; k < nd[c].nchild; ++k) {
+            const int64_t ch = nd[c].child0 + k;
+            double d[3] = {nd[ch].z[0] - nd[c].z[0], nd[ch].z[1] - nd[c].z[1], nd[ch].z[2] - nd[c].z[2]};
+            orc_m2m(p, basis, M + ch * nc, d, M + c * nc);
+        }
+    }
+    /* interaction phase, grouped by target for the parallel loop */
+    int64_t* cnt = (int64_t*)calloc(nn + 1, sizeof(int64_t));
+    for (int64_t k = 0; k < m2l.n; ++k) cnt[m2l.v[k].a + 1]++;
+    for (int64_t c = 0; c < nn; ++c) cnt[c + 1] += cnt[c];
+    int64_t* src = (int64_t*)malloc(sizeof(int64_t) * (m2l.n > 0 ? m2l.n : 1));
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nn + 1));
+        memcpy(fill, cnt, sizeof(int64_t) * (nn + 1));
+        for (int64_t k = 0; k < m2l.n; ++k) src[fill[m2l.v[k].a]++] = m2l.v[k].b;
+        free(fill);
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < nn; ++c) {
+        if (!need[c]) continue;
+        for (int64_t k = cnt[c]; k < cnt[c + 1]; ++k) {
+            const int64_t s = src[k];
+            double r[3] = {nd[c].z[0] - nd[s].z[0], nd[c].z[1] - nd[s].z[1], nd[c].z[2] - nd[s].z[2]};
+            orc_m2l(p, basis, M + s * nc, r, L + c * nc);
+        }
+    }
+    for (int64_t c = 0; c < nn; ++c) {   /* parents precede children: forward order is top-down */
+        if (!nd[c].nchild || !need[c]) continue;
+        for (int k = 0; k < nd[c].nchild; ++k) {
+            const int64_t ch = nd[c].child0 + k;
+            if (!need[ch]) continue;
+            double d[3] = {nd[ch].z[0] - nd[c].z[0], nd[ch].z[1] - nd[c].z[1], nd[ch].z[2] - nd[c].z[2]};
+            orc_l2l(p, basis, L + c * nc, d, L + ch * nc);
+        }
+    }
+    /* near-field lists by target leaf */
+    int64_t* pc = (int64_t*)calloc(nn + 1, sizeof(int64_t));
+    for (int64_t k = 0; k < p2p.n; ++k) pc[p2p.v[k].a + 1]++;
+    for (int64_t c = 0; c < nn; ++c) pc[c + 1] += pc[c];
+    int64_t* psrc = (int64_t*)malloc(sizeof(int64_t) * (p2p.n > 0 ? p2p.n : 1));
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nn + 1));
+        memcpy(fill, pc, sizeof(int64_t) * (nn + 1));
+        for (int64_t k = 0; k < p2p.n; ++k) psrc[fill[p2p.v[k].a]++] = p2p.v[k].b;
+        free(fill);
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < ntarg; ++t) {
+        const int64_t i = nsample >= 0 ? sample[t] : t;
+        const int64_t c = leaf_of[pos_of[i]];
+        double rb[3] = {x[i] - nd[c].z[0], y[i] - nd[c].z[1], z[i] - nd[c].z[2]}, o[4];
+        orc_l2p(p, basis, L + c * nc, rb, o);
+        double ph = o[0], gx = o[1], gy = o[2], gz = o[3];
+        for (int64_t k = pc[c]; k < pc[c + 1]; ++k) {
+            const int64_t s = psrc[k];
+            for (int64_t a = nd[s].b; a < nd[s].e; ++a) {
+                const int64_t j = kv[a].idx;
+                if (j == i) continue;
+                double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+                double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 == 0.0) continue;
+                double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
+                ph += q[j] * ir;
+                gx += q[j] * dx * ir3; gy += q[j] * dy * ir3; gz += q[j] * dz * ir3;
+            }
+        }
+        pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
+    }
+    free(kv); free(nd); free(qa.v); free(qb.v); free(m2l.v); free(p2p.v);
+    free(pos_of); free(leaf_of); free(need); free(M); free(L); free(cnt); free(src); free(pc); free(psrc);
+    return 0;
+}
