@@ -71,13 +71,19 @@ typedef struct {
     int p;                 /* expansion order, 0..10 (Eq. phi expansion, App. B)      */
     int basis;             /* fmm_basis                                                */
     int prec;              /* fmm_precision                                            */
-    int adaptive;          /* 0: uniform octree of depth `depth` over [0,1)^3          */
+    int adaptive;          /* 0: uniform octree of depth `depth` over [0,1)^3;
+                              1: adaptive octree over the bounding cube of the data,
+                              cells split while they hold more than max_leaf
+                              particles, lists from a dual-tree traversal (App. C) */
     int depth;             /* uniform octree depth (leaves = 8^depth), 0..10           */
     int max_leaf;          /* adaptive trees: maximum particles per leaf               */
     double theta;          /* adaptive trees: opening parameter of the MAC (App. C)    */
     int learned_p;         /* reserved: per-interaction order selection                */
     double target_rel_err; /* reserved: target relative force error                    */
-    int use_graph;         /* 1: replay fmm_evaluate from a captured CUDA graph        */
+    int use_graph;         /* 1 (adaptive trees, non-default stream): after the first
+                              evaluation, capture the operator sequence P2M..P2P into
+                              a CUDA graph and replay it while the tree keeps its
+                              sizes and buffers                                        */
 } fmm_config;
 
 typedef struct fmm_plan fmm_plan;
@@ -98,8 +104,10 @@ int fmm_ncoef(int p, int basis);
  * directly.
  * ------------------------------------------------------------------------- */
 
-/* Creates a plan.  Validates cfg (p in 0..10, basis, prec, depth in 0..10,
- * adaptive == 0) and returns FMM_ERR_ARG / FMM_ERR_UNSUPPORTED otherwise.
+/* Creates a plan.  Validates cfg (p in 0..10, basis, prec, depth in 0..9;
+ * adaptive plans: max_leaf >= 1, 0 <= theta <= 1, prec FMM_FP64 or
+ * FMM_FP32; the tensor-core form needs the traceless basis and p <= 8) and
+ * returns FMM_ERR_ARG / FMM_ERR_UNSUPPORTED otherwise.
  * *out receives the plan (NULL on failure).  Allocates no particle storage. */
 int fmm_create(const fmm_config* cfg, fmm_plan** out);
 
@@ -235,6 +243,13 @@ int fmm_direct(int64_t n, const double* x, const double* y, const double* z,
 int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, const double* x, const double* y,
                          const double* z, const double* q, double* pot, double* ax, double* ay,
                          double* az, void* stream);
+
+/* Sizes of the plan's tree and lists after fmm_build_tree, written to
+ * out[0..min(nout,8)): number of cells, leaves, M2L pairs, P2P (leaf) pairs,
+ * M2L target cells, autotuned M2L blocks per SM (0 before the first M2L),
+ * tree levels, and 1 when a captured operator graph is held.  For uniform
+ * trees the list entries are 0 (the lists are implicit). */
+int fmm_plan_stats(const fmm_plan* plan, int64_t* out, int nout);
 
 /* Number of kernels this library launched since it was loaded (all plans and
  * operator calls), counted on the host at each launch. */

@@ -1,0 +1,107 @@
+// Adaptive-octree plan state and launchers (fmm_adaptive*.cu).
+#pragma once
+#include <vector>
+
+#include "fmm_internal.h"
+
+namespace fmm {
+
+struct AdState {
+    int64_t n = 0;
+    int nc = 0;
+    int nn = 0, nleaf = 0, nm2l = 0, np2p = 0, ntarg = 0;
+    std::vector<int> lvl;   // level L: nodes [lvl[L], lvl[L+1])
+    // particles (sorted) and sort buffers
+    double *xs = nullptr, *ys = nullptr, *zs = nullptr, *qs = nullptr;
+    int* perm = nullptr;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    int *v0 = nullptr, *v1 = nullptr, *hist = nullptr, *hsum = nullptr, *scr = nullptr;
+    double *box = nullptr, *part = nullptr;
+    // nodes
+    int *lev = nullptr, *ix = nullptr, *iy = nullptr, *iz = nullptr, *nb = nullptr, *ne = nullptr;
+    int *child0 = nullptr, *nchild = nullptr, *parent = nullptr;
+    double *zc = nullptr, *rad = nullptr;
+    int *bounds = nullptr, *nch = nullptr, *choff = nullptr;
+    // traversal
+    int2 *q0 = nullptr, *q1 = nullptr;
+    int *cm = nullptr, *cp = nullptr, *cq = nullptr, *om = nullptr, *op = nullptr, *oq = nullptr;
+    int2 *m2l = nullptr, *p2p = nullptr;
+    int *moff = nullptr, *msrc = nullptr, *poff = nullptr, *psrc = nullptr, *order = nullptr, *leaf = nullptr;
+    int64_t* lstart = nullptr;
+    double* lcen = nullptr;
+    // expansions (node-major)
+    double *Mleaf = nullptr, *M = nullptr, *L = nullptr;
+    float* M32 = nullptr;
+    int* counter = nullptr;
+    // capacities (bytes)
+    size_t cap_xs = 0, cap_ys = 0, cap_zs = 0, cap_qs = 0, cap_perm = 0, cap_k0 = 0, cap_k1 = 0, cap_v0 = 0,
+           cap_v1 = 0, cap_hist = 0, cap_hsum = 0, cap_scr = 0, cap_box = 0, cap_part = 0, cap_lev = 0, cap_ix = 0,
+           cap_iy = 0, cap_iz = 0, cap_nb = 0, cap_ne = 0, cap_child0 = 0, cap_nchild = 0, cap_parent = 0,
+           cap_zc = 0, cap_rad = 0, cap_bounds = 0, cap_nch = 0, cap_choff = 0, cap_q0 = 0, cap_q1 = 0, cap_cm = 0,
+           cap_cp = 0, cap_cq = 0, cap_om = 0, cap_op = 0, cap_oq = 0, cap_m2l = 0, cap_p2p = 0, cap_moff = 0,
+           cap_msrc = 0, cap_poff = 0, cap_psrc = 0, cap_order = 0, cap_leaf = 0, cap_lstart = 0, cap_lcen = 0,
+           cap_Mleaf = 0, cap_M = 0, cap_L = 0, cap_M32 = 0, cap_counter = 0;
+    // autotuned persistent grid of the M2L kernel
+    int m2l_blocks = 0, m2l_blocks_per_sm = 0;
+    float m2l_tuned_ms = 0.f;
+    // captured operator sequence
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ok = false;
+    const void* graph_key[8] = {nullptr};
+};
+
+void ad_free(AdState* a);
+int ad_build(AdState* a, int64_t n, const double* x, const double* y, const double* z, const double* q,
+             int max_leaf, double theta, int nc, int prec, cudaStream_t s);
+int ad_run_p2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s);
+int ad_run_m2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s);
+int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s);
+int ad_run_l2l(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s);
+int ad_run_l2p(AdState* a, int p, int basis, const DevTables& T, double* pot, double* ax, double* ay, double* az,
+               cudaStream_t s);
+int ad_run_p2p(AdState* a, int prec, int sms, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+
+// fmm_adaptive.cu
+void radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,
+                int* scratch, cudaStream_t s);
+int ad_bbox(int64_t n, const double* x, const double* y, const double* z, double* part, double* box, cudaStream_t s);
+int ad_morton(int64_t n, const double* x, const double* y, const double* z, const double* box, uint64_t* key,
+              int* val, cudaStream_t s);
+int ad_gather(int64_t n, const int* perm, const double* x, const double* y, const double* z, const double* q,
+              double* xs, double* ys, double* zs, double* qs, cudaStream_t s);
+int ad_split_count(int lb, int le, int max_leaf, const int* lev, const int* nb, const int* ne, const uint64_t* key,
+                   int* bounds, int* nch, cudaStream_t s);
+int ad_split_write(int lb, int le, const int* bounds, const int* nch, const int* choff, int* lev, int* ix, int* iy,
+                   int* iz, int* nb, int* ne, int* child0, int* nchild, int* parent, cudaStream_t s);
+int ad_centres(int nn, const int* lev, const int* ix, const int* iy, const int* iz, const double* box, double* zc,
+               cudaStream_t s);
+int ad_radii(int lb, int le, const int* nb, const int* ne, const int* child0, const int* nchild, const double* zc,
+             const double* xs, const double* ys, const double* zs, double* rad, cudaStream_t s);
+int ad_trav_count(int nq, const int2* q, double theta, const int* nchild, const double* zc, const double* rad,
+                  int* cm, int* cp, int* cq, cudaStream_t s);
+int ad_trav_write(int nq, const int2* q, double theta, const int* nchild, const int* child0, const double* zc,
+                  const double* rad, const int* om, const int* op, const int* oq, int mbase, int pbase, int2* m2l,
+                  int2* p2p, int2* qn, cudaStream_t s);
+int ad_pair_keys(int n, const int2* pr, uint64_t* key, int* val, cudaStream_t s);
+int ad_pair_csr(int n, const uint64_t* key, const int* val, const int2* pr, int* src, int* cnt, cudaStream_t s);
+int ad_len_keys(int nn, const int* off, uint64_t* key, int* val, cudaStream_t s);
+int ad_leaf_keys(int nn, const int* nchild, const int* nb, uint64_t* key, int* val, cudaStream_t s);
+int ad_leaf_arrays(int nleaf, int64_t n, const int* leaf, const int* nb, const double* zc, int64_t* lstart,
+                   double* lcen, cudaStream_t s);
+int ad_leafM_to_nodes(int nleaf, int nc, const int* leaf, const double* Ml, double* Mn, cudaStream_t s);
+int ad_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
+int ad_m2m(int p, int basis, int lb, int le, const int* child0, const int* nchild, const double* zc, double* Mn,
+           const DevTables& T, cudaStream_t s);
+int ad_l2l(int p, int basis, int lb, int le, const int* parent, const double* zc, double* Ln, const DevTables& T,
+           cudaStream_t s);
+int ad_l2p(int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne, const double* zc,
+           const double* xs, const double* ys, const double* zs, const int* perm, const double* Ln,
+           const DevTables& T, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+int ad_p2p(int prec, int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne,
+           const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
+           const int* perm, double* pot, double* ax, double* ay, double* az, int* counter, int blocks,
+           cudaStream_t s);
+int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off, const int* src,
+                    const double* zc, const void* M, double* Ln, int* counter, int blocks, cudaStream_t s);
+
+}  // namespace fmm

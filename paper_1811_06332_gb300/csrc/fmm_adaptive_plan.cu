@@ -1,0 +1,310 @@
+// Adaptive-octree plan state: builds the tree and the interaction lists on
+// the device (host loop over levels and traversal steps, sizes read back),
+// and runs the operator sequence P2M, M2M, M2L, L2L, L2P, P2P over it.
+//
+// Batching: M2L and P2P run as persistent kernels that take work from an
+// atomic counter (M2L targets ordered by list length, longest first); the
+// persistent grid size of M2L is picked by timing candidates on the first
+// evaluation of a plan (autotuner); the operator sequence can be captured
+// into a CUDA graph and replayed while the tree and lists keep their sizes.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fmm_adaptive.h"
+
+namespace fmm {
+
+static int grow_bytes(void** p, size_t* cap, size_t need) {
+    if (need <= *cap) return 0;
+    size_t nc = need + need / 2 + 4096;
+    void* q = nullptr;
+    if (cudaMalloc(&q, nc) != cudaSuccess) return -3;
+    if (*p) {
+        if (cudaMemcpy(q, *p, *cap, cudaMemcpyDeviceToDevice) != cudaSuccess) { cudaFree(q); return -2; }
+        cudaFree(*p);
+    }
+    *p = q;
+    *cap = nc;
+    return 0;
+}
+#define GROW(ptr, capname, bytes)                                                            \
+    do {                                                                                     \
+        int r_ = grow_bytes((void**)&(ptr), &(capname), (size_t)(bytes));                  \
+        if (r_) return r_;                                                                   \
+    } while (0)
+
+void ad_free(AdState* a) {
+    if (!a) return;
+    void* ptrs[] = {a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
+                    a->box, a->part, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0, a->nchild, a->parent,
+                    a->zc, a->rad, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
+                    a->oq, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->lstart,
+                    a->lcen, a->Mleaf, a->M, a->L, a->M32, a->counter};
+    for (void* p : ptrs) cudaFree(p);
+    if (a->gexec) cudaGraphExecDestroy(a->gexec);
+    delete a;
+}
+
+static int d2h_int(const int* d, int* h, cudaStream_t s) {
+    if (cudaMemcpyAsync(h, d, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -2;
+    return cudaStreamSynchronize(s) == cudaSuccess ? 0 : -2;
+}
+
+// exclusive scan of n ints into out[0..n]; returns the total in *tot
+static int scan_total(const int* in, int* out, int n, int* scr, int* tot, cudaStream_t s) {
+    scan_excl_int(in, out, n, scr, s);
+    return d2h_int(out + n, tot, s);
+}
+
+// sort (key, val) pairs by the low `bits` of key
+static int sort_pairs(AdState* a, int64_t n, int bits, cudaStream_t s) {
+    const int64_t nblk = (n + 2047) / 2048;
+    GROW(a->hist, a->cap_hist, (256 * nblk + 1) * 4);
+    GROW(a->hsum, a->cap_hsum, (256 * nblk + 1) * 4);
+    radix_sort(n, a->k0, a->v0, a->k1, a->v1, bits, a->hist, a->hsum, a->scr, s);
+    return 0;
+}
+
+int ad_build(AdState* a, int64_t n, const double* x, const double* y, const double* z, const double* q,
+             int max_leaf, double theta, int nc, int prec, cudaStream_t s) {
+    a->n = n;
+    a->nc = nc;
+    a->graph_ok = false;
+    // per-particle storage
+    GROW(a->xs, a->cap_xs, n * 8); GROW(a->ys, a->cap_ys, n * 8); GROW(a->zs, a->cap_zs, n * 8);
+    GROW(a->qs, a->cap_qs, n * 8);
+    const int64_t nk = n > 1 ? n : 2;
+    GROW(a->k0, a->cap_k0, nk * 8); GROW(a->k1, a->cap_k1, nk * 8);
+    GROW(a->v0, a->cap_v0, nk * 4); GROW(a->v1, a->cap_v1, nk * 4);
+    GROW(a->scr, a->cap_scr, (size_t)1 << 22);
+    GROW(a->box, a->cap_box, 64);
+    GROW(a->part, a->cap_part, 256 * 6 * 8);
+    GROW(a->counter, a->cap_counter, 64);
+    if (n == 0) { a->nn = 0; a->nleaf = 0; a->nm2l = 0; a->np2p = 0; a->ntarg = 0; return 0; }
+    ad_bbox(n, x, y, z, a->part, a->box, s);
+    ad_morton(n, x, y, z, a->box, a->k0, a->v0, s);
+    if (int r = sort_pairs(a, n, 63, s)) return r;
+    GROW(a->perm, a->cap_perm, n * 4);
+    cudaMemcpyAsync(a->perm, a->v0, n * 4, cudaMemcpyDeviceToDevice, s);
+    ad_gather(n, a->perm, x, y, z, q, a->xs, a->ys, a->zs, a->qs, s);
+    // sorted keys stay in k0; keep a copy (k0/k1 are reused by later sorts)
+    uint64_t* keys = a->k1;
+    cudaMemcpyAsync(keys, a->k0, n * 8, cudaMemcpyDeviceToDevice, s);
+    // ---------------- tree, level by level ----------------
+    int cap = 1024;
+    auto node_cap = [&](int need) -> int {
+        const size_t nd = (size_t)need;
+        GROW(a->lev, a->cap_lev, nd * 4); GROW(a->ix, a->cap_ix, nd * 4); GROW(a->iy, a->cap_iy, nd * 4);
+        GROW(a->iz, a->cap_iz, nd * 4); GROW(a->nb, a->cap_nb, nd * 4); GROW(a->ne, a->cap_ne, nd * 4);
+        GROW(a->child0, a->cap_child0, nd * 4); GROW(a->nchild, a->cap_nchild, nd * 4);
+        GROW(a->parent, a->cap_parent, nd * 4);
+        return 0;
+    };
+    if (int r = node_cap(cap)) return r;
+    {
+        const int zero = 0, nn1 = (int)n, m1 = -1;
+        cudaMemcpyAsync(a->lev, &zero, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->ix, &zero, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->iy, &zero, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->iz, &zero, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->nb, &zero, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->ne, &nn1, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->parent, &m1, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->child0, &m1, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->nchild, &zero, 4, cudaMemcpyHostToDevice, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;   // host values must land first
+    }
+    a->lvl.assign(1, 0);
+    int lb = 0, le = 1;
+    while (le > lb) {
+        a->lvl.push_back(le);
+        const int m = le - lb;
+        GROW(a->bounds, a->cap_bounds, (size_t)m * 9 * 4);
+        GROW(a->nch, a->cap_nch, (size_t)(m + 1) * 4);
+        GROW(a->choff, a->cap_choff, (size_t)(m + 1) * 4);
+        ad_split_count(lb, le, max_leaf, a->lev, a->nb, a->ne, keys, a->bounds, a->nch, s);
+        int tot = 0;
+        if (scan_total(a->nch, a->choff, m, a->scr, &tot, s)) return -2;
+        if (le + tot > cap) {
+            cap = 2 * (le + tot);
+            if (int r = node_cap(cap)) return r;
+        }
+        ad_split_write(lb, le, a->bounds, a->nch, a->choff, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0,
+                       a->nchild, a->parent, s);
+        lb = le;
+        le = le + tot;
+    }
+    a->nn = le;
+    // lvl: level L holds nodes [lvl[L], lvl[L+1]); the last entry is nn
+    GROW(a->zc, a->cap_zc, (size_t)a->nn * 24);
+    GROW(a->rad, a->cap_rad, (size_t)a->nn * 8);
+    ad_centres(a->nn, a->lev, a->ix, a->iy, a->iz, a->box, a->zc, s);
+    for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
+        ad_radii(a->lvl[L], a->lvl[L + 1], a->nb, a->ne, a->child0, a->nchild, a->zc, a->xs, a->ys, a->zs, a->rad, s);
+    // ---------------- directed dual traversal ----------------
+    int nq = 1, nm = 0, np = 0;
+    GROW(a->q0, a->cap_q0, 64);
+    {
+        const int2 root = make_int2(0, 0);
+        cudaMemcpyAsync(a->q0, &root, 8, cudaMemcpyHostToDevice, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
+    }
+    while (nq > 0) {
+        GROW(a->cm, a->cap_cm, (size_t)(nq + 1) * 4); GROW(a->cp, a->cap_cp, (size_t)(nq + 1) * 4);
+        GROW(a->cq, a->cap_cq, (size_t)(nq + 1) * 4); GROW(a->om, a->cap_om, (size_t)(nq + 1) * 4);
+        GROW(a->op, a->cap_op, (size_t)(nq + 1) * 4); GROW(a->oq, a->cap_oq, (size_t)(nq + 1) * 4);
+        ad_trav_count(nq, (const int2*)a->q0, theta, a->nchild, a->zc, a->rad, a->cm, a->cp, a->cq, s);
+        int tm = 0, tp = 0, tq = 0;
+        if (scan_total(a->cm, a->om, nq, a->scr, &tm, s) || scan_total(a->cp, a->op, nq, a->scr, &tp, s) ||
+            scan_total(a->cq, a->oq, nq, a->scr, &tq, s))
+            return -2;
+        GROW(a->m2l, a->cap_m2l, (size_t)(nm + tm + 1) * 8);
+        GROW(a->p2p, a->cap_p2p, (size_t)(np + tp + 1) * 8);
+        GROW(a->q1, a->cap_q1, (size_t)(tq + 1) * 8);
+        ad_trav_write(nq, (const int2*)a->q0, theta, a->nchild, a->child0, a->zc, a->rad, a->om, a->op, a->oq, nm,
+                      np, (int2*)a->m2l, (int2*)a->p2p, (int2*)a->q1, s);
+        nm += tm;
+        np += tp;
+        std::swap(a->q0, a->q1);
+        std::swap(a->cap_q0, a->cap_q1);
+        nq = tq;
+    }
+    a->nm2l = nm;
+    a->np2p = np;
+    // ---------------- lists by target (stable) ----------------
+    auto csr = [&](void* pairs, int npair, int** off, size_t* cap_off, int** srcp, size_t* cap_src) -> int {
+        GROW(*off, *cap_off, (size_t)(a->nn + 1) * 4);
+        GROW(*srcp, *cap_src, (size_t)(npair + 1) * 4);
+        GROW(a->cm, a->cap_cm, (size_t)(a->nn + 1) * 4);
+        cudaMemsetAsync(a->cm, 0, (size_t)(a->nn + 1) * 4, s);
+        if (npair > 0) {
+            GROW(a->k0, a->cap_k0, (size_t)npair * 8); GROW(a->k1, a->cap_k1, (size_t)npair * 8);
+            GROW(a->v0, a->cap_v0, (size_t)npair * 4); GROW(a->v1, a->cap_v1, (size_t)npair * 4);
+            ad_pair_keys(npair, (const int2*)pairs, a->k0, a->v0, s);
+            int bits = 1;
+            while ((1ll << bits) < a->nn) ++bits;
+            if (int r = sort_pairs(a, npair, bits, s)) return r;
+            ad_pair_csr(npair, a->k0, a->v0, (const int2*)pairs, *srcp, a->cm, s);
+        }
+        int tot = 0;
+        return scan_total(a->cm, *off, a->nn, a->scr, &tot, s);
+    };
+    if (int r = csr(a->m2l, nm, &a->moff, &a->cap_moff, &a->msrc, &a->cap_msrc)) return r;
+    if (int r = csr(a->p2p, np, &a->poff, &a->cap_poff, &a->psrc, &a->cap_psrc)) return r;
+    // M2L work order (longest list first) and the number of targets with a list
+    GROW(a->k0, a->cap_k0, (size_t)a->nn * 8); GROW(a->k1, a->cap_k1, (size_t)a->nn * 8);
+    GROW(a->v0, a->cap_v0, (size_t)a->nn * 4); GROW(a->v1, a->cap_v1, (size_t)a->nn * 4);
+    ad_len_keys(a->nn, a->moff, a->k0, a->v0, s);
+    if (int r = sort_pairs(a, a->nn, 31, s)) return r;
+    GROW(a->order, a->cap_order, (size_t)a->nn * 4);
+    cudaMemcpyAsync(a->order, a->v0, (size_t)a->nn * 4, cudaMemcpyDeviceToDevice, s);
+    // leaves in particle order
+    ad_leaf_keys(a->nn, a->nchild, a->nb, a->k0, a->v0, s);
+    if (int r = sort_pairs(a, a->nn, 33, s)) return r;
+    GROW(a->leaf, a->cap_leaf, (size_t)a->nn * 4);
+    cudaMemcpyAsync(a->leaf, a->v0, (size_t)a->nn * 4, cudaMemcpyDeviceToDevice, s);
+    // counts back on the host: leaves, targets with M2L work
+    {
+        std::vector<int> nch(a->nn), off(a->nn + 1);
+        cudaMemcpyAsync(nch.data(), a->nchild, (size_t)a->nn * 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(off.data(), a->moff, (size_t)(a->nn + 1) * 4, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
+        int nl = 0, nt = 0;
+        for (int c = 0; c < a->nn; ++c) { nl += nch[c] == 0; nt += off[c + 1] > off[c]; }
+        a->nleaf = nl;
+        a->ntarg = nt;
+    }
+    GROW(a->lstart, a->cap_lstart, (size_t)(a->nleaf + 1) * 8);
+    GROW(a->lcen, a->cap_lcen, (size_t)a->nleaf * 24);
+    ad_leaf_arrays(a->nleaf, n, a->leaf, a->nb, a->zc, a->lstart, a->lcen, s);
+    GROW(a->Mleaf, a->cap_Mleaf, (size_t)a->nleaf * nc * 8);
+    GROW(a->M, a->cap_M, (size_t)a->nn * nc * 8);
+    GROW(a->L, a->cap_L, (size_t)a->nn * nc * 8);
+    if (prec != 0) GROW(a->M32, a->cap_M32, (size_t)a->nn * nc * 4);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+int ad_run_p2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s) {
+    if (a->n == 0) return 0;
+    launch_p2m(p, basis, 0, a->nleaf, a->lstart, nullptr, a->xs, a->ys, a->zs, a->qs, a->lcen, 0, 1.0, a->Mleaf,
+               a->nleaf, T, s);
+    ad_leafM_to_nodes(a->nleaf, a->nc, a->leaf, a->Mleaf, a->M, s);
+    return 0;
+}
+
+int ad_run_m2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s) {
+    if (a->n == 0) return 0;
+    for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
+        ad_m2m(p, basis, a->lvl[L], a->lvl[L + 1], a->child0, a->nchild, a->zc, a->M, T, s);
+    return 0;
+}
+
+static int m2l_launch(AdState* a, int p, int basis, int prec, int blocks, cudaStream_t s) {
+    cudaMemsetAsync(a->counter, 0, 4, s);
+    const void* M = prec ? (const void*)a->M32 : (const void*)a->M;
+    return launch_m2l_list(p, basis, prec ? 1 : 0, a->ntarg, a->order, a->moff, a->msrc, a->zc, M, a->L, a->counter,
+                           blocks, s);
+}
+
+int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s) {
+    if (a->n == 0) return 0;
+    cudaMemsetAsync(a->L, 0, (size_t)a->nn * a->nc * 8, s);
+    if (prec) ad_to_f32((int64_t)a->nn * a->nc, a->M, a->M32, s);
+    if (a->ntarg == 0) return 0;
+    if (a->m2l_blocks == 0) {
+        // autotune the persistent grid on the first evaluation: candidates of
+        // 1..4 blocks of 128 threads per SM, each timed once after a warm-up
+        // (the kernel overwrites its targets, so repeating it is harmless)
+        int best = sms, bestb = 0;
+        float bt = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int k = 1; k <= 4; ++k) {
+            const int blocks = k * sms;
+            m2l_launch(a, p, basis, prec, blocks, s);
+            cudaEventRecord(e0, s);
+            m2l_launch(a, p, basis, prec, blocks, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < bt) { bt = ms; best = blocks; bestb = k; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        a->m2l_blocks = best;
+        a->m2l_blocks_per_sm = bestb;
+        a->m2l_tuned_ms = bt;
+    }
+    if (m2l_launch(a, p, basis, prec, a->m2l_blocks, s) != 0) return -1;
+    count_launch();
+    return 0;
+}
+
+int ad_run_l2l(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s) {
+    if (a->n == 0) return 0;
+    for (int L = 1; L + 1 < (int)a->lvl.size(); ++L)
+        ad_l2l(p, basis, a->lvl[L], a->lvl[L + 1], a->parent, a->zc, a->L, T, s);
+    return 0;
+}
+
+int ad_run_l2p(AdState* a, int p, int basis, const DevTables& T, double* pot, double* ax, double* ay, double* az,
+               cudaStream_t s) {
+    if (a->n == 0) return 0;
+    ad_l2p(p, basis, a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->perm, a->L, T, pot, ax, ay, az,
+           s);
+    return 0;
+}
+
+int ad_run_p2p(AdState* a, int prec, int sms, double* pot, double* ax, double* ay, double* az, cudaStream_t s) {
+    if (a->n == 0) return 0;
+    cudaMemsetAsync(a->counter + 1, 0, 4, s);
+    ad_p2p(prec ? 1 : 0, a->nleaf, a->leaf, a->poff, a->psrc, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs,
+           a->perm, pot, ax, ay, az, a->counter + 1, 4 * sms, s);
+    return 0;
+}
+
+}  // namespace fmm

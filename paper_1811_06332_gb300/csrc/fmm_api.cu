@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "fmm_gb300.h"
+#include "fmm_adaptive.h"
 #include "fmm_internal.h"
 
 namespace fmm {
@@ -60,6 +61,9 @@ struct fmm_plan {
     // host-call staging
     double* stage = nullptr;
     int64_t stage_n = 0;
+    // adaptive octree state (cfg.adaptive)
+    AdState* ad = nullptr;
+    int sms = 152;
 };
 
 static void* tc_maps_at(fmm_plan* pl, int l) {
@@ -131,6 +135,23 @@ int fmm_ncoef(int p, int basis) {
 const char* fmm_last_error(const fmm_plan* plan) { return plan ? plan->err.c_str() : t_err.c_str(); }
 
 int64_t fmm_kernel_launches(void) { return g_launches.load(); }
+
+int fmm_plan_stats(const fmm_plan* pl, int64_t* out, int nout) {
+    if (!pl || !out || nout < 0) return fail_plan(nullptr, FMM_ERR_ARG, "null plan or output");
+    int64_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (pl->ad) {
+        const AdState* A = pl->ad;
+        v[0] = A->nn; v[1] = A->nleaf; v[2] = A->nm2l; v[3] = A->np2p; v[4] = A->ntarg;
+        v[5] = A->m2l_blocks_per_sm; v[6] = A->lvl.empty() ? 0 : (int64_t)A->lvl.size() - 1;
+        v[7] = A->gexec ? 1 : 0;
+    } else {
+        int64_t cells = 0;
+        for (int l = 0; l <= pl->depth; ++l) cells += (int64_t)1 << (3 * l);
+        v[0] = cells; v[1] = pl->nleaf; v[6] = pl->depth + 1;
+    }
+    for (int k = 0; k < nout && k < 8; ++k) out[k] = v[k];
+    return FMM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // operator-level entry points
@@ -325,13 +346,22 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     if (cfg->p < 0 || cfg->p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", cfg->p, FMM_PMAX);
     if (cfg->basis != 0 && cfg->basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", cfg->basis);
     if (cfg->prec < FMM_FP64 || cfg->prec > FMM_GEMM_BF16X3) FAIL(FMM_ERR_ARG, "unknown precision %d", cfg->prec);
-    if (cfg->adaptive) FAIL(FMM_ERR_UNSUPPORTED, "adaptive trees are not available in this build");
+    if (cfg->adaptive) {
+        if (cfg->max_leaf < 1) FAIL(FMM_ERR_ARG, "max_leaf=%d must be >= 1", cfg->max_leaf);
+        if (!(cfg->theta >= 0.0 && cfg->theta <= 1.0)) FAIL(FMM_ERR_ARG, "theta outside [0, 1]");
+        if (cfg->prec != FMM_FP64 && cfg->prec != FMM_FP32)
+            FAIL(FMM_ERR_UNSUPPORTED, "adaptive trees support FMM_FP64 and FMM_FP32");
+    }
     if (cfg->depth < 0 || cfg->depth > 9) FAIL(FMM_ERR_ARG, "depth=%d outside 0..9", cfg->depth);
     if (cfg->prec == FMM_GEMM_TF32X3) FAIL(FMM_ERR_UNSUPPORTED, "the TF32x3 tensor-core form is not available yet");
     if (cfg->prec == FMM_GEMM_BF16X3 && !tc_supported(cfg->p, cfg->basis))
         FAIL(FMM_ERR_UNSUPPORTED, "the tensor-core form needs the traceless basis and 1 <= p <= 8");
     pl = new fmm_plan();
     pl->cfg = *cfg;
+    if (cfg->adaptive) {
+        pl->ad = new AdState();
+        pl->depth = 0;
+    }
     pl->depth = cfg->depth;
     pl->nleaf = (int64_t)1 << (3 * cfg->depth);
     pl->nc = ncoef_of(cfg->p, cfg->basis);
@@ -339,6 +369,11 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     int dev;
     if (int rc = tables_for_current(pl, &dev)) { fmm_destroy(pl); return rc; }
     pl->dev = dev;
+    cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cfg->adaptive) {
+        *out = pl;
+        return FMM_OK;
+    }
     std::vector<double> W, V;
     build_translation(cfg->p, cfg->basis, W, V);
     const size_t mb = W.size() * sizeof(double);
@@ -418,6 +453,7 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
 
 void fmm_destroy(fmm_plan* pl) {
     if (!pl) return;
+    ad_free(pl->ad);
     free_tree(pl);
     cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32);
     cudaFree(pl->Kbf); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32);
@@ -429,6 +465,15 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
     if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
     if (n < 0 || n > (int64_t)0x7fffffff) FAIL(FMM_ERR_ARG, "n=%lld outside 0..2^31-1", (long long)n);
     if (n > 0 && (!x || !y || !z || !q)) FAIL(FMM_ERR_ARG, "null particle array");
+    if (pl->ad) {
+        const int rc = ad_build(pl->ad, n, x, y, z, q, pl->cfg.max_leaf, pl->cfg.theta, pl->nc,
+                                pl->cfg.prec == FMM_FP64 ? 0 : 1, S(stream));
+        if (rc == -3) FAIL(FMM_ERR_OOM, "allocating adaptive tree storage failed");
+        if (rc) FAIL(FMM_ERR_CUDA, "adaptive tree build failed: %s", cudaGetErrorString(cudaGetLastError()));
+        pl->n = n;
+        pl->built = true;
+        return FMM_OK;
+    }
     if (n != pl->n) {
         free_tree(pl);
         const int64_t nn = n > 0 ? n : 1;
@@ -488,6 +533,7 @@ static double* Llev(fmm_plan* pl, int l) { return pl->Lbuf + pl->lvl_off[l]; }
 
 int fmm_p2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
+    if (pl->ad) { ad_run_p2m(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     const int d = pl->depth;
     launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, d, pl->nleaf, pl->start, pl->xs,
                     pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32);
@@ -497,6 +543,7 @@ int fmm_p2m(fmm_plan* pl, void* stream) {
 
 int fmm_m2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
+    if (pl->ad) { ad_run_m2m(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     if (pl->W32) {
         for (int l = pl->depth - 1; l >= 2; --l) {
             launch_shift32(pl->cfg.p, pl->cfg.basis, 1, l, pl->W32, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
@@ -515,6 +562,12 @@ int fmm_m2m(fmm_plan* pl, void* stream) {
 
 int fmm_m2l(fmm_plan* pl, void* stream) {
     NEED_TREE();
+    if (pl->ad) {
+        if (ad_run_m2l(pl->ad, pl->cfg.p, pl->cfg.basis, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->sms, S(stream)))
+            FAIL(FMM_ERR_UNSUPPORTED, "no list M2L kernel for this order and basis");
+        CKLAUNCH();
+        return FMM_OK;
+    }
     if (pl->cfg.prec == FMM_GEMM_BF16X3 && pl->depth >= 2) {
         // levels 2..3 (grids smaller than one 8x4x4 tile) on the FP32 grouped kernel
         const int lt = pl->depth < 3 ? pl->depth : 3;
@@ -555,6 +608,7 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
 
 int fmm_l2l(fmm_plan* pl, void* stream) {
     NEED_TREE();
+    if (pl->ad) { ad_run_l2l(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     if (pl->V32) {
         for (int l = 2; l < pl->depth; ++l) {
             launch_shift32(pl->cfg.p, pl->cfg.basis, 0, l, pl->V32, Llev(pl, l), (int64_t)1 << (3 * l),
@@ -574,6 +628,11 @@ int fmm_l2l(fmm_plan* pl, void* stream) {
 int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void* stream) {
     NEED_TREE();
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
+    if (pl->ad) {
+        ad_run_l2p(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], pot, ax, ay, az, S(stream));
+        CKLAUNCH();
+        return FMM_OK;
+    }
     if (pl->depth >= 2)
         launch_l2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, pl->depth, pl->nleaf,
                          pl->start, pl->xs, pl->ys, pl->zs, pl->perm, Llev(pl, pl->depth), g_tab[pl->dev], pot, ax,
@@ -587,6 +646,11 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
 int fmm_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void* stream) {
     NEED_TREE();
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
+    if (pl->ad) {
+        ad_run_p2p(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->sms, pot, ax, ay, az, S(stream));
+        CKLAUNCH();
+        return FMM_OK;
+    }
     if (pl->pos32)
         launch_p2p32(pl->depth, pl->nleaf, pl->start, pl->pos32, pl->perm, pot, ax, ay, az, S(stream));
     else
@@ -602,6 +666,31 @@ int fmm_evaluate(fmm_plan* pl, int64_t n, const double* x, const double* y, cons
     if (n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
     int rc;
     if ((rc = fmm_build_tree(pl, n, x, y, z, q, stream))) return rc;
+    if (pl->ad && pl->cfg.use_graph && stream && pl->ad->m2l_blocks > 0 && n > 0) {
+        // replay the captured operator sequence while the tree keeps its
+        // sizes and buffers; capture it again otherwise
+        AdState* A = pl->ad;
+        const void* key[8] = {A->M, A->L, A->msrc, A->psrc, pot, ax, (const void*)(intptr_t)A->nn,
+                              (const void*)(intptr_t)(((int64_t)A->ntarg << 32) ^ A->nleaf ^ (A->nm2l * 7919LL))};
+        if (!A->gexec || memcmp(key, A->graph_key, sizeof key) != 0) {
+            if (A->gexec) { cudaGraphExecDestroy(A->gexec); A->gexec = nullptr; }
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(S(stream), cudaStreamCaptureModeThreadLocal));
+            const int r1 = fmm_p2m(pl, stream) | fmm_m2m(pl, stream) | fmm_m2l(pl, stream) | fmm_l2l(pl, stream) |
+                           fmm_l2p(pl, pot, ax, ay, az, stream) | fmm_p2p(pl, pot, ax, ay, az, stream);
+            const cudaError_t ce = cudaStreamEndCapture(S(stream), &g);
+            if (r1 || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                FAIL(FMM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&A->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) FAIL(FMM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+            memcpy(A->graph_key, key, sizeof key);
+        }
+        CK(cudaGraphLaunch(A->gexec, S(stream)));
+        return FMM_OK;
+    }
     if ((rc = fmm_p2m(pl, stream))) return rc;
     if ((rc = fmm_m2m(pl, stream))) return rc;
     if ((rc = fmm_m2l(pl, stream))) return rc;

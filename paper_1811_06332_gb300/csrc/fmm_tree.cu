@@ -98,6 +98,10 @@ static void scan_excl(const int* in, int* out, int64_t m, int* scratch, cudaStre
     count_launch();
 }
 
+void scan_excl_int(const int* in, int* out, int64_t m, int* scratch, cudaStream_t s) {
+    scan_excl(in, out, m, scratch, s);
+}
+
 __global__ void k_scatter(int64_t n, const int* __restrict__ key, const int* __restrict__ start,
                           int* __restrict__ fill, int* __restrict__ order) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -595,6 +595,105 @@ def emit_shift_dispatch():
     return "\n".join(L) + "\n"
 
 
+def emit_list_file(p, basis, T):
+    """M2L over explicit interaction lists (adaptive trees): one thread per
+    target node of a work queue ordered by list length; the D-tensor of each
+    (target, source) pair is computed on the fly (physical units), every
+    output component accumulates in a register, and expansions are stored
+    node-major ([node][ncoef]) so each thread reads one contiguous block.
+    Work is handed out in warps of 32 targets from an atomic counter
+    (persistent grid)."""
+    syml = sym_list(p)
+    pos = {n: i for i, n in enumerate(syml)}
+    outs = syml if basis == 0 else tl_list(p)
+    tpos = {n: i for i, n in enumerate(tl_list(p))}
+    nc = len(outs)
+    L = ['// Generated by gen.py: list M2L (adaptive trees), p = %d, basis %d, %s.' % (p, basis, T),
+         '#include "../fmm_device.cuh"', "namespace fmm {",
+         "__global__ void __launch_bounds__(128)",
+         "m2l_list_p%d_b%d_%s(int ntarg, const int* __restrict__ order, const int* __restrict__ off,"
+         " const int* __restrict__ src, const double* __restrict__ zc, const %s* __restrict__ Mn,"
+         " double* __restrict__ Ln, int* __restrict__ counter) {" % (p, basis, T, T),
+         "  typedef %s T;" % T,
+         "  const int lane = threadIdx.x & 31;",
+         "  for (;;) {",
+         "    int base = 0;",
+         "    if (lane == 0) base = atomicAdd(counter, 32);",
+         "    base = __shfl_sync(0xffffffffu, base, 0);",
+         "    if (base >= ntarg) break;",
+         "    const int w = base + lane;",
+         "    if (w >= ntarg) continue;",
+         "    const int t = order[w];",
+         "    const double tx = zc[3 * t], ty = zc[3 * t + 1], tz = zc[3 * t + 2];"]
+    for a in range(nc):
+        L.append("    T a%d = T(0);" % a)
+    L.append("    for (int k = off[t]; k < off[t + 1]; ++k) {")
+    L.append("      const int s = src[k];")
+    L.append("      const T x = T(tx - zc[3 * s]), y = T(ty - zc[3 * s + 1]), z = T(tz - zc[3 * s + 2]);")
+    L.append("      const T* __restrict__ Ms = Mn + (int64_t)s * %d;" % nc)
+    L.append("      T d[%d];" % ns(p))
+    L.append("  " + gen_dtensor(p).replace("\n", "\n  "))
+    for b in range(p + 1):
+        blk = rank_sym(b)
+        L.append("      {")
+        for m in blk:
+            if basis == 0:
+                L.append("        const T m_%d_%d_%d = Ms[%d];" % (m + (pos[m],)))
+            elif m[2] <= 1:
+                L.append("        const T m_%d_%d_%d = Ms[%d];" % (m + (tpos[m],)))
+            else:
+                L.append("        const T m_%d_%d_%d = -m_%d_%d_%d - m_%d_%d_%d;" % (
+                    m + (m[0] + 2, m[1], m[2] - 2) + (m[0], m[1] + 2, m[2] - 2)))
+        for m in blk:
+            users = [(a, n) for a, n in enumerate(outs) if sum(n) + b <= p]
+            if not users:
+                continue
+            f = mfact(m)
+            mc = "m_%d_%d_%d" % m if f == 1 else "(m_%d_%d_%d * %s)" % (m + (lit(Fraction(1, f)),))
+            L.append("        { const T c = %s;" % mc)
+            for a, n in users:
+                L.append("          a%d = fma(c, d[%d], a%d);" % (a, pos[add(n, m)], a))
+            L.append("        }")
+        L.append("      }")
+    L.append("    }")
+    for a in range(nc):
+        L.append("    Ln[(int64_t)t * %d + %d] = (double)a%d;" % (nc, a, a))
+    L.append("  }")
+    L.append("}")
+    L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
+             " const double* zc, const void* M, double* Ln, int* counter, int blocks, cudaStream_t s) {"
+             % (p, basis, T))
+    L.append("  m2l_list_p%d_b%d_%s<<<blocks, 128, 0, s>>>(ntarg, order, off, src, zc, (const %s*)M, Ln,"
+             " counter);" % (p, basis, T, T))
+    L.append("  return 0;")
+    L.append("}")
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
+def emit_list_dispatch():
+    L = ['// Generated by gen.py: dispatch of the list M2L kernels.', '#include "../fmm_device.cuh"',
+         "namespace fmm {"]
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            for T in ("float", "double"):
+                L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
+                         " const double* zc, const void* M, double* Ln, int* counter, int blocks, cudaStream_t s);"
+                         % (p, b, T))
+    L.append("int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off,"
+             " const int* src, const double* zc, const void* M, double* Ln, int* counter, int blocks,"
+             " cudaStream_t s) {")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            for k, T in ((0, "double"), (1, "float")):
+                L.append("  if (p == %d && basis == %d && prec == %d) return launch_m2l_list_p%d_b%d_%s(ntarg, order,"
+                         " off, src, zc, M, Ln, counter, blocks, s);" % (p, b, k, p, b, T))
+    L.append("  return -1;")
+    L.append("}")
+    L.append("}  // namespace fmm")
+    return "\n".join(L) + "\n"
+
+
 def emit_grouped_dispatch():
     L = ['// Generated by gen.py: dispatch and layout of the FP32 offset-grouped M2L.',
          '#include "../fmm_device.cuh"', "namespace fmm {"]
@@ -678,6 +777,15 @@ def generate(out=OUT):
             fs = os.path.join(out, "shift_P%d_b%d.cu" % (p, basis))
             write_if_changed(fs, emit_shift_file(p, basis))
             files.append(fs)
+    for p in range(0, PMAX + 1):
+        for basis in (0, 1):
+            for T in ("float", "double"):
+                fl = os.path.join(out, "list_P%d_b%d_%s.cu" % (p, basis, T))
+                write_if_changed(fl, emit_list_file(p, basis, T))
+                files.append(fl)
+    fld = os.path.join(out, "list_dispatch.cu")
+    write_if_changed(fld, emit_list_dispatch())
+    files.append(fld)
     fsd = os.path.join(out, "shift_dispatch.cu")
     write_if_changed(fsd, emit_shift_dispatch())
     files.append(fsd)

@@ -23,7 +23,7 @@ EXPORTS = [
     "fmm_ncoef", "fmm_create", "fmm_destroy", "fmm_last_error", "fmm_build_tree", "fmm_p2m", "fmm_m2m",
     "fmm_m2l", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate", "fmm_evaluate_host", "fmm_op_dtensor",
     "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
-    "fmm_kernel_launches", "fmm_evaluate_noalloc",
+    "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_plan_stats",
 ]
 
 
@@ -72,6 +72,7 @@ def lib():
             "fmm_direct": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_kernel_launches": ([], _i64),
             "fmm_evaluate_noalloc": ([_int, _int, _int, _i64] + [_vp] * 9, _int),
+            "fmm_plan_stats": ([_vp, _vp, _int], _int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -216,6 +217,15 @@ class Plan:
             return a.data_ptr()
         self._c(lib().fmm_evaluate_host(self.h, len(x), hp(x), hp(y), hp(z), hp(q), hp(pot), hp(ax), hp(ay),
                                         hp(az), _stream(stream)))
+
+    def stats(self):
+        """Tree and list sizes (fmm_plan_stats)."""
+        import numpy as np
+        v = np.zeros(8, dtype=np.int64)
+        self._c(lib().fmm_plan_stats(self.h, v.ctypes.data, 8))
+        keys = ("cells", "leaves", "m2l_pairs", "p2p_pairs", "m2l_targets", "m2l_blocks_per_sm", "levels",
+                "graph")
+        return dict(zip(keys, v.tolist()))
 
     def evaluate(self, x, y, z, q, stream=None):
         """Convenience: allocates outputs, returns (pot, acc[3, n]) device tensors."""
