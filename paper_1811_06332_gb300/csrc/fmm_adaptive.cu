@@ -353,26 +353,6 @@ __global__ void k_leaf_keys(int nn, const int* __restrict__ nchild, const int* _
     key[c] = nchild[c] ? 0xffffffffull : (uint64_t)nb[c];
     val[c] = c;
 }
-__global__ void k_leaf_arrays(int nleaf, int64_t n, const int* __restrict__ leaf, const int* __restrict__ nb,
-                              const double* __restrict__ zc, int64_t* __restrict__ lstart,
-                              double* __restrict__ lcen) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > nleaf) return;
-    if (k == nleaf) { lstart[k] = n; return; }
-    const int c = leaf[k];
-    lstart[k] = nb[c];
-    lcen[k] = zc[3 * c];
-    lcen[nleaf + k] = zc[3 * c + 1];
-    lcen[2 * nleaf + k] = zc[3 * c + 2];
-}
-// leaf-major [ncoef][nleaf] -> node-major [node][ncoef]
-__global__ void k_leafM_to_nodes(int nleaf, int nc, const int* __restrict__ leaf, const double* __restrict__ Ml,
-                                 double* __restrict__ Mn) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)nleaf * nc) return;
-    const int k = (int)(t % nleaf), m = (int)(t / nleaf);
-    Mn[(int64_t)leaf[k] * nc + m] = Ml[t];
-}
 
 __global__ void k_gather_sorted(int64_t n, const int* __restrict__ perm, const double* __restrict__ x,
                                 const double* __restrict__ y, const double* __restrict__ z,
@@ -394,19 +374,34 @@ __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __r
 // ---------------------------------------------------------------------------
 // M2M (Eq. M2M / M2M part 2): parents [lb, le) of one level, one warp each;
 // the children's shifted full-symmetric sums accumulate in shared memory,
-// then (traceless) one detrace; the parent is overwritten.
-template <int WARPS>
+// then (traceless) one detrace; the parent is overwritten.  The binomial
+// weights are split into factorials,
+//   sum_k C(n,k) (-d)^(n-k) M_k = n! sum_k (M_k / k!) ((-d)^(n-k) / (n-k)!),
+// so the inner loop reads shared memory only (per-block tables of 1/k! and
+// n! per symmetric position).
+template <typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_m2m_tree(int p, int basis, int lb, int le, const int* __restrict__ child0, const int* __restrict__ nchild,
            const double* __restrict__ zc, double* __restrict__ Mn, const double* __restrict__ detr,
            const double* __restrict__ expand, DevOffsets off) {
-    __shared__ double sX[WARPS][FMM_NS_MAX], sY[WARPS][FMM_NS_MAX], sA[WARPS][FMM_NT_MAX];
-    __shared__ double sP[WARPS][3][FMM_PMAX + 1];
+    __shared__ double sX[WARPS][FMM_NS_MAX], sA[WARPS][FMM_NT_MAX];
+    __shared__ T sXt[WARPS][FMM_NS_MAX], sY[WARPS][FMM_NS_MAX];
+    __shared__ T sP[WARPS][3][FMM_PMAX + 1];
+    __shared__ T sInvF[FMM_NS_MAX], sFac[FMM_NS_MAX];
+    __shared__ int sIdx[FMM_NS_MAX];
+    const int ns = ns_of(p), nc = ncoef_of(p, basis);
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
+        const double inv = c_invfact[nx] * c_invfact[ny] * c_invfact[nz];
+        sInvF[s] = T(inv);
+        sFac[s] = T(1.0 / inv);   // nx! ny! nz! (exact: factorials up to 10! are integers below 2^24)
+        sIdx[s] = nx | (ny << 8) | (nz << 16);
+    }
+    __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lb + blockIdx.x * WARPS + w;
     if (c >= le || nchild[c] == 0) return;
-    const int ns = ns_of(p), nc = ncoef_of(p, basis);
-    for (int s = lane; s < ns; s += 32) sY[w][s] = 0.0;
+    for (int s = lane; s < ns; s += 32) sY[w][s] = T(0);
     for (int k = 0; k < nchild[c]; ++k) {
         const int ch = child0[c] + k;
         __syncwarp();
@@ -414,53 +409,59 @@ k_m2m_tree(int p, int basis, int lb, int le, const int* __restrict__ child0, con
             for (int t = lane; t < nc; t += 32) sA[w][t] = Mn[(int64_t)ch * nc + t];
             __syncwarp();
             expand_tl_warp(p, sA[w], sX[w], expand, off, lane);
+            __syncwarp();
+            for (int s = lane; s < ns; s += 32) sXt[w][s] = T(sX[w][s]) * sInvF[s];
         } else {
-            for (int s = lane; s < ns; s += 32) sX[w][s] = Mn[(int64_t)ch * nc + s];
+            for (int s = lane; s < ns; s += 32) sXt[w][s] = T(Mn[(int64_t)ch * nc + s]) * sInvF[s];
         }
         if (lane < 3) {
             const double md = -(zc[3 * ch + lane] - zc[3 * c + lane]);
             double v = 1.0;
-            sP[w][lane][0] = 1.0;
-            for (int j = 1; j <= p; ++j) { v *= md; sP[w][lane][j] = v; }
+            sP[w][lane][0] = T(1);
+            for (int j = 1; j <= p; ++j) { v *= md; sP[w][lane][j] = T(v * c_invfact[j]); }
         }
         __syncwarp();
         for (int s = lane; s < ns; s += 32) {
-            const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
-            double v = 0.0;
+            const int id = sIdx[s];
+            const int nx = id & 255, ny = (id >> 8) & 255, nz = id >> 16;
+            T v = T(0);
             for (int kx = 0; kx <= nx; ++kx)
-                for (int ky = 0; ky <= ny; ++ky)
-                    for (int kz = 0; kz <= nz; ++kz)
-                        v += c_binom[nx][kx] * c_binom[ny][ky] * c_binom[nz][kz] * sP[w][0][nx - kx] *
-                             sP[w][1][ny - ky] * sP[w][2][nz - kz] * sX[w][pos_sym(kx, ky, kz)];
-            sY[w][s] += v;
+                for (int ky = 0; ky <= ny; ++ky) {
+                    const T wxy = sP[w][0][nx - kx] * sP[w][1][ny - ky];
+                    for (int kz = 0; kz <= nz; ++kz) v += wxy * sP[w][2][nz - kz] * sXt[w][pos_sym(kx, ky, kz)];
+                }
+            sY[w][s] += v * sFac[s];
         }
     }
     __syncwarp();
     if (!basis) {
-        for (int s = lane; s < ns; s += 32) Mn[(int64_t)c * nc + s] = sY[w][s];
+        for (int s = lane; s < ns; s += 32) Mn[(int64_t)c * nc + s] = (double)sY[w][s];
         return;
     }
+    for (int s = lane; s < ns; s += 32) sX[w][s] = (double)sY[w][s];
+    __syncwarp();
     for (int t = lane; t < nc; t += 32) {
         const int nx = c_tl_idx[t][0], nz = c_tl_idx[t][2];
         const int j = c_tl_idx[t][0] + c_tl_idx[t][1] + nz;
         const int cols = (j + 1) * (j + 2) / 2;
         const int row = (j - nx) * (j - nx + 1) / 2 + nz;
         const double* R = detr + off.detr[j] + row * cols;
-        const double* Ys = &sY[w][ns_of(j - 1)];
+        const double* Ys = &sX[w][ns_of(j - 1)];
         double v = 0.0;
-        for (int s = 0; s < cols; ++s) v += R[s] * Ys[s];
+        for (int s2 = 0; s2 < cols; ++s2) v += R[s2] * Ys[s2];
         Mn[(int64_t)c * nc + t] = v;
     }
 }
 
 // L2L (Eq. L2L): children [lb, le) of one level, one warp each, add the
 // parent's shifted expansion.
-template <int WARPS>
+template <typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_l2l_tree(int p, int basis, int lb, int le, const int* __restrict__ parent, const double* __restrict__ zc,
            double* __restrict__ Ln, const double* __restrict__ expand, DevOffsets off) {
     __shared__ double sX[WARPS][FMM_NS_MAX], sA[WARPS][FMM_NT_MAX];
-    __shared__ double sP[WARPS][3][FMM_PMAX + 1];
+    __shared__ T sXt[WARPS][FMM_NS_MAX];
+    __shared__ T sP[WARPS][3][FMM_PMAX + 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lb + blockIdx.x * WARPS + w;
     if (c >= le) return;
@@ -476,77 +477,32 @@ k_l2l_tree(int p, int basis, int lb, int le, const int* __restrict__ parent, con
     if (lane < 3) {
         const double d = zc[3 * c + lane] - zc[3 * pa + lane];
         double v = 1.0;
-        sP[w][lane][0] = 1.0;
-        for (int j = 1; j <= p; ++j) { v *= d; sP[w][lane][j] = v * c_invfact[j]; }
+        sP[w][lane][0] = T(1);
+        for (int j = 1; j <= p; ++j) { v *= d; sP[w][lane][j] = T(v * c_invfact[j]); }
     }
+    __syncwarp();
+    for (int s = lane; s < ns; s += 32) sXt[w][s] = T(sX[w][s]);
     __syncwarp();
     for (int o = lane; o < nc; o += 32) {
         int nx, ny, nz;
         if (basis) { nx = c_tl_idx[o][0]; ny = c_tl_idx[o][1]; nz = c_tl_idx[o][2]; }
         else { nx = c_sym_idx[o][0]; ny = c_sym_idx[o][1]; nz = c_sym_idx[o][2]; }
         const int rem = p - nx - ny - nz;
-        double v = 0.0;
+        T v = T(0);
         for (int kx = 0; kx <= rem; ++kx)
-            for (int ky = 0; ky <= rem - kx; ++ky)
+            for (int ky = 0; ky <= rem - kx; ++ky) {
+                const T wxy = sP[w][0][kx] * sP[w][1][ky];
                 for (int kz = 0; kz <= rem - kx - ky; ++kz)
-                    v += sP[w][0][kx] * sP[w][1][ky] * sP[w][2][kz] * sX[w][pos_sym(nx + kx, ny + ky, nz + kz)];
-        Ln[(int64_t)c * nc + o] += v;
-    }
-}
-
-// L2P (Eq. L2P) at the leaves, one warp per leaf, lanes over particles;
-// overwrites pot = -Phi, acc = grad Phi in caller order.
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
-k_l2p_tree(int p, int basis, int nleaf, const int* __restrict__ leaf, const int* __restrict__ nb,
-           const int* __restrict__ ne, const double* __restrict__ zc, const double* __restrict__ xs,
-           const double* __restrict__ ys, const double* __restrict__ zs, const int* __restrict__ perm,
-           const double* __restrict__ Ln, const double* __restrict__ expand, DevOffsets off,
-           double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az) {
-    __shared__ double sX[WARPS][FMM_NS_MAX], sA[WARPS][FMM_NT_MAX];
-    __shared__ double sP[WARPS][32][3][FMM_PMAX + 1];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * WARPS + w;
-    if (k >= nleaf) return;
-    const int c = leaf[k];
-    const int ns = ns_of(p), nc = ncoef_of(p, basis);
-    if (basis) {
-        for (int t = lane; t < nc; t += 32) sA[w][t] = Ln[(int64_t)c * nc + t];
-        __syncwarp();
-        expand_tl_warp(p, sA[w], sX[w], expand, off, lane);
-    } else {
-        for (int s = lane; s < ns; s += 32) sX[w][s] = Ln[(int64_t)c * nc + s];
-    }
-    __syncwarp();
-    for (int a0 = nb[c]; a0 < ne[c]; a0 += 32) {
-        const int a = a0 + lane;
-        if (a >= ne[c]) break;
-        const double rr[3] = {xs[a] - zc[3 * c], ys[a] - zc[3 * c + 1], zs[a] - zc[3 * c + 2]};
-        for (int d = 0; d < 3; ++d) {
-            double v = 1.0;
-            sP[w][lane][d][0] = 1.0;
-            for (int j = 1; j <= p; ++j) { v *= rr[d]; sP[w][lane][d][j] = v * c_invfact[j]; }
-        }
-        double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-        for (int s = 0; s < ns; ++s) {
-            const int kx = c_sym_idx[s][0], ky = c_sym_idx[s][1], kz = c_sym_idx[s][2];
-            const double wgt = sP[w][lane][0][kx] * sP[w][lane][1][ky] * sP[w][lane][2][kz];
-            ph += wgt * sX[w][s];
-            if (kx + ky + kz < p) {
-                gx += wgt * sX[w][pos_sym(kx + 1, ky, kz)];
-                gy += wgt * sX[w][pos_sym(kx, ky + 1, kz)];
-                gz += wgt * sX[w][pos_sym(kx, ky, kz + 1)];
+                    v += wxy * sP[w][2][kz] * sXt[w][pos_sym(nx + kx, ny + ky, nz + kz)];
             }
-        }
-        const int o = perm[a];
-        pot[o] = -ph; ax[o] = gx; ay[o] = gy; az[o] = gz;
+        Ln[(int64_t)c * nc + o] += (double)v;   // accumulation into the FP64 expansion
     }
 }
 
-// P2P over the near-field lists: one warp per target leaf taken from an
+// FP64 P2P over the near-field lists: one warp per target leaf taken from an
 // atomic work counter (persistent grid); lane groups split the staged
-// sources; positions relative to the target leaf centre (FP32 form keeps
-// its relative accuracy).  Accumulates into caller order.
+// sources; positions relative to the target leaf centre.  Accumulates into
+// caller order.  (The FP32 form has its own kernel, k_ad_p2p32.)
 template <typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_p2p_tree(int nwork, const int* __restrict__ work, const int* __restrict__ off, const int* __restrict__ src,
@@ -684,61 +640,44 @@ int ad_leaf_keys(int nn, const int* nchild, const int* nb, uint64_t* key, int* v
     count_launch();
     return 0;
 }
-int ad_leaf_arrays(int nleaf, int64_t n, const int* leaf, const int* nb, const double* zc, int64_t* lstart,
-                   double* lcen, cudaStream_t s) {
-    k_leaf_arrays<<<G256(nleaf + 1)>>>(nleaf, n, leaf, nb, zc, lstart, lcen);
-    count_launch();
-    return 0;
-}
-int ad_leafM_to_nodes(int nleaf, int nc, const int* leaf, const double* Ml, double* Mn, cudaStream_t s) {
-    if (nleaf) { k_leafM_to_nodes<<<G256((int64_t)nleaf * nc)>>>(nleaf, nc, leaf, Ml, Mn); count_launch(); }
-    return 0;
-}
 int ad_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
     if (n) { k_f64_to_f32<<<G256(n)>>>(n, a, b); count_launch(); }
     return 0;
 }
-int ad_m2m(int p, int basis, int lb, int le, const int* child0, const int* nchild, const double* zc, double* Mn,
+int ad_m2m(int prec, int p, int basis, int lb, int le, const int* child0, const int* nchild, const double* zc,
+           double* Mn, const DevTables& T, cudaStream_t s) {
+    if (le <= lb) return 0;
+    constexpr int W = 4;
+    const unsigned g = (unsigned)((le - lb + W - 1) / W);
+    if (prec)
+        k_m2m_tree<float, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, child0, nchild, zc, Mn, T.detr, T.expand,
+                                                  T.offsets());
+    else
+        k_m2m_tree<double, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, child0, nchild, zc, Mn, T.detr, T.expand,
+                                                   T.offsets());
+    count_launch();
+    return 0;
+}
+int ad_l2l(int prec, int p, int basis, int lb, int le, const int* parent, const double* zc, double* Ln,
            const DevTables& T, cudaStream_t s) {
     if (le <= lb) return 0;
     constexpr int W = 4;
-    k_m2m_tree<W><<<(unsigned)((le - lb + W - 1) / W), W * 32, 0, s>>>(p, basis, lb, le, child0, nchild, zc, Mn,
-                                                                       T.detr, T.expand, T.offsets());
+    const unsigned g = (unsigned)((le - lb + W - 1) / W);
+    if (prec)
+        k_l2l_tree<float, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, parent, zc, Ln, T.expand, T.offsets());
+    else
+        k_l2l_tree<double, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, parent, zc, Ln, T.expand, T.offsets());
     count_launch();
     return 0;
 }
-int ad_l2l(int p, int basis, int lb, int le, const int* parent, const double* zc, double* Ln, const DevTables& T,
-           cudaStream_t s) {
-    if (le <= lb) return 0;
-    constexpr int W = 4;
-    k_l2l_tree<W><<<(unsigned)((le - lb + W - 1) / W), W * 32, 0, s>>>(p, basis, lb, le, parent, zc, Ln, T.expand,
-                                                                       T.offsets());
-    count_launch();
-    return 0;
-}
-int ad_l2p(int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne, const double* zc,
-           const double* xs, const double* ys, const double* zs, const int* perm, const double* Ln,
-           const DevTables& T, double* pot, double* ax, double* ay, double* az, cudaStream_t s) {
-    if (nleaf <= 0) return 0;
-    constexpr int W = 2;
-    k_l2p_tree<W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(p, basis, nleaf, leaf, nb, ne, zc, xs, ys, zs,
-                                                                     perm, Ln, T.expand, T.offsets(), pot, ax, ay,
-                                                                     az);
-    count_launch();
-    return 0;
-}
-int ad_p2p(int prec, int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne,
+int ad_p2p(int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne,
            const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
            const int* perm, double* pot, double* ax, double* ay, double* az, int* counter, int blocks,
            cudaStream_t s) {
     if (nwork <= 0) return 0;
     constexpr int W = 4;
-    if (prec == 0)
-        k_p2p_tree<double, W><<<blocks, W * 32, 0, s>>>(nwork, work, off, src, nb, ne, zc, xs, ys, zs, qs, perm, pot,
-                                                        ax, ay, az, counter);
-    else
-        k_p2p_tree<float, W><<<blocks, W * 32, 0, s>>>(nwork, work, off, src, nb, ne, zc, xs, ys, zs, qs, perm, pot,
-                                                       ax, ay, az, counter);
+    k_p2p_tree<double, W><<<blocks, W * 32, 0, s>>>(nwork, work, off, src, nb, ne, zc, xs, ys, zs, qs, perm, pot, ax,
+                                                    ay, az, counter);
     count_launch();
     return 0;
 }

@@ -27,10 +27,11 @@ struct AdState {
     int *cm = nullptr, *cp = nullptr, *cq = nullptr, *om = nullptr, *op = nullptr, *oq = nullptr;
     int2 *m2l = nullptr, *p2p = nullptr;
     int *moff = nullptr, *msrc = nullptr, *poff = nullptr, *psrc = nullptr, *order = nullptr, *leaf = nullptr;
-    int64_t* lstart = nullptr;
-    double* lcen = nullptr;
+    int4* ic = nullptr;        // integer node centres (fmm_adaptive_leaf.cu)
+    float4* pos32 = nullptr;   // FP32 form: particle offsets from their leaf centre, charge
+    float scale32 = 0.f;       // side / 2^22: unit of the integer centres
     // expansions (node-major)
-    double *Mleaf = nullptr, *M = nullptr, *L = nullptr;
+    double *M = nullptr, *L = nullptr;
     float* M32 = nullptr;
     int* counter = nullptr;
     // capacities (bytes)
@@ -39,8 +40,8 @@ struct AdState {
            cap_iy = 0, cap_iz = 0, cap_nb = 0, cap_ne = 0, cap_child0 = 0, cap_nchild = 0, cap_parent = 0,
            cap_zc = 0, cap_rad = 0, cap_bounds = 0, cap_nch = 0, cap_choff = 0, cap_q0 = 0, cap_q1 = 0, cap_cm = 0,
            cap_cp = 0, cap_cq = 0, cap_om = 0, cap_op = 0, cap_oq = 0, cap_m2l = 0, cap_p2p = 0, cap_moff = 0,
-           cap_msrc = 0, cap_poff = 0, cap_psrc = 0, cap_order = 0, cap_leaf = 0, cap_lstart = 0, cap_lcen = 0,
-           cap_Mleaf = 0, cap_M = 0, cap_L = 0, cap_M32 = 0, cap_counter = 0;
+           cap_msrc = 0, cap_poff = 0, cap_psrc = 0, cap_order = 0, cap_leaf = 0, cap_ic = 0, cap_pos32 = 0,
+           cap_M = 0, cap_L = 0, cap_M32 = 0, cap_counter = 0;
     // autotuned persistent grid of the M2L kernel
     int m2l_blocks = 0, m2l_blocks_per_sm = 0;
     float m2l_tuned_ms = 0.f;
@@ -53,11 +54,11 @@ struct AdState {
 void ad_free(AdState* a);
 int ad_build(AdState* a, int64_t n, const double* x, const double* y, const double* z, const double* q,
              int max_leaf, double theta, int nc, int prec, cudaStream_t s);
-int ad_run_p2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s);
-int ad_run_m2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s);
+int ad_run_p2m(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s);
+int ad_run_m2m(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s);
 int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s);
-int ad_run_l2l(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s);
-int ad_run_l2p(AdState* a, int p, int basis, const DevTables& T, double* pot, double* ax, double* ay, double* az,
+int ad_run_l2l(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s);
+int ad_run_l2p(AdState* a, int prec, int p, int basis, const DevTables& T, double* pot, double* ax, double* ay, double* az,
                cudaStream_t s);
 int ad_run_p2p(AdState* a, int prec, int sms, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
 
@@ -86,22 +87,32 @@ int ad_pair_keys(int n, const int2* pr, uint64_t* key, int* val, cudaStream_t s)
 int ad_pair_csr(int n, const uint64_t* key, const int* val, const int2* pr, int* src, int* cnt, cudaStream_t s);
 int ad_len_keys(int nn, const int* off, uint64_t* key, int* val, cudaStream_t s);
 int ad_leaf_keys(int nn, const int* nchild, const int* nb, uint64_t* key, int* val, cudaStream_t s);
-int ad_leaf_arrays(int nleaf, int64_t n, const int* leaf, const int* nb, const double* zc, int64_t* lstart,
-                   double* lcen, cudaStream_t s);
-int ad_leafM_to_nodes(int nleaf, int nc, const int* leaf, const double* Ml, double* Mn, cudaStream_t s);
 int ad_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
-int ad_m2m(int p, int basis, int lb, int le, const int* child0, const int* nchild, const double* zc, double* Mn,
+int ad_m2m(int prec, int p, int basis, int lb, int le, const int* child0, const int* nchild, const double* zc, double* Mn,
            const DevTables& T, cudaStream_t s);
-int ad_l2l(int p, int basis, int lb, int le, const int* parent, const double* zc, double* Ln, const DevTables& T,
+int ad_l2l(int prec, int p, int basis, int lb, int le, const int* parent, const double* zc, double* Ln, const DevTables& T,
            cudaStream_t s);
-int ad_l2p(int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne, const double* zc,
-           const double* xs, const double* ys, const double* zs, const int* perm, const double* Ln,
-           const DevTables& T, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
-int ad_p2p(int prec, int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne,
+int ad_p2p(int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne,
            const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
            const int* perm, double* pot, double* ax, double* ay, double* az, int* counter, int blocks,
            cudaStream_t s);
 int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off, const int* src,
-                    const double* zc, const void* M, double* Ln, int* counter, int blocks, cudaStream_t s);
+                    const double* zc, const int4* ic, float scale, const void* M, double* Ln, int* counter,
+                    int blocks, cudaStream_t s);
+
+// fmm_adaptive_leaf.cu
+int ad_pos32(int nleaf, const int* leaf, const int* nb, const int* ne, const double* zc, const double* xs,
+             const double* ys, const double* zs, const double* qs, float4* pos32, cudaStream_t s);
+int ad_icentre(int nn, const int* lev, const int* ix, const int* iy, const int* iz, int4* ic, cudaStream_t s);
+int ad_p2m_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
+                const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
+                const float4* pos32, double* Mn, const DevTables& Tb, cudaStream_t s);
+int ad_l2p_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
+                const double* zc, const double* xs, const double* ys, const double* zs, const float4* pos32,
+                const int* perm, const double* Ln, const DevTables& Tb, double* pot, double* ax, double* ay,
+                double* az, cudaStream_t s);
+int ad_p2p32(int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne, const int4* ic,
+             float scale, const float4* pos32, const int* perm, double* pot, double* ax, double* ay, double* az,
+             int* counter, int blocks, cudaStream_t s);
 
 }  // namespace fmm

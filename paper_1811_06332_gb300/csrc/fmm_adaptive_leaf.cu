@@ -1,0 +1,406 @@
+// Leaf kernels of the adaptive-octree FMM, specialised per order p and per
+// arithmetic type (double for FMM_FP64, float for FMM_FP32):
+//   P2M (Eq. P2M)  A_m = sum_a q_a (-(x_a - z))^m about the leaf centre z,
+//                  SYM: M = A, TRACELESS: Mbar = D[A] (independent comps);
+//   L2P (Eq. L2P)  Phi = sum_k (x - z)^k / k! L_k and its gradient;
+//   P2P            near field over the leaf pairs of the interaction lists.
+// Expansions are node-major ([node][ncoef]) in physical units.
+//
+// The FP32 form reads particles as FP32 offsets from the centre of their own
+// leaf (pos32), and takes the offset between two node centres from their
+// integer coordinates (ic = (2i+1) 2^(21-level) per axis, in units of
+// side/2^22): an exact integer difference rounded once to FP32.  No FP64
+// arithmetic runs per particle pair or per source, which matters on a part
+// whose FP64 rate is 1/64 of its FP32 rate.
+#include "fmm_adaptive.h"
+
+namespace fmm {
+
+// pos32[a] = (x_a - z_c, y_a - z_c, z_a - z_c, q_a) for the leaf c holding a
+__global__ void k_ad_pos32(int nleaf, const int* __restrict__ leaf, const int* __restrict__ nb,
+                           const int* __restrict__ ne, const double* __restrict__ zc, const double* __restrict__ xs,
+                           const double* __restrict__ ys, const double* __restrict__ zs,
+                           const double* __restrict__ qs, float4* __restrict__ pos32) {
+    const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (k >= nleaf) return;
+    const int c = leaf[k];
+    const double cx = zc[3 * c], cy = zc[3 * c + 1], cz = zc[3 * c + 2];
+    for (int a = nb[c] + lane; a < ne[c]; a += 32)
+        pos32[a] = make_float4((float)(xs[a] - cx), (float)(ys[a] - cy), (float)(zs[a] - cz), (float)qs[a]);
+}
+
+// ic[c] = integer centre of node c (see above), w = level
+__global__ void k_ad_icentre(int nn, const int* __restrict__ lev, const int* __restrict__ ix,
+                             const int* __restrict__ iy, const int* __restrict__ iz, int4* __restrict__ ic) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nn) return;
+    const int sh = 21 - lev[c];
+    ic[c] = make_int4((2 * ix[c] + 1) << sh, (2 * iy[c] + 1) << sh, (2 * iz[c] + 1) << sh, lev[c]);
+}
+
+// ---------------------------------------------------------------------------
+// P2M: one warp per leaf; lane owns the column (nx, ny) of multi-indices and
+// walks nz upward (one product per component and particle).
+// ---------------------------------------------------------------------------
+template <int P, typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_ad_p2m(int basis, int nleaf, const int* __restrict__ leaf, const int* __restrict__ nb, const int* __restrict__ ne,
+         const double* __restrict__ zc, const double* __restrict__ xs, const double* __restrict__ ys,
+         const double* __restrict__ zs, const double* __restrict__ qs, const float4* __restrict__ pos32,
+         double* __restrict__ Mn, const double* __restrict__ detr, DevOffsets off) {
+    constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
+    constexpr int NCOL = (P + 1) * (P + 2) / 2;
+    constexpr int KC = (NCOL + 31) / 32;
+    __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
+    __shared__ double sA[WARPS][NS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * WARPS + w;
+    if (k >= nleaf) return;
+    const int c = leaf[k];
+    const int b = nb[c], e = ne[c];
+    T acc[KC][P + 1];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk)
+#pragma unroll
+        for (int j = 0; j <= P; ++j) acc[kk][j] = T(0);
+    int cnx[KC], cny[KC];
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+        int col = lane + 32 * kk, nx = 0;
+        while (nx <= P && col >= P + 1 - nx) { col -= P + 1 - nx; ++nx; }
+        cnx[kk] = nx;
+        cny[kk] = col;
+    }
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    if (!pos32) { cx = zc[3 * c]; cy = zc[3 * c + 1]; cz = zc[3 * c + 2]; }
+    for (int a0 = b; a0 < e; a0 += 32) {
+        const int a = a0 + lane;
+        __syncwarp();
+        if (a < e) {
+            if (pos32) {
+                const float4 v = pos32[a];
+                sx[w][lane] = T(-v.x); sy[w][lane] = T(-v.y); sz[w][lane] = T(-v.z); sq[w][lane] = T(v.w);
+            } else {
+                sx[w][lane] = T(cx - xs[a]); sy[w][lane] = T(cy - ys[a]); sz[w][lane] = T(cz - zs[a]);
+                sq[w][lane] = T(qs[a]);
+            }
+        }
+        __syncwarp();
+        const int cnt = min(32, e - a0);
+        for (int i = 0; i < cnt; ++i) {
+            const T rx = sx[w][i], ry = sy[w][i], rz = sz[w][i], qa = sq[w][i];
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                if (lane + 32 * kk < NCOL) {
+                    T wgt = qa;
+                    for (int t = 0; t < cnx[kk]; ++t) wgt *= rx;
+                    for (int t = 0; t < cny[kk]; ++t) wgt *= ry;
+                    const int rem = P - cnx[kk] - cny[kk];
+#pragma unroll
+                    for (int j = 0; j <= P; ++j)
+                        if (j <= rem) { acc[kk][j] += wgt; wgt *= rz; }
+                }
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+        if (lane + 32 * kk < NCOL) {
+            const int rem = P - cnx[kk] - cny[kk];
+#pragma unroll
+            for (int j = 0; j <= P; ++j)
+                if (j <= rem) sA[w][pos_sym(cnx[kk], cny[kk], j)] = (double)acc[kk][j];
+        }
+    }
+    __syncwarp();
+    if (!basis) {
+        for (int s = lane; s < NS; s += 32) Mn[(int64_t)c * NS + s] = sA[w][s];
+        return;
+    }
+    constexpr int NT = (P + 1) * (P + 1);
+    for (int t = lane; t < NT; t += 32) {
+        const int nx = c_tl_idx[t][0], nz = c_tl_idx[t][2];
+        const int j = nx + c_tl_idx[t][1] + nz;
+        const int cols = (j + 1) * (j + 2) / 2;
+        const int row = (j - nx) * (j - nx + 1) / 2 + nz;
+        const double* R = detr + off.detr[j] + row * cols;
+        const double* As = &sA[w][ns_of(j - 1)];
+        double v = 0.0;
+        for (int s = 0; s < cols; ++s) v += R[s] * As[s];
+        Mn[(int64_t)c * NT + t] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2P: one warp per leaf, lanes over particles; the full symmetric local
+// expansion (dependent traceless components rebuilt) in shared memory.
+// Overwrites pot = -Phi and acc = grad Phi in caller order.
+// ---------------------------------------------------------------------------
+template <int P, typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restrict__ nb, const int* __restrict__ ne,
+         const double* __restrict__ zc, const double* __restrict__ xs, const double* __restrict__ ys,
+         const double* __restrict__ zs, const float4* __restrict__ pos32, const int* __restrict__ perm,
+         const double* __restrict__ Ln, const double* __restrict__ expand, DevOffsets off,
+         double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az) {
+    constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
+    constexpr int NT = (P + 1) * (P + 1);
+    __shared__ double sA[WARPS][NT];
+    __shared__ T sL[WARPS][NS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * WARPS + w;
+    if (k >= nleaf) return;
+    const int c = leaf[k];
+    const int b = nb[c], e = ne[c];
+    if (b == e) return;
+    if (basis) {
+        for (int t = lane; t < NT; t += 32) sA[w][t] = Ln[(int64_t)c * NT + t];
+        __syncwarp();
+        for (int s = lane; s < NS; s += 32) {
+            const int nx = c_sym_idx[s][0], nz = c_sym_idx[s][2];
+            const int j = nx + c_sym_idx[s][1] + nz;
+            const int row = (j - nx) * (j - nx + 1) / 2 + nz;
+            const double* E = expand + off.expand[j] + row * (2 * j + 1);
+            double v = 0.0;
+            for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][j * j + t];
+            sL[w][s] = T(v);
+        }
+    } else {
+        for (int s = lane; s < NS; s += 32) sL[w][s] = T(Ln[(int64_t)c * NS + s]);
+    }
+    __syncwarp();
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    if (!pos32) { cx = zc[3 * c]; cy = zc[3 * c + 1]; cz = zc[3 * c + 2]; }
+    const T* L = sL[w];
+    for (int a0 = b; a0 < e; a0 += 32) {
+        const int a = a0 + lane;
+        if (a >= e) break;
+        T rx, ry, rz;
+        if (pos32) {
+            const float4 v = pos32[a];
+            rx = T(v.x); ry = T(v.y); rz = T(v.z);
+        } else {
+            rx = T(xs[a] - cx); ry = T(ys[a] - cy); rz = T(zs[a] - cz);
+        }
+        T fx[P + 1], fy[P + 1], fz[P + 1];
+        fx[0] = fy[0] = fz[0] = T(1);
+#pragma unroll
+        for (int kk = 1; kk <= P; ++kk) {
+            fx[kk] = fx[kk - 1] * rx * T(1.0 / kk);
+            fy[kk] = fy[kk - 1] * ry * T(1.0 / kk);
+            fz[kk] = fz[kk - 1] * rz * T(1.0 / kk);
+        }
+        T ph = 0, gx = 0, gy = 0, gz = 0;
+#pragma unroll
+        for (int kx = 0; kx <= P; ++kx) {
+            T xp = 0, xgx = 0, xgy = 0, xgz = 0;
+#pragma unroll
+            for (int ky = 0; ky <= P - kx; ++ky) {
+                T s_p = 0, s_gx = 0, s_gy = 0, s_gz = 0;
+#pragma unroll
+                for (int kz = 0; kz <= P - kx - ky; ++kz) {
+                    s_p += fz[kz] * L[pos_sym(kx, ky, kz)];
+                    if (kx + ky + kz < P) {
+                        s_gx += fz[kz] * L[pos_sym(kx + 1, ky, kz)];
+                        s_gy += fz[kz] * L[pos_sym(kx, ky + 1, kz)];
+                        s_gz += fz[kz] * L[pos_sym(kx, ky, kz + 1)];
+                    }
+                }
+                xp += fy[ky] * s_p; xgx += fy[ky] * s_gx; xgy += fy[ky] * s_gy; xgz += fy[ky] * s_gz;
+            }
+            ph += fx[kx] * xp; gx += fx[kx] * xgx; gy += fx[kx] * xgy; gz += fx[kx] * xgz;
+        }
+        const int o = perm[a];
+        pot[o] = -(double)ph;
+        ax[o] = (double)gx;
+        ay[o] = (double)gy;
+        az[o] = (double)gz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 P2P over the near-field lists: one warp per target leaf from an
+// atomic work counter (persistent grid).  Up to 64 targets per pass: above
+// 32 each lane keeps two targets; at or below 16 the targets are spread over
+// lane groups that split the staged sources and are summed by shuffles.
+// Sources are staged 32 at a time as float4 (offset from the target leaf
+// centre, charge); r = 0 pairs (the particle itself, coincident points)
+// contribute nothing.  Accumulates into caller order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void p2p_acc(const float4 s, float xi, float yi, float zi, float& ph, float& gx,
+                                        float& gy, float& gz) {
+    const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float qir = s.w * ir, qir3 = qir * ir * ir;
+    ph += qir;
+    gx = fmaf(qir3, dx, gx);
+    gy = fmaf(qir3, dy, gy);
+    gz = fmaf(qir3, dz, gz);
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_ad_p2p32(int nwork, const int* __restrict__ work, const int* __restrict__ off, const int* __restrict__ src,
+           const int* __restrict__ nb, const int* __restrict__ ne, const int4* __restrict__ ic, float scale,
+           const float4* __restrict__ pos32, const int* __restrict__ perm, double* __restrict__ pot,
+           double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az, int* __restrict__ counter) {
+    __shared__ float4 ss[WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nwork) break;
+        const int c = work[item];
+        const int4 ct = ic[c];
+        const int b = nb[c], e = ne[c];
+        const int k0 = off[c], k1 = off[c + 1];
+        for (int t0 = b; t0 < e; t0 += 64) {
+            const int tn = min(64, e - t0);
+            if (tn > 32) {
+                // two targets per lane
+                const int i0 = t0 + lane, i1 = t0 + 32 + lane;
+                const bool a1 = lane < tn - 32;
+                const float4 p0 = pos32[i0];
+                const float4 p1 = a1 ? pos32[i1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float ph0 = 0.f, gx0 = 0.f, gy0 = 0.f, gz0 = 0.f, ph1 = 0.f, gx1 = 0.f, gy1 = 0.f, gz1 = 0.f;
+                for (int k = k0; k < k1; ++k) {
+                    const int S = src[k];
+                    const int4 cs = ic[S];
+                    const float ox = (float)(cs.x - ct.x) * scale, oy = (float)(cs.y - ct.y) * scale,
+                                oz = (float)(cs.z - ct.z) * scale;
+                    const int sb = nb[S], se = ne[S];
+                    for (int s0 = sb; s0 < se; s0 += 32) {
+                        __syncwarp();
+                        if (s0 + lane < se) {
+                            const float4 v = pos32[s0 + lane];
+                            ss[w][lane] = make_float4(v.x + ox, v.y + oy, v.z + oz, v.w);
+                        }
+                        __syncwarp();
+                        const int cnt = min(32, se - s0);
+                        for (int j = 0; j < cnt; ++j) {
+                            const float4 sv = ss[w][j];
+                            p2p_acc(sv, p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
+                            p2p_acc(sv, p1.x, p1.y, p1.z, ph1, gx1, gy1, gz1);
+                        }
+                    }
+                }
+                int o = perm[i0];
+                pot[o] -= (double)ph0; ax[o] += (double)gx0; ay[o] += (double)gy0; az[o] += (double)gz0;
+                if (a1) {
+                    o = perm[i1];
+                    pot[o] -= (double)ph1; ax[o] += (double)gx1; ay[o] += (double)gy1; az[o] += (double)gz1;
+                }
+            } else {
+                int tp = 1;
+                while (tp < tn) tp <<= 1;
+                const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
+                const int ti = t0 + tl;
+                const bool act = tl < tn;
+                const float4 pi = act ? pos32[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                for (int k = k0; k < k1; ++k) {
+                    const int S = src[k];
+                    const int4 cs = ic[S];
+                    const float ox = (float)(cs.x - ct.x) * scale, oy = (float)(cs.y - ct.y) * scale,
+                                oz = (float)(cs.z - ct.z) * scale;
+                    const int sb = nb[S], se = ne[S];
+                    for (int s0 = sb; s0 < se; s0 += 32) {
+                        __syncwarp();
+                        if (s0 + lane < se) {
+                            const float4 v = pos32[s0 + lane];
+                            ss[w][lane] = make_float4(v.x + ox, v.y + oy, v.z + oz, v.w);
+                        }
+                        __syncwarp();
+                        const int cnt = min(32, se - s0);
+                        if (act)
+                            for (int j = grp; j < cnt; j += G) p2p_acc(ss[w][j], pi.x, pi.y, pi.z, ph, gx, gy, gz);
+                    }
+                }
+                for (int o = tp; o < 32; o <<= 1) {
+                    ph += __shfl_xor_sync(0xffffffffu, ph, o); gx += __shfl_xor_sync(0xffffffffu, gx, o);
+                    gy += __shfl_xor_sync(0xffffffffu, gy, o); gz += __shfl_xor_sync(0xffffffffu, gz, o);
+                }
+                if (act && grp == 0) {
+                    const int o = perm[ti];
+                    pot[o] -= (double)ph; ax[o] += (double)gx; ay[o] += (double)gy; az[o] += (double)gz;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int ad_pos32(int nleaf, const int* leaf, const int* nb, const int* ne, const double* zc, const double* xs,
+             const double* ys, const double* zs, const double* qs, float4* pos32, cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+    k_ad_pos32<<<(unsigned)(((int64_t)nleaf * 32 + 255) / 256), 256, 0, s>>>(nleaf, leaf, nb, ne, zc, xs, ys, zs, qs,
+                                                                            pos32);
+    count_launch();
+    return 0;
+}
+
+int ad_icentre(int nn, const int* lev, const int* ix, const int* iy, const int* iz, int4* ic, cudaStream_t s) {
+    if (nn <= 0) return 0;
+    k_ad_icentre<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, lev, ix, iy, iz, ic);
+    count_launch();
+    return 0;
+}
+
+#define AD_P_SWITCH(P_, CALL) \
+    switch (P_) {             \
+        case 0: CALL(0); break; case 1: CALL(1); break; case 2: CALL(2); break; case 3: CALL(3); break; \
+        case 4: CALL(4); break; case 5: CALL(5); break; case 6: CALL(6); break; case 7: CALL(7); break; \
+        case 8: CALL(8); break; case 9: CALL(9); break; default: CALL(10); break; }
+
+int ad_p2m_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
+                const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
+                const float4* pos32, double* Mn, const DevTables& Tb, cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+    constexpr int W = 4;
+    const unsigned g = (unsigned)((nleaf + W - 1) / W);
+#define C64(P) k_ad_p2m<P, double, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, qs, nullptr, \
+                                                            Mn, Tb.detr, Tb.offsets())
+#define C32(P) k_ad_p2m<P, float, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, qs, pos32, \
+                                                           Mn, Tb.detr, Tb.offsets())
+    if (prec == 0) { AD_P_SWITCH(p, C64) } else { AD_P_SWITCH(p, C32) }
+#undef C64
+#undef C32
+    count_launch();
+    return 0;
+}
+
+int ad_l2p_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
+                const double* zc, const double* xs, const double* ys, const double* zs, const float4* pos32,
+                const int* perm, const double* Ln, const DevTables& Tb, double* pot, double* ax, double* ay,
+                double* az, cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+    constexpr int W = 4;
+    const unsigned g = (unsigned)((nleaf + W - 1) / W);
+#define C64(P) k_ad_l2p<P, double, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, nullptr, \
+                                                            perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az)
+#define C32(P) k_ad_l2p<P, float, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, pos32, \
+                                                           perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az)
+    if (prec == 0) { AD_P_SWITCH(p, C64) } else { AD_P_SWITCH(p, C32) }
+#undef C64
+#undef C32
+    count_launch();
+    return 0;
+}
+
+int ad_p2p32(int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne, const int4* ic,
+             float scale, const float4* pos32, const int* perm, double* pot, double* ax, double* ay, double* az,
+             int* counter, int blocks, cudaStream_t s) {
+    if (nwork <= 0) return 0;
+    constexpr int W = 4;
+    k_ad_p2p32<W><<<(unsigned)blocks, W * 32, 0, s>>>(nwork, work, off, src, nb, ne, ic, scale, pos32, perm, pot, ax,
+                                                     ay, az, counter);
+    count_launch();
+    return 0;
+}
+
+}  // namespace fmm

@@ -40,8 +40,8 @@ void ad_free(AdState* a) {
     void* ptrs[] = {a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
                     a->box, a->part, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0, a->nchild, a->parent,
                     a->zc, a->rad, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
-                    a->oq, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->lstart,
-                    a->lcen, a->Mleaf, a->M, a->L, a->M32, a->counter};
+                    a->oq, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
+                    a->pos32, a->M, a->L, a->M32, a->counter};
     for (void* p : ptrs) cudaFree(p);
     if (a->gexec) cudaGraphExecDestroy(a->gexec);
     delete a;
@@ -216,36 +216,44 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         a->nleaf = nl;
         a->ntarg = nt;
     }
-    GROW(a->lstart, a->cap_lstart, (size_t)(a->nleaf + 1) * 8);
-    GROW(a->lcen, a->cap_lcen, (size_t)a->nleaf * 24);
-    ad_leaf_arrays(a->nleaf, n, a->leaf, a->nb, a->zc, a->lstart, a->lcen, s);
-    GROW(a->Mleaf, a->cap_Mleaf, (size_t)a->nleaf * nc * 8);
+    // integer centres (FP32 centre offsets) and FP32 particle offsets
+    GROW(a->ic, a->cap_ic, (size_t)a->nn * 16);
+    ad_icentre(a->nn, a->lev, a->ix, a->iy, a->iz, a->ic, s);
+    if (prec != 0) {
+        GROW(a->pos32, a->cap_pos32, (size_t)n * 16);
+        ad_pos32(a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs, a->pos32, s);
+    }
+    {
+        double side = 0.0;
+        cudaMemcpyAsync(&side, a->box + 3, 8, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
+        a->scale32 = (float)(side / 4194304.0);
+    }
     GROW(a->M, a->cap_M, (size_t)a->nn * nc * 8);
     GROW(a->L, a->cap_L, (size_t)a->nn * nc * 8);
     if (prec != 0) GROW(a->M32, a->cap_M32, (size_t)a->nn * nc * 4);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int ad_run_p2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s) {
+int ad_run_p2m(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s) {
     if (a->n == 0) return 0;
-    launch_p2m(p, basis, 0, a->nleaf, a->lstart, nullptr, a->xs, a->ys, a->zs, a->qs, a->lcen, 0, 1.0, a->Mleaf,
-               a->nleaf, T, s);
-    ad_leafM_to_nodes(a->nleaf, a->nc, a->leaf, a->Mleaf, a->M, s);
+    ad_p2m_leaf(prec, p, basis, a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs, a->pos32, a->M,
+                T, s);
     return 0;
 }
 
-int ad_run_m2m(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s) {
+int ad_run_m2m(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s) {
     if (a->n == 0) return 0;
     for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
-        ad_m2m(p, basis, a->lvl[L], a->lvl[L + 1], a->child0, a->nchild, a->zc, a->M, T, s);
+        ad_m2m(prec, p, basis, a->lvl[L], a->lvl[L + 1], a->child0, a->nchild, a->zc, a->M, T, s);
     return 0;
 }
 
 static int m2l_launch(AdState* a, int p, int basis, int prec, int blocks, cudaStream_t s) {
     cudaMemsetAsync(a->counter, 0, 4, s);
     const void* M = prec ? (const void*)a->M32 : (const void*)a->M;
-    return launch_m2l_list(p, basis, prec ? 1 : 0, a->ntarg, a->order, a->moff, a->msrc, a->zc, M, a->L, a->counter,
-                           blocks, s);
+    return launch_m2l_list(p, basis, prec ? 1 : 0, a->ntarg, a->order, a->moff, a->msrc, a->zc, a->ic, a->scale32, M,
+                           a->L, a->counter, blocks, s);
 }
 
 int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s) {
@@ -284,26 +292,30 @@ int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s) 
     return 0;
 }
 
-int ad_run_l2l(AdState* a, int p, int basis, const DevTables& T, cudaStream_t s) {
+int ad_run_l2l(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s) {
     if (a->n == 0) return 0;
     for (int L = 1; L + 1 < (int)a->lvl.size(); ++L)
-        ad_l2l(p, basis, a->lvl[L], a->lvl[L + 1], a->parent, a->zc, a->L, T, s);
+        ad_l2l(prec, p, basis, a->lvl[L], a->lvl[L + 1], a->parent, a->zc, a->L, T, s);
     return 0;
 }
 
-int ad_run_l2p(AdState* a, int p, int basis, const DevTables& T, double* pot, double* ax, double* ay, double* az,
+int ad_run_l2p(AdState* a, int prec, int p, int basis, const DevTables& T, double* pot, double* ax, double* ay, double* az,
                cudaStream_t s) {
     if (a->n == 0) return 0;
-    ad_l2p(p, basis, a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->perm, a->L, T, pot, ax, ay, az,
-           s);
+    ad_l2p_leaf(prec, p, basis, a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->pos32, a->perm, a->L,
+                T, pot, ax, ay, az, s);
     return 0;
 }
 
 int ad_run_p2p(AdState* a, int prec, int sms, double* pot, double* ax, double* ay, double* az, cudaStream_t s) {
     if (a->n == 0) return 0;
     cudaMemsetAsync(a->counter + 1, 0, 4, s);
-    ad_p2p(prec ? 1 : 0, a->nleaf, a->leaf, a->poff, a->psrc, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs,
-           a->perm, pot, ax, ay, az, a->counter + 1, 4 * sms, s);
+    if (prec)
+        ad_p2p32(a->nleaf, a->leaf, a->poff, a->psrc, a->nb, a->ne, a->ic, a->scale32, a->pos32, a->perm, pot, ax, ay,
+                 az, a->counter + 1, 4 * sms, s);
+    else
+        ad_p2p(a->nleaf, a->leaf, a->poff, a->psrc, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs, a->perm, pot,
+               ax, ay, az, a->counter + 1, 4 * sms, s);
     return 0;
 }
 

@@ -533,7 +533,7 @@ static double* Llev(fmm_plan* pl, int l) { return pl->Lbuf + pl->lvl_off[l]; }
 
 int fmm_p2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
-    if (pl->ad) { ad_run_p2m(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
+    if (pl->ad) { ad_run_p2m(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     const int d = pl->depth;
     launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, d, pl->nleaf, pl->start, pl->xs,
                     pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32);
@@ -543,7 +543,7 @@ int fmm_p2m(fmm_plan* pl, void* stream) {
 
 int fmm_m2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
-    if (pl->ad) { ad_run_m2m(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
+    if (pl->ad) { ad_run_m2m(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     if (pl->W32) {
         for (int l = pl->depth - 1; l >= 2; --l) {
             launch_shift32(pl->cfg.p, pl->cfg.basis, 1, l, pl->W32, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
@@ -608,7 +608,7 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
 
 int fmm_l2l(fmm_plan* pl, void* stream) {
     NEED_TREE();
-    if (pl->ad) { ad_run_l2l(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
+    if (pl->ad) { ad_run_l2l(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     if (pl->V32) {
         for (int l = 2; l < pl->depth; ++l) {
             launch_shift32(pl->cfg.p, pl->cfg.basis, 0, l, pl->V32, Llev(pl, l), (int64_t)1 << (3 * l),
@@ -629,7 +629,7 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
     NEED_TREE();
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
     if (pl->ad) {
-        ad_run_l2p(pl->ad, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], pot, ax, ay, az, S(stream));
+        ad_run_l2p(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], pot, ax, ay, az, S(stream));
         CKLAUNCH();
         return FMM_OK;
     }

@@ -612,8 +612,8 @@ def emit_list_file(p, basis, T):
          '#include "../fmm_device.cuh"', "namespace fmm {",
          "__global__ void __launch_bounds__(128)",
          "m2l_list_p%d_b%d_%s(int ntarg, const int* __restrict__ order, const int* __restrict__ off,"
-         " const int* __restrict__ src, const double* __restrict__ zc, const %s* __restrict__ Mn,"
-         " double* __restrict__ Ln, int* __restrict__ counter) {" % (p, basis, T, T),
+         " const int* __restrict__ src, const double* __restrict__ zc, const int4* __restrict__ ic, float scale,"
+         " const %s* __restrict__ Mn, double* __restrict__ Ln, int* __restrict__ counter) {" % (p, basis, T, T),
          "  typedef %s T;" % T,
          "  const int lane = threadIdx.x & 31;",
          "  for (;;) {",
@@ -623,13 +623,22 @@ def emit_list_file(p, basis, T):
          "    if (base >= ntarg) break;",
          "    const int w = base + lane;",
          "    if (w >= ntarg) continue;",
-         "    const int t = order[w];",
-         "    const double tx = zc[3 * t], ty = zc[3 * t + 1], tz = zc[3 * t + 2];"]
+         "    const int t = order[w];"]
+    if T == "double":
+        L.append("    const double tx = zc[3 * t], ty = zc[3 * t + 1], tz = zc[3 * t + 2];")
+    else:
+        # centre offsets from the integer node centres: exact integer
+        # difference, one FP32 rounding (no FP64 arithmetic per pair)
+        L.append("    const int4 it = ic[t];")
     for a in range(nc):
         L.append("    T a%d = T(0);" % a)
     L.append("    for (int k = off[t]; k < off[t + 1]; ++k) {")
     L.append("      const int s = src[k];")
-    L.append("      const T x = T(tx - zc[3 * s]), y = T(ty - zc[3 * s + 1]), z = T(tz - zc[3 * s + 2]);")
+    if T == "double":
+        L.append("      const T x = T(tx - zc[3 * s]), y = T(ty - zc[3 * s + 1]), z = T(tz - zc[3 * s + 2]);")
+    else:
+        L.append("      const int4 is = ic[s];")
+        L.append("      const T x = T(it.x - is.x) * scale, y = T(it.y - is.y) * scale, z = T(it.z - is.z) * scale;")
     L.append("      const T* __restrict__ Ms = Mn + (int64_t)s * %d;" % nc)
     L.append("      T d[%d];" % ns(p))
     L.append("  " + gen_dtensor(p).replace("\n", "\n  "))
@@ -661,10 +670,10 @@ def emit_list_file(p, basis, T):
     L.append("  }")
     L.append("}")
     L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
-             " const double* zc, const void* M, double* Ln, int* counter, int blocks, cudaStream_t s) {"
-             % (p, basis, T))
-    L.append("  m2l_list_p%d_b%d_%s<<<blocks, 128, 0, s>>>(ntarg, order, off, src, zc, (const %s*)M, Ln,"
-             " counter);" % (p, basis, T, T))
+             " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int* counter, int blocks,"
+             " cudaStream_t s) {" % (p, basis, T))
+    L.append("  m2l_list_p%d_b%d_%s<<<blocks, 128, 0, s>>>(ntarg, order, off, src, zc, ic, scale, (const %s*)M,"
+             " Ln, counter);" % (p, basis, T, T))
     L.append("  return 0;")
     L.append("}")
     L.append("}  // namespace fmm")
@@ -678,16 +687,16 @@ def emit_list_dispatch():
         for b in (0, 1):
             for T in ("float", "double"):
                 L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
-                         " const double* zc, const void* M, double* Ln, int* counter, int blocks, cudaStream_t s);"
-                         % (p, b, T))
+                         " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int* counter,"
+                         " int blocks, cudaStream_t s);" % (p, b, T))
     L.append("int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off,"
-             " const int* src, const double* zc, const void* M, double* Ln, int* counter, int blocks,"
-             " cudaStream_t s) {")
+             " const int* src, const double* zc, const int4* ic, float scale, const void* M, double* Ln,"
+             " int* counter, int blocks, cudaStream_t s) {")
     for p in range(PMAX + 1):
         for b in (0, 1):
             for k, T in ((0, "double"), (1, "float")):
                 L.append("  if (p == %d && basis == %d && prec == %d) return launch_m2l_list_p%d_b%d_%s(ntarg, order,"
-                         " off, src, zc, M, Ln, counter, blocks, s);" % (p, b, k, p, b, T))
+                         " off, src, zc, ic, scale, M, Ln, counter, blocks, s);" % (p, b, k, p, b, T))
     L.append("  return -1;")
     L.append("}")
     L.append("}  // namespace fmm")
