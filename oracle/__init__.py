@@ -20,7 +20,12 @@ is all in that C file, each routine citing the equation it restates:
 * ``fmm_uniform``  -- App. C on a uniform octree with the standard
                       (Chebyshev distance >= 2) separation criterion
 * ``fmm_adaptive`` -- App. C on an adaptive octree: MAC
-                      theta |z_A - z_B| > r_A + r_B, dual-tree traversal
+                      theta |z_A - z_B| > r_A + r_B, dual-tree traversal,
+                      optionally with one M2L order per pair
+* ``adaptive_pairs`` -- per-pair features and truncation-error labels for
+                      choosing each pair's order (an addition to the paper)
+* ``mlp``          -- the order-choosing MLP: forward, backward, Adam, BF16
+                      rounding, order selection (numpy, FP64)
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (closed forms, finite differences, identities,
@@ -76,6 +81,22 @@ def lib():
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i64p, _dp, _dp, _dp, _dp,
                                        _i64p]
         L.orc_fmm_adaptive.restype = ctypes.c_int
+        L.orc_fmm_adaptive_orders.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_int64, _i64p, _dp, _dp, _dp, _dp, _i64p]
+        L.orc_fmm_adaptive_orders.restype = ctypes.c_int
+        L.orc_adaptive_pairs.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]
+        L.orc_adaptive_pairs.restype = ctypes.c_int64
+        L.orc_ncols_features.restype = ctypes.c_int
+        L.orc_pair_error.argtypes = [ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int,
+                                     _dp, _dp, _dp]
+        L.orc_pair_error.restype = ctypes.c_double
+        L.orc_adaptive_tree.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_adaptive_tree.restype = ctypes.c_int64
+        L.orc_ncols_labels.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -230,11 +251,13 @@ def fmm_uniform(x, y, z, q, depth: int, p: int, basis: int, sample=None):
     return pot, np.stack([ax, ay, az])
 
 
-def fmm_adaptive(x, y, z, q, max_leaf: int, theta: float, p: int, basis: int, sample=None):
+def fmm_adaptive(x, y, z, q, max_leaf: int, theta: float, p: int, basis: int, sample=None, pair_orders=None):
     """Adaptive-octree FMM with the dual-tree traversal and MAC of App. C.
 
     Returns pot (n,), acc (3, n) and stats {nodes, m2l_pairs, p2p_pairs,
-    leaves}; with ``sample`` only those particles are evaluated."""
+    leaves}; with ``sample`` only those particles are evaluated.  With
+    ``pair_orders`` (one int per M2L pair, in the order of
+    ``adaptive_pairs``) each pair's M2L is truncated at its own order."""
     x, y, z, q = (_f64(v) for v in (x, y, z, q))
     n = len(x)
     if sample is None:
@@ -244,9 +267,71 @@ def fmm_adaptive(x, y, z, q, max_leaf: int, theta: float, p: int, basis: int, sa
         ns, sp, nout = len(sample), sample.ctypes.data_as(_i64p), len(sample)
     pot, ax, ay, az = (np.zeros(nout) for _ in range(4))
     st = np.zeros(5, dtype=np.int64)
-    rc = lib().orc_fmm_adaptive(n, _d(x), _d(y), _d(z), _d(q), max_leaf, float(theta), p, basis, ns, sp,
-                                _d(pot), _d(ax), _d(ay), _d(az), st.ctypes.data_as(_i64p))
+    if pair_orders is None:
+        po, npo = None, 0
+    else:
+        pair_orders = np.ascontiguousarray(pair_orders, dtype=np.int8)
+        po, npo = pair_orders.ctypes.data, len(pair_orders)
+    rc = lib().orc_fmm_adaptive_orders(n, _d(x), _d(y), _d(z), _d(q), max_leaf, float(theta), p, basis, po, npo,
+                                       ns, sp, _d(pot), _d(ax), _d(ay), _d(az), st.ctypes.data_as(_i64p))
     if rc != 0:
-        raise ValueError("orc_fmm_adaptive rejected its arguments")
+        raise ValueError("orc_fmm_adaptive rejected its arguments (%d)" % rc)
     keys = ("nodes", "m2l_pairs", "p2p_pairs", "leaves", "covered_pairs")
     return pot, np.stack([ax, ay, az]), dict(zip(keys, st.tolist()))
+
+
+NFEAT = 11      # features per M2L pair (see fmm_oracle.c)
+NLABEL = 9      # labels per pair: orders 2..10
+
+
+def adaptive_pairs(x, y, z, q, max_leaf: int, theta: float, features=True, labels=False):
+    """M2L pairs of the adaptive tree, ordered by (target, source).
+
+    Returns (target, source) node indices and, on request, the (npair, 11)
+    features and (npair, 9) labels (log10 relative force error of the
+    pair's M2L at orders 2..10) defined in fmm_oracle.c."""
+    x, y, z, q = (_f64(v) for v in (x, y, z, q))
+    n = len(x)
+    L = lib()
+    np_ = L.orc_adaptive_pairs(n, _d(x), _d(y), _d(z), _d(q), max_leaf, float(theta), 0, None, None, None, None)
+    if np_ < 0:
+        raise ValueError("orc_adaptive_pairs rejected its arguments")
+    tgt = np.zeros(np_, dtype=np.int64)
+    src = np.zeros(np_, dtype=np.int64)
+    feat = np.zeros((np_, NFEAT)) if features else None
+    lab = np.zeros((np_, NLABEL)) if labels else None
+    got = L.orc_adaptive_pairs(n, _d(x), _d(y), _d(z), _d(q), max_leaf, float(theta), np_, tgt.ctypes.data,
+                               src.ctypes.data, feat.ctypes.data if features else None,
+                               lab.ctypes.data if labels else None)
+    assert got == np_
+    return tgt, src, feat, lab
+
+
+def pair_error(p, src_xyzq, zA, zB, targets):
+    """Relative force error of the order-p M2L + L2P of the source particles
+    (P2M about zA) at the target points (<= 64) against their exact field."""
+    xa, ya, za, qa = (_f64(v) for v in src_xyzq)
+    t = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(-1, 3).T)
+    zA, zB = _f64(zA), _f64(zB)
+    tx, ty, tz = (np.ascontiguousarray(t[k]) for k in range(3))
+    e = lib().orc_pair_error(p, len(xa), _d(xa), _d(ya), _d(za), _d(qa), _d(zA), _d(zB), t.shape[1], _d(tx),
+                             _d(ty), _d(tz))
+    if e < 0:
+        raise ValueError("orc_pair_error rejected its arguments")
+    return e
+
+
+def adaptive_tree(x, y, z, max_leaf: int):
+    """Nodes of the adaptive octree: (nn, 4) centre and radius, (nn, 2)
+    sorted-position ranges, and the sorted order of the particles."""
+    x, y, z = (_f64(v) for v in (x, y, z))
+    n = len(x)
+    L = lib()
+    nn = L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, 0, None, None, None)
+    zr = np.zeros((nn, 4))
+    rg = np.zeros((nn, 2), dtype=np.int64)
+    order = np.zeros(n, dtype=np.int64)
+    got = L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, nn, zr.ctypes.data, rg.ctypes.data,
+                              order.ctypes.data)
+    assert got == nn
+    return zr, rg, order

@@ -710,13 +710,31 @@ static double dist3(const double* a, const double* b) {
     return sqrt(dx * dx + dy * dy + dz * dz);
 }
 
-int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* z, const double* q,
-                     int max_leaf, double theta, int p, int basis, int64_t nsample, const int64_t* sample,
-                     double* pot, double* ax, double* ay, double* az, int64_t* stats /* [5] or NULL */) {
-    orc_init();
-    if (p < 0 || p > ORC_PMAX || max_leaf < 1 || theta < 0.0 || n < 0) return -1;
-    int64_t ntarg = nsample >= 0 ? nsample : n;
-    if (n == 0) return 0;
+static int pair_cmp(const void* a, const void* b) {
+    const pair_t* p = (const pair_t*)a;
+    const pair_t* q = (const pair_t*)b;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    return p->b < q->b ? -1 : (p->b > q->b);
+}
+
+typedef struct {
+    int64_t n, nn;
+    kv_t* kv;        /* particles sorted by (key, index) */
+    anode_t* nd;     /* nodes, level by level (parents before children) */
+    plist_t m2l;     /* (target, source), sorted by target then source */
+    plist_t p2p;     /* (target leaf, source leaf), traversal order */
+} atree_t;
+
+static void atree_free(atree_t* T) {
+    free(T->kv); free(T->nd); free(T->m2l.v); free(T->p2p.v);
+    memset(T, 0, sizeof(*T));
+}
+
+/* Octree, geometry and interaction lists as described above (n > 0). */
+static void atree_build(atree_t* T, int64_t n, const double* x, const double* y, const double* z, int max_leaf,
+                        double theta) {
+    memset(T, 0, sizeof(*T));
+    T->n = n;
     /* bounding cube */
     double lo[3] = {x[0], y[0], z[0]}, hi[3] = {x[0], y[0], z[0]};
     for (int64_t i = 0; i < n; ++i) {
@@ -823,15 +841,71 @@ int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* 
         }
         plist_t t = qa; qa = qb; qb = t;
     }
+    free(qa.v); free(qb.v);
+    if (m2l.n > 1) qsort(m2l.v, m2l.n, sizeof(pair_t), pair_cmp);
+    T->nn = nn; T->kv = kv; T->nd = nd; T->m2l = m2l; T->p2p = p2p;
+}
+
+/* Upward pass: P2M at the leaves (Eq. P2M), M2M to the root (Eq. M2M). */
+static void atree_multipoles(const atree_t* T, const double* x, const double* y, const double* z, const double* q,
+                             int p, int basis, double* M) {
+    const int nc = orc_ncoef(p, basis);
+    const anode_t* nd = T->nd;
+    const kv_t* kv = T->kv;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t c = 0; c < T->nn; ++c) {
+        if (nd[c].nchild) continue;
+        const int64_t cnt = nd[c].e - nd[c].b;
+        double* buf = (double*)malloc(sizeof(double) * 4 * cnt);
+        for (int64_t a = 0; a < cnt; ++a) {
+            const int64_t i = kv[nd[c].b + a].idx;
+            buf[a] = x[i]; buf[cnt + a] = y[i]; buf[2 * cnt + a] = z[i]; buf[3 * cnt + a] = q[i];
+        }
+        orc_p2m(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, buf + 3 * cnt, nd[c].z, M + c * nc);
+        free(buf);
+    }
+    for (int64_t c = T->nn - 1; c >= 0; --c) {   /* children follow parents: reverse order is bottom-up */
+        if (!nd[c].nchild) continue;
+        for (int k = 0; k < nd[c].nchild; ++k) {
+            const int64_t ch = nd[c].child0 + k;
+            double d[3] = {nd[ch].z[0] - nd[c].z[0], nd[ch].z[1] - nd[c].z[1], nd[ch].z[2] - nd[c].z[2]};
+            orc_m2m(p, basis, M + ch * nc, d, M + c * nc);
+        }
+    }
+}
+
+/* Adaptive FMM.  pair_p (optional, npair_p entries) gives each M2L pair its
+ * own truncation order 0 <= p_k <= p, in the order of orc_adaptive_pairs
+ * (target, then source): the pair contributes the terms |n| + |m| <= p_k of
+ * Eq. M2L (ranks 0..p_k of the stored expansions, which are prefixes of the
+ * order-p storage).  Every other operator runs at order p. */
+int orc_fmm_adaptive_orders(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                            int max_leaf, double theta, int p, int basis, const signed char* pair_p,
+                            int64_t npair_p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
+                            double* ay, double* az, int64_t* stats /* [5] or NULL */) {
+    orc_init();
+    if (p < 0 || p > ORC_PMAX || max_leaf < 1 || theta < 0.0 || n < 0) return -1;
+    int64_t ntarg = nsample >= 0 ? nsample : n;
+    if (n == 0) return 0;
+    atree_t T;
+    atree_build(&T, n, x, y, z, max_leaf, theta);
+    const int64_t nn = T.nn;
+    const anode_t* nd = T.nd;
+    const kv_t* kv = T.kv;
+    if (pair_p) {
+        if (npair_p != T.m2l.n) { atree_free(&T); return -2; }
+        for (int64_t k = 0; k < npair_p; ++k)
+            if (pair_p[k] < 0 || pair_p[k] > p) { atree_free(&T); return -1; }
+    }
     if (stats) {
         /* stats: nodes, M2L pairs, P2P pairs, leaves, and the number of ordered
            particle pairs the lists cover (n^2 when every pair is covered once) */
-        stats[0] = nn; stats[1] = m2l.n; stats[2] = p2p.n; stats[3] = 0; stats[4] = 0;
+        stats[0] = nn; stats[1] = T.m2l.n; stats[2] = T.p2p.n; stats[3] = 0; stats[4] = 0;
         for (int64_t c = 0; c < nn; ++c) stats[3] += nd[c].nchild == 0;
-        for (int64_t k = 0; k < m2l.n; ++k)
-            stats[4] += (nd[m2l.v[k].a].e - nd[m2l.v[k].a].b) * (nd[m2l.v[k].b].e - nd[m2l.v[k].b].b);
-        for (int64_t k = 0; k < p2p.n; ++k)
-            stats[4] += (nd[p2p.v[k].a].e - nd[p2p.v[k].a].b) * (nd[p2p.v[k].b].e - nd[p2p.v[k].b].b);
+        for (int64_t k = 0; k < T.m2l.n; ++k)
+            stats[4] += (nd[T.m2l.v[k].a].e - nd[T.m2l.v[k].a].b) * (nd[T.m2l.v[k].b].e - nd[T.m2l.v[k].b].b);
+        for (int64_t k = 0; k < T.p2p.n; ++k)
+            stats[4] += (nd[T.p2p.v[k].a].e - nd[T.p2p.v[k].a].b) * (nd[T.p2p.v[k].b].e - nd[T.p2p.v[k].b].b);
     }
     /* which nodes feed sampled targets */
     int64_t* pos_of = (int64_t*)malloc(sizeof(int64_t) * n);   /* sorted position of particle */
@@ -849,45 +923,30 @@ int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* 
     const int nc = orc_ncoef(p, basis);
     double* M = (double*)calloc((size_t)nn * nc, sizeof(double));
     double* L = (double*)calloc((size_t)nn * nc, sizeof(double));
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t c = 0; c < nn; ++c) {
-        if (nd[c].nchild) continue;
-        const int64_t cnt = nd[c].e - nd[c].b;
-        double* buf = (double*)malloc(sizeof(double) * 4 * cnt);
-        for (int64_t a = 0; a < cnt; ++a) {
-            const int64_t i = kv[nd[c].b + a].idx;
-            buf[a] = x[i]; buf[cnt + a] = y[i]; buf[2 * cnt + a] = z[i]; buf[3 * cnt + a] = q[i];
-        }
-        orc_p2m(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, buf + 3 * cnt, nd[c].z, M + c * nc);
-        free(buf);
-    }
-    for (int64_t c = nn - 1; c >= 0; --c) {   /* children precede nothing: reverse order is bottom-up */
-        if (!nd[c].nchild) continue;
-        for (int k = 0; k < nd[c].nchild; ++k) {
-            const int64_t ch = nd[c].child0 + k;
-            double d[3] = {nd[ch].z[0] - nd[c].z[0], nd[ch].z[1] - nd[c].z[1], nd[ch].z[2] - nd[c].z[2]};
-            orc_m2m(p, basis, M + ch * nc, d, M + c * nc);
-        }
-    }
-    /* interaction phase, grouped by target for the parallel loop */
+    atree_multipoles(&T, x, y, z, q, p, basis, M);
+    /* interaction phase: the sorted M2L list is already grouped by target */
     int64_t* cnt = (int64_t*)calloc(nn + 1, sizeof(int64_t));
-    for (int64_t k = 0; k < m2l.n; ++k) cnt[m2l.v[k].a + 1]++;
+    for (int64_t k = 0; k < T.m2l.n; ++k) cnt[T.m2l.v[k].a + 1]++;
     for (int64_t c = 0; c < nn; ++c) cnt[c + 1] += cnt[c];
-    int64_t* src = (int64_t*)malloc(sizeof(int64_t) * (m2l.n > 0 ? m2l.n : 1));
-    {
-        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nn + 1));
-        memcpy(fill, cnt, sizeof(int64_t) * (nn + 1));
-        for (int64_t k = 0; k < m2l.n; ++k) src[fill[m2l.v[k].a]++] = m2l.v[k].b;
-        free(fill);
-    }
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t c = 0; c < nn; ++c) {
         if (!need[c]) continue;
+        double* Lk = (double*)malloc(sizeof(double) * nc);
         for (int64_t k = cnt[c]; k < cnt[c + 1]; ++k) {
-            const int64_t s = src[k];
+            const int64_t s = T.m2l.v[k].b;
             double r[3] = {nd[c].z[0] - nd[s].z[0], nd[c].z[1] - nd[s].z[1], nd[c].z[2] - nd[s].z[2]};
-            orc_m2l(p, basis, M + s * nc, r, L + c * nc);
+            if (!pair_p) {
+                orc_m2l(p, basis, M + s * nc, r, L + c * nc);
+            } else {
+                /* order p_k on the rank prefix, added into the order-p L */
+                const int pk = pair_p[k];
+                const int nck = orc_ncoef(pk, basis);
+                memset(Lk, 0, sizeof(double) * nc);
+                orc_m2l(pk, basis, M + s * nc, r, Lk);
+                for (int t = 0; t < nck; ++t) L[c * nc + t] += Lk[t];
+            }
         }
+        free(Lk);
     }
     for (int64_t c = 0; c < nn; ++c) {   /* parents precede children: forward order is top-down */
         if (!nd[c].nchild || !need[c]) continue;
@@ -900,13 +959,13 @@ int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* 
     }
     /* near-field lists by target leaf */
     int64_t* pc = (int64_t*)calloc(nn + 1, sizeof(int64_t));
-    for (int64_t k = 0; k < p2p.n; ++k) pc[p2p.v[k].a + 1]++;
+    for (int64_t k = 0; k < T.p2p.n; ++k) pc[T.p2p.v[k].a + 1]++;
     for (int64_t c = 0; c < nn; ++c) pc[c + 1] += pc[c];
-    int64_t* psrc = (int64_t*)malloc(sizeof(int64_t) * (p2p.n > 0 ? p2p.n : 1));
+    int64_t* psrc = (int64_t*)malloc(sizeof(int64_t) * (T.p2p.n > 0 ? T.p2p.n : 1));
     {
         int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nn + 1));
         memcpy(fill, pc, sizeof(int64_t) * (nn + 1));
-        for (int64_t k = 0; k < p2p.n; ++k) psrc[fill[p2p.v[k].a]++] = p2p.v[k].b;
+        for (int64_t k = 0; k < T.p2p.n; ++k) psrc[fill[T.p2p.v[k].a]++] = T.p2p.v[k].b;
         free(fill);
     }
 #pragma omp parallel for schedule(dynamic, 64)
@@ -931,7 +990,206 @@ int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* 
         }
         pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
     }
-    free(kv); free(nd); free(qa.v); free(qb.v); free(m2l.v); free(p2p.v);
-    free(pos_of); free(leaf_of); free(need); free(M); free(L); free(cnt); free(src); free(pc); free(psrc);
+    atree_free(&T);
+    free(pos_of); free(leaf_of); free(need); free(M); free(L); free(cnt); free(pc); free(psrc);
     return 0;
+}
+
+int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                     int max_leaf, double theta, int p, int basis, int64_t nsample, const int64_t* sample,
+                     double* pot, double* ax, double* ay, double* az, int64_t* stats /* [5] or NULL */) {
+    return orc_fmm_adaptive_orders(n, x, y, z, q, max_leaf, theta, p, basis, NULL, 0, nsample, sample, pot, ax,
+                                   ay, az, stats);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-pair data for choosing the M2L order of each pair (learned order;      */
+/* the paper fixes one p per run, so everything below is an addition on top  */
+/* of its operators, each quantity written out from its definition).         */
+/*                                                                            */
+/* Pairs come in the order (target, then source).  For a pair with source A,  */
+/* target B, offset d = z_B - z_A, radii r_A, r_B, particle counts n_A, n_B   */
+/* and full symmetric multipoles (Eq. P2M/M2M, any order >= 4):               */
+/*   a = max(r_A/|d|, 1e-6),  b = max(r_B/|d|, 1e-6)                          */
+/*   f0 = ln(a + b)   (the MAC ratio of App. C)                               */
+/*   f1 = ln a,  f2 = ln b                                                    */
+/*   f3..f6 = ln max(|M_A^(j)| / (|M_A,0| r_A^j), 1e-6),  j = 1..4            */
+/*   f7..f8 = the same for the target's own multipole M_B, j = 1..2           */
+/*   f9 = ln n_A,  f10 = ln n_B                                               */
+/* where |M^(j)|^2 = sum_{|m|=j} j!/m! M_m^2 is the Frobenius norm of the     */
+/* rank-j symmetric tensor (a ratio with a zero denominator counts as 0).     */
+/*                                                                            */
+/* Label of the pair at order p (p = 2..10): the relative error of the force  */
+/* the pair's order-p M2L (followed by L2P at order p) produces at target     */
+/* particles y_j of B, against the direct sum g over A's particles:           */
+/*   e_p = sqrt(sum_j |g_p(y_j) - g(y_j)|^2 / sum_j |g(y_j)|^2),              */
+/*   label_p = log10(max(e_p, 1e-12)).                                        */
+/* The y_j are all of B's particles when n_B <= 64, else the 64 at sorted     */
+/* positions b_B + floor(j n_B / 64), j = 0..63.                              */
+/* The source multipole is the order-10 one, so every p <= 10 reads its rank  */
+/* prefix.                                                                    */
+/* ------------------------------------------------------------------------ */
+#define ORC_NF 11
+#define ORC_NLAB 9
+
+static double rank_norm(const double* M, int j) {
+    /* Frobenius norm of the rank-j block of a full symmetric polytensor */
+    const int off = orc_ncoef_sym(j - 1);
+    double s = 0.0;
+    for (int t = 0; t < (j + 1) * (j + 2) / 2; ++t) {
+        const int* n = g_sym[off + t];
+        const double mult = g_fact[j] / mfact(n[0], n[1], n[2]);
+        s += mult * M[off + t] * M[off + t];
+    }
+    return sqrt(s);
+}
+
+static double shape_feature(const double* M, int j, double r) {
+    const double m0 = fabs(M[0]);
+    double g = 0.0;
+    if (m0 > 0.0 && r > 0.0) g = rank_norm(M, j) / (m0 * ipow(r, j));
+    return log(g > 1e-6 ? g : 1e-6);
+}
+
+/* Relative force error at the points (xt, yt, zt) of the order-p M2L of a
+ * source multipole M (full symmetric, order >= p, about zA) towards zB,
+ * followed by L2P at order p, against the exact field g of the given source
+ * particles (the definition of the label above, for one p). */
+static double pair_error(int p, const double* M, const double zA[3], const double zB[3], int nt,
+                         const double (*yv)[3], const double (*g)[3], double* Lp /* ncoef_sym(p) */) {
+    const double d[3] = {zB[0] - zA[0], zB[1] - zA[1], zB[2] - zA[2]};
+    memset(Lp, 0, sizeof(double) * orc_ncoef_sym(p));
+    orc_m2l(p, 0, M, d, Lp);
+    double num = 0.0, den = 0.0;
+    for (int j = 0; j < nt; ++j) {
+        const double rb[3] = {yv[j][0] - zB[0], yv[j][1] - zB[1], yv[j][2] - zB[2]};
+        double o[4];
+        orc_l2p(p, 0, Lp, rb, o);
+        for (int c = 0; c < 3; ++c) {
+            num += (o[1 + c] - g[j][c]) * (o[1 + c] - g[j][c]);
+            den += g[j][c] * g[j][c];
+        }
+    }
+    return den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+/* The same from source particles (P2M about zA at order p) and up to 64
+ * target points; used to check the per-pair labels. */
+double orc_pair_error(int p, int64_t na, const double* xa, const double* ya, const double* za, const double* qa,
+                      const double zA[3], const double zB[3], int nt, const double* xt, const double* yt,
+                      const double* zt) {
+    orc_init();
+    if (p < 0 || p > ORC_PMAX || nt < 1 || nt > 64) return -1.0;
+    const int nc = orc_ncoef_sym(p);
+    double* M = (double*)calloc(nc, sizeof(double));
+    double* Lp = (double*)malloc(sizeof(double) * nc);
+    double yv[64][3], g[64][3];
+    orc_p2m(p, 0, na, xa, ya, za, qa, zA, M);
+    for (int j = 0; j < nt; ++j) {
+        yv[j][0] = xt[j]; yv[j][1] = yt[j]; yv[j][2] = zt[j];
+        g[j][0] = g[j][1] = g[j][2] = 0.0;
+        for (int64_t i = 0; i < na; ++i) {
+            const double dx = xa[i] - yv[j][0], dy = ya[i] - yv[j][1], dz = za[i] - yv[j][2];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
+            g[j][0] += qa[i] * dx * ir3; g[j][1] += qa[i] * dy * ir3; g[j][2] += qa[i] * dz * ir3;
+        }
+    }
+    const double e = pair_error(p, M, zA, zB, nt, (const double (*)[3])yv, (const double (*)[3])g, Lp);
+    free(M); free(Lp);
+    return e;
+}
+
+/* The adaptive tree itself: per node (centre x, y, z, radius) and the range
+ * [b, e) of sorted positions it holds; order[a] = the particle at sorted
+ * position a.  Returns the node count (arrays written when cap allows). */
+int64_t orc_adaptive_tree(int64_t n, const double* x, const double* y, const double* z, int max_leaf, int64_t cap,
+                          double* zr, int64_t* range, int64_t* order) {
+    orc_init();
+    if (max_leaf < 1 || n < 1) return -1;
+    atree_t T;
+    atree_build(&T, n, x, y, z, max_leaf, 0.0);
+    const int64_t nn = T.nn;
+    if (cap >= nn) {
+        for (int64_t c = 0; c < nn; ++c) {
+            if (zr) { zr[4 * c] = T.nd[c].z[0]; zr[4 * c + 1] = T.nd[c].z[1]; zr[4 * c + 2] = T.nd[c].z[2];
+                      zr[4 * c + 3] = T.nd[c].r; }
+            if (range) { range[2 * c] = T.nd[c].b; range[2 * c + 1] = T.nd[c].e; }
+        }
+        if (order) for (int64_t a = 0; a < n; ++a) order[a] = T.kv[a].idx;
+    }
+    atree_free(&T);
+    return nn;
+}
+
+int orc_ncols_features(void) { return ORC_NF; }
+int orc_ncols_labels(void) { return ORC_NLAB; }
+
+int64_t orc_adaptive_pairs(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                           int max_leaf, double theta, int64_t cap, int64_t* tgt, int64_t* src, double* feat,
+                           double* lab) {
+    orc_init();
+    if (max_leaf < 1 || theta < 0.0 || n < 0) return -1;
+    if (n == 0) return 0;
+    atree_t T;
+    atree_build(&T, n, x, y, z, max_leaf, theta);
+    const int64_t np = T.m2l.n;
+    if (cap < np || (!tgt && !src && !feat && !lab)) { atree_free(&T); return np; }
+    const anode_t* nd = T.nd;
+    const kv_t* kv = T.kv;
+    const int P = 10, nc = orc_ncoef_sym(P);
+    double* M = NULL;
+    if (feat || lab) {
+        M = (double*)calloc((size_t)T.nn * nc, sizeof(double));
+        atree_multipoles(&T, x, y, z, q, P, 0, M);
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < np; ++k) {
+        const int64_t B = T.m2l.v[k].a, A = T.m2l.v[k].b;
+        if (tgt) tgt[k] = B;
+        if (src) src[k] = A;
+        const double d[3] = {nd[B].z[0] - nd[A].z[0], nd[B].z[1] - nd[A].z[1], nd[B].z[2] - nd[A].z[2]};
+        const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (feat) {
+            double* f = feat + k * ORC_NF;
+            double a = nd[A].r / dn, b = nd[B].r / dn;
+            if (a < 1e-6) a = 1e-6;
+            if (b < 1e-6) b = 1e-6;
+            f[0] = log(a + b);
+            f[1] = log(a);
+            f[2] = log(b);
+            for (int j = 1; j <= 4; ++j) f[2 + j] = shape_feature(M + A * nc, j, nd[A].r);
+            for (int j = 1; j <= 2; ++j) f[6 + j] = shape_feature(M + B * nc, j, nd[B].r);
+            f[9] = log((double)(nd[A].e - nd[A].b));
+            f[10] = log((double)(nd[B].e - nd[B].b));
+        }
+        if (lab) {
+            const int64_t nB = nd[B].e - nd[B].b;
+            const int ny = nB <= 64 ? (int)nB : 64;
+            double yv[64][3], g[64][3];
+            for (int j = 0; j < ny; ++j) {
+                const int64_t sp = nd[B].b + (nB <= 64 ? j : (int64_t)j * nB / 64);
+                const int64_t t = kv[sp].idx;
+                yv[j][0] = x[t]; yv[j][1] = y[t]; yv[j][2] = z[t];
+                g[j][0] = g[j][1] = g[j][2] = 0.0;
+                for (int64_t s = nd[A].b; s < nd[A].e; ++s) {
+                    const int64_t i = kv[s].idx;
+                    const double dx = x[i] - yv[j][0], dy = y[i] - yv[j][1], dz = z[i] - yv[j][2];
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    const double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
+                    g[j][0] += q[i] * dx * ir3; g[j][1] += q[i] * dy * ir3; g[j][2] += q[i] * dz * ir3;
+                }
+            }
+            double* Lp = (double*)malloc(sizeof(double) * nc);
+            for (int p = 2; p <= P; ++p) {
+                const double e = pair_error(p, M + A * nc, nd[A].z, nd[B].z, ny, (const double (*)[3])yv,
+                                            (const double (*)[3])g, Lp);
+                lab[k * ORC_NLAB + (p - 2)] = log10(e > 1e-12 ? e : 1e-12);
+            }
+            free(Lp);
+        }
+    }
+    free(M);
+    atree_free(&T);
+    return np;
 }
