@@ -61,8 +61,10 @@ typedef enum { FMM_BASIS_SYM = 0, FMM_BASIS_TRACELESS = 1 } fmm_basis;
 
 typedef enum {
     FMM_FP64 = 0,        /* every operator in FP64                                     */
-    FMM_FP32 = 1,        /* P2M, M2L, L2P, P2P arithmetic in FP32; D-tensors, M2M, L2L
-                            and every stored expansion in FP64                           */
+    FMM_FP32 = 1,        /* operator arithmetic in FP32 (uniform trees: P2M, M2L, L2P,
+                            P2P and, for p <= 8, M2M and L2L; adaptive trees: every
+                            operator); tree geometry, D-tensor tables and every stored
+                            expansion in FP64                                            */
     FMM_GEMM_TF32X3 = 2, /* M2L as offset-grouped tensor-core GEMMs, TF32 hi/lo, 3 passes */
     FMM_GEMM_BF16X3 = 3  /* M2L as offset-grouped tensor-core GEMMs, BF16 hi/lo, 3 passes */
 } fmm_precision;
@@ -78,8 +80,13 @@ typedef struct {
     int depth;             /* uniform octree depth (leaves = 8^depth), 0..10           */
     int max_leaf;          /* adaptive trees: maximum particles per leaf               */
     double theta;          /* adaptive trees: opening parameter of the MAC (App. C)    */
-    int learned_p;         /* reserved: per-interaction order selection                */
-    double target_rel_err; /* reserved: target relative force error                    */
+    int learned_p;         /* adaptive trees, FMM_BASIS_SYM, 4 <= p <= 10: 1 gives every
+                              M2L pair its own order in 0..p (chosen by the model set
+                              with fmm_set_mlp, or given by fmm_set_pair_orders); p is
+                              the order of every other operator and of the storage   */
+    double target_rel_err; /* learned_p: the model picks, per pair, the lowest order
+                              whose predicted relative force error is at most
+                              target_rel_err * kappa (kappa stored with the model)    */
     int use_graph;         /* 1 (adaptive trees, non-default stream): after the first
                               evaluation, capture the operator sequence P2M..P2P into
                               a CUDA graph and replay it while the tree keeps its
@@ -245,15 +252,88 @@ int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, const double* x
                          double* az, void* stream);
 
 /* Sizes of the plan's tree and lists after fmm_build_tree, written to
- * out[0..min(nout,8)): number of cells, leaves, M2L pairs, P2P (leaf) pairs,
+ * out[0..min(nout,19)): number of cells, leaves, M2L pairs, P2P (leaf) pairs,
  * M2L target cells, autotuned M2L blocks per SM (0 before the first M2L),
- * tree levels, and 1 when a captured operator graph is held.  For uniform
- * trees the list entries are 0 (the lists are implicit). */
+ * tree levels, 1 when a captured operator graph is held, then (learned_p
+ * plans, after an M2L) the number of M2L pairs at each order 0..10.  For
+ * uniform trees the list entries are 0 (the lists are implicit). */
 int fmm_plan_stats(const fmm_plan* plan, int64_t* out, int nout);
 
 /* Number of kernels this library launched since it was loaded (all plans and
  * operator calls), counted on the host at each launch. */
 int64_t fmm_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------
+ * Learned per-pair M2L order.  The paper fixes one order p per run; these
+ * calls add a model that picks an order for every M2L pair of an adaptive
+ * tree from 11 features of the pair, so that pairs far inside the MAC use
+ * fewer terms of Eq. M2L than pairs near its boundary.
+ *
+ * Features of a pair (source A, target B, d = z_B - z_A, radii r, particle
+ * counts n, full symmetric multipoles M):
+ *   a = max(r_A/|d|, 1e-6), b = max(r_B/|d|, 1e-6); f0 = ln(a+b) (the MAC
+ *   ratio, App. C), f1 = ln a, f2 = ln b; f3..f6 = ln max(|M_A^(j)| /
+ *   (|M_A,0| r_A^j), 1e-6) for j = 1..4 with |M^(j)|^2 = sum_{|m|=j} j!/m!
+ *   M_m^2; f7, f8 = the same for M_B, j = 1, 2; f9 = ln n_A; f10 = ln n_B.
+ * Label of a pair at order q (q = 2..10): log10 max(e_q, 1e-12), e_q the
+ * relative force error of the pair's order-q M2L + L2P (Eqs. M2L, L2P) at
+ * up to 64 particles of B (all when n_B <= 64, else sorted positions
+ * b_B + floor(j n_B / 64)) against the direct sum over A's particles.
+ *
+ * Model: 11 -> 64 -> 64 -> 64 -> 9, ReLU; predicted log10 error at orders
+ * 2..10.  Parameter blob (FMM_MLP_NBLOB floats): [0..8) header {6332, 1,
+ * 11, 64, 9, 2, log10 kappa, 0}, [8..19) feature means, [19..30) feature
+ * standard deviations, then W1 (64x11 row-major), b1, W2 (64x64), b2, W3,
+ * b3, W4 (9x64), b4.  Inference rounds weights and the input of every layer
+ * to BF16 (nearest even) and accumulates in FP32 on the tensor cores.
+ * ------------------------------------------------------------------------- */
+#define FMM_MLP_NF 11
+#define FMM_MLP_NOUT 9
+#define FMM_MLP_NBLOB 9703
+
+/* M2L pair list of an adaptive plan after fmm_build_tree, grouped by target
+ * (the order every per-pair array below uses): host arrays tgt[k], src[k]
+ * (node indices; nodes are numbered level by level, children in octant
+ * order).  *count receives the number of pairs; nothing is written when cap
+ * is smaller.  Synchronous. */
+int fmm_plan_pairs(fmm_plan* plan, int32_t* tgt, int32_t* src, int64_t cap, int64_t* count);
+
+/* Features (device float [npair][FMM_MLP_NF]) and, when labels != NULL,
+ * labels (device double [npair][FMM_MLP_NOUT]) of the plan's M2L pairs.
+ * Runs P2M and M2M itself.  Labels need FMM_FP64, FMM_BASIS_SYM and p = 10;
+ * features need p >= 4 and FMM_BASIS_SYM.  FMM_ERR_STATE before
+ * fmm_build_tree. */
+int fmm_pair_data(fmm_plan* plan, float* feat, double* labels, void* stream);
+
+/* Mean squared error of the model over n samples (device feat [n][11],
+ * labels [n][9], FP32) and its gradient with respect to blob[30..)
+ * (host grad, FMM_MLP_NBLOB - 30 floats), in FP32.  Synchronous. */
+int fmm_mlp_grad(const float* blob, int64_t n, const float* feat, const float* labels, float* loss,
+                 float* grad, void* stream);
+
+/* Trains the model in FP32 with Adam (beta1 0.9, beta2 0.999, eps 1e-8):
+ * epochs passes over the samples in the order of `order` (device int32
+ * permutation of 0..n-1, supplied by the caller), minibatches of `batch`,
+ * learning rate lr.  blob (host, FMM_MLP_NBLOB floats) holds the initial
+ * parameters and receives the trained ones; with fit_moments != 0 the
+ * feature means and deviations are first set from the data.  loss_out
+ * (host, epochs floats, may be NULL) receives each epoch's mean batch loss.
+ * Allocates and frees its own scratch.  Synchronous. */
+int fmm_mlp_train(float* blob, int64_t n, const float* feat, const float* labels, const int32_t* order,
+                  int epochs, int batch, float lr, int fit_moments, float* loss_out, void* stream);
+
+/* BF16 tensor-core inference: pred (device float [n][9]) from feat (device
+ * float [n][11]).  blob is host memory. */
+int fmm_mlp_predict(const float* blob, int64_t n, const float* feat, float* pred, void* stream);
+
+/* Gives a learned_p plan its model (host blob, copied).  Synchronous. */
+int fmm_set_mlp(fmm_plan* plan, const float* blob, int64_t nblob);
+
+/* Gives every M2L pair of the current tree its order (host int8, n entries
+ * in the order of fmm_plan_pairs, each in 0..p) instead of the model; NULL
+ * returns to the model.  The orders stay in force while later builds keep
+ * the same number of pairs.  Synchronous. */
+int fmm_set_pair_orders(fmm_plan* plan, const int8_t* orders, int64_t n);
 
 #ifdef __cplusplus
 }

@@ -328,12 +328,17 @@ __global__ void k_pair_keys(int n, const int2* __restrict__ pr, uint64_t* __rest
     key[k] = (uint64_t)pr[k].x;
     val[k] = k;
 }
+// sorted pairs -> CSR sources and per-target counts; a count is the segment
+// end minus the segment start, so only the two boundary threads of each
+// target's segment touch its counter (no same-address atomic chains)
 __global__ void k_pair_csr(int n, const uint64_t* __restrict__ key, const int* __restrict__ val,
                            const int2* __restrict__ pr, int* __restrict__ src, int* __restrict__ cnt) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     src[k] = pr[val[k]].y;
-    atomicAdd(&cnt[(int)key[k]], 1);
+    const uint64_t t = key[k];
+    if (k == 0 || key[k - 1] != t) atomicAdd(&cnt[(int)t], -k);
+    if (k == n - 1 || key[k + 1] != t) atomicAdd(&cnt[(int)t], k + 1);
 }
 
 // M2L work order: targets with non-empty lists, longest lists first

@@ -42,6 +42,16 @@ struct AdState {
            cap_cp = 0, cap_cq = 0, cap_om = 0, cap_op = 0, cap_oq = 0, cap_m2l = 0, cap_p2p = 0, cap_moff = 0,
            cap_msrc = 0, cap_poff = 0, cap_psrc = 0, cap_order = 0, cap_leaf = 0, cap_ic = 0, cap_pos32 = 0,
            cap_M = 0, cap_L = 0, cap_M32 = 0, cap_counter = 0;
+    // learned per-pair M2L order (fmm_learn.cu, fmm_mlp_tc.cu)
+    int* ptgt = nullptr;           // M2L pair -> target node
+    float* nodeF = nullptr;        // per node: shape terms 1..4, ln count, radius, 0, 0
+    signed char* porder = nullptr; // order of each M2L pair
+    int* iota = nullptr;           // 0..nn-1: target order of the per-order M2L launches
+    int *bcnt = nullptr, *boff = nullptr, *bsrc = nullptr;   // pairs grouped by (order, target)
+    size_t cap_ptgt = 0, cap_nodeF = 0, cap_porder = 0, cap_iota = 0, cap_bcnt = 0, cap_boff = 0, cap_bsrc = 0;
+    bool orders_fixed = false;     // orders given by the caller instead of the model
+    int64_t n_orders = 0;
+    unsigned gen = 0;              // bumped whenever a buffer moves
     // autotuned persistent grid of the M2L kernel
     int m2l_blocks = 0, m2l_blocks_per_sm = 0;
     float m2l_tuned_ms = 0.f;
@@ -61,6 +71,14 @@ int ad_run_l2l(AdState* a, int prec, int p, int basis, const DevTables& T, cudaS
 int ad_run_l2p(AdState* a, int prec, int p, int basis, const DevTables& T, double* pot, double* ax, double* ay, double* az,
                cudaStream_t s);
 int ad_run_p2p(AdState* a, int prec, int sms, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+int ad_learn_prepare(AdState* a, cudaStream_t s);
+int ad_run_m2l_orders(AdState* a, int p, int basis, int prec, int sms, const unsigned char* mlp, float thr, int* err,
+                      cudaStream_t s);
+int ad_order_counts(AdState* a, int p, int64_t* out, cudaStream_t s);
+int ad_order_keys(int n, const signed char* porder, uint64_t* key, int* val, cudaStream_t s);
+int ad_bucket_csr(int n, int nn, const uint64_t* key, const int* val, const int* ptgt, const int* msrc, int* bsrc,
+                  int* bcnt, cudaStream_t s);
+int ad_iota(int n, int* a, cudaStream_t s);
 
 // fmm_adaptive.cu
 void radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,
@@ -97,8 +115,8 @@ int ad_p2p(int nwork, const int* work, const int* off, const int* src, const int
            const int* perm, double* pot, double* ax, double* ay, double* az, int* counter, int blocks,
            cudaStream_t s);
 int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off, const int* src,
-                    const double* zc, const int4* ic, float scale, const void* M, double* Ln, int* counter,
-                    int blocks, cudaStream_t s);
+                    const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld, int accum,
+                    int* counter, int blocks, cudaStream_t s);
 
 // fmm_adaptive_leaf.cu
 int ad_pos32(int nleaf, const int* leaf, const int* nb, const int* ne, const double* zc, const double* xs,

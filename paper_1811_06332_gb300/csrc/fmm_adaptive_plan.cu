@@ -13,11 +13,13 @@
 #include <vector>
 
 #include "fmm_adaptive.h"
+#include "fmm_learn.h"
 
 namespace fmm {
 
-static int grow_bytes(void** p, size_t* cap, size_t need) {
+static int grow_bytes(void** p, size_t* cap, size_t need, unsigned* gen) {
     if (need <= *cap) return 0;
+    ++*gen;
     size_t nc = need + need / 2 + 4096;
     void* q = nullptr;
     if (cudaMalloc(&q, nc) != cudaSuccess) return -3;
@@ -31,7 +33,7 @@ static int grow_bytes(void** p, size_t* cap, size_t need) {
 }
 #define GROW(ptr, capname, bytes)                                                            \
     do {                                                                                     \
-        int r_ = grow_bytes((void**)&(ptr), &(capname), (size_t)(bytes));                  \
+        int r_ = grow_bytes((void**)&(ptr), &(capname), (size_t)(bytes), &a->gen);         \
         if (r_) return r_;                                                                   \
     } while (0)
 
@@ -41,7 +43,8 @@ void ad_free(AdState* a) {
                     a->box, a->part, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0, a->nchild, a->parent,
                     a->zc, a->rad, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
                     a->oq, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
-                    a->pos32, a->M, a->L, a->M32, a->counter};
+                    a->pos32, a->M, a->L, a->M32, a->counter, a->ptgt, a->nodeF, a->porder, a->iota,
+                    a->bcnt, a->boff, a->bsrc};
     for (void* p : ptrs) cudaFree(p);
     if (a->gexec) cudaGraphExecDestroy(a->gexec);
     delete a;
@@ -156,10 +159,15 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         GROW(a->cq, a->cap_cq, (size_t)(nq + 1) * 4); GROW(a->om, a->cap_om, (size_t)(nq + 1) * 4);
         GROW(a->op, a->cap_op, (size_t)(nq + 1) * 4); GROW(a->oq, a->cap_oq, (size_t)(nq + 1) * 4);
         ad_trav_count(nq, (const int2*)a->q0, theta, a->nchild, a->zc, a->rad, a->cm, a->cp, a->cq, s);
-        int tm = 0, tp = 0, tq = 0;
-        if (scan_total(a->cm, a->om, nq, a->scr, &tm, s) || scan_total(a->cp, a->op, nq, a->scr, &tp, s) ||
-            scan_total(a->cq, a->oq, nq, a->scr, &tq, s))
-            return -2;
+        int tot3[3] = {0, 0, 0};
+        scan_excl_int(a->cm, a->om, nq, a->scr, s);
+        scan_excl_int(a->cp, a->op, nq, a->scr, s);
+        scan_excl_int(a->cq, a->oq, nq, a->scr, s);
+        cudaMemcpyAsync(&tot3[0], a->om + nq, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&tot3[1], a->op + nq, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&tot3[2], a->oq + nq, 4, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
+        const int tm = tot3[0], tp = tot3[1], tq = tot3[2];
         GROW(a->m2l, a->cap_m2l, (size_t)(nm + tm + 1) * 8);
         GROW(a->p2p, a->cap_p2p, (size_t)(np + tp + 1) * 8);
         GROW(a->q1, a->cap_q1, (size_t)(tq + 1) * 8);
@@ -253,7 +261,7 @@ static int m2l_launch(AdState* a, int p, int basis, int prec, int blocks, cudaSt
     cudaMemsetAsync(a->counter, 0, 4, s);
     const void* M = prec ? (const void*)a->M32 : (const void*)a->M;
     return launch_m2l_list(p, basis, prec ? 1 : 0, a->ntarg, a->order, a->moff, a->msrc, a->zc, a->ic, a->scale32, M,
-                           a->L, a->counter, blocks, s);
+                           a->L, a->nc, 0, a->counter, blocks, s);
 }
 
 int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s) {
@@ -316,6 +324,67 @@ int ad_run_p2p(AdState* a, int prec, int sms, double* pot, double* ax, double* a
     else
         ad_p2p(a->nleaf, a->leaf, a->poff, a->psrc, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs, a->perm, pot,
                ax, ay, az, a->counter + 1, 4 * sms, s);
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// learned per-pair order
+// ---------------------------------------------------------------------------
+int ad_learn_prepare(AdState* a, cudaStream_t s) {
+    const size_t nn = (size_t)(a->nn > 0 ? a->nn : 1), np = (size_t)(a->nm2l > 0 ? a->nm2l : 1);
+    GROW(a->ptgt, a->cap_ptgt, np * 4);
+    GROW(a->nodeF, a->cap_nodeF, nn * 32);
+    GROW(a->porder, a->cap_porder, np);
+    GROW(a->iota, a->cap_iota, nn * 4);
+    GROW(a->bcnt, a->cap_bcnt, (FMM_PMAX + 1) * nn * 4 + 4);
+    GROW(a->boff, a->cap_boff, (FMM_PMAX + 1) * nn * 4 + 4);
+    GROW(a->bsrc, a->cap_bsrc, np * 4);
+    if (a->nn > 0) {
+        ad_pair_targets_launch(a->nn, a->nm2l, a->moff, a->ptgt, s);
+        ad_iota(a->nn, a->iota, s);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+// M2L with one order per pair: the model (or the caller's orders) gives the
+// order, the pairs are grouped by (order, target) with a stable sort, and
+// one list M2L per order accumulates the rank prefix |n| + |m| <= q of Eq.
+// M2L into the order-p local expansions.
+int ad_run_m2l_orders(AdState* a, int p, int basis, int prec, int sms, const unsigned char* mlp, float thr, int* err,
+                      cudaStream_t s) {
+    if (a->n == 0) return 0;
+    cudaMemsetAsync(a->L, 0, (size_t)a->nn * a->nc * 8, s);
+    if (prec) ad_to_f32((int64_t)a->nn * a->nc, a->M, a->M32, s);
+    if (a->nm2l == 0) return 0;
+    if (!a->orders_fixed) {
+        ad_node_features(a, s);
+        mlp_orders_dev(mlp, a, thr, p, sms, err, s);
+    }
+    ad_order_keys(a->nm2l, a->porder, a->k0, a->v0, s);
+    if (int r = sort_pairs(a, a->nm2l, 4, s)) return r;
+    const int nb = p + 1;
+    cudaMemsetAsync(a->bcnt, 0, (size_t)nb * a->nn * 4 + 4, s);
+    ad_bucket_csr(a->nm2l, a->nn, a->k0, a->v0, a->ptgt, a->msrc, a->bsrc, a->bcnt, s);
+    scan_excl_int(a->bcnt, a->boff, (int64_t)nb * a->nn, a->scr, s);
+    cudaMemsetAsync(a->counter + 2, 0, (size_t)nb * 4, s);
+    const void* M = prec ? (const void*)a->M32 : (const void*)a->M;
+    const int blocks = a->m2l_blocks > 0 ? a->m2l_blocks : 2 * sms;
+    for (int q = 0; q < nb; ++q)
+        launch_m2l_list(q, basis, prec ? 1 : 0, a->nn, a->iota, a->boff + (size_t)q * a->nn, a->bsrc, a->zc, a->ic,
+                        a->scale32, M, a->L, a->nc, 1, a->counter + 2 + q, blocks, s);
+    return 0;
+}
+
+// pairs per order 0..p of the last grouping (host, synchronises)
+int ad_order_counts(AdState* a, int p, int64_t* out, cudaStream_t s) {
+    const int nb = p + 1;
+    std::vector<int> h(nb + 1, 0);
+    if (a->nm2l > 0 && a->boff) {
+        for (int q = 0; q <= nb; ++q)
+            cudaMemcpyAsync(&h[q], a->boff + (size_t)q * a->nn, 4, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
+    }
+    for (int q = 0; q < nb; ++q) out[q] = h[q + 1] - h[q];
     return 0;
 }
 

@@ -12,6 +12,7 @@
 #include "fmm_gb300.h"
 #include "fmm_adaptive.h"
 #include "fmm_internal.h"
+#include "fmm_learn.h"
 
 namespace fmm {
 static std::atomic<int64_t> g_launches{0};
@@ -64,6 +65,10 @@ struct fmm_plan {
     // adaptive octree state (cfg.adaptive)
     AdState* ad = nullptr;
     int sms = 152;
+    // learned per-pair order (cfg.learned_p)
+    unsigned char* mlp_dev = nullptr;   // packed BF16 model (MLP_DEV_BYTES)
+    bool mlp_set = false;
+    float log10_kappa = 0.f;
 };
 
 static void* tc_maps_at(fmm_plan* pl, int l) {
@@ -138,7 +143,9 @@ int64_t fmm_kernel_launches(void) { return g_launches.load(); }
 
 int fmm_plan_stats(const fmm_plan* pl, int64_t* out, int nout) {
     if (!pl || !out || nout < 0) return fail_plan(nullptr, FMM_ERR_ARG, "null plan or output");
-    int64_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t v[19] = {0};
+    if (pl->ad && pl->cfg.learned_p && nout > 8 && pl->built)
+        ad_order_counts(pl->ad, pl->cfg.p, v + 8, 0);
     if (pl->ad) {
         const AdState* A = pl->ad;
         v[0] = A->nn; v[1] = A->nleaf; v[2] = A->nm2l; v[3] = A->np2p; v[4] = A->ntarg;
@@ -149,7 +156,7 @@ int fmm_plan_stats(const fmm_plan* pl, int64_t* out, int nout) {
         for (int l = 0; l <= pl->depth; ++l) cells += (int64_t)1 << (3 * l);
         v[0] = cells; v[1] = pl->nleaf; v[6] = pl->depth + 1;
     }
-    for (int k = 0; k < nout && k < 8; ++k) out[k] = v[k];
+    for (int k = 0; k < nout && k < 19; ++k) out[k] = v[k];
     return FMM_OK;
 }
 
@@ -352,6 +359,12 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         if (cfg->prec != FMM_FP64 && cfg->prec != FMM_FP32)
             FAIL(FMM_ERR_UNSUPPORTED, "adaptive trees support FMM_FP64 and FMM_FP32");
     }
+    if (cfg->learned_p) {
+        if (!cfg->adaptive) FAIL(FMM_ERR_UNSUPPORTED, "learned_p needs an adaptive tree");
+        if (cfg->basis != FMM_BASIS_SYM) FAIL(FMM_ERR_UNSUPPORTED, "learned_p needs FMM_BASIS_SYM");
+        if (cfg->p < 4) FAIL(FMM_ERR_ARG, "learned_p needs p >= 4 (the features read ranks 1..4)");
+        if (!(cfg->target_rel_err > 0.0)) FAIL(FMM_ERR_ARG, "learned_p needs target_rel_err > 0");
+    }
     if (cfg->depth < 0 || cfg->depth > 9) FAIL(FMM_ERR_ARG, "depth=%d outside 0..9", cfg->depth);
     if (cfg->prec == FMM_GEMM_TF32X3) FAIL(FMM_ERR_UNSUPPORTED, "the TF32x3 tensor-core form is not available yet");
     if (cfg->prec == FMM_GEMM_BF16X3 && !tc_supported(cfg->p, cfg->basis))
@@ -371,6 +384,11 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     pl->dev = dev;
     cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
     if (cfg->adaptive) {
+        if (cfg->learned_p &&
+            (cudaMalloc(&pl->derr, sizeof(int)) != cudaSuccess || cudaMemset(pl->derr, 0, sizeof(int)) != cudaSuccess)) {
+            fmm_destroy(pl);
+            return fail_plan(nullptr, FMM_ERR_OOM, "allocating the device error word failed");
+        }
         *out = pl;
         return FMM_OK;
     }
@@ -456,7 +474,7 @@ void fmm_destroy(fmm_plan* pl) {
     ad_free(pl->ad);
     free_tree(pl);
     cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32);
-    cudaFree(pl->Kbf); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32);
+    cudaFree(pl->Kbf); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
     delete pl;
 }
 
@@ -470,6 +488,12 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
                                 pl->cfg.prec == FMM_FP64 ? 0 : 1, S(stream));
         if (rc == -3) FAIL(FMM_ERR_OOM, "allocating adaptive tree storage failed");
         if (rc) FAIL(FMM_ERR_CUDA, "adaptive tree build failed: %s", cudaGetErrorString(cudaGetLastError()));
+        if (pl->cfg.learned_p) {
+            const int r2 = ad_learn_prepare(pl->ad, S(stream));
+            if (r2 == -3) FAIL(FMM_ERR_OOM, "allocating learned-order storage failed");
+            if (r2) FAIL(FMM_ERR_CUDA, "learned-order set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+            if (pl->ad->orders_fixed && pl->ad->n_orders != pl->ad->nm2l) pl->ad->orders_fixed = false;
+        }
         pl->n = n;
         pl->built = true;
         return FMM_OK;
@@ -563,6 +587,16 @@ int fmm_m2m(fmm_plan* pl, void* stream) {
 int fmm_m2l(fmm_plan* pl, void* stream) {
     NEED_TREE();
     if (pl->ad) {
+        if (pl->cfg.learned_p) {
+            if (!pl->ad->orders_fixed && !pl->mlp_set)
+                FAIL(FMM_ERR_STATE, "learned_p plan without a model (fmm_set_mlp) or pair orders (fmm_set_pair_orders)");
+            const float thr = (float)log10(pl->cfg.target_rel_err) + pl->log10_kappa;
+            if (ad_run_m2l_orders(pl->ad, pl->cfg.p, pl->cfg.basis, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->sms,
+                                  pl->mlp_dev, thr, pl->derr, S(stream)))
+                FAIL(FMM_ERR_CUDA, "per-order M2L failed: %s", cudaGetErrorString(cudaGetLastError()));
+            CKLAUNCH();
+            return FMM_OK;
+        }
         if (ad_run_m2l(pl->ad, pl->cfg.p, pl->cfg.basis, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->sms, S(stream)))
             FAIL(FMM_ERR_UNSUPPORTED, "no list M2L kernel for this order and basis");
         CKLAUNCH();
@@ -666,12 +700,15 @@ int fmm_evaluate(fmm_plan* pl, int64_t n, const double* x, const double* y, cons
     if (n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
     int rc;
     if ((rc = fmm_build_tree(pl, n, x, y, z, q, stream))) return rc;
-    if (pl->ad && pl->cfg.use_graph && stream && pl->ad->m2l_blocks > 0 && n > 0) {
+    if (pl->ad && pl->cfg.use_graph && stream && n > 0 &&
+        (pl->ad->m2l_blocks > 0 || (pl->cfg.learned_p && (pl->mlp_set || pl->ad->orders_fixed)))) {
         // replay the captured operator sequence while the tree keeps its
         // sizes and buffers; capture it again otherwise
         AdState* A = pl->ad;
-        const void* key[8] = {A->M, A->L, A->msrc, A->psrc, pot, ax, (const void*)(intptr_t)A->nn,
-                              (const void*)(intptr_t)(((int64_t)A->ntarg << 32) ^ A->nleaf ^ (A->nm2l * 7919LL))};
+        const void* key[8] = {A->M, pot, ax, (const void*)(intptr_t)A->gen, (const void*)(intptr_t)A->nn,
+                              (const void*)(intptr_t)(((int64_t)A->ntarg << 32) ^ A->nleaf ^ (A->nm2l * 7919LL)),
+                              (const void*)(intptr_t)((A->orders_fixed ? 1 : 0) | (pl->mlp_set ? 2 : 0)),
+                              (const void*)(intptr_t)A->m2l_blocks};
         if (!A->gexec || memcmp(key, A->graph_key, sizeof key) != 0) {
             if (A->gexec) { cudaGraphExecDestroy(A->gexec); A->gexec = nullptr; }
             cudaGraph_t g = nullptr;
@@ -731,6 +768,150 @@ int fmm_evaluate_host(fmm_plan* pl, int64_t n, const double* x, const double* y,
         CK(cudaMemcpy(&herr, pl->derr, sizeof(int), cudaMemcpyDeviceToHost));
         if (herr) FAIL(FMM_ERR_TIMEOUT, "a bounded wait in the tensor-core M2L gave up (code %d)", herr);
     }
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned per-pair order
+// ---------------------------------------------------------------------------
+static int check_blob(fmm_plan* pl, const float* blob) {
+    if (!blob) FAIL(FMM_ERR_ARG, "blob is NULL");
+    if (blob[0] != 6332.f || blob[1] != 1.f || blob[2] != (float)FMM_MLP_NF || blob[3] != 64.f ||
+        blob[4] != (float)FMM_MLP_NOUT || blob[5] != 2.f)
+        FAIL(FMM_ERR_ARG, "blob header is not {6332, 1, 11, 64, 9, 2, ...}");
+    for (int f = 0; f < FMM_MLP_NF; ++f)
+        if (!(blob[FMM_MLP_OFF_SD + f] > 0.f)) FAIL(FMM_ERR_ARG, "feature deviation %d is not positive", f);
+    return FMM_OK;
+}
+
+static int need_pairs(fmm_plan* pl, cudaStream_t s) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (!pl->ad) FAIL(FMM_ERR_ARG, "not an adaptive plan");
+    if (!pl->built) FAIL(FMM_ERR_STATE, "fmm_build_tree has not been called");
+    const int r = ad_learn_prepare(pl->ad, s);
+    if (r == -3) FAIL(FMM_ERR_OOM, "allocating pair storage failed");
+    if (r) FAIL(FMM_ERR_CUDA, "pair set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return FMM_OK;
+}
+
+int fmm_plan_pairs(fmm_plan* pl, int32_t* tgt, int32_t* src, int64_t cap, int64_t* count) {
+    if (int rc = need_pairs(pl, 0)) return rc;
+    const int64_t np = pl->ad->nm2l;
+    if (count) *count = np;
+    if (cap < np || np == 0) return FMM_OK;
+    if (!tgt || !src) FAIL(FMM_ERR_ARG, "null output array");
+    CK(cudaMemcpy(tgt, pl->ad->ptgt, (size_t)np * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(src, pl->ad->msrc, (size_t)np * 4, cudaMemcpyDeviceToHost));
+    return FMM_OK;
+}
+
+int fmm_pair_data(fmm_plan* pl, float* feat, double* labels, void* stream) {
+    if (int rc = need_pairs(pl, S(stream))) return rc;
+    if (pl->cfg.basis != FMM_BASIS_SYM || pl->cfg.p < 4) FAIL(FMM_ERR_ARG, "pair data needs FMM_BASIS_SYM and p >= 4");
+    if (labels && (pl->cfg.p != 10 || pl->cfg.prec != FMM_FP64))
+        FAIL(FMM_ERR_ARG, "labels need p = 10 and FMM_FP64");
+    if (pl->ad->nm2l > 0 && !feat && !labels) FAIL(FMM_ERR_ARG, "nothing to write");
+    if (int rc = fmm_p2m(pl, stream)) return rc;
+    if (int rc = fmm_m2m(pl, stream)) return rc;
+    ad_node_features(pl->ad, S(stream));
+    if (feat) ad_pair_features(pl->ad, feat, S(stream));
+    if (labels) ad_pair_labels(pl->ad, labels, S(stream));
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_mlp_grad(const float* blob, int64_t n, const float* feat, const float* labels, float* loss, float* grad,
+                 void* stream) {
+    fmm_plan* pl = nullptr;
+    if (int rc = check_blob(pl, blob)) return rc;
+    if (n < 1 || n > (1 << 20)) FAIL(FMM_ERR_ARG, "n=%lld outside 1..2^20", (long long)n);
+    if (!feat || !labels || !loss || !grad) FAIL(FMM_ERR_ARG, "null array");
+    const int rc = mlp_grad_host(blob, n, feat, labels, loss, grad, S(stream));
+    if (rc == -3) FAIL(FMM_ERR_OOM, "allocating trainer scratch failed");
+    if (rc) FAIL(FMM_ERR_CUDA, "gradient pass failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return FMM_OK;
+}
+
+int fmm_mlp_train(float* blob, int64_t n, const float* feat, const float* labels, const int32_t* order, int epochs,
+                  int batch, float lr, int fit_moments, float* loss_out, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (!blob) FAIL(FMM_ERR_ARG, "blob is NULL");
+    if (!fit_moments)
+        if (int rc = check_blob(pl, blob)) return rc;
+    if (n < 1 || n > (int64_t)0x7fffffff) FAIL(FMM_ERR_ARG, "n=%lld outside 1..2^31-1", (long long)n);
+    if (!feat || !labels || !order) FAIL(FMM_ERR_ARG, "null array");
+    if (epochs < 0 || batch < 1 || batch > (1 << 20) || !(lr > 0.f)) FAIL(FMM_ERR_ARG, "bad epochs, batch or lr");
+    const int rc = mlp_train_host(blob, n, feat, labels, order, epochs, batch, lr, fit_moments, loss_out, S(stream));
+    if (rc == -3) FAIL(FMM_ERR_OOM, "allocating trainer storage failed");
+    if (rc) FAIL(FMM_ERR_CUDA, "training failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return FMM_OK;
+}
+
+int fmm_mlp_predict(const float* blob, int64_t n, const float* feat, float* pred, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (int rc = check_blob(pl, blob)) return rc;
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n == 0) return FMM_OK;
+    if (!feat || !pred) FAIL(FMM_ERR_ARG, "null array");
+    std::vector<unsigned char> h(MLP_DEV_BYTES);
+    mlp_pack_device(blob, h.data());
+    unsigned char* d = nullptr;
+    int* derr = nullptr;
+    int dev = 0, sms = 152;
+    CK(cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaMalloc(&d, MLP_DEV_BYTES) != cudaSuccess || cudaMalloc(&derr, 4) != cudaSuccess) {
+        cudaFree(d);
+        FAIL(FMM_ERR_OOM, "allocating model storage failed");
+    }
+    cudaStream_t s = S(stream);
+    int herr = 0;
+    bool ok = cudaMemcpyAsync(d, h.data(), MLP_DEV_BYTES, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemsetAsync(derr, 0, 4, s) == cudaSuccess;
+    if (ok) {
+        mlp_predict_dev(d, n, feat, pred, sms, derr, s);
+        ok = cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+             cudaStreamSynchronize(s) == cudaSuccess;
+    }
+    const cudaError_t e = cudaGetLastError();
+    cudaFree(d);
+    cudaFree(derr);
+    if (!ok || e != cudaSuccess) FAIL(FMM_ERR_CUDA, "inference failed: %s", cudaGetErrorString(e));
+    if (herr) FAIL(FMM_ERR_TIMEOUT, "a bounded wait in the tensor-core inference gave up (code %d)", herr);
+    return FMM_OK;
+}
+
+int fmm_set_mlp(fmm_plan* pl, const float* blob, int64_t nblob) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (!pl->cfg.learned_p) FAIL(FMM_ERR_ARG, "plan was not created with learned_p");
+    if (nblob != FMM_MLP_NBLOB) FAIL(FMM_ERR_ARG, "nblob=%lld, expected %d", (long long)nblob, FMM_MLP_NBLOB);
+    if (int rc = check_blob(pl, blob)) return rc;
+    std::vector<unsigned char> h(MLP_DEV_BYTES);
+    mlp_pack_device(blob, h.data());
+    if (!pl->mlp_dev && cudaMalloc(&pl->mlp_dev, MLP_DEV_BYTES) != cudaSuccess) {
+        pl->mlp_dev = nullptr;
+        FAIL(FMM_ERR_OOM, "allocating model storage failed");
+    }
+    CK(cudaMemcpy(pl->mlp_dev, h.data(), MLP_DEV_BYTES, cudaMemcpyHostToDevice));
+    pl->log10_kappa = blob[6];
+    pl->mlp_set = true;
+    return FMM_OK;
+}
+
+int fmm_set_pair_orders(fmm_plan* pl, const int8_t* orders, int64_t n) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (!pl->cfg.learned_p) FAIL(FMM_ERR_ARG, "plan was not created with learned_p");
+    if (!orders) {
+        if (pl->ad) pl->ad->orders_fixed = false;
+        return FMM_OK;
+    }
+    if (int rc = need_pairs(pl, 0)) return rc;
+    if (n != pl->ad->nm2l) FAIL(FMM_ERR_ARG, "n=%lld, the tree has %d M2L pairs", (long long)n, pl->ad->nm2l);
+    for (int64_t k = 0; k < n; ++k)
+        if (orders[k] < 0 || orders[k] > pl->cfg.p) FAIL(FMM_ERR_ARG, "order %d of pair %lld outside 0..p", orders[k], (long long)k);
+    if (n > 0) CK(cudaMemcpy(pl->ad->porder, orders, (size_t)n, cudaMemcpyHostToDevice));
+    pl->ad->orders_fixed = true;
+    pl->ad->n_orders = n;
     return FMM_OK;
 }
 

@@ -613,7 +613,8 @@ def emit_list_file(p, basis, T):
          "__global__ void __launch_bounds__(128)",
          "m2l_list_p%d_b%d_%s(int ntarg, const int* __restrict__ order, const int* __restrict__ off,"
          " const int* __restrict__ src, const double* __restrict__ zc, const int4* __restrict__ ic, float scale,"
-         " const %s* __restrict__ Mn, double* __restrict__ Ln, int* __restrict__ counter) {" % (p, basis, T, T),
+         " const %s* __restrict__ Mn, double* __restrict__ Ln, int ld, int accum, int* __restrict__ counter) {"
+         % (p, basis, T, T),
          "  typedef %s T;" % T,
          "  const int lane = threadIdx.x & 31;",
          "  for (;;) {",
@@ -639,7 +640,7 @@ def emit_list_file(p, basis, T):
     else:
         L.append("      const int4 is = ic[s];")
         L.append("      const T x = T(it.x - is.x) * scale, y = T(it.y - is.y) * scale, z = T(it.z - is.z) * scale;")
-    L.append("      const T* __restrict__ Ms = Mn + (int64_t)s * %d;" % nc)
+    L.append("      const T* __restrict__ Ms = Mn + (int64_t)s * ld;")
     L.append("      T d[%d];" % ns(p))
     L.append("  " + gen_dtensor(p).replace("\n", "\n  "))
     for b in range(p + 1):
@@ -665,15 +666,21 @@ def emit_list_file(p, basis, T):
             L.append("        }")
         L.append("      }")
     L.append("    }")
+    L.append("    double* __restrict__ Lt = Ln + (int64_t)t * ld;")
+    L.append("    if (accum) {")
     for a in range(nc):
-        L.append("    Ln[(int64_t)t * %d + %d] = (double)a%d;" % (nc, a, a))
+        L.append("      Lt[%d] += (double)a%d;" % (a, a))
+    L.append("    } else {")
+    for a in range(nc):
+        L.append("      Lt[%d] = (double)a%d;" % (a, a))
+    L.append("    }")
     L.append("  }")
     L.append("}")
     L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
-             " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int* counter, int blocks,"
-             " cudaStream_t s) {" % (p, basis, T))
+             " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld, int accum,"
+             " int* counter, int blocks, cudaStream_t s) {" % (p, basis, T))
     L.append("  m2l_list_p%d_b%d_%s<<<blocks, 128, 0, s>>>(ntarg, order, off, src, zc, ic, scale, (const %s*)M,"
-             " Ln, counter);" % (p, basis, T, T))
+             " Ln, ld, accum, counter);" % (p, basis, T, T))
     L.append("  return 0;")
     L.append("}")
     L.append("}  // namespace fmm")
@@ -687,16 +694,16 @@ def emit_list_dispatch():
         for b in (0, 1):
             for T in ("float", "double"):
                 L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
-                         " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int* counter,"
-                         " int blocks, cudaStream_t s);" % (p, b, T))
+                         " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld,"
+                         " int accum, int* counter, int blocks, cudaStream_t s);" % (p, b, T))
     L.append("int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off,"
-             " const int* src, const double* zc, const int4* ic, float scale, const void* M, double* Ln,"
-             " int* counter, int blocks, cudaStream_t s) {")
+             " const int* src, const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld,"
+             " int accum, int* counter, int blocks, cudaStream_t s) {")
     for p in range(PMAX + 1):
         for b in (0, 1):
             for k, T in ((0, "double"), (1, "float")):
                 L.append("  if (p == %d && basis == %d && prec == %d) return launch_m2l_list_p%d_b%d_%s(ntarg, order,"
-                         " off, src, zc, ic, scale, M, Ln, counter, blocks, s);" % (p, b, k, p, b, T))
+                         " off, src, zc, ic, scale, M, Ln, ld, accum, counter, blocks, s);" % (p, b, k, p, b, T))
     L.append("  return -1;")
     L.append("}")
     L.append("}  // namespace fmm")

@@ -23,8 +23,11 @@ EXPORTS = [
     "fmm_ncoef", "fmm_create", "fmm_destroy", "fmm_last_error", "fmm_build_tree", "fmm_p2m", "fmm_m2m",
     "fmm_m2l", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate", "fmm_evaluate_host", "fmm_op_dtensor",
     "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
-    "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_plan_stats",
+    "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
+    "fmm_mlp_grad", "fmm_mlp_train", "fmm_mlp_predict", "fmm_set_mlp", "fmm_set_pair_orders",
 ]
+
+MLP_NF, MLP_NOUT, MLP_NBLOB = 11, 9, 9703
 
 
 class FMMError(RuntimeError):
@@ -73,6 +76,13 @@ def lib():
             "fmm_kernel_launches": ([], _i64),
             "fmm_evaluate_noalloc": ([_int, _int, _int, _i64] + [_vp] * 9, _int),
             "fmm_plan_stats": ([_vp, _vp, _int], _int),
+            "fmm_plan_pairs": ([_vp, _vp, _vp, _i64, _vp], _int),
+            "fmm_pair_data": ([_vp, _vp, _vp, _vp], _int),
+            "fmm_mlp_grad": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp], _int),
+            "fmm_mlp_train": ([_vp, _i64, _vp, _vp, _vp, _int, _int, ctypes.c_float, _int, _vp, _vp], _int),
+            "fmm_mlp_predict": ([_vp, _i64, _vp, _vp, _vp], _int),
+            "fmm_set_mlp": ([_vp, _vp, _i64], _int),
+            "fmm_set_pair_orders": ([_vp, _vp, _i64], _int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -145,6 +155,41 @@ def fmm_op_l2p(p, basis, L, rb, out, stream=None):
     _check(lib().fmm_op_l2p(p, basis, L.shape[1], _ptr(L), _ptr(rb), _ptr(out), _stream(stream)))
 
 
+def _host_f32(blob):
+    import numpy as np
+    b = np.ascontiguousarray(blob, dtype=np.float32)
+    if b.shape != (MLP_NBLOB,):
+        raise ValueError("blob must hold %d floats" % MLP_NBLOB)
+    return b
+
+
+def fmm_mlp_grad(blob, feat, labels, stream=None):
+    """Loss and gradient (numpy, FP32) of the order model over the samples
+    (device float32 feat [n, 11], labels [n, 9])."""
+    import numpy as np
+    b = _host_f32(blob)
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(MLP_NBLOB - 30, dtype=np.float32)
+    _check(lib().fmm_mlp_grad(b.ctypes.data, feat.shape[0], _ptr(feat), _ptr(labels), loss.ctypes.data,
+                              grad.ctypes.data, _stream(stream)))
+    return float(loss[0]), grad
+
+
+def fmm_mlp_train(blob, feat, labels, order, epochs, batch, lr, fit_moments=True, stream=None):
+    """Trains in place on a copy of blob; returns (trained blob, per-epoch loss)."""
+    import numpy as np
+    b = _host_f32(blob).copy()
+    losses = np.zeros(max(epochs, 1), dtype=np.float32)
+    _check(lib().fmm_mlp_train(b.ctypes.data, feat.shape[0], _ptr(feat), _ptr(labels), _ptr(order), epochs, batch,
+                               float(lr), int(fit_moments), losses.ctypes.data, _stream(stream)))
+    return b, losses[:epochs]
+
+
+def fmm_mlp_predict(blob, feat, pred, stream=None):
+    b = _host_f32(blob)
+    _check(lib().fmm_mlp_predict(b.ctypes.data, feat.shape[0], _ptr(feat), _ptr(pred), _stream(stream)))
+
+
 def fmm_direct(x, y, z, q, pot, ax, ay, az, targets=None, stream=None):
     nt = len(targets) if targets is not None else len(x)
     _check(lib().fmm_direct(len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), nt, _ptr(targets), _ptr(pot),
@@ -158,9 +203,10 @@ class Plan:
     """Owns an fmm_plan (uniform octree FMM of App. C)."""
 
     def __init__(self, p, basis=BASIS_SYM, prec=FP64, depth=3, use_graph=False, adaptive=False,
-                 max_leaf=64, theta=0.5):
+                 max_leaf=64, theta=0.5, learned_p=False, target_rel_err=1e-4):
         cfg = Config(p=p, basis=basis, prec=prec, adaptive=int(adaptive), depth=depth, max_leaf=max_leaf,
-                     theta=theta, learned_p=0, target_rel_err=1e-4, use_graph=int(use_graph))
+                     theta=theta, learned_p=int(learned_p), target_rel_err=target_rel_err,
+                     use_graph=int(use_graph))
         h = _vp()
         _check(lib().fmm_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h
@@ -219,13 +265,50 @@ class Plan:
                                         hp(az), _stream(stream)))
 
     def stats(self):
-        """Tree and list sizes (fmm_plan_stats)."""
+        """Tree and list sizes (fmm_plan_stats); learned_p plans add the
+        number of M2L pairs per order."""
         import numpy as np
-        v = np.zeros(8, dtype=np.int64)
-        self._c(lib().fmm_plan_stats(self.h, v.ctypes.data, 8))
+        v = np.zeros(19, dtype=np.int64)
+        self._c(lib().fmm_plan_stats(self.h, v.ctypes.data, 19))
         keys = ("cells", "leaves", "m2l_pairs", "p2p_pairs", "m2l_targets", "m2l_blocks_per_sm", "levels",
                 "graph")
-        return dict(zip(keys, v.tolist()))
+        out = dict(zip(keys, v[:8].tolist()))
+        if self.cfg.learned_p:
+            out["pairs_per_order"] = v[8:8 + self.cfg.p + 1].tolist()
+        return out
+
+    def pairs(self):
+        """M2L pairs (target, source) as numpy int32 arrays, grouped by target."""
+        import numpy as np
+        cnt = ctypes.c_int64(0)
+        self._c(lib().fmm_plan_pairs(self.h, None, None, 0, ctypes.byref(cnt)))
+        t = np.zeros(cnt.value, dtype=np.int32)
+        s = np.zeros(cnt.value, dtype=np.int32)
+        self._c(lib().fmm_plan_pairs(self.h, t.ctypes.data, s.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return t, s
+
+    def pair_data(self, labels=False, stream=None):
+        """Device tensors: features [npair, 11] (float32) and, on request,
+        labels [npair, 9] (float64) of the plan's M2L pairs."""
+        t, _ = self.pairs()
+        n = len(t)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        feat = torch.empty((n, MLP_NF), dtype=torch.float32, device=dev)
+        lab = torch.empty((n, MLP_NOUT), dtype=torch.float64, device=dev) if labels else None
+        self._c(lib().fmm_pair_data(self.h, _ptr(feat), _ptr(lab), _stream(stream)))
+        return feat, lab
+
+    def set_mlp(self, blob):
+        b = _host_f32(blob)
+        self._c(lib().fmm_set_mlp(self.h, b.ctypes.data, len(b)))
+
+    def set_pair_orders(self, orders):
+        import numpy as np
+        if orders is None:
+            self._c(lib().fmm_set_pair_orders(self.h, None, 0))
+            return
+        o = np.ascontiguousarray(orders, dtype=np.int8)
+        self._c(lib().fmm_set_pair_orders(self.h, o.ctypes.data, len(o)))
 
     def evaluate(self, x, y, z, q, stream=None):
         """Convenience: allocates outputs, returns (pot, acc[3, n]) device tensors."""
