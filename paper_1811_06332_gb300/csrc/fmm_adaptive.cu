@@ -388,7 +388,11 @@ template <typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_m2m_tree(int p, int basis, int lb, int le, const int* __restrict__ child0, const int* __restrict__ nchild,
            const double* __restrict__ zc, double* __restrict__ Mn, const double* __restrict__ detr,
-           const double* __restrict__ expand, DevOffsets off) {
+           const double* __restrict__ expand, DevOffsets off, const int* __restrict__ lev, double side) {
+    // FP32 form: expansions in the scaled units of their cell (side h_c):
+    // Mt_m = M_m / h_c^|m|; the child's (h/2) terms gain 2^-|k|, the shift
+    // uses delta / h_parent.  FP64 form: physical units.
+    constexpr bool SCALED = sizeof(T) == 4;
     __shared__ double sX[WARPS][FMM_NS_MAX], sA[WARPS][FMM_NT_MAX];
     __shared__ T sXt[WARPS][FMM_NS_MAX], sY[WARPS][FMM_NS_MAX];
     __shared__ T sP[WARPS][3][FMM_PMAX + 1];
@@ -415,12 +419,19 @@ k_m2m_tree(int p, int basis, int lb, int le, const int* __restrict__ child0, con
             __syncwarp();
             expand_tl_warp(p, sA[w], sX[w], expand, off, lane);
             __syncwarp();
-            for (int s = lane; s < ns; s += 32) sXt[w][s] = T(sX[w][s]) * sInvF[s];
+            for (int s = lane; s < ns; s += 32)
+                sXt[w][s] = T(SCALED ? ldexp(sX[w][s], -(c_sym_idx[s][0] + c_sym_idx[s][1] + c_sym_idx[s][2]))
+                                     : sX[w][s]) * sInvF[s];
         } else {
-            for (int s = lane; s < ns; s += 32) sXt[w][s] = T(Mn[(int64_t)ch * nc + s]) * sInvF[s];
+            for (int s = lane; s < ns; s += 32) {
+                const double v = Mn[(int64_t)ch * nc + s];
+                sXt[w][s] = T(SCALED ? ldexp(v, -(c_sym_idx[s][0] + c_sym_idx[s][1] + c_sym_idx[s][2])) : v) *
+                            sInvF[s];
+            }
         }
         if (lane < 3) {
-            const double md = -(zc[3 * ch + lane] - zc[3 * c + lane]);
+            const double hinv = SCALED ? ldexp(1.0 / side, lev[c]) : 1.0;
+            const double md = -(zc[3 * ch + lane] - zc[3 * c + lane]) * hinv;
             double v = 1.0;
             sP[w][lane][0] = T(1);
             for (int j = 1; j <= p; ++j) { v *= md; sP[w][lane][j] = T(v * c_invfact[j]); }
@@ -463,7 +474,11 @@ k_m2m_tree(int p, int basis, int lb, int le, const int* __restrict__ child0, con
 template <typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_l2l_tree(int p, int basis, int lb, int le, const int* __restrict__ parent, const double* __restrict__ zc,
-           double* __restrict__ Ln, const double* __restrict__ expand, DevOffsets off) {
+           double* __restrict__ Ln, const double* __restrict__ expand, DevOffsets off, const int* __restrict__ lev,
+           double side) {
+    // FP32 form: Lt_n = L_n h_c^(|n|+1); the shift uses delta / h_parent and
+    // the child's (h/2) output gains 2^-(|n|+1).  FP64 form: physical units.
+    constexpr bool SCALED = sizeof(T) == 4;
     __shared__ double sX[WARPS][FMM_NS_MAX], sA[WARPS][FMM_NT_MAX];
     __shared__ T sXt[WARPS][FMM_NS_MAX];
     __shared__ T sP[WARPS][3][FMM_PMAX + 1];
@@ -480,7 +495,8 @@ k_l2l_tree(int p, int basis, int lb, int le, const int* __restrict__ parent, con
         for (int s = lane; s < ns; s += 32) sX[w][s] = Ln[(int64_t)pa * nc + s];
     }
     if (lane < 3) {
-        const double d = zc[3 * c + lane] - zc[3 * pa + lane];
+        const double hinv = SCALED ? ldexp(1.0 / side, lev[pa]) : 1.0;
+        const double d = (zc[3 * c + lane] - zc[3 * pa + lane]) * hinv;
         double v = 1.0;
         sP[w][lane][0] = T(1);
         for (int j = 1; j <= p; ++j) { v *= d; sP[w][lane][j] = T(v * c_invfact[j]); }
@@ -500,7 +516,8 @@ k_l2l_tree(int p, int basis, int lb, int le, const int* __restrict__ parent, con
                 for (int kz = 0; kz <= rem - kx - ky; ++kz)
                     v += wxy * sP[w][2][kz] * sXt[w][pos_sym(nx + kx, ny + ky, nz + kz)];
             }
-        Ln[(int64_t)c * nc + o] += (double)v;   // accumulation into the FP64 expansion
+        // accumulation into the FP64 expansion
+        Ln[(int64_t)c * nc + o] += SCALED ? ldexp((double)v, -(nx + ny + nz + 1)) : (double)v;
     }
 }
 
@@ -650,28 +667,30 @@ int ad_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
     return 0;
 }
 int ad_m2m(int prec, int p, int basis, int lb, int le, const int* child0, const int* nchild, const double* zc,
-           double* Mn, const DevTables& T, cudaStream_t s) {
+           double* Mn, const DevTables& T, const int* lev, double side, cudaStream_t s) {
     if (le <= lb) return 0;
     constexpr int W = 4;
     const unsigned g = (unsigned)((le - lb + W - 1) / W);
     if (prec)
         k_m2m_tree<float, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, child0, nchild, zc, Mn, T.detr, T.expand,
-                                                  T.offsets());
+                                                  T.offsets(), lev, side);
     else
         k_m2m_tree<double, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, child0, nchild, zc, Mn, T.detr, T.expand,
-                                                   T.offsets());
+                                                   T.offsets(), lev, side);
     count_launch();
     return 0;
 }
 int ad_l2l(int prec, int p, int basis, int lb, int le, const int* parent, const double* zc, double* Ln,
-           const DevTables& T, cudaStream_t s) {
+           const DevTables& T, const int* lev, double side, cudaStream_t s) {
     if (le <= lb) return 0;
     constexpr int W = 4;
     const unsigned g = (unsigned)((le - lb + W - 1) / W);
     if (prec)
-        k_l2l_tree<float, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, parent, zc, Ln, T.expand, T.offsets());
+        k_l2l_tree<float, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, parent, zc, Ln, T.expand, T.offsets(), lev,
+                                                  side);
     else
-        k_l2l_tree<double, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, parent, zc, Ln, T.expand, T.offsets());
+        k_l2l_tree<double, W><<<g, W * 32, 0, s>>>(p, basis, lb, le, parent, zc, Ln, T.expand, T.offsets(), lev,
+                                                   side);
     count_launch();
     return 0;
 }

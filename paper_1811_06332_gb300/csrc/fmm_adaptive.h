@@ -30,6 +30,7 @@ struct AdState {
     int4* ic = nullptr;        // integer node centres (fmm_adaptive_leaf.cu)
     float4* pos32 = nullptr;   // FP32 form: particle offsets from their leaf centre, charge
     float scale32 = 0.f;       // side / 2^22: unit of the integer centres
+    double side = 0.0;         // side of the root cube (cell of level l: side / 2^l)
     // expansions (node-major)
     double *M = nullptr, *L = nullptr;
     float* M32 = nullptr;
@@ -107,9 +108,9 @@ int ad_len_keys(int nn, const int* off, uint64_t* key, int* val, cudaStream_t s)
 int ad_leaf_keys(int nn, const int* nchild, const int* nb, uint64_t* key, int* val, cudaStream_t s);
 int ad_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
 int ad_m2m(int prec, int p, int basis, int lb, int le, const int* child0, const int* nchild, const double* zc, double* Mn,
-           const DevTables& T, cudaStream_t s);
+           const DevTables& T, const int* lev, double side, cudaStream_t s);
 int ad_l2l(int prec, int p, int basis, int lb, int le, const int* parent, const double* zc, double* Ln, const DevTables& T,
-           cudaStream_t s);
+           const int* lev, double side, cudaStream_t s);
 int ad_p2p(int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne,
            const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
            const int* perm, double* pot, double* ax, double* ay, double* az, int* counter, int blocks,
@@ -124,11 +125,11 @@ int ad_pos32(int nleaf, const int* leaf, const int* nb, const int* ne, const dou
 int ad_icentre(int nn, const int* lev, const int* ix, const int* iy, const int* iz, int4* ic, cudaStream_t s);
 int ad_p2m_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
                 const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
-                const float4* pos32, double* Mn, const DevTables& Tb, cudaStream_t s);
+                const float4* pos32, double* Mn, const DevTables& Tb, const int* lev, double side, cudaStream_t s);
 int ad_l2p_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
                 const double* zc, const double* xs, const double* ys, const double* zs, const float4* pos32,
                 const int* perm, const double* Ln, const DevTables& Tb, double* pot, double* ax, double* ay,
-                double* az, cudaStream_t s);
+                double* az, const int* lev, double side, cudaStream_t s);
 int ad_p2p32(int nwork, const int* work, const int* off, const int* src, const int* nb, const int* ne, const int4* ic,
              float scale, const float4* pos32, const int* perm, double* pot, double* ax, double* ay, double* az,
              int* counter, int blocks, cudaStream_t s);

@@ -4,7 +4,10 @@
 //                  SYM: M = A, TRACELESS: Mbar = D[A] (independent comps);
 //   L2P (Eq. L2P)  Phi = sum_k (x - z)^k / k! L_k and its gradient;
 //   P2P            near field over the leaf pairs of the interaction lists.
-// Expansions are node-major ([node][ncoef]) in physical units.
+// Expansions are node-major ([node][ncoef]); the FP64 form keeps them in
+// physical units, the FP32 form in the scaled units of their cell (side
+// h = side/2^level): Mt_m = M_m / h^|m|, Lt_n = L_n h^(|n|+1), which keeps
+// every power of a cell size inside the FP32 range at any depth and order.
 //
 // The FP32 form reads particles as FP32 offsets from the centre of their own
 // leaf (pos32), and takes the offset between two node centres from their
@@ -47,7 +50,10 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_ad_p2m(int basis, int nleaf, const int* __restrict__ leaf, const int* __restrict__ nb, const int* __restrict__ ne,
          const double* __restrict__ zc, const double* __restrict__ xs, const double* __restrict__ ys,
          const double* __restrict__ zs, const double* __restrict__ qs, const float4* __restrict__ pos32,
-         double* __restrict__ Mn, const double* __restrict__ detr, DevOffsets off) {
+         double* __restrict__ Mn, const double* __restrict__ detr, DevOffsets off, const int* __restrict__ lev,
+         double side) {
+    // FP32 form (pos32 given): moments in the leaf's scaled units,
+    // Mt_m = sum_a q_a (-(x_a - z)/h)^m with h = side / 2^level
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
     constexpr int KC = (NCOL + 31) / 32;
@@ -73,13 +79,15 @@ k_ad_p2m(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
     }
     double cx = 0.0, cy = 0.0, cz = 0.0;
     if (!pos32) { cx = zc[3 * c]; cy = zc[3 * c + 1]; cz = zc[3 * c + 2]; }
+    const float hinv = pos32 ? (float)ldexp(1.0 / side, lev[c]) : 1.f;
     for (int a0 = b; a0 < e; a0 += 32) {
         const int a = a0 + lane;
         __syncwarp();
         if (a < e) {
             if (pos32) {
                 const float4 v = pos32[a];
-                sx[w][lane] = T(-v.x); sy[w][lane] = T(-v.y); sz[w][lane] = T(-v.z); sq[w][lane] = T(v.w);
+                sx[w][lane] = T(-v.x * hinv); sy[w][lane] = T(-v.y * hinv); sz[w][lane] = T(-v.z * hinv);
+                sq[w][lane] = T(v.w);
             } else {
                 sx[w][lane] = T(cx - xs[a]); sy[w][lane] = T(cy - ys[a]); sz[w][lane] = T(cz - zs[a]);
                 sq[w][lane] = T(qs[a]);
@@ -143,7 +151,10 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
          const double* __restrict__ zc, const double* __restrict__ xs, const double* __restrict__ ys,
          const double* __restrict__ zs, const float4* __restrict__ pos32, const int* __restrict__ perm,
          const double* __restrict__ Ln, const double* __restrict__ expand, DevOffsets off,
-         double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az) {
+         double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az,
+         const int* __restrict__ lev, double side) {
+    // FP32 form (pos32 given): scaled units of the leaf, Lt_n = L_n h^(|n|+1):
+    // Phi = (1/h) sum_k (r/h)^k/k! Lt_k, grad = (1/h^2) sum_k (r/h)^k/k! Lt_{k+e_i}
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NT = (P + 1) * (P + 1);
     __shared__ double sA[WARPS][NT];
@@ -172,6 +183,8 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
     __syncwarp();
     double cx = 0.0, cy = 0.0, cz = 0.0;
     if (!pos32) { cx = zc[3 * c]; cy = zc[3 * c + 1]; cz = zc[3 * c + 2]; }
+    const double hinv_d = pos32 ? ldexp(1.0 / side, lev[c]) : 1.0;
+    const float hinv = (float)hinv_d;
     const T* L = sL[w];
     for (int a0 = b; a0 < e; a0 += 32) {
         const int a = a0 + lane;
@@ -179,7 +192,7 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
         T rx, ry, rz;
         if (pos32) {
             const float4 v = pos32[a];
-            rx = T(v.x); ry = T(v.y); rz = T(v.z);
+            rx = T(v.x * hinv); ry = T(v.y * hinv); rz = T(v.z * hinv);
         } else {
             rx = T(xs[a] - cx); ry = T(ys[a] - cy); rz = T(zs[a] - cz);
         }
@@ -212,10 +225,10 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
             ph += fx[kx] * xp; gx += fx[kx] * xgx; gy += fx[kx] * xgy; gz += fx[kx] * xgz;
         }
         const int o = perm[a];
-        pot[o] = -(double)ph;
-        ax[o] = (double)gx;
-        ay[o] = (double)gy;
-        az[o] = (double)gz;
+        pot[o] = -(double)ph * hinv_d;
+        ax[o] = (double)gx * hinv_d * hinv_d;
+        ay[o] = (double)gy * hinv_d * hinv_d;
+        az[o] = (double)gz * hinv_d * hinv_d;
     }
 }
 
@@ -359,14 +372,14 @@ int ad_icentre(int nn, const int* lev, const int* ix, const int* iy, const int* 
 
 int ad_p2m_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
                 const double* zc, const double* xs, const double* ys, const double* zs, const double* qs,
-                const float4* pos32, double* Mn, const DevTables& Tb, cudaStream_t s) {
+                const float4* pos32, double* Mn, const DevTables& Tb, const int* lev, double side, cudaStream_t s) {
     if (nleaf <= 0) return 0;
     constexpr int W = 4;
     const unsigned g = (unsigned)((nleaf + W - 1) / W);
 #define C64(P) k_ad_p2m<P, double, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, qs, nullptr, \
-                                                            Mn, Tb.detr, Tb.offsets())
+                                                            Mn, Tb.detr, Tb.offsets(), lev, side)
 #define C32(P) k_ad_p2m<P, float, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, qs, pos32, \
-                                                           Mn, Tb.detr, Tb.offsets())
+                                                           Mn, Tb.detr, Tb.offsets(), lev, side)
     if (prec == 0) { AD_P_SWITCH(p, C64) } else { AD_P_SWITCH(p, C32) }
 #undef C64
 #undef C32
@@ -377,14 +390,16 @@ int ad_p2m_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const in
 int ad_l2p_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const int* nb, const int* ne,
                 const double* zc, const double* xs, const double* ys, const double* zs, const float4* pos32,
                 const int* perm, const double* Ln, const DevTables& Tb, double* pot, double* ax, double* ay,
-                double* az, cudaStream_t s) {
+                double* az, const int* lev, double side, cudaStream_t s) {
     if (nleaf <= 0) return 0;
     constexpr int W = 4;
     const unsigned g = (unsigned)((nleaf + W - 1) / W);
 #define C64(P) k_ad_l2p<P, double, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, nullptr, \
-                                                            perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az)
+                                                            perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az, \
+                                                            lev, side)
 #define C32(P) k_ad_l2p<P, float, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, pos32, \
-                                                           perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az)
+                                                           perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az, \
+                                                           lev, side)
     if (prec == 0) { AD_P_SWITCH(p, C64) } else { AD_P_SWITCH(p, C32) }
 #undef C64
 #undef C32

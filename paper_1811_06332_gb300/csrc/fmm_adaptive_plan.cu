@@ -236,6 +236,7 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         cudaMemcpyAsync(&side, a->box + 3, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
         a->scale32 = (float)(side / 4194304.0);
+        a->side = side;
     }
     GROW(a->M, a->cap_M, (size_t)a->nn * nc * 8);
     GROW(a->L, a->cap_L, (size_t)a->nn * nc * 8);
@@ -246,14 +247,14 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
 int ad_run_p2m(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s) {
     if (a->n == 0) return 0;
     ad_p2m_leaf(prec, p, basis, a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs, a->pos32, a->M,
-                T, s);
+                T, a->lev, a->side, s);
     return 0;
 }
 
 int ad_run_m2m(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s) {
     if (a->n == 0) return 0;
     for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
-        ad_m2m(prec, p, basis, a->lvl[L], a->lvl[L + 1], a->child0, a->nchild, a->zc, a->M, T, s);
+        ad_m2m(prec, p, basis, a->lvl[L], a->lvl[L + 1], a->child0, a->nchild, a->zc, a->M, T, a->lev, a->side, s);
     return 0;
 }
 
@@ -303,7 +304,7 @@ int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s) 
 int ad_run_l2l(AdState* a, int prec, int p, int basis, const DevTables& T, cudaStream_t s) {
     if (a->n == 0) return 0;
     for (int L = 1; L + 1 < (int)a->lvl.size(); ++L)
-        ad_l2l(prec, p, basis, a->lvl[L], a->lvl[L + 1], a->parent, a->zc, a->L, T, s);
+        ad_l2l(prec, p, basis, a->lvl[L], a->lvl[L + 1], a->parent, a->zc, a->L, T, a->lev, a->side, s);
     return 0;
 }
 
@@ -311,7 +312,7 @@ int ad_run_l2p(AdState* a, int prec, int p, int basis, const DevTables& T, doubl
                cudaStream_t s) {
     if (a->n == 0) return 0;
     ad_l2p_leaf(prec, p, basis, a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->pos32, a->perm, a->L,
-                T, pot, ax, ay, az, s);
+                T, pot, ax, ay, az, a->lev, a->side, s);
     return 0;
 }
 

@@ -23,12 +23,15 @@ namespace fmm {
 // ---------------------------------------------------------------------------
 // node data: shape terms of the multipole (ranks 1..4), ln count, radius
 // ---------------------------------------------------------------------------
+// (multipoles of FP32 plans are stored in the cell's scaled units,
+// Mt_m = M_m / h^|m|: the ratio then uses r / h in place of r)
 __global__ void k_node_feat(int nn, int ld, const double* __restrict__ Mn, const double* __restrict__ rad,
-                            const int* __restrict__ nb, const int* __restrict__ ne, float* __restrict__ nodeF) {
+                            const int* __restrict__ nb, const int* __restrict__ ne, const int* __restrict__ lev,
+                            int scaled, double side, float* __restrict__ nodeF) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nn) return;
     const double* M = Mn + (int64_t)c * ld;
-    const double m0 = fabs(M[0]), r = rad[c];
+    const double m0 = fabs(M[0]), r = scaled ? rad[c] * ldexp(1.0 / side, lev[c]) : rad[c];
     float out[8];
     double rj = 1.0;
     for (int j = 1; j <= 4; ++j) {
@@ -45,7 +48,7 @@ __global__ void k_node_feat(int nn, int ld, const double* __restrict__ Mn, const
         out[j - 1] = (float)log(g > 1e-6 ? g : 1e-6);
     }
     out[4] = logf((float)(ne[c] - nb[c]));
-    out[5] = (float)r;
+    out[5] = (float)rad[c];
     out[6] = 0.f;
     out[7] = 0.f;
     float4* o = (float4*)(nodeF + 8 * (int64_t)c);
@@ -330,7 +333,8 @@ __global__ void k_mlp_adam(float* __restrict__ prm, const float* __restrict__ gr
 // ---------------------------------------------------------------------------
 int ad_node_features(AdState* a, cudaStream_t s) {
     if (a->nn <= 0) return 0;
-    k_node_feat<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->nc, a->M, a->rad, a->nb, a->ne, a->nodeF);
+    k_node_feat<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->nc, a->M, a->rad, a->nb, a->ne, a->lev,
+                                                    a->pos32 ? 1 : 0, a->side, a->nodeF);
     count_launch();
     return 0;
 }

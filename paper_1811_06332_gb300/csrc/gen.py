@@ -629,8 +629,12 @@ def emit_list_file(p, basis, T):
         L.append("    const double tx = zc[3 * t], ty = zc[3 * t + 1], tz = zc[3 * t + 2];")
     else:
         # centre offsets from the integer node centres: exact integer
-        # difference, one FP32 rounding (no FP64 arithmetic per pair)
+        # difference, one FP32 rounding (no FP64 arithmetic per pair).
+        # Scaled units (FP32 form): Mt_A = M_A / h_A^|m|, Lt_B = L_B h_B^(|n|+1),
+        # so Lt_n = sum_m (h_A/h_B)^|m| Mt_m/m! D_{n+m}(d/h_B); h_c = side/2^level,
+        # d/h_B = (ic_B - ic_A) 2^(level_B - 22), h_A/h_B = 2^(level_B - level_A).
         L.append("    const int4 it = ic[t];")
+        L.append("    const T sB = ldexpf(1.0f, it.w - 22);")
     for a in range(nc):
         L.append("    T a%d = T(0);" % a)
     L.append("    for (int k = off[t]; k < off[t + 1]; ++k) {")
@@ -639,13 +643,17 @@ def emit_list_file(p, basis, T):
         L.append("      const T x = T(tx - zc[3 * s]), y = T(ty - zc[3 * s + 1]), z = T(tz - zc[3 * s + 2]);")
     else:
         L.append("      const int4 is = ic[s];")
-        L.append("      const T x = T(it.x - is.x) * scale, y = T(it.y - is.y) * scale, z = T(it.z - is.z) * scale;")
+        L.append("      const T x = T(it.x - is.x) * sB, y = T(it.y - is.y) * sB, z = T(it.z - is.z) * sB;")
+        L.append("      const T rho = ldexpf(1.0f, it.w - is.w);")
+        L.append("      T rp = T(1);")
     L.append("      const T* __restrict__ Ms = Mn + (int64_t)s * ld;")
     L.append("      T d[%d];" % ns(p))
     L.append("  " + gen_dtensor(p).replace("\n", "\n  "))
     for b in range(p + 1):
         blk = rank_sym(b)
         L.append("      {")
+        if T == "float" and b > 0:
+            L.append("        rp *= rho;")
         for m in blk:
             if basis == 0:
                 L.append("        const T m_%d_%d_%d = Ms[%d];" % (m + (pos[m],)))
@@ -660,6 +668,8 @@ def emit_list_file(p, basis, T):
                 continue
             f = mfact(m)
             mc = "m_%d_%d_%d" % m if f == 1 else "(m_%d_%d_%d * %s)" % (m + (lit(Fraction(1, f)),))
+            if T == "float" and b > 0:
+                mc = "(%s * rp)" % mc
             L.append("        { const T c = %s;" % mc)
             for a, n in users:
                 L.append("          a%d = fma(c, d[%d], a%d);" % (a, pos[add(n, m)], a))

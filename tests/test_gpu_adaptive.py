@@ -105,3 +105,20 @@ def test_plummer_large_fp32_sampled(F):
     assert st["m2l_pairs"] == ost["m2l_pairs"] and st["p2p_pairs"] == ost["p2p_pairs"]
     ep, ea = errs(res[0][s], res[1][:, s], pref, aref)
     assert ep < 5e-6 and ea < 5e-6, (ep, ea)
+
+
+@pytest.mark.parametrize("p,basis", [(10, 0), (8, 1)])
+def test_fp32_high_order_deep_tree(F, p, basis):
+    """Deep cells (blobs of sigma 0.005, 2^17 particles, 8 per leaf) at high
+    order: in physical units D_k(r) ~ |k|!/r^(|k|+1) leaves the FP32 range,
+    the scaled units of the FP32 form keep it finite and at FP32 accuracy
+    against the FP64 form on the same tree."""
+    n = 131072
+    x, y, z = inputs.blobs(n, 9, sigma_lo=0.005, sigma_hi=0.006)
+    q = inputs.masses_equal(n)
+    (r32,), st32 = run(F, x, y, z, q, p, basis, F.FP32, 8, 0.5)
+    (r64,), st64 = run(F, x, y, z, q, p, basis, F.FP64, 8, 0.5)
+    assert st32["levels"] >= 10   # cells of side <= 2^-10
+    assert np.all(np.isfinite(r32[0])) and np.all(np.isfinite(r32[1]))
+    ep, ea = errs(r32[0], r32[1], r64[0], r64[1])
+    assert ep < 2e-6 and ea < 2e-5, (ep, ea)
