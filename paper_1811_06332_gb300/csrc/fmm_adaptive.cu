@@ -662,6 +662,17 @@ int ad_leaf_keys(int nn, const int* nchild, const int* nb, uint64_t* key, int* v
     count_launch();
     return 0;
 }
+__global__ void k_f64_to_f32_rows(int64_t rows, int nc, int ldm, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * ldm) return;
+    const int64_t r = t / ldm;
+    const int j = (int)(t % ldm);
+    b[t] = j < nc ? (float)a[r * nc + j] : 0.f;
+}
+int ad_to_f32_rows(int64_t rows, int nc, int ldm, const double* a, float* b, cudaStream_t s) {
+    if (rows > 0) { k_f64_to_f32_rows<<<G256(rows * ldm)>>>(rows, nc, ldm, a, b); count_launch(); }
+    return 0;
+}
 int ad_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
     if (n) { k_f64_to_f32<<<G256(n)>>>(n, a, b); count_launch(); }
     return 0;

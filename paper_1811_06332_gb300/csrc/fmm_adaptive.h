@@ -116,8 +116,11 @@ int ad_p2p(int nwork, const int* work, const int* off, const int* src, const int
            const int* perm, double* pot, double* ax, double* ay, double* az, int* counter, int blocks,
            cudaStream_t s);
 int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off, const int* src,
-                    const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld, int accum,
-                    int* counter, int blocks, cudaStream_t s);
+                    const double* zc, const int4* ic, float scale, const void* M, int ldm, double* Ln, int ld,
+                    int accum, int* counter, int blocks, cudaStream_t s);
+// FP32 multipole rows are padded to a multiple of 4 floats (16-byte loads)
+inline int ld32_of(int nc) { return (nc + 3) & ~3; }
+int ad_to_f32_rows(int64_t rows, int nc, int ldm, const double* a, float* b, cudaStream_t s);
 
 // fmm_adaptive_leaf.cu
 int ad_pos32(int nleaf, const int* leaf, const int* nb, const int* ne, const double* zc, const double* xs,

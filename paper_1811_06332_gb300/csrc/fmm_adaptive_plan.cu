@@ -240,7 +240,7 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
     }
     GROW(a->M, a->cap_M, (size_t)a->nn * nc * 8);
     GROW(a->L, a->cap_L, (size_t)a->nn * nc * 8);
-    if (prec != 0) GROW(a->M32, a->cap_M32, (size_t)a->nn * nc * 4);
+    if (prec != 0) GROW(a->M32, a->cap_M32, (size_t)a->nn * ld32_of(nc) * 4);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -262,13 +262,13 @@ static int m2l_launch(AdState* a, int p, int basis, int prec, int blocks, cudaSt
     cudaMemsetAsync(a->counter, 0, 4, s);
     const void* M = prec ? (const void*)a->M32 : (const void*)a->M;
     return launch_m2l_list(p, basis, prec ? 1 : 0, a->ntarg, a->order, a->moff, a->msrc, a->zc, a->ic, a->scale32, M,
-                           a->L, a->nc, 0, a->counter, blocks, s);
+                           prec ? ld32_of(a->nc) : a->nc, a->L, a->nc, 0, a->counter, blocks, s);
 }
 
 int ad_run_m2l(AdState* a, int p, int basis, int prec, int sms, cudaStream_t s) {
     if (a->n == 0) return 0;
     cudaMemsetAsync(a->L, 0, (size_t)a->nn * a->nc * 8, s);
-    if (prec) ad_to_f32((int64_t)a->nn * a->nc, a->M, a->M32, s);
+    if (prec) ad_to_f32_rows(a->nn, a->nc, ld32_of(a->nc), a->M, a->M32, s);
     if (a->ntarg == 0) return 0;
     if (a->m2l_blocks == 0) {
         // autotune the persistent grid on the first evaluation: candidates of
@@ -355,7 +355,7 @@ int ad_run_m2l_orders(AdState* a, int p, int basis, int prec, int sms, const uns
                       cudaStream_t s) {
     if (a->n == 0) return 0;
     cudaMemsetAsync(a->L, 0, (size_t)a->nn * a->nc * 8, s);
-    if (prec) ad_to_f32((int64_t)a->nn * a->nc, a->M, a->M32, s);
+    if (prec) ad_to_f32_rows(a->nn, a->nc, ld32_of(a->nc), a->M, a->M32, s);
     if (a->nm2l == 0) return 0;
     if (!a->orders_fixed) {
         ad_node_features(a, s);
@@ -372,7 +372,7 @@ int ad_run_m2l_orders(AdState* a, int p, int basis, int prec, int sms, const uns
     const int blocks = a->m2l_blocks > 0 ? a->m2l_blocks : 2 * sms;
     for (int q = 0; q < nb; ++q)
         launch_m2l_list(q, basis, prec ? 1 : 0, a->nn, a->iota, a->boff + (size_t)q * a->nn, a->bsrc, a->zc, a->ic,
-                        a->scale32, M, a->L, a->nc, 1, a->counter + 2 + q, blocks, s);
+                        a->scale32, M, prec ? ld32_of(a->nc) : a->nc, a->L, a->nc, 1, a->counter + 2 + q, blocks, s);
     return 0;
 }
 

@@ -613,8 +613,8 @@ def emit_list_file(p, basis, T):
          "__global__ void __launch_bounds__(128)",
          "m2l_list_p%d_b%d_%s(int ntarg, const int* __restrict__ order, const int* __restrict__ off,"
          " const int* __restrict__ src, const double* __restrict__ zc, const int4* __restrict__ ic, float scale,"
-         " const %s* __restrict__ Mn, double* __restrict__ Ln, int ld, int accum, int* __restrict__ counter) {"
-         % (p, basis, T, T),
+         " const %s* __restrict__ Mn, int ldm, double* __restrict__ Ln, int ld, int accum,"
+         " int* __restrict__ counter) {" % (p, basis, T, T),
          "  typedef %s T;" % T,
          "  const int lane = threadIdx.x & 31;",
          "  for (;;) {",
@@ -646,7 +646,11 @@ def emit_list_file(p, basis, T):
         L.append("      const T x = T(it.x - is.x) * sB, y = T(it.y - is.y) * sB, z = T(it.z - is.z) * sB;")
         L.append("      const T rho = ldexpf(1.0f, it.w - is.w);")
         L.append("      T rp = T(1);")
-    L.append("      const T* __restrict__ Ms = Mn + (int64_t)s * ld;")
+    if T == "double":
+        L.append("      const T* __restrict__ Ms = Mn + (int64_t)s * ldm;")
+    else:
+        # FP32 multipoles sit in rows padded to a multiple of 4: 16-byte loads
+        L.append("      const float4* __restrict__ Mv = (const float4*)(Mn + (int64_t)s * ldm);")
     L.append("      T d[%d];" % ns(p))
     L.append("  " + gen_dtensor(p).replace("\n", "\n  "))
     for b in range(p + 1):
@@ -654,11 +658,18 @@ def emit_list_file(p, basis, T):
         L.append("      {")
         if T == "float" and b > 0:
             L.append("        rp *= rho;")
+        stored = [pos[m] for m in blk] if basis == 0 else [tpos[m] for m in blk if m[2] <= 1]
+        if T == "float":
+            for qv in range(min(stored) // 4, max(stored) // 4 + 1):
+                L.append("        const float4 q%d = Mv[%d];" % (qv, qv))
+
+        def mload(i):
+            return ("q%d.%s" % (i // 4, "xyzw"[i % 4])) if T == "float" else ("Ms[%d]" % i)
         for m in blk:
             if basis == 0:
-                L.append("        const T m_%d_%d_%d = Ms[%d];" % (m + (pos[m],)))
+                L.append("        const T m_%d_%d_%d = %s;" % (m + (mload(pos[m]),)))
             elif m[2] <= 1:
-                L.append("        const T m_%d_%d_%d = Ms[%d];" % (m + (tpos[m],)))
+                L.append("        const T m_%d_%d_%d = %s;" % (m + (mload(tpos[m]),)))
             else:
                 L.append("        const T m_%d_%d_%d = -m_%d_%d_%d - m_%d_%d_%d;" % (
                     m + (m[0] + 2, m[1], m[2] - 2) + (m[0], m[1] + 2, m[2] - 2)))
@@ -687,10 +698,10 @@ def emit_list_file(p, basis, T):
     L.append("  }")
     L.append("}")
     L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
-             " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld, int accum,"
-             " int* counter, int blocks, cudaStream_t s) {" % (p, basis, T))
+             " const double* zc, const int4* ic, float scale, const void* M, int ldm, double* Ln, int ld,"
+             " int accum, int* counter, int blocks, cudaStream_t s) {" % (p, basis, T))
     L.append("  m2l_list_p%d_b%d_%s<<<blocks, 128, 0, s>>>(ntarg, order, off, src, zc, ic, scale, (const %s*)M,"
-             " Ln, ld, accum, counter);" % (p, basis, T, T))
+             " ldm, Ln, ld, accum, counter);" % (p, basis, T, T))
     L.append("  return 0;")
     L.append("}")
     L.append("}  // namespace fmm")
@@ -704,16 +715,16 @@ def emit_list_dispatch():
         for b in (0, 1):
             for T in ("float", "double"):
                 L.append("int launch_m2l_list_p%d_b%d_%s(int ntarg, const int* order, const int* off, const int* src,"
-                         " const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld,"
-                         " int accum, int* counter, int blocks, cudaStream_t s);" % (p, b, T))
+                         " const double* zc, const int4* ic, float scale, const void* M, int ldm, double* Ln,"
+                         " int ld, int accum, int* counter, int blocks, cudaStream_t s);" % (p, b, T))
     L.append("int launch_m2l_list(int p, int basis, int prec, int ntarg, const int* order, const int* off,"
-             " const int* src, const double* zc, const int4* ic, float scale, const void* M, double* Ln, int ld,"
-             " int accum, int* counter, int blocks, cudaStream_t s) {")
+             " const int* src, const double* zc, const int4* ic, float scale, const void* M, int ldm, double* Ln,"
+             " int ld, int accum, int* counter, int blocks, cudaStream_t s) {")
     for p in range(PMAX + 1):
         for b in (0, 1):
             for k, T in ((0, "double"), (1, "float")):
                 L.append("  if (p == %d && basis == %d && prec == %d) return launch_m2l_list_p%d_b%d_%s(ntarg, order,"
-                         " off, src, zc, ic, scale, M, Ln, ld, accum, counter, blocks, s);" % (p, b, k, p, b, T))
+                         " off, src, zc, ic, scale, M, ldm, Ln, ld, accum, counter, blocks, s);" % (p, b, k, p, b, T))
     L.append("  return -1;")
     L.append("}")
     L.append("}  // namespace fmm")
