@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_ad_p2m(int basis, int nleaf, const int* __restrict__ leaf, const int* __restrict__ nb, const int* __restrict__ ne,
          const double* __restrict__ zc, const double* __restrict__ xs, const double* __restrict__ ys,
          const double* __restrict__ zs, const double* __restrict__ qs, const float4* __restrict__ pos32,
-         double* __restrict__ Mn, const double* __restrict__ detr, DevOffsets off, const int* __restrict__ lev,
+         double* __restrict__ Mn, const T* __restrict__ detr, DevOffsets off, const int* __restrict__ lev,
          double side) {
     // FP32 form (pos32 given): moments in the leaf's scaled units,
     // Mt_m = sum_a q_a (-(x_a - z)/h)^m with h = side / 2^level
@@ -58,7 +58,7 @@ k_ad_p2m(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
     constexpr int KC = (NCOL + 31) / 32;
     __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
-    __shared__ double sA[WARPS][NS];
+    __shared__ T sA[WARPS][NS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x * WARPS + w;
     if (k >= nleaf) return;
@@ -118,12 +118,12 @@ k_ad_p2m(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
             const int rem = P - cnx[kk] - cny[kk];
 #pragma unroll
             for (int j = 0; j <= P; ++j)
-                if (j <= rem) sA[w][pos_sym(cnx[kk], cny[kk], j)] = (double)acc[kk][j];
+                if (j <= rem) sA[w][pos_sym(cnx[kk], cny[kk], j)] = acc[kk][j];
         }
     }
     __syncwarp();
     if (!basis) {
-        for (int s = lane; s < NS; s += 32) Mn[(int64_t)c * NS + s] = sA[w][s];
+        for (int s = lane; s < NS; s += 32) Mn[(int64_t)c * NS + s] = (double)sA[w][s];
         return;
     }
     constexpr int NT = (P + 1) * (P + 1);
@@ -132,11 +132,11 @@ k_ad_p2m(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
         const int j = nx + c_tl_idx[t][1] + nz;
         const int cols = (j + 1) * (j + 2) / 2;
         const int row = (j - nx) * (j - nx + 1) / 2 + nz;
-        const double* R = detr + off.detr[j] + row * cols;
-        const double* As = &sA[w][ns_of(j - 1)];
-        double v = 0.0;
+        const T* R = detr + off.detr[j] + row * cols;
+        const T* As = &sA[w][ns_of(j - 1)];
+        T v = T(0);
         for (int s = 0; s < cols; ++s) v += R[s] * As[s];
-        Mn[(int64_t)c * NT + t] = v;
+        Mn[(int64_t)c * NT + t] = (double)v;
     }
 }
 
@@ -150,14 +150,14 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restrict__ nb, const int* __restrict__ ne,
          const double* __restrict__ zc, const double* __restrict__ xs, const double* __restrict__ ys,
          const double* __restrict__ zs, const float4* __restrict__ pos32, const int* __restrict__ perm,
-         const double* __restrict__ Ln, const double* __restrict__ expand, DevOffsets off,
+         const double* __restrict__ Ln, const T* __restrict__ expand, DevOffsets off,
          double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az,
          const int* __restrict__ lev, double side) {
     // FP32 form (pos32 given): scaled units of the leaf, Lt_n = L_n h^(|n|+1):
     // Phi = (1/h) sum_k (r/h)^k/k! Lt_k, grad = (1/h^2) sum_k (r/h)^k/k! Lt_{k+e_i}
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NT = (P + 1) * (P + 1);
-    __shared__ double sA[WARPS][NT];
+    __shared__ T sA[WARPS][NT];
     __shared__ T sL[WARPS][NS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x * WARPS + w;
@@ -166,16 +166,16 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
     const int b = nb[c], e = ne[c];
     if (b == e) return;
     if (basis) {
-        for (int t = lane; t < NT; t += 32) sA[w][t] = Ln[(int64_t)c * NT + t];
+        for (int t = lane; t < NT; t += 32) sA[w][t] = T(Ln[(int64_t)c * NT + t]);
         __syncwarp();
         for (int s = lane; s < NS; s += 32) {
             const int nx = c_sym_idx[s][0], nz = c_sym_idx[s][2];
             const int j = nx + c_sym_idx[s][1] + nz;
             const int row = (j - nx) * (j - nx + 1) / 2 + nz;
-            const double* E = expand + off.expand[j] + row * (2 * j + 1);
-            double v = 0.0;
+            const T* E = expand + off.expand[j] + row * (2 * j + 1);
+            T v = T(0);
             for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][j * j + t];
-            sL[w][s] = T(v);
+            sL[w][s] = v;
         }
     } else {
         for (int s = lane; s < NS; s += 32) sL[w][s] = T(Ln[(int64_t)c * NS + s]);
@@ -379,7 +379,7 @@ int ad_p2m_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const in
 #define C64(P) k_ad_p2m<P, double, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, qs, nullptr, \
                                                             Mn, Tb.detr, Tb.offsets(), lev, side)
 #define C32(P) k_ad_p2m<P, float, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, qs, pos32, \
-                                                           Mn, Tb.detr, Tb.offsets(), lev, side)
+                                                           Mn, Tb.detr32, Tb.offsets(), lev, side)
     if (prec == 0) { AD_P_SWITCH(p, C64) } else { AD_P_SWITCH(p, C32) }
 #undef C64
 #undef C32
@@ -398,7 +398,7 @@ int ad_l2p_leaf(int prec, int p, int basis, int nleaf, const int* leaf, const in
                                                             perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az, \
                                                             lev, side)
 #define C32(P) k_ad_l2p<P, float, W><<<g, W * 32, 0, s>>>(basis, nleaf, leaf, nb, ne, zc, xs, ys, zs, pos32, \
-                                                           perm, Ln, Tb.expand, Tb.offsets(), pot, ax, ay, az, \
+                                                           perm, Ln, Tb.expand32, Tb.offsets(), pot, ax, ay, az, \
                                                            lev, side)
     if (prec == 0) { AD_P_SWITCH(p, C64) } else { AD_P_SWITCH(p, C32) }
 #undef C64

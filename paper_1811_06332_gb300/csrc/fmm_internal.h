@@ -18,6 +18,9 @@ struct DevTables {
     double* detr = nullptr;
     double* expand = nullptr;
     double* reduce = nullptr;
+    float* detr32 = nullptr;     // FP32 copies (FP32 forms)
+    float* expand32 = nullptr;
+    float* reduce32 = nullptr;
     int detr_off[FMM_PMAX + 2];
     int expand_off[FMM_PMAX + 2];
     int reduce_off[FMM_PMAX + 2];

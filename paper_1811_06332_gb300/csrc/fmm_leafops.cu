@@ -19,12 +19,12 @@ template <int P, typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
            const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
-           double* __restrict__ M, const double* __restrict__ reduce, DevOffsets off,
+           double* __restrict__ M, const T* __restrict__ reduce, DevOffsets off,
            const float4* __restrict__ pos32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
     __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
-    __shared__ double sA[WARPS][NS];
+    __shared__ T sA[WARPS][NS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * WARPS + w;
     if (c >= nleaf) return;
@@ -91,23 +91,24 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
             const int rem = P - cnx[k] - cny[k];
 #pragma unroll
             for (int j = 0; j <= P; ++j)
-                if (j <= rem) sA[w][pos_sym(cnx[k], cny[k], j)] = (double)acc[k][j];
+                if (j <= rem) sA[w][pos_sym(cnx[k], cny[k], j)] = acc[k][j];
         }
     }
     __syncwarp();
     if (!basis) {
-        for (int s = lane; s < NS; s += 32) M[(int64_t)s * nleaf + c] = sA[w][s];
+        for (int s = lane; s < NS; s += 32) M[(int64_t)s * nleaf + c] = (double)sA[w][s];
         return;
     }
+    // reduced representative, in the arithmetic type (FP32 tables for the FP32 form)
     constexpr int NT = (P + 1) * (P + 1);
     for (int t = lane; t < NT; t += 32) {
         const int j = c_tl_idx[t][0] + c_tl_idx[t][1] + c_tl_idx[t][2];
         const int cols = (j + 1) * (j + 2) / 2;
-        const double* R = reduce + off.reduce[j] + (t - j * j) * cols;
-        const double* As = &sA[w][ns_of(j - 1)];
-        double v = 0.0;
+        const T* R = reduce + off.reduce[j] + (t - j * j) * cols;
+        const T* As = &sA[w][ns_of(j - 1)];
+        T v = T(0);
         for (int s = 0; s < cols; ++s) v += R[s] * As[s];
-        M[(int64_t)t * nleaf + c] = v;
+        M[(int64_t)t * nleaf + c] = (double)v;
     }
 }
 
@@ -121,11 +122,11 @@ template <int P, typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
             const double* __restrict__ ys, const double* __restrict__ zs, const int* __restrict__ perm,
-            const double* __restrict__ Lt, const double* __restrict__ expand, DevOffsets off,
+            const double* __restrict__ Lt, const T* __restrict__ expand, DevOffsets off,
             double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az,
             const float4* __restrict__ pos32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
-    __shared__ double sA[WARPS][NS];
+    __shared__ T sA[WARPS][NS];
     __shared__ T sL[WARPS][NS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * WARPS + w;
@@ -134,16 +135,16 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
     if (b == e) return;
     if (basis) {
         constexpr int NT = (P + 1) * (P + 1);
-        for (int t = lane; t < NT; t += 32) sA[w][t] = Lt[(int64_t)t * nleaf + c];
+        for (int t = lane; t < NT; t += 32) sA[w][t] = T(Lt[(int64_t)t * nleaf + c]);
         __syncwarp();
         for (int s = lane; s < NS; s += 32) {
             const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
             const int j = nx + ny + nz;
             const int row = (j - nx) * (j - nx + 1) / 2 + nz;
-            const double* E = expand + off.expand[j] + row * (2 * j + 1);
-            double v = 0.0;
+            const T* E = expand + off.expand[j] + row * (2 * j + 1);
+            T v = T(0);
             for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][j * j + t];
-            sL[w][s] = T(v);
+            sL[w][s] = v;
         }
     } else {
         for (int s = lane; s < NS; s += 32) sL[w][s] = T(Lt[(int64_t)s * nleaf + c]);
@@ -280,13 +281,21 @@ k_p2p_leaf2(int depth, int64_t nleaf, const int* __restrict__ start, const doubl
     }
 }
 
+template <typename T>
+static const T* tab_of(const double* d, const float* f);
+template <>
+const double* tab_of<double>(const double* d, const float*) { return d; }
+template <>
+const float* tab_of<float>(const double*, const float* f) { return f; }
+
 template <int P, typename T>
 static void p2m_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
                        const double* zs, const double* qs, double* M, const DevTables& Tb, cudaStream_t s,
                        const float4* pos32) {
     constexpr int W = 4;
     k_p2m_leaf<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(basis, depth, nleaf, start, xs, ys, zs,
-                                                                           qs, M, Tb.reduce, Tb.offsets(), pos32);
+                                                                           qs, M, tab_of<T>(Tb.reduce, Tb.reduce32),
+                                                                           Tb.offsets(), pos32);
 }
 template <int P, typename T>
 static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
@@ -294,7 +303,8 @@ static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, co
                        double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32) {
     constexpr int W = 4;
     k_l2p_leaf2<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(
-        basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb.expand, Tb.offsets(), pot, ax, ay, az, pos32);
+        basis, depth, nleaf, start, xs, ys, zs, perm, Lt, tab_of<T>(Tb.expand, Tb.expand32), Tb.offsets(), pot, ax,
+        ay, az, pos32);
 }
 
 #define FMM_P_SWITCH(P_, CALL) \
