@@ -274,22 +274,27 @@ int64_t fmm_kernel_launches(void);
  *   a = max(r_A/|d|, 1e-6), b = max(r_B/|d|, 1e-6); f0 = ln(a+b) (the MAC
  *   ratio, App. C), f1 = ln a, f2 = ln b; f3..f6 = ln max(|M_A^(j)| /
  *   (|M_A,0| r_A^j), 1e-6) for j = 1..4 with |M^(j)|^2 = sum_{|m|=j} j!/m!
- *   M_m^2; f7, f8 = the same for M_B, j = 1, 2; f9 = ln n_A; f10 = ln n_B.
+ *   M_m^2; f7, f8 = the same for M_B, j = 1, 2; f9 = ln n_A; f10 = ln n_B;
+ *   f11 = ln max(g_AB / T_B, 1e-12), the pair's share of a far-field
+ *   magnitude estimate: g_AB = |M_A,0| / |d|^2, T_B = the sum of g over the
+ *   M2L lists of B and of all its ancestors.
  * Label of a pair at order q (q = 2..10): log10 max(e_q, 1e-12), e_q the
- * relative force error of the pair's order-q M2L + L2P (Eqs. M2L, L2P) at
- * up to 64 particles of B (all when n_B <= 64, else sorted positions
- * b_B + floor(j n_B / 64)) against the direct sum over A's particles.
+ * force error of the pair's order-q M2L + L2P (Eqs. M2L, L2P) at up to 64
+ * particles of B (all when n_B <= 64, else sorted positions
+ * b_B + floor(j n_B / 64)) against the direct sum over A's particles,
+ * relative to the total force at those particles (direct sum over all
+ * particles): sqrt(sum |g_q - g|^2 / sum |a|^2).
  *
- * Model: 11 -> 64 -> 64 -> 64 -> 9, ReLU; predicted log10 error at orders
- * 2..10.  Parameter blob (FMM_MLP_NBLOB floats): [0..8) header {6332, 1,
- * 11, 64, 9, 2, log10 kappa, 0}, [8..19) feature means, [19..30) feature
- * standard deviations, then W1 (64x11 row-major), b1, W2 (64x64), b2, W3,
+ * Model: 12 -> 64 -> 64 -> 64 -> 9, ReLU; predicted log10 error at orders
+ * 2..10.  Parameter blob (FMM_MLP_NBLOB floats): [0..8) header {6332, 2,
+ * 12, 64, 9, 2, log10 kappa, 0}, [8..20) feature means, [20..32) feature
+ * standard deviations, then W1 (64x12 row-major), b1, W2 (64x64), b2, W3,
  * b3, W4 (9x64), b4.  Inference rounds weights and the input of every layer
  * to BF16 (nearest even) and accumulates in FP32 on the tensor cores.
  * ------------------------------------------------------------------------- */
-#define FMM_MLP_NF 11
+#define FMM_MLP_NF 12
 #define FMM_MLP_NOUT 9
-#define FMM_MLP_NBLOB 9703
+#define FMM_MLP_NBLOB 9769
 
 /* M2L pair list of an adaptive plan after fmm_build_tree, grouped by target
  * (the order every per-pair array below uses): host arrays tgt[k], src[k]
@@ -300,14 +305,15 @@ int fmm_plan_pairs(fmm_plan* plan, int32_t* tgt, int32_t* src, int64_t cap, int6
 
 /* Features (device float [npair][FMM_MLP_NF]) and, when labels != NULL,
  * labels (device double [npair][FMM_MLP_NOUT]) of the plan's M2L pairs.
- * Runs P2M and M2M itself.  Labels need FMM_FP64, FMM_BASIS_SYM and p = 10;
- * features need p >= 4 and FMM_BASIS_SYM.  FMM_ERR_STATE before
+ * Runs P2M and M2M itself; labels also run an O(n^2) FP64 direct sum for
+ * the total forces, so they need n <= 2^18, FMM_FP64, FMM_BASIS_SYM and
+ * p = 10; features need p >= 4 and FMM_BASIS_SYM.  FMM_ERR_STATE before
  * fmm_build_tree. */
 int fmm_pair_data(fmm_plan* plan, float* feat, double* labels, void* stream);
 
-/* Mean squared error of the model over n samples (device feat [n][11],
- * labels [n][9], FP32) and its gradient with respect to blob[30..)
- * (host grad, FMM_MLP_NBLOB - 30 floats), in FP32.  Synchronous. */
+/* Mean squared error of the model over n samples (device feat [n][12],
+ * labels [n][9], FP32) and its gradient with respect to blob[32..)
+ * (host grad, FMM_MLP_NBLOB - 32 floats), in FP32.  Synchronous. */
 int fmm_mlp_grad(const float* blob, int64_t n, const float* feat, const float* labels, float* loss,
                  float* grad, void* stream);
 
@@ -323,7 +329,7 @@ int fmm_mlp_train(float* blob, int64_t n, const float* feat, const float* labels
                   int epochs, int batch, float lr, int fit_moments, float* loss_out, void* stream);
 
 /* BF16 tensor-core inference: pred (device float [n][9]) from feat (device
- * float [n][11]).  blob is host memory. */
+ * float [n][12]).  blob is host memory. */
 int fmm_mlp_predict(const float* blob, int64_t n, const float* feat, float* pred, void* stream);
 
 /* Gives a learned_p plan its model (host blob, copied).  Synchronous. */

@@ -94,7 +94,7 @@ def lib():
                                      _dp, _dp, _dp]
         L.orc_pair_error.restype = ctypes.c_double
         L.orc_adaptive_tree.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int64,
-                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_adaptive_tree.restype = ctypes.c_int64
         L.orc_ncols_labels.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
@@ -280,16 +280,17 @@ def fmm_adaptive(x, y, z, q, max_leaf: int, theta: float, p: int, basis: int, sa
     return pot, np.stack([ax, ay, az]), dict(zip(keys, st.tolist()))
 
 
-NFEAT = 11      # features per M2L pair (see fmm_oracle.c)
+NFEAT = 12      # features per M2L pair (see fmm_oracle.c)
 NLABEL = 9      # labels per pair: orders 2..10
 
 
 def adaptive_pairs(x, y, z, q, max_leaf: int, theta: float, features=True, labels=False):
     """M2L pairs of the adaptive tree, ordered by (target, source).
 
-    Returns (target, source) node indices and, on request, the (npair, 11)
-    features and (npair, 9) labels (log10 relative force error of the
-    pair's M2L at orders 2..10) defined in fmm_oracle.c."""
+    Returns (target, source) node indices and, on request, the (npair, 12)
+    features and (npair, 9) labels (log10 force error of the pair's M2L at
+    orders 2..10 relative to the total force at the target's particles)
+    defined in fmm_oracle.c."""
     x, y, z, q = (_f64(v) for v in (x, y, z, q))
     n = len(x)
     L = lib()
@@ -321,17 +322,19 @@ def pair_error(p, src_xyzq, zA, zB, targets):
     return e
 
 
-def adaptive_tree(x, y, z, max_leaf: int):
+def adaptive_tree(x, y, z, max_leaf: int, parents=False):
     """Nodes of the adaptive octree: (nn, 4) centre and radius, (nn, 2)
-    sorted-position ranges, and the sorted order of the particles."""
+    sorted-position ranges, the sorted order of the particles and, on
+    request, each node's parent (-1 for the root)."""
     x, y, z = (_f64(v) for v in (x, y, z))
     n = len(x)
     L = lib()
-    nn = L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, 0, None, None, None)
+    nn = L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, 0, None, None, None, None)
     zr = np.zeros((nn, 4))
     rg = np.zeros((nn, 2), dtype=np.int64)
     order = np.zeros(n, dtype=np.int64)
+    par = np.zeros(nn, dtype=np.int64)
     got = L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, nn, zr.ctypes.data, rg.ctypes.data,
-                              order.ctypes.data)
+                              order.ctypes.data, par.ctypes.data)
     assert got == nn
-    return zr, rg, order
+    return (zr, rg, order, par) if parents else (zr, rg, order)

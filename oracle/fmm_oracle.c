@@ -1016,20 +1016,25 @@ int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* 
 /*   f3..f6 = ln max(|M_A^(j)| / (|M_A,0| r_A^j), 1e-6),  j = 1..4            */
 /*   f7..f8 = the same for the target's own multipole M_B, j = 1..2           */
 /*   f9 = ln n_A,  f10 = ln n_B                                               */
+/*   f11 = ln max(g_AB / T_B, 1e-12): the pair's share of a far-field          */
+/*         magnitude estimate, g_AB = |M_A,0| / |d|^2 and T_B the sum of g     */
+/*         over the M2L lists of B and of all its ancestors                   */
 /* where |M^(j)|^2 = sum_{|m|=j} j!/m! M_m^2 is the Frobenius norm of the     */
 /* rank-j symmetric tensor (a ratio with a zero denominator counts as 0).     */
 /*                                                                            */
-/* Label of the pair at order p (p = 2..10): the relative error of the force  */
-/* the pair's order-p M2L (followed by L2P at order p) produces at target     */
-/* particles y_j of B, against the direct sum g over A's particles:           */
-/*   e_p = sqrt(sum_j |g_p(y_j) - g(y_j)|^2 / sum_j |g(y_j)|^2),              */
+/* Label of the pair at order p (p = 2..10): the error of the force the       */
+/* pair's order-p M2L (followed by L2P at order p) produces at target         */
+/* particles y_j of B, against the direct sum g over A's particles, relative  */
+/* to the total force a at those particles (direct sum over all particles,    */
+/* the particle itself excluded):                                             */
+/*   e_p = sqrt(sum_j |g_p(y_j) - g(y_j)|^2 / sum_j |a(y_j)|^2),              */
 /*   label_p = log10(max(e_p, 1e-12)).                                        */
 /* The y_j are all of B's particles when n_B <= 64, else the 64 at sorted     */
 /* positions b_B + floor(j n_B / 64), j = 0..63.                              */
 /* The source multipole is the order-10 one, so every p <= 10 reads its rank  */
 /* prefix.                                                                    */
 /* ------------------------------------------------------------------------ */
-#define ORC_NF 11
+#define ORC_NF 12
 #define ORC_NLAB 9
 
 static double rank_norm(const double* M, int j) {
@@ -1100,11 +1105,12 @@ double orc_pair_error(int p, int64_t na, const double* xa, const double* ya, con
     return e;
 }
 
-/* The adaptive tree itself: per node (centre x, y, z, radius) and the range
- * [b, e) of sorted positions it holds; order[a] = the particle at sorted
- * position a.  Returns the node count (arrays written when cap allows). */
+/* The adaptive tree itself: per node (centre x, y, z, radius), the range
+ * [b, e) of sorted positions it holds and its parent (-1 for the root);
+ * order[a] = the particle at sorted position a.  Returns the node count
+ * (arrays written when cap allows). */
 int64_t orc_adaptive_tree(int64_t n, const double* x, const double* y, const double* z, int max_leaf, int64_t cap,
-                          double* zr, int64_t* range, int64_t* order) {
+                          double* zr, int64_t* range, int64_t* order, int64_t* parent) {
     orc_init();
     if (max_leaf < 1 || n < 1) return -1;
     atree_t T;
@@ -1115,6 +1121,7 @@ int64_t orc_adaptive_tree(int64_t n, const double* x, const double* y, const dou
             if (zr) { zr[4 * c] = T.nd[c].z[0]; zr[4 * c + 1] = T.nd[c].z[1]; zr[4 * c + 2] = T.nd[c].z[2];
                       zr[4 * c + 3] = T.nd[c].r; }
             if (range) { range[2 * c] = T.nd[c].b; range[2 * c + 1] = T.nd[c].e; }
+            if (parent) parent[c] = T.nd[c].parent;
         }
         if (order) for (int64_t a = 0; a < n; ++a) order[a] = T.kv[a].idx;
     }
@@ -1143,6 +1150,25 @@ int64_t orc_adaptive_pairs(int64_t n, const double* x, const double* y, const do
         M = (double*)calloc((size_t)T.nn * nc, sizeof(double));
         atree_multipoles(&T, x, y, z, q, P, 0, M);
     }
+    /* far-field magnitude estimate T_B (feature f11) */
+    double* Tf = NULL;
+    if (feat) {
+        double* S = (double*)calloc((size_t)T.nn, sizeof(double));
+        Tf = (double*)calloc((size_t)T.nn, sizeof(double));
+        for (int64_t k = 0; k < np; ++k) {
+            const int64_t B = T.m2l.v[k].a, A = T.m2l.v[k].b;
+            const double dd = dist3(nd[A].z, nd[B].z);
+            S[B] += fabs(M[A * nc]) / (dd * dd);
+        }
+        for (int64_t c = 0; c < T.nn; ++c) Tf[c] = S[c] + (nd[c].parent >= 0 ? Tf[nd[c].parent] : 0.0);
+        free(S);
+    }
+    /* total force at every particle (label denominators), caller order */
+    double* at[4] = {NULL, NULL, NULL, NULL};
+    if (lab) {
+        for (int c = 0; c < 4; ++c) at[c] = (double*)malloc(sizeof(double) * n);
+        orc_direct(n, x, y, z, q, -1, NULL, at[0], at[1], at[2], at[3]);
+    }
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t k = 0; k < np; ++k) {
         const int64_t B = T.m2l.v[k].a, A = T.m2l.v[k].b;
@@ -1162,6 +1188,10 @@ int64_t orc_adaptive_pairs(int64_t n, const double* x, const double* y, const do
             for (int j = 1; j <= 2; ++j) f[6 + j] = shape_feature(M + B * nc, j, nd[B].r);
             f[9] = log((double)(nd[A].e - nd[A].b));
             f[10] = log((double)(nd[B].e - nd[B].b));
+            {
+                const double share = Tf[B] > 0.0 ? fabs(M[A * nc]) / (dn * dn) / Tf[B] : 0.0;
+                f[11] = log(share > 1e-12 ? share : 1e-12);
+            }
         }
         if (lab) {
             const int64_t nB = nd[B].e - nd[B].b;
@@ -1180,16 +1210,27 @@ int64_t orc_adaptive_pairs(int64_t n, const double* x, const double* y, const do
                     g[j][0] += q[i] * dx * ir3; g[j][1] += q[i] * dy * ir3; g[j][2] += q[i] * dz * ir3;
                 }
             }
+            /* relative to the pair's own force -> relative to the total force */
+            double own = 0.0, tot = 0.0;
+            for (int j = 0; j < ny; ++j) {
+                const int64_t sp = nd[B].b + (nB <= 64 ? j : (int64_t)j * nB / 64);
+                const int64_t t = kv[sp].idx;
+                own += g[j][0] * g[j][0] + g[j][1] * g[j][1] + g[j][2] * g[j][2];
+                tot += at[1][t] * at[1][t] + at[2][t] * at[2][t] + at[3][t] * at[3][t];
+            }
+            const double scale = tot > 0.0 ? sqrt(own / tot) : 0.0;
             double* Lp = (double*)malloc(sizeof(double) * nc);
             for (int p = 2; p <= P; ++p) {
-                const double e = pair_error(p, M + A * nc, nd[A].z, nd[B].z, ny, (const double (*)[3])yv,
-                                            (const double (*)[3])g, Lp);
+                const double e = scale * pair_error(p, M + A * nc, nd[A].z, nd[B].z, ny, (const double (*)[3])yv,
+                                                    (const double (*)[3])g, Lp);
                 lab[k * ORC_NLAB + (p - 2)] = log10(e > 1e-12 ? e : 1e-12);
             }
             free(Lp);
         }
     }
     free(M);
+    free(Tf);
+    for (int c = 0; c < 4; ++c) free(at[c]);
     atree_free(&T);
     return np;
 }

@@ -3,11 +3,11 @@ fixes one expansion order per run).
 
 TEST INFRASTRUCTURE ONLY (same rules as the rest of ``oracle/``).
 
-The model maps the 11 per-pair features of ``oracle.adaptive_pairs`` to the
+The model maps the 12 per-pair features of ``oracle.adaptive_pairs`` to the
 predicted log10 force error of the pair's M2L at orders 2..10:
 
     z0 = (f - mu) / sd
-    h1 = relu(W1 z0 + b1)          W1: 64 x 11
+    h1 = relu(W1 z0 + b1)          W1: 64 x 12
     h2 = relu(W2 h1 + b2)          W2: 64 x 64
     h3 = relu(W3 h2 + b3)          W3: 64 x 64
     y  = W4 h3 + b4                W4:  9 x 64
@@ -18,12 +18,12 @@ the weights and every layer input (z0, h1, h2, h3) to bfloat16 (round to
 nearest even) and accumulates in FP32; this module emulates that rounding
 exactly and accumulates in FP64.
 
-Parameter blob (float32, 9703 values):
-    [0:8]   header: tag 6332, version 1, NF=11, H=64, NOUT=9, p_lo=2,
+Parameter blob (float32, 9769 values):
+    [0:8]   header: tag 6332, version 2, NF=12, H=64, NOUT=9, p_lo=2,
             log10 kappa, 0
-    [8:19]  mu,  [19:30] sd
-    [30:]   W1 (row-major, 64x11), b1, W2, b2, W3, b3, W4 (9x64), b4
-The trainable parameters are blob[30:].
+    [8:20]  mu,  [20:32] sd
+    [32:]   W1 (row-major, 64x12), b1, W2, b2, W3, b3, W4 (9x64), b4
+The trainable parameters are blob[32:].
 
 Loss for training: L = mean over samples and the 9 outputs of (y - t)^2.
 Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
@@ -33,7 +33,7 @@ from __future__ import annotations
 
 import numpy as np
 
-NF, H, NOUT, P_LO = 11, 64, 9, 2
+NF, H, NOUT, P_LO = 12, 64, 9, 2
 HDR = 8
 OFF_MU = HDR
 OFF_SD = HDR + NF
@@ -63,7 +63,7 @@ def pack(d):
 
 
 def header(log10_kappa=0.0):
-    return np.array([6332.0, 1.0, NF, H, NOUT, P_LO, log10_kappa, 0.0])
+    return np.array([6332.0, 2.0, NF, H, NOUT, P_LO, log10_kappa, 0.0])
 
 
 def bf16_round(a):

@@ -776,9 +776,9 @@ int fmm_evaluate_host(fmm_plan* pl, int64_t n, const double* x, const double* y,
 // ---------------------------------------------------------------------------
 static int check_blob(fmm_plan* pl, const float* blob) {
     if (!blob) FAIL(FMM_ERR_ARG, "blob is NULL");
-    if (blob[0] != 6332.f || blob[1] != 1.f || blob[2] != (float)FMM_MLP_NF || blob[3] != 64.f ||
+    if (blob[0] != 6332.f || blob[1] != FMM_MLP_VERSION || blob[2] != (float)FMM_MLP_NF || blob[3] != 64.f ||
         blob[4] != (float)FMM_MLP_NOUT || blob[5] != 2.f)
-        FAIL(FMM_ERR_ARG, "blob header is not {6332, 1, 11, 64, 9, 2, ...}");
+        FAIL(FMM_ERR_ARG, "blob header is not {6332, 2, 12, 64, 9, 2, ...}");
     for (int f = 0; f < FMM_MLP_NF; ++f)
         if (!(blob[FMM_MLP_OFF_SD + f] > 0.f)) FAIL(FMM_ERR_ARG, "feature deviation %d is not positive", f);
     return FMM_OK;
@@ -811,11 +811,25 @@ int fmm_pair_data(fmm_plan* pl, float* feat, double* labels, void* stream) {
     if (labels && (pl->cfg.p != 10 || pl->cfg.prec != FMM_FP64))
         FAIL(FMM_ERR_ARG, "labels need p = 10 and FMM_FP64");
     if (pl->ad->nm2l > 0 && !feat && !labels) FAIL(FMM_ERR_ARG, "nothing to write");
+    if (labels && pl->n > (1 << 18)) FAIL(FMM_ERR_ARG, "labels need n <= 2^18 (O(n^2) direct sum)");
     if (int rc = fmm_p2m(pl, stream)) return rc;
     if (int rc = fmm_m2m(pl, stream)) return rc;
     ad_node_features(pl->ad, S(stream));
+    ad_far_estimate(pl->ad, S(stream));
     if (feat) ad_pair_features(pl->ad, feat, S(stream));
-    if (labels) ad_pair_labels(pl->ad, labels, S(stream));
+    if (labels && pl->n > 0) {
+        // total forces at every particle (sorted order), FP64 direct sum
+        AdState* A = pl->ad;
+        double* tot = nullptr;
+        if (cudaMalloc(&tot, (size_t)4 * pl->n * sizeof(double)) != cudaSuccess)
+            FAIL(FMM_ERR_OOM, "allocating the label scratch failed");
+        launch_direct(pl->n, A->xs, A->ys, A->zs, A->qs, pl->n, nullptr, tot, tot + pl->n, tot + 2 * pl->n,
+                      tot + 3 * pl->n, S(stream));
+        ad_pair_labels(A, labels, tot + pl->n, tot + 2 * pl->n, tot + 3 * pl->n, S(stream));
+        const cudaError_t e = cudaStreamSynchronize(S(stream));
+        cudaFree(tot);
+        if (e != cudaSuccess) FAIL(FMM_ERR_CUDA, "label pass failed: %s", cudaGetErrorString(e));
+    }
     CKLAUNCH();
     return FMM_OK;
 }

@@ -9,12 +9,15 @@
 //   f0 = ln(a + b) (the MAC ratio of App. C), f1 = ln a, f2 = ln b,
 //   f3..f6 = ln max(|M_A^(j)| / (|M_A,0| r_A^j), 1e-6), j = 1..4,
 //   f7..f8 = the same for M_B, j = 1..2,  f9 = ln n_A, f10 = ln n_B,
+//   f11 = ln max(g_AB / T_B, 1e-12), g_AB = |M_A,0|/|d|^2 and T_B the sum of
+//         g over the M2L lists of B and of all its ancestors,
 // with |M^(j)|^2 = sum_{|m|=j} j!/m! M_m^2 (Frobenius norm of the rank-j
 // symmetric tensor; a ratio with a zero denominator counts as 0).
-// Label of a pair at order p: log10 max(e_p, 1e-12), e_p the relative error
-// of the force of the pair's order-p M2L + L2P (Eqs. M2L, L2P) at up to 64
-// target particles of B (all when n_B <= 64, else sorted positions
-// b_B + floor(j n_B/64)) against the direct sum over A's particles.
+// Label of a pair at order p: log10 max(e_p, 1e-12), e_p the error of the
+// force of the pair's order-p M2L + L2P (Eqs. M2L, L2P) at up to 64 target
+// particles of B (all when n_B <= 64, else sorted positions
+// b_B + floor(j n_B/64)) against the direct sum over A's particles, relative
+// to the total force at those particles.
 #include "fmm_adaptive.h"
 #include "fmm_learn.h"
 
@@ -49,11 +52,38 @@ __global__ void k_node_feat(int nn, int ld, const double* __restrict__ Mn, const
     }
     out[4] = logf((float)(ne[c] - nb[c]));
     out[5] = (float)rad[c];
-    out[6] = 0.f;
-    out[7] = 0.f;
+    out[6] = 0.f;           // T_c, set by the far-field estimate
+    out[7] = (float)m0;     // |M_0| (the same in scaled units)
     float4* o = (float4*)(nodeF + 8 * (int64_t)c);
     o[0] = make_float4(out[0], out[1], out[2], out[3]);
     o[1] = make_float4(out[4], out[5], out[6], out[7]);
+}
+
+// far-field magnitude estimate: S_c = sum over c's M2L list of |M_A,0|/|d|^2,
+// then T_c = sum of S over c and its ancestors (written to nodeF slot 6)
+__global__ void k_far_sum(int nn, const int* __restrict__ off, const int* __restrict__ src,
+                          const int4* __restrict__ ic, float scale, const float* __restrict__ nodeF,
+                          float* __restrict__ S) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nn) return;
+    const int4 it = ic[c];
+    float acc = 0.f;
+    for (int k = off[c]; k < off[c + 1]; ++k) {
+        const int A = src[k];
+        const int4 ia = ic[A];
+        const float dx = (float)(it.x - ia.x) * scale, dy = (float)(it.y - ia.y) * scale,
+                    dz = (float)(it.z - ia.z) * scale;
+        acc += nodeF[8 * (int64_t)A + 7] / (dx * dx + dy * dy + dz * dz);
+    }
+    S[c] = acc;
+}
+__global__ void k_far_down(int nn, const int* __restrict__ parent, const float* __restrict__ S,
+                           float* __restrict__ nodeF) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nn) return;
+    float t = 0.f;
+    for (int a = c; a >= 0; a = parent[a]) t += S[a];
+    nodeF[8 * (int64_t)c + 6] = t;
 }
 
 // M2L pair index -> its target (CSR rows expanded)
@@ -116,7 +146,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_pair_labels(int npair, const int* __restrict__ ptgt, const int* __restrict__ msrc, const double* __restrict__ zc,
               const int* __restrict__ nb, const int* __restrict__ ne, const double* __restrict__ xs,
               const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
-              const double* __restrict__ Mn, int ld, double* __restrict__ lab) {
+              const double* __restrict__ Mn, int ld, const double* __restrict__ atx,
+              const double* __restrict__ aty, const double* __restrict__ atz, double* __restrict__ lab) {
     __shared__ double sM[WARPS][LBL_NS], sD[WARPS][LBL_NS], sL[WARPS][LBL_NS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blockIdx.x * WARPS + w;
@@ -132,6 +163,7 @@ k_pair_labels(int npair, const int* __restrict__ ptgt, const int* __restrict__ m
     const int ny = nB <= 64 ? nB : 64;
     double rb[2][3], g[2][3];
     bool act[2];
+    double tot = 0.0;   // squared total force at this lane's targets
     for (int u = 0; u < 2; ++u) {
         const int j = lane + 32 * u;
         act[u] = j < ny;
@@ -139,6 +171,7 @@ k_pair_labels(int npair, const int* __restrict__ ptgt, const int* __restrict__ m
         rb[u][0] = rb[u][1] = rb[u][2] = 0.0;
         if (!act[u]) continue;
         const int sp = bB + (nB <= 64 ? j : (int)((int64_t)j * nB / 64));
+        tot += atx[sp] * atx[sp] + aty[sp] * aty[sp] + atz[sp] * atz[sp];
         const double y[3] = {xs[sp], ys[sp], zs[sp]};
         for (int c = 0; c < 3; ++c) rb[u][c] = y[c] - zc[3 * B + c];
         for (int a = nb[A]; a < ne[A]; ++a) {
@@ -150,8 +183,7 @@ k_pair_labels(int npair, const int* __restrict__ ptgt, const int* __restrict__ m
             g[u][2] += qs[a] * dz * ir3;
         }
     }
-    const double den = warp_sum(g[0][0] * g[0][0] + g[0][1] * g[0][1] + g[0][2] * g[0][2] + g[1][0] * g[1][0] +
-                                g[1][1] * g[1][1] + g[1][2] * g[1][2]);
+    const double den = warp_sum(tot);
     for (int p = 2; p <= LBL_P; ++p) {
         __syncwarp();
         // Eq. M2L at order p: L_n = sum_{|m| <= p-|n|} M_m/m! D_{n+m}
@@ -395,6 +427,15 @@ int ad_bucket_csr(int n, int nn, const uint64_t* key, const int* val, const int*
     return 0;
 }
 
+int ad_far_estimate(AdState* a, cudaStream_t s) {
+    if (a->nn <= 0) return 0;
+    k_far_sum<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->moff, a->msrc, a->ic, a->scale32, a->nodeF, a->fsum);
+    k_far_down<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->parent, a->fsum, a->nodeF);
+    count_launch();
+    count_launch();
+    return 0;
+}
+
 int ad_pair_features(AdState* a, float* feat, cudaStream_t s) {
     if (a->nm2l <= 0) return 0;
     k_pair_features<<<(a->nm2l + 255) / 256, 256, 0, s>>>(a->nm2l, a->ptgt, a->msrc, a->ic, a->scale32, a->nodeF,
@@ -403,11 +444,11 @@ int ad_pair_features(AdState* a, float* feat, cudaStream_t s) {
     return 0;
 }
 
-int ad_pair_labels(AdState* a, double* lab, cudaStream_t s) {
+int ad_pair_labels(AdState* a, double* lab, const double* atx, const double* aty, const double* atz, cudaStream_t s) {
     if (a->nm2l <= 0) return 0;
     constexpr int W = 4;
     k_pair_labels<W><<<(a->nm2l + W - 1) / W, W * 32, 0, s>>>(a->nm2l, a->ptgt, a->msrc, a->zc, a->nb, a->ne, a->xs,
-                                                             a->ys, a->zs, a->qs, a->M, a->nc, lab);
+                                                             a->ys, a->zs, a->qs, a->M, a->nc, atx, aty, atz, lab);
     count_launch();
     return 0;
 }

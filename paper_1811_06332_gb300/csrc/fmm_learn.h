@@ -12,33 +12,38 @@ constexpr int FMM_MLP_OFF_MU = 8;
 constexpr int FMM_MLP_OFF_SD = 8 + FMM_MLP_NF;
 constexpr int FMM_MLP_OFF_PAR = 8 + 2 * FMM_MLP_NF;
 constexpr int FMM_MLP_NPAR = FMM_MLP_NBLOB - FMM_MLP_OFF_PAR;
-static_assert(FMM_MLP_NPAR == 64 * 11 + 64 + 2 * (64 * 64 + 64) + 9 * 64 + 9, "parameter count");
+// offsets of the parameter blocks inside the trainable parameters
+constexpr int MLP_W1 = 0, MLP_B1 = 64 * FMM_MLP_NF, MLP_W2 = MLP_B1 + 64, MLP_B2 = MLP_W2 + 64 * 64,
+              MLP_W3 = MLP_B2 + 64, MLP_B3 = MLP_W3 + 64 * 64, MLP_W4 = MLP_B3 + 64, MLP_B4 = MLP_W4 + 9 * 64;
+static_assert(FMM_MLP_NPAR == MLP_B4 + 9, "parameter count");
+constexpr float FMM_MLP_VERSION = 2.f;
 
-// trainable parameters in blob order: W1 (64x11, row-major), b1, W2 (64x64),
+// trainable parameters in blob order: W1 (64xNF, row-major), b1, W2 (64x64),
 // b2, W3 (64x64), b3, W4 (9x64), b4
 struct MlpView {
     const float *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4;
     __host__ __device__ explicit MlpView(const float* p)
-        : W1(p), b1(p + 704), W2(p + 768), b2(p + 4864), W3(p + 4928), b3(p + 9024), W4(p + 9088), b4(p + 9664) {}
+        : W1(p + MLP_W1), b1(p + MLP_B1), W2(p + MLP_W2), b2(p + MLP_B2), W3(p + MLP_W3), b3(p + MLP_B3),
+          W4(p + MLP_W4), b4(p + MLP_B4) {}
 };
 
 // parameter t -> layer l (1..4), output row u, input column j (-1: bias)
 __host__ __device__ inline void mlp_param_index(int t, int& l, int& u, int& j) {
-    if (t < 704) { l = 1; u = t / 11; j = t % 11; }
-    else if (t < 768) { l = 1; u = t - 704; j = -1; }
-    else if (t < 4864) { l = 2; u = (t - 768) / 64; j = (t - 768) % 64; }
-    else if (t < 4928) { l = 2; u = t - 4864; j = -1; }
-    else if (t < 9024) { l = 3; u = (t - 4928) / 64; j = (t - 4928) % 64; }
-    else if (t < 9088) { l = 3; u = t - 9024; j = -1; }
-    else if (t < 9664) { l = 4; u = (t - 9088) / 64; j = (t - 9088) % 64; }
-    else { l = 4; u = t - 9664; j = -1; }
+    if (t < MLP_B1) { l = 1; u = t / FMM_MLP_NF; j = t % FMM_MLP_NF; }
+    else if (t < MLP_W2) { l = 1; u = t - MLP_B1; j = -1; }
+    else if (t < MLP_B2) { l = 2; u = (t - MLP_W2) / 64; j = (t - MLP_W2) % 64; }
+    else if (t < MLP_W3) { l = 2; u = t - MLP_B2; j = -1; }
+    else if (t < MLP_B3) { l = 3; u = (t - MLP_W3) / 64; j = (t - MLP_W3) % 64; }
+    else if (t < MLP_W4) { l = 3; u = t - MLP_B3; j = -1; }
+    else if (t < MLP_B4) { l = 4; u = (t - MLP_W4) / 64; j = (t - MLP_W4) % 64; }
+    else { l = 4; u = t - MLP_B4; j = -1; }
 }
 
 __host__ __device__ inline double c_fact_small(int j) { return j <= 1 ? 1.0 : j == 2 ? 2.0 : j == 3 ? 6.0 : 24.0; }
 
 // Features of the M2L pair (source A, target B) from per-node data:
-// nodeF[8c..8c+7] = (shape_1..shape_4, ln n_c, r_c, 0, 0) and the integer
-// centres ic (offset d = (ic_B - ic_A) * scale).
+// nodeF[8c..8c+7] = (shape_1..shape_4, ln n_c, r_c, T_c, |M_c,0|) and the
+// integer centres ic (offset d = (ic_B - ic_A) * scale).
 __device__ __forceinline__ void pair_features(int A, int B, const int4* __restrict__ ic, float scale,
                                               const float* __restrict__ nodeF, float* f) {
     const int4 ia = ic[A], ib = ic[B];
@@ -55,13 +60,15 @@ __device__ __forceinline__ void pair_features(int A, int B, const int4* __restri
     f[7] = b0.x; f[8] = b0.y;
     f[9] = a1.x;
     f[10] = b1.x;
+    f[11] = logf(fmaxf(b1.z > 0.f ? a1.w / (dn * dn) / b1.z : 0.f, 1e-12f));
 }
 
 // fmm_learn.cu
 int ad_node_features(AdState* a, cudaStream_t s);
 int ad_pair_targets_launch(int nn, int npair, const int* off, int* ptgt, cudaStream_t s);
 int ad_pair_features(AdState* a, float* feat, cudaStream_t s);
-int ad_pair_labels(AdState* a, double* lab, cudaStream_t s);
+int ad_pair_labels(AdState* a, double* lab, const double* atx, const double* aty, const double* atz, cudaStream_t s);
+int ad_far_estimate(AdState* a, cudaStream_t s);
 int mlp_grad_host(const float* blob, int64_t n, const float* feat, const float* lab, float* loss_out, float* grad_out,
                   cudaStream_t s);
 int mlp_train_host(float* blob, int64_t n, const float* feat, const float* lab, const int* order, int epochs,

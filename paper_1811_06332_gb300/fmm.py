@@ -27,7 +27,7 @@ EXPORTS = [
     "fmm_mlp_grad", "fmm_mlp_train", "fmm_mlp_predict", "fmm_set_mlp", "fmm_set_pair_orders",
 ]
 
-MLP_NF, MLP_NOUT, MLP_NBLOB = 11, 9, 9703
+MLP_NF, MLP_NOUT, MLP_NBLOB = 12, 9, 9769
 
 
 class FMMError(RuntimeError):
@@ -165,11 +165,11 @@ def _host_f32(blob):
 
 def fmm_mlp_grad(blob, feat, labels, stream=None):
     """Loss and gradient (numpy, FP32) of the order model over the samples
-    (device float32 feat [n, 11], labels [n, 9])."""
+    (device float32 feat [n, 12], labels [n, 9])."""
     import numpy as np
     b = _host_f32(blob)
     loss = np.zeros(1, dtype=np.float32)
-    grad = np.zeros(MLP_NBLOB - 30, dtype=np.float32)
+    grad = np.zeros(MLP_NBLOB - 2 * MLP_NF - 8, dtype=np.float32)
     _check(lib().fmm_mlp_grad(b.ctypes.data, feat.shape[0], _ptr(feat), _ptr(labels), loss.ctypes.data,
                               grad.ctypes.data, _stream(stream)))
     return float(loss[0]), grad
@@ -288,7 +288,7 @@ class Plan:
         return t, s
 
     def pair_data(self, labels=False, stream=None):
-        """Device tensors: features [npair, 11] (float32) and, on request,
+        """Device tensors: features [npair, 12] (float32) and, on request,
         labels [npair, 9] (float64) of the plan's M2L pairs."""
         t, _ = self.pairs()
         n = len(t)

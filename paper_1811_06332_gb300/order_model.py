@@ -7,8 +7,8 @@ fmm_evaluate, fmm_direct); this module draws the seeded random numbers
 (initial weights, sample order, sampled targets) and passes them in.
 
 Parameter blob layout (FMM_MLP_NBLOB floats, include/fmm_gb300.h):
-header {6332, 1, 11, 64, 9, 2, log10 kappa, 0}, 11 means, 11 deviations,
-W1 (64x11), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (9x64), b4.
+header {6332, 2, 12, 64, 9, 2, log10 kappa, 0}, 12 means, 12 deviations,
+W1 (64x12), b1, W2 (64x64), b2, W3 (64x64), b3, W4 (9x64), b4.
 """
 from __future__ import annotations
 
@@ -18,8 +18,8 @@ import torch
 from . import fmm as F
 from . import inputs
 
-NF, H, NOUT = 11, 64, 9
-HDR, OFF_PAR = 8, 8 + 2 * 11
+NF, H, NOUT = 12, 64, 9
+HDR, OFF_PAR = 8, 8 + 2 * 12
 SHAPES = [(H, NF), (H,), (H, H), (H,), (H, H), (H,), (NOUT, H), (NOUT,)]
 NBLOB = OFF_PAR + sum(int(np.prod(s)) for s in SHAPES)
 assert NBLOB == F.MLP_NBLOB
@@ -29,7 +29,7 @@ def init_blob(seed: int, log10_kappa: float = 0.0) -> np.ndarray:
     """He-uniform weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)) from the seeded
     generator, zero biases, identity feature normalisation."""
     b = np.zeros(NBLOB)
-    b[:HDR] = [6332.0, 1.0, NF, H, NOUT, 2.0, log10_kappa, 0.0]
+    b[:HDR] = [6332.0, 2.0, NF, H, NOUT, 2.0, log10_kappa, 0.0]
     b[HDR + NF:HDR + 2 * NF] = 1.0
     o = OFF_PAR
     for k, shp in enumerate(SHAPES):
@@ -79,10 +79,13 @@ def force_error(acc, Xd, nsample: int, seed: int) -> float:
 
 
 def calibrate(blob, X, p: int, max_leaf: int, theta: float, target: float, prec=F.FP32,
-              grid=(0.0, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0), margin: float = 0.8, seed: int = 5):
+              grid=tuple(-2.0 + 0.25 * k for k in range(13)), margin: float = 0.8, seed: int = 5):
     """Largest log10 kappa of the grid (tried in increasing order, stopping at
     the first miss) whose learned FMM on the set X meets margin * target.
-    Returns (blob with that kappa, [(log10 kappa, error, mean order)])."""
+    The labels measure a pair's error against the total force at its
+    targets, and a target collects the errors of all its pairs, so kappa is
+    typically below 1.  Returns (blob with that kappa, [(log10 kappa, error,
+    mean order)])."""
     dev = torch.device("cuda", torch.cuda.current_device())
     Xd = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in X]
     best = None

@@ -38,7 +38,7 @@ def test_bf16_round_ties_to_even():
 
 # ---------------------------------------------------------------- forward
 def test_forward_hand_built_network():
-    """W1 copies the normalised features into the first 11 hidden units,
+    """W1 copies the normalised features into the first 12 hidden units,
     W2 and W3 are identities, W4 row k sums units with weight (k+1):
     y_k = (k+1) sum_j relu((f_j - mu_j)/sd_j) + b4_k."""
     d = mlp.unpack(_random_blob(3))
@@ -132,12 +132,12 @@ def plummer_pairs():
     x, y, z = inputs.plummer(n, 21)
     q = inputs.masses_equal(n)
     tgt, src, feat, lab = O.adaptive_pairs(x, y, z, q, 16, 0.6, features=True, labels=True)
-    zr, rg, order = O.adaptive_tree(x, y, z, 16)
-    return (x, y, z, q), tgt, src, feat, lab, zr, rg, order
+    zr, rg, order, par = O.adaptive_tree(x, y, z, 16, parents=True)
+    return (x, y, z, q), tgt, src, feat, lab, zr, rg, order, par
 
 
 def test_pairs_are_the_m2l_list(plummer_pairs):
-    (x, y, z, q), tgt, src, feat, lab, zr, rg, order = plummer_pairs
+    (x, y, z, q), tgt, src, feat, lab, zr, rg, order, par = plummer_pairs
     _, _, st = O.fmm_adaptive(x, y, z, q, 16, 0.6, 2, O.SYM, sample=[0])
     assert len(tgt) == st["m2l_pairs"] > 0
     key = tgt * (tgt.max() + 1) + src
@@ -156,7 +156,7 @@ def test_shape_features_closed_forms(plummer_pairs):
     multipole q(-r)^(x)j of Frobenius norm |q| r^j: its shape features are
     ln 1 = 0.  Every ratio is at most 1 (the norm of a sum of rank-one
     tensors is at most the sum of the norms, each <= q r_A^j)."""
-    (x, y, z, q), tgt, src, feat, lab, zr, rg, order = plummer_pairs
+    (x, y, z, q), tgt, src, feat, lab, zr, rg, order, par = plummer_pairs
     one = (rg[src, 1] - rg[src, 0]) == 1
     assert one.sum() > 10
     np.testing.assert_allclose(feat[one, 3:7], 0.0, atol=1e-9)
@@ -166,8 +166,10 @@ def test_shape_features_closed_forms(plummer_pairs):
 
 def test_labels_equal_direct_definition(plummer_pairs):
     """Labels from the tree's M2M-built multipoles equal the definition
-    recomputed from the pair's particles (P2M at the source centre)."""
-    (x, y, z, q), tgt, src, feat, lab, zr, rg, order = plummer_pairs
+    recomputed from the pair's particles (P2M at the source centre), with
+    the pair's own field and the total field at the targets taken from the
+    oracle's direct sum (pinned separately)."""
+    (x, y, z, q), tgt, src, feat, lab, zr, rg, order, par = plummer_pairs
     pick = np.unique((inputs.u01(31, 0, 25) * len(tgt)).astype(int))
     for k in pick:
         A, B = src[k], tgt[k]
@@ -175,14 +177,40 @@ def test_labels_equal_direct_definition(plummer_pairs):
         nb = rg[B, 1] - rg[B, 0]
         sp = np.arange(nb) if nb <= 64 else (np.arange(64) * nb) // 64
         ib = order[rg[B, 0] + sp]
+        # own field: A's particles plus B's sample points carrying no charge
+        xs = np.concatenate([x[ia], x[ib]]); ys = np.concatenate([y[ia], y[ib]])
+        zs = np.concatenate([z[ia], z[ib]]); qs = np.concatenate([q[ia], np.zeros(len(ib))])
+        _, g_own = O.direct(xs, ys, zs, qs, targets=np.arange(len(ia), len(ia) + len(ib)))
+        _, g_tot = O.direct(x, y, z, q, targets=ib)
+        scale = np.sqrt((g_own ** 2).sum() / (g_tot ** 2).sum())
         for p in (2, 5, 10):
             e = O.pair_error(p, (x[ia], y[ia], z[ia], q[ia]), zr[A, :3], zr[B, :3],
                              np.stack([x[ib], y[ib], z[ib]], 1))
-            assert abs(np.log10(max(e, 1e-12)) - lab[k, p - 2]) < 1e-8, (k, p)
+            assert abs(np.log10(max(e * scale, 1e-12)) - lab[k, p - 2]) < 1e-8, (k, p)
+
+
+def test_far_field_share_feature(plummer_pairs):
+    """f11 is the log of the pair's share of a sum of positive terms over the
+    target's list and its ancestors' lists: every share is <= 1, the shares
+    of one target's own list sum to at most 1, and to exactly 1 when no
+    ancestor of the target has an M2L list."""
+    (x, y, z, q), tgt, src, feat, lab, zr, rg, order, par = plummer_pairs
+    assert np.all(feat[:, 11] <= 1e-12)
+    share = np.exp(feat[:, 11])
+    tot = np.bincount(tgt, weights=share, minlength=len(zr))
+    assert np.all(tot <= 1 + 1e-9)
+    has_list = np.bincount(tgt, minlength=len(zr)) > 0
+    anc_list = np.zeros(len(zr), dtype=bool)
+    for c in range(len(zr)):          # parents precede children
+        if par[c] >= 0:
+            anc_list[c] = anc_list[par[c]] or has_list[par[c]]
+    only = has_list & ~anc_list
+    assert only.sum() > 0
+    np.testing.assert_allclose(tot[only], 1.0, rtol=1e-12)
 
 
 def test_labels_decrease_with_order(plummer_pairs):
-    (x, y, z, q), tgt, src, feat, lab, zr, rg, order = plummer_pairs
+    (x, y, z, q), tgt, src, feat, lab, zr, rg, order, par = plummer_pairs
     m = lab.mean(0)
     assert np.all(np.diff(m) < -0.2)
     # geometric decay: the mean slope is near log10 of a typical separation ratio
