@@ -85,8 +85,11 @@ typedef struct {
                               with fmm_set_mlp, or given by fmm_set_pair_orders); p is
                               the order of every other operator and of the storage   */
     double target_rel_err; /* learned_p: the model picks, per pair, the lowest order
-                              whose predicted relative force error is at most
-                              target_rel_err * kappa (kappa stored with the model)    */
+                              whose predicted error is at most
+                              target_rel_err * kappa / sqrt(K_B), kappa stored with
+                              the model, K_B the number of M2L pairs of the target
+                              and its ancestors (errors of independent pairs add in
+                              quadrature at a target)                                  */
     int use_graph;         /* 1 (adaptive trees, non-default stream): after the first
                               evaluation, capture the operator sequence P2M..P2P into
                               a CUDA graph and replay it while the tree keeps its
@@ -274,7 +277,8 @@ int64_t fmm_kernel_launches(void);
  *   a = max(r_A/|d|, 1e-6), b = max(r_B/|d|, 1e-6); f0 = ln(a+b) (the MAC
  *   ratio, App. C), f1 = ln a, f2 = ln b; f3..f6 = ln max(|M_A^(j)| /
  *   (|M_A,0| r_A^j), 1e-6) for j = 1..4 with |M^(j)|^2 = sum_{|m|=j} j!/m!
- *   M_m^2; f7, f8 = the same for M_B, j = 1, 2; f9 = ln n_A; f10 = ln n_B;
+ *   M_m^2; f7, f8 = the same for M_B, j = 1, 2; f9 = ln min(n_A, 1024);
+ *   f10 = ln min(n_B, 1024);
  *   f11 = ln max(g_AB / T_B, 1e-12), the pair's share of a far-field
  *   magnitude estimate: g_AB = |M_A,0| / |d|^2, T_B = the sum of g over the
  *   M2L lists of B and of all its ancestors.

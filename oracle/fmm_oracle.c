@@ -1015,7 +1015,8 @@ int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* 
 /*   f1 = ln a,  f2 = ln b                                                    */
 /*   f3..f6 = ln max(|M_A^(j)| / (|M_A,0| r_A^j), 1e-6),  j = 1..4            */
 /*   f7..f8 = the same for the target's own multipole M_B, j = 1..2           */
-/*   f9 = ln n_A,  f10 = ln n_B                                               */
+/*   f9 = ln min(n_A, 1024),  f10 = ln min(n_B, 1024) (counts saturate, so a */
+/*         model trained on small sets sees no unseen values on large ones)  */
 /*   f11 = ln max(g_AB / T_B, 1e-12): the pair's share of a far-field          */
 /*         magnitude estimate, g_AB = |M_A,0| / |d|^2 and T_B the sum of g     */
 /*         over the M2L lists of B and of all its ancestors                   */
@@ -1186,8 +1187,8 @@ int64_t orc_adaptive_pairs(int64_t n, const double* x, const double* y, const do
             f[2] = log(b);
             for (int j = 1; j <= 4; ++j) f[2 + j] = shape_feature(M + A * nc, j, nd[A].r);
             for (int j = 1; j <= 2; ++j) f[6 + j] = shape_feature(M + B * nc, j, nd[B].r);
-            f[9] = log((double)(nd[A].e - nd[A].b));
-            f[10] = log((double)(nd[B].e - nd[B].b));
+            f[9] = log((double)(nd[A].e - nd[A].b < 1024 ? nd[A].e - nd[A].b : 1024));
+            f[10] = log((double)(nd[B].e - nd[B].b < 1024 ? nd[B].e - nd[B].b : 1024));
             {
                 const double share = Tf[B] > 0.0 ? fabs(M[A * nc]) / (dn * dn) / Tf[B] : 0.0;
                 f[11] = log(share > 1e-12 ? share : 1e-12);

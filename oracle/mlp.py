@@ -13,7 +13,9 @@ predicted log10 force error of the pair's M2L at orders 2..10:
     y  = W4 h3 + b4                W4:  9 x 64
 
 and the pair takes the lowest order p in 2..P whose prediction is at most
-``log10(target) + log10(kappa)``, or P when none is.  The BF16 form rounds
+``log10(target) + log10(kappa) - log10(K_B)/2``, or P when none is; K_B is
+the number of M2L pairs of the target and its ancestors (independent pair
+errors add in quadrature at a target).  The BF16 form rounds
 the weights and every layer input (z0, h1, h2, h3) to bfloat16 (round to
 nearest even) and accumulates in FP32; this module emulates that rounding
 exactly and accumulates in FP64.
@@ -130,12 +132,26 @@ def adam_step(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def select(pred, log10_target, log10_kappa, p_max=10):
-    """Lowest order p in 2..p_max with pred[p-2] <= threshold, else p_max."""
-    thr = log10_target + log10_kappa
+def select(pred, log10_target, log10_kappa, p_max=10, log10_k=None):
+    """Lowest order p in 2..p_max with pred[p-2] <= threshold, else p_max.
+    threshold = log10_target + log10_kappa - log10(K_B)/2 with log10_k the
+    per-pair log10 K_B (the M2L pairs of the target and its ancestors), or
+    without that term when log10_k is None."""
     pred = np.asarray(pred)
+    thr = log10_target + log10_kappa - (0.0 if log10_k is None else 0.5 * np.asarray(log10_k))
+    thr = np.broadcast_to(thr, (pred.shape[0],))
     out = np.full(pred.shape[0], p_max, dtype=np.int8)
     for p in range(p_max, P_LO - 1, -1):
         ok = pred[:, p - P_LO] <= thr
         out[ok] = p
     return out
+
+
+def chain_pairs(tgt, parent):
+    """K_B per node: the number of M2L pairs whose target is the node or one
+    of its ancestors (parents precede children in the node numbering)."""
+    cnt = np.bincount(np.asarray(tgt), minlength=len(parent)).astype(np.float64)
+    K = np.zeros(len(parent))
+    for c in range(len(parent)):
+        K[c] = cnt[c] + (K[parent[c]] if parent[c] >= 0 else 0.0)
+    return K

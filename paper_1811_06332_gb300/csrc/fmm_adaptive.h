@@ -49,9 +49,10 @@ struct AdState {
     signed char* porder = nullptr; // order of each M2L pair
     int* iota = nullptr;           // 0..nn-1: target order of the per-order M2L launches
     int *bcnt = nullptr, *boff = nullptr, *bsrc = nullptr;   // pairs grouped by (order, target)
-    float* fsum = nullptr;         // per node: far-field magnitude sum over its own M2L list
+    float* fsum = nullptr;         // per node: far-field magnitude sum and pair count of its own M2L list
+    float* nodeK = nullptr;        // per node: log10 of the M2L pairs on its ancestor chain (itself included)
     size_t cap_ptgt = 0, cap_nodeF = 0, cap_porder = 0, cap_iota = 0, cap_bcnt = 0, cap_boff = 0, cap_bsrc = 0,
-           cap_fsum = 0;
+           cap_fsum = 0, cap_nodeK = 0;
     bool orders_fixed = false;     // orders given by the caller instead of the model
     int64_t n_orders = 0;
     unsigned gen = 0;              // bumped whenever a buffer moves

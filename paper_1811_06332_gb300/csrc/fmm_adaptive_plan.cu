@@ -44,7 +44,7 @@ void ad_free(AdState* a) {
                     a->zc, a->rad, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
                     a->oq, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
                     a->pos32, a->M, a->L, a->M32, a->counter, a->ptgt, a->nodeF, a->porder, a->iota,
-                    a->bcnt, a->boff, a->bsrc, a->fsum};
+                    a->bcnt, a->boff, a->bsrc, a->fsum, a->nodeK};
     for (void* p : ptrs) cudaFree(p);
     if (a->gexec) cudaGraphExecDestroy(a->gexec);
     delete a;
@@ -340,7 +340,8 @@ int ad_learn_prepare(AdState* a, cudaStream_t s) {
     GROW(a->bcnt, a->cap_bcnt, (FMM_PMAX + 1) * nn * 4 + 4);
     GROW(a->boff, a->cap_boff, (FMM_PMAX + 1) * nn * 4 + 4);
     GROW(a->bsrc, a->cap_bsrc, np * 4);
-    GROW(a->fsum, a->cap_fsum, nn * 4);
+    GROW(a->fsum, a->cap_fsum, 2 * nn * 4);
+    GROW(a->nodeK, a->cap_nodeK, nn * 4);
     if (a->nn > 0) {
         ad_pair_targets_launch(a->nn, a->nm2l, a->moff, a->ptgt, s);
         ad_iota(a->nn, a->iota, s);

@@ -8,7 +8,8 @@
 //   a = max(r_A/|d|, 1e-6), b = max(r_B/|d|, 1e-6)
 //   f0 = ln(a + b) (the MAC ratio of App. C), f1 = ln a, f2 = ln b,
 //   f3..f6 = ln max(|M_A^(j)| / (|M_A,0| r_A^j), 1e-6), j = 1..4,
-//   f7..f8 = the same for M_B, j = 1..2,  f9 = ln n_A, f10 = ln n_B,
+//   f7..f8 = the same for M_B, j = 1..2,  f9 = ln min(n_A, 1024),
+//   f10 = ln min(n_B, 1024),
 //   f11 = ln max(g_AB / T_B, 1e-12), g_AB = |M_A,0|/|d|^2 and T_B the sum of
 //         g over the M2L lists of B and of all its ancestors,
 // with |M^(j)|^2 = sum_{|m|=j} j!/m! M_m^2 (Frobenius norm of the rank-j
@@ -50,7 +51,7 @@ __global__ void k_node_feat(int nn, int ld, const double* __restrict__ Mn, const
         if (m0 > 0.0 && r > 0.0) g = sqrt(s) / (m0 * rj);
         out[j - 1] = (float)log(g > 1e-6 ? g : 1e-6);
     }
-    out[4] = logf((float)(ne[c] - nb[c]));
+    out[4] = logf((float)min(ne[c] - nb[c], 1024));   // counts saturate at 1024
     out[5] = (float)rad[c];
     out[6] = 0.f;           // T_c, set by the far-field estimate
     out[7] = (float)m0;     // |M_0| (the same in scaled units)
@@ -63,7 +64,7 @@ __global__ void k_node_feat(int nn, int ld, const double* __restrict__ Mn, const
 // then T_c = sum of S over c and its ancestors (written to nodeF slot 6)
 __global__ void k_far_sum(int nn, const int* __restrict__ off, const int* __restrict__ src,
                           const int4* __restrict__ ic, float scale, const float* __restrict__ nodeF,
-                          float* __restrict__ S) {
+                          float* __restrict__ S, float* __restrict__ K) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nn) return;
     const int4 it = ic[c];
@@ -76,14 +77,17 @@ __global__ void k_far_sum(int nn, const int* __restrict__ off, const int* __rest
         acc += nodeF[8 * (int64_t)A + 7] / (dx * dx + dy * dy + dz * dz);
     }
     S[c] = acc;
+    K[c] = (float)(off[c + 1] - off[c]);
 }
+// (also K_c = number of M2L pairs of c and its ancestors, stored as log10 max(K_c, 1))
 __global__ void k_far_down(int nn, const int* __restrict__ parent, const float* __restrict__ S,
-                           float* __restrict__ nodeF) {
+                           const float* __restrict__ K, float* __restrict__ nodeF, float* __restrict__ nodeK) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nn) return;
-    float t = 0.f;
-    for (int a = c; a >= 0; a = parent[a]) t += S[a];
+    float t = 0.f, kk = 0.f;
+    for (int a = c; a >= 0; a = parent[a]) { t += S[a]; kk += K[a]; }
     nodeF[8 * (int64_t)c + 6] = t;
+    nodeK[c] = log10f(fmaxf(kk, 1.f));
 }
 
 // M2L pair index -> its target (CSR rows expanded)
@@ -429,8 +433,9 @@ int ad_bucket_csr(int n, int nn, const uint64_t* key, const int* val, const int*
 
 int ad_far_estimate(AdState* a, cudaStream_t s) {
     if (a->nn <= 0) return 0;
-    k_far_sum<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->moff, a->msrc, a->ic, a->scale32, a->nodeF, a->fsum);
-    k_far_down<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->parent, a->fsum, a->nodeF);
+    k_far_sum<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->moff, a->msrc, a->ic, a->scale32, a->nodeF, a->fsum,
+                                                  a->fsum + a->nn);
+    k_far_down<<<(a->nn + 255) / 256, 256, 0, s>>>(a->nn, a->parent, a->fsum, a->fsum + a->nn, a->nodeF, a->nodeK);
     count_launch();
     count_launch();
     return 0;

@@ -3,7 +3,7 @@
 // Each CTA (128 threads, persistent over tiles) takes 128 M2L pairs per
 // tile, one pair per thread (= one TMEM lane).  The four layers are four
 // dense products with FP32 accumulation in TMEM:
-//     D[128 x 64] = A[128 x 16] . W1^T      (features, BF16, padded 11 -> 16)
+//     D[128 x 64] = A[128 x 16] . W1^T      (features, BF16, padded 12 -> 16)
 //     D[128 x 64] = A[128 x 64] . W2^T      (h1 in BF16), then W3 the same way
 //     D[128 x 16] = A[128 x 64] . W4^T      (9 outputs padded to 16)
 // Between layers every thread reads its TMEM row (tcgen05.ld), adds the
@@ -104,26 +104,28 @@ __device__ __forceinline__ void mt_ld16(uint32_t ta, float* out) {
     for (int e = 0; e < 16; ++e) out[e] = __uint_as_float(v[e]);
 }
 
-// row r of the next A operand (K = 64) from 64 FP32 values: bias, ReLU, BF16
-__device__ __forceinline__ void mt_store_hidden(unsigned char* sA, int r, const float* acc, const float* bias) {
+// half (32 columns, c0 = 0 or 4 chunks of 8) of row r of the next A operand
+// (K = 64) from FP32 values: bias, ReLU, BF16
+__device__ __forceinline__ void mt_store_hidden(unsigned char* sA, int r, const float* acc, const float* bias, int c0) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < 4; ++c) {
         __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(fmaxf(acc[8 * c + e] + bias[8 * c + e], 0.f));
-        *(uint4*)(sA + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = *(const uint4*)h;
+        *(uint4*)(sA + (r >> 3) * 1024 + (c0 + c) * 128 + (r & 7) * 16) = *(const uint4*)h;
     }
 }
 
-// MODE 0: features read from feat[n][11], predictions written to pred[n][9].
+// MODE 0: features read from feat[n][12], predictions written to pred[n][9].
 // MODE 1: features of the plan's M2L pairs, the chosen order (lowest p in
-//         2..pmax whose prediction is <= thr, else pmax) written to porder.
+//         2..pmax whose prediction is <= thr - log10(K_B)/2, else pmax)
+//         written to porder.
 template <int MODE>
 __global__ void __launch_bounds__(128)
 k_mlp_tc(int64_t n, const unsigned char* __restrict__ wdev, const float* __restrict__ feat, float* __restrict__ pred,
          const int* __restrict__ ptgt, const int* __restrict__ msrc, const int4* __restrict__ ic, float scale,
-         const float* __restrict__ nodeF, float thr, int pmax, signed char* __restrict__ porder,
-         int* __restrict__ err) {
+         const float* __restrict__ nodeF, const float* __restrict__ nodeK, float thr, int pmax,
+         signed char* __restrict__ porder, int* __restrict__ err) {
     extern __shared__ unsigned char mt_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)mt_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = sm + MT_A;
@@ -172,7 +174,7 @@ k_mlp_tc(int64_t n, const unsigned char* __restrict__ wdev, const float* __restr
             *(uint4*)(sA + (tid >> 3) * 256 + (tid & 7) * 16) = *(const uint4*)&z[0];
             *(uint4*)(sA + (tid >> 3) * 256 + 128 + (tid & 7) * 16) = *(const uint4*)&z[8];
         }
-        float acc[64];
+        float acc[32];
         for (int layer = 0; layer < 4; ++layer) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -189,9 +191,11 @@ k_mlp_tc(int64_t n, const unsigned char* __restrict__ wdev, const float* __restr
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (layer < 3) {
-                mt_ld32(trow, acc);
-                mt_ld32(trow + 32, acc + 32);
-                mt_store_hidden(sA, tid, acc, layer == 0 ? b1 : layer == 1 ? b2 : b3);
+                const float* bias = layer == 0 ? b1 : layer == 1 ? b2 : b3;
+                mt_ld32(trow, acc);            // columns 0..31
+                mt_store_hidden(sA, tid, acc, bias, 0);
+                mt_ld32(trow + 32, acc);       // columns 32..63
+                mt_store_hidden(sA, tid, acc, bias + 32, 4);
             } else {
                 mt_ld16(trow, acc);
             }
@@ -204,9 +208,12 @@ k_mlp_tc(int64_t n, const unsigned char* __restrict__ wdev, const float* __restr
             if (MODE == 0) {
                 for (int j = 0; j < FMM_MLP_NOUT; ++j) pred[k * FMM_MLP_NOUT + j] = y[j];
             } else {
+                // budget per pair: target / sqrt(K_B), K_B the M2L pairs on the
+                // target's ancestor chain (nodeK = log10 K_B)
+                const float tk = thr - 0.5f * nodeK[ptgt[k]];
                 int p = pmax;
                 for (int q = pmax; q >= 2; --q)
-                    if (y[q - 2] <= thr) p = q;
+                    if (y[q - 2] <= tk) p = q;
                 porder[k] = (signed char)p;
             }
         }
@@ -261,7 +268,7 @@ void mlp_pack_device(const float* blob, unsigned char* out) {
 
 static int mt_grid(int64_t n, int sms) {
     const int64_t tiles = (n + 127) / 128;
-    const int64_t g = (int64_t)sms * 4;
+    const int64_t g = (int64_t)sms * 5;   // 5 CTAs per SM: 40 KB shared memory and 72 registers each
     return (int)(tiles < g ? tiles : g);
 }
 
@@ -269,7 +276,7 @@ int mlp_predict_dev(const unsigned char* wdev, int64_t n, const float* feat, flo
                     cudaStream_t s) {
     if (n <= 0) return 0;
     k_mlp_tc<0><<<mt_grid(n, sms), 128, MT_SMEM, s>>>(n, wdev, feat, pred, nullptr, nullptr, nullptr, 0.f, nullptr,
-                                                      0.f, 0, nullptr, err);
+                                                      nullptr, 0.f, 0, nullptr, err);
     count_launch();
     return 0;
 }
@@ -277,7 +284,8 @@ int mlp_predict_dev(const unsigned char* wdev, int64_t n, const float* feat, flo
 int mlp_orders_dev(const unsigned char* wdev, AdState* a, float thr, int pmax, int sms, int* err, cudaStream_t s) {
     if (a->nm2l <= 0) return 0;
     k_mlp_tc<1><<<mt_grid(a->nm2l, sms), 128, MT_SMEM, s>>>(a->nm2l, wdev, nullptr, nullptr, a->ptgt, a->msrc, a->ic,
-                                                            a->scale32, a->nodeF, thr, pmax, a->porder, err);
+                                                            a->scale32, a->nodeF, a->nodeK, thr, pmax, a->porder,
+                                                            err);
     count_launch();
     return 0;
 }

@@ -79,13 +79,13 @@ def force_error(acc, Xd, nsample: int, seed: int) -> float:
 
 
 def calibrate(blob, X, p: int, max_leaf: int, theta: float, target: float, prec=F.FP32,
-              grid=tuple(-2.0 + 0.25 * k for k in range(13)), margin: float = 0.8, seed: int = 5):
+              grid=tuple(-1.0 + 0.25 * k for k in range(13)), margin: float = 0.8, seed: int = 5):
     """Largest log10 kappa of the grid (tried in increasing order, stopping at
     the first miss) whose learned FMM on the set X meets margin * target.
-    The labels measure a pair's error against the total force at its
-    targets, and a target collects the errors of all its pairs, so kappa is
-    typically below 1.  Returns (blob with that kappa, [(log10 kappa, error,
-    mean order)])."""
+    The budget per pair is target * kappa / sqrt(K_B) (fmm_config); kappa
+    absorbs what that scaling leaves out (correlated pair errors, the near
+    field).  Returns (blob with that kappa, [(log10 kappa, error, mean
+    order)])."""
     dev = torch.device("cuda", torch.cuda.current_device())
     Xd = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in X]
     best = None

@@ -235,7 +235,10 @@ def test_learned_fmm_meets_target_with_fewer_terms(trained_blob):
     assert mean_p < 8.0
     # the same decisions as the oracle composition (features -> BF16 MLP -> select)
     tgt_o, src_o, feat_o, _ = O.adaptive_pairs(*X, 16, 0.6, features=True, labels=False)
-    ords_o = mlp.select(mlp.forward(blob, feat_o.astype(np.float32), bf16=True), -4.0, float(blob[6]), 10)
+    _, _, _, par = O.adaptive_tree(*X[:3], 16, parents=True)
+    lk = np.log10(np.maximum(mlp.chain_pairs(tgt_o, par), 1.0))[tgt_o]
+    ords_o = mlp.select(mlp.forward(blob, feat_o.astype(np.float32), bf16=True), -4.0, float(blob[6]), 10,
+                        log10_k=lk)
     counts_o = np.bincount(ords_o, minlength=11)
     assert np.abs(cnt - counts_o).sum() <= 0.01 * cnt.sum()
     plan.close()

@@ -108,6 +108,17 @@ def test_select_lowest_order_meeting_threshold():
                      [-9, -9, -9, -9, -9, -9, -9, -9, -9]], dtype=float)
     np.testing.assert_array_equal(mlp.select(pred, -5.0, 0.5, 10), [6, 10, 2])
     np.testing.assert_array_equal(mlp.select(pred, -5.0, 0.5, 8), [6, 8, 2])
+    # K_B = 100 lowers the threshold by one decade: -4.5 -> -5.5, first <= is p=7 (col 5 = -6)
+    np.testing.assert_array_equal(mlp.select(pred, -5.0, 0.5, 10, log10_k=[2.0, 2.0, 2.0]), [7, 10, 2])
+
+
+def test_chain_pairs_counts_ancestor_lists():
+    #        0
+    #      1   2
+    #     3 4
+    parent = np.array([-1, 0, 0, 1, 1])
+    tgt = np.array([1, 1, 2, 3, 3, 3, 4])     # node 1 has 2 pairs, 2 one, 3 three, 4 one
+    np.testing.assert_array_equal(mlp.chain_pairs(tgt, parent), [0, 2, 1, 5, 3])
 
 
 # ---------------------------------------------------------------- labels
@@ -147,8 +158,8 @@ def test_pairs_are_the_m2l_list(plummer_pairs):
     rho = (np.maximum(zr[src, 3] / d, 1e-6) + np.maximum(zr[tgt, 3] / d, 1e-6))
     assert np.all(0.6 * d > zr[src, 3] + zr[tgt, 3])
     np.testing.assert_allclose(feat[:, 0], np.log(rho), rtol=0, atol=1e-12)
-    np.testing.assert_allclose(feat[:, 9], np.log(rg[src, 1] - rg[src, 0]), atol=1e-12)
-    np.testing.assert_allclose(feat[:, 10], np.log(rg[tgt, 1] - rg[tgt, 0]), atol=1e-12)
+    np.testing.assert_allclose(feat[:, 9], np.log(np.minimum(rg[src, 1] - rg[src, 0], 1024)), atol=1e-12)
+    np.testing.assert_allclose(feat[:, 10], np.log(np.minimum(rg[tgt, 1] - rg[tgt, 0], 1024)), atol=1e-12)
 
 
 def test_shape_features_closed_forms(plummer_pairs):
