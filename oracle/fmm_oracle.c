@@ -667,7 +667,7 @@ int orc_num_threads(void) {
 /* Interaction lists come from a directed dual-tree traversal (App. C, after  */
 /* Dehnen): start from (root, root); a self pair of an inner cell expands to  */
 /* all ordered pairs of its children; a pair (A target, B source) is accepted */
-/* for M2L when theta |z_A - z_B| > r_A + r_B (the MAC), goes to P2P when both */
+/* for M2L when theta |z_A - z_B| > r_A + r_B (the MAC, evaluated squared), goes to P2P when both */
 /* are leaves, and otherwise the larger cell (by radius; the target on ties)  */
 /* is opened, or the one that is not a leaf.  theta = 0 accepts nothing, so   */
 /* the method reduces to the direct sum.                                       */
@@ -831,7 +831,15 @@ static void atree_build(atree_t* T, int64_t n, const double* x, const double* y,
                         for (int j = 0; j < nd[A].nchild; ++j) pl_push(&qb, nd[A].child0 + i, nd[A].child0 + j);
                 continue;
             }
-            if (theta * dist3(nd[A].z, nd[B].z) > nd[A].r + nd[B].r) { pl_push(&m2l, A, B); continue; }
+            /* the MAC of App. C, theta |z_A - z_B| > r_A + r_B, compared squared
+               (both sides are non-negative): theta^2 |z_A - z_B|^2 > (r_A + r_B)^2 */
+            {
+                const double dx = nd[A].z[0] - nd[B].z[0], dy = nd[A].z[1] - nd[B].z[1],
+                             dz = nd[A].z[2] - nd[B].z[2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                const double sr = nd[A].r + nd[B].r;
+                if (theta * theta * d2 > sr * sr) { pl_push(&m2l, A, B); continue; }
+            }
             if (la && lb) { pl_push(&p2p, A, B); continue; }
             if (!la && (lb || nd[A].r >= nd[B].r)) {
                 for (int i = 0; i < nd[A].nchild; ++i) pl_push(&qb, nd[A].child0 + i, B);

@@ -276,38 +276,48 @@ __global__ void k_radii(int lb, int le, const int* __restrict__ nb, const int* _
 // ---------------------------------------------------------------------------
 // directed dual-tree traversal, one breadth-first step per launch pair
 // ---------------------------------------------------------------------------
-// mode per pair: 0 = M2L, 1 = P2P, 2 = self split, 3 = split target, 4 = split source
+// mode per pair: 0 = M2L, 1 = P2P, 2 = self split, 3 = split target, 4 = split source.
+// The MAC theta |z_A - z_B| > r_A + r_B is evaluated squared (both sides are
+// non-negative), theta^2 |z_A - z_B|^2 > (r_A + r_B)^2, with explicitly rounded
+// FP64 operations in the oracle's order: no square root per pair.
 __device__ __forceinline__ int trav_mode(int A, int B, double theta, const int* nchild, const double* zc,
                                          const double* rad) {
     const bool la = nchild[A] == 0, lb = nchild[B] == 0;
     if (A == B) return la ? 1 : 2;
-    if (__dmul_rn(theta, dist3_rn(zc + 3 * A, zc + 3 * B)) > __dadd_rn(rad[A], rad[B])) return 0;
+    const double* a = zc + 3 * A;
+    const double* b = zc + 3 * B;
+    const double dx = __dsub_rn(a[0], b[0]), dy = __dsub_rn(a[1], b[1]), dz = __dsub_rn(a[2], b[2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double sr = __dadd_rn(rad[A], rad[B]);
+    if (__dmul_rn(__dmul_rn(theta, theta), d2) > __dmul_rn(sr, sr)) return 0;
     if (la && lb) return 1;
     if (!la && (lb || rad[A] >= rad[B])) return 3;
     return 4;
 }
 
+// decides every pair of the frontier once (mode kept for the write pass)
 __global__ void k_trav_count(int nq, const int2* __restrict__ q, double theta, const int* __restrict__ nchild,
                              const double* __restrict__ zc, const double* __restrict__ rad, int* __restrict__ cm,
-                             int* __restrict__ cp, int* __restrict__ cq) {
+                             int* __restrict__ cp, int* __restrict__ cq, unsigned char* __restrict__ mode) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nq) return;
     const int A = q[k].x, B = q[k].y;
     const int m = trav_mode(A, B, theta, nchild, zc, rad);
+    mode[k] = (unsigned char)m;
     cm[k] = m == 0;
     cp[k] = m == 1;
     cq[k] = m == 2 ? nchild[A] * nchild[A] : m == 3 ? nchild[A] : m == 4 ? nchild[B] : 0;
 }
 
-__global__ void k_trav_write(int nq, const int2* __restrict__ q, double theta, const int* __restrict__ nchild,
-                             const int* __restrict__ child0, const double* __restrict__ zc,
-                             const double* __restrict__ rad, const int* __restrict__ om, const int* __restrict__ op,
-                             const int* __restrict__ oq, int mbase, int pbase, int2* __restrict__ m2l,
-                             int2* __restrict__ p2p, int2* __restrict__ qn) {
+__global__ void k_trav_write(int nq, const int2* __restrict__ q, const unsigned char* __restrict__ mode,
+                             const int* __restrict__ nchild, const int* __restrict__ child0,
+                             const int* __restrict__ om, const int* __restrict__ op, const int* __restrict__ oq,
+                             int mbase, int pbase, int2* __restrict__ m2l, int2* __restrict__ p2p,
+                             int2* __restrict__ qn) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nq) return;
     const int A = q[k].x, B = q[k].y;
-    const int m = trav_mode(A, B, theta, nchild, zc, rad);
+    const int m = mode[k];
     if (m == 0) { m2l[mbase + om[k]] = make_int2(A, B); return; }
     if (m == 1) { p2p[pbase + op[k]] = make_int2(A, B); return; }
     int o = oq[k];
@@ -632,15 +642,15 @@ int ad_radii(int lb, int le, const int* nb, const int* ne, const int* child0, co
     return 0;
 }
 int ad_trav_count(int nq, const int2* q, double theta, const int* nchild, const double* zc, const double* rad,
-                  int* cm, int* cp, int* cq, cudaStream_t s) {
-    k_trav_count<<<G256(nq)>>>(nq, q, theta, nchild, zc, rad, cm, cp, cq);
+                  int* cm, int* cp, int* cq, unsigned char* mode, cudaStream_t s) {
+    k_trav_count<<<G256(nq)>>>(nq, q, theta, nchild, zc, rad, cm, cp, cq, mode);
     count_launch();
     return 0;
 }
-int ad_trav_write(int nq, const int2* q, double theta, const int* nchild, const int* child0, const double* zc,
-                  const double* rad, const int* om, const int* op, const int* oq, int mbase, int pbase, int2* m2l,
-                  int2* p2p, int2* qn, cudaStream_t s) {
-    k_trav_write<<<G256(nq)>>>(nq, q, theta, nchild, child0, zc, rad, om, op, oq, mbase, pbase, m2l, p2p, qn);
+int ad_trav_write(int nq, const int2* q, const unsigned char* mode, const int* nchild, const int* child0,
+                  const int* om, const int* op, const int* oq, int mbase, int pbase, int2* m2l, int2* p2p, int2* qn,
+                  cudaStream_t s) {
+    k_trav_write<<<G256(nq)>>>(nq, q, mode, nchild, child0, om, op, oq, mbase, pbase, m2l, p2p, qn);
     count_launch();
     return 0;
 }

@@ -25,6 +25,7 @@ struct AdState {
     // traversal
     int2 *q0 = nullptr, *q1 = nullptr;
     int *cm = nullptr, *cp = nullptr, *cq = nullptr, *om = nullptr, *op = nullptr, *oq = nullptr;
+    unsigned char* tmode = nullptr;   // traversal decision of each frontier pair
     int2 *m2l = nullptr, *p2p = nullptr;
     int *moff = nullptr, *msrc = nullptr, *poff = nullptr, *psrc = nullptr, *order = nullptr, *leaf = nullptr;
     int4* ic = nullptr;        // integer node centres (fmm_adaptive_leaf.cu)
@@ -40,7 +41,7 @@ struct AdState {
            cap_v1 = 0, cap_hist = 0, cap_hsum = 0, cap_scr = 0, cap_box = 0, cap_part = 0, cap_lev = 0, cap_ix = 0,
            cap_iy = 0, cap_iz = 0, cap_nb = 0, cap_ne = 0, cap_child0 = 0, cap_nchild = 0, cap_parent = 0,
            cap_zc = 0, cap_rad = 0, cap_bounds = 0, cap_nch = 0, cap_choff = 0, cap_q0 = 0, cap_q1 = 0, cap_cm = 0,
-           cap_cp = 0, cap_cq = 0, cap_om = 0, cap_op = 0, cap_oq = 0, cap_m2l = 0, cap_p2p = 0, cap_moff = 0,
+           cap_cp = 0, cap_cq = 0, cap_om = 0, cap_op = 0, cap_oq = 0, cap_tmode = 0, cap_m2l = 0, cap_p2p = 0, cap_moff = 0,
            cap_msrc = 0, cap_poff = 0, cap_psrc = 0, cap_order = 0, cap_leaf = 0, cap_ic = 0, cap_pos32 = 0,
            cap_M = 0, cap_L = 0, cap_M32 = 0, cap_counter = 0;
     // learned per-pair M2L order (fmm_learn.cu, fmm_mlp_tc.cu)
@@ -101,10 +102,10 @@ int ad_centres(int nn, const int* lev, const int* ix, const int* iy, const int* 
 int ad_radii(int lb, int le, const int* nb, const int* ne, const int* child0, const int* nchild, const double* zc,
              const double* xs, const double* ys, const double* zs, double* rad, cudaStream_t s);
 int ad_trav_count(int nq, const int2* q, double theta, const int* nchild, const double* zc, const double* rad,
-                  int* cm, int* cp, int* cq, cudaStream_t s);
-int ad_trav_write(int nq, const int2* q, double theta, const int* nchild, const int* child0, const double* zc,
-                  const double* rad, const int* om, const int* op, const int* oq, int mbase, int pbase, int2* m2l,
-                  int2* p2p, int2* qn, cudaStream_t s);
+                  int* cm, int* cp, int* cq, unsigned char* mode, cudaStream_t s);
+int ad_trav_write(int nq, const int2* q, const unsigned char* mode, const int* nchild, const int* child0,
+                  const int* om, const int* op, const int* oq, int mbase, int pbase, int2* m2l, int2* p2p, int2* qn,
+                  cudaStream_t s);
 int ad_pair_keys(int n, const int2* pr, uint64_t* key, int* val, cudaStream_t s);
 int ad_pair_csr(int n, const uint64_t* key, const int* val, const int2* pr, int* src, int* cnt, cudaStream_t s);
 int ad_len_keys(int nn, const int* off, uint64_t* key, int* val, cudaStream_t s);

@@ -42,7 +42,7 @@ void ad_free(AdState* a) {
     void* ptrs[] = {a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
                     a->box, a->part, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0, a->nchild, a->parent,
                     a->zc, a->rad, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
-                    a->oq, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
+                    a->oq, a->tmode, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
                     a->pos32, a->M, a->L, a->M32, a->counter, a->ptgt, a->nodeF, a->porder, a->iota,
                     a->bcnt, a->boff, a->bsrc, a->fsum, a->nodeK};
     for (void* p : ptrs) cudaFree(p);
@@ -158,7 +158,8 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         GROW(a->cm, a->cap_cm, (size_t)(nq + 1) * 4); GROW(a->cp, a->cap_cp, (size_t)(nq + 1) * 4);
         GROW(a->cq, a->cap_cq, (size_t)(nq + 1) * 4); GROW(a->om, a->cap_om, (size_t)(nq + 1) * 4);
         GROW(a->op, a->cap_op, (size_t)(nq + 1) * 4); GROW(a->oq, a->cap_oq, (size_t)(nq + 1) * 4);
-        ad_trav_count(nq, (const int2*)a->q0, theta, a->nchild, a->zc, a->rad, a->cm, a->cp, a->cq, s);
+        GROW(a->tmode, a->cap_tmode, (size_t)(nq + 1));
+        ad_trav_count(nq, (const int2*)a->q0, theta, a->nchild, a->zc, a->rad, a->cm, a->cp, a->cq, a->tmode, s);
         int tot3[3] = {0, 0, 0};
         scan_excl_int(a->cm, a->om, nq, a->scr, s);
         scan_excl_int(a->cp, a->op, nq, a->scr, s);
@@ -171,8 +172,8 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         GROW(a->m2l, a->cap_m2l, (size_t)(nm + tm + 1) * 8);
         GROW(a->p2p, a->cap_p2p, (size_t)(np + tp + 1) * 8);
         GROW(a->q1, a->cap_q1, (size_t)(tq + 1) * 8);
-        ad_trav_write(nq, (const int2*)a->q0, theta, a->nchild, a->child0, a->zc, a->rad, a->om, a->op, a->oq, nm,
-                      np, (int2*)a->m2l, (int2*)a->p2p, (int2*)a->q1, s);
+        ad_trav_write(nq, (const int2*)a->q0, a->tmode, a->nchild, a->child0, a->om, a->op, a->oq, nm, np,
+                      (int2*)a->m2l, (int2*)a->p2p, (int2*)a->q1, s);
         nm += tm;
         np += tp;
         std::swap(a->q0, a->q1);
