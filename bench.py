@@ -248,9 +248,15 @@ def run_gpu(args):
     tc = None
     if prec == F.GEMM_BF16X3:
         # executed tensor-core work of levels 4..6: per tile of 128 targets and
-        # offset, 3 passes of a 128 x 96 x 96 BF16 product
+        # offset, 3 passes; the local components run in N-chunks of cw rows,
+        # chunk j (lowest rank a_j) over the (p - a_j + 1)^2 multipole columns
+        # it needs, rounded up to K-steps of 16 (the kernel's chunk rule)
+        cw = int(os.environ.get("FMM_TC_CHUNK", "32"))
+        nc = (P + 1) ** 2
+        rank = [a for a in range(P + 1) for _ in range(2 * a + 1)]
+        cols = sum(cw * 16 * (((P - rank[r0] + 1) ** 2 + 15) // 16) for r0 in range(0, nc, cw))
         tiles = sum(8 ** (l - 1) // 128 * 8 for l in range(4, DEPTH + 1))
-        tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * 96 * 96}
+        tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * cols}
     if prec == F.FP64:
         peak = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
         peak_note = "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
@@ -529,11 +535,26 @@ def run_learned(args):
                 stream.synchronize()
                 if k >= warmup:
                     times.append(e0.elapsed_time(e1))
+        err = order_model.force_error(out[1:], X, 4096, 5)
+        # stage breakdown through the per-operator entry points (no graph)
+        names = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p"]
+        with torch.cuda.stream(stream):
+            flush.fill_(0.5)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+            ev[0].record(stream)
+            plan.fmm_build_tree(*X, stream=stream); ev[1].record(stream)
+            plan.fmm_p2m(stream=stream); ev[2].record(stream)
+            plan.fmm_m2m(stream=stream); ev[3].record(stream)
+            plan.fmm_m2l(stream=stream); ev[4].record(stream)
+            plan.fmm_l2l(stream=stream); ev[5].record(stream)
+            plan.fmm_l2p(out[0], out[1], out[2], out[3], stream=stream); ev[6].record(stream)
+            plan.fmm_p2p(out[0], out[1], out[2], out[3], stream=stream); ev[7].record(stream)
+            stream.synchronize()
+        stages = {nm: round(ev[i].elapsed_time(ev[i + 1]), 3) for i, nm in enumerate(names)}
         st = plan.stats()
         plan.close()
-        err = order_model.force_error(out[1:], X, 4096, 5)
         r = {"p": p, "ms_per_step": float(np.mean(times)), "rel_force_err": err,
-             "particles_per_s": n / (np.mean(times) * 1e-3), "m2l_pairs": st["m2l_pairs"]}
+             "particles_per_s": n / (np.mean(times) * 1e-3), "m2l_pairs": st["m2l_pairs"], "stage_ms": stages}
         if "pairs_per_order" in st:
             c = np.array(st["pairs_per_order"], dtype=np.float64)
             r["pairs_per_order"] = st["pairs_per_order"]
