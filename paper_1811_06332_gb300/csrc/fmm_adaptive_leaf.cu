@@ -235,10 +235,13 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
 // ---------------------------------------------------------------------------
 // FP32 P2P over the near-field lists: one warp per target leaf from an
 // atomic work counter (persistent grid).  Up to 64 targets per pass: above
-// 32 each lane keeps two targets; at or below 16 the targets are spread over
-// lane groups that split the staged sources and are summed by shuffles.
-// Sources are staged 32 at a time as float4 (offset from the target leaf
-// centre, charge); r = 0 pairs (the particle itself, coincident points)
+// 32 each lane keeps two, at or below 16 the targets are spread over lane
+// groups that split the staged sources and are summed by shuffles.
+// Sources of up to 32 source leaves are taken together: a warp prefix sum of
+// their counts maps lane g of a chunk to (leaf, particle) by a fixed
+// five-step search, so every staged chunk holds 32 sources (float4: offset
+// from the target leaf centre via the integer centres, charge) whatever the
+// leaf sizes.  r = 0 pairs (the particle itself, coincident points)
 // contribute nothing.  Accumulates into caller order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void p2p_acc(const float4 s, float xi, float yi, float zi, float& ph, float& gx,
@@ -251,6 +254,30 @@ __device__ __forceinline__ void p2p_acc(const float4 s, float xi, float yi, floa
     gx = fmaf(qir3, dx, gx);
     gy = fmaf(qir3, dy, gy);
     gz = fmaf(qir3, dz, gz);
+}
+
+// Stages chunk [c0, c0 + 32) of the concatenated sources of one batch of
+// source leaves into ss (lane l holds leaf l of the batch: start sb, count
+// excl/incl prefix, centre offset o*).  Returns the number staged.
+__device__ __forceinline__ int p2p_stage(float4* ss, int lane, int c0, int total, int incl, int excl, int sb,
+                                         float ox, float oy, float oz, const float4* __restrict__ pos32) {
+    const int g = min(c0 + lane, total - 1);
+    int i = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, i + step - 1);
+        if (v <= g) i += step;
+    }
+    const int sbi = __shfl_sync(0xffffffffu, sb, i), exi = __shfl_sync(0xffffffffu, excl, i);
+    const float oxi = __shfl_sync(0xffffffffu, ox, i), oyi = __shfl_sync(0xffffffffu, oy, i),
+                ozi = __shfl_sync(0xffffffffu, oz, i);
+    __syncwarp();
+    if (c0 + lane < total) {
+        const float4 v = pos32[sbi + (g - exi)];
+        ss[lane] = make_float4(v.x + oxi, v.y + oyi, v.z + ozi, v.w);
+    }
+    __syncwarp();
+    return min(32, total - c0);
 }
 
 template <int WARPS>
@@ -272,74 +299,62 @@ k_ad_p2p32(int nwork, const int* __restrict__ work, const int* __restrict__ off,
         const int k0 = off[c], k1 = off[c + 1];
         for (int t0 = b; t0 < e; t0 += 64) {
             const int tn = min(64, e - t0);
-            if (tn > 32) {
-                // two targets per lane
-                const int i0 = t0 + lane, i1 = t0 + 32 + lane;
-                const bool a1 = lane < tn - 32;
-                const float4 p0 = pos32[i0];
-                const float4 p1 = a1 ? pos32[i1] : make_float4(0.f, 0.f, 0.f, 0.f);
-                float ph0 = 0.f, gx0 = 0.f, gy0 = 0.f, gz0 = 0.f, ph1 = 0.f, gx1 = 0.f, gy1 = 0.f, gz1 = 0.f;
-                for (int k = k0; k < k1; ++k) {
-                    const int S = src[k];
+            const bool two = tn > 32;
+            int tp = 1;
+            while (tp < tn) tp <<= 1;
+            const int G = two ? 1 : 32 / tp, grp = two ? 0 : lane / tp, tl = two ? lane : lane % tp;
+            const int i0 = t0 + tl, i1 = t0 + 32 + lane;
+            const bool a0 = two ? true : tl < tn, a1 = two && lane < tn - 32;
+            const float4 p0 = a0 ? pos32[i0] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 p1 = a1 ? pos32[i1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float ph0 = 0.f, gx0 = 0.f, gy0 = 0.f, gz0 = 0.f, ph1 = 0.f, gx1 = 0.f, gy1 = 0.f, gz1 = 0.f;
+            for (int kb = k0; kb < k1; kb += 32) {
+                // metadata of up to 32 source leaves, one per lane
+                const int kk = kb + lane;
+                int cntS = 0, sb = 0;
+                float ox = 0.f, oy = 0.f, oz = 0.f;
+                if (kk < k1) {
+                    const int S = src[kk];
                     const int4 cs = ic[S];
-                    const float ox = (float)(cs.x - ct.x) * scale, oy = (float)(cs.y - ct.y) * scale,
-                                oz = (float)(cs.z - ct.z) * scale;
-                    const int sb = nb[S], se = ne[S];
-                    for (int s0 = sb; s0 < se; s0 += 32) {
-                        __syncwarp();
-                        if (s0 + lane < se) {
-                            const float4 v = pos32[s0 + lane];
-                            ss[w][lane] = make_float4(v.x + ox, v.y + oy, v.z + oz, v.w);
-                        }
-                        __syncwarp();
-                        const int cnt = min(32, se - s0);
+                    ox = (float)(cs.x - ct.x) * scale;
+                    oy = (float)(cs.y - ct.y) * scale;
+                    oz = (float)(cs.z - ct.z) * scale;
+                    sb = nb[S];
+                    cntS = ne[S] - sb;
+                }
+                int incl = cntS;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
+                for (int c0 = 0; c0 < total; c0 += 32) {
+                    const int cnt = p2p_stage(ss[w], lane, c0, total, incl, excl, sb, ox, oy, oz, pos32);
+                    if (two) {
                         for (int j = 0; j < cnt; ++j) {
                             const float4 sv = ss[w][j];
                             p2p_acc(sv, p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
                             p2p_acc(sv, p1.x, p1.y, p1.z, ph1, gx1, gy1, gz1);
                         }
+                    } else if (a0) {
+                        for (int j = grp; j < cnt; j += G) p2p_acc(ss[w][j], p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
                     }
                 }
-                int o = perm[i0];
-                pot[o] -= (double)ph0; ax[o] += (double)gx0; ay[o] += (double)gy0; az[o] += (double)gz0;
-                if (a1) {
-                    o = perm[i1];
-                    pot[o] -= (double)ph1; ax[o] += (double)gx1; ay[o] += (double)gy1; az[o] += (double)gz1;
-                }
-            } else {
-                int tp = 1;
-                while (tp < tn) tp <<= 1;
-                const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
-                const int ti = t0 + tl;
-                const bool act = tl < tn;
-                const float4 pi = act ? pos32[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
-                float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-                for (int k = k0; k < k1; ++k) {
-                    const int S = src[k];
-                    const int4 cs = ic[S];
-                    const float ox = (float)(cs.x - ct.x) * scale, oy = (float)(cs.y - ct.y) * scale,
-                                oz = (float)(cs.z - ct.z) * scale;
-                    const int sb = nb[S], se = ne[S];
-                    for (int s0 = sb; s0 < se; s0 += 32) {
-                        __syncwarp();
-                        if (s0 + lane < se) {
-                            const float4 v = pos32[s0 + lane];
-                            ss[w][lane] = make_float4(v.x + ox, v.y + oy, v.z + oz, v.w);
-                        }
-                        __syncwarp();
-                        const int cnt = min(32, se - s0);
-                        if (act)
-                            for (int j = grp; j < cnt; j += G) p2p_acc(ss[w][j], pi.x, pi.y, pi.z, ph, gx, gy, gz);
-                    }
-                }
+            }
+            if (!two) {
                 for (int o = tp; o < 32; o <<= 1) {
-                    ph += __shfl_xor_sync(0xffffffffu, ph, o); gx += __shfl_xor_sync(0xffffffffu, gx, o);
-                    gy += __shfl_xor_sync(0xffffffffu, gy, o); gz += __shfl_xor_sync(0xffffffffu, gz, o);
+                    ph0 += __shfl_xor_sync(0xffffffffu, ph0, o); gx0 += __shfl_xor_sync(0xffffffffu, gx0, o);
+                    gy0 += __shfl_xor_sync(0xffffffffu, gy0, o); gz0 += __shfl_xor_sync(0xffffffffu, gz0, o);
                 }
-                if (act && grp == 0) {
-                    const int o = perm[ti];
-                    pot[o] -= (double)ph; ax[o] += (double)gx; ay[o] += (double)gy; az[o] += (double)gz;
-                }
+            }
+            if (a0 && grp == 0) {
+                const int o = perm[i0];
+                pot[o] -= (double)ph0; ax[o] += (double)gx0; ay[o] += (double)gy0; az[o] += (double)gz0;
+            }
+            if (a1) {
+                const int o = perm[i1];
+                pot[o] -= (double)ph1; ax[o] += (double)gx1; ay[o] += (double)gy1; az[o] += (double)gz1;
             }
         }
     }

@@ -322,7 +322,7 @@ int ad_run_p2p(AdState* a, int prec, int sms, double* pot, double* ax, double* a
     cudaMemsetAsync(a->counter + 1, 0, 4, s);
     if (prec)
         ad_p2p32(a->nleaf, a->leaf, a->poff, a->psrc, a->nb, a->ne, a->ic, a->scale32, a->pos32, a->perm, pot, ax, ay,
-                 az, a->counter + 1, 4 * sms, s);
+                 az, a->counter + 1, 8 * sms, s);
     else
         ad_p2p(a->nleaf, a->leaf, a->poff, a->psrc, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs, a->perm, pot,
                ax, ay, az, a->counter + 1, 4 * sms, s);
