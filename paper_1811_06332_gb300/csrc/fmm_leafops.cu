@@ -385,22 +385,48 @@ k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* _
         const float4 pa = va ? pos[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 pb = vb ? pos[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
         float fa = 0.f, xa = 0.f, ya = 0.f, za = 0.f, fb = 0.f, xb = 0.f, yb = 0.f, zb = 0.f;
-#pragma unroll 1
-        for (int nb = 0; nb < 27; ++nb) {
-            const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+        // the 27 neighbour leaves, one per lane: start, count, centre offset
+        int cntS = 0, sbS = 0;
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (lane < 27) {
+            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
             const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
-            if (jx < 0 || jy < 0 || jz < 0 || jx >= side || jy >= side || jz >= side) continue;
-            const int64_t S = cell_index(depth, jx, jy, jz);
-            const int sb = start[S], se = start[S + 1];
-            const float ox = dx * h, oy = dy * h, oz = dz * h;
-            for (int s0 = sb; s0 < se; s0 += 32) {
+            if (jx >= 0 && jy >= 0 && jz >= 0 && jx < side && jy < side && jz < side) {
+                const int64_t S = cell_index(depth, jx, jy, jz);
+                sbS = start[S];
+                cntS = start[S + 1] - sbS;
+                ox = dx * h; oy = dy * h; oz = dz * h;
+            }
+        }
+        int incl = cntS;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
+        // full 32-wide chunks of the concatenated neighbour sources
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            {
+                const int g = min(c0 + lane, total - 1);
+                int i = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, incl, i + step - 1);
+                    if (v <= g) i += step;
+                }
+                const int sbi = __shfl_sync(0xffffffffu, sbS, i), exi = __shfl_sync(0xffffffffu, excl, i);
+                const float oxi = __shfl_sync(0xffffffffu, ox, i), oyi = __shfl_sync(0xffffffffu, oy, i),
+                            ozi = __shfl_sync(0xffffffffu, oz, i);
                 __syncwarp();
-                if (s0 + lane < se) {
-                    const float4 v = pos[s0 + lane];
-                    sP[w][lane] = make_float4(v.x + ox, v.y + oy, v.z + oz, v.w);
+                if (c0 + lane < total) {
+                    const float4 v = pos[sbi + (g - exi)];
+                    sP[w][lane] = make_float4(v.x + oxi, v.y + oyi, v.z + ozi, v.w);
                 }
                 __syncwarp();
-                const int cnt = min(32, se - s0);
+            }
+            {
+                const int cnt = min(32, total - c0);
                 for (int k = grp; k < cnt; k += G) {
                     const float4 sv = sP[w][k];
                     {
