@@ -11,9 +11,10 @@
 namespace fmm {
 
 // ---------------------------------------------------------------------------
-// P2M: one warp per leaf.  Particles are staged 32 at a time; lane c owns
-// the column (nx, ny) of multi-indices and walks nz upward, multiplying by
-// the particle's z offset, so each particle costs one product per component.
+// P2M: one warp per leaf.  Particles are staged 32 at a time together with
+// the powers of their offsets (one particle per lane); lane c owns the column
+// (nx, ny) of multi-indices and adds q x^nx y^ny z^j for every j of the
+// column, one fused product per component and particle.
 // ---------------------------------------------------------------------------
 template <int P, typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
@@ -24,6 +25,7 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
     __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
+    __shared__ T sPw[WARPS][32][3][P + 1];
     __shared__ T sA[WARPS][NS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * WARPS + w;
@@ -65,21 +67,29 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
                 sq[w][lane] = T(qs[a]);
             }
         }
-        __syncwarp();
+        // powers of the staged offsets, one (particle, axis) per lane: sPw[i][d][j] = r_d^j
         const int cnt = min(32, e - a0);
+        if (lane < cnt) {
+            const T r[3] = {sx[w][lane], sy[w][lane], sz[w][lane]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                T v = T(1);
+#pragma unroll
+                for (int j = 0; j <= P; ++j) { sPw[w][lane][d][j] = v; v *= r[d]; }
+            }
+        }
+        __syncwarp();
         for (int i = 0; i < cnt; ++i) {
-            const T rx = sx[w][i], ry = sy[w][i], rz = sz[w][i], qa = sq[w][i];
+            const T qa = sq[w][i];
 #pragma unroll
             for (int k = 0; k < KC; ++k) {
                 if (lane + 32 * k < NCOL) {
-                    T wgt = qa;
-                    for (int t = 0; t < cnx[k]; ++t) wgt *= rx;
-                    for (int t = 0; t < cny[k]; ++t) wgt *= ry;
+                    // q x^nx y^ny, then the column's z powers: one product per component
+                    const T wgt = qa * sPw[w][i][0][cnx[k]] * sPw[w][i][1][cny[k]];
                     const int rem = P - cnx[k] - cny[k];
 #pragma unroll
-                    for (int j = 0; j <= P; ++j) {
-                        if (j <= rem) { acc[k][j] += wgt; wgt *= rz; }
-                    }
+                    for (int j = 0; j <= P; ++j)
+                        if (j <= rem) acc[k][j] = fma(wgt, sPw[w][i][2][j], acc[k][j]);
                 }
             }
         }
