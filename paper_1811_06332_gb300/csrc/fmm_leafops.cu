@@ -123,9 +123,10 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
 }
 
 // ---------------------------------------------------------------------------
-// L2P: one warp per leaf, lanes over particles.  The expansion (full
-// symmetric, dependent traceless components rebuilt) sits in shared memory
-// and every lane reads the same coefficient at the same time.  Nested sums
+// L2P: one half-warp per leaf (two leaves per warp), lanes over particles.
+// The expansion (full symmetric, dependent traceless components rebuilt)
+// sits in shared memory and the lanes of a half read the same coefficient at
+// the same time.  Nested sums
 // Phi = sum_kx ax[kx] sum_ky ay[ky] sum_kz az[kz] L[kx,ky,kz].
 // ---------------------------------------------------------------------------
 template <int P, typename T, int WARPS>
@@ -136,37 +137,41 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
             double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az,
             const float4* __restrict__ pos32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
-    __shared__ T sA[WARPS][NS];
-    __shared__ T sL[WARPS][NS];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * WARPS + w;
-    if (c >= nleaf) return;
-    const int b = start[c], e = start[c + 1];
-    if (b == e) return;
+    __shared__ T sA[WARPS][2][NS];
+    __shared__ T sL[WARPS][2][NS];
+    // two leaves per warp, one per half-warp (leaves hold ~16 particles)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, hl = lane & 15;
+    const int64_t c = ((int64_t)blockIdx.x * WARPS + w) * 2 + h;
+    const bool valid = c < nleaf;
+    const int b = valid ? start[c] : 0, e = valid ? start[c + 1] : 0;
     if (basis) {
         constexpr int NT = (P + 1) * (P + 1);
-        for (int t = lane; t < NT; t += 32) sA[w][t] = T(Lt[(int64_t)t * nleaf + c]);
+        for (int t = hl; t < NT; t += 16)
+            if (valid) sA[w][h][t] = T(Lt[(int64_t)t * nleaf + c]);
         __syncwarp();
-        for (int s = lane; s < NS; s += 32) {
+        for (int s = hl; s < NS; s += 16) {
+            if (!valid) continue;
             const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
             const int j = nx + ny + nz;
             const int row = (j - nx) * (j - nx + 1) / 2 + nz;
             const T* E = expand + off.expand[j] + row * (2 * j + 1);
             T v = T(0);
-            for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][j * j + t];
-            sL[w][s] = v;
+            for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][h][j * j + t];
+            sL[w][h][s] = v;
         }
     } else {
-        for (int s = lane; s < NS; s += 32) sL[w][s] = T(Lt[(int64_t)s * nleaf + c]);
+        for (int s = hl; s < NS; s += 16)
+            if (valid) sL[w][h][s] = T(Lt[(int64_t)s * nleaf + c]);
     }
     __syncwarp();
+    if (!valid || b == e) return;
     int ix, iy, iz;
     cell_coords(depth, c, ix, iy, iz);
-    const double inv_h = (double)(1 << depth), h = 1.0 / inv_h;
-    const double cx = (ix + 0.5) * h, cy = (iy + 0.5) * h, cz = (iz + 0.5) * h;
-    const T* L = sL[w];
-    for (int a0 = b; a0 < e; a0 += 32) {
-        const int a = a0 + lane;
+    const double inv_h = (double)(1 << depth), hc = 1.0 / inv_h;
+    const double cx = (ix + 0.5) * hc, cy = (iy + 0.5) * hc, cz = (iz + 0.5) * hc;
+    const T* L = sL[w][h];
+    for (int a0 = b; a0 < e; a0 += 16) {
+        const int a = a0 + hl;
         if (a >= e) break;
         T rx, ry, rz;
         if (pos32) {
@@ -312,7 +317,7 @@ static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, co
                        const double* zs, const int* perm, const double* Lt, const DevTables& Tb, double* pot,
                        double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32) {
     constexpr int W = 4;
-    k_l2p_leaf2<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(
+    k_l2p_leaf2<P, T, W><<<(unsigned)((nleaf + 2 * W - 1) / (2 * W)), W * 32, 0, s>>>(
         basis, depth, nleaf, start, xs, ys, zs, perm, Lt, tab_of<T>(Tb.expand, Tb.expand32), Tb.offsets(), pot, ax,
         ay, az, pos32);
 }
