@@ -248,6 +248,17 @@ __global__ void k_centres(int nn, const int* __restrict__ lev, const int* __rest
     zc[3 * c + 2] = __dadd_rn(box[2], __dmul_rn((double)iz[c] + 0.5, h));
 }
 
+// radii in units of side / 2^22 (the unit of the integer centres), rounded to FP32
+__global__ void k_radf(int nn, const double* __restrict__ rad, const double* __restrict__ box,
+                       float* __restrict__ radf) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nn) radf[c] = (float)(rad[c] / box[3] * 4194304.0);
+}
+int ad_radf(int nn, const double* rad, const double* box, float* radf, cudaStream_t s) {
+    if (nn > 0) { k_radf<<<(nn + 255) / 256, 256, 0, s>>>(nn, rad, box, radf); count_launch(); }
+    return 0;
+}
+
 // radii of the nodes [lb, le) (one level), children already done
 __global__ void k_radii(int lb, int le, const int* __restrict__ nb, const int* __restrict__ ne,
                         const int* __restrict__ child0, const int* __restrict__ nchild, const double* __restrict__ zc,
@@ -295,14 +306,44 @@ __device__ __forceinline__ int trav_mode(int A, int B, double theta, const int* 
     return 4;
 }
 
+// FP32 screen of the MAC, in units of side / 2^22 so that no operand leaves
+// FP32's normal range: the centre offset is the exact integer difference of
+// the integer centres (below 2^23, exact in FP32), the radii are FP32
+// copies in the same unit.  Outside a relative band around the boundary
+// (wider than the FP32 rounding plus that of the FP64 centres) the FP32
+// comparison gives the FP64 rule's answer; inside it the pair is decided by
+// trav_mode in FP64.  Returns 0 (accept), 1 (reject), 2 (undecided).
+__device__ __forceinline__ int mac_screen(int A, int B, float theta2, float band, const int4* __restrict__ ic,
+                                          const float* __restrict__ radf) {
+    const int4 a = ic[A], b = ic[B];
+    const float dx = (float)(a.x - b.x), dy = (float)(a.y - b.y), dz = (float)(a.z - b.z);
+    const float lhs = theta2 * (dx * dx + dy * dy + dz * dz);
+    const float sr = radf[A] + radf[B];
+    const float rhs = sr * sr;
+    if (lhs > rhs * (1.f + band)) return 0;
+    if (lhs < rhs * (1.f - band)) return 1;
+    return 2;
+}
+
 // decides every pair of the frontier once (mode kept for the write pass)
 __global__ void k_trav_count(int nq, const int2* __restrict__ q, double theta, const int* __restrict__ nchild,
                              const double* __restrict__ zc, const double* __restrict__ rad, int* __restrict__ cm,
-                             int* __restrict__ cp, int* __restrict__ cq, unsigned char* __restrict__ mode) {
+                             int* __restrict__ cp, int* __restrict__ cq, unsigned char* __restrict__ mode,
+                             const int4* __restrict__ ic, const float* __restrict__ radf, float theta2,
+                             float band) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nq) return;
     const int A = q[k].x, B = q[k].y;
-    const int m = trav_mode(A, B, theta, nchild, zc, rad);
+    int m;
+    const int sc = A == B ? 2 : mac_screen(A, B, theta2, band, ic, radf);
+    if (sc == 0) {
+        m = 0;
+    } else if (sc == 1) {
+        const bool la = nchild[A] == 0, lb = nchild[B] == 0;
+        m = (la && lb) ? 1 : (!la && (lb || rad[A] >= rad[B])) ? 3 : 4;
+    } else {
+        m = trav_mode(A, B, theta, nchild, zc, rad);
+    }
     mode[k] = (unsigned char)m;
     cm[k] = m == 0;
     cp[k] = m == 1;
@@ -642,8 +683,10 @@ int ad_radii(int lb, int le, const int* nb, const int* ne, const int* child0, co
     return 0;
 }
 int ad_trav_count(int nq, const int2* q, double theta, const int* nchild, const double* zc, const double* rad,
-                  int* cm, int* cp, int* cq, unsigned char* mode, cudaStream_t s) {
-    k_trav_count<<<G256(nq)>>>(nq, q, theta, nchild, zc, rad, cm, cp, cq, mode);
+                  int* cm, int* cp, int* cq, unsigned char* mode, const int4* ic, const float* radf, float band,
+                  cudaStream_t s) {
+    k_trav_count<<<G256(nq)>>>(nq, q, theta, nchild, zc, rad, cm, cp, cq, mode, ic, radf,
+                               (float)(theta * theta), band);
     count_launch();
     return 0;
 }

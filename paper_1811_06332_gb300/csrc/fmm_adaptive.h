@@ -21,6 +21,7 @@ struct AdState {
     int *lev = nullptr, *ix = nullptr, *iy = nullptr, *iz = nullptr, *nb = nullptr, *ne = nullptr;
     int *child0 = nullptr, *nchild = nullptr, *parent = nullptr;
     double *zc = nullptr, *rad = nullptr;
+    float* radf = nullptr;   // radii / (side / 2^22) rounded to FP32 (MAC screen)
     int *bounds = nullptr, *nch = nullptr, *choff = nullptr;
     // traversal
     int2 *q0 = nullptr, *q1 = nullptr;
@@ -31,6 +32,7 @@ struct AdState {
     int4* ic = nullptr;        // integer node centres (fmm_adaptive_leaf.cu)
     float4* pos32 = nullptr;   // FP32 form: particle offsets from their leaf centre, charge
     float scale32 = 0.f;       // side / 2^22: unit of the integer centres
+    float mac_band = 1e-5f;    // relative band of the FP32 MAC screen
     double side = 0.0;         // side of the root cube (cell of level l: side / 2^l)
     // expansions (node-major)
     double *M = nullptr, *L = nullptr;
@@ -40,7 +42,7 @@ struct AdState {
     size_t cap_xs = 0, cap_ys = 0, cap_zs = 0, cap_qs = 0, cap_perm = 0, cap_k0 = 0, cap_k1 = 0, cap_v0 = 0,
            cap_v1 = 0, cap_hist = 0, cap_hsum = 0, cap_scr = 0, cap_box = 0, cap_part = 0, cap_lev = 0, cap_ix = 0,
            cap_iy = 0, cap_iz = 0, cap_nb = 0, cap_ne = 0, cap_child0 = 0, cap_nchild = 0, cap_parent = 0,
-           cap_zc = 0, cap_rad = 0, cap_bounds = 0, cap_nch = 0, cap_choff = 0, cap_q0 = 0, cap_q1 = 0, cap_cm = 0,
+           cap_zc = 0, cap_rad = 0, cap_radf = 0, cap_bounds = 0, cap_nch = 0, cap_choff = 0, cap_q0 = 0, cap_q1 = 0, cap_cm = 0,
            cap_cp = 0, cap_cq = 0, cap_om = 0, cap_op = 0, cap_oq = 0, cap_tmode = 0, cap_m2l = 0, cap_p2p = 0, cap_moff = 0,
            cap_msrc = 0, cap_poff = 0, cap_psrc = 0, cap_order = 0, cap_leaf = 0, cap_ic = 0, cap_pos32 = 0,
            cap_M = 0, cap_L = 0, cap_M32 = 0, cap_counter = 0;
@@ -102,7 +104,9 @@ int ad_centres(int nn, const int* lev, const int* ix, const int* iy, const int* 
 int ad_radii(int lb, int le, const int* nb, const int* ne, const int* child0, const int* nchild, const double* zc,
              const double* xs, const double* ys, const double* zs, double* rad, cudaStream_t s);
 int ad_trav_count(int nq, const int2* q, double theta, const int* nchild, const double* zc, const double* rad,
-                  int* cm, int* cp, int* cq, unsigned char* mode, cudaStream_t s);
+                  int* cm, int* cp, int* cq, unsigned char* mode, const int4* ic, const float* radf, float band,
+                  cudaStream_t s);
+int ad_radf(int nn, const double* rad, const double* box, float* radf, cudaStream_t s);
 int ad_trav_write(int nq, const int2* q, const unsigned char* mode, const int* nchild, const int* child0,
                   const int* om, const int* op, const int* oq, int mbase, int pbase, int2* m2l, int2* p2p, int2* qn,
                   cudaStream_t s);

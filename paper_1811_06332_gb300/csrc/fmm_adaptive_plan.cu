@@ -41,7 +41,7 @@ void ad_free(AdState* a) {
     if (!a) return;
     void* ptrs[] = {a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
                     a->box, a->part, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0, a->nchild, a->parent,
-                    a->zc, a->rad, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
+                    a->zc, a->rad, a->radf, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
                     a->oq, a->tmode, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
                     a->pos32, a->M, a->L, a->M32, a->counter, a->ptgt, a->nodeF, a->porder, a->iota,
                     a->bcnt, a->boff, a->bsrc, a->fsum, a->nodeK};
@@ -146,6 +146,26 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
     ad_centres(a->nn, a->lev, a->ix, a->iy, a->iz, a->box, a->zc, s);
     for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
         ad_radii(a->lvl[L], a->lvl[L + 1], a->nb, a->ne, a->child0, a->nchild, a->zc, a->xs, a->ys, a->zs, a->rad, s);
+    // integer centres (FP32 centre offsets), FP32 radii (MAC screen), cell side
+    GROW(a->ic, a->cap_ic, (size_t)a->nn * 16);
+    ad_icentre(a->nn, a->lev, a->ix, a->iy, a->iz, a->ic, s);
+    GROW(a->radf, a->cap_radf, (size_t)a->nn * 4);
+    ad_radf(a->nn, a->rad, a->box, a->radf, s);
+    {
+        double bx[4] = {0.0, 0.0, 0.0, 0.0};
+        cudaMemcpyAsync(bx, a->box, 32, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
+        const double side = bx[3];
+        a->scale32 = (float)(side / 4194304.0);
+        a->side = side;
+        // relative band of the FP32 MAC screen: 1e-5 covers its own rounding
+        // (~5e-7); the second term bounds the rounding of the FP64 centre
+        // offsets, whose absolute error grows with the cube's distance from
+        // the origin, relative to the smallest offset side / 2^22
+        const double lo = fmax(fabs(bx[0]), fmax(fabs(bx[1]), fabs(bx[2])));
+        const double band = 1e-5 + ldexp(lo / side + 2.0, -27);
+        a->mac_band = band < 0.5 ? (float)band : 0.5f;
+    }
     // ---------------- directed dual traversal ----------------
     int nq = 1, nm = 0, np = 0;
     GROW(a->q0, a->cap_q0, 64);
@@ -159,7 +179,8 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         GROW(a->cq, a->cap_cq, (size_t)(nq + 1) * 4); GROW(a->om, a->cap_om, (size_t)(nq + 1) * 4);
         GROW(a->op, a->cap_op, (size_t)(nq + 1) * 4); GROW(a->oq, a->cap_oq, (size_t)(nq + 1) * 4);
         GROW(a->tmode, a->cap_tmode, (size_t)(nq + 1));
-        ad_trav_count(nq, (const int2*)a->q0, theta, a->nchild, a->zc, a->rad, a->cm, a->cp, a->cq, a->tmode, s);
+        ad_trav_count(nq, (const int2*)a->q0, theta, a->nchild, a->zc, a->rad, a->cm, a->cp, a->cq, a->tmode, a->ic,
+                      a->radf, a->mac_band, s);
         int tot3[3] = {0, 0, 0};
         scan_excl_int(a->cm, a->om, nq, a->scr, s);
         scan_excl_int(a->cp, a->op, nq, a->scr, s);
@@ -225,19 +246,10 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         a->nleaf = nl;
         a->ntarg = nt;
     }
-    // integer centres (FP32 centre offsets) and FP32 particle offsets
-    GROW(a->ic, a->cap_ic, (size_t)a->nn * 16);
-    ad_icentre(a->nn, a->lev, a->ix, a->iy, a->iz, a->ic, s);
+    // FP32 particle offsets from their leaf centre
     if (prec != 0) {
         GROW(a->pos32, a->cap_pos32, (size_t)n * 16);
         ad_pos32(a->nleaf, a->leaf, a->nb, a->ne, a->zc, a->xs, a->ys, a->zs, a->qs, a->pos32, s);
-    }
-    {
-        double side = 0.0;
-        cudaMemcpyAsync(&side, a->box + 3, 8, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;
-        a->scale32 = (float)(side / 4194304.0);
-        a->side = side;
     }
     GROW(a->M, a->cap_M, (size_t)a->nn * nc * 8);
     GROW(a->L, a->cap_L, (size_t)a->nn * nc * 8);
