@@ -42,8 +42,10 @@ NOMINAL = {"sm_count": 152, "fp64_fma_per_clk_sm": 2, "fp32_fma_per_clk_sm": 128
 # DRAM bytes (read + write) of the M2L kernels per step, from one ncu capture
 # of the level-6 launch (profiles/m2l_*_level6_uniform4M_p8.md) scaled by the
 # cells of all M2L levels; set to None whenever the kernel changes.
-M2L_TRAFFIC = {"fp32": (643.8e6 + 154.9e6) * (299584 / 262144),
-               "bf16x3": (772.4e6 + 174.4e6) * (299520 / 262144)}
+M2L_TRAFFIC = {"fp32": (643.8e6 + 154.9e6) * (299584 / 262144)}
+# nominal dense tensor rates (PFLOP/s): a TF32 contraction takes the measured
+# BF16 peak scaled by their ratio
+NOMINAL_TENSOR = {"bf16": 2.25, "tf32": 1.1}
 
 
 def peaks():
@@ -178,7 +180,7 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    forms = {"fp64": F.FP64, "fp32": F.FP32, "bf16x3": F.GEMM_BF16X3}
+    forms = {"fp64": F.FP64, "fp32": F.FP32, "bf16x3": F.GEMM_BF16X3, "tf32x3": F.GEMM_TF32X3}
     form = args.form
     prec = forms[form]
     # each rank evaluates its own independent particle set (weak scaling)
@@ -246,15 +248,17 @@ def run_gpu(args):
     pk, pk_kind = peaks()
     mhz = pk.get("sm_max_mhz", 2070.0)
     tc = None
-    if prec == F.GEMM_BF16X3:
+    if prec in (F.GEMM_BF16X3, F.GEMM_TF32X3):
         # executed tensor-core work of levels 4..6: per tile of 128 targets and
         # offset, 3 passes; the local components run in N-chunks of cw rows,
         # chunk j (lowest rank a_j) over the (p - a_j + 1)^2 multipole columns
-        # it needs, rounded up to K-steps of 16 (the kernel's chunk rule)
+        # it needs, rounded up to K-steps of 16 (BF16) or 8 (TF32) columns
+        # (the kernel's chunk rule)
         cw = int(os.environ.get("FMM_TC_CHUNK", "32"))
+        ks = 16 if prec == F.GEMM_BF16X3 else 8
         nc = (P + 1) ** 2
-        rank = [a for a in range(P + 1) for _ in range(2 * a + 1)]
-        cols = sum(cw * 16 * (((P - rank[r0] + 1) ** 2 + 15) // 16) for r0 in range(0, nc, cw))
+        rk = [a for a in range(P + 1) for _ in range(2 * a + 1)]   # rank of each traceless component
+        cols = sum(cw * ks * (((P - rk[r0] + 1) ** 2 + ks - 1) // ks) for r0 in range(0, nc, cw))
         tiles = sum(8 ** (l - 1) // 128 * 8 for l in range(4, DEPTH + 1))
         tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * cols}
     if prec == F.FP64:
@@ -270,10 +274,14 @@ def run_gpu(args):
             "m2l_ms_per_step": m2l_ms}
     if tc is not None:
         bf = pk.get("bf16_tflops", 1900.0)
+        src = "bf16_tflops of MEASURED_PEAKS.json (%s, burst)" % pk_kind
+        if prec == F.GEMM_TF32X3:
+            bf *= NOMINAL_TENSOR["tf32"] / NOMINAL_TENSOR["bf16"]
+            src += " x nominal TF32/BF16 ratio 1.1/2.25"
         ex = tc["executed_flop_per_step"] / (m2l_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": "m2l (tensor cores at levels 4..6; FP32 SIMT at 2..3)",
                 "achieved": ex, "peak": bf, "unit": "TFLOP/s", "frac": ex / bf, "traffic": M2L_TRAFFIC.get(form),
-                "peak_source": "bf16_tflops of MEASURED_PEAKS.json (%s, burst)" % pk_kind,
+                "peak_source": src,
                 "executed_flop_per_step": tc["executed_flop_per_step"],
                 "algorithmic_flop_per_step": npairs * 2 * fma,
                 "algorithmic_tflops": achieved, "m2l_ms_per_step": m2l_ms}
@@ -325,7 +333,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32 (P2M, M2L, L2P, P2P) + f64",
-                  "bf16x3": "bf16x3 tensor-core M2L + f32 (P2M, L2P, P2P) + f64"}[form],
+                  "bf16x3": "bf16x3 tensor-core M2L + f32 (P2M, L2P, P2P) + f64",
+                  "tf32x3": "tf32x3 tensor-core M2L + f32 (P2M, L2P, P2P) + f64"}[form],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": form, "p": P, "basis": "traceless", "depth": DEPTH,
                    "particles_per_gpu": N_PART, "m2l_pairs": npairs, "l2": "flushed (256 MiB write) before each step"},
@@ -604,7 +613,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32", "bf16x3", "tf32x3"])
     ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l", "adaptive", "learned"])
     ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
     ap.add_argument("--no-cpu", action="store_true")

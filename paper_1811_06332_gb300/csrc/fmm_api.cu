@@ -49,7 +49,7 @@ struct fmm_plan {
     float* K32 = nullptr;    // 343 x kstride packed FP32 M2L matrices (FMM_FP32)
     float* M32 = nullptr;    // FP32 copy of the multipoles (FMM_FP32)
     int kst = 0;
-    // tensor-core form (FMM_GEMM_BF16X3)
+    // tensor-core forms (FMM_GEMM_BF16X3, FMM_GEMM_TF32X3)
     void* Kbf = nullptr;                 // 343 x {hi, lo} preformatted matrices
     void* Mbf = nullptr;                 // per level >= 4: hi then lo operand tiles
     int64_t mbf_off[FMM_PMAX + 2];       // element offset of level l's hi block
@@ -70,6 +70,8 @@ struct fmm_plan {
     bool mlp_set = false;
     float log10_kappa = 0.f;
 };
+
+static bool is_tc(int prec) { return prec == FMM_GEMM_BF16X3 || prec == FMM_GEMM_TF32X3; }
 
 static void* tc_maps_at(fmm_plan* pl, int l) {
     // 64-byte aligned block of the host-side tensor maps of level l
@@ -366,8 +368,7 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         if (!(cfg->target_rel_err > 0.0)) FAIL(FMM_ERR_ARG, "learned_p needs target_rel_err > 0");
     }
     if (cfg->depth < 0 || cfg->depth > 9) FAIL(FMM_ERR_ARG, "depth=%d outside 0..9", cfg->depth);
-    if (cfg->prec == FMM_GEMM_TF32X3) FAIL(FMM_ERR_UNSUPPORTED, "the TF32x3 tensor-core form is not available yet");
-    if (cfg->prec == FMM_GEMM_BF16X3 && !tc_supported(cfg->p, cfg->basis))
+    if ((cfg->prec == FMM_GEMM_BF16X3 || cfg->prec == FMM_GEMM_TF32X3) && !tc_supported(cfg->p, cfg->basis))
         FAIL(FMM_ERR_UNSUPPORTED, "the tensor-core form needs the traceless basis and 1 <= p <= 8");
     pl = new fmm_plan();
     pl->cfg = *cfg;
@@ -441,12 +442,13 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
              cudaMemcpy(pl->W32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(pl->V32, v32.data(), v32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
     }
-    if (ok && cfg->prec == FMM_GEMM_BF16X3) {
-        ok = cudaMalloc(&pl->Kbf, tc_b_bytes()) == cudaSuccess && cudaMalloc(&pl->derr, sizeof(int)) == cudaSuccess &&
-             cudaMemset(pl->derr, 0, sizeof(int)) == cudaSuccess && tc_build_b(cfg->p, pl->Dtab, pl->Kbf, 0) == 0 &&
+    if (ok && is_tc(cfg->prec)) {
+        const int tf = cfg->prec == FMM_GEMM_TF32X3;
+        ok = cudaMalloc(&pl->Kbf, tc_b_bytes(tf)) == cudaSuccess && cudaMalloc(&pl->derr, sizeof(int)) == cudaSuccess &&
+             cudaMemset(pl->derr, 0, sizeof(int)) == cudaSuccess && tc_build_b(cfg->p, tf, pl->Dtab, pl->Kbf, 0) == 0 &&
              cudaDeviceSynchronize() == cudaSuccess;
     }
-    if (ok && (cfg->prec == FMM_FP32 || cfg->prec == FMM_GEMM_BF16X3)) {
+    if (ok && (cfg->prec == FMM_FP32 || is_tc(cfg->prec))) {
         pl->kst = grouped_kstride(cfg->p, cfg->basis);
         const int cap = pl->kst;
         std::vector<unsigned char> ent((size_t)6 * cap);
@@ -517,22 +519,23 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             free_tree(pl);
             FAIL(FMM_ERR_OOM, "allocating tree storage for n=%lld failed", (long long)n);
         }
-        if (pl->cfg.prec == FMM_GEMM_BF16X3) {
+        if (is_tc(pl->cfg.prec)) {
+            const int tf = pl->cfg.prec == FMM_GEMM_TF32X3, es = tc_elem_bytes(tf);
             int64_t tb = 0;
             for (int l = 0; l <= pl->depth; ++l) {
                 pl->mbf_off[l] = tb;
                 if (l >= 4) tb += 2 * (int64_t)tc_m_elems(l);
             }
             pl->maps.assign((size_t)(pl->depth + 1) * tc_maps_bytes() + 64, 0);
-            if (tb > 0 && cudaMalloc(&pl->Mbf, tb * 2) != cudaSuccess) {
+            if (tb > 0 && cudaMalloc(&pl->Mbf, tb * es) != cudaSuccess) {
                 cudaGetLastError();
                 free_tree(pl);
                 FAIL(FMM_ERR_OOM, "allocating tensor-core operands failed");
             }
             for (int l = 4; l <= pl->depth; ++l) {
-                char* hi = (char*)pl->Mbf + pl->mbf_off[l] * 2;
-                char* lo = hi + tc_m_elems(l) * 2;
-                if (tc_encode_maps(l, hi, lo, tc_maps_at(pl, l)) != 0) {
+                char* hi = (char*)pl->Mbf + pl->mbf_off[l] * es;
+                char* lo = hi + tc_m_elems(l) * es;
+                if (tc_encode_maps(l, tf, hi, lo, tc_maps_at(pl, l)) != 0) {
                     free_tree(pl);
                     FAIL(FMM_ERR_CUDA, "encoding TMA tensor maps failed");
                 }
@@ -602,7 +605,8 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
         CKLAUNCH();
         return FMM_OK;
     }
-    if (pl->cfg.prec == FMM_GEMM_BF16X3 && pl->depth >= 2) {
+    if (is_tc(pl->cfg.prec) && pl->depth >= 2) {
+        const int tf = pl->cfg.prec == FMM_GEMM_TF32X3, es = tc_elem_bytes(tf);
         // levels 2..3 (grids smaller than one 8x4x4 tile) on the FP32 grouped kernel
         const int lt = pl->depth < 3 ? pl->depth : 3;
         const int64_t b = pl->lvl_off[2], e = pl->lvl_off[lt] + ((int64_t)pl->nc << (3 * lt));
@@ -613,10 +617,10 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
             for (int k = 0; k < parts; ++k) count_launch();
         }
         for (int l = 4; l <= pl->depth; ++l) {
-            char* hi = (char*)pl->Mbf + pl->mbf_off[l] * 2;
-            char* lo = hi + tc_m_elems(l) * 2;
-            if (tc_m2l_level(pl->cfg.p, l, Mlev(pl, l), hi, lo, tc_maps_at(pl, l), pl->Kbf, Llev(pl, l), pl->derr,
-                             S(stream)) != 0)
+            char* hi = (char*)pl->Mbf + pl->mbf_off[l] * es;
+            char* lo = hi + tc_m_elems(l) * es;
+            if (tc_m2l_level(pl->cfg.p, tf, l, Mlev(pl, l), hi, lo, tc_maps_at(pl, l), pl->Kbf, Llev(pl, l),
+                             pl->derr, S(stream)) != 0)
                 FAIL(FMM_ERR_CUDA, "tensor-core M2L launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         }
         CKLAUNCH();

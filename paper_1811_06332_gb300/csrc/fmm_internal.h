@@ -134,14 +134,16 @@ int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, 
                  double* ax, double* ay, double* az, cudaStream_t s);
 
 // fmm_m2l_tc.cu (tensor-core offset-grouped M2L, traceless basis)
+// tf selects the operand type: 0 = BF16 hi/lo, 1 = TF32 hi/lo
 int tc_supported(int p, int basis);
-size_t tc_b_bytes();
+size_t tc_b_bytes(int tf);
+int tc_elem_bytes(int tf);
 size_t tc_m_elems(int l);
 size_t tc_maps_bytes();
-int tc_build_b(int p, const double* Dtab, void* B, cudaStream_t s);
-int tc_encode_maps(int l, void* hi, void* lo, void* out_maps);
-int tc_m2l_level(int p, int l, const double* M, void* hi, void* lo, const void* maps, const void* B, double* Lt,
-                 int* err, cudaStream_t s);
+int tc_build_b(int p, int tf, const double* Dtab, void* B, cudaStream_t s);
+int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps);
+int tc_m2l_level(int p, int tf, int l, const double* M, void* hi, void* lo, const void* maps, const void* B,
+                 double* Lt, int* err, cudaStream_t s);
 
 // fmm_tree.cu
 size_t tree_scratch_bytes(int64_t n, int64_t nleaf);

@@ -10,8 +10,12 @@
 // with A_o the source multipoles (reduced traceless representative, padded
 // 81 -> 96) fetched by a 5-D TMA tensor load whose out-of-range part is
 // zero-filled (grid boundary), and B_o the precomputed matrix fetched by a
-// bulk copy.  Split precision: x = hi + lo in BF16, three MMAs per K-step
+// bulk copy.  Split precision: x = hi + lo, three MMAs per K-step
 // (hi.hi + hi.lo + lo.hi), FP32 accumulation in TMEM, FP64 write-out.
+// Two operand types share the kernel: BF16 (kind::f16, 16 columns per
+// K-step) and TF32 (kind::tf32, 8 columns per K-step).  A K-step is 32
+// bytes of a row in both, so the shared-memory layouts agree byte for byte;
+// TF32 rows are twice as long and are streamed in two K-parts per offset.
 //
 // Roles: warp 0 lane 0 issues copies, warp 1 owns TMEM and lane 0 issues
 // tcgen05.mma, warps 2..5 drain TMEM (each reads its lane quadrant).
@@ -28,26 +32,35 @@ namespace fmm {
 
 constexpr int TC_K = 96;                       // padded multipole components (K)
 constexpr int TC_N = 96;                       // padded local components (N)
-constexpr int TC_CH = TC_K / 8;                // 16-byte chunks along K
-constexpr int TC_NCH = TC_N / 16;              // N-chunks of 16 local components
-constexpr int TC_A_BYTES = 128 * TC_K * 2;     // 24576
-constexpr int TC_BMAX = TC_N * TC_K * 2;       // 18432: bound on one packed matrix
+constexpr int TC_CH = 12;                      // 16-byte chunks of one A row per K-part
+constexpr int TC_PSTEPS = 6;                   // K-steps (32 bytes of a row) per K-part
+constexpr int TC_NCH = TC_N / 16;              // N-chunks of at least 16 local components
+constexpr int TC_A_BYTES = 128 * TC_CH * 16;   // 24576: one A operand (hi or lo) of one K-part
+constexpr int TC_PMAX = TC_N * TC_PSTEPS * 32; // 18432: bound on one part block (hi or lo) of a matrix
 constexpr int TC_STAGES = 3;
 constexpr int TC_TMEM_COLS = 128;
 constexpr long TC_SPIN = 1L << 24;             // bounded waits
 
 // The matrix of one offset is block-triangular in rank (|n| + |m| <= p), so
-// local components are processed in N-chunks of 16: chunk j (rows 16j..16j+15,
-// lowest rank a_j) only multiplies multipole components of rank <= p - a_j,
-// i.e. the first kch[j] K-steps of 16.  Chunk j's packed block holds 16 rows
-// x 16 kch[j] columns in the K-major core-matrix layout (SBO = 256 kch[j]).
+// local components are processed in N-chunks: chunk j (rows cw j .. cw j +
+// cw - 1, lowest rank a_j) only multiplies multipole components of rank
+// <= p - a_j, i.e. the first kch[j] K-steps.  Part t of a matrix holds the
+// K-steps 6t .. 6t + 5: chunk j contributes nk[t][j] of them, as cw rows x
+// 32 nk[t][j] bytes in the K-major core-matrix layout (SBO = 256 nk[t][j]).
+// One offset's matrix is stored as {part 0 hi, part 0 lo, part 1 hi, ...}.
 struct TcChunks {
-    int cw;             // chunk width (local components per chunk, N of one MMA)
-    int nch;            // chunks holding real rows
-    int kch[TC_NCH];    // K-steps of chunk j
-    int boff[TC_NCH];   // byte offset of chunk j inside a packed matrix
-    int bbytes;         // bytes of one packed matrix (hi or lo)
-    int nst;            // pipeline stages that fit in shared memory (2 or 3)
+    int tf;                  // 0: BF16 operands, 1: TF32 operands
+    int np;                  // K-parts per offset (1 for BF16; 1 or 2 for TF32, by p)
+    int cw;                  // chunk width (local components per chunk, N of one MMA)
+    int nch;                 // chunks holding real rows
+    int kch[TC_NCH];         // K-steps of chunk j
+    int nk[2][TC_NCH];       // K-steps of chunk j inside part t
+    int boff[2][TC_NCH];     // byte offset of chunk j inside the block of part t
+    int pbytes[2];           // bytes of part t's block (hi or lo), a multiple of 1024
+    int poff[2];             // byte offset of part t's hi block inside one offset's matrix
+    int mbytes;              // bytes of one offset's matrix (every part, hi and lo)
+    int stage;               // bytes of one pipeline stage
+    int nst;                 // pipeline stages that fit in shared memory (2 or 3)
 };
 
 struct TcMaps {
@@ -82,24 +95,42 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint3
     return d;                // layout type 0: no swizzle
 }
 
-// Instruction descriptor: kind::f16, BF16 x BF16 -> F32, both K-major.
-__host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N) {
-    return (1u << 4)                       // D format F32
-           | (1u << 7)                     // A format BF16
-           | (1u << 10)                    // B format BF16
-           | ((uint32_t)(N >> 3) << 17)    // N
-           | ((uint32_t)(M >> 4) << 24);   // M
+// Instruction descriptor, both operands K-major, F32 accumulator:
+// kind::f16 with BF16 x BF16 (format 1), or kind::tf32 with TF32 x TF32
+// (format 2).
+__host__ __device__ constexpr uint32_t make_idesc(int tf, int M, int N) {
+    return (1u << 4)                                  // D format F32
+           | ((tf ? 2u : 1u) << 7)                    // A format
+           | ((tf ? 2u : 1u) << 10)                   // B format
+           | ((uint32_t)(N >> 3) << 17)               // N
+           | ((uint32_t)(M >> 4) << 24);              // M
 }
 
 __device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
 
+template <int TF>
+__device__ __forceinline__ void tc_mma(uint32_t dcol, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    if constexpr (TF)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+}
+
+template <int TF>
 __global__ void __launch_bounds__(192, 1)
 k_m2l_tc(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrows,
-         const __nv_bfloat16* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
+         const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int TC_STAGE = 2 * TC_A_BYTES + 2 * ch.bbytes;   // bbytes is a multiple of 1024
-    uint64_t* bars = (uint64_t*)(smem + ch.nst * TC_STAGE);
+    uint64_t* bars = (uint64_t*)(smem + ch.nst * ch.stage);
     uint64_t* full = bars;                 // [TC_STAGES]
     uint64_t* empty = bars + TC_STAGES;    // [TC_STAGES]
     uint64_t* done = bars + 2 * TC_STAGES;
@@ -138,34 +169,40 @@ k_m2l_tc(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrow
         for (int u = 0; u < 216 && ok; ++u) {
             const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;
             if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-            const int s = it % ch.nst;
-            const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
-            if (!(ok = mbar_wait(smem_u32(&empty[s]), ph ^ 1u, err, 1))) break;
-            const uint32_t fb = smem_u32(&full[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(TC_STAGE) : "memory");
             const int scls = ((cx + ox) & 1) | (((cy + oy) & 1) << 1) | (((cz + oz) & 1) << 2);
             const int c1 = 8 * ti + floor_half(cx + ox), c3 = 4 * tj + floor_half(cy + oy),
                       c4 = 4 * tk + floor_half(cz + oz);
-            unsigned char* st = smem + s * TC_STAGE;
             const CUtensorMap* mh = &maps.hi[scls];
             const CUtensorMap* ml = &maps.lo[scls];
-            asm volatile(
-                "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st)),
-                "l"((uint64_t)mh), "r"(0), "r"(c1), "r"(0), "r"(c3), "r"(c4), "r"(fb)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st + TC_A_BYTES)),
-                "l"((uint64_t)ml), "r"(0), "r"(c1), "r"(0), "r"(c3), "r"(c4), "r"(fb)
-                : "memory");
             const int ridx = (3 - oz) * 49 + (3 - oy) * 7 + (3 - ox);   // r = target - source = -o
-            const unsigned char* kb = (const unsigned char*)Kmat + (int64_t)ridx * 2 * ch.bbytes;
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                             smem_u32(st + 2 * TC_A_BYTES)),
-                         "l"((uint64_t)kb), "r"(2 * ch.bbytes), "r"(fb)
-                         : "memory");
-            ++it;
+            for (int pt = 0; pt < ch.np; ++pt) {
+                const int s = it % ch.nst;
+                const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
+                if (!(ok = mbar_wait(smem_u32(&empty[s]), ph ^ 1u, err, 1))) break;
+                const uint32_t fb = smem_u32(&full[s]);
+                const int bb = 2 * ch.pbytes[pt];
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                             "r"(2 * TC_A_BYTES + bb)
+                             : "memory");
+                unsigned char* st = smem + s * ch.stage;
+                asm volatile(
+                    "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st)),
+                    "l"((uint64_t)mh), "r"(0), "r"(c1), "r"(TC_CH * pt), "r"(c3), "r"(c4), "r"(fb)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st + TC_A_BYTES)),
+                    "l"((uint64_t)ml), "r"(0), "r"(c1), "r"(TC_CH * pt), "r"(c3), "r"(c4), "r"(fb)
+                    : "memory");
+                const unsigned char* kb = Kmat + (int64_t)ridx * ch.mbytes + ch.poff[pt];
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(st + 2 * TC_A_BYTES)),
+                    "l"((uint64_t)kb), "r"(bb), "r"(fb)
+                    : "memory");
+                ++it;
+            }
         }
         // drain: every issued stage has landed before the CTA may exit
         const int first = it > ch.nst ? it - ch.nst : 0;
@@ -173,41 +210,41 @@ k_m2l_tc(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrow
             mbar_wait(smem_u32(&full[k % ch.nst]), (uint32_t)(k / ch.nst) & 1u, err, 2);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc = make_idesc_bf16(128, ch.cw);
+        const uint32_t idesc = make_idesc(TF, 128, ch.cw);
         int it = 0;
         bool ok = true;
-        for (int u = 0; u < 216; ++u) {
+        for (int u = 0; u < 216 && ok; ++u) {
             const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;
             if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-            const int s = it % ch.nst;
-            const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
-            if (!(ok = mbar_wait(smem_u32(&full[s]), ph, err, 3))) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = smem_u32(smem + s * TC_STAGE);
-            const uint32_t a_addr[2] = {base, base + TC_A_BYTES};
-            const uint32_t b_addr[2] = {base + 2 * TC_A_BYTES, base + 2 * TC_A_BYTES + ch.bbytes};
-            for (int j = 0; j < ch.nch; ++j) {
-                const uint32_t dcol = tmem + (uint32_t)(ch.cw * j);
-                const uint32_t sbo = 256u * ch.kch[j];
+            for (int pt = 0; pt < ch.np; ++pt) {
+                const int s = it % ch.nst;
+                const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
+                if (!(ok = mbar_wait(smem_u32(&full[s]), ph, err, 3))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = smem_u32(smem + s * ch.stage);
+                const uint32_t a_addr[2] = {base, base + TC_A_BYTES};
+                const uint32_t b_addr[2] = {base + 2 * TC_A_BYTES, base + 2 * TC_A_BYTES + ch.pbytes[pt]};
+                for (int j = 0; j < ch.nch; ++j) {
+                    const int nk = ch.nk[pt][j];
+                    const uint32_t dcol = tmem + (uint32_t)(ch.cw * j);
+                    const uint32_t sbo = 256u * nk;
 #pragma unroll
-                for (int pass = 0; pass < 3; ++pass) {
-                    const int ia = pass == 2 ? 1 : 0, ib = pass == 1 ? 1 : 0;   // hi.hi, hi.lo, lo.hi
-                    for (int ks = 0; ks < ch.kch[j]; ++ks) {
-                        const uint64_t ad = make_desc(a_addr[ia] + ks * 256, 128, TC_CH * 128);
-                        const uint64_t bd = make_desc(b_addr[ib] + ch.boff[j] + ks * 256, 128, sbo);
-                        const uint32_t acc = (it > 0 || pass > 0 || ks > 0) ? 1u : 0u;
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                            : "memory");
+                    for (int pass = 0; pass < 3; ++pass) {
+                        const int ia = pass == 2 ? 1 : 0, ib = pass == 1 ? 1 : 0;   // hi.hi, hi.lo, lo.hi
+                        for (int ks = 0; ks < nk; ++ks) {
+                            const uint64_t ad = make_desc(a_addr[ia] + ks * 256, 128, TC_CH * 128);
+                            const uint64_t bd = make_desc(b_addr[ib] + ch.boff[pt][j] + ks * 256, 128, sbo);
+                            // part 0 of the first offset holds at least one K-step of every chunk
+                            const uint32_t acc = (it > 0 || pass > 0 || ks > 0) ? 1u : 0u;
+                            tc_mma<TF>(dcol, ad, bd, idesc, acc);
+                        }
                     }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty[s]))
+                             : "memory");
+                ++it;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&empty[s]))
-                         : "memory");
-            ++it;
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(done))
@@ -259,53 +296,88 @@ k_m2l_tc(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrow
 // ---------------------------------------------------------------------------
 // Operand preparation
 // ---------------------------------------------------------------------------
+// Split of an FP64 value into hi + lo of the operand type.  BF16 rounds to
+// nearest even (the CUDA conversion); TF32 (a 32-bit container whose low 13
+// mantissa bits are zero) rounds the FP32 value to nearest, ties away from
+// zero, on the magnitude bits.  Both parts are exact in the operand type, so
+// the tensor core reads them without further rounding.
+__device__ __forceinline__ uint32_t tf32_round(float v) {
+    return (__float_as_uint(v) + 0x1000u) & 0xFFFFE000u;
+}
+template <int TF>
+struct TcSplit;
+template <>
+struct TcSplit<0> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ void split(double x, T& h, T& l) {
+        h = __double2bfloat16(x);
+        l = __double2bfloat16(x - (double)__bfloat162float(h));
+    }
+};
+template <>
+struct TcSplit<1> {
+    using T = uint32_t;
+    static __device__ __forceinline__ void split(double x, T& h, T& l) {
+        h = tf32_round((float)x);
+        l = tf32_round((float)(x - (double)__uint_as_float(h)));
+    }
+};
+
 // Multipoles of one level (FP64, [ncoef][ncell], parity-class numbering) ->
-// BF16 hi/lo in the TMA layout [class][k][j][chunk][i][8] (components padded
-// to 96).  One thread per (cell, chunk).
-__global__ void k_tc_split_m(int l, int nc, const double* __restrict__ M, __nv_bfloat16* __restrict__ hi,
-                             __nv_bfloat16* __restrict__ lo) {
+// hi/lo operands in the TMA layout [class][k][j][chunk][i][16 bytes]
+// (components padded to 96; 8 BF16 or 4 TF32 per 16-byte chunk).  One
+// thread per (cell, chunk).
+template <int TF>
+__global__ void k_tc_split_m(int l, int nc, const double* __restrict__ M, void* __restrict__ hi_,
+                             void* __restrict__ lo_) {
+    using T = typename TcSplit<TF>::T;
+    constexpr int EPC = 16 / (int)sizeof(T);        // elements per 16-byte chunk
+    constexpr int NCH = TC_K / EPC;                 // chunks per row
     const int hs = 1 << (l - 1);
     const int64_t h3 = (int64_t)hs * hs * hs, ncell = 8 * h3;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncell * TC_CH) return;
+    if (t >= ncell * NCH) return;
     const int c = (int)(t / ncell);
     const int64_t idx = t % ncell;
     const int cls = (int)(idx / h3);
     const int64_t lin = idx % h3;
     const int i = (int)(lin % hs), j = (int)((lin / hs) % hs), k = (int)(lin / ((int64_t)hs * hs));
-    __align__(16) __nv_bfloat16 vh[8], vl[8];
+    __align__(16) T vh[EPC], vl[EPC];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int m = 8 * c + e;
+    for (int e = 0; e < EPC; ++e) {
+        const int m = EPC * c + e;
         const double x = m < nc ? M[(int64_t)m * ncell + idx] : 0.0;
-        const __nv_bfloat16 h = __double2bfloat16(x);
-        vh[e] = h;
-        vl[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+        TcSplit<TF>::split(x, vh[e], vl[e]);
     }
-    const int64_t o = ((((int64_t)cls * hs + k) * hs + j) * TC_CH + c) * hs + i;
-    *(uint4*)(hi + o * 8) = *(const uint4*)vh;
-    *(uint4*)(lo + o * 8) = *(const uint4*)vl;
+    const int64_t o = ((((int64_t)cls * hs + k) * hs + j) * NCH + c) * hs + i;
+    *(uint4*)((unsigned char*)hi_ + o * 16) = *(const uint4*)vh;
+    *(uint4*)((unsigned char*)lo_ + o * 16) = *(const uint4*)vl;
 }
 
 // Kt_r(n, m) = D_{n+m}(r)/m! (traceless basis, reduced multipole columns),
-// zero outside |n| + |m| <= p and in the padding, split into BF16 hi/lo and
-// stored per offset as N-chunks: chunk j = rows 16j..16j+15 by 16 kch[j]
-// columns, K-major core-matrix layout, byte (r/8)*256 kch[j] + (m/8)*128 +
-// (r%8)*16 + (m%8)*2 inside the chunk.  One thread per (offset, row, column
-// group of 8).
+// zero outside |n| + |m| <= p and in the padding, split into hi/lo and
+// stored per offset as parts of N-chunks: 16-byte column group c lies in
+// K-step c/2 of part t = (c/2)/6; chunk j's rows rr at byte
+// (rr/8) 256 nk[t][j] + (c - 12 t) 128 + (rr%8) 16 inside its block.  One
+// thread per (offset, row, 16-byte column group).
+template <int TF>
 __global__ void k_tc_build_b(int p, int nc, const TcChunks ch, const double* __restrict__ Dtab,
-                             __nv_bfloat16* __restrict__ B) {
+                             unsigned char* __restrict__ B) {
+    using T = typename TcSplit<TF>::T;
+    constexpr int EPC = 16 / (int)sizeof(T);
+    constexpr int NCH = TC_K / EPC;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)343 * TC_N * TC_CH) return;
-    const int r = (int)(t / (TC_N * TC_CH));
-    const int n = (int)((t / TC_CH) % TC_N), c = (int)(t % TC_CH);
+    if (t >= (int64_t)343 * TC_N * NCH) return;
+    const int r = (int)(t / (TC_N * NCH));
+    const int n = (int)((t / NCH) % TC_N), c = (int)(t % NCH);
     const int j = n / ch.cw, rr = n % ch.cw;
-    if (j >= ch.nch || c >= 2 * ch.kch[j]) return;
+    const int step = c / 2, pt = step / TC_PSTEPS;
+    if (j >= ch.nch || step >= ch.kch[j]) return;
     const int ns = ns_of(p);
-    __align__(16) __nv_bfloat16 vh[8], vl[8];
+    __align__(16) T vh[EPC], vl[EPC];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int m = 8 * c + e;
+    for (int e = 0; e < EPC; ++e) {
+        const int m = EPC * c + e;
         double v = 0.0;
         if (n < nc && m < nc) {
             const int nx = c_tl_idx[n][0], ny = c_tl_idx[n][1], nz = c_tl_idx[n][2];
@@ -314,14 +386,13 @@ __global__ void k_tc_build_b(int p, int nc, const TcChunks ch, const double* __r
                 v = Dtab[(int64_t)r * ns + pos_sym(nx + mx, ny + my, nz + mz)] * c_invfact[mx] * c_invfact[my] *
                     c_invfact[mz];
         }
-        const __nv_bfloat16 h = __double2bfloat16(v);
-        vh[e] = h;
-        vl[e] = __double2bfloat16(v - (double)__bfloat162float(h));
+        TcSplit<TF>::split(v, vh[e], vl[e]);
     }
-    const int64_t boff = ch.boff[j] + (rr / 8) * 256 * ch.kch[j] + c * 128 + (rr % 8) * 16;   // bytes
-    unsigned char* bh = (unsigned char*)B + (int64_t)r * 2 * ch.bbytes;
+    const int64_t boff = ch.poff[pt] + ch.boff[pt][j] + (rr / 8) * 256 * ch.nk[pt][j] +
+                         (c - 2 * TC_PSTEPS * pt) * 128 + (rr % 8) * 16;   // bytes
+    unsigned char* bh = B + (int64_t)r * ch.mbytes;
     *(uint4*)(bh + boff) = *(const uint4*)vh;
-    *(uint4*)(bh + ch.bbytes + boff) = *(const uint4*)vl;
+    *(uint4*)(bh + ch.pbytes[pt] + boff) = *(const uint4*)vl;
 }
 
 // ---------------------------------------------------------------------------
@@ -330,7 +401,8 @@ __global__ void k_tc_build_b(int p, int nc, const TcChunks ch, const double* __r
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 int tc_supported(int p, int basis) { return basis == 1 && p >= 1 && ncoef_of(p, basis) <= TC_K; }
-size_t tc_b_bytes() { return (size_t)343 * 2 * TC_BMAX; }
+size_t tc_b_bytes(int tf) { return (size_t)343 * 2 * TC_PMAX * (tf ? 2 : 1); }
+int tc_elem_bytes(int tf) { return tf ? 4 : 2; }
 
 // Chunk width: the N of one MMA.  Wider chunks issue fewer, larger MMAs;
 // narrower ones skip more of the zero triangle.  FMM_TC_CHUNK (16, 32, 48 or
@@ -347,42 +419,59 @@ static int tc_chunk_width() {
     return cw;
 }
 
-static TcChunks tc_chunks(int p) {
-    TcChunks c;
+static TcChunks tc_chunks(int p, int tf) {
+    TcChunks c{};
     const int nc = ncoef_of(p, 1);
+    const int cps = tf ? 8 : 16;   // columns per K-step
+    c.tf = tf;
     c.cw = tc_chunk_width();
     c.nch = (nc + c.cw - 1) / c.cw;
-    int off = 0;
-    for (int j = 0; j < TC_NCH; ++j) {
-        c.kch[j] = 0;
-        c.boff[j] = off;
-        if (j < c.nch) {
-            const int r0 = c.cw * j;
-            const int a = fmm_tl_idx[r0][0] + fmm_tl_idx[r0][1] + fmm_tl_idx[r0][2];   // lowest rank in chunk
-            const int cols = (p - a + 1) * (p - a + 1);
-            c.kch[j] = (cols + 15) / 16;
-            off += 32 * c.cw * c.kch[j];
-        }
+    for (int j = 0; j < c.nch; ++j) {
+        const int r0 = c.cw * j;
+        const int a = fmm_tl_idx[r0][0] + fmm_tl_idx[r0][1] + fmm_tl_idx[r0][2];   // lowest rank in chunk
+        const int cols = (p - a + 1) * (p - a + 1);
+        c.kch[j] = (cols + cps - 1) / cps;
     }
-    c.bbytes = (off + 1023) / 1024 * 1024;
-    c.nst = TC_STAGES * (2 * TC_A_BYTES + 2 * c.bbytes) + 1280 <= 227 * 1024 ? TC_STAGES : 2;
+    // chunk 0 (rank 0) needs the most K-steps; parts beyond it would be empty
+    c.np = (c.kch[0] + TC_PSTEPS - 1) / TC_PSTEPS;
+    int pbmax = 0, off_all = 0;
+    for (int pt = 0; pt < c.np; ++pt) {
+        int off = 0;
+        for (int j = 0; j < TC_NCH; ++j) {
+            const int nk = j < c.nch ? c.kch[j] - TC_PSTEPS * pt : 0;
+            c.nk[pt][j] = nk < 0 ? 0 : nk > TC_PSTEPS ? TC_PSTEPS : nk;
+            c.boff[pt][j] = off;
+            off += 32 * c.cw * c.nk[pt][j];
+        }
+        c.pbytes[pt] = (off + 1023) / 1024 * 1024;
+        c.poff[pt] = off_all;
+        off_all += 2 * c.pbytes[pt];
+        pbmax = c.pbytes[pt] > pbmax ? c.pbytes[pt] : pbmax;
+    }
+    c.mbytes = off_all;
+    c.stage = 2 * TC_A_BYTES + 2 * pbmax;
+    c.nst = TC_STAGES * c.stage + 1280 <= 227 * 1024 ? TC_STAGES : 2;
     return c;
 }
 
 size_t tc_m_elems(int l) { return l < 1 ? 0 : ((size_t)8 << (3 * (l - 1))) * TC_K; }
 
-int tc_build_b(int p, const double* Dtab, void* B, cudaStream_t s) {
-    const int64_t tot = (int64_t)343 * TC_N * TC_CH;
-    if (cudaMemsetAsync(B, 0, tc_b_bytes(), s) != cudaSuccess) return -2;
-    k_tc_build_b<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p), Dtab,
-                                                               (__nv_bfloat16*)B);
+int tc_build_b(int p, int tf, const double* Dtab, void* B, cudaStream_t s) {
+    const int64_t tot = (int64_t)343 * TC_N * (TC_K * tc_elem_bytes(tf) / 16);
+    if (cudaMemsetAsync(B, 0, tc_b_bytes(tf), s) != cudaSuccess) return -2;
+    const unsigned g = (unsigned)((tot + 255) / 256);
+    if (tf)
+        k_tc_build_b<1><<<g, 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p, 1), Dtab, (unsigned char*)B);
+    else
+        k_tc_build_b<0><<<g, 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p, 0), Dtab, (unsigned char*)B);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 // Encodes the 16 tensor maps (8 classes x hi/lo) of one level.
-// Tensor dims (innermost first): e (8), i (hs), chunk (12), j (hs), k (hs).
-int tc_encode_maps(int l, void* hi, void* lo, void* out_maps) {
+// Tensor dims (innermost first): e (16 bytes), i (hs), chunk (12 or 24), j (hs), k (hs);
+// the box takes one K-part (12 chunks) of an 8 x 4 x 4 brick.
+int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps) {
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
         void* fn = nullptr;
@@ -393,17 +482,20 @@ int tc_encode_maps(int l, void* hi, void* lo, void* out_maps) {
         g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     TcMaps* maps = (TcMaps*)out_maps;
+    const int es = tc_elem_bytes(tf), epc = 16 / es;
+    const cuuint64_t nch = (cuuint64_t)(TC_K / epc);
     const cuuint64_t hs = (cuuint64_t)1 << (l - 1);
-    const cuuint64_t dims[5] = {8, hs, (cuuint64_t)TC_CH, hs, hs};
-    const cuuint64_t strides[4] = {16, hs * 16, (cuuint64_t)TC_CH * hs * 16, hs * TC_CH * hs * 16};
-    const cuuint32_t box[5] = {8, 8, (cuuint32_t)TC_CH, 4, 4};
+    const cuuint64_t dims[5] = {(cuuint64_t)epc, hs, nch, hs, hs};
+    const cuuint64_t strides[4] = {16, hs * 16, nch * hs * 16, hs * nch * hs * 16};
+    const cuuint32_t box[5] = {(cuuint32_t)epc, 8, (cuuint32_t)TC_CH, 4, 4};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const size_t cls_elems = (size_t)hs * hs * hs * TC_K;
+    const size_t cls_bytes = (size_t)hs * hs * hs * TC_K * es;
+    const CUtensorMapDataType dt = tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     for (int c = 0; c < 8; ++c) {
         for (int h = 0; h < 2; ++h) {
-            void* base = (char*)(h ? lo : hi) + c * cls_elems * sizeof(__nv_bfloat16);
-            CUresult r = g_encode(h ? &maps->lo[c] : &maps->hi[c], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims,
-                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            void* base = (char*)(h ? lo : hi) + c * cls_bytes;
+            CUresult r = g_encode(h ? &maps->lo[c] : &maps->hi[c], dt, 5, base, dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return -1;
         }
@@ -412,22 +504,37 @@ int tc_encode_maps(int l, void* hi, void* lo, void* out_maps) {
 }
 size_t tc_maps_bytes() { return sizeof(TcMaps); }
 
-int tc_m2l_level(int p, int l, const double* M, void* hi, void* lo, const void* maps, const void* B, double* Lt,
-                 int* err, cudaStream_t s) {
+template <int TF>
+static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const void* B, double* Lt, int64_t ncell,
+                     int* err, cudaStream_t s) {
+    const int hs = 1 << (l - 1);
+    const int smem = ch.nst * ch.stage + 1024 + 256;
+    if (cudaFuncSetAttribute(k_m2l_tc<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return -2;
+    const int tpc = (hs / 8) * (hs / 4) * (hs / 4);
+    k_m2l_tc<TF><<<(unsigned)(8 * tpc), 192, smem, s>>>(*(const TcMaps*)maps, ch, l, nc, (const unsigned char*)B,
+                                                        Lt, ncell, err);
+    count_launch();
+    return 0;
+}
+
+int tc_m2l_level(int p, int tf, int l, const double* M, void* hi, void* lo, const void* maps, const void* B,
+                 double* Lt, int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
     if (hs < 8) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const int nc = ncoef_of(p, 1);
-    const int64_t tot = ncell * TC_CH;
-    k_tc_split_m<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(l, nc, M, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
+    const int64_t tot = ncell * (TC_K * tc_elem_bytes(tf) / 16);
+    const unsigned g = (unsigned)((tot + 255) / 256);
+    if (tf)
+        k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, M, hi, lo);
+    else
+        k_tc_split_m<0><<<g, 256, 0, s>>>(l, nc, M, hi, lo);
     count_launch();
-    const TcChunks ch = tc_chunks(p);
-    const int smem = ch.nst * (2 * TC_A_BYTES + 2 * ch.bbytes) + 1024 + 256;
-    if (cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return -2;
-    const int tpc = (hs / 8) * (hs / 4) * (hs / 4);
-    k_m2l_tc<<<(unsigned)(8 * tpc), 192, smem, s>>>(*(const TcMaps*)maps, ch, l, nc, (const __nv_bfloat16*)B, Lt,
-                                                    ncell, err);
-    count_launch();
+    const TcChunks ch = tc_chunks(p, tf);
+    const int rc = tf ? tc_launch<1>(ch, l, nc, maps, B, Lt, ncell, err, s)
+                      : tc_launch<0>(ch, l, nc, maps, B, Lt, ncell, err, s);
+    if (rc != 0) return rc;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

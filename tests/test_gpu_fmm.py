@@ -174,8 +174,43 @@ def test_tensor_core_form_vs_oracle(F, depth, n):
     assert ep < 5e-5 and ea < 5e-5, (ep, ea, per)
 
 
+@pytest.mark.parametrize("depth,n", [(4, 40000), (5, 131072)])
+def test_tensor_core_tf32_form_vs_oracle(F, depth, n):
+    """The same offset-grouped tensor-core M2L with TF32 hi/lo operands
+    (kind::tf32, two K-parts per offset), traceless p = 8, against the FP64
+    oracle on 200 sampled particles.  The TF32 split keeps ~21 bits per
+    operand, so what remains is the FP32 accumulation in TMEM, over twice
+    the K-steps of the BF16 form: measured 2e-6 to 8e-6 normwise at these
+    sizes (the BF16 form 2e-6 to 6e-6, the FP32 SIMT form 4e-7 to 7e-7).
+    Bound: 2e-5 on pot and acc."""
+    x, y, z = inputs.uniform_cube(n, 21 + depth)
+    q = inputs.masses_equal(n)
+    pot, acc = run(F, x, y, z, q, 8, 1, depth, prec=F.GEMM_TF32X3)
+    s = np.sort(np.unique((inputs.u01(7, 93, 200) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, 8, 1, sample=s)
+    ep, ea, per = errs(pot[s], acc[:, s], pref, aref)
+    assert ep < 2e-5 and ea < 2e-5, (ep, ea, per)
+
+
+@pytest.mark.parametrize("p", [2, 6])
+def test_tensor_core_forms_low_order(F, p):
+    """Both tensor-core forms at lower orders (fewer N-chunks and K-steps
+    than p = 8; at p = 2 the TF32 form streams one K-part per offset, at
+    p = 6 two), depth 4, against the FP64 oracle."""
+    n, depth = 30000, 4
+    x, y, z = inputs.uniform_cube(n, 40 + p)
+    q = inputs.masses_open_unit(n, 40 + p)
+    s = np.sort(np.unique((inputs.u01(9, 94, 120) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, 1, sample=s)
+    for prec, tol in ((F.GEMM_BF16X3, 5e-5), (F.GEMM_TF32X3, 2e-5)):
+        pot, acc = run(F, x, y, z, q, p, 1, depth, prec=prec)
+        ep, ea, per = errs(pot[s], acc[:, s], pref, aref)
+        assert ep < tol and ea < tol, (prec, ep, ea, per)
+
+
 def test_tensor_core_form_rejects_unsupported(F):
-    with pytest.raises(F.FMMError):
-        F.Plan(p=9, basis=1, prec=F.GEMM_BF16X3, depth=4)
-    with pytest.raises(F.FMMError):
-        F.Plan(p=6, basis=0, prec=F.GEMM_BF16X3, depth=4)
+    for prec in (F.GEMM_BF16X3, F.GEMM_TF32X3):
+        with pytest.raises(F.FMMError):
+            F.Plan(p=9, basis=1, prec=prec, depth=4)
+        with pytest.raises(F.FMMError):
+            F.Plan(p=6, basis=0, prec=prec, depth=4)
