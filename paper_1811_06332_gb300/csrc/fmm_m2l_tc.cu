@@ -59,13 +59,33 @@ struct TcChunks {
     int pbytes[2];           // bytes of part t's block (hi or lo), a multiple of 1024
     int poff[2];             // byte offset of part t's hi block inside one offset's matrix
     int mbytes;              // bytes of one offset's matrix (every part, hi and lo)
-    int stage;               // bytes of one pipeline stage
+    int stage;               // bytes of one pipeline stage (brick kernel)
     int nst;                 // pipeline stages that fit in shared memory (2 or 3)
+    int bstage;              // bytes of one matrix stage (slab kernel): 2 x largest part block
+    int nbst;                // matrix stages of the slab kernel (2 to 4)
 };
 
 struct TcMaps {
     CUtensorMap hi[8];
     CUtensorMap lo[8];
+};
+
+// Source-slab variant (levels with at least 16 cells per class and axis).
+// A CTA owns a column of 8 x 16 x 1 target cells of one class.  For one
+// source class and one z shift dz in {-1, 0, 1}, the sources of the (up to
+// 9) offsets with x, y shifts dx, dy in {-1, 0, 1} all lie in one slab of
+// 10 x 18 x 1 cells, stored [j][chunk][i][16 bytes]: the A operand of
+// offset (dx, dy) starts at row i = dx + 1 of group j = dy + 1.  Core
+// matrices stay 8 consecutive 16-byte rows; LBO (next chunk along K) is
+// 160 bytes and SBO (next group of 8 rows) 1920 bytes.  The slab is
+// fetched once for its offsets instead of once per offset.
+constexpr int SL_I = 10, SL_J = 18;
+constexpr int SL_BYTES = SL_I * TC_CH * SL_J * 16;   // 34560: one slab operand (hi or lo) of one K-part
+
+struct alignas(64) TcLevelMaps {
+    TcMaps brick;   // box 8 x 4 x 4 cells (brick kernel)
+    TcMaps slab;    // box 10 x 18 x 1 cells (slab kernel)
+    int slab_ok;    // slab maps encoded (class grid of at least 16 per axis)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -293,6 +313,231 @@ k_m2l_tc(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrow
     }
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape)
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(ta));
+}
+
+// Slab kernel.  Two rings: 2 slab buffers ({hi, lo} of one K-part) and
+// nbst matrix stages.  The producer (warp 0) walks (source class, dz, part)
+// slabs and, after each slab, the matrices of its offsets.  The cost of an
+// MMA here is set by its issue rather than by its tensor work, so two warps
+// issue (warps 1 and 6, alternate offsets) into two TMEM accumulators of
+// 128 columns each, which the epilogue (warps 2..5) adds.  A slab is freed
+// when both issuers have committed its MMAs.
+constexpr int SL_THREADS = 224;
+template <int TF>
+__global__ void __launch_bounds__(SL_THREADS, 1)
+k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrows,
+              const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* bring = smem + 4 * SL_BYTES;
+    uint64_t* bars = (uint64_t*)(bring + ch.nbst * ch.bstage);
+    uint64_t* sfull = bars;        // [2]
+    uint64_t* sempty = bars + 2;   // [2]
+    uint64_t* bfull = bars + 4;    // [4]
+    uint64_t* bempty = bars + 8;   // [4]
+    uint64_t* done = bars + 12;
+    uint32_t* tslot = (uint32_t*)(bars + 13);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int hs = 1 << (l - 1);
+    const int nti = hs / 8, ntj = hs / 16;
+    const int tpc = nti * ntj * hs;
+    const int cls = blockIdx.x / tpc, t = blockIdx.x % tpc;
+    const int ti = t % nti, tj = (t / nti) % ntj, tk = t / (nti * ntj);
+    const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sfull[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&sempty[b])));
+        }
+        for (int b = 0; b < ch.nbst; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bempty[b])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(done)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(2 * TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- producer ----------------
+        int sl = 0, bt = 0;
+        bool ok = true;
+        for (int sc = 0; sc < 8 && ok; ++sc) {
+            const int sx = sc & 1, sy = (sc >> 1) & 1, sz = sc >> 2;
+            for (int dz = -1; dz <= 1 && ok; ++dz) {
+                if (tk + dz < 0 || tk + dz >= hs) continue;   // plane outside the grid: no sources
+                const int oz = 2 * dz + sz - cz;
+                for (int pt = 0; pt < ch.np && ok; ++pt) {
+                    const int buf = sl & 1;
+                    if (!(ok = mbar_wait(smem_u32(&sempty[buf]), ((uint32_t)(sl >> 1) & 1u) ^ 1u, err, 11))) break;
+                    const uint32_t fb = smem_u32(&sfull[buf]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                 "r"(2 * SL_BYTES)
+                                 : "memory");
+                    unsigned char* st = smem + buf * 2 * SL_BYTES;
+                    const int c1 = 8 * ti - 1, c3 = 16 * tj - 1, c4 = tk + dz;
+                    asm volatile(
+                        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st)),
+                        "l"((uint64_t)&maps.hi[sc]), "r"(0), "r"(c1), "r"(TC_CH * pt), "r"(c3), "r"(c4), "r"(fb)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st + SL_BYTES)),
+                        "l"((uint64_t)&maps.lo[sc]), "r"(0), "r"(c1), "r"(TC_CH * pt), "r"(c3), "r"(c4), "r"(fb)
+                        : "memory");
+                    ++sl;
+                    for (int dy = -1; dy <= 1 && ok; ++dy) {
+                        const int oy = 2 * dy + sy - cy;
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int ox = 2 * dx + sx - cx;
+                            if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+                            const int bs = bt % ch.nbst;
+                            if (!(ok = mbar_wait(smem_u32(&bempty[bs]), ((uint32_t)(bt / ch.nbst) & 1u) ^ 1u, err,
+                                                 12)))
+                                break;
+                            const uint32_t bb = smem_u32(&bfull[bs]);
+                            const int nb = 2 * ch.pbytes[pt];
+                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(nb)
+                                         : "memory");
+                            const int ridx = (3 - oz) * 49 + (3 - oy) * 7 + (3 - ox);   // r = -o
+                            const unsigned char* kb = Kmat + (int64_t)ridx * ch.mbytes + ch.poff[pt];
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                                "[%3];" ::"r"(smem_u32(bring + bs * ch.bstage)),
+                                "l"((uint64_t)kb), "r"(nb), "r"(bb)
+                                : "memory");
+                            ++bt;
+                        }
+                    }
+                }
+            }
+        }
+        // drain: every issued copy has landed before the CTA may exit
+        for (int k = sl > 2 ? sl - 2 : 0; k < sl; ++k)
+            mbar_wait(smem_u32(&sfull[k & 1]), (uint32_t)(k >> 1) & 1u, err, 13);
+        for (int k = bt > ch.nbst ? bt - ch.nbst : 0; k < bt; ++k)
+            mbar_wait(smem_u32(&bfull[k % ch.nbst]), (uint32_t)(k / ch.nbst) & 1u, err, 13);
+    } else if ((warp == 1 || warp == 6) && lane == 0) {
+        // ---------------- MMA issuers ----------------
+        const int w = warp == 1 ? 0 : 1;
+        const uint32_t dbase = tmem + (uint32_t)(w * TC_TMEM_COLS);
+        const uint32_t idesc = make_idesc(TF, 128, ch.cw);
+        int sl = 0, bt = 0;
+        bool ok = true, first = true;
+        for (int sc = 0; sc < 8 && ok; ++sc) {
+            const int sx = sc & 1, sy = (sc >> 1) & 1, sz = sc >> 2;
+            for (int dz = -1; dz <= 1 && ok; ++dz) {
+                if (tk + dz < 0 || tk + dz >= hs) continue;
+                const int oz = 2 * dz + sz - cz;
+                for (int pt = 0; pt < ch.np && ok; ++pt) {
+                    const int buf = sl & 1;
+                    if (!(ok = mbar_wait(smem_u32(&sfull[buf]), (uint32_t)(sl >> 1) & 1u, err, 14))) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sbase = smem_u32(smem + buf * 2 * SL_BYTES);
+                    for (int dy = -1; dy <= 1 && ok; ++dy) {
+                        const int oy = 2 * dy + sy - cy;
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int ox = 2 * dx + sx - cx;
+                            if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+                            const int mine = (bt & 1) == w;
+                            const int bs = bt % ch.nbst;
+                            ++bt;
+                            if (!mine) continue;
+                            if (!(ok = mbar_wait(smem_u32(&bfull[bs]), (uint32_t)((bt - 1) / ch.nbst) & 1u, err, 15)))
+                                break;
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t bbase = smem_u32(bring + bs * ch.bstage);
+                            const uint32_t aoff = (uint32_t)(((dy + 1) * TC_CH * SL_I + (dx + 1)) * 16);
+                            // descriptors of K-step 0; a K-step adds 320 bytes (A) or 256 bytes (B),
+                            // i.e. 20 or 16 in the address field (no carry: shared addresses < 2^18)
+                            const uint64_t ah = make_desc(sbase + aoff, SL_I * 16, TC_CH * SL_I * 16);
+                            const uint64_t al = make_desc(sbase + SL_BYTES + aoff, SL_I * 16, TC_CH * SL_I * 16);
+                            for (int j = 0; j < ch.nch; ++j) {
+                                const int nk = ch.nk[pt][j];
+                                const uint32_t dcol = dbase + (uint32_t)(ch.cw * j);
+                                const uint64_t bh = make_desc(bbase + ch.boff[pt][j], 128, 256u * nk);
+                                const uint64_t bl = make_desc(bbase + ch.pbytes[pt] + ch.boff[pt][j], 128, 256u * nk);
+                                // the first offset of each issuer (part 0) holds a K-step of every chunk
+                                tc_mma<TF>(dcol, ah, bh, idesc, first ? 0u : 1u);
+                                for (int ks = 1; ks < nk; ++ks) tc_mma<TF>(dcol, ah + 20 * ks, bh + 16 * ks, idesc, 1u);
+                                for (int ks = 0; ks < nk; ++ks) tc_mma<TF>(dcol, ah + 20 * ks, bl + 16 * ks, idesc, 1u);
+                                for (int ks = 0; ks < nk; ++ks) tc_mma<TF>(dcol, al + 20 * ks, bh + 16 * ks, idesc, 1u);
+                            }
+                            first = false;
+                            asm volatile(
+                                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                    smem_u32(&bempty[bs]))
+                                : "memory");
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&sempty[buf]))
+                                 : "memory");
+                    ++sl;
+                }
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(done))
+                     : "memory");
+    } else if (warp >= 2 && warp <= 5) {
+        // ---------------- epilogue: TMEM (two accumulators) -> FP64 L ----------------
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(smem_u32(done), 0u, err, 16);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int i = row & 7, j = row >> 3;
+        const int64_t h3 = (int64_t)hs * hs * hs;
+        const int64_t tg = (int64_t)cls * h3 + ((int64_t)tk * hs + (16 * tj + j)) * hs + (8 * ti + i);
+#pragma unroll 1
+        for (int cb = 0; cb < TC_N / 32; ++cb) {
+            uint32_t v[32], u[32];
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
+            tmem_ld32(ta, v);
+            tmem_ld32(ta + TC_TMEM_COLS, u);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (ok) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const int n = cb * 32 + e;
+                    if (n < nrows)
+                        Lt[(int64_t)n * ncell + tg] = (double)__uint_as_float(v[e]) + (double)__uint_as_float(u[e]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_TMEM_COLS));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Operand preparation
 // ---------------------------------------------------------------------------
@@ -410,7 +655,7 @@ int tc_elem_bytes(int tf) { return tf ? 4 : 2; }
 static int tc_chunk_width() {
     static int cw = 0;
     if (!cw) {
-        cw = 32;
+        cw = 96;
         if (const char* e = getenv("FMM_TC_CHUNK")) {
             const int v = atoi(e);
             if (v == 16 || v == 32 || v == 48 || v == 96) cw = v;
@@ -451,6 +696,9 @@ static TcChunks tc_chunks(int p, int tf) {
     c.mbytes = off_all;
     c.stage = 2 * TC_A_BYTES + 2 * pbmax;
     c.nst = TC_STAGES * c.stage + 1280 <= 227 * 1024 ? TC_STAGES : 2;
+    c.bstage = 2 * pbmax;
+    const int nb = (227 * 1024 - 1280 - 4 * SL_BYTES) / c.bstage;   // at least 2: bstage <= 2 TC_PMAX
+    c.nbst = nb > 4 ? 4 : nb;
     return c;
 }
 
@@ -468,9 +716,31 @@ int tc_build_b(int p, int tf, const double* Dtab, void* B, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-// Encodes the 16 tensor maps (8 classes x hi/lo) of one level.
-// Tensor dims (innermost first): e (16 bytes), i (hs), chunk (12 or 24), j (hs), k (hs);
-// the box takes one K-part (12 chunks) of an 8 x 4 x 4 brick.
+// Encodes the tensor maps (8 classes x hi/lo) of one level for both
+// kernels.  Tensor dims (innermost first): e (16 bytes), i (hs), chunk (12
+// or 24), j (hs), k (hs); a box takes one K-part (12 chunks) of an 8 x 4 x 4
+// brick, or of a 10 x 18 x 1 slab where the class grid has 16 cells per
+// axis or more.
+static int encode_set(TcMaps* m, int tf, void* hi, void* lo, cuuint64_t hs, const cuuint32_t box[5]) {
+    const int es = tc_elem_bytes(tf), epc = 16 / es;
+    const cuuint64_t nch = (cuuint64_t)(TC_K / epc);
+    const cuuint64_t dims[5] = {(cuuint64_t)epc, hs, nch, hs, hs};
+    const cuuint64_t strides[4] = {16, hs * 16, nch * hs * 16, hs * nch * hs * 16};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const size_t cls_bytes = (size_t)hs * hs * hs * TC_K * es;
+    const CUtensorMapDataType dt = tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    for (int c = 0; c < 8; ++c) {
+        for (int h = 0; h < 2; ++h) {
+            void* base = (char*)(h ? lo : hi) + c * cls_bytes;
+            CUresult r = g_encode(h ? &m->lo[c] : &m->hi[c], dt, 5, base, dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return -1;
+        }
+    }
+    return 0;
+}
+
 int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps) {
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
@@ -481,39 +751,41 @@ int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps) {
             return -2;
         g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    TcMaps* maps = (TcMaps*)out_maps;
-    const int es = tc_elem_bytes(tf), epc = 16 / es;
-    const cuuint64_t nch = (cuuint64_t)(TC_K / epc);
+    TcLevelMaps* maps = (TcLevelMaps*)out_maps;
+    const int epc = 16 / tc_elem_bytes(tf);
     const cuuint64_t hs = (cuuint64_t)1 << (l - 1);
-    const cuuint64_t dims[5] = {(cuuint64_t)epc, hs, nch, hs, hs};
-    const cuuint64_t strides[4] = {16, hs * 16, nch * hs * 16, hs * nch * hs * 16};
-    const cuuint32_t box[5] = {(cuuint32_t)epc, 8, (cuuint32_t)TC_CH, 4, 4};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const size_t cls_bytes = (size_t)hs * hs * hs * TC_K * es;
-    const CUtensorMapDataType dt = tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    for (int c = 0; c < 8; ++c) {
-        for (int h = 0; h < 2; ++h) {
-            void* base = (char*)(h ? lo : hi) + c * cls_bytes;
-            CUresult r = g_encode(h ? &maps->lo[c] : &maps->hi[c], dt, 5, base, dims, strides, box, estr,
-                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return -1;
-        }
+    const cuuint32_t brick[5] = {(cuuint32_t)epc, 8, (cuuint32_t)TC_CH, 4, 4};
+    if (encode_set(&maps->brick, tf, hi, lo, hs, brick) != 0) return -1;
+    maps->slab_ok = 0;
+    if (hs >= 16 && !getenv("FMM_TC_NO_SLAB")) {
+        const cuuint32_t slab[5] = {(cuuint32_t)epc, SL_I, (cuuint32_t)TC_CH, SL_J, 1};
+        maps->slab_ok = encode_set(&maps->slab, tf, hi, lo, hs, slab) == 0;
     }
     return 0;
 }
-size_t tc_maps_bytes() { return sizeof(TcMaps); }
+size_t tc_maps_bytes() { return sizeof(TcLevelMaps); }
 
 template <int TF>
 static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const void* B, double* Lt, int64_t ncell,
                      int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
-    const int smem = ch.nst * ch.stage + 1024 + 256;
-    if (cudaFuncSetAttribute(k_m2l_tc<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return -2;
-    const int tpc = (hs / 8) * (hs / 4) * (hs / 4);
-    k_m2l_tc<TF><<<(unsigned)(8 * tpc), 192, smem, s>>>(*(const TcMaps*)maps, ch, l, nc, (const unsigned char*)B,
-                                                        Lt, ncell, err);
+    const TcLevelMaps* m = (const TcLevelMaps*)maps;
+    if (m->slab_ok) {
+        const int smem = 4 * SL_BYTES + ch.nbst * ch.bstage + 1024 + 256;
+        if (cudaFuncSetAttribute(k_m2l_tc_slab<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess)
+            return -2;
+        const int tpc = (hs / 8) * (hs / 16) * hs;
+        k_m2l_tc_slab<TF><<<(unsigned)(8 * tpc), SL_THREADS, smem, s>>>(m->slab, ch, l, nc, (const unsigned char*)B, Lt,
+                                                                 ncell, err);
+    } else {
+        const int smem = ch.nst * ch.stage + 1024 + 256;
+        if (cudaFuncSetAttribute(k_m2l_tc<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return -2;
+        const int tpc = (hs / 8) * (hs / 4) * (hs / 4);
+        k_m2l_tc<TF><<<(unsigned)(8 * tpc), 192, smem, s>>>(m->brick, ch, l, nc, (const unsigned char*)B, Lt,
+                                                            ncell, err);
+    }
     count_launch();
     return 0;
 }
