@@ -429,8 +429,10 @@ def emit_grouped_file(p, basis):
                  " iz = 2 * (int)(t / ((int64_t)hs * hs)) + cz;")
         for a in range(r1 - r0):
             L.append("  float a%d = 0.f;" % a)
+        L.append("  // offsets of this block: group blockIdx.y of gridDim.y (one group on large levels)")
+        L.append("  const int u0 = (int)blockIdx.y * 216 / (int)gridDim.y, u1 = ((int)blockIdx.y + 1) * 216 / (int)gridDim.y;")
         L.append("  #pragma unroll 1")
-        L.append("  for (int u = 0; u < 216; ++u) {")
+        L.append("  for (int u = u0; u < u1; ++u) {")
         L.append("    const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;")
         L.append("    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;")
         L.append("    const float* Kg = K + (int64_t)((3 - oz) * 49 + (3 - oy) * 7 + (3 - ox)) * %d + %d;" % (kst, off[r0]))
@@ -449,15 +451,23 @@ def emit_grouped_file(p, basis):
         L.append("  }")
         L.append("  if (!act) return;")
         L.append("  const int64_t tg = (int64_t)cls * h3 + t;")
+        L.append("  if (gridDim.y == 1) {")
         for r in range(r0, r1):
-            L.append("  Lt[(int64_t)%d * ncell + tg] = (double)a%d;" % (r, r - r0))
+            L.append("    Lt[(int64_t)%d * ncell + tg] = (double)a%d;" % (r, r - r0))
+        L.append("  } else {")
+        for r in range(r0, r1):
+            L.append("    atomicAdd(Lt + (int64_t)%d * ncell + tg, (double)a%d);" % (r, r - r0))
+        L.append("  }")
         L.append("}")
+    L.append("// groups > 1 splits the 216 offset slots of every target over that many")
+    L.append("// blocks (small levels); the partial sums are added into a zeroed Lt.")
     L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
-             " cudaStream_t s) {" % (p, basis))
+             " cudaStream_t s, int groups) {" % (p, basis))
     L.append("  const int hs = (1 << l) >> 1;")
     L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + 127) / 128;")
+    L.append("  if (groups > 1 && cudaMemsetAsync(Lt, 0, (size_t)%d * ncell * sizeof(double), s) != cudaSuccess) return -1;" % len(rows))
     for k in range(len(parts)):
-        L.append("  m2l_grp_p%d_b%d_r%d<<<(unsigned)(8 * bpc), 128, 0, s>>>(l, M, Lt, K, ncell);" % (p, basis, k))
+        L.append("  m2l_grp_p%d_b%d_r%d<<<dim3((unsigned)(8 * bpc), (unsigned)groups), 128, 0, s>>>(l, M, Lt, K, ncell);" % (p, basis, k))
     L.append("  return %d;" % len(parts))
     L.append("}")
     L.append("}  // namespace fmm")
@@ -737,12 +747,20 @@ def emit_grouped_dispatch():
     for p in range(PMAX + 1):
         for b in (0, 1):
             L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
-                     " cudaStream_t s);" % (p, b))
+                     " cudaStream_t s, int groups);" % (p, b))
+    L.append("// Levels with fewer target blocks than about four per SM split the offsets")
+    L.append("// of every target over up to 27 blocks.")
     L.append("int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K,"
              " int64_t ncell, cudaStream_t s) {")
+    L.append("  static int sms = 0;")
+    L.append("  if (!sms) { int d = 0; cudaGetDevice(&d); cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);"
+             " if (sms <= 0) sms = 1; }")
+    L.append("  const int64_t hs = (int64_t)1 << (l - 1), blocks = 8 * ((hs * hs * hs + 127) / 128);")
+    L.append("  int64_t g = (4 * (int64_t)sms + blocks - 1) / blocks;")
+    L.append("  const int groups = (int)(g < 1 ? 1 : g > 27 ? 27 : g);")
     for p in range(PMAX + 1):
         for b in (0, 1):
-            L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s);"
+            L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s, groups);"
                      % (p, b, p, b))
     L.append("  return -1;")
     L.append("}")
