@@ -15,7 +15,7 @@ the dominant kernel (M2L), the oracle timed on the host cores, an
 end-to-end figure through fmm_evaluate_host, and SM clocks sampled during the
 timed region.
 
-  python bench.py [--gpus N --steps K --warmup W] [--form fp64|fp32]
+  python bench.py [--gpus N --steps K --warmup W] [--form bf16x3|tf32x3|fp32|fp64]
   python bench.py --impl reference ...      # the FP64 CPU oracle
   python bench.py --workload m2l ...        # per-pair M2L micro-benchmark sweep
 """
@@ -249,17 +249,17 @@ def run_gpu(args):
     mhz = pk.get("sm_max_mhz", 2070.0)
     tc = None
     if prec in (F.GEMM_BF16X3, F.GEMM_TF32X3):
-        # executed tensor-core work of levels 4..6: per tile of 128 targets and
+        # executed tensor-core work of levels 5..6: per tile of 128 targets and
         # offset, 3 passes; the local components run in N-chunks of cw rows,
         # chunk j (lowest rank a_j) over the (p - a_j + 1)^2 multipole columns
         # it needs, rounded up to K-steps of 16 (BF16) or 8 (TF32) columns
         # (the kernel's chunk rule)
-        cw = int(os.environ.get("FMM_TC_CHUNK", "32"))
+        cw = int(os.environ.get("FMM_TC_CHUNK", "48" if prec == F.GEMM_BF16X3 else "32"))
         ks = 16 if prec == F.GEMM_BF16X3 else 8
         nc = (P + 1) ** 2
         rk = [a for a in range(P + 1) for _ in range(2 * a + 1)]   # rank of each traceless component
         cols = sum(cw * ks * (((P - rk[r0] + 1) ** 2 + ks - 1) // ks) for r0 in range(0, nc, cw))
-        tiles = sum(8 ** (l - 1) // 128 * 8 for l in range(4, DEPTH + 1))
+        tiles = sum(8 ** (l - 1) // 128 * 8 for l in range(5, DEPTH + 1))
         tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * cols}
     if prec == F.FP64:
         peak = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
@@ -279,7 +279,7 @@ def run_gpu(args):
             bf *= NOMINAL_TENSOR["tf32"] / NOMINAL_TENSOR["bf16"]
             src += " x nominal TF32/BF16 ratio 1.1/2.25"
         ex = tc["executed_flop_per_step"] / (m2l_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": "m2l (tensor cores at levels 4..6; FP32 SIMT at 2..3)",
+        roof = {"bound": "tensor", "kernel": "m2l (tensor cores at levels 5..6; FP32 SIMT at 2..4)",
                 "achieved": ex, "peak": bf, "unit": "TFLOP/s", "frac": ex / bf, "traffic": M2L_TRAFFIC.get(form),
                 "peak_source": src,
                 "executed_flop_per_step": tc["executed_flop_per_step"],
@@ -613,7 +613,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp32", choices=["fp64", "fp32", "bf16x3", "tf32x3"])
+    ap.add_argument("--form", default="bf16x3", choices=["fp64", "fp32", "bf16x3", "tf32x3"])
     ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l", "adaptive", "learned"])
     ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
     ap.add_argument("--no-cpu", action="store_true")

@@ -524,7 +524,7 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             int64_t tb = 0;
             for (int l = 0; l <= pl->depth; ++l) {
                 pl->mbf_off[l] = tb;
-                if (l >= 4) tb += 2 * (int64_t)tc_m_elems(l);
+                if (l >= tc_first_level()) tb += 2 * (int64_t)tc_m_elems(l);
             }
             pl->maps.assign((size_t)(pl->depth + 1) * tc_maps_bytes() + 64, 0);
             if (tb > 0 && cudaMalloc(&pl->Mbf, tb * es) != cudaSuccess) {
@@ -532,7 +532,7 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
                 free_tree(pl);
                 FAIL(FMM_ERR_OOM, "allocating tensor-core operands failed");
             }
-            for (int l = 4; l <= pl->depth; ++l) {
+            for (int l = tc_first_level(); l <= pl->depth; ++l) {
                 char* hi = (char*)pl->Mbf + pl->mbf_off[l] * es;
                 char* lo = hi + tc_m_elems(l) * es;
                 if (tc_encode_maps(l, tf, hi, lo, tc_maps_at(pl, l)) != 0) {
@@ -607,8 +607,9 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
     }
     if (is_tc(pl->cfg.prec) && pl->depth >= 2) {
         const int tf = pl->cfg.prec == FMM_GEMM_TF32X3, es = tc_elem_bytes(tf);
-        // levels 2..3 (grids smaller than one 8x4x4 tile) on the FP32 grouped kernel
-        const int lt = pl->depth < 3 ? pl->depth : 3;
+        // levels below the first tensor-core level (class grids smaller than one
+        // 8 x 16 x 1 column) on the FP32 grouped kernel
+        const int lt = pl->depth < tc_first_level() - 1 ? pl->depth : tc_first_level() - 1;
         const int64_t b = pl->lvl_off[2], e = pl->lvl_off[lt] + ((int64_t)pl->nc << (3 * lt));
         launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
         for (int l = 2; l <= lt; ++l) {
@@ -616,7 +617,7 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
                                              pl->K32, (int64_t)1 << (3 * l), S(stream));
             for (int k = 0; k < parts; ++k) count_launch();
         }
-        for (int l = 4; l <= pl->depth; ++l) {
+        for (int l = tc_first_level(); l <= pl->depth; ++l) {
             char* hi = (char*)pl->Mbf + pl->mbf_off[l] * es;
             char* lo = hi + tc_m_elems(l) * es;
             if (tc_m2l_level(pl->cfg.p, tf, l, Mlev(pl, l), hi, lo, tc_maps_at(pl, l), pl->Kbf, Llev(pl, l),

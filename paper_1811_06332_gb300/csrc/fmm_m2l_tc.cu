@@ -4,23 +4,24 @@
 // 189 integer offsets o, and all pairs with one offset share one matrix
 //     Kt_o(n, m) = D_{n+m}(-o)/m!      (cell units, |n| + |m| <= p)
 // so M2L is a sum of dense products  Lt[T, :] += Mt[T + o, :] . Kt_o^T.
-// Per CTA: a tile of 128 target cells (a brick of 8 x 4 x 4 in one class)
+// Per CTA: a column of 128 target cells (8 x 16 x 1 in one class)
 // accumulates over all 189 offsets in TMEM:
 //     D[128 cells x 96] += A_o[128 cells x 96] . B_o[96 x 96]^T
 // with A_o the source multipoles (reduced traceless representative, padded
-// 81 -> 96) fetched by a 5-D TMA tensor load whose out-of-range part is
-// zero-filled (grid boundary), and B_o the precomputed matrix fetched by a
-// bulk copy.  Split precision: x = hi + lo, three MMAs per K-step
-// (hi.hi + hi.lo + lo.hi), FP32 accumulation in TMEM, FP64 write-out.
-// Two operand types share the kernel: BF16 (kind::f16, 16 columns per
-// K-step) and TF32 (kind::tf32, 8 columns per K-step).  A K-step is 32
-// bytes of a row in both, so the shared-memory layouts agree byte for byte;
-// TF32 rows are twice as long and are streamed in two K-parts per offset.
+// 81 -> 96) read from a source slab that a 5-D TMA tensor load brings in
+// once for up to 9 offsets (out-of-range cells zero-filled at the grid
+// boundary), and B_o the precomputed matrix fetched by a bulk copy.
+// Split precision: x = hi + lo, three MMAs per K-step (hi.hi + hi.lo +
+// lo.hi), FP32 accumulation in TMEM, FP64 write-out.  Two operand types
+// share the kernel: BF16 (kind::f16, 16 columns per K-step) and TF32
+// (kind::tf32, 8 columns per K-step).  A K-step is 32 bytes of a row in
+// both, so the shared-memory layouts agree byte for byte; TF32 rows are
+// twice as long and are streamed in two K-parts.
 //
-// Roles: warp 0 lane 0 issues copies, warp 1 owns TMEM and lane 0 issues
-// tcgen05.mma, warps 2..5 drain TMEM (each reads its lane quadrant).
-// Stages form a 3-deep mbarrier ring; every wait is bounded and reports a
-// timeout through an error word instead of hanging.
+// Roles: warp 0 lane 0 issues copies, lane 0 of 2 or 4 warps issues
+// tcgen05.mma (each into its own TMEM accumulator), warps 2..5 drain and
+// add the accumulators (each reads its lane quadrant).  Every wait is
+// bounded and reports a timeout through an error word instead of hanging.
 #include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -35,10 +36,8 @@ constexpr int TC_N = 96;                       // padded local components (N)
 constexpr int TC_CH = 12;                      // 16-byte chunks of one A row per K-part
 constexpr int TC_PSTEPS = 6;                   // K-steps (32 bytes of a row) per K-part
 constexpr int TC_NCH = TC_N / 16;              // N-chunks of at least 16 local components
-constexpr int TC_A_BYTES = 128 * TC_CH * 16;   // 24576: one A operand (hi or lo) of one K-part
 constexpr int TC_PMAX = TC_N * TC_PSTEPS * 32; // 18432: bound on one part block (hi or lo) of a matrix
-constexpr int TC_STAGES = 3;
-constexpr int TC_TMEM_COLS = 128;
+constexpr int TC_TMEM_COLS = 128;             // one accumulator (96 columns used)
 constexpr long TC_SPIN = 1L << 24;             // bounded waits
 
 // The matrix of one offset is block-triangular in rank (|n| + |m| <= p), so
@@ -59,10 +58,9 @@ struct TcChunks {
     int pbytes[2];           // bytes of part t's block (hi or lo), a multiple of 1024
     int poff[2];             // byte offset of part t's hi block inside one offset's matrix
     int mbytes;              // bytes of one offset's matrix (every part, hi and lo)
-    int stage;               // bytes of one pipeline stage (brick kernel)
-    int nst;                 // pipeline stages that fit in shared memory (2 or 3)
-    int bstage;              // bytes of one matrix stage (slab kernel): 2 x largest part block
-    int nbst;                // matrix stages of the slab kernel (2 to 4)
+    int bstage;              // bytes of one matrix stage: 2 x largest part block
+    int nbst;                // matrix stages (2 or 4)
+    int niss;                // MMA-issuing warps (2 or 4; divides nbst)
 };
 
 struct TcMaps {
@@ -70,8 +68,8 @@ struct TcMaps {
     CUtensorMap lo[8];
 };
 
-// Source-slab variant (levels with at least 16 cells per class and axis).
-// A CTA owns a column of 8 x 16 x 1 target cells of one class.  For one
+// Source slabs (levels with at least 16 cells per class and axis).  A CTA
+// owns a column of 8 x 16 x 1 target cells of one class.  For one
 // source class and one z shift dz in {-1, 0, 1}, the sources of the (up to
 // 9) offsets with x, y shifts dx, dy in {-1, 0, 1} all lie in one slab of
 // 10 x 18 x 1 cells, stored [j][chunk][i][16 bytes]: the A operand of
@@ -83,9 +81,7 @@ constexpr int SL_I = 10, SL_J = 18;
 constexpr int SL_BYTES = SL_I * TC_CH * SL_J * 16;   // 34560: one slab operand (hi or lo) of one K-part
 
 struct alignas(64) TcLevelMaps {
-    TcMaps brick;   // box 8 x 4 x 4 cells (brick kernel)
-    TcMaps slab;    // box 10 x 18 x 1 cells (slab kernel)
-    int slab_ok;    // slab maps encoded (class grid of at least 16 per axis)
+    TcMaps slab;    // box 10 x 18 x 1 cells, one K-part
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -126,8 +122,6 @@ __host__ __device__ constexpr uint32_t make_idesc(int tf, int M, int N) {
            | ((uint32_t)(M >> 4) << 24);              // M
 }
 
-__device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
-
 template <int TF>
 __device__ __forceinline__ void tc_mma(uint32_t dcol, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     if constexpr (TF)
@@ -144,175 +138,6 @@ __device__ __forceinline__ void tc_mma(uint32_t dcol, uint64_t ad, uint64_t bd, 
             : "memory");
 }
 
-template <int TF>
-__global__ void __launch_bounds__(192, 1)
-k_m2l_tc(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrows,
-         const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = (uint64_t*)(smem + ch.nst * ch.stage);
-    uint64_t* full = bars;                 // [TC_STAGES]
-    uint64_t* empty = bars + TC_STAGES;    // [TC_STAGES]
-    uint64_t* done = bars + 2 * TC_STAGES;
-    uint32_t* tslot = (uint32_t*)(bars + 2 * TC_STAGES + 1);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int hs = 1 << (l - 1);
-    const int nti = hs / 8, ntj = hs / 4;
-    const int tpc = nti * ntj * (hs / 4);
-    const int cls = blockIdx.x / tpc, t = blockIdx.x % tpc;
-    const int ti = t % nti, tj = (t / nti) % ntj, tk = t / (nti * ntj);
-    const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < ch.nst; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(TC_TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-
-    if (warp == 0 && lane == 0) {
-        // ---------------- producer ----------------
-        int it = 0;
-        bool ok = true;
-        for (int u = 0; u < 216 && ok; ++u) {
-            const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;
-            if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-            const int scls = ((cx + ox) & 1) | (((cy + oy) & 1) << 1) | (((cz + oz) & 1) << 2);
-            const int c1 = 8 * ti + floor_half(cx + ox), c3 = 4 * tj + floor_half(cy + oy),
-                      c4 = 4 * tk + floor_half(cz + oz);
-            const CUtensorMap* mh = &maps.hi[scls];
-            const CUtensorMap* ml = &maps.lo[scls];
-            const int ridx = (3 - oz) * 49 + (3 - oy) * 7 + (3 - ox);   // r = target - source = -o
-            for (int pt = 0; pt < ch.np; ++pt) {
-                const int s = it % ch.nst;
-                const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
-                if (!(ok = mbar_wait(smem_u32(&empty[s]), ph ^ 1u, err, 1))) break;
-                const uint32_t fb = smem_u32(&full[s]);
-                const int bb = 2 * ch.pbytes[pt];
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                             "r"(2 * TC_A_BYTES + bb)
-                             : "memory");
-                unsigned char* st = smem + s * ch.stage;
-                asm volatile(
-                    "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st)),
-                    "l"((uint64_t)mh), "r"(0), "r"(c1), "r"(TC_CH * pt), "r"(c3), "r"(c4), "r"(fb)
-                    : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st + TC_A_BYTES)),
-                    "l"((uint64_t)ml), "r"(0), "r"(c1), "r"(TC_CH * pt), "r"(c3), "r"(c4), "r"(fb)
-                    : "memory");
-                const unsigned char* kb = Kmat + (int64_t)ridx * ch.mbytes + ch.poff[pt];
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(st + 2 * TC_A_BYTES)),
-                    "l"((uint64_t)kb), "r"(bb), "r"(fb)
-                    : "memory");
-                ++it;
-            }
-        }
-        // drain: every issued stage has landed before the CTA may exit
-        const int first = it > ch.nst ? it - ch.nst : 0;
-        for (int k = first; k < it; ++k)
-            mbar_wait(smem_u32(&full[k % ch.nst]), (uint32_t)(k / ch.nst) & 1u, err, 2);
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        const uint32_t idesc = make_idesc(TF, 128, ch.cw);
-        int it = 0;
-        bool ok = true;
-        for (int u = 0; u < 216 && ok; ++u) {
-            const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;
-            if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-            for (int pt = 0; pt < ch.np; ++pt) {
-                const int s = it % ch.nst;
-                const uint32_t ph = (uint32_t)(it / ch.nst) & 1u;
-                if (!(ok = mbar_wait(smem_u32(&full[s]), ph, err, 3))) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t base = smem_u32(smem + s * ch.stage);
-                const uint32_t a_addr[2] = {base, base + TC_A_BYTES};
-                const uint32_t b_addr[2] = {base + 2 * TC_A_BYTES, base + 2 * TC_A_BYTES + ch.pbytes[pt]};
-                for (int j = 0; j < ch.nch; ++j) {
-                    const int nk = ch.nk[pt][j];
-                    const uint32_t dcol = tmem + (uint32_t)(ch.cw * j);
-                    const uint32_t sbo = 256u * nk;
-#pragma unroll
-                    for (int pass = 0; pass < 3; ++pass) {
-                        const int ia = pass == 2 ? 1 : 0, ib = pass == 1 ? 1 : 0;   // hi.hi, hi.lo, lo.hi
-                        for (int ks = 0; ks < nk; ++ks) {
-                            const uint64_t ad = make_desc(a_addr[ia] + ks * 256, 128, TC_CH * 128);
-                            const uint64_t bd = make_desc(b_addr[ib] + ch.boff[pt][j] + ks * 256, 128, sbo);
-                            // part 0 of the first offset holds at least one K-step of every chunk
-                            const uint32_t acc = (it > 0 || pass > 0 || ks > 0) ? 1u : 0u;
-                            tc_mma<TF>(dcol, ad, bd, idesc, acc);
-                        }
-                    }
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&empty[s]))
-                             : "memory");
-                ++it;
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(done))
-                     : "memory");
-        (void)ok;
-    } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> FP64 L ----------------
-        bool ok = true;
-        if (lane == 0) ok = mbar_wait(smem_u32(done), 0u, err, 4);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        __syncwarp();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int q = warp & 3;
-        const int row = q * 32 + lane;
-        const int i = row & 7, j = (row >> 3) & 3, k = row >> 5;
-        const int64_t h3 = (int64_t)hs * hs * hs;
-        const int64_t tg = (int64_t)cls * h3 + ((int64_t)(4 * tk + k) * hs + (4 * tj + j)) * hs + (8 * ti + i);
-#pragma unroll
-        for (int cb = 0; cb < TC_N / 32; ++cb) {
-            uint32_t v[32];
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (ok) {
-#pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int n = cb * 32 + e;
-                    if (n < nrows) Lt[(int64_t)n * ncell + tg] = (double)__uint_as_float(v[e]);
-                }
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 1) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
-    }
-}
-
 // 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape)
 __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
     asm volatile(
@@ -325,16 +150,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
         : "r"(ta));
 }
 
-// Slab kernel.  Two rings: 2 slab buffers ({hi, lo} of one K-part) and
-// nbst matrix stages.  The producer (warp 0) walks (source class, dz, part)
-// slabs and, after each slab, the matrices of its offsets.  The cost of an
-// MMA here is set by its issue rather than by its tensor work, so two warps
-// issue (warps 1 and 6, alternate offsets) into two TMEM accumulators of
-// 128 columns each, which the epilogue (warps 2..5) adds.  A slab is freed
-// when both issuers have committed its MMAs.
-constexpr int SL_THREADS = 224;
-template <int TF>
-__global__ void __launch_bounds__(SL_THREADS, 1)
+// Two rings: 2 slab buffers ({hi, lo} of one K-part) and nbst matrix
+// stages.  The producer (warp 0) walks (source class, dz, part) slabs and,
+// after each slab, the matrices of its offsets.  The MMAs of one offset are
+// small (N <= 96), and their cost is set by their issue more than by their
+// tensor work, so NISS warps (1 and 6, 7, ...) issue round-robin over the
+// offsets, each into its own TMEM accumulator of 128 columns; the epilogue
+// (warps 2..5) adds them.  A slab is freed when every issuer has committed
+// its MMAs.  NISS divides nbst, so every matrix stage has one issuer, which
+// waits on its phases in order (a parity wait cannot tell phases two apart).
+template <int NISS>
+constexpr int sl_threads() { return 32 * (5 + NISS); }
+template <int TF, int NISS>
+__global__ void __launch_bounds__(sl_threads<NISS>(), 1)
 k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrows,
               const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
@@ -355,22 +183,26 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
     const int cls = blockIdx.x / tpc, t = blockIdx.x % tpc;
     const int ti = t % nti, tj = (t / nti) % ntj, tk = t / (nti * ntj);
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
+    if (ch.niss != NISS || ch.nbst % NISS != 0 || ch.nbst > 4) {   // launch/config mismatch: no barrier is used
+        if (threadIdx.x == 0) atomicExch(err, 17);
+        return;
+    }
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sfull[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&sempty[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sempty[b])), "r"(NISS));
         }
         for (int b = 0; b < ch.nbst; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bfull[b])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bempty[b])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(done)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(done)), "r"(NISS));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(2 * TC_TMEM_COLS));
+                     "r"(NISS * TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -438,9 +270,9 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
             mbar_wait(smem_u32(&sfull[k & 1]), (uint32_t)(k >> 1) & 1u, err, 13);
         for (int k = bt > ch.nbst ? bt - ch.nbst : 0; k < bt; ++k)
             mbar_wait(smem_u32(&bfull[k % ch.nbst]), (uint32_t)(k / ch.nbst) & 1u, err, 13);
-    } else if ((warp == 1 || warp == 6) && lane == 0) {
+    } else if ((warp == 1 || warp >= 6) && lane == 0) {
         // ---------------- MMA issuers ----------------
-        const int w = warp == 1 ? 0 : 1;
+        const int w = warp == 1 ? 0 : warp - 5;
         const uint32_t dbase = tmem + (uint32_t)(w * TC_TMEM_COLS);
         const uint32_t idesc = make_idesc(TF, 128, ch.cw);
         int sl = 0, bt = 0;
@@ -460,7 +292,7 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
                         for (int dx = -1; dx <= 1; ++dx) {
                             const int ox = 2 * dx + sx - cx;
                             if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
-                            const int mine = (bt & 1) == w;
+                            const int mine = bt % NISS == w;
                             const int bs = bt % ch.nbst;
                             ++bt;
                             if (!mine) continue;
@@ -502,7 +334,7 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
                          smem_u32(done))
                      : "memory");
     } else if (warp >= 2 && warp <= 5) {
-        // ---------------- epilogue: TMEM (two accumulators) -> FP64 L ----------------
+        // ---------------- epilogue: TMEM (NISS accumulators) -> FP64 L ----------------
         bool ok = true;
         if (lane == 0) ok = mbar_wait(smem_u32(done), 0u, err, 16);
         ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -515,17 +347,25 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
         const int64_t tg = (int64_t)cls * h3 + ((int64_t)tk * hs + (16 * tj + j)) * hs + (8 * ti + i);
 #pragma unroll 1
         for (int cb = 0; cb < TC_N / 32; ++cb) {
-            uint32_t v[32], u[32];
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
+            double acc[32];
+            uint32_t v[32];
             tmem_ld32(ta, v);
-            tmem_ld32(ta + TC_TMEM_COLS, u);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc[e] = (double)__uint_as_float(v[e]);
+#pragma unroll 1
+            for (int w = 1; w < NISS; ++w) {
+                tmem_ld32(ta + (uint32_t)(w * TC_TMEM_COLS), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 32; ++e) acc[e] += (double)__uint_as_float(v[e]);
+            }
             if (ok) {
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
                     const int n = cb * 32 + e;
-                    if (n < nrows)
-                        Lt[(int64_t)n * ncell + tg] = (double)__uint_as_float(v[e]) + (double)__uint_as_float(u[e]);
+                    if (n < nrows) Lt[(int64_t)n * ncell + tg] = acc[e];
                 }
             }
         }
@@ -534,7 +374,8 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(NISS * TC_TMEM_COLS));
     }
 }
 
@@ -650,18 +491,15 @@ size_t tc_b_bytes(int tf) { return (size_t)343 * 2 * TC_PMAX * (tf ? 2 : 1); }
 int tc_elem_bytes(int tf) { return tf ? 4 : 2; }
 
 // Chunk width: the N of one MMA.  Wider chunks issue fewer, larger MMAs;
-// narrower ones skip more of the zero triangle.  FMM_TC_CHUNK (16, 32, 48 or
-// 96) overrides the default for tuning.
-static int tc_chunk_width() {
-    static int cw = 0;
-    if (!cw) {
-        cw = 96;
-        if (const char* e = getenv("FMM_TC_CHUNK")) {
-            const int v = atoi(e);
-            if (v == 16 || v == 32 || v == 48 || v == 96) cw = v;
-        }
+// narrower ones skip more of the zero triangle and leave room for four
+// matrix stages (four issuers).  Measured best at p = 8: 48 for BF16, 32
+// for TF32.  FMM_TC_CHUNK (16, 32, 48 or 96) overrides it for tuning.
+static int tc_chunk_width(int tf) {
+    if (const char* e = getenv("FMM_TC_CHUNK")) {
+        const int v = atoi(e);
+        if (v == 16 || v == 32 || v == 48 || v == 96) return v;
     }
-    return cw;
+    return tf ? 32 : 48;
 }
 
 static TcChunks tc_chunks(int p, int tf) {
@@ -669,7 +507,7 @@ static TcChunks tc_chunks(int p, int tf) {
     const int nc = ncoef_of(p, 1);
     const int cps = tf ? 8 : 16;   // columns per K-step
     c.tf = tf;
-    c.cw = tc_chunk_width();
+    c.cw = tc_chunk_width(tf);
     c.nch = (nc + c.cw - 1) / c.cw;
     for (int j = 0; j < c.nch; ++j) {
         const int r0 = c.cw * j;
@@ -694,14 +532,14 @@ static TcChunks tc_chunks(int p, int tf) {
         pbmax = c.pbytes[pt] > pbmax ? c.pbytes[pt] : pbmax;
     }
     c.mbytes = off_all;
-    c.stage = 2 * TC_A_BYTES + 2 * pbmax;
-    c.nst = TC_STAGES * c.stage + 1280 <= 227 * 1024 ? TC_STAGES : 2;
     c.bstage = 2 * pbmax;
     const int nb = (227 * 1024 - 1280 - 4 * SL_BYTES) / c.bstage;   // at least 2: bstage <= 2 TC_PMAX
-    c.nbst = nb > 4 ? 4 : nb;
+    c.nbst = nb >= 4 ? 4 : 2;
+    c.niss = c.nbst;
     return c;
 }
 
+int tc_first_level() { return 5; }   // class grid of 16 cells per axis: one slab column fits
 size_t tc_m_elems(int l) { return l < 1 ? 0 : ((size_t)8 << (3 * (l - 1))) * TC_K; }
 
 int tc_build_b(int p, int tf, const double* Dtab, void* B, cudaStream_t s) {
@@ -716,11 +554,9 @@ int tc_build_b(int p, int tf, const double* Dtab, void* B, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-// Encodes the tensor maps (8 classes x hi/lo) of one level for both
-// kernels.  Tensor dims (innermost first): e (16 bytes), i (hs), chunk (12
-// or 24), j (hs), k (hs); a box takes one K-part (12 chunks) of an 8 x 4 x 4
-// brick, or of a 10 x 18 x 1 slab where the class grid has 16 cells per
-// axis or more.
+// Encodes the tensor maps (8 classes x hi/lo) of one level.  Tensor dims
+// (innermost first): e (16 bytes), i (hs), chunk (12 or 24), j (hs), k (hs);
+// the box takes one K-part (12 chunks) of a 10 x 18 x 1 slab.
 static int encode_set(TcMaps* m, int tf, void* hi, void* lo, cuuint64_t hs, const cuuint32_t box[5]) {
     const int es = tc_elem_bytes(tf), epc = 16 / es;
     const cuuint64_t nch = (cuuint64_t)(TC_K / epc);
@@ -754,38 +590,24 @@ int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps) {
     TcLevelMaps* maps = (TcLevelMaps*)out_maps;
     const int epc = 16 / tc_elem_bytes(tf);
     const cuuint64_t hs = (cuuint64_t)1 << (l - 1);
-    const cuuint32_t brick[5] = {(cuuint32_t)epc, 8, (cuuint32_t)TC_CH, 4, 4};
-    if (encode_set(&maps->brick, tf, hi, lo, hs, brick) != 0) return -1;
-    maps->slab_ok = 0;
-    if (hs >= 16 && !getenv("FMM_TC_NO_SLAB")) {
-        const cuuint32_t slab[5] = {(cuuint32_t)epc, SL_I, (cuuint32_t)TC_CH, SL_J, 1};
-        maps->slab_ok = encode_set(&maps->slab, tf, hi, lo, hs, slab) == 0;
-    }
-    return 0;
+    if (hs < 16) return -1;
+    const cuuint32_t slab[5] = {(cuuint32_t)epc, SL_I, (cuuint32_t)TC_CH, SL_J, 1};
+    return encode_set(&maps->slab, tf, hi, lo, hs, slab) == 0 ? 0 : -1;
 }
 size_t tc_maps_bytes() { return sizeof(TcLevelMaps); }
 
-template <int TF>
+template <int TF, int NISS>
 static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const void* B, double* Lt, int64_t ncell,
                      int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
     const TcLevelMaps* m = (const TcLevelMaps*)maps;
-    if (m->slab_ok) {
-        const int smem = 4 * SL_BYTES + ch.nbst * ch.bstage + 1024 + 256;
-        if (cudaFuncSetAttribute(k_m2l_tc_slab<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-            cudaSuccess)
-            return -2;
-        const int tpc = (hs / 8) * (hs / 16) * hs;
-        k_m2l_tc_slab<TF><<<(unsigned)(8 * tpc), SL_THREADS, smem, s>>>(m->slab, ch, l, nc, (const unsigned char*)B, Lt,
-                                                                 ncell, err);
-    } else {
-        const int smem = ch.nst * ch.stage + 1024 + 256;
-        if (cudaFuncSetAttribute(k_m2l_tc<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-            return -2;
-        const int tpc = (hs / 8) * (hs / 4) * (hs / 4);
-        k_m2l_tc<TF><<<(unsigned)(8 * tpc), 192, smem, s>>>(m->brick, ch, l, nc, (const unsigned char*)B, Lt,
-                                                            ncell, err);
-    }
+    const int smem = 4 * SL_BYTES + ch.nbst * ch.bstage + 1024 + 256;
+    if (cudaFuncSetAttribute(k_m2l_tc_slab<TF, NISS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -2;
+    const int tpc = (hs / 8) * (hs / 16) * hs;
+    k_m2l_tc_slab<TF, NISS><<<(unsigned)(8 * tpc), sl_threads<NISS>(), smem, s>>>(
+        m->slab, ch, l, nc, (const unsigned char*)B, Lt, ncell, err);
     count_launch();
     return 0;
 }
@@ -793,7 +615,7 @@ static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const 
 int tc_m2l_level(int p, int tf, int l, const double* M, void* hi, void* lo, const void* maps, const void* B,
                  double* Lt, int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
-    if (hs < 8) return -1;
+    if (hs < 16) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const int nc = ncoef_of(p, 1);
     const int64_t tot = ncell * (TC_K * tc_elem_bytes(tf) / 16);
@@ -804,8 +626,11 @@ int tc_m2l_level(int p, int tf, int l, const double* M, void* hi, void* lo, cons
         k_tc_split_m<0><<<g, 256, 0, s>>>(l, nc, M, hi, lo);
     count_launch();
     const TcChunks ch = tc_chunks(p, tf);
-    const int rc = tf ? tc_launch<1>(ch, l, nc, maps, B, Lt, ncell, err, s)
-                      : tc_launch<0>(ch, l, nc, maps, B, Lt, ncell, err, s);
+    if (ch.niss != 2 && ch.niss != 4) return -1;
+    const int rc = tf ? (ch.niss == 4 ? tc_launch<1, 4>(ch, l, nc, maps, B, Lt, ncell, err, s)
+                                      : tc_launch<1, 2>(ch, l, nc, maps, B, Lt, ncell, err, s))
+                      : (ch.niss == 4 ? tc_launch<0, 4>(ch, l, nc, maps, B, Lt, ncell, err, s)
+                                      : tc_launch<0, 2>(ch, l, nc, maps, B, Lt, ncell, err, s));
     if (rc != 0) return rc;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
