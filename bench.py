@@ -35,14 +35,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FMM particles/s at 1e-4 rel force err; M2L pairs/s vs plain FP64 GPU form"
 N_PART, DEPTH, P, BASIS = 4194304, 6, 8, 1
+TC_LEVEL = 5   # first level on the tensor cores (class grid of 16 cells per axis)
 SEED = 3
 WORKLOAD = "uniform cube, 4,194,304 particles, equal masses 1/N, depth-6 octree (262,144 leaves), traceless p=8"
 L2_FLUSH_BYTES = 256 << 20
 NOMINAL = {"sm_count": 152, "fp64_fma_per_clk_sm": 2, "fp32_fma_per_clk_sm": 128}
-# DRAM bytes (read + write) of the M2L kernels per step, from one ncu capture
-# of the level-6 launch (profiles/m2l_*_level6_uniform4M_p8.md) scaled by the
-# cells of all M2L levels; set to None whenever the kernel changes.
-M2L_TRAFFIC = {"fp32": (643.8e6 + 154.9e6) * (299584 / 262144)}
+# DRAM bytes (read + write) of the dominant kernel per step, from one ncu
+# capture of its level-6 launch (profiles/m2l_*_level6_uniform4M_p8.md)
+# scaled by the cells of the levels it runs on (BF16x3: the slab kernel at
+# levels 5..6, operand-split launches excluded); None for a form whose kernel
+# changed since its counters were taken.
+M2L_TRAFFIC = {"bf16x3": (792.2e6 + 156.1e6) * (294912 / 262144)}
 # nominal dense tensor rates (PFLOP/s): a TF32 contraction takes the measured
 # BF16 peak scaled by their ratio
 NOMINAL_TENSOR = {"bf16": 2.25, "tf32": 1.1}
@@ -59,19 +62,20 @@ def peaks():
 
 
 def m2l_pairs_uniform(depth):
-    """Number of M2L (target, source) pairs of the uniform interaction lists."""
-    tot = 0
-    for l in range(2, depth + 1):
-        s = 1 << l
-        i = np.arange(s)
-        p = i >> 1
-        # per axis: sources j in [2p-2, 2p+3] inside the grid, per target i
-        cnt_all = np.minimum(2 * p + 3, s - 1) - np.maximum(2 * p - 2, 0) + 1
-        cnt_adj = np.minimum(i + 1, s - 1) - np.maximum(i - 1, 0) + 1
-        a3 = np.einsum("i,j,k->", cnt_all, cnt_all, cnt_all)
-        b3 = np.einsum("i,j,k->", cnt_adj, cnt_adj, cnt_adj)
-        tot += int(a3 - b3)
-    return tot
+    """Number of M2L (target, source) pairs of the uniform interaction lists
+    (per axis: sources j in [2p-2, 2p+3] inside the grid, p the parent of i)."""
+    return sum(m2l_pairs_level(l) for l in range(2, depth + 1))
+
+
+def m2l_pairs_level(l):
+    """M2L pairs of uniform level l (sources in the parents' neighbours'
+    children, minus the target's own neighbours), grid boundary included."""
+    s = 1 << l
+    i = np.arange(s)
+    p = i >> 1
+    cnt_all = np.minimum(2 * p + 3, s - 1) - np.maximum(2 * p - 2, 0) + 1
+    cnt_adj = np.minimum(i + 1, s - 1) - np.maximum(i - 1, 0) + 1
+    return int(np.einsum("i,j,k->", cnt_all, cnt_all, cnt_all) - np.einsum("i,j,k->", cnt_adj, cnt_adj, cnt_adj))
 
 
 def m2l_fma_per_pair(p, basis):
@@ -192,20 +196,24 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     plan = F.Plan(p=P, basis=BASIS, prec=prec, depth=DEPTH)
 
-    stages = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p"]
+    # M2L runs as two calls, levels 2..4 and 5..6 (the tensor-core levels of
+    # the tensor-core forms), so that the dominant kernel is timed on its own
+    stages = ["tree", "p2m", "m2m", "m2l_2_4", "m2l_5_6", "l2l", "l2p", "p2p"]
+    NST = len(stages)
 
     def step(ev):
         ev[0].record(stream)
         plan.fmm_build_tree(*X); ev[1].record(stream)
         plan.fmm_p2m(); ev[2].record(stream)
         plan.fmm_m2m(); ev[3].record(stream)
-        plan.fmm_m2l(); ev[4].record(stream)
-        plan.fmm_l2l(); ev[5].record(stream)
-        plan.fmm_l2p(out[0], out[1], out[2], out[3]); ev[6].record(stream)
-        plan.fmm_p2p(out[0], out[1], out[2], out[3]); ev[7].record(stream)
+        plan.fmm_m2l_levels(2, TC_LEVEL - 1); ev[4].record(stream)
+        plan.fmm_m2l_levels(TC_LEVEL, DEPTH); ev[5].record(stream)
+        plan.fmm_l2l(); ev[6].record(stream)
+        plan.fmm_l2p(out[0], out[1], out[2], out[3]); ev[7].record(stream)
+        plan.fmm_p2p(out[0], out[1], out[2], out[3]); ev[8].record(stream)
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
-    wev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(NST + 1)] for _ in range(args.steps)]
+    wev = [torch.cuda.Event(enable_timing=True) for _ in range(NST + 1)]
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step(wev)
@@ -223,7 +231,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    per_stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(7)] for k in range(args.steps)])
+    per_stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(NST)] for k in range(args.steps)])
     step_ms = per_stage.sum(1)
     t_ms = float(step_ms.mean())
     if world > 1:
@@ -242,8 +250,10 @@ def run_gpu(args):
     acc = out[1:, tsel]
     rel_err = float(torch.sqrt(((acc - ref[1:]) ** 2).sum() / (ref[1:] ** 2).sum()).item())
 
-    m2l_ms = float(per_stage[:, 3].mean())
+    m2l_ms = float((per_stage[:, 3] + per_stage[:, 4]).mean())
+    tc_ms = float(per_stage[:, 4].mean())
     npairs = m2l_pairs_uniform(DEPTH)
+    tc_pairs = sum(m2l_pairs_level(l) for l in range(TC_LEVEL, DEPTH + 1))
     fma = m2l_fma_per_pair(P, BASIS)
     pk, pk_kind = peaks()
     mhz = pk.get("sm_max_mhz", 2070.0)
@@ -278,13 +288,20 @@ def run_gpu(args):
         if prec == F.GEMM_TF32X3:
             bf *= NOMINAL_TENSOR["tf32"] / NOMINAL_TENSOR["bf16"]
             src += " x nominal TF32/BF16 ratio 1.1/2.25"
-        ex = tc["executed_flop_per_step"] / (m2l_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": "m2l (tensor cores at levels 5..6; FP32 SIMT at 2..4)",
-                "achieved": ex, "peak": bf, "unit": "TFLOP/s", "frac": ex / bf, "traffic": M2L_TRAFFIC.get(form),
-                "peak_source": src,
-                "executed_flop_per_step": tc["executed_flop_per_step"],
-                "algorithmic_flop_per_step": npairs * 2 * fma,
-                "algorithmic_tflops": achieved, "m2l_ms_per_step": m2l_ms}
+        # algorithmic work of the split-precision form: 3 products (hi.hi,
+        # hi.lo, lo.hi) of every nonzero matrix entry per pair; the executed
+        # work adds the padding of the dense MMA tiles
+        alg = tc_pairs * 3 * 2 * fma
+        ach = alg / (tc_ms * 1e-3) / 1e12
+        ex = tc["executed_flop_per_step"] / (tc_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor",
+                "kernel": "tensor-core M2L, levels %d..%d (%d pairs; operand split included)" % (TC_LEVEL, DEPTH,
+                                                                                               tc_pairs),
+                "achieved": ach, "peak": bf, "unit": "TFLOP/s", "frac": ach / bf, "traffic": M2L_TRAFFIC.get(form),
+                "peak_source": src, "kernel_ms_per_step": tc_ms,
+                "algorithmic_flop_per_step": alg, "executed_flop_per_step": tc["executed_flop_per_step"],
+                "executed_tflops": ex, "executed_frac": ex / bf,
+                "m2l_all_levels_ms_per_step": m2l_ms}
 
     # plain FP64 GPU form beside it (same workload, fewer steps)
     fp64 = None
@@ -339,7 +356,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "form": form, "p": P, "basis": "traceless", "depth": DEPTH,
                    "particles_per_gpu": N_PART, "m2l_pairs": npairs, "l2": "flushed (256 MiB write) before each step"},
         "rel_force_err": rel_err,
-        "stage_ms": {s: float(per_stage[:, i].mean()) for i, s in enumerate(stages)},
+        "stage_ms": dict({s: float(per_stage[:, i].mean()) for i, s in enumerate(stages)}, m2l=m2l_ms),
         "m2l_pairs_per_s": world * npairs / (m2l_ms * 1e-3),
         "fp64_form": fp64,
         "vs_fp64_form": value / world / fp64["value"],

@@ -144,6 +144,13 @@ int fmm_m2m(fmm_plan* plan, void* stream);
 /* M2L over the interaction lists of levels 2..depth (Eq. M2L, Sec. 2.1),
  * r = z_target - z_source, in the plan's precision form. */
 int fmm_m2l(fmm_plan* plan, void* stream);
+/* M2L of the uniform levels lmin..lmax only (clamped to 2..depth; Eq. M2L,
+ * Sec. 2.1).  Levels are independent, so calling it on disjoint ranges that
+ * cover 2..depth computes what fmm_m2l computes (used to time the
+ * tensor-core levels apart from the rest).  Adaptive plans:
+ * FMM_ERR_UNSUPPORTED; lmin > lmax: FMM_ERR_ARG; before fmm_build_tree:
+ * FMM_ERR_STATE. */
+int fmm_m2l_levels(fmm_plan* plan, int lmin, int lmax, void* stream);
 /* L2L top-down (Eq. L2L, Sec. 2.1), delta = z_child - z_parent. */
 int fmm_l2l(fmm_plan* plan, void* stream);
 /* L2P (Eq. L2P, Sec. 2.1): OVERWRITES pot, ax, ay, az (device, length n,

@@ -587,6 +587,8 @@ int fmm_m2m(fmm_plan* pl, void* stream) {
     return FMM_OK;
 }
 
+static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream);
+
 int fmm_m2l(fmm_plan* pl, void* stream) {
     NEED_TREE();
     if (pl->ad) {
@@ -605,32 +607,42 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
         CKLAUNCH();
         return FMM_OK;
     }
-    if (is_tc(pl->cfg.prec) && pl->depth >= 2) {
+    return m2l_uniform(pl, 2, pl->depth, stream);
+}
+
+// M2L of the uniform levels lo..hi (clamped to 2..depth) of any form.
+static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
+    if (lo < 2) lo = 2;
+    if (hi > pl->depth) hi = pl->depth;
+    if (lo > hi) return FMM_OK;
+    if (is_tc(pl->cfg.prec)) {
         const int tf = pl->cfg.prec == FMM_GEMM_TF32X3, es = tc_elem_bytes(tf);
         // levels below the first tensor-core level (class grids smaller than one
         // 8 x 16 x 1 column) on the FP32 grouped kernel
-        const int lt = pl->depth < tc_first_level() - 1 ? pl->depth : tc_first_level() - 1;
-        const int64_t b = pl->lvl_off[2], e = pl->lvl_off[lt] + ((int64_t)pl->nc << (3 * lt));
-        launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
-        for (int l = 2; l <= lt; ++l) {
-            const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
-                                             pl->K32, (int64_t)1 << (3 * l), S(stream));
-            for (int k = 0; k < parts; ++k) count_launch();
+        const int lt = hi < tc_first_level() - 1 ? hi : tc_first_level() - 1;
+        if (lo <= lt) {
+            const int64_t b = pl->lvl_off[lo], e = pl->lvl_off[lt] + ((int64_t)pl->nc << (3 * lt));
+            launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
+            for (int l = lo; l <= lt; ++l) {
+                const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
+                                                 pl->K32, (int64_t)1 << (3 * l), S(stream));
+                for (int k = 0; k < parts; ++k) count_launch();
+            }
         }
-        for (int l = tc_first_level(); l <= pl->depth; ++l) {
-            char* hi = (char*)pl->Mbf + pl->mbf_off[l] * es;
-            char* lo = hi + tc_m_elems(l) * es;
-            if (tc_m2l_level(pl->cfg.p, tf, l, Mlev(pl, l), hi, lo, tc_maps_at(pl, l), pl->Kbf, Llev(pl, l),
+        for (int l = lo > tc_first_level() ? lo : tc_first_level(); l <= hi; ++l) {
+            char* hp = (char*)pl->Mbf + pl->mbf_off[l] * es;
+            char* lp = hp + tc_m_elems(l) * es;
+            if (tc_m2l_level(pl->cfg.p, tf, l, Mlev(pl, l), hp, lp, tc_maps_at(pl, l), pl->Kbf, Llev(pl, l),
                              pl->derr, S(stream)) != 0)
                 FAIL(FMM_ERR_CUDA, "tensor-core M2L launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         }
         CKLAUNCH();
         return FMM_OK;
     }
-    if (pl->cfg.prec == FMM_FP32 && pl->depth >= 2) {
-        const int64_t b = pl->lvl_off[2], e = pl->lvl_off[pl->depth] + ((int64_t)pl->nc << (3 * pl->depth));
+    if (pl->cfg.prec == FMM_FP32) {
+        const int64_t b = pl->lvl_off[lo], e = pl->lvl_off[hi] + ((int64_t)pl->nc << (3 * hi));
         launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
-        for (int l = 2; l <= pl->depth; ++l) {
+        for (int l = lo; l <= hi; ++l) {
             const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
                                              pl->K32, (int64_t)1 << (3 * l), S(stream));
             for (int k = 0; k < parts; ++k) count_launch();
@@ -638,11 +650,18 @@ int fmm_m2l(fmm_plan* pl, void* stream) {
         CKLAUNCH();
         return FMM_OK;
     }
-    for (int l = 2; l <= pl->depth; ++l)
+    for (int l = lo; l <= hi; ++l)
         launch_m2l_fp64_level(pl->cfg.p, pl->cfg.basis, l, pl->Dtab, Mlev(pl, l), Llev(pl, l),
                               (int64_t)1 << (3 * l), S(stream));
     CKLAUNCH();
     return FMM_OK;
+}
+
+int fmm_m2l_levels(fmm_plan* pl, int lmin, int lmax, void* stream) {
+    NEED_TREE();
+    if (pl->ad) FAIL(FMM_ERR_UNSUPPORTED, "fmm_m2l_levels needs a uniform octree (adaptive plans use fmm_m2l)");
+    if (lmin > lmax) FAIL(FMM_ERR_ARG, "lmin=%d > lmax=%d", lmin, lmax);
+    return m2l_uniform(pl, lmin, lmax, stream);
 }
 
 int fmm_l2l(fmm_plan* pl, void* stream) {

@@ -210,6 +210,38 @@ def test_tensor_core_forms_low_order(F, p):
         assert ep < tol and ea < tol, (prec, ep, ea, per)
 
 
+@pytest.mark.parametrize("form", ["GEMM_BF16X3", "FP32", "FP64"])
+def test_m2l_levels_split_equals_m2l(F, form):
+    """fmm_m2l_levels over disjoint level ranges covering 2..depth gives
+    fmm_m2l's result (levels are independent); up to the order of the FP64
+    atomic adds of the split small levels."""
+    n, depth, p = 131072, 5, 6
+    x, y, z = inputs.uniform_cube(n, 51)
+    q = inputs.masses_equal(n)
+    X = [g(a) for a in (x, y, z, q)]
+    plan = F.Plan(p=p, basis=1, prec=getattr(F, form), depth=depth)
+    outs = []
+    for split in (False, True):
+        o = torch.zeros((4, n), dtype=torch.float64, device="cuda")
+        plan.fmm_build_tree(*X)
+        plan.fmm_p2m()
+        plan.fmm_m2m()
+        if split:
+            plan.fmm_m2l_levels(2, 4)
+            plan.fmm_m2l_levels(5, 9)
+        else:
+            plan.fmm_m2l()
+        plan.fmm_l2l()
+        plan.fmm_l2p(o[0], o[1], o[2], o[3])
+        plan.fmm_p2p(o[0], o[1], o[2], o[3])
+        torch.cuda.synchronize()
+        outs.append(o.cpu().numpy())
+    with pytest.raises(F.FMMError):
+        plan.fmm_m2l_levels(4, 3)
+    plan.close()
+    np.testing.assert_allclose(outs[1], outs[0], rtol=1e-12, atol=0)
+
+
 def test_tensor_core_form_rejects_unsupported(F):
     for prec in (F.GEMM_BF16X3, F.GEMM_TF32X3):
         with pytest.raises(F.FMMError):
