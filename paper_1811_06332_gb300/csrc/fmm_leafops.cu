@@ -372,9 +372,27 @@ int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const
 // FP32 P2P on positions relative to leaf centres: one warp per target leaf,
 // two targets per lane (each staged source is used twice from registers),
 // lane groups split the sources, one 16-byte shared load per source.  The
-// self pair and coincident pairs have r^2 == 0 exactly and are dropped by a
-// select, as the direct sum skips them.
+// target leaf itself comes first among the 27 neighbour leaves: only the
+// chunks that hold its particles can contain the self pair or coincident
+// pairs (r^2 == 0 exactly, dropped by a select as the direct sum skips
+// them); particles of distinct leaves never coincide, so the other chunks
+// run without the select.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void p2p32_pair(const float4 sv, const float4 p, float& f, float& x, float& y, float& z) {
+    const float rx = sv.x - p.x, ry = sv.y - p.y, rz = sv.z - p.z;
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    const float ir = rsqrtf(r2);
+    const float qir = sv.w * ir, qir3 = qir * ir * ir;
+    f += qir; x = fmaf(qir3, rx, x); y = fmaf(qir3, ry, y); z = fmaf(qir3, rz, z);
+}
+__device__ __forceinline__ void p2p32_pair_guarded(const float4 sv, const float4 p, float& f, float& x, float& y,
+                                                   float& z) {
+    const float rx = sv.x - p.x, ry = sv.y - p.y, rz = sv.z - p.z;
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float qir = sv.w * ir, qir3 = qir * ir * ir;
+    f += qir; x = fmaf(qir3, rx, x); y = fmaf(qir3, ry, y); z = fmaf(qir3, rz, z);
+}
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* __restrict__ pos,
@@ -404,7 +422,9 @@ k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* _
         int cntS = 0, sbS = 0;
         float ox = 0.f, oy = 0.f, oz = 0.f;
         if (lane < 27) {
-            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+            // lane 0: the target leaf (neighbour 13); lanes 1..26: the others in order
+            const int d = lane == 0 ? 13 : lane <= 13 ? lane - 1 : lane;
+            const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
             const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
             if (jx >= 0 && jy >= 0 && jz >= 0 && jx < side && jy < side && jz < side) {
                 const int64_t S = cell_index(depth, jx, jy, jz);
@@ -420,6 +440,7 @@ k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* _
             if (lane >= o) incl += v;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
+        const int nself = __shfl_sync(0xffffffffu, cntS, 0);   // sources of the target leaf: [0, nself)
         // full 32-wide chunks of the concatenated neighbour sources
         for (int c0 = 0; c0 < total; c0 += 32) {
             {
@@ -442,21 +463,18 @@ k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* _
             }
             {
                 const int cnt = min(32, total - c0);
-                for (int k = grp; k < cnt; k += G) {
-                    const float4 sv = sP[w][k];
-                    {
-                        const float rx = sv.x - pa.x, ry = sv.y - pa.y, rz = sv.z - pa.z;
-                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                        const float qir = sv.w * ir, qir3 = qir * ir * ir;
-                        fa += qir; xa = fmaf(qir3, rx, xa); ya = fmaf(qir3, ry, ya); za = fmaf(qir3, rz, za);
+                if (c0 < nself) {
+                    for (int k = grp; k < cnt; k += G) {
+                        const float4 sv = sP[w][k];
+                        p2p32_pair_guarded(sv, pa, fa, xa, ya, za);
+                        p2p32_pair_guarded(sv, pb, fb, xb, yb, zb);
                     }
-                    {
-                        const float rx = sv.x - pb.x, ry = sv.y - pb.y, rz = sv.z - pb.z;
-                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                        const float qir = sv.w * ir, qir3 = qir * ir * ir;
-                        fb += qir; xb = fmaf(qir3, rx, xb); yb = fmaf(qir3, ry, yb); zb = fmaf(qir3, rz, zb);
+                } else {
+#pragma unroll 2
+                    for (int k = grp; k < cnt; k += G) {
+                        const float4 sv = sP[w][k];
+                        p2p32_pair(sv, pa, fa, xa, ya, za);
+                        p2p32_pair(sv, pb, fb, xb, yb, zb);
                     }
                 }
             }
