@@ -11,6 +11,46 @@
 namespace fmm {
 
 // ---------------------------------------------------------------------------
+// 16-byte shared-memory access helpers (P2M power tables, L2P columns)
+// ---------------------------------------------------------------------------
+// padded length (a multiple of 16 bytes); offset of column (kx, ky) in the
+// column-nested layout of a symmetric tensor of rank <= P
+template <typename T>
+__host__ __device__ constexpr int pad16(int len) {
+    return (len + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T));
+}
+template <int P, typename T>
+__host__ __device__ constexpr int nested_col_off(int kx, int ky) {
+    int off = 0;
+    for (int x = 0; x <= P; ++x)
+        for (int y = 0; y <= P - x; ++y) {
+            if (x == kx && y == ky) return off;
+            off += pad16<T>(P + 1 - x - y);
+        }
+    return off;
+}
+// loads n (compile-time after unrolling) consecutive coefficients from a 16-byte aligned shared address
+template <typename T, int N>
+__device__ __forceinline__ void load16(const T* __restrict__ src, T (&dst)[N]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < (N + 3) / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(src)[q];
+            if (4 * q + 0 < N) dst[4 * q + 0] = v.x;
+            if (4 * q + 1 < N) dst[4 * q + 1] = v.y;
+            if (4 * q + 2 < N) dst[4 * q + 2] = v.z;
+            if (4 * q + 3 < N) dst[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < (N + 1) / 2; ++q) {
+            const double2 v = reinterpret_cast<const double2*>(src)[q];
+            if (2 * q + 0 < N) dst[2 * q + 0] = v.x;
+            if (2 * q + 1 < N) dst[2 * q + 1] = v.y;
+        }
+    }
+}
+// ---------------------------------------------------------------------------
 // P2M: one warp per leaf.  Particles are staged 32 at a time together with
 // the powers of their offsets (one particle per lane); lane c owns the column
 // (nx, ny) of multi-indices and adds q x^nx y^ny z^j for every j of the
@@ -24,8 +64,11 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
            const float4* __restrict__ pos32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
+    // powers per axis; FP32 rows padded to 16 bytes for vector loads (FP64 rows
+    // unpadded: at p = 10 padding would pass the 48 KB of static shared memory)
+    constexpr int PP = sizeof(T) == 4 ? pad16<T>(P + 1) : P + 1;
     __shared__ T sx[WARPS][32], sy[WARPS][32], sz[WARPS][32], sq[WARPS][32];
-    __shared__ T sPw[WARPS][32][3][P + 1];
+    __shared__ __align__(16) T sPw[WARPS][32][3][PP];
     __shared__ T sA[WARPS][NS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * WARPS + w;
@@ -81,6 +124,13 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
         __syncwarp();
         for (int i = 0; i < cnt; ++i) {
             const T qa = sq[w][i];
+            T zp[P + 1];   // the particle's z powers (same address across the warp)
+            if constexpr (sizeof(T) == 4) {
+                load16<T, P + 1>(sPw[w][i][2], zp);   // 16-byte loads
+            } else {
+#pragma unroll
+                for (int j = 0; j <= P; ++j) zp[j] = sPw[w][i][2][j];
+            }
 #pragma unroll
             for (int k = 0; k < KC; ++k) {
                 if (lane + 32 * k < NCOL) {
@@ -89,7 +139,7 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
                     const int rem = P - cnx[k] - cny[k];
 #pragma unroll
                     for (int j = 0; j <= P; ++j)
-                        if (j <= rem) acc[k][j] = fma(wgt, sPw[w][i][2][j], acc[k][j]);
+                        if (j <= rem) acc[k][j] = fma(wgt, zp[j], acc[k][j]);
                 }
             }
         }
@@ -125,10 +175,62 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
 // ---------------------------------------------------------------------------
 // L2P: one half-warp per leaf (two leaves per warp), lanes over particles.
 // The expansion (full symmetric, dependent traceless components rebuilt)
-// sits in shared memory and the lanes of a half read the same coefficient at
-// the same time.  Nested sums
+// sits in shared memory in a column-nested layout: column (kx, ky) holds
+// L[kx, ky, 0..P-kx-ky] contiguously from a 16-byte aligned offset, so a
+// lane reads a column with 16-byte loads (the lanes of a half read the same
+// address at the same time).  Nested sums
 // Phi = sum_kx ax[kx] sum_ky ay[ky] sum_kz az[kz] L[kx,ky,kz].
 // ---------------------------------------------------------------------------
+// the column sums of one (kx, ky): potential and the three gradient components
+template <int P, typename T, int KX, int KY>
+__device__ __forceinline__ void l2p_column(const T* __restrict__ Ln, const T (&fz)[P + 1], T& s_p, T& s_gx, T& s_gy,
+                                           T& s_gz) {
+    constexpr int LEN = P + 1 - KX - KY;
+    T c0[LEN];
+    load16<T, LEN>(Ln + nested_col_off<P, T>(KX, KY), c0);
+    s_p = T(0);
+#pragma unroll
+    for (int kz = 0; kz < LEN; ++kz) s_p = fma(fz[kz], c0[kz], s_p);
+    s_gx = s_gy = s_gz = T(0);
+    if constexpr (LEN > 1) {
+        T c1[LEN - 1], c2[LEN - 1];
+        load16<T, LEN - 1>(Ln + nested_col_off<P, T>(KX + 1, KY), c1);
+        load16<T, LEN - 1>(Ln + nested_col_off<P, T>(KX, KY + 1), c2);
+#pragma unroll
+        for (int kz = 0; kz < LEN - 1; ++kz) {
+            s_gx = fma(fz[kz], c1[kz], s_gx);
+            s_gy = fma(fz[kz], c2[kz], s_gy);
+            s_gz = fma(fz[kz], c0[kz + 1], s_gz);
+        }
+    }
+}
+template <int P, typename T, int KX, int KY>
+__device__ __forceinline__ void l2p_row(const T* __restrict__ Ln, const T (&fy)[P + 1], const T (&fz)[P + 1],
+                                        T& sx_p, T& sx_gx, T& sx_gy, T& sx_gz) {
+    if constexpr (KY <= P - KX) {
+        T s_p, s_gx, s_gy, s_gz;
+        l2p_column<P, T, KX, KY>(Ln, fz, s_p, s_gx, s_gy, s_gz);
+        sx_p = fma(fy[KY], s_p, sx_p);
+        sx_gx = fma(fy[KY], s_gx, sx_gx);
+        sx_gy = fma(fy[KY], s_gy, sx_gy);
+        sx_gz = fma(fy[KY], s_gz, sx_gz);
+        l2p_row<P, T, KX, KY + 1>(Ln, fy, fz, sx_p, sx_gx, sx_gy, sx_gz);
+    }
+}
+template <int P, typename T, int KX>
+__device__ __forceinline__ void l2p_all(const T* __restrict__ Ln, const T (&fx)[P + 1], const T (&fy)[P + 1],
+                                        const T (&fz)[P + 1], T& ph, T& gx, T& gy, T& gz) {
+    if constexpr (KX <= P) {
+        T sx_p = T(0), sx_gx = T(0), sx_gy = T(0), sx_gz = T(0);
+        l2p_row<P, T, KX, 0>(Ln, fy, fz, sx_p, sx_gx, sx_gy, sx_gz);
+        ph = fma(fx[KX], sx_p, ph);
+        gx = fma(fx[KX], sx_gx, gx);
+        gy = fma(fx[KX], sx_gy, gy);
+        gz = fma(fx[KX], sx_gz, gz);
+        l2p_all<P, T, KX + 1>(Ln, fx, fy, fz, ph, gx, gy, gz);
+    }
+}
+
 template <int P, typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
@@ -137,8 +239,9 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
             double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az,
             const float4* __restrict__ pos32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
+    constexpr int NN = nested_col_off<P, T>(P + 1, 0);   // nested layout size (a multiple of 16 bytes)
     __shared__ T sA[WARPS][2][NS];
-    __shared__ T sL[WARPS][2][NS];
+    __shared__ __align__(16) T sN[WARPS][2][NN];
     // two leaves per warp, one per half-warp (leaves hold ~16 particles)
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, h = lane >> 4, hl = lane & 15;
     const int64_t c = ((int64_t)blockIdx.x * WARPS + w) * 2 + h;
@@ -157,11 +260,13 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
             const T* E = expand + off.expand[j] + row * (2 * j + 1);
             T v = T(0);
             for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][h][j * j + t];
-            sL[w][h][s] = v;
+            sN[w][h][nested_col_off<P, T>(nx, ny) + nz] = v;
         }
     } else {
         for (int s = hl; s < NS; s += 16)
-            if (valid) sL[w][h][s] = T(Lt[(int64_t)s * nleaf + c]);
+            if (valid)
+                sN[w][h][nested_col_off<P, T>(c_sym_idx[s][0], c_sym_idx[s][1]) + c_sym_idx[s][2]] =
+                    T(Lt[(int64_t)s * nleaf + c]);
     }
     __syncwarp();
     if (!valid || b == e) return;
@@ -169,7 +274,7 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
     cell_coords(depth, c, ix, iy, iz);
     const double inv_h = (double)(1 << depth), hc = 1.0 / inv_h;
     const double cx = (ix + 0.5) * hc, cy = (iy + 0.5) * hc, cz = (iz + 0.5) * hc;
-    const T* L = sL[w][h];
+    const T* Ln = sN[w][h];
     for (int a0 = b; a0 < e; a0 += 16) {
         const int a = a0 + hl;
         if (a >= e) break;
@@ -189,25 +294,7 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
             fz[k] = fz[k - 1] * rz * T(1.0 / k);
         }
         T ph = 0, gx = 0, gy = 0, gz = 0;
-#pragma unroll
-        for (int kx = 0; kx <= P; ++kx) {
-            T sx_p = 0, sx_gx = 0, sx_gy = 0, sx_gz = 0;
-#pragma unroll
-            for (int ky = 0; ky <= P - kx; ++ky) {
-                T s_p = 0, s_gx = 0, s_gy = 0, s_gz = 0;
-#pragma unroll
-                for (int kz = 0; kz <= P - kx - ky; ++kz) {
-                    s_p += fz[kz] * L[pos_sym(kx, ky, kz)];
-                    if (kx + ky + kz < P) {
-                        s_gx += fz[kz] * L[pos_sym(kx + 1, ky, kz)];
-                        s_gy += fz[kz] * L[pos_sym(kx, ky + 1, kz)];
-                        s_gz += fz[kz] * L[pos_sym(kx, ky, kz + 1)];
-                    }
-                }
-                sx_p += fy[ky] * s_p; sx_gx += fy[ky] * s_gx; sx_gy += fy[ky] * s_gy; sx_gz += fy[ky] * s_gz;
-            }
-            ph += fx[kx] * sx_p; gx += fx[kx] * sx_gx; gy += fx[kx] * sx_gy; gz += fx[kx] * sx_gz;
-        }
+        l2p_all<P, T, 0>(Ln, fx, fy, fz, ph, gx, gy, gz);
         const int o = perm[a];
         pot[o] = -(double)ph * inv_h;
         ax[o] = (double)gx * inv_h * inv_h;
