@@ -242,13 +242,16 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
 // five-step search, so every staged chunk holds 32 sources (float4: offset
 // from the target leaf centre via the integer centres, charge) whatever the
 // leaf sizes.  r = 0 pairs (the particle itself, coincident points)
-// contribute nothing.  Accumulates into caller order.
+// contribute nothing: they occur only among the target leaf's own
+// particles, so only the chunks that hold them take the r^2 == 0 select.
+// Accumulates into caller order.
 // ---------------------------------------------------------------------------
+template <bool GUARD>
 __device__ __forceinline__ void p2p_acc(const float4 s, float xi, float yi, float zi, float& ph, float& gx,
                                         float& gy, float& gz) {
     const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float ir = GUARD ? (r2 > 0.f ? rsqrtf(r2) : 0.f) : rsqrtf(r2);
     const float qir = s.w * ir, qir3 = qir * ir * ir;
     ph += qir;
     gx = fmaf(qir3, dx, gx);
@@ -329,16 +332,39 @@ k_ad_p2p32(int nwork, const int* __restrict__ work, const int* __restrict__ off,
                     if (lane >= o) incl += v;
                 }
                 const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
+                // the target leaf's own particles in this batch: [s0, s1) of the concatenation
+                const unsigned selfm = __ballot_sync(0xffffffffu, kk < k1 && src[kk < k1 ? kk : k0] == c);
+                int s0 = total, s1 = total;
+                if (selfm) {
+                    const int sl = __ffs(selfm) - 1;
+                    s0 = __shfl_sync(0xffffffffu, excl, sl);
+                    s1 = __shfl_sync(0xffffffffu, incl, sl);
+                }
                 for (int c0 = 0; c0 < total; c0 += 32) {
                     const int cnt = p2p_stage(ss[w], lane, c0, total, incl, excl, sb, ox, oy, oz, pos32);
+                    const bool guard = c0 < s1 && c0 + 32 > s0;
                     if (two) {
-                        for (int j = 0; j < cnt; ++j) {
-                            const float4 sv = ss[w][j];
-                            p2p_acc(sv, p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
-                            p2p_acc(sv, p1.x, p1.y, p1.z, ph1, gx1, gy1, gz1);
+                        if (guard) {
+                            for (int j = 0; j < cnt; ++j) {
+                                const float4 sv = ss[w][j];
+                                p2p_acc<true>(sv, p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
+                                p2p_acc<true>(sv, p1.x, p1.y, p1.z, ph1, gx1, gy1, gz1);
+                            }
+                        } else {
+                            for (int j = 0; j < cnt; ++j) {
+                                const float4 sv = ss[w][j];
+                                p2p_acc<false>(sv, p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
+                                p2p_acc<false>(sv, p1.x, p1.y, p1.z, ph1, gx1, gy1, gz1);
+                            }
                         }
                     } else if (a0) {
-                        for (int j = grp; j < cnt; j += G) p2p_acc(ss[w][j], p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
+                        if (guard) {
+                            for (int j = grp; j < cnt; j += G)
+                                p2p_acc<true>(ss[w][j], p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
+                        } else {
+                            for (int j = grp; j < cnt; j += G)
+                                p2p_acc<false>(ss[w][j], p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
+                        }
                     }
                 }
             }
