@@ -412,22 +412,20 @@ struct TcSplit<1> {
 // Multipoles of one level (FP64, [ncoef][ncell], parity-class numbering) ->
 // hi/lo operands in the TMA layout [class][k][j][chunk][i][16 bytes]
 // (components padded to 96; 8 BF16 or 4 TF32 per 16-byte chunk).  One
-// thread per (cell, chunk).
+// thread per (cell, chunk): blockIdx.y is the chunk, the cell index splits
+// into class and (i, j, k) by shifts (the class grid side is a power of 2).
 template <int TF>
 __global__ void k_tc_split_m(int l, int nc, const double* __restrict__ M, void* __restrict__ hi_,
                              void* __restrict__ lo_) {
     using T = typename TcSplit<TF>::T;
     constexpr int EPC = 16 / (int)sizeof(T);        // elements per 16-byte chunk
     constexpr int NCH = TC_K / EPC;                 // chunks per row
-    const int hs = 1 << (l - 1);
-    const int64_t h3 = (int64_t)hs * hs * hs, ncell = 8 * h3;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncell * NCH) return;
-    const int c = (int)(t / ncell);
-    const int64_t idx = t % ncell;
-    const int cls = (int)(idx / h3);
-    const int64_t lin = idx % h3;
-    const int i = (int)(lin % hs), j = (int)((lin / hs) % hs), k = (int)(lin / ((int64_t)hs * hs));
+    const int lh = l - 1, hs = 1 << lh, mask = hs - 1;
+    const int ncell = 8 << (3 * lh);
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncell) return;
+    const int c = blockIdx.y;
+    const int i = idx & mask, j = (idx >> lh) & mask, k = (idx >> (2 * lh)) & mask, cls = idx >> (3 * lh);
     __align__(16) T vh[EPC], vl[EPC];
 #pragma unroll
     for (int e = 0; e < EPC; ++e) {
@@ -618,8 +616,8 @@ int tc_m2l_level(int p, int tf, int l, const double* M, void* hi, void* lo, cons
     if (hs < 16) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const int nc = ncoef_of(p, 1);
-    const int64_t tot = ncell * (TC_K * tc_elem_bytes(tf) / 16);
-    const unsigned g = (unsigned)((tot + 255) / 256);
+    if (ncell > ((int64_t)1 << 30)) return -1;   // 32-bit cell indices in k_tc_split_m
+    const dim3 g((unsigned)((ncell + 255) / 256), (unsigned)(TC_K * tc_elem_bytes(tf) / 16));
     if (tf)
         k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, M, hi, lo);
     else
