@@ -65,8 +65,11 @@ typedef enum {
                             P2P and, for p <= 8, M2M and L2L; adaptive trees: every
                             operator); tree geometry, D-tensor tables and every stored
                             expansion in FP64                                            */
-    FMM_GEMM_TF32X3 = 2, /* M2L as offset-grouped tensor-core GEMMs, TF32 hi/lo, 3 passes */
-    FMM_GEMM_BF16X3 = 3  /* M2L as offset-grouped tensor-core GEMMs, BF16 hi/lo, 3 passes */
+    FMM_GEMM_TF32X3 = 2, /* as FMM_FP32, but M2L of the uniform levels >= 5 (class grids of
+                            16+ cells per axis) as offset-grouped tensor-core GEMMs with
+                            TF32 hi/lo operands, 3 products, FP32 accumulation; traceless
+                            basis, p <= 8, uniform trees                                  */
+    FMM_GEMM_BF16X3 = 3  /* the same with BF16 hi/lo operands                            */
 } fmm_precision;
 
 typedef struct {
@@ -77,7 +80,7 @@ typedef struct {
                               1: adaptive octree over the bounding cube of the data,
                               cells split while they hold more than max_leaf
                               particles, lists from a dual-tree traversal (App. C) */
-    int depth;             /* uniform octree depth (leaves = 8^depth), 0..10           */
+    int depth;             /* uniform octree depth (leaves = 8^depth), 0..9            */
     int max_leaf;          /* adaptive trees: maximum particles per leaf               */
     double theta;          /* adaptive trees: opening parameter of the MAC (App. C)    */
     int learned_p;         /* adaptive trees, FMM_BASIS_SYM, 4 <= p <= 10: 1 gives every
