@@ -272,6 +272,19 @@ int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, const double* x
  * uniform trees the list entries are 0 (the lists are implicit). */
 int fmm_plan_stats(const fmm_plan* plan, int64_t* out, int nout);
 
+/* Host-side layout of the tensor-core M2L kernel (no GPU needed; for
+ * diagnostics and tests) for order p (1..8, traceless) and prec
+ * FMM_GEMM_BF16X3 or FMM_GEMM_TF32X3, written to out[0..min(nout,42)):
+ * N-chunk width cw, chunks nch, K-parts per offset np, matrix stages nbst,
+ * MMA-issuing warps niss, bytes of a matrix stage, bytes of one offset's
+ * packed matrix, dynamic shared bytes per CTA, then K-steps per chunk
+ * kch[6], K-steps per part and chunk nk[2][6], byte offsets of the chunks in
+ * a part's block boff[2][6], bytes of a part's block (hi or lo) pbytes[2],
+ * byte offsets of the parts poff[2].  The chunk width follows the
+ * FMM_TC_CHUNK environment variable as the kernel does.  Returns the count
+ * written, or FMM_ERR_ARG. */
+int fmm_tc_layout(int p, int prec, int* out, int nout);
+
 /* Number of kernels this library launched since it was loaded (all plans and
  * operator calls), counted on the host at each launch. */
 int64_t fmm_kernel_launches(void);

@@ -143,6 +143,12 @@ const char* fmm_last_error(const fmm_plan* plan) { return plan ? plan->err.c_str
 
 int64_t fmm_kernel_launches(void) { return g_launches.load(); }
 
+int fmm_tc_layout(int p, int prec, int* out, int nout) {
+    if (prec != FMM_GEMM_BF16X3 && prec != FMM_GEMM_TF32X3) return FMM_ERR_ARG;
+    if (!tc_supported(p, FMM_BASIS_TRACELESS) || !out || nout < 0) return FMM_ERR_ARG;
+    return tc_layout(p, prec == FMM_GEMM_TF32X3, out, nout);
+}
+
 int fmm_plan_stats(const fmm_plan* pl, int64_t* out, int nout) {
     if (!pl || !out || nout < 0) return fail_plan(nullptr, FMM_ERR_ARG, "null plan or output");
     int64_t v[19] = {0};

@@ -137,6 +137,7 @@ int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, 
 // tf selects the operand type: 0 = BF16 hi/lo, 1 = TF32 hi/lo
 int tc_supported(int p, int basis);
 int tc_first_level();   // levels below run on the FP32 grouped kernel
+int tc_layout(int p, int tf, int* out, int nout);
 size_t tc_b_bytes(int tf);
 int tc_elem_bytes(int tf);
 size_t tc_m_elems(int l);

@@ -537,6 +537,25 @@ static TcChunks tc_chunks(int p, int tf) {
     return c;
 }
 
+// Host-side layout of the kernel for (p, operand type), for diagnostics:
+// cw, nch, np, nbst, niss, bstage, mbytes, shared bytes, kch[6], nk[2][6],
+// boff[2][6], pbytes[2], poff[2] (42 ints).  Returns the count written.
+int tc_layout(int p, int tf, int* out, int nout) {
+    const TcChunks c = tc_chunks(p, tf);
+    int v[42], n = 0;
+    v[n++] = c.cw; v[n++] = c.nch; v[n++] = c.np; v[n++] = c.nbst; v[n++] = c.niss; v[n++] = c.bstage;
+    v[n++] = c.mbytes; v[n++] = 4 * SL_BYTES + c.nbst * c.bstage + 1024 + 256;
+    for (int j = 0; j < TC_NCH; ++j) v[n++] = c.kch[j];
+    for (int t = 0; t < 2; ++t)
+        for (int j = 0; j < TC_NCH; ++j) v[n++] = c.nk[t][j];
+    for (int t = 0; t < 2; ++t)
+        for (int j = 0; j < TC_NCH; ++j) v[n++] = c.boff[t][j];
+    v[n++] = c.pbytes[0]; v[n++] = c.pbytes[1]; v[n++] = c.poff[0]; v[n++] = c.poff[1];
+    const int m = nout < n ? nout : n;
+    for (int i = 0; i < m; ++i) out[i] = v[i];
+    return m;
+}
+
 int tc_first_level() { return 5; }   // class grid of 16 cells per axis: one slab column fits
 size_t tc_m_elems(int l) { return l < 1 ? 0 : ((size_t)8 << (3 * (l - 1))) * TC_K; }
 

@@ -21,7 +21,8 @@ FP64, FP32, GEMM_TF32X3, GEMM_BF16X3 = 0, 1, 2, 3
 
 EXPORTS = [
     "fmm_ncoef", "fmm_create", "fmm_destroy", "fmm_last_error", "fmm_build_tree", "fmm_p2m", "fmm_m2m",
-    "fmm_m2l", "fmm_m2l_levels", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate", "fmm_evaluate_host", "fmm_op_dtensor",
+    "fmm_m2l", "fmm_m2l_levels", "fmm_tc_layout", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate",
+    "fmm_evaluate_host", "fmm_op_dtensor",
     "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
     "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
     "fmm_mlp_grad", "fmm_mlp_train", "fmm_mlp_predict", "fmm_set_mlp", "fmm_set_pair_orders",
@@ -62,6 +63,7 @@ def lib():
             "fmm_build_tree": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_p2m": ([_vp, _vp], _int), "fmm_m2m": ([_vp, _vp], _int),
             "fmm_m2l": ([_vp, _vp], _int), "fmm_m2l_levels": ([_vp, _int, _int, _vp], _int),
+            "fmm_tc_layout": ([_int, _int, _vp, _int], _int),
             "fmm_l2l": ([_vp, _vp], _int),
             "fmm_l2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_p2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
