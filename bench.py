@@ -67,6 +67,28 @@ def m2l_pairs_uniform(depth):
     return sum(m2l_pairs_level(l) for l in range(2, depth + 1))
 
 
+def max_over_ranks(v, world, dist, device):
+    """Maximum of a per-rank value (a time) over the ranks: the job's time is
+    its slowest rank's.  One rank: v itself."""
+    if world <= 1:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank holds its own independent set)."""
+    return world * units_per_rank / seconds
+
+
+def rank_seed(rank):
+    """Input seed of a rank: every rank evaluates its own particle set."""
+    return SEED + 1000 * rank
+
+
 def m2l_pairs_level(l):
     """M2L pairs of uniform level l (sources in the parents' neighbours'
     children, minus the target's own neighbours), grid boundary included."""
@@ -188,7 +210,7 @@ def run_gpu(args):
     form = args.form
     prec = forms[form]
     # each rank evaluates its own independent particle set (weak scaling)
-    x, y, z = inputs.uniform_cube(N_PART, SEED + 1000 * rank)
+    x, y, z = inputs.uniform_cube(N_PART, rank_seed(rank))
     q = inputs.masses_equal(N_PART)
     X = [torch.from_numpy(a).to(dev) for a in (x, y, z, q)]
     out = torch.empty((4, N_PART), dtype=torch.float64, device=dev)
@@ -233,12 +255,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     per_stage = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(NST)] for k in range(args.steps)])
     step_ms = per_stage.sum(1)
-    t_ms = float(step_ms.mean())
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * N_PART / (t_ms * 1e-3)
+    t_ms = max_over_ranks(float(step_ms.mean()), world, dist, dev)
+    value = job_rate(N_PART, world, t_ms * 1e-3)
 
     # accuracy: relative force error against an FP64 direct sum on 4096 sampled targets
     torch.cuda.synchronize()
@@ -336,7 +354,8 @@ def run_gpu(args):
             t0 = time.perf_counter()
             plan.fmm_evaluate_host(*hx, ho[0], ho[1], ho[2], ho[3])
             tms.append(time.perf_counter() - t0)
-        e2e = {"value": world * N_PART / float(np.mean(tms)), "unit": "particles/s",
+        e2e = {"value": job_rate(N_PART, world, max_over_ranks(float(np.mean(tms)), world, dist, dev)),
+               "unit": "particles/s",
                "h2d_bytes_per_step": 4 * 8 * N_PART, "d2h_bytes_per_step": 4 * 8 * N_PART,
                "host_api": "fmm_evaluate_host"}
 
