@@ -41,7 +41,7 @@ WORKLOAD = "uniform cube, 4,194,304 particles, equal masses 1/N, depth-6 octree 
 L2_FLUSH_BYTES = 256 << 20
 NOMINAL = {"sm_count": 152, "fp64_fma_per_clk_sm": 2, "fp32_fma_per_clk_sm": 128}
 # DRAM bytes (read + write) of the dominant kernel per step, from one ncu
-# capture of its level-6 launch (profiles/m2l_*_level6_uniform4M_p8.md)
+# capture of its level-6 launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # scaled by the cells of the levels it runs on (BF16x3: the slab kernel at
 # levels 5..6, operand-split launches excluded); None for a form whose kernel
 # changed since its counters were taken.

@@ -9,7 +9,7 @@
  * reference leg may load it.  The CUDA library never links, includes or calls
  * anything here, and nothing here is shared with it.
  *
- * Conventions (each one a reading of the paper, listed again in the design doc):
+ * Conventions (each one a reading of the paper where it leaves a choice open):
  *  - multi-index notation of App. D: n = (nx,ny,nz), |n| = nx+ny+nz,
  *    n! = nx! ny! nz!, r^n = x^nx y^ny z^nz; a negative component makes the
  *    whole term zero.
