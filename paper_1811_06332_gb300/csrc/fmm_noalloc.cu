@@ -45,8 +45,7 @@ constexpr int64_t NA_BYTES = O_TREE + NA_TREE_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 struct NaState {
-    bool ready = false;
-    unsigned char* base = nullptr;  // device address of g_noalloc_scratch on this device
+    unsigned char* base = nullptr;  // device address of g_noalloc_scratch whose tables are uploaded
     int p = -1, basis = -1;         // translation matrices currently held
 };
 NaState g_na[64];
@@ -87,13 +86,26 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
     if (e != cudaSuccess) return na_fail(FMM_ERR_CUDA, "cudaGetDevice failed", e);
     if (dev < 0 || dev >= 64) return na_fail(FMM_ERR_UNSUPPORTED, "device ordinal above 63");
     NaState& st = g_na[dev];
-    if (!st.ready) {
-        // one-time set-up on this device: device address of the array and
-        // the constant combinatorial tables
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return na_fail(FMM_ERR_CUDA, "cudaGetSymbolAddress failed", e);
-        unsigned char* b = (unsigned char*)ptr;
+    // Set-up and rebuilds copy from host memory and wait for the stream;
+    // neither may be recorded into a graph that the caller is capturing.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return na_fail(FMM_ERR_CUDA, "cudaStreamIsCapturing failed", e);
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    const char* cap_msg =
+        "the first call on a device, and a call whose (p, basis) differs from the previous call's, "
+        "must not be made while the stream is being captured";
+    if (capturing && (!st.base || st.p != p || st.basis != basis)) return na_fail(FMM_ERR_STATE, cap_msg);
+    // The array's device address is looked up on every call: a changed
+    // address (the module was loaded again) repeats the set-up.
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return na_fail(FMM_ERR_CUDA, "cudaGetSymbolAddress failed", e);
+    unsigned char* b = (unsigned char*)ptr;
+    const bool setup = st.base != b;
+    if (setup && capturing) return na_fail(FMM_ERR_STATE, cap_msg);
+    if (setup) {
+        // one-time set-up on this device: the constant combinatorial tables
         double offs[343 * 3];
         for (int o = 0; o < 343; ++o) {
             const int rx = o % 7 - 3, ry = (o / 7) % 7 - 3, rz = o / 49 - 3;
@@ -102,25 +114,27 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
             offs[3 * o + 1] = near ? 10.0 : ry;
             offs[3 * o + 2] = near ? 10.0 : rz;
         }
+        st.base = nullptr;
+        st.p = st.basis = -1;
         if ((e = cudaMemcpy(b + O_DETR, fmm_detr_val, sizeof(fmm_detr_val), cudaMemcpyHostToDevice)) ||
             (e = cudaMemcpy(b + O_EXPAND, fmm_expand_val, sizeof(fmm_expand_val), cudaMemcpyHostToDevice)) ||
             (e = cudaMemcpy(b + O_REDUCE, fmm_reduce_val, sizeof(fmm_reduce_val), cudaMemcpyHostToDevice)) ||
             (e = cudaMemcpy(b + O_OFFS, offs, sizeof(offs), cudaMemcpyHostToDevice)))
             return na_fail(FMM_ERR_CUDA, "uploading tables failed", e);
         st.base = b;
-        st.ready = true;
     }
-    unsigned char* b = st.base;
     const int nc = ncoef_of(p, basis);
     if (st.p != p || st.basis != basis) {
         // translation matrices and D-tensor table for this order and basis
         std::vector<double> W, V;
         build_translation(p, basis, W, V);
+        st.p = st.basis = -1;
         if ((e = cudaMemcpyAsync(b + O_W, W.data(), W.size() * 8, cudaMemcpyHostToDevice, s)) ||
             (e = cudaMemcpyAsync(b + O_V, V.data(), V.size() * 8, cudaMemcpyHostToDevice, s)))
             return na_fail(FMM_ERR_CUDA, "uploading translation matrices failed", e);
         static_assert(NA_MAX_P == 6, "na_dtable covers p = 0..6");
-        na_dtable(p, (const double*)(b + O_OFFS), (double*)(b + O_DTAB), s);
+        if (na_dtable(p, (const double*)(b + O_OFFS), (double*)(b + O_DTAB), s) != 0)
+            return na_fail(FMM_ERR_CUDA, "D-tensor table launch failed", cudaGetLastError());
         count_launch();
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess)  // host vectors W, V go out of scope
             return na_fail(FMM_ERR_CUDA, "set-up of matrices failed", e);
@@ -148,11 +162,10 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
     const double* W = (const double*)(b + O_W);
     const double* V = (const double*)(b + O_V);
     const double* Dtab = (const double*)(b + O_DTAB);
-    // the same kernels, in the same order, as fmm_evaluate with FMM_FP64
+    // the kernels fmm_evaluate runs for an FMM_FP64 uniform plan, in its order
     if (launch_uniform_tree(n, depth, x, y, z, q, xs, ys, zs, qs, perm, start, b + O_TREE, s) != 0)
         return na_fail(FMM_ERR_CUDA, "tree build failed", cudaGetLastError());
-    launch_p2m(p, basis, 1, nleaf, nullptr, start, xs, ys, zs, qs, nullptr, depth, (double)(1 << depth),
-               Mb + lo[depth], nleaf, T, s);
+    launch_p2m_leaf(0, p, basis, depth, nleaf, start, xs, ys, zs, qs, Mb + lo[depth], T, s);
     for (int l = depth - 1; l >= 2; --l)
         launch_m2m_level(p, basis, l, W, Mb + lo[l + 1], (int64_t)1 << (3 * (l + 1)), Mb + lo[l],
                          (int64_t)1 << (3 * l), s);
@@ -162,10 +175,10 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
         launch_l2l_level(p, basis, l, V, Lb + lo[l], (int64_t)1 << (3 * l), Lb + lo[l + 1],
                          (int64_t)1 << (3 * (l + 1)), s);
     if (depth >= 2)
-        launch_l2p_leaf(p, basis, depth, nleaf, start, xs, ys, zs, perm, Lb + lo[depth], T, pot, ax, ay, az, s);
+        launch_l2p_leaf2(0, p, basis, depth, nleaf, start, xs, ys, zs, perm, Lb + lo[depth], T, pot, ax, ay, az, s);
     else
         launch_zero4(n, pot, ax, ay, az, s);
-    launch_p2p_leaf(0, depth, nleaf, start, xs, ys, zs, qs, perm, pot, ax, ay, az, s);
+    launch_p2p_leaf2(0, depth, nleaf, start, xs, ys, zs, qs, perm, pot, ax, ay, az, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return na_fail(FMM_ERR_CUDA, "kernel launch failed", e);
     return FMM_OK;
 }
