@@ -173,21 +173,35 @@ int fmm_evaluate(fmm_plan* plan, int64_t n, const double* x, const double* y,
                  double* ay, double* az, void* stream);
 
 /* fmm_evaluate on HOST arrays (length n, caller order): copies the inputs to
- * the device, evaluates, copies the outputs back and waits for the stream.
+ * the device, evaluates, copies the outputs back and waits for the stream;
+ * returns fmm_sync_status's verdict.
  * Uses plan-owned staging buffers; page-locked host memory gives full copy
  * speed but is not required.  Synchronous. */
 int fmm_evaluate_host(fmm_plan* plan, int64_t n, const double* x, const double* y,
                       const double* z, const double* q, double* pot, double* ax,
                       double* ay, double* az, void* stream);
 
+/* Waits for `stream`, then reports whether a bounded wait inside one of the
+ * plan's tensor-core kernels (the M2L of the tensor-core forms, the order
+ * model's inference of learned_p plans) gave up since the previous check:
+ * FMM_ERR_TIMEOUT if so (the outputs of the work queued since that check are
+ * undefined; the report clears the plan's device error word), FMM_OK
+ * otherwise.  The queueing calls (fmm_m2l, fmm_evaluate, ...) return before
+ * their kernels run and cannot see such a timeout; fmm_evaluate_host calls
+ * this before it returns.  Synchronous. */
+int fmm_sync_status(fmm_plan* plan, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Operator-level batched entry points (independent items, physical units).
  * ------------------------------------------------------------------------- */
 
 /* D-tensor D_k(r) = grad^k |r|^{-1} for all |k| <= p (Eq. traceless grad,
- * App. A), full symmetric storage.  r: [3][n] doubles; D: [C(p+3,3)][n] of
- * doubles (prec FMM_FP64) or floats (FMM_FP32).  r must be nonzero. */
-int fmm_op_dtensor(int p, int prec, int64_t n, const double* r, void* D, void* stream);
+ * App. A).  r: [3][n] doubles, nonzero.  basis FMM_BASIS_SYM: D is
+ * [C(p+3,3)][n] in full symmetric storage; FMM_BASIS_TRACELESS: D is
+ * [(p+1)^2][n], the independent components (nz <= 1) of the traceless
+ * storage (D is trace free, so they determine it).  Elements are doubles
+ * (prec FMM_FP64) or floats (FMM_FP32, computed in FP32). */
+int fmm_op_dtensor(int p, int basis, int prec, int64_t n, const double* r, void* D, void* stream);
 
 /* P2M (Eq. P2M, Sec. 2.1; traceless: Mbar = D[M] per rank, Eq. Detracer of
  * App. A) for ncell particle groups: particles of group c are
@@ -200,9 +214,10 @@ int fmm_op_p2m(int p, int basis, int64_t ncell, const int64_t* start, const doub
 
 /* M2M (Eq. M2M / M2M part 2, Sec. 2.1): Mp[:,i] += shift of Mc[:,i] by
  * delta[:,i] = z_child - z_parent (traceless: followed by D[]).  Mc, Mp:
- * [ncoef][n] doubles (distinct arrays); delta: [3][n]. */
-int fmm_op_m2m(int p, int basis, int64_t n, const double* Mc, const double* delta,
-               double* Mp, void* stream);
+ * [ncoef][n] (distinct arrays) of doubles (prec FMM_FP64) or floats
+ * (FMM_FP32, computed in FP32); delta: [3][n] doubles. */
+int fmm_op_m2m(int p, int basis, int prec, int64_t n, const void* Mc, const double* delta,
+               void* Mp, void* stream);
 
 /* M2L (Eq. M2L, Sec. 2.1) for n independent pairs with the D-tensor computed
  * on the fly: L[:,i] (+)= sum_{|m|<=p-|n|} M_m[:,i]/m! D_{n+m}(r[:,i]).
@@ -212,15 +227,18 @@ int fmm_op_m2l(int p, int basis, int prec, int64_t n, const void* M, const doubl
                void* L, int accumulate, void* stream);
 
 /* L2L (Eq. L2L, Sec. 2.1): Lc[:,i] += shift of Lp[:,i] by
- * delta[:,i] = z_child - z_parent.  [ncoef][n] doubles, distinct arrays. */
-int fmm_op_l2l(int p, int basis, int64_t n, const double* Lp, const double* delta,
-               double* Lc, void* stream);
+ * delta[:,i] = z_child - z_parent.  Lp, Lc: [ncoef][n] (distinct arrays) of
+ * doubles (prec FMM_FP64) or floats (FMM_FP32, computed in FP32); delta:
+ * [3][n] doubles. */
+int fmm_op_l2l(int p, int basis, int prec, int64_t n, const void* Lp, const double* delta,
+               void* Lc, void* stream);
 
 /* L2P (Eq. L2P, Sec. 2.1): out[0][i] = Phi, out[1..3][i] = grad Phi at
  * offset rb[:,i] from the expansion centre (the paper's positive sign).
- * L: [ncoef][n]; rb: [3][n]; out: [4][n], OVERWRITTEN. */
-int fmm_op_l2p(int p, int basis, int64_t n, const double* L, const double* rb,
-               double* out, void* stream);
+ * L: [ncoef][n] and out: [4][n] (OVERWRITTEN) of doubles (prec FMM_FP64) or
+ * floats (FMM_FP32, computed in FP32); rb: [3][n] doubles. */
+int fmm_op_l2p(int p, int basis, int prec, int64_t n, const void* L, const double* rb,
+               void* out, void* stream);
 
 /* FP64 direct sum (Eq. PhiAB, App. B) of all n sources onto nt targets
  * (indices into the sources, int64 device array; NULL = all n, nt ignored),
@@ -236,10 +254,11 @@ int fmm_direct(int64_t n, const double* x, const double* y, const double* z,
  * front, or that cannot afford the device-wide synchronisation which
  * cudaMalloc/cudaFree may cause in the middle of a time step.
  *
- * fmm_evaluate_noalloc computes what fmm_evaluate computes for a plan with
- * {p, basis, FMM_FP64, uniform octree of depth `depth`} and returns the same
- * numbers, but it allocates nothing: no cudaMalloc, no cudaFree, no
- * allocating library routine.  Its working memory (sorted particles, leaf
+ * fmm_evaluate_noalloc runs the kernels that fmm_evaluate runs for a plan
+ * with {p, basis, FMM_FP64, uniform octree of depth `depth`}, in the same
+ * order, and its results agree with that plan's to within 1e-12 relative;
+ * but it allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  Its working memory (sorted particles, leaf
  * ranges, tree-build counters, expansions, translation matrices, tables) is
  * one fixed __device__ array of FMM_NOALLOC_BYTES_APPROX bytes that every GPU
  * which loads this library holds until the process exits.  Limits:
@@ -248,14 +267,18 @@ int fmm_direct(int64_t n, const double* x, const double* y, const double* z,
  * a message, before any work is queued.  x, y, z, q, pot, ax, ay, az are
  * device arrays of length n in caller order (outputs overwritten).
  *
- * The first call on a device does the set-up (finds the array's device
- * address, uploads constant tables; synchronous), and a call whose (p, basis)
- * differs from the previous call's on that device rebuilds the translation
- * matrices (synchronous).  Make the first call before any stream capture.
- * Every call on a device shares the one array and overwrites what the
- * previous call left there; calls that overlap on the GPU (different streams
- * or threads without ordering between them) race and corrupt each other's
- * results.  Errors: fmm_last_error(NULL). */
+ * The first call on a device does the set-up (uploads constant tables into
+ * the array; synchronous), and a call whose (p, basis) differs from the
+ * previous call's on that device rebuilds the translation matrices and the
+ * D-tensor table held in the array (synchronous).  Make the first call
+ * before any stream capture.  A call that needs the set-up or a rebuild
+ * while its stream is being captured returns FMM_ERR_STATE and queues
+ * nothing.  The array's device address is looked up on every call, and a
+ * changed address repeats the set-up; calling cudaDeviceReset between calls
+ * is not supported.  Every call on a device shares the one array and
+ * overwrites what the previous call left there; calls that overlap on the
+ * GPU (different streams or threads without ordering between them) race and
+ * corrupt each other's results.  Errors: fmm_last_error(NULL). */
 #define FMM_NOALLOC_MAX_N 65536
 #define FMM_NOALLOC_MAX_DEPTH 3
 #define FMM_NOALLOC_MAX_P 6
@@ -292,7 +315,7 @@ int64_t fmm_kernel_launches(void);
 /* ---------------------------------------------------------------------------
  * Learned per-pair M2L order.  The paper fixes one order p per run; these
  * calls add a model that picks an order for every M2L pair of an adaptive
- * tree from 11 features of the pair, so that pairs far inside the MAC use
+ * tree from 12 features of the pair, so that pairs far inside the MAC use
  * fewer terms of Eq. M2L than pairs near its boundary.
  *
  * Features of a pair (source A, target B, d = z_B - z_A, radii r, particle
@@ -361,6 +384,13 @@ int fmm_mlp_predict(const float* blob, int64_t n, const float* feat, float* pred
 
 /* Gives a learned_p plan its model (host blob, copied).  Synchronous. */
 int fmm_set_mlp(fmm_plan* plan, const float* blob, int64_t nblob);
+
+/* The order each M2L pair of the current tree used in the last M2L (host
+ * int8, in the order of fmm_plan_pairs): the model's choice, or the orders
+ * given by fmm_set_pair_orders.  *count receives the number of pairs;
+ * nothing is written when cap is smaller.  FMM_ERR_STATE before
+ * fmm_build_tree or before an M2L of the current tree.  Synchronous. */
+int fmm_plan_pair_orders(fmm_plan* plan, int8_t* orders, int64_t cap, int64_t* count);
 
 /* Gives every M2L pair of the current tree its order (host int8, n entries
  * in the order of fmm_plan_pairs, each in 0..p) instead of the model; NULL

@@ -57,6 +57,7 @@ struct AdState {
     size_t cap_ptgt = 0, cap_nodeF = 0, cap_porder = 0, cap_iota = 0, cap_bcnt = 0, cap_boff = 0, cap_bsrc = 0,
            cap_fsum = 0, cap_nodeK = 0;
     bool orders_fixed = false;     // orders given by the caller instead of the model
+    bool orders_chosen = false;    // porder holds the model's orders for the current tree
     int64_t n_orders = 0;
     unsigned gen = 0;              // bumped whenever a buffer moves
     // autotuned persistent grid of the M2L kernel

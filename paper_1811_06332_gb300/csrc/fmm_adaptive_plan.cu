@@ -376,6 +376,7 @@ int ad_run_m2l_orders(AdState* a, int p, int basis, int prec, int sms, const uns
         ad_node_features(a, s);
         ad_far_estimate(a, s);
         mlp_orders_dev(mlp, a, thr, p, sms, err, s);
+        a->orders_chosen = true;
     }
     ad_order_keys(a->nm2l, a->porder, a->k0, a->v0, s);
     if (int r = sort_pairs(a, a->nm2l, 4, s)) return r;

@@ -112,7 +112,7 @@ static int tables_for_current(fmm_plan* pl, int* dev_out) {
 }
 
 typedef int (*pair_launch_t)(int, int, int64_t, const void*, const double*, void*, int, cudaStream_t);
-typedef int (*dten_launch_t)(int, int64_t, const double*, void*, cudaStream_t);
+typedef int (*dten_launch_t)(int, int, int64_t, const double*, void*, cudaStream_t);
 typedef int (*dtab_launch_t)(int, const double*, double*, cudaStream_t);
 static const pair_launch_t k_pair[FMM_PMAX + 1] = {
     launch_m2l_pair_p0, launch_m2l_pair_p1, launch_m2l_pair_p2, launch_m2l_pair_p3,
@@ -171,13 +171,14 @@ int fmm_plan_stats(const fmm_plan* pl, int64_t* out, int nout) {
 // ---------------------------------------------------------------------------
 // operator-level entry points
 // ---------------------------------------------------------------------------
-int fmm_op_dtensor(int p, int prec, int64_t n, const double* r, void* D, void* stream) {
+int fmm_op_dtensor(int p, int basis, int prec, int64_t n, const double* r, void* D, void* stream) {
     fmm_plan* pl = nullptr;
     if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
     if (prec != FMM_FP64 && prec != FMM_FP32) FAIL(FMM_ERR_ARG, "prec must be FMM_FP64 or FMM_FP32");
     if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
     if (n > 0 && (!r || !D)) FAIL(FMM_ERR_ARG, "null array");
-    k_dten[p](prec, n, r, D, S(stream));
+    k_dten[p](basis, prec, n, r, D, S(stream));
     if (n > 0) count_launch();
     CKLAUNCH();
     return FMM_OK;
@@ -211,43 +212,48 @@ int fmm_op_p2m(int p, int basis, int64_t ncell, const int64_t* start, const doub
     return FMM_OK;
 }
 
-int fmm_op_m2m(int p, int basis, int64_t n, const double* Mc, const double* delta, double* Mp, void* stream) {
+int fmm_op_m2m(int p, int basis, int prec, int64_t n, const void* Mc, const double* delta, void* Mp,
+               void* stream) {
     fmm_plan* pl = nullptr;
     if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
     if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (prec != FMM_FP64 && prec != FMM_FP32) FAIL(FMM_ERR_ARG, "prec must be FMM_FP64 or FMM_FP32");
     if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
     if (n > 0 && (!Mc || !delta || !Mp)) FAIL(FMM_ERR_ARG, "null array");
     if (n > 0 && Mc == Mp) FAIL(FMM_ERR_ARG, "Mc and Mp must be distinct");
     int dev;
     if (int rc = tables_for_current(pl, &dev)) return rc;
-    launch_m2m_general(p, basis, n, Mc, delta, Mp, g_tab[dev], S(stream));
+    launch_m2m_general(prec, p, basis, n, Mc, delta, Mp, g_tab[dev], S(stream));
     CKLAUNCH();
     return FMM_OK;
 }
 
-int fmm_op_l2l(int p, int basis, int64_t n, const double* Lp, const double* delta, double* Lc, void* stream) {
+int fmm_op_l2l(int p, int basis, int prec, int64_t n, const void* Lp, const double* delta, void* Lc,
+               void* stream) {
     fmm_plan* pl = nullptr;
     if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
     if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (prec != FMM_FP64 && prec != FMM_FP32) FAIL(FMM_ERR_ARG, "prec must be FMM_FP64 or FMM_FP32");
     if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
     if (n > 0 && (!Lp || !delta || !Lc)) FAIL(FMM_ERR_ARG, "null array");
     if (n > 0 && Lp == Lc) FAIL(FMM_ERR_ARG, "Lp and Lc must be distinct");
     int dev;
     if (int rc = tables_for_current(pl, &dev)) return rc;
-    launch_l2l_general(p, basis, n, Lp, delta, Lc, g_tab[dev], S(stream));
+    launch_l2l_general(prec, p, basis, n, Lp, delta, Lc, g_tab[dev], S(stream));
     CKLAUNCH();
     return FMM_OK;
 }
 
-int fmm_op_l2p(int p, int basis, int64_t n, const double* L, const double* rb, double* out, void* stream) {
+int fmm_op_l2p(int p, int basis, int prec, int64_t n, const void* L, const double* rb, void* out, void* stream) {
     fmm_plan* pl = nullptr;
     if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
     if (basis != 0 && basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", basis);
+    if (prec != FMM_FP64 && prec != FMM_FP32) FAIL(FMM_ERR_ARG, "prec must be FMM_FP64 or FMM_FP32");
     if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
     if (n > 0 && (!L || !rb || !out)) FAIL(FMM_ERR_ARG, "null array");
     int dev;
     if (int rc = tables_for_current(pl, &dev)) return rc;
-    launch_l2p_general(p, basis, n, L, rb, out, g_tab[dev], S(stream));
+    launch_l2p_general(prec, p, basis, n, L, rb, out, g_tab[dev], S(stream));
     CKLAUNCH();
     return FMM_OK;
 }
@@ -501,6 +507,7 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             if (r2 == -3) FAIL(FMM_ERR_OOM, "allocating learned-order storage failed");
             if (r2) FAIL(FMM_ERR_CUDA, "learned-order set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
             if (pl->ad->orders_fixed && pl->ad->n_orders != pl->ad->nm2l) pl->ad->orders_fixed = false;
+            pl->ad->orders_chosen = false;
         }
         pl->n = n;
         pl->built = true;
@@ -792,13 +799,21 @@ int fmm_evaluate_host(fmm_plan* pl, int64_t n, const double* x, const double* y,
                           stream);
     if (rc) return rc;
     for (int k = 0; k < 4; ++k) CK(cudaMemcpyAsync(outp[k], d + (size_t)(4 + k) * n, b, cudaMemcpyDeviceToHost, s));
+    return fmm_sync_status(pl, stream);
+}
+
+int fmm_sync_status(fmm_plan* pl, void* stream) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    cudaStream_t s = S(stream);
     CK(cudaStreamSynchronize(s));
-    if (pl->derr) {
-        int herr = 0;
-        CK(cudaMemcpy(&herr, pl->derr, sizeof(int), cudaMemcpyDeviceToHost));
-        if (herr) FAIL(FMM_ERR_TIMEOUT, "a bounded wait in the tensor-core M2L gave up (code %d)", herr);
-    }
-    return FMM_OK;
+    if (!pl->derr) return FMM_OK;
+    int herr = 0;
+    CK(cudaMemcpy(&herr, pl->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!herr) return FMM_OK;
+    // reported once: the word is cleared for the work queued after this call
+    CK(cudaMemset(pl->derr, 0, sizeof(int)));
+    FAIL(FMM_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel gave up (code %d); the outputs of the work "
+                          "queued since the previous status check are undefined", herr);
 }
 
 // ---------------------------------------------------------------------------
@@ -939,6 +954,21 @@ int fmm_set_mlp(fmm_plan* pl, const float* blob, int64_t nblob) {
     CK(cudaMemcpy(pl->mlp_dev, h.data(), MLP_DEV_BYTES, cudaMemcpyHostToDevice));
     pl->log10_kappa = blob[6];
     pl->mlp_set = true;
+    return FMM_OK;
+}
+
+int fmm_plan_pair_orders(fmm_plan* pl, int8_t* orders, int64_t cap, int64_t* count) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (!pl->cfg.learned_p || !pl->ad) FAIL(FMM_ERR_ARG, "plan was not created with learned_p");
+    if (!pl->built) FAIL(FMM_ERR_STATE, "fmm_build_tree has not been called");
+    const int64_t np = pl->ad->nm2l;
+    if (count) *count = np;
+    if (cap < np || np == 0) return FMM_OK;
+    if (!orders) FAIL(FMM_ERR_ARG, "null output array");
+    if (!pl->ad->porder || (!pl->ad->orders_fixed && !pl->ad->orders_chosen))
+        FAIL(FMM_ERR_STATE, "no M2L has chosen the orders of this tree's pairs yet");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(orders, pl->ad->porder, (size_t)np, cudaMemcpyDeviceToHost));
     return FMM_OK;
 }
 

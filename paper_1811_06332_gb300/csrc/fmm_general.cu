@@ -1,20 +1,44 @@
-// General-shift M2M, L2L, L2P (operator-level entry points) and the FP64
-// direct sum.
+// General-shift M2M, L2L, L2P (operator-level entry points, FP64 or FP32
+// storage and arithmetic) and the FP64 direct sum.
 #include "fmm_internal.h"
 
 namespace fmm {
 
+template <typename T>
+static const T* gtab(const double* d, const float* f);
+template <>
+const double* gtab<double>(const double* d, const float*) { return d; }
+template <>
+const float* gtab<float>(const double*, const float* f) { return f; }
+
+// Rebuilds the full symmetric polytensor X from independent traceless
+// components A (trace condition, App. B); lanes stride the output.
+template <typename T>
+__device__ __forceinline__ void expand_tl_warp_t(int p, const T* A, T* X, const T* expand, const DevOffsets& off,
+                                                 int lane) {
+    const int ns = ns_of(p);
+    for (int s = lane; s < ns; s += 32) {
+        const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
+        const int j = nx + ny + nz;
+        const int row = (j - nx) * (j - nx + 1) / 2 + nz;
+        const T* E = expand + off.expand[j] + row * (2 * j + 1);
+        T v = T(0);
+        for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * A[j * j + t];
+        X[s] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // General-shift M2M (Eq. M2M / M2M part 2):  Y_n = sum_{k<=n} n!/(k!(n-k)!)
 // (-delta)^{n-k} X_k, traceless: Mbar = D[Y].  Public (Mbar) format.
-// One warp per item.
+// One warp per item; T is the storage and arithmetic type.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(128)
-k_m2m_general(int p, int basis, int64_t n, const double* __restrict__ Mc, const double* __restrict__ delta,
-              double* __restrict__ Mp, const double* __restrict__ detr, const double* __restrict__ expand,
-              DevOffsets off) {
-    __shared__ double sX[4][FMM_NS_MAX], sY[4][FMM_NS_MAX], sA[4][FMM_NT_MAX];
-    __shared__ double sP[4][3][FMM_PMAX + 1];
+k_m2m_general(int p, int basis, int64_t n, const T* __restrict__ Mc, const double* __restrict__ delta,
+              T* __restrict__ Mp, const T* __restrict__ detr, const T* __restrict__ expand, DevOffsets off) {
+    __shared__ T sX[4][FMM_NS_MAX], sY[4][FMM_NS_MAX], sA[4][FMM_NT_MAX];
+    __shared__ T sP[4][3][FMM_PMAX + 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 4 + w;
     if (i >= n) return;
@@ -22,24 +46,24 @@ k_m2m_general(int p, int basis, int64_t n, const double* __restrict__ Mc, const 
     if (basis) {
         for (int t = lane; t < nc; t += 32) sA[w][t] = Mc[(int64_t)t * n + i];
         __syncwarp();
-        expand_tl_warp(p, sA[w], sX[w], expand, off, lane);
+        expand_tl_warp_t<T>(p, sA[w], sX[w], expand, off, lane);
     } else {
         for (int s = lane; s < ns; s += 32) sX[w][s] = Mc[(int64_t)s * n + i];
     }
     if (lane < 3) {
-        const double md = -delta[(int64_t)lane * n + i];
-        double v = 1.0;
-        sP[w][lane][0] = 1.0;
+        const T md = T(-delta[(int64_t)lane * n + i]);
+        T v = T(1);
+        sP[w][lane][0] = T(1);
         for (int k = 1; k <= p; ++k) { v *= md; sP[w][lane][k] = v; }
     }
     __syncwarp();
     for (int s = lane; s < ns; s += 32) {
         const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
-        double v = 0.0;
+        T v = T(0);
         for (int kx = 0; kx <= nx; ++kx)
             for (int ky = 0; ky <= ny; ++ky)
                 for (int kz = 0; kz <= nz; ++kz)
-                    v += c_binom[nx][kx] * c_binom[ny][ky] * c_binom[nz][kz] * sP[w][0][nx - kx] *
+                    v += T(c_binom[nx][kx] * c_binom[ny][ky] * c_binom[nz][kz]) * sP[w][0][nx - kx] *
                          sP[w][1][ny - ky] * sP[w][2][nz - kz] * sX[w][pos_sym(kx, ky, kz)];
         sY[w][s] = v;
     }
@@ -53,19 +77,26 @@ k_m2m_general(int p, int basis, int64_t n, const double* __restrict__ Mc, const 
         const int j = c_tl_idx[t][0] + c_tl_idx[t][1] + nz;
         const int cols = (j + 1) * (j + 2) / 2;
         const int row = (j - nx) * (j - nx + 1) / 2 + nz;
-        const double* R = detr + off.detr[j] + row * cols;
-        const double* Ys = &sY[w][ns_of(j - 1)];
-        double v = 0.0;
+        const T* R = detr + off.detr[j] + row * cols;
+        const T* Ys = &sY[w][ns_of(j - 1)];
+        T v = T(0);
         for (int s = 0; s < cols; ++s) v += R[s] * Ys[s];
         Mp[(int64_t)t * n + i] += v;
     }
 }
 
-int launch_m2m_general(int p, int basis, int64_t n, const double* Mc, const double* delta, double* Mp,
+int launch_m2m_general(int prec, int p, int basis, int64_t n, const void* Mc, const double* delta, void* Mp,
                        const DevTables& T, cudaStream_t s) {
     if (n <= 0) return 0;
-    k_m2m_general<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(p, basis, n, Mc, delta, Mp, T.detr, T.expand,
-                                                          T.offsets());
+    const unsigned g = (unsigned)((n + 3) / 4);
+    if (prec == 0)
+        k_m2m_general<double><<<g, 128, 0, s>>>(p, basis, n, (const double*)Mc, delta, (double*)Mp,
+                                                gtab<double>(T.detr, T.detr32), gtab<double>(T.expand, T.expand32),
+                                                T.offsets());
+    else
+        k_m2m_general<float><<<g, 128, 0, s>>>(p, basis, n, (const float*)Mc, delta, (float*)Mp,
+                                               gtab<float>(T.detr, T.detr32), gtab<float>(T.expand, T.expand32),
+                                               T.offsets());
     count_launch();
     return 0;
 }
@@ -73,13 +104,14 @@ int launch_m2m_general(int p, int basis, int64_t n, const double* Mc, const doub
 // ---------------------------------------------------------------------------
 // General-shift L2L (Eq. L2L): Y_n = sum_{|k|<=p-|n|} delta^k/k! X_{n+k};
 // and L2P (Eq. L2P): Phi = sum_k rb^k/k! X_k, dPhi/dx_i = sum_k rb^k/k! X_{k+e_i}.
-// One warp per item, public storage.
+// One warp per item, public storage; T is the storage and arithmetic type.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(128)
-k_l2l_general(int p, int basis, int64_t n, const double* __restrict__ Lp, const double* __restrict__ delta,
-              double* __restrict__ Lc, const double* __restrict__ expand, DevOffsets off) {
-    __shared__ double sX[4][FMM_NS_MAX], sA[4][FMM_NT_MAX];
-    __shared__ double sP[4][3][FMM_PMAX + 1];
+k_l2l_general(int p, int basis, int64_t n, const T* __restrict__ Lp, const double* __restrict__ delta,
+              T* __restrict__ Lc, const T* __restrict__ expand, DevOffsets off) {
+    __shared__ T sX[4][FMM_NS_MAX], sA[4][FMM_NT_MAX];
+    __shared__ T sP[4][3][FMM_PMAX + 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 4 + w;
     if (i >= n) return;
@@ -87,15 +119,15 @@ k_l2l_general(int p, int basis, int64_t n, const double* __restrict__ Lp, const 
     if (basis) {
         for (int t = lane; t < nc; t += 32) sA[w][t] = Lp[(int64_t)t * n + i];
         __syncwarp();
-        expand_tl_warp(p, sA[w], sX[w], expand, off, lane);
+        expand_tl_warp_t<T>(p, sA[w], sX[w], expand, off, lane);
     } else {
         for (int s = lane; s < ns; s += 32) sX[w][s] = Lp[(int64_t)s * n + i];
     }
     if (lane < 3) {
-        const double d = delta[(int64_t)lane * n + i];
-        double v = 1.0;
-        sP[w][lane][0] = 1.0;
-        for (int k = 1; k <= p; ++k) { v *= d; sP[w][lane][k] = v * c_invfact[k]; }
+        const T d = T(delta[(int64_t)lane * n + i]);
+        T v = T(1);
+        sP[w][lane][0] = T(1);
+        for (int k = 1; k <= p; ++k) { v *= d; sP[w][lane][k] = v * T(c_invfact[k]); }
     }
     __syncwarp();
     for (int o = lane; o < nc; o += 32) {
@@ -103,7 +135,7 @@ k_l2l_general(int p, int basis, int64_t n, const double* __restrict__ Lp, const 
         if (basis) { nx = c_tl_idx[o][0]; ny = c_tl_idx[o][1]; nz = c_tl_idx[o][2]; }
         else { nx = c_sym_idx[o][0]; ny = c_sym_idx[o][1]; nz = c_sym_idx[o][2]; }
         const int rem = p - nx - ny - nz;
-        double v = 0.0;
+        T v = T(0);
         for (int kx = 0; kx <= rem; ++kx)
             for (int ky = 0; ky <= rem - kx; ++ky)
                 for (int kz = 0; kz <= rem - kx - ky; ++kz)
@@ -112,19 +144,32 @@ k_l2l_general(int p, int basis, int64_t n, const double* __restrict__ Lp, const 
     }
 }
 
-int launch_l2l_general(int p, int basis, int64_t n, const double* Lp, const double* delta, double* Lc,
+int launch_l2l_general(int prec, int p, int basis, int64_t n, const void* Lp, const double* delta, void* Lc,
                        const DevTables& T, cudaStream_t s) {
     if (n <= 0) return 0;
-    k_l2l_general<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(p, basis, n, Lp, delta, Lc, T.expand, T.offsets());
+    const unsigned g = (unsigned)((n + 3) / 4);
+    if (prec == 0)
+        k_l2l_general<double><<<g, 128, 0, s>>>(p, basis, n, (const double*)Lp, delta, (double*)Lc,
+                                                gtab<double>(T.expand, T.expand32), T.offsets());
+    else
+        k_l2l_general<float><<<g, 128, 0, s>>>(p, basis, n, (const float*)Lp, delta, (float*)Lc,
+                                               gtab<float>(T.expand, T.expand32), T.offsets());
     count_launch();
     return 0;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(128)
-k_l2p_general(int p, int basis, int64_t n, const double* __restrict__ L, const double* __restrict__ rb,
-              double* __restrict__ out, const double* __restrict__ expand, DevOffsets off) {
-    __shared__ double sX[4][FMM_NS_MAX], sA[4][FMM_NT_MAX];
-    __shared__ double sP[4][3][FMM_PMAX + 1];
+k_l2p_general(int p, int basis, int64_t n, const T* __restrict__ L, const double* __restrict__ rb,
+              T* __restrict__ out, const T* __restrict__ expand, DevOffsets off) {
+    __shared__ T sX[4][FMM_NS_MAX], sA[4][FMM_NT_MAX];
+    __shared__ T sP[4][3][FMM_PMAX + 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 4 + w;
     if (i >= n) return;
@@ -132,21 +177,21 @@ k_l2p_general(int p, int basis, int64_t n, const double* __restrict__ L, const d
     if (basis) {
         for (int t = lane; t < nc; t += 32) sA[w][t] = L[(int64_t)t * n + i];
         __syncwarp();
-        expand_tl_warp(p, sA[w], sX[w], expand, off, lane);
+        expand_tl_warp_t<T>(p, sA[w], sX[w], expand, off, lane);
     } else {
         for (int s = lane; s < ns; s += 32) sX[w][s] = L[(int64_t)s * n + i];
     }
     if (lane < 3) {
-        const double d = rb[(int64_t)lane * n + i];
-        double v = 1.0;
-        sP[w][lane][0] = 1.0;
-        for (int k = 1; k <= p; ++k) { v *= d; sP[w][lane][k] = v * c_invfact[k]; }
+        const T d = T(rb[(int64_t)lane * n + i]);
+        T v = T(1);
+        sP[w][lane][0] = T(1);
+        for (int k = 1; k <= p; ++k) { v *= d; sP[w][lane][k] = v * T(c_invfact[k]); }
     }
     __syncwarp();
-    double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    T ph = T(0), gx = T(0), gy = T(0), gz = T(0);
     for (int s = lane; s < ns; s += 32) {
         const int kx = c_sym_idx[s][0], ky = c_sym_idx[s][1], kz = c_sym_idx[s][2];
-        const double wgt = sP[w][0][kx] * sP[w][1][ky] * sP[w][2][kz];
+        const T wgt = sP[w][0][kx] * sP[w][1][ky] * sP[w][2][kz];
         ph += wgt * sX[w][s];
         if (kx + ky + kz < p) {
             gx += wgt * sX[w][pos_sym(kx + 1, ky, kz)];
@@ -154,16 +199,22 @@ k_l2p_general(int p, int basis, int64_t n, const double* __restrict__ L, const d
             gz += wgt * sX[w][pos_sym(kx, ky, kz + 1)];
         }
     }
-    ph = warp_sum(ph); gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
+    ph = warp_sum_t(ph); gx = warp_sum_t(gx); gy = warp_sum_t(gy); gz = warp_sum_t(gz);
     if (lane == 0) {
         out[i] = ph; out[n + i] = gx; out[2 * n + i] = gy; out[3 * n + i] = gz;
     }
 }
 
-int launch_l2p_general(int p, int basis, int64_t n, const double* L, const double* rb, double* out,
+int launch_l2p_general(int prec, int p, int basis, int64_t n, const void* L, const double* rb, void* out,
                        const DevTables& T, cudaStream_t s) {
     if (n <= 0) return 0;
-    k_l2p_general<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(p, basis, n, L, rb, out, T.expand, T.offsets());
+    const unsigned g = (unsigned)((n + 3) / 4);
+    if (prec == 0)
+        k_l2p_general<double><<<g, 128, 0, s>>>(p, basis, n, (const double*)L, rb, (double*)out,
+                                                gtab<double>(T.expand, T.expand32), T.offsets());
+    else
+        k_l2p_general<float><<<g, 128, 0, s>>>(p, basis, n, (const float*)L, rb, (float*)out,
+                                               gtab<float>(T.expand, T.expand32), T.offsets());
     count_launch();
     return 0;
 }

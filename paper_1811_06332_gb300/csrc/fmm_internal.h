@@ -65,7 +65,7 @@ static __device__ __noinline__ void expand_tl_warp(int p, const double* A, doubl
 
 // generated per-order launchers (csrc/_gen/pair_P<p>.cu)
 #define FMM_DECL_P(P)                                                                                   \
-    int launch_dtensor_p##P(int prec, int64_t n, const double* r, void* D, cudaStream_t s);            \
+    int launch_dtensor_p##P(int basis, int prec, int64_t n, const double* r, void* D, cudaStream_t s); \
     int launch_m2l_pair_p##P(int basis, int prec, int64_t n, const void* M, const double* r, void* L, \
                              int accumulate, cudaStream_t s);                                           \
     int launch_dtable_p##P(int noff, const double* o, double* D, cudaStream_t s);
@@ -77,11 +77,12 @@ FMM_DECL_P(6) FMM_DECL_P(7) FMM_DECL_P(8) FMM_DECL_P(9) FMM_DECL_P(10)
 int launch_p2m(int p, int basis, int mode, int64_t ncell, const int64_t* start64, const int* start32,
                const double* x, const double* y, const double* z, const double* q, const double* centre,
                int depth, double inv_h, double* M, int64_t ldm, const DevTables& T, cudaStream_t s);
-int launch_m2m_general(int p, int basis, int64_t n, const double* Mc, const double* delta, double* Mp,
+// prec 0: double storage and arithmetic, 1: float
+int launch_m2m_general(int prec, int p, int basis, int64_t n, const void* Mc, const double* delta, void* Mp,
                        const DevTables& T, cudaStream_t s);
-int launch_l2l_general(int p, int basis, int64_t n, const double* Lp, const double* delta, double* Lc,
+int launch_l2l_general(int prec, int p, int basis, int64_t n, const void* Lp, const double* delta, void* Lc,
                        const DevTables& T, cudaStream_t s);
-int launch_l2p_general(int p, int basis, int64_t n, const double* L, const double* rb, double* out,
+int launch_l2p_general(int prec, int p, int basis, int64_t n, const void* L, const double* rb, void* out,
                        const DevTables& T, cudaStream_t s);
 int launch_direct(int64_t n, const double* x, const double* y, const double* z, const double* q, int64_t nt,
                   const int64_t* targets, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
@@ -91,13 +92,7 @@ int launch_l2l_level(int p, int basis, int l, const double* V, const double* Lpa
                      int64_t nch, cudaStream_t s);
 int launch_m2l_fp64_level(int p, int basis, int l, const double* Dtab, const double* Mt, double* Lt,
                           int64_t ncell, cudaStream_t s);
-int launch_l2p_leaf(int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
-                    const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& T,
-                    double* pot, double* ax, double* ay, double* az, cudaStream_t s);
 int launch_zero4(int64_t n, double* a, double* b, double* c, double* d, cudaStream_t s);
-int launch_p2p_leaf(int prec, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
-                    const double* zs, const double* qs, const int* perm, double* pot, double* ax, double* ay,
-                    double* az, cudaStream_t s);
 
 // fmm_leafops.cu (prec 0: double arithmetic, 1: float arithmetic)
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,

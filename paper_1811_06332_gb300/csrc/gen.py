@@ -304,15 +304,34 @@ def emit_pair_file(p):
     L.append("  for (int i = 0; i < %d; ++i) D[(int64_t)i * n + t] = d[i];" % ns(p))
     L.append("}")
     L.append("")
+    # traceless storage: D is trace free (harmonic), so the independent
+    # components (nz <= 1, traceless order) determine it
+    spos = {n: i for i, n in enumerate(sym_list(p))}
+    tsel = ", ".join(str(spos[n]) for n in tl_list(p))
+    L.append("template <typename T> __global__ void __launch_bounds__(128)")
+    L.append("dtensor_pair_tl_p%d(int64_t n, const double* __restrict__ r, T* __restrict__ D) {" % p)
+    L.append("  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;")
+    L.append("  if (t >= n) return;")
+    L.append("  const T x = T(r[t]), y = T(r[n + t]), z = T(r[2 * n + t]);")
+    L.append("  T d[%d];" % ns(p))
+    L.append(gen_dtensor(p))
+    L.append("  constexpr int sel[%d] = {%s};" % (len(tl_list(p)), tsel))
+    L.append("  #pragma unroll")
+    L.append("  for (int i = 0; i < %d; ++i) D[(int64_t)i * n + t] = d[sel[i]];" % len(tl_list(p)))
+    L.append("}")
+    L.append("")
     L.append("template <typename T> __device__ __forceinline__ void dtensor_p%d(T x, T y, T z, T* d) {" % p)
     L.append(gen_dtensor(p))
     L.append("}")
     L.append("")
-    L.append("int launch_dtensor_p%d(int prec, int64_t n, const double* r, void* D, cudaStream_t s) {" % p)
+    L.append("int launch_dtensor_p%d(int basis, int prec, int64_t n, const double* r, void* D, cudaStream_t s) {"
+             % p)
     L.append("  if (n <= 0) return 0;")
     L.append("  const unsigned g = (unsigned)((n + 127) / 128);")
-    L.append("  if (prec == 0) dtensor_pair_p%d<double><<<g, 128, 0, s>>>(n, r, (double*)D);" % p)
-    L.append("  else dtensor_pair_p%d<float><<<g, 128, 0, s>>>(n, r, (float*)D);" % p)
+    L.append("  if (basis == 0 && prec == 0) dtensor_pair_p%d<double><<<g, 128, 0, s>>>(n, r, (double*)D);" % p)
+    L.append("  else if (basis == 0) dtensor_pair_p%d<float><<<g, 128, 0, s>>>(n, r, (float*)D);" % p)
+    L.append("  else if (prec == 0) dtensor_pair_tl_p%d<double><<<g, 128, 0, s>>>(n, r, (double*)D);" % p)
+    L.append("  else dtensor_pair_tl_p%d<float><<<g, 128, 0, s>>>(n, r, (float*)D);" % p)
     L.append("  return 0;")
     L.append("}")
     L.append("int launch_m2l_pair_p%d(int basis, int prec, int64_t n, const void* M, const double* r, void* L,"

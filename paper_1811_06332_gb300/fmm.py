@@ -24,8 +24,9 @@ EXPORTS = [
     "fmm_m2l", "fmm_m2l_levels", "fmm_tc_layout", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate",
     "fmm_evaluate_host", "fmm_op_dtensor",
     "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
-    "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
+    "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_sync_status", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
     "fmm_mlp_grad", "fmm_mlp_train", "fmm_mlp_predict", "fmm_set_mlp", "fmm_set_pair_orders",
+    "fmm_plan_pair_orders",
 ]
 
 MLP_NF, MLP_NOUT, MLP_NBLOB = 12, 9, 9769
@@ -69,12 +70,13 @@ def lib():
             "fmm_p2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_evaluate": ([_vp, _i64] + [_vp] * 9, _int),
             "fmm_evaluate_host": ([_vp, _i64] + [_vp] * 9, _int),
-            "fmm_op_dtensor": ([_int, _int, _i64, _vp, _vp, _vp], _int),
+            "fmm_op_dtensor": ([_int, _int, _int, _i64, _vp, _vp, _vp], _int),
             "fmm_op_p2m": ([_int, _int, _i64] + [_vp] * 8, _int),
-            "fmm_op_m2m": ([_int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_op_m2m": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
             "fmm_op_m2l": ([_int, _int, _int, _i64, _vp, _vp, _vp, _int, _vp], _int),
-            "fmm_op_l2l": ([_int, _int, _i64, _vp, _vp, _vp, _vp], _int),
-            "fmm_op_l2p": ([_int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_op_l2l": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_op_l2p": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_sync_status": ([_vp, _vp], _int),
             "fmm_direct": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_kernel_launches": ([], _i64),
             "fmm_evaluate_noalloc": ([_int, _int, _int, _i64] + [_vp] * 9, _int),
@@ -86,6 +88,7 @@ def lib():
             "fmm_mlp_predict": ([_vp, _i64, _vp, _vp, _vp], _int),
             "fmm_set_mlp": ([_vp, _vp, _i64], _int),
             "fmm_set_pair_orders": ([_vp, _vp, _i64], _int),
+            "fmm_plan_pair_orders": ([_vp, _vp, _i64, _vp], _int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -132,8 +135,8 @@ def kernel_launches() -> int:
 # ---------------------------------------------------------------------------
 # operator-level calls (device tensors, physical units)
 # ---------------------------------------------------------------------------
-def fmm_op_dtensor(p, prec, r, D, stream=None):
-    _check(lib().fmm_op_dtensor(p, prec, r.shape[1], _ptr(r), _ptr(D), _stream(stream)))
+def fmm_op_dtensor(p, prec, r, D, basis=BASIS_SYM, stream=None):
+    _check(lib().fmm_op_dtensor(p, basis, prec, r.shape[1], _ptr(r), _ptr(D), _stream(stream)))
 
 
 def fmm_op_p2m(p, basis, start, x, y, z, q, centre, M, stream=None):
@@ -141,8 +144,14 @@ def fmm_op_p2m(p, basis, start, x, y, z, q, centre, M, stream=None):
                             _ptr(centre), _ptr(M), _stream(stream)))
 
 
+def _prec_of(t):
+    return FP32 if t.dtype == torch.float32 else FP64
+
+
 def fmm_op_m2m(p, basis, Mc, delta, Mp, stream=None):
-    _check(lib().fmm_op_m2m(p, basis, Mc.shape[1], _ptr(Mc), _ptr(delta), _ptr(Mp), _stream(stream)))
+    """FP64 or FP32 by the dtype of Mc (Mp must match)."""
+    _check(lib().fmm_op_m2m(p, basis, _prec_of(Mc), Mc.shape[1], _ptr(Mc), _ptr(delta), _ptr(Mp),
+                            _stream(stream)))
 
 
 def fmm_op_m2l(p, basis, prec, M, r, L, accumulate=False, stream=None):
@@ -151,11 +160,14 @@ def fmm_op_m2l(p, basis, prec, M, r, L, accumulate=False, stream=None):
 
 
 def fmm_op_l2l(p, basis, Lp, delta, Lc, stream=None):
-    _check(lib().fmm_op_l2l(p, basis, Lp.shape[1], _ptr(Lp), _ptr(delta), _ptr(Lc), _stream(stream)))
+    """FP64 or FP32 by the dtype of Lp (Lc must match)."""
+    _check(lib().fmm_op_l2l(p, basis, _prec_of(Lp), Lp.shape[1], _ptr(Lp), _ptr(delta), _ptr(Lc),
+                            _stream(stream)))
 
 
 def fmm_op_l2p(p, basis, L, rb, out, stream=None):
-    _check(lib().fmm_op_l2p(p, basis, L.shape[1], _ptr(L), _ptr(rb), _ptr(out), _stream(stream)))
+    """FP64 or FP32 by the dtype of L (out must match)."""
+    _check(lib().fmm_op_l2p(p, basis, _prec_of(L), L.shape[1], _ptr(L), _ptr(rb), _ptr(out), _stream(stream)))
 
 
 def _host_f32(blob):
@@ -270,6 +282,11 @@ class Plan:
         self._c(lib().fmm_evaluate_host(self.h, len(x), hp(x), hp(y), hp(z), hp(q), hp(pot), hp(ax), hp(ay),
                                         hp(az), _stream(stream)))
 
+    def sync_status(self, stream=None):
+        """Waits for the stream; raises FMMError (FMM_ERR_TIMEOUT) if a bounded
+        device wait of the plan's tensor-core kernels gave up since the last check."""
+        self._c(lib().fmm_sync_status(self.h, _stream(stream)))
+
     def stats(self):
         """Tree and list sizes (fmm_plan_stats); learned_p plans add the
         number of M2L pairs per order."""
@@ -307,6 +324,15 @@ class Plan:
     def set_mlp(self, blob):
         b = _host_f32(blob)
         self._c(lib().fmm_set_mlp(self.h, b.ctypes.data, len(b)))
+
+    def pair_orders(self):
+        """Order each M2L pair used in the last M2L (numpy int8, fmm_plan_pairs order)."""
+        import numpy as np
+        cnt = ctypes.c_int64(0)
+        self._c(lib().fmm_plan_pair_orders(self.h, None, 0, ctypes.byref(cnt)))
+        o = np.zeros(cnt.value, dtype=np.int8)
+        self._c(lib().fmm_plan_pair_orders(self.h, o.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return o
 
     def set_pair_orders(self, orders):
         import numpy as np

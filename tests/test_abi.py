@@ -49,7 +49,10 @@ def test_host_validation(F):
     assert L.fmm_op_m2l(4, 0, 0, 10, None, None, None, 0, None) == F.ERR_ARG
     assert L.fmm_op_m2l(4, 0, 0, -1, None, None, None, 0, None) == F.ERR_ARG
     assert b"null" in L.fmm_last_error(None) or b"n < 0" in L.fmm_last_error(None)
-    assert L.fmm_op_dtensor(4, 3, 10, None, None, None) == F.ERR_ARG
+    assert L.fmm_op_dtensor(4, 0, 3, 10, None, None, None) == F.ERR_ARG
+    assert L.fmm_op_dtensor(4, 2, 0, 10, None, None, None) == F.ERR_ARG
+    assert L.fmm_op_m2m(4, 0, 2, 10, None, None, None, None) == F.ERR_ARG
+    assert L.fmm_op_l2p(4, 0, 0, -1, None, None, None, None) == F.ERR_ARG
     assert L.fmm_direct(-1, None, None, None, None, 0, None, None, None, None, None, None) == F.ERR_ARG
     h = ctypes.c_void_p()
     assert L.fmm_create(None, ctypes.byref(h)) == F.ERR_ARG

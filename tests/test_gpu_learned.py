@@ -242,3 +242,35 @@ def test_learned_fmm_meets_target_with_fewer_terms(trained_blob):
     counts_o = np.bincount(ords_o, minlength=11)
     assert np.abs(cnt - counts_o).sum() <= 0.01 * cnt.sum()
     plan.close()
+
+
+def test_learned_orders_large_blob_set_match_oracle(trained_blob):
+    """2^20 particles of the blob mixture, FP32 learned-order plan (storage
+    order 6, the model picks each pair's order): the oracle, run on the same
+    tree with the orders the GPU used, agrees on 200 sampled targets within
+    the FP32 form's 5e-6."""
+    blob = trained_blob[0]
+    n = 1 << 20
+    x, y, z = inputs.blobs(n, 5)
+    q = inputs.masses_equal(n)
+    Xd = [_dev(a) for a in (x, y, z, q)]
+    plan = F.Plan(p=6, basis=F.BASIS_SYM, prec=F.FP32, adaptive=True, max_leaf=64, theta=0.6, learned_p=True,
+                  target_rel_err=1e-4)
+    plan.set_mlp(blob)
+    pot, acc = plan.evaluate(*Xd)
+    plan.sync_status()
+    ords = plan.pair_orders()
+    tgt_o, src_o = O.adaptive_pairs(x, y, z, q, 64, 0.6, features=False, labels=False)[:2]
+    idx = _gpu_to_oracle_index(plan, tgt_o, src_o)
+    plan.close()
+    ords_o = np.empty(len(idx), dtype=np.int8)
+    ords_o[idx] = ords
+    cnt = np.bincount(ords, minlength=7)
+    print("orders", cnt.tolist())
+    assert (cnt > 0).sum() >= 2          # the model mixes orders
+    s = np.sort(np.unique((inputs.u01(5, 98, 200) * n).astype(np.int64)))
+    pref, aref, _ = O.fmm_adaptive(x, y, z, q, 64, 0.6, 6, O.SYM, sample=s, pair_orders=ords_o)
+    p_, a_ = pot.cpu().numpy()[s], acc.cpu().numpy()[:, s]
+    ep = np.linalg.norm(p_ - pref) / np.linalg.norm(pref)
+    ea = np.linalg.norm(a_ - aref) / np.linalg.norm(aref)
+    assert ep < 5e-6 and ea < 5e-6, (ep, ea)
