@@ -42,10 +42,10 @@ L2_FLUSH_BYTES = 256 << 20
 NOMINAL = {"sm_count": 152, "fp64_fma_per_clk_sm": 2, "fp32_fma_per_clk_sm": 128}
 # DRAM bytes (read + write) of the dominant kernel per step, from one ncu
 # capture of its level-6 launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# scaled by the cells of the levels it runs on (BF16x3: the slab kernel at
-# levels 5..6, operand-split launches excluded); None for a form whose kernel
-# changed since its counters were taken.
-M2L_TRAFFIC = {"bf16x3": (792.2e6 + 156.1e6) * (294912 / 262144)}
+# scaled by the cells of the levels it runs on, with the profile summary it
+# comes from; a form is absent while its kernel has changed since its
+# counters were taken (traffic is then reported as null).
+M2L_TRAFFIC = {}
 # nominal dense tensor rates (PFLOP/s): a TF32 contraction takes the measured
 # BF16 peak scaled by their ratio
 NOMINAL_TENSOR = {"bf16": 2.25, "tf32": 1.1}
@@ -101,12 +101,76 @@ def m2l_pairs_level(l):
 
 
 def m2l_fma_per_pair(p, basis):
-    """FMAs of one M2L as the kernels execute it: symmetric -> C(p+6,6);
+    """FMAs of one M2L as the SIMT kernels execute it: symmetric -> C(p+6,6);
     traceless on the reduced representative -> sum_a (2a+1)(p-a+1)^2."""
     if basis == 0:
         from math import comb
         return comb(p + 6, 6)
     return sum((2 * a + 1) * (p - a + 1) ** 2 for a in range(p + 1))
+
+
+def m2l_alg_fma_per_pair(p, basis):
+    """Algorithmic FMAs of one M2L (Eq. M2L with independent local outputs
+    and full multipoles): symmetric C(p+6,6); traceless
+    F_tl(p) = sum_n (2n+1) C(p-n+3,3) (2079 at p = 8)."""
+    from math import comb
+    if basis == 0:
+        return comb(p + 6, 6)
+    return sum((2 * n + 1) * comb(p - n + 3, 3) for n in range(p + 1))
+
+
+def p2p_pairs_uniform(x, y, z, depth):
+    """Particle pairs of the uniform near field: every particle against the
+    particles of its own and its (up to 26) adjacent leaves, self excluded."""
+    s = 1 << depth
+    ix = [np.minimum((v * s).astype(np.int64), s - 1) for v in (x, y, z)]
+    cnt = np.zeros((s, s, s), dtype=np.int64)
+    np.add.at(cnt, (ix[2], ix[1], ix[0]), 1)
+    pad = np.pad(cnt, 1)
+    box = sum(pad[1 + a:1 + a + s, 1 + b:1 + b + s, 1 + c:1 + c + s]
+              for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1))
+    return int((cnt * box).sum() - len(x))
+
+
+P2P_FLOP_PER_PAIR = 20   # 3 differences, |r|^2 (3), 1/|r| (1), 1/|r|^3 (2), q terms (2), pot and acc sums (4), 5 adds
+
+
+def roofline_per_op(stage, form, nc, depth, n, npart_pairs, pk, mhz, fp_peak, alg_m2l_flop, tc_roof):
+    """Roofline of each operator of the step.  HBM-bound operators take
+    their algorithmic bytes (the inputs and outputs they must move in the
+    library's storage formats, each once); P2P takes its FP32 (FP64) ALU
+    work; M2L the tensor (ALU) work."""
+    hbm = pk.get("hbm_gbs", 6800.0)
+    leaves = 8 ** depth
+    cells = lambda l: 8 ** l   # noqa: E731
+    es = 8
+    pos = 16 if form != "fp64" else 32        # float4 leaf-relative positions (FP32 forms) or x, y, z, q doubles
+    out = {}
+
+    def hb(name, bytes_, ms, what):
+        ach = bytes_ / (ms * 1e-3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "ms": ms, "algorithmic_bytes": bytes_, "bytes_are": what}
+    hb("p2m", n * pos + leaves * (4 + nc * es), stage["p2m"],
+       "particles in, leaf ranges, leaf multipoles out (FP64)")
+    m2m_b = sum(cells(l + 1) * nc * es + cells(l) * nc * es for l in range(2, depth))
+    hb("m2m", m2m_b, stage["m2m"], "child multipoles in, parent multipoles out, levels 6 -> 2")
+    l2l_b = sum(cells(l) * nc * es + 2 * cells(l + 1) * nc * es for l in range(2, depth))
+    hb("l2l", l2l_b, stage["l2l"], "parent locals in, child locals read and written, levels 2 -> 6")
+    hb("l2p", leaves * nc * es + n * (pos + 4 + 4 * 8), stage["l2p"],
+       "leaf locals in, particles and permutation in, pot and acc out (FP64)")
+    p2p_flop = npart_pairs * P2P_FLOP_PER_PAIR
+    ach = p2p_flop / (stage["p2p"] * 1e-3) / 1e12
+    out["p2p"] = {"bound": "alu", "achieved": ach, "peak": fp_peak, "unit": "TFLOP/s", "frac": ach / fp_peak,
+                  "ms": stage["p2p"], "pairs": npart_pairs, "flop_per_pair": P2P_FLOP_PER_PAIR,
+                  "pairs_per_s": npart_pairs / (stage["p2p"] * 1e-3)}
+    m2l_ms = stage["m2l_2_4"] + stage["m2l_5_6"]
+    ach = alg_m2l_flop / (m2l_ms * 1e-3) / 1e12
+    out["m2l"] = {"bound": "alu" if tc_roof is None else "tensor", "achieved": ach,
+                  "peak": fp_peak if tc_roof is None else tc_roof, "unit": "TFLOP/s",
+                  "frac": ach / (fp_peak if tc_roof is None else tc_roof), "ms": m2l_ms,
+                  "levels": "2..%d" % depth}
+    return out
 
 
 class Clocks:
@@ -273,6 +337,7 @@ def run_gpu(args):
     npairs = m2l_pairs_uniform(DEPTH)
     tc_pairs = sum(m2l_pairs_level(l) for l in range(TC_LEVEL, DEPTH + 1))
     fma = m2l_fma_per_pair(P, BASIS)
+    afma = m2l_alg_fma_per_pair(P, BASIS)
     pk, pk_kind = peaks()
     mhz = pk.get("sm_max_mhz", 2070.0)
     tc = None
@@ -295,50 +360,72 @@ def run_gpu(args):
     else:
         peak = NOMINAL["sm_count"] * NOMINAL["fp32_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
         peak_note = "FP32 ALU: 152 SMs x 128 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
-    achieved = npairs * fma * 2 / (m2l_ms * 1e-3) / 1e12
+    traffic, traffic_src = M2L_TRAFFIC.get(form, (None, "no capture of the current kernel"))
+    achieved = npairs * afma * 2 / (m2l_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "m2l (levels 2..6, %d pairs per step)" % npairs,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": M2L_TRAFFIC.get(form), "peak_source": peak_note, "flops_per_pair": 2 * fma,
-            "m2l_ms_per_step": m2l_ms}
+            "traffic": traffic, "traffic_source": traffic_src, "peak_source": peak_note,
+            "flops_per_pair": 2 * afma,
+            "flops_per_pair_is": "algorithmic, Eq. M2L with full multipoles (F_tl(8) = 2079 FMA)",
+            "executed_flops_per_pair": 2 * fma, "m2l_ms_per_step": m2l_ms}
     if tc is not None:
         bf = pk.get("bf16_tflops", 1900.0)
         src = "bf16_tflops of MEASURED_PEAKS.json (%s, burst)" % pk_kind
         if prec == F.GEMM_TF32X3:
             bf *= NOMINAL_TENSOR["tf32"] / NOMINAL_TENSOR["bf16"]
             src += " x nominal TF32/BF16 ratio 1.1/2.25"
-        # algorithmic work of the split-precision form: 3 products (hi.hi,
-        # hi.lo, lo.hi) of every nonzero matrix entry per pair; the executed
-        # work adds the padding of the dense MMA tiles
-        alg = tc_pairs * 3 * 2 * fma
+        # algorithmic work: Eq. M2L with independent local outputs and full
+        # multipoles, 2 F_tl(p) flop per pair (the method's work, one
+        # product); the executed work adds the three split-precision
+        # products and the padding of the dense MMA tiles
+        alg = tc_pairs * 2 * afma
         ach = alg / (tc_ms * 1e-3) / 1e12
         ex = tc["executed_flop_per_step"] / (tc_ms * 1e-3) / 1e12
         roof = {"bound": "tensor",
                 "kernel": "tensor-core M2L, levels %d..%d (%d pairs; operand split included)" % (TC_LEVEL, DEPTH,
                                                                                                tc_pairs),
-                "achieved": ach, "peak": bf, "unit": "TFLOP/s", "frac": ach / bf, "traffic": M2L_TRAFFIC.get(form),
-                "peak_source": src, "kernel_ms_per_step": tc_ms,
+                "achieved": ach, "peak": bf, "unit": "TFLOP/s", "frac": ach / bf, "traffic": traffic,
+                "traffic_source": traffic_src, "peak_source": src, "kernel_ms_per_step": tc_ms,
+                "flops_per_pair": 2 * afma,
+                "flops_per_pair_is": "algorithmic, Eq. M2L with full multipoles (F_tl(8) = 2079 FMA)",
                 "algorithmic_flop_per_step": alg, "executed_flop_per_step": tc["executed_flop_per_step"],
                 "executed_tflops": ex, "executed_frac": ex / bf,
+                "split_product_tflops": 3 * tc_pairs * 2 * fma / (tc_ms * 1e-3) / 1e12,
                 "m2l_all_levels_ms_per_step": m2l_ms}
+
+    stage_mean = {st: float(per_stage[:, i].mean()) for i, st in enumerate(stages)}
+    per_op = roofline_per_op(stage_mean, form, (P + 1) ** 2, DEPTH, N_PART, p2p_pairs_uniform(x, y, z, DEPTH), pk,
+                             mhz, peak if prec == F.FP64 else
+                             NOMINAL["sm_count"] * NOMINAL["fp32_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12,
+                             npairs * 2 * afma, roof["peak"] if tc is not None else None)
 
     # plain FP64 GPU form beside it (same workload, fewer steps)
     fp64 = None
     if prec != F.FP64 and not args.no_fp64:
         p64 = F.Plan(p=P, basis=BASIS, prec=F.FP64, depth=DEPTH)
-        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         p64.fmm_evaluate(*X, out[0], out[1], out[2], out[3])
-        flush.fill_(2.0)
-        e0.record(stream)
-        p64.fmm_build_tree(*X); p64.fmm_p2m(); p64.fmm_m2m()
-        e1.record(stream)
-        p64.fmm_m2l()
-        e2.record(stream)
-        p64.fmm_l2l(); p64.fmm_l2p(out[0], out[1], out[2], out[3]); p64.fmm_p2p(out[0], out[1], out[2], out[3])
-        e3.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e3)
-        fp64 = {"value": N_PART / (ms * 1e-3), "m2l_pairs_per_s": npairs / (e1.elapsed_time(e2) * 1e-3),
-                "ms_per_step": ms}
+        tot, m2l64 = [], []
+        for k in range(args.fp64_steps):
+            e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+            flush.fill_(2.0 + k)
+            e0.record(stream)
+            p64.fmm_build_tree(*X); p64.fmm_p2m(); p64.fmm_m2m()
+            e1.record(stream)
+            p64.fmm_m2l()
+            e2.record(stream)
+            p64.fmm_l2l(); p64.fmm_l2p(out[0], out[1], out[2], out[3]); p64.fmm_p2p(out[0], out[1], out[2], out[3])
+            e3.record(stream)
+            torch.cuda.synchronize()
+            tot.append(e0.elapsed_time(e3))
+            m2l64.append(e1.elapsed_time(e2))
+        ms, mm = float(np.mean(tot)), float(np.mean(m2l64))
+        pk64 = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
+        a64 = npairs * 2 * afma / (mm * 1e-3) / 1e12
+        fp64 = {"value": N_PART / (ms * 1e-3), "m2l_pairs_per_s": npairs / (mm * 1e-3), "ms_per_step": ms,
+                "steps": len(tot), "m2l_ms": mm,
+                "m2l_roofline": {"bound": "alu", "achieved": a64, "peak": pk64, "unit": "TFLOP/s",
+                                 "frac": a64 / pk64, "executed_frac": npairs * 2 * fma / (mm * 1e-3) / 1e12 / pk64,
+                                 "peak_source": "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz" % mhz}}
         p64.close()
     else:
         fp64 = {"value": value / world, "m2l_pairs_per_s": npairs / (m2l_ms * 1e-3), "ms_per_step": t_ms}
@@ -380,6 +467,7 @@ def run_gpu(args):
         "fp64_form": fp64,
         "vs_fp64_form": value / world / fp64["value"],
         "roofline": roof,
+        "roofline_per_op": per_op,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -655,6 +743,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.workload == "fmm":
         args.warmup = 3
