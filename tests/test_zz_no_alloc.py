@@ -63,6 +63,12 @@ def test_noalloc_matches_fmm_evaluate_twice_in_a_row(F):
     # fmm_evaluate; a call that changes (p, basis) rebuilds the matrices in
     # the fixed array and must leave the device's free memory unchanged
     cases = [(4, 0, 3, 4096, 1), (6, 1, 3, 20000, 2), (3, 1, 2, 3000, 3), (5, 0, 1, 777, 4)]
+    # The first call in a process may load the library's device module that
+    # holds the fixed array (lazy module loading), which takes the array's
+    # own memory; every call after it must allocate nothing.
+    w = _inputs(64, 30)
+    assert _noalloc(F, 2, 1, 1, w, torch.zeros((4, 64), dtype=torch.float64, device=DEV)) == F.OK
+    torch.cuda.synchronize()
     for p, basis, depth, n, seed in cases:
         X = _inputs(n, seed)
         pot, acc = _reference(F, p, basis, depth, X)
