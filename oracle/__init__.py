@@ -98,6 +98,11 @@ def lib():
         L.orc_adaptive_tree.restype = ctypes.c_int64
         L.orc_ncols_labels.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_p2m_dipole.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64] + [_dp] * 8
+        L.orc_direct_dipole.argtypes = [ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int64, _i64p] + [_dp] * 4
+        L.orc_fmm_uniform_dipole.argtypes = [ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int] * 3 + \
+            [ctypes.c_int64, _i64p] + [_dp] * 4
+        L.orc_fmm_uniform_dipole.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -170,6 +175,48 @@ def p2m(p: int, basis: int, x, y, z, q, zc) -> np.ndarray:
     out = np.zeros(ncoef(p, basis))
     lib().orc_p2m(p, basis, len(x), _d(x), _d(y), _d(z), _d(q), _d(zc), _d(out))
     return out
+
+
+def p2m_dipole(p: int, basis: int, x, y, z, px, py, pz, zc) -> np.ndarray:
+    """Multipole of point dipoles (App. B): the pure dipole M_{e_i} = -p_i
+    of each, shifted by M2M from x_a to zc."""
+    x, y, z, px, py, pz, zc = (_f64(v) for v in (x, y, z, px, py, pz, zc))
+    out = np.zeros(ncoef(p, basis))
+    lib().orc_p2m_dipole(p, basis, len(x), _d(x), _d(y), _d(z), _d(px), _d(py), _d(pz), _d(zc), _d(out))
+    return out
+
+
+def direct_dipole(x, y, z, q, px, py, pz, targets=None):
+    """O(N^2) FP64 sum over charges and point dipoles: pot = -Phi,
+    acc = grad Phi (Phi the paper's positive potential)."""
+    x, y, z, q, px, py, pz = (_f64(v) for v in (x, y, z, q, px, py, pz))
+    n = len(x)
+    if targets is None:
+        nt, tp = n, None
+    else:
+        targets = np.ascontiguousarray(targets, dtype=np.int64)
+        nt, tp = len(targets), targets.ctypes.data_as(_i64p)
+    pot, ax, ay, az = (np.zeros(nt) for _ in range(4))
+    lib().orc_direct_dipole(n, _d(x), _d(y), _d(z), _d(q), _d(px), _d(py), _d(pz), nt, tp, _d(pot), _d(ax),
+                            _d(ay), _d(az))
+    return pot, np.stack([ax, ay, az])
+
+
+def fmm_uniform_dipole(x, y, z, q, px, py, pz, depth: int, p: int, basis: int, sample=None):
+    """Uniform-octree FMM with point dipoles beside the charges."""
+    x, y, z, q, px, py, pz = (_f64(v) for v in (x, y, z, q, px, py, pz))
+    n = len(x)
+    if sample is None:
+        ns, sp, nout = -1, None, n
+    else:
+        sample = np.ascontiguousarray(sample, dtype=np.int64)
+        ns, sp, nout = len(sample), sample.ctypes.data_as(_i64p), len(sample)
+    pot, ax, ay, az = (np.zeros(nout) for _ in range(4))
+    rc = lib().orc_fmm_uniform_dipole(n, _d(x), _d(y), _d(z), _d(q), _d(px), _d(py), _d(pz), depth, p, basis,
+                                      ns, sp, _d(pot), _d(ax), _d(ay), _d(az))
+    if rc != 0:
+        raise ValueError("orc_fmm_uniform_dipole rejected its arguments")
+    return pot, np.stack([ax, ay, az])
 
 
 def m2m(p: int, basis: int, M: np.ndarray, delta) -> np.ndarray:

@@ -444,6 +444,65 @@ void orc_direct(int64_t n, const double* x, const double* y, const double* z,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Point dipoles (App. B, "Dipoles and higher order multipoles").  A point   */
+/* dipole p at x_a is read as the limit of charges +q at x_a + s and -q at    */
+/* x_a - s with p = 2 q s.  About x_a its multipole (Eq. P2M, M_n =           */
+/* sum q (-r_a)^n) is the pure dipole M_{e_i} = -p_i, every other component  */
+/* zero; P2M of dipoles shifts that pure dipole to the expansion centre with */
+/* M2M (Eq. M2M), delta = x_a - z_A (child: the dipole's own centre).  A      */
+/* rank-1 tensor is traceless, so the traceless shift applies as it is.      */
+/* Added into M.                                                             */
+/* ------------------------------------------------------------------------ */
+void orc_p2m_dipole(int p, int basis, int64_t na, const double* x, const double* y, const double* z,
+                    const double* px, const double* py, const double* pz, const double zc[3], double* M) {
+    orc_init();
+    int nc = orc_ncoef(p, basis);
+    double Md[NS_MAX];
+    for (int64_t a = 0; a < na; ++a) {
+        for (int i = 0; i < nc; ++i) Md[i] = 0.0;
+        if (p >= 1) {
+            const double pv[3] = {px[a], py[a], pz[a]};
+            for (int d = 0; d < 3; ++d) {
+                const int e[3] = {d == 0, d == 1, d == 2};
+                const int pos = basis ? g_pos_tl[e[0]][e[1]][e[2]] : g_pos_sym[e[0]][e[1]][e[2]];
+                Md[pos] = -pv[d];
+            }
+        }
+        const double delta[3] = {x[a] - zc[0], y[a] - zc[1], z[a] - zc[2]};
+        orc_m2m(p, basis, Md, delta, M);
+    }
+}
+
+/* Potential and gradient of sources with charges q and dipoles (px, py, pz) */
+/* at x_i (the paper's positive Phi): a charge adds q/|d|, a dipole          */
+/* p.d/|d|^3, d = x_i - x_j; gradients -q d/|d|^3 and p/|d|^3 -             */
+/* 3 (p.d) d/|d|^5.  Output sign convention as orc_direct: pot = -Phi,       */
+/* acc = grad Phi.  targets == NULL: every particle.                         */
+void orc_direct_dipole(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                       const double* px, const double* py, const double* pz, int64_t nt, const int64_t* targets,
+                       double* pot, double* ax, double* ay, double* az) {
+    int64_t cnt = targets ? nt : n;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < cnt; ++t) {
+        int64_t i = targets ? targets[t] : t;
+        double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3] = {x[i] - x[j], y[i] - y[j], z[i] - z[j]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir, ir5 = ir3 * ir * ir;
+            double pd = px[j] * d[0] + py[j] * d[1] + pz[j] * d[2];
+            ph += q[j] * ir + pd * ir3;
+            gx += -q[j] * d[0] * ir3 + px[j] * ir3 - 3.0 * pd * d[0] * ir5;
+            gy += -q[j] * d[1] * ir3 + py[j] * ir3 - 3.0 * pd * d[1] * ir5;
+            gz += -q[j] * d[2] * ir3 + pz[j] * ir3 - 3.0 * pd * d[2] * ir5;
+        }
+        pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Uniform-octree FMM (App. C, with the octree and "standard" separation     */
 /* criterion of the uniform workloads): leaves at level `depth` of the unit   */
 /* cube [0,1)^3, leaf of a particle i_d = min(floor(x_d 2^depth), 2^depth-1).  */
@@ -483,10 +542,10 @@ static int leaf_coord(double v, int side) {
     return i;
 }
 
-int orc_fmm_uniform(int64_t n, const double* x, const double* y, const double* z,
-                    const double* q, int depth, int p, int basis, int64_t nsample,
-                    const int64_t* sample, double* pot, double* ax, double* ay,
-                    double* az) {
+static int fmm_uniform_impl(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                            const double* px, const double* py, const double* pz, int depth, int p, int basis,
+                            int64_t nsample, const int64_t* sample, double* pot, double* ax, double* ay,
+                            double* az) {
     orc_init();
     if (p < 0 || p > ORC_PMAX || depth < 0 || depth > 10) return -1;
     int side = 1 << depth;
@@ -551,6 +610,16 @@ int orc_fmm_uniform(int64_t n, const double* x, const double* y, const double* z
             buf[a] = x[i]; buf[cnt + a] = y[i]; buf[2 * cnt + a] = z[i]; buf[3 * cnt + a] = q[i];
         }
         orc_p2m(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, buf + 3 * cnt, zc, U.M[depth] + c * nc);
+        if (px) {
+            double* pb = (double*)malloc(sizeof(double) * 3 * cnt);
+            for (int64_t a = 0; a < cnt; ++a) {
+                int64_t i = U.order[b + a];
+                pb[a] = px[i]; pb[cnt + a] = py[i]; pb[2 * cnt + a] = pz[i];
+            }
+            orc_p2m_dipole(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, pb, pb + cnt, pb + 2 * cnt, zc,
+                           U.M[depth] + c * nc);
+            free(pb);
+        }
         free(buf);
     }
     for (int l = depth - 1; l >= 0; --l) {
@@ -636,6 +705,14 @@ int orc_fmm_uniform(int64_t n, const double* x, const double* y, const double* z
                         double ir = 1.0 / sqrt(r2), ir3 = ir * ir * ir;
                         ph += q[j] * ir;
                         gx += q[j] * dx * ir3; gy += q[j] * dy * ir3; gz += q[j] * dz * ir3;
+                        if (px) {   /* dipole source; d = x_i - x_j = -(dx, dy, dz) */
+                            double ir5 = ir3 * ir * ir;
+                            double pd = -(px[j] * dx + py[j] * dy + pz[j] * dz);
+                            ph += pd * ir3;
+                            gx += px[j] * ir3 + 3.0 * pd * dx * ir5;
+                            gy += py[j] * ir3 + 3.0 * pd * dy * ir5;
+                            gz += pz[j] * ir3 + 3.0 * pd * dz * ir5;
+                        }
                     }
                 }
         pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
@@ -645,6 +722,23 @@ int orc_fmm_uniform(int64_t n, const double* x, const double* y, const double* z
     free(U.M); free(U.L); free(need);
     free(leaf); free(U.leaf_start); free(U.order);
     return 0;
+}
+
+int orc_fmm_uniform(int64_t n, const double* x, const double* y, const double* z,
+                    const double* q, int depth, int p, int basis, int64_t nsample,
+                    const int64_t* sample, double* pot, double* ax, double* ay,
+                    double* az) {
+    return fmm_uniform_impl(n, x, y, z, q, NULL, NULL, NULL, depth, p, basis, nsample, sample, pot, ax, ay, az);
+}
+
+/* The uniform FMM with point dipoles (px, py, pz) beside the charges q:    */
+/* P2M adds the shifted pure dipoles (orc_p2m_dipole), the near field adds  */
+/* the dipole terms of orc_direct_dipole; the other operators are the same. */
+int orc_fmm_uniform_dipole(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                           const double* px, const double* py, const double* pz, int depth, int p, int basis,
+                           int64_t nsample, const int64_t* sample, double* pot, double* ax, double* ay,
+                           double* az) {
+    return fmm_uniform_impl(n, x, y, z, q, px, py, pz, depth, p, basis, nsample, sample, pot, ax, ay, az);
 }
 
 int orc_num_threads(void) {
