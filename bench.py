@@ -280,7 +280,8 @@ def run_gpu(args):
     out = torch.empty((4, N_PART), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    plan = F.Plan(p=P, basis=BASIS, prec=prec, depth=DEPTH)
+    tc_form = prec in (F.GEMM_BF16X3, F.GEMM_TF32X3)
+    plan = F.Plan(p=P, basis=BASIS, prec=prec, depth=DEPTH, autotune=tc_form)
 
     # M2L runs as two calls, levels 2..4 and 5..6 (the tensor-core levels of
     # the tensor-core forms), so that the dominant kernel is timed on its own
@@ -347,13 +348,16 @@ def run_gpu(args):
         # chunk j (lowest rank a_j) over the (p - a_j + 1)^2 multipole columns
         # it needs, rounded up to K-steps of 16 (BF16) or 8 (TF32) columns
         # (the kernel's chunk rule)
-        cw = int(os.environ.get("FMM_TC_CHUNK", "48" if prec == F.GEMM_BF16X3 else "32"))
+        tuning = plan.tuning()
+        cw = tuning["cw"]
         ks = 16 if prec == F.GEMM_BF16X3 else 8
         nc = (P + 1) ** 2
         rk = [a for a in range(P + 1) for _ in range(2 * a + 1)]   # rank of each traceless component
         cols = sum(cw * ks * (((P - rk[r0] + 1) ** 2 + ks - 1) // ks) for r0 in range(0, nc, cw))
         tiles = sum(8 ** (l - 1) // 128 * 8 for l in range(5, DEPTH + 1))
-        tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * cols}
+        # both kernels execute 3 cw columns per K-step and chunk (3 MMAs of N = cw, or the
+        # stacked hi/lo MMA of N = 2 cw and the lo.hi MMA of N = cw)
+        tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * cols, "shape": tuning}
     if prec == F.FP64:
         peak = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
         peak_note = "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
@@ -391,6 +395,7 @@ def run_gpu(args):
                 "algorithmic_flop_per_step": alg, "executed_flop_per_step": tc["executed_flop_per_step"],
                 "executed_tflops": ex, "executed_frac": ex / bf,
                 "split_product_tflops": 3 * tc_pairs * 2 * fma / (tc_ms * 1e-3) / 1e12,
+                "kernel_shape": tc["shape"],
                 "m2l_all_levels_ms_per_step": m2l_ms}
 
     stage_mean = {st: float(per_stage[:, i].mean()) for i, st in enumerate(stages)}
@@ -423,8 +428,12 @@ def run_gpu(args):
         a64 = npairs * 2 * afma / (mm * 1e-3) / 1e12
         fp64 = {"value": N_PART / (ms * 1e-3), "m2l_pairs_per_s": npairs / (mm * 1e-3), "ms_per_step": ms,
                 "steps": len(tot), "m2l_ms": mm,
-                "m2l_roofline": {"bound": "alu", "achieved": a64, "peak": pk64, "unit": "TFLOP/s",
-                                 "frac": a64 / pk64, "executed_frac": npairs * 2 * fma / (mm * 1e-3) / 1e12 / pk64,
+                "m2l_roofline": {"bound": "alu", "achieved": npairs * 2 * fma / (mm * 1e-3) / 1e12, "peak": pk64,
+                                 "unit": "TFLOP/s", "frac": npairs * 2 * fma / (mm * 1e-3) / 1e12 / pk64,
+                                 "flops_per_pair": 2 * fma,
+                                 "flops_per_pair_is": "executed: the reduced traceless representative, "
+                                                      "sum_a (2a+1)(p-a+1)^2 = 1365 FMA at p = 8",
+                                 "frac_of_F_tl_count": a64 / pk64,
                                  "peak_source": "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz" % mhz}}
         p64.close()
     else:

@@ -97,6 +97,14 @@ typedef struct {
                               evaluation, capture the operator sequence P2M..P2P into
                               a CUDA graph and replay it while the tree keeps its
                               sizes and buffers                                        */
+    int autotune;          /* tensor-core forms: 1 takes the kernel shape stored for
+                              this GPU, p, basis, form and depth in the tuning cache
+                              (the JSON file FMM_TUNE_CACHE, else
+                              $XDG_CACHE_HOME/fmm_gb300/tune.json, else
+                              $HOME/.cache/fmm_gb300/tune.json); without an entry,
+                              the first M2L that reaches a tensor-core level times
+                              every candidate shape on the deepest level, keeps the
+                              fastest and stores it.  0: the default shape          */
 } fmm_config;
 
 typedef struct fmm_plan fmm_plan;
@@ -171,6 +179,21 @@ int fmm_p2p(fmm_plan* plan, double* pot, double* ax, double* ay, double* az, voi
 int fmm_evaluate(fmm_plan* plan, int64_t n, const double* x, const double* y,
                  const double* z, const double* q, double* pot, double* ax,
                  double* ay, double* az, void* stream);
+
+/* fmm_evaluate with point dipoles (App. B, "Dipoles and higher order
+ * multipoles") beside the charges: particle i carries the charge q[i] and
+ * the dipole moment (px[i], py[i], pz[i]) (device arrays, caller order; use
+ * zeros for either).  A point dipole p at x_a acts as the limit of charges
+ * +q at x_a + s and -q at x_a - s with p = 2 q s: P2M adds the pure dipole
+ * M_{e_i} = -p_i shifted by M2M from x_a to the leaf centre, the near field
+ * adds the dipole field (potential p.d/|d|^3, d = x - x_a), and M2M, M2L,
+ * L2L, L2P are unchanged.  Outputs as fmm_evaluate (pot = -Phi, acc =
+ * grad Phi).  Uniform plans in FMM_FP64 (either basis); others return
+ * FMM_ERR_UNSUPPORTED. */
+int fmm_evaluate_dipoles(fmm_plan* plan, int64_t n, const double* x, const double* y,
+                         const double* z, const double* q, const double* px, const double* py,
+                         const double* pz, double* pot, double* ax, double* ay, double* az,
+                         void* stream);
 
 /* fmm_evaluate on HOST arrays (length n, caller order): copies the inputs to
  * the device, evaluates, copies the outputs back and waits for the stream;
@@ -282,7 +305,7 @@ int fmm_direct(int64_t n, const double* x, const double* y, const double* z,
 #define FMM_NOALLOC_MAX_N 65536
 #define FMM_NOALLOC_MAX_DEPTH 3
 #define FMM_NOALLOC_MAX_P 6
-#define FMM_NOALLOC_BYTES_APPROX 5300000
+#define FMM_NOALLOC_BYTES_APPROX 7540000
 int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, const double* x, const double* y,
                          const double* z, const double* q, double* pot, double* ax, double* ay,
                          double* az, void* stream);
@@ -295,9 +318,10 @@ int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, const double* x
  * uniform trees the list entries are 0 (the lists are implicit). */
 int fmm_plan_stats(const fmm_plan* plan, int64_t* out, int nout);
 
-/* Host-side layout of the tensor-core M2L kernel (no GPU needed; for
- * diagnostics and tests) for order p (1..8, traceless) and prec
- * FMM_GEMM_BF16X3 or FMM_GEMM_TF32X3, written to out[0..min(nout,42)):
+/* Host-side layout of the TF32 form's tensor-core M2L kernel, the one that
+ * streams each offset's precomputed matrix (no GPU needed; for diagnostics
+ * and tests), for order p (1..8, traceless) and prec FMM_GEMM_TF32X3,
+ * written to out[0..min(nout,42)):
  * N-chunk width cw, chunks nch, K-parts per offset np, matrix stages nbst,
  * MMA-issuing warps niss, bytes of a matrix stage, bytes of one offset's
  * packed matrix, dynamic shared bytes per CTA, then K-steps per chunk
@@ -307,6 +331,47 @@ int fmm_plan_stats(const fmm_plan* plan, int64_t* out, int nout);
  * FMM_TC_CHUNK environment variable as the kernel does.  Returns the count
  * written, or FMM_ERR_ARG. */
 int fmm_tc_layout(int p, int prec, int* out, int nout);
+
+/* Host-side layout of the BF16 form's tensor-core M2L kernel, which builds
+ * each offset's matrix B_o(n, m) = D_{n+m}(-o) in shared memory from the
+ * offset's D vector (no GPU needed; for diagnostics and tests), for order p
+ * (1..8), chunk width cw (16, 32, 48 or 96 local rows; the hi and lo rows of
+ * a chunk are stacked into one MMA of N = 2 cw) and niss (1 or 2)
+ * MMA-issuing warps, written to out[0..min(nout,19)): cw, chunks nch, bytes
+ * of a matrix stage, stages nb, niss, nonzero 16-byte groups of a matrix
+ * ngroups, dynamic shared bytes per CTA, K-steps per chunk kch[6], byte
+ * offsets of the chunks in a stage coff[6].  When gcap > 0, groups receives
+ * up to gcap words of the group table, 4 per group: the symmetric storage
+ * positions of n + m for its 8 multipole columns m (one byte each, 255 where
+ * |n| + |m| > p), then the byte offsets of its hi and lo 16 bytes in a
+ * stage.  Returns the count written to out, or FMM_ERR_ARG. */
+int fmm_tc_gen_layout(int p, int cw, int niss, int* out, int nout, uint32_t* groups, int gcap);
+
+/* Kernel shape of a tensor-core plan's M2L (Eq. M2L regrouped by offset).
+ * kernel 0: each offset's matrix precomputed in global memory and streamed
+ * into shared memory (BF16 or TF32 operands); kernel 1: each offset's matrix
+ * built in shared memory from the offset's D vector (BF16 operands only).
+ * cw: chunk width, the local components per MMA (16, 32, 48 or 96).
+ * fmm_set_tc_shape fixes the shape (rebuilding the plan's offset tables;
+ * synchronous); FMM_ERR_ARG for a shape the plan's form has not.
+ * fmm_plan_tuning writes to out[0..min(nout, 5 + 4 ncand)): kernel, cw,
+ * MMA-issuing warps, how the shape was chosen (0 default, 1 autotuned in
+ * this plan, 2 read from the tuning cache, 3 set by fmm_set_tc_shape),
+ * ncand, then per autotuner candidate kernel, cw, issuing warps and its
+ * time on the deepest level in microseconds.  Returns the count written. */
+int fmm_set_tc_shape(fmm_plan* plan, int kernel, int cw);
+int fmm_plan_tuning(const fmm_plan* plan, int* out, int nout);
+
+/* The tuning cache itself (host only; for tools and tests): a JSON object
+ * {"<key>": {"kernel": k, "cw": c, "niss": n, "ms": t}, ...} in the file
+ * `path`.  fmm_tune_cache_get writes vals[0..3) = {kernel, cw, niss} of
+ * `key` and returns 1, or returns 0 when the file or the entry is missing
+ * or malformed.  fmm_tune_cache_put stores vals[0..3) and ms under `key`
+ * (replacing an earlier entry, creating the file's directories) and returns
+ * FMM_OK, or FMM_ERR_STATE when the file cannot be written.  A plan's key
+ * is "<GPU name>|p=<p>|basis=<basis>|prec=<prec>|depth=<depth>". */
+int fmm_tune_cache_get(const char* path, const char* key, int* vals);
+int fmm_tune_cache_put(const char* path, const char* key, const int* vals, double ms);
 
 /* Number of kernels this library launched since it was loaded (all plans and
  * operator calls), counted on the host at each launch. */

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -47,10 +48,16 @@ struct fmm_plan {
     double* V = nullptr;     // 8 x nc x nc  (L2L)
     double* Dtab = nullptr;  // 343 x ns     (M2L, integer offsets in cell units)
     float* K32 = nullptr;    // 343 x kstride packed FP32 M2L matrices (FMM_FP32)
+    double* K64 = nullptr;   // 343 x kstride packed FP64 M2L matrices (FMM_FP64)
     float* M32 = nullptr;    // FP32 copy of the multipoles (FMM_FP32)
     int kst = 0;
     // tensor-core forms (FMM_GEMM_BF16X3, FMM_GEMM_TF32X3)
-    void* Kbf = nullptr;                 // 343 x {hi, lo} preformatted matrices
+    void* Kbf = nullptr;                 // 343 x {hi, lo} preformatted matrices (streamed-matrix kernel)
+    void* Kgen = nullptr;                // BF16: group table + FP32 D vectors (on-chip-matrix kernel)
+    int tc_kern = 0, tc_cw = 48, tc_niss = 4;   // kernel shape in use
+    int tc_source = 0;                   // 0 default, 1 autotuned, 2 from the cache, 3 set by the caller
+    int tc_ncand = 0;
+    int tc_cand[8][4];                   // autotuner candidates: kernel, cw, niss, microseconds
     void* Mbf = nullptr;                 // per level >= 4: hi then lo operand tiles
     int64_t mbf_off[FMM_PMAX + 2];       // element offset of level l's hi block
     std::vector<unsigned char> maps;     // tensor maps, one block per level
@@ -59,6 +66,8 @@ struct fmm_plan {
     float4* pos32 = nullptr;
     float* W32 = nullptr;
     float* V32 = nullptr;
+    // point dipoles in sorted order (fmm_evaluate_dipoles)
+    double* dip = nullptr;
     // host-call staging
     double* stage = nullptr;
     int64_t stage_n = 0;
@@ -78,6 +87,95 @@ static void* tc_maps_at(fmm_plan* pl, int l) {
     uintptr_t b = ((uintptr_t)pl->maps.data() + 63) & ~(uintptr_t)63;
     return (void*)(b + (size_t)l * tc_maps_bytes());
 }
+
+// ---------------------------------------------------------------------------
+// tensor-core kernel shape: kernel (0: streamed matrices, 1: matrices built
+// on chip, BF16 only) and chunk width; the autotuner times the candidates on
+// the plan's deepest level and keeps the fastest, cached on disk
+// ---------------------------------------------------------------------------
+static bool tc_shape_valid(int tf, int kern, int cw) {
+    if (kern == 0) return cw == 16 || cw == 32 || cw == 48 || cw == 96;
+    return kern == 1 && !tf && (cw == 16 || cw == 32 || cw == 48 || cw == 96);
+}
+
+static int tc_set_shape(fmm_plan* pl, int kern, int cw, cudaStream_t s) {
+    const int tf = pl->cfg.prec == FMM_GEMM_TF32X3;
+    if (kern == 0) {
+        if (tc_build_mat(pl->cfg.p, tf, cw, pl->Dtab, pl->Kbf, s) != 0) return -2;
+        pl->tc_niss = tc_mat_niss(pl->cfg.p, tf, cw);
+    } else {
+        if (tg_build(pl->cfg.p, cw, 1, pl->Dtab, pl->Kgen, s) != 0) return -2;
+        pl->tc_niss = 1;
+    }
+    pl->tc_kern = kern;
+    pl->tc_cw = cw;
+    return 0;
+}
+
+static std::string tc_cache_path() {
+    if (const char* e = getenv("FMM_TUNE_CACHE")) return e;
+    if (const char* x = getenv("XDG_CACHE_HOME"))
+        if (*x) return std::string(x) + "/fmm_gb300/tune.json";
+    if (const char* h = getenv("HOME"))
+        if (*h) return std::string(h) + "/.cache/fmm_gb300/tune.json";
+    return "";
+}
+
+static std::string tc_cache_key(const fmm_plan* pl) {
+    cudaDeviceProp prop;
+    std::string gpu = cudaGetDeviceProperties(&prop, pl->dev) == cudaSuccess ? prop.name : "unknown GPU";
+    char buf[160];
+    snprintf(buf, sizeof buf, "|p=%d|basis=%d|prec=%d|depth=%d", pl->cfg.p, pl->cfg.basis, pl->cfg.prec, pl->depth);
+    return gpu + buf;
+}
+
+// M2L of one tensor-core level in the plan's current kernel shape
+static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
+    const int tf = pl->cfg.prec == FMM_GEMM_TF32X3, es = tc_elem_bytes(tf);
+    char* hp = (char*)pl->Mbf + pl->mbf_off[l] * es;
+    char* lp = hp + tc_m_elems(l) * es;
+    return tc_m2l_level(pl->cfg.p, tf, pl->tc_kern, pl->tc_cw, pl->tc_niss, l, pl->Mbuf + pl->lvl_off[l], hp, lp,
+                        tc_maps_at(pl, l), pl->tc_kern ? pl->Kgen : pl->Kbf, pl->Lbuf + pl->lvl_off[l], pl->derr, s);
+}
+
+// Times every candidate shape on level `l` (one warm-up and one timed
+// launch each; the level's locals are overwritten by the real call after)
+// and keeps the fastest.
+static int tc_autotune(fmm_plan* pl, int l, cudaStream_t s) {
+    const int tf = pl->cfg.prec == FMM_GEMM_TF32X3;
+    static const int cand_bf16[][2] = {{0, 32}, {0, 48}, {0, 96}, {1, 48}, {1, 96}};
+    static const int cand_tf32[][2] = {{0, 16}, {0, 32}, {0, 48}};
+    const int (*cand)[2] = tf ? cand_tf32 : cand_bf16;
+    const int nc = tf ? 3 : 5;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -2;
+    int best = -1;
+    float bt = 1e30f;
+    pl->tc_ncand = 0;
+    for (int c = 0; c < nc; ++c) {
+        if (tc_set_shape(pl, cand[c][0], cand[c][1], s) != 0) { best = -2; break; }
+        if (tc_level_call(pl, l, s) != 0) { best = -2; break; }
+        cudaEventRecord(e0, s);
+        if (tc_level_call(pl, l, s) != 0) { best = -2; break; }
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { best = -2; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        int* r = pl->tc_cand[pl->tc_ncand++];
+        r[0] = cand[c][0]; r[1] = cand[c][1]; r[2] = pl->tc_niss; r[3] = (int)(ms * 1000.f);
+        if (ms < bt) { bt = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) return -2;
+    if (tc_set_shape(pl, cand[best][0], cand[best][1], s) != 0) return -2;
+    pl->tc_source = 1;
+    const std::string path = tc_cache_path();
+    if (!path.empty())
+        tune_cache_put(path.c_str(), tc_cache_key(pl).c_str(), pl->tc_kern, pl->tc_cw, pl->tc_niss, bt);
+    return 0;
+}
+
 
 static int fail_plan(fmm_plan* pl, int code, const char* fmt, ...) {
     char buf[512];
@@ -144,9 +242,51 @@ const char* fmm_last_error(const fmm_plan* plan) { return plan ? plan->err.c_str
 int64_t fmm_kernel_launches(void) { return g_launches.load(); }
 
 int fmm_tc_layout(int p, int prec, int* out, int nout) {
-    if (prec != FMM_GEMM_BF16X3 && prec != FMM_GEMM_TF32X3) return FMM_ERR_ARG;
+    if (prec != FMM_GEMM_TF32X3) return FMM_ERR_ARG;
     if (!tc_supported(p, FMM_BASIS_TRACELESS) || !out || nout < 0) return FMM_ERR_ARG;
     return tc_layout(p, prec == FMM_GEMM_TF32X3, out, nout);
+}
+
+int fmm_tc_gen_layout(int p, int cw, int niss, int* out, int nout, uint32_t* groups, int gcap) {
+    if (!out || nout < 0 || gcap < 0 || (gcap > 0 && !groups)) return fail_plan(nullptr, FMM_ERR_ARG, "bad output");
+    const int n = tg_layout_host(p, cw, niss, out, nout, groups, gcap);
+    if (n < 0) return fail_plan(nullptr, FMM_ERR_ARG, "p=%d, cw=%d, niss=%d not supported", p, cw, niss);
+    return n;
+}
+
+int fmm_set_tc_shape(fmm_plan* pl, int kernel, int cw) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (!is_tc(pl->cfg.prec) || pl->ad) FAIL(FMM_ERR_ARG, "not a tensor-core plan");
+    if (!tc_shape_valid(pl->cfg.prec == FMM_GEMM_TF32X3, kernel, cw))
+        FAIL(FMM_ERR_ARG, "kernel %d with chunk width %d is not a shape of this form", kernel, cw);
+    if (tc_set_shape(pl, kernel, cw, 0) != 0 || cudaDeviceSynchronize() != cudaSuccess)
+        FAIL(FMM_ERR_CUDA, "building the offset matrices failed: %s", cudaGetErrorString(cudaGetLastError()));
+    pl->tc_source = 3;
+    return FMM_OK;
+}
+
+int fmm_plan_tuning(const fmm_plan* pl, int* out, int nout) {
+    if (!pl || !out || nout < 0) return fail_plan(nullptr, FMM_ERR_ARG, "null plan or output");
+    if (!is_tc(pl->cfg.prec) || pl->ad) return fail_plan(nullptr, FMM_ERR_ARG, "not a tensor-core plan");
+    int v[5 + 4 * 8], n = 0;
+    v[n++] = pl->tc_kern; v[n++] = pl->tc_cw; v[n++] = pl->tc_niss; v[n++] = pl->tc_source; v[n++] = pl->tc_ncand;
+    for (int c = 0; c < pl->tc_ncand; ++c)
+        for (int k = 0; k < 4; ++k) v[n++] = pl->tc_cand[c][k];
+    const int m = nout < n ? nout : n;
+    for (int i = 0; i < m; ++i) out[i] = v[i];
+    return m;
+}
+
+int fmm_tune_cache_get(const char* path, const char* key, int* vals) {
+    if (!path || !key || !vals) return fail_plan(nullptr, FMM_ERR_ARG, "null argument");
+    return tune_cache_get(path, key, vals, vals + 1, vals + 2, nullptr);
+}
+
+int fmm_tune_cache_put(const char* path, const char* key, const int* vals, double ms) {
+    if (!path || !key || !vals) return fail_plan(nullptr, FMM_ERR_ARG, "null argument");
+    const int r = tune_cache_put(path, key, vals[0], vals[1], vals[2], ms);
+    if (r == -2) return fail_plan(nullptr, FMM_ERR_STATE, "writing %s failed", path);
+    return r == 0 ? FMM_OK : fail_plan(nullptr, FMM_ERR_ARG, "bad path or key");
 }
 
 int fmm_plan_stats(const fmm_plan* pl, int64_t* out, int nout) {
@@ -278,6 +418,8 @@ static void free_tree(fmm_plan* pl) {
     cudaFree(pl->xs); cudaFree(pl->ys); cudaFree(pl->zs); cudaFree(pl->qs);
     cudaFree(pl->perm); cudaFree(pl->start); cudaFree(pl->scratch);
     cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32); cudaFree(pl->Mbf); cudaFree(pl->pos32);
+    cudaFree(pl->dip);
+    pl->dip = nullptr;
     pl->pos32 = nullptr;
     pl->M32 = nullptr;
     pl->Mbf = nullptr;
@@ -456,11 +598,25 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     }
     if (ok && is_tc(cfg->prec)) {
         const int tf = cfg->prec == FMM_GEMM_TF32X3;
-        ok = cudaMalloc(&pl->Kbf, tc_b_bytes(tf)) == cudaSuccess && cudaMalloc(&pl->derr, sizeof(int)) == cudaSuccess &&
-             cudaMemset(pl->derr, 0, sizeof(int)) == cudaSuccess && tc_build_b(cfg->p, tf, pl->Dtab, pl->Kbf, 0) == 0 &&
-             cudaDeviceSynchronize() == cudaSuccess;
+        ok = cudaMalloc(&pl->Kbf, tc_mat_bytes(tf)) == cudaSuccess && cudaMalloc(&pl->derr, sizeof(int)) == cudaSuccess &&
+             cudaMemset(pl->derr, 0, sizeof(int)) == cudaSuccess &&
+             (tf || cudaMalloc(&pl->Kgen, tg_b_bytes()) == cudaSuccess) &&
+             tc_set_shape(pl, 0, tc_default_cw(tf), 0) == 0 && cudaDeviceSynchronize() == cudaSuccess;
+        if (ok && cfg->autotune) {
+            // a shape measured earlier for this GPU, order, basis, form and depth
+            int k = 0, cw = 0, ni = 0;
+            const std::string path = tc_cache_path();
+            if (!path.empty() && tune_cache_get(path.c_str(), tc_cache_key(pl).c_str(), &k, &cw, &ni, nullptr) == 1 &&
+                tc_shape_valid(tf, k, cw)) {
+                ok = tc_set_shape(pl, k, cw, 0) == 0 && cudaDeviceSynchronize() == cudaSuccess;
+                pl->tc_source = 2;
+            }
+        }
     }
-    if (ok && (cfg->prec == FMM_FP32 || is_tc(cfg->prec))) {
+    if (ok) {
+        // packed per-offset matrices of the grouped M2L: FP32 (FP32 form and
+        // the small levels of the tensor-core forms) or FP64 (FP64 form)
+        const bool f64 = cfg->prec == FMM_FP64;
         pl->kst = grouped_kstride(cfg->p, cfg->basis);
         const int cap = pl->kst;
         std::vector<unsigned char> ent((size_t)6 * cap);
@@ -468,9 +624,13 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         ok = grouped_entries(cfg->p, cfg->basis, ent.data(), cap) >= 0 &&
              cudaMalloc(&dent, ent.size()) == cudaSuccess &&
              cudaMemcpy(dent, ent.data(), ent.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMalloc(&pl->K32, (size_t)343 * pl->kst * sizeof(float)) == cudaSuccess;
+             (f64 ? cudaMalloc(&pl->K64, (size_t)343 * pl->kst * sizeof(double))
+                  : cudaMalloc(&pl->K32, (size_t)343 * pl->kst * sizeof(float))) == cudaSuccess;
         if (ok) {
-            launch_build_ktab(cfg->p, cfg->basis, pl->kst, dent, pl->Dtab, pl->K32, 0);
+            if (f64)
+                launch_build_ktab64(cfg->p, cfg->basis, pl->kst, dent, pl->Dtab, pl->K64, 0);
+            else
+                launch_build_ktab(cfg->p, cfg->basis, pl->kst, dent, pl->Dtab, pl->K32, 0);
             ok = cudaDeviceSynchronize() == cudaSuccess;
         }
         cudaFree(dent);
@@ -487,8 +647,8 @@ void fmm_destroy(fmm_plan* pl) {
     if (!pl) return;
     ad_free(pl->ad);
     free_tree(pl);
-    cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32);
-    cudaFree(pl->Kbf); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
+    cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32); cudaFree(pl->K64);
+    cudaFree(pl->Kbf); cudaFree(pl->Kgen); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
     delete pl;
 }
 
@@ -642,13 +802,13 @@ static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
                 for (int k = 0; k < parts; ++k) count_launch();
             }
         }
-        for (int l = lo > tc_first_level() ? lo : tc_first_level(); l <= hi; ++l) {
-            char* hp = (char*)pl->Mbf + pl->mbf_off[l] * es;
-            char* lp = hp + tc_m_elems(l) * es;
-            if (tc_m2l_level(pl->cfg.p, tf, l, Mlev(pl, l), hp, lp, tc_maps_at(pl, l), pl->Kbf, Llev(pl, l),
-                             pl->derr, S(stream)) != 0)
+        const int l0 = lo > tc_first_level() ? lo : tc_first_level();
+        if (l0 <= hi && pl->cfg.autotune && pl->tc_source == 0 && tc_autotune(pl, pl->depth, S(stream)) != 0)
+            FAIL(FMM_ERR_CUDA, "tensor-core autotuning failed: %s", cudaGetErrorString(cudaGetLastError()));
+        (void)es;
+        for (int l = l0; l <= hi; ++l)
+            if (tc_level_call(pl, l, S(stream)) != 0)
                 FAIL(FMM_ERR_CUDA, "tensor-core M2L launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-        }
         CKLAUNCH();
         return FMM_OK;
     }
@@ -663,9 +823,11 @@ static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
         CKLAUNCH();
         return FMM_OK;
     }
-    for (int l = lo; l <= hi; ++l)
-        launch_m2l_fp64_level(pl->cfg.p, pl->cfg.basis, l, pl->Dtab, Mlev(pl, l), Llev(pl, l),
-                              (int64_t)1 << (3 * l), S(stream));
+    for (int l = lo; l <= hi; ++l) {
+        const int parts = launch_m2l_grp64(pl->cfg.p, pl->cfg.basis, l, Mlev(pl, l), Llev(pl, l), pl->K64,
+                                           (int64_t)1 << (3 * l), S(stream));
+        for (int k = 0; k < parts; ++k) count_launch();
+    }
     CKLAUNCH();
     return FMM_OK;
 }
@@ -771,6 +933,39 @@ int fmm_evaluate(fmm_plan* pl, int64_t n, const double* x, const double* y, cons
     if ((rc = fmm_l2l(pl, stream))) return rc;
     if ((rc = fmm_l2p(pl, pot, ax, ay, az, stream))) return rc;
     if ((rc = fmm_p2p(pl, pot, ax, ay, az, stream))) return rc;
+    return FMM_OK;
+}
+
+int fmm_evaluate_dipoles(fmm_plan* pl, int64_t n, const double* x, const double* y, const double* z, const double* q,
+                         const double* px, const double* py, const double* pz, double* pot, double* ax, double* ay,
+                         double* az, void* stream) {
+    if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
+    if (pl->ad || pl->cfg.prec != FMM_FP64)
+        FAIL(FMM_ERR_UNSUPPORTED, "point dipoles need a uniform octree and FMM_FP64");
+    if (n > 0 && (!px || !py || !pz || !pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null array");
+    int rc;
+    if ((rc = fmm_build_tree(pl, n, x, y, z, q, stream))) return rc;
+    cudaStream_t s = S(stream);
+    if (!pl->dip && cudaMalloc(&pl->dip, (size_t)3 * (n > 0 ? n : 1) * sizeof(double)) != cudaSuccess) {
+        pl->dip = nullptr;
+        cudaGetLastError();
+        FAIL(FMM_ERR_OOM, "allocating the sorted dipole moments failed");
+    }
+    double *pxs = pl->dip, *pys = pl->dip + n, *pzs = pl->dip + 2 * n;
+    launch_gather3(n, pl->perm, px, py, pz, pxs, pys, pzs, s);
+    const int d = pl->depth;
+    // P2M of charges and dipoles (the general P2M kernel writes the plan's
+    // scaled leaf multipoles; traceless: the reduced representative)
+    launch_p2m(pl->cfg.p, pl->cfg.basis, 1, pl->nleaf, nullptr, pl->start, pl->xs, pl->ys, pl->zs, pl->qs, nullptr, d,
+               (double)(1 << d), Mlev(pl, d), pl->nleaf, g_tab[pl->dev], s, pxs, pys, pzs);
+    CKLAUNCH();
+    if ((rc = fmm_m2m(pl, stream))) return rc;
+    if ((rc = fmm_m2l(pl, stream))) return rc;
+    if ((rc = fmm_l2l(pl, stream))) return rc;
+    if ((rc = fmm_l2p(pl, pot, ax, ay, az, stream))) return rc;
+    if ((rc = fmm_p2p(pl, pot, ax, ay, az, stream))) return rc;
+    launch_p2p_dipole(d, pl->nleaf, pl->start, pl->xs, pl->ys, pl->zs, pxs, pys, pzs, pl->perm, pot, ax, ay, az, s);
+    CKLAUNCH();
     return FMM_OK;
 }
 

@@ -76,7 +76,13 @@ FMM_DECL_P(6) FMM_DECL_P(7) FMM_DECL_P(8) FMM_DECL_P(9) FMM_DECL_P(10)
 // fmm_ops.cu
 int launch_p2m(int p, int basis, int mode, int64_t ncell, const int64_t* start64, const int* start32,
                const double* x, const double* y, const double* z, const double* q, const double* centre,
-               int depth, double inv_h, double* M, int64_t ldm, const DevTables& T, cudaStream_t s);
+               int depth, double inv_h, double* M, int64_t ldm, const DevTables& T, cudaStream_t s,
+               const double* px = nullptr, const double* py = nullptr, const double* pz = nullptr);
+int launch_p2p_dipole(int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
+                      const double* zs, const double* pxs, const double* pys, const double* pzs, const int* perm,
+                      double* pot, double* ax, double* ay, double* az, cudaStream_t s);
+int launch_gather3(int64_t n, const int* perm, const double* a, const double* b, const double* c, double* oa,
+                   double* ob, double* oc, cudaStream_t s);
 // prec 0: double storage and arithmetic, 1: float
 int launch_m2m_general(int prec, int p, int basis, int64_t n, const void* Mc, const double* delta, void* Mp,
                        const DevTables& T, cudaStream_t s);
@@ -90,8 +96,6 @@ int launch_m2m_level(int p, int basis, int l, const double* W, const double* Mch
                      int64_t npa, cudaStream_t s);
 int launch_l2l_level(int p, int basis, int l, const double* V, const double* Lpa, int64_t npa, double* Lch,
                      int64_t nch, cudaStream_t s);
-int launch_m2l_fp64_level(int p, int basis, int l, const double* Dtab, const double* Mt, double* Lt,
-                          int64_t ncell, cudaStream_t s);
 int launch_zero4(int64_t n, double* a, double* b, double* c, double* d, cudaStream_t s);
 
 // fmm_leafops.cu (prec 0: double arithmetic, 1: float arithmetic)
@@ -113,6 +117,11 @@ int grouped_entries(int p, int basis, unsigned char* out, int cap);
 int launch_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
 int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K, int64_t ncell,
                    cudaStream_t s);
+// FP64 form of the grouped M2L (packed FP64 matrices)
+int launch_build_ktab64(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, double* K,
+                        cudaStream_t s);
+int launch_m2l_grp64(int p, int basis, int l, const double* M, double* Lt, const double* K, int64_t ncell,
+                     cudaStream_t s);
 int grouped_kstride(int p, int basis);
 
 // fmm_api.cu: translation matrices of the uniform octree in scaled units
@@ -133,14 +142,32 @@ int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, 
 int tc_supported(int p, int basis);
 int tc_first_level();   // levels below run on the FP32 grouped kernel
 int tc_layout(int p, int tf, int* out, int nout);
-size_t tc_b_bytes(int tf);
+size_t tc_mat_bytes(int tf);
+int tc_default_cw(int tf);
+int tc_mat_niss(int p, int tf, int cw);
 int tc_elem_bytes(int tf);
 size_t tc_m_elems(int l);
 size_t tc_maps_bytes();
-int tc_build_b(int p, int tf, const double* Dtab, void* B, cudaStream_t s);
+// kern 0: per-offset matrices streamed from global memory (tc_build_mat at
+// chunk width cw; niss follows from the layout); kern 1 (BF16 only): the
+// matrices built on chip (tg_build; niss 1 or 2)
+int tc_build_mat(int p, int tf, int cw, const double* Dtab, void* B, cudaStream_t s);
 int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps);
-int tc_m2l_level(int p, int tf, int l, const double* M, void* hi, void* lo, const void* maps, const void* B,
-                 double* Lt, int* err, cudaStream_t s);
+int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double* M, void* hi, void* lo,
+                 const void* maps, const void* B, double* Lt, int* err, cudaStream_t s);
+// fmm_m2l_tcgen.cu (BF16 hi/lo form, offset matrices built on chip)
+int tg_supported(int p);
+size_t tg_b_bytes();
+int tg_build(int p, int cw, int niss, const double* Dtab, void* B, cudaStream_t s);
+int tg_m2l_level(int p, int cw, int niss, int l, const void* maps, const void* B, double* Lt, int* err,
+                 cudaStream_t s);
+int tg_layout_host(int p, int cw, int niss, int* out, int nout, uint32_t* groups, int gcap);
+int tg_default_cw();
+int tg_default_niss();
+
+// fmm_tune.cu: cache of autotuned tensor-core kernel shapes (JSON file)
+int tune_cache_get(const char* path, const char* key, int* kernel, int* cw, int* niss, double* ms);
+int tune_cache_put(const char* path, const char* key, int kernel, int cw, int niss, double ms);
 
 // fmm_tree.cu
 size_t tree_scratch_bytes(int64_t n, int64_t nleaf);

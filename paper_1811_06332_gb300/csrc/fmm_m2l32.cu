@@ -21,6 +21,41 @@ __global__ void k_build_ktab(int ns, int ksz, int kst, const unsigned char* __re
     K[i] = v;
 }
 
+// The same packed matrices kept in FP64 (the plain FP64 form's grouped M2L).
+__global__ void k_build_ktab64(int ns, int ksz, int kst, const unsigned char* __restrict__ ent,
+                               const double* __restrict__ Dtab, double* __restrict__ K) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)343 * kst) return;
+    const int r = (int)(i / kst), e = (int)(i % kst);
+    double v = 0.0;
+    if (e < ksz) {
+        const unsigned char* t = ent + 6 * e;
+        const double d = Dtab[(int64_t)r * ns + pos_sym(t[0] + t[3], t[1] + t[4], t[2] + t[5])];
+        v = d * c_invfact[t[3]] * c_invfact[t[4]] * c_invfact[t[5]];
+    }
+    K[i] = v;
+}
+
+static int packed_size(int p, int basis) {
+    int ksz = 0;
+    const int nc = ncoef_of(p, basis);
+    for (int r = 0; r < nc; ++r) {
+        const unsigned char* n = basis ? fmm_tl_idx[r] : fmm_sym_idx[r];
+        const int rem = p - n[0] - n[1] - n[2];
+        ksz += basis ? nt_of(rem) : ns_of(rem);
+    }
+    return ksz;
+}
+
+int launch_build_ktab64(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, double* K,
+                        cudaStream_t s) {
+    const int ksz = packed_size(p, basis);
+    const int64_t tot = (int64_t)343 * kst;
+    k_build_ktab64<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ns_of(p), ksz, kst, ent, Dtab, K);
+    count_launch();
+    return ksz;
+}
+
 int launch_build_ktab(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, float* K,
                       cudaStream_t s) {
     int ksz = 0;

@@ -1,4 +1,9 @@
-// Offset-grouped M2L on the 5th-generation tensor cores (Eq. M2L regrouped).
+// Offset-grouped M2L on the 5th-generation tensor cores (Eq. M2L regrouped),
+// with each offset's matrix precomputed in global memory and streamed by
+// bulk copies (the streamed-matrix kernel; fmm_m2l_tcgen.cu holds the
+// kernel that builds the matrices on chip, a second autotuner candidate of
+// the BF16 form).  This file also holds the operand split of the
+// multipoles and the TMA tensor maps, which both kernels use.
 //
 // On a uniform level, every target cell of one parity class sees the same
 // 189 integer offsets o, and all pairs with one offset share one matrix
@@ -28,17 +33,12 @@
 #include <cuda_bf16.h>
 
 #include "fmm_internal.h"
+#include "fmm_tc_common.cuh"
 
 namespace fmm {
 
-constexpr int TC_K = 96;                       // padded multipole components (K)
-constexpr int TC_N = 96;                       // padded local components (N)
-constexpr int TC_CH = 12;                      // 16-byte chunks of one A row per K-part
-constexpr int TC_PSTEPS = 6;                   // K-steps (32 bytes of a row) per K-part
-constexpr int TC_NCH = TC_N / 16;              // N-chunks of at least 16 local components
 constexpr int TC_PMAX = TC_N * TC_PSTEPS * 32; // 18432: bound on one part block (hi or lo) of a matrix
 constexpr int TC_TMEM_COLS = 128;             // one accumulator (96 columns used)
-constexpr long TC_SPIN = 1L << 24;             // bounded waits
 
 // The matrix of one offset is block-triangular in rank (|n| + |m| <= p), so
 // local components are processed in N-chunks: chunk j (rows cw j .. cw j +
@@ -62,93 +62,6 @@ struct TcChunks {
     int nbst;                // matrix stages (2 or 4)
     int niss;                // MMA-issuing warps (2 or 4; divides nbst)
 };
-
-struct TcMaps {
-    CUtensorMap hi[8];
-    CUtensorMap lo[8];
-};
-
-// Source slabs (levels with at least 16 cells per class and axis).  A CTA
-// owns a column of 8 x 16 x 1 target cells of one class.  For one
-// source class and one z shift dz in {-1, 0, 1}, the sources of the (up to
-// 9) offsets with x, y shifts dx, dy in {-1, 0, 1} all lie in one slab of
-// 10 x 18 x 1 cells, stored [j][chunk][i][16 bytes]: the A operand of
-// offset (dx, dy) starts at row i = dx + 1 of group j = dy + 1.  Core
-// matrices stay 8 consecutive 16-byte rows; LBO (next chunk along K) is
-// 160 bytes and SBO (next group of 8 rows) 1920 bytes.  The slab is
-// fetched once for its offsets instead of once per offset.
-constexpr int SL_I = 10, SL_J = 18;
-constexpr int SL_BYTES = SL_I * TC_CH * SL_J * 16;   // 34560: one slab operand (hi or lo) of one K-part
-
-struct alignas(64) TcLevelMaps {
-    TcMaps slab;    // box 10 x 18 x 1 cells, one K-part
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-    for (long it = 0; it < TC_SPIN; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    atomicExch(err, code);
-    return false;
-}
-
-// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
-// 8 rows x 16 bytes stored as 128 contiguous bytes; LBO = distance between
-// core matrices along K, SBO = distance between 8-row groups.
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version
-    return d;                // layout type 0: no swizzle
-}
-
-// Instruction descriptor, both operands K-major, F32 accumulator:
-// kind::f16 with BF16 x BF16 (format 1), or kind::tf32 with TF32 x TF32
-// (format 2).
-__host__ __device__ constexpr uint32_t make_idesc(int tf, int M, int N) {
-    return (1u << 4)                                  // D format F32
-           | ((tf ? 2u : 1u) << 7)                    // A format
-           | ((tf ? 2u : 1u) << 10)                   // B format
-           | ((uint32_t)(N >> 3) << 17)               // N
-           | ((uint32_t)(M >> 4) << 24);              // M
-}
-
-template <int TF>
-__device__ __forceinline__ void tc_mma(uint32_t dcol, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-    if constexpr (TF)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
-    else
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane (32x32b shape)
-__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(ta));
-}
 
 // Two rings: 2 slab buffers ({hi, lo} of one K-part) and nbst matrix
 // stages.  The producer (warp 0) walks (source class, dz, part) slabs and,
@@ -411,11 +324,13 @@ struct TcSplit<1> {
 
 // Multipoles of one level (FP64, [ncoef][ncell], parity-class numbering) ->
 // hi/lo operands in the TMA layout [class][k][j][chunk][i][16 bytes]
-// (components padded to 96; 8 BF16 or 4 TF32 per 16-byte chunk).  One
+// (components padded to 96; 8 BF16 or 4 TF32 per 16-byte chunk); with
+// `scale` each component m is multiplied by 1/m! first (the operand of the
+// kernel whose offset matrices hold D_{n+m} without the 1/m! weight).  One
 // thread per (cell, chunk): blockIdx.y is the chunk, the cell index splits
 // into class and (i, j, k) by shifts (the class grid side is a power of 2).
 template <int TF>
-__global__ void k_tc_split_m(int l, int nc, const double* __restrict__ M, void* __restrict__ hi_,
+__global__ void k_tc_split_m(int l, int nc, int scale, const double* __restrict__ M, void* __restrict__ hi_,
                              void* __restrict__ lo_) {
     using T = typename TcSplit<TF>::T;
     constexpr int EPC = 16 / (int)sizeof(T);        // elements per 16-byte chunk
@@ -430,7 +345,8 @@ __global__ void k_tc_split_m(int l, int nc, const double* __restrict__ M, void* 
 #pragma unroll
     for (int e = 0; e < EPC; ++e) {
         const int m = EPC * c + e;
-        const double x = m < nc ? M[(int64_t)m * ncell + idx] : 0.0;
+        double x = m < nc ? M[(int64_t)m * ncell + idx] : 0.0;
+        if (scale && m < nc) x *= c_invfact[c_tl_idx[m][0]] * c_invfact[c_tl_idx[m][1]] * c_invfact[c_tl_idx[m][2]];
         TcSplit<TF>::split(x, vh[e], vl[e]);
     }
     const int64_t o = ((((int64_t)cls * hs + k) * hs + j) * NCH + c) * hs + i;
@@ -485,27 +401,30 @@ __global__ void k_tc_build_b(int p, int nc, const TcChunks ch, const double* __r
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 int tc_supported(int p, int basis) { return basis == 1 && p >= 1 && ncoef_of(p, basis) <= TC_K; }
-size_t tc_b_bytes(int tf) { return (size_t)343 * 2 * TC_PMAX * (tf ? 2 : 1); }
+// bytes of the per-offset matrices (any chunk width) of the streamed-matrix kernel
+size_t tc_mat_bytes(int tf) { return (size_t)343 * 2 * TC_PMAX * (tf ? 2 : 1); }
 int tc_elem_bytes(int tf) { return tf ? 4 : 2; }
 
 // Chunk width: the N of one MMA.  Wider chunks issue fewer, larger MMAs;
 // narrower ones skip more of the zero triangle and leave room for four
 // matrix stages (four issuers).  Measured best at p = 8: 48 for BF16, 32
-// for TF32.  FMM_TC_CHUNK (16, 32, 48 or 96) overrides it for tuning.
-static int tc_chunk_width(int tf) {
+// for TF32; the autotuner times the candidates.  For the layout
+// diagnostics, FMM_TC_CHUNK (16, 32, 48 or 96) overrides the default.
+int tc_default_cw(int tf) { return tf ? 32 : 48; }
+static int tc_chunk_width_env(int tf) {
     if (const char* e = getenv("FMM_TC_CHUNK")) {
         const int v = atoi(e);
         if (v == 16 || v == 32 || v == 48 || v == 96) return v;
     }
-    return tf ? 32 : 48;
+    return tc_default_cw(tf);
 }
 
-static TcChunks tc_chunks(int p, int tf) {
+static TcChunks tc_chunks(int p, int tf, int cw) {
     TcChunks c{};
     const int nc = ncoef_of(p, 1);
     const int cps = tf ? 8 : 16;   // columns per K-step
     c.tf = tf;
-    c.cw = tc_chunk_width(tf);
+    c.cw = cw;
     c.nch = (nc + c.cw - 1) / c.cw;
     for (int j = 0; j < c.nch; ++j) {
         const int r0 = c.cw * j;
@@ -541,7 +460,7 @@ static TcChunks tc_chunks(int p, int tf) {
 // cw, nch, np, nbst, niss, bstage, mbytes, shared bytes, kch[6], nk[2][6],
 // boff[2][6], pbytes[2], poff[2] (42 ints).  Returns the count written.
 int tc_layout(int p, int tf, int* out, int nout) {
-    const TcChunks c = tc_chunks(p, tf);
+    const TcChunks c = tc_chunks(p, tf, tc_chunk_width_env(tf));
     int v[42], n = 0;
     v[n++] = c.cw; v[n++] = c.nch; v[n++] = c.np; v[n++] = c.nbst; v[n++] = c.niss; v[n++] = c.bstage;
     v[n++] = c.mbytes; v[n++] = 4 * SL_BYTES + c.nbst * c.bstage + 1024 + 256;
@@ -559,17 +478,23 @@ int tc_layout(int p, int tf, int* out, int nout) {
 int tc_first_level() { return 5; }   // class grid of 16 cells per axis: one slab column fits
 size_t tc_m_elems(int l) { return l < 1 ? 0 : ((size_t)8 << (3 * (l - 1))) * TC_K; }
 
-int tc_build_b(int p, int tf, const double* Dtab, void* B, cudaStream_t s) {
+// Per-offset matrices of the streamed-matrix kernel in the layout of chunk
+// width cw (a plan rebuilds them when its chunk width changes).
+int tc_build_mat(int p, int tf, int cw, const double* Dtab, void* B, cudaStream_t s) {
     const int64_t tot = (int64_t)343 * TC_N * (TC_K * tc_elem_bytes(tf) / 16);
-    if (cudaMemsetAsync(B, 0, tc_b_bytes(tf), s) != cudaSuccess) return -2;
+    if (cudaMemsetAsync(B, 0, tc_mat_bytes(tf), s) != cudaSuccess) return -2;
     const unsigned g = (unsigned)((tot + 255) / 256);
     if (tf)
-        k_tc_build_b<1><<<g, 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p, 1), Dtab, (unsigned char*)B);
+        k_tc_build_b<1><<<g, 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p, 1, cw), Dtab, (unsigned char*)B);
     else
-        k_tc_build_b<0><<<g, 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p, 0), Dtab, (unsigned char*)B);
+        k_tc_build_b<0><<<g, 256, 0, s>>>(p, ncoef_of(p, 1), tc_chunks(p, 0, cw), Dtab, (unsigned char*)B);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
+
+// MMA-issuing warps of the streamed-matrix kernel at chunk width cw (as many
+// as matrix stages fit, 2 or 4)
+int tc_mat_niss(int p, int tf, int cw) { return tc_chunks(p, tf, cw).niss; }
 
 // Encodes the tensor maps (8 classes x hi/lo) of one level.  Tensor dims
 // (innermost first): e (16 bytes), i (hs), chunk (12 or 24), j (hs), k (hs);
@@ -629,20 +554,27 @@ static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const 
     return 0;
 }
 
-int tc_m2l_level(int p, int tf, int l, const double* M, void* hi, void* lo, const void* maps, const void* B,
-                 double* Lt, int* err, cudaStream_t s) {
+int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double* M, void* hi, void* lo,
+                 const void* maps, const void* B, double* Lt, int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
     if (hs < 16) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const int nc = ncoef_of(p, 1);
     if (ncell > ((int64_t)1 << 30)) return -1;   // 32-bit cell indices in k_tc_split_m
     const dim3 g((unsigned)((ncell + 255) / 256), (unsigned)(TC_K * tc_elem_bytes(tf) / 16));
+    if (kern == 1 && tf) return -1;   // the on-chip kernel takes BF16 operands
+    // the on-chip kernel's matrices hold D_{n+m} alone: its operand carries 1/m!
     if (tf)
-        k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, M, hi, lo);
+        k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, 0, M, hi, lo);
     else
-        k_tc_split_m<0><<<g, 256, 0, s>>>(l, nc, M, hi, lo);
+        k_tc_split_m<0><<<g, 256, 0, s>>>(l, nc, kern == 1, M, hi, lo);
     count_launch();
-    const TcChunks ch = tc_chunks(p, tf);
+    if (kern == 1) {
+        const int rc = tg_m2l_level(p, cw, niss, l, maps, B, Lt, err, s);
+        if (rc != 0) return rc;
+        return cudaGetLastError() == cudaSuccess ? 0 : -2;
+    }
+    const TcChunks ch = tc_chunks(p, tf, cw);
     if (ch.niss != 2 && ch.niss != 4) return -1;
     const int rc = tf ? (ch.niss == 4 ? tc_launch<1, 4>(ch, l, nc, maps, B, Lt, ncell, err, s)
                                       : tc_launch<1, 2>(ch, l, nc, maps, B, Lt, ncell, err, s))

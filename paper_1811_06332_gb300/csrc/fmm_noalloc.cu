@@ -28,7 +28,10 @@ constexpr int64_t O_EXPAND = O_DETR + al(sizeof(fmm_detr_val));
 constexpr int64_t O_REDUCE = O_EXPAND + al(sizeof(fmm_expand_val));
 constexpr int64_t O_OFFS = O_REDUCE + al(sizeof(fmm_reduce_val));
 constexpr int64_t O_DTAB = O_OFFS + al(343 * 3 * 8);
-constexpr int64_t O_W = O_DTAB + al(343 * NA_NC * 8);
+constexpr int64_t NA_KST = 924;   // packed grouped-M2L entries, largest for p = 6: C(12, 6) (symmetric)
+constexpr int64_t O_ENT = O_DTAB + al(343 * NA_NC * 8);
+constexpr int64_t O_K64 = O_ENT + al(6 * NA_KST);
+constexpr int64_t O_W = O_K64 + al(343 * NA_KST * 8);
 constexpr int64_t O_V = O_W + al(8 * NA_NC * NA_NC * 8);
 constexpr int64_t O_XS = O_V + al(8 * NA_NC * NA_NC * 8);
 constexpr int64_t O_PERM = O_XS + al(4 * NA_MAX_N * 8);
@@ -39,6 +42,8 @@ constexpr int64_t O_TREE = O_L + al(NA_NC * NA_NCELL * 8);
 // tree-build scratch: keys[n], order[n], fill[nleaf], scan block sums
 constexpr int64_t NA_TREE_BYTES = al(NA_MAX_N * 4) + al(NA_MAX_N * 4) + al(NA_NLEAF * 4) + 4 * 256 + 1024;
 constexpr int64_t NA_BYTES = O_TREE + NA_TREE_BYTES;
+static_assert(NA_BYTES <= FMM_NOALLOC_BYTES_APPROX && NA_BYTES > FMM_NOALLOC_BYTES_APPROX - 100000,
+              "FMM_NOALLOC_BYTES_APPROX states the array's size");
 
 // The scratch array.  In host code its name is a host-side stand-in, not a
 // device address: the device address is obtained with cudaGetSymbolAddress.
@@ -136,7 +141,15 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
         if (na_dtable(p, (const double*)(b + O_OFFS), (double*)(b + O_DTAB), s) != 0)
             return na_fail(FMM_ERR_CUDA, "D-tensor table launch failed", cudaGetLastError());
         count_launch();
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)  // host vectors W, V go out of scope
+        // packed FP64 matrices of the grouped M2L, as the FP64 plan builds them
+        const int kst = grouped_kstride(p, basis);
+        if (kst < 0 || kst > NA_KST) return na_fail(FMM_ERR_ARG, "grouped M2L layout exceeds the fixed array");
+        unsigned char ent[6 * NA_KST];
+        if (grouped_entries(p, basis, ent, kst) < 0) return na_fail(FMM_ERR_ARG, "grouped M2L layout failed");
+        if ((e = cudaMemcpyAsync(b + O_ENT, ent, (size_t)6 * kst, cudaMemcpyHostToDevice, s)))
+            return na_fail(FMM_ERR_CUDA, "uploading the grouped M2L layout failed", e);
+        launch_build_ktab64(p, basis, kst, b + O_ENT, (const double*)(b + O_DTAB), (double*)(b + O_K64), s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)  // host arrays W, V, ent go out of scope
             return na_fail(FMM_ERR_CUDA, "set-up of matrices failed", e);
         st.p = p;
         st.basis = basis;
@@ -161,7 +174,7 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
     for (int l = 0; l <= depth; ++l) { lo[l] = tot; tot += (int64_t)nc << (3 * l); }
     const double* W = (const double*)(b + O_W);
     const double* V = (const double*)(b + O_V);
-    const double* Dtab = (const double*)(b + O_DTAB);
+    const double* K64 = (const double*)(b + O_K64);
     // the kernels fmm_evaluate runs for an FMM_FP64 uniform plan, in its order
     if (launch_uniform_tree(n, depth, x, y, z, q, xs, ys, zs, qs, perm, start, b + O_TREE, s) != 0)
         return na_fail(FMM_ERR_CUDA, "tree build failed", cudaGetLastError());
@@ -169,8 +182,10 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
     for (int l = depth - 1; l >= 2; --l)
         launch_m2m_level(p, basis, l, W, Mb + lo[l + 1], (int64_t)1 << (3 * (l + 1)), Mb + lo[l],
                          (int64_t)1 << (3 * l), s);
-    for (int l = 2; l <= depth; ++l)
-        launch_m2l_fp64_level(p, basis, l, Dtab, Mb + lo[l], Lb + lo[l], (int64_t)1 << (3 * l), s);
+    for (int l = 2; l <= depth; ++l) {
+        const int parts = launch_m2l_grp64(p, basis, l, Mb + lo[l], Lb + lo[l], K64, (int64_t)1 << (3 * l), s);
+        for (int k = 0; k < parts; ++k) count_launch();
+    }
     for (int l = 2; l < depth; ++l)
         launch_l2l_level(p, basis, l, V, Lb + lo[l], (int64_t)1 << (3 * l), Lb + lo[l + 1],
                          (int64_t)1 << (3 * (l + 1)), s);

@@ -419,54 +419,59 @@ def kstride(p, basis):
     return (grouped_layout(p, basis)[3] + 3) // 4 * 4
 
 
-def emit_grouped_file(p, basis):
-    """FP32 offset-grouped M2L over the uniform interaction lists of one
-    level: one thread per target cell, the block's 128 targets share one
-    parity class and hence one sequence of 189 offsets; the packed matrix of
-    each offset is staged in shared memory and read by every thread at the
-    same address, the source multipole sits in registers."""
+def emit_grouped_file(p, basis, T="float"):
+    """Offset-grouped M2L over the uniform interaction lists of one level, in
+    FP32 (T = float) or FP64 (T = double) arithmetic: one thread per target
+    cell, the block's 128 targets share one parity class and hence one
+    sequence of 189 offsets; the packed matrix of each offset is staged in
+    shared memory and read by every thread at the same address, the source
+    multipole sits in registers, and every thread runs the same unrolled
+    FMA sequence (no divergence over the rank triangle)."""
     rows, pre, off, ksz = grouped_layout(p, basis)
     kst = kstride(p, basis)
-    L = ['// Generated by gen.py: FP32 offset-grouped M2L, p = %d, basis %d.' % (p, basis),
+    f64 = T == "double"
+    sfx = "64" if f64 else ""
+    L = ['// Generated by gen.py: %s offset-grouped M2L, p = %d, basis %d.' % ("FP64" if f64 else "FP32", p, basis),
          '#include "../fmm_device.cuh"',
          "namespace fmm {"]
-    parts = grouped_parts(p, basis)
+    # FP64 values take two registers: half the row budget
+    parts = grouped_parts(p, basis, budget=100 if f64 else 200)
     for k, (r0, r1) in enumerate(parts):
         klen = off[r1] - off[r0]
         ncol = pre[r0]
         L.append("__global__ void __launch_bounds__(128)")
-        L.append("m2l_grp_p%d_b%d_r%d(int l, const float* __restrict__ M, double* __restrict__ Lt,"
-                 " const float* __restrict__ K, int64_t ncell) {" % (p, basis, k))
-        L.append("  __shared__ __align__(16) float sK[%d];" % ((klen + 3) // 4 * 4))
-        L.append("  const int side = 1 << l, hs = side >> 1;")
-        L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + 127) / 128;")
+        L.append("m2l_grp%s_p%d_b%d_r%d(int l, const %s* __restrict__ M, double* __restrict__ Lt,"
+                 " const %s* __restrict__ K, int64_t ncell) {" % (sfx, p, basis, k, T, T))
+        L.append("  __shared__ __align__(16) %s sK[%d];" % (T, (klen + 3) // 4 * 4))
+        L.append("  const int side = 1 << l, hs = side >> 1, bs = (int)blockDim.x;   // 128 or (FP64 small levels) 32")
+        L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + bs - 1) / bs;")
         L.append("  const int cls = (int)(blockIdx.x / bpc);")
-        L.append("  const int64_t t = (int64_t)(blockIdx.x % bpc) * 128 + threadIdx.x;")
+        L.append("  const int64_t t = (int64_t)(blockIdx.x % bpc) * bs + threadIdx.x;")
         L.append("  const bool act = t < h3;")
         L.append("  const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;")
         L.append("  const int ix = 2 * (int)(t % hs) + cx, iy = 2 * (int)((t / hs) % hs) + cy,"
                  " iz = 2 * (int)(t / ((int64_t)hs * hs)) + cz;")
         for a in range(r1 - r0):
-            L.append("  float a%d = 0.f;" % a)
+            L.append("  %s a%d = 0;" % (T, a))
         L.append("  // offsets of this block: group blockIdx.y of gridDim.y (one group on large levels)")
         L.append("  const int u0 = (int)blockIdx.y * 216 / (int)gridDim.y, u1 = ((int)blockIdx.y + 1) * 216 / (int)gridDim.y;")
         L.append("  #pragma unroll 1")
         L.append("  for (int u = u0; u < u1; ++u) {")
         L.append("    const int ox = -2 - cx + u % 6, oy = -2 - cy + (u / 6) % 6, oz = -2 - cz + u / 36;")
         L.append("    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;")
-        L.append("    const float* Kg = K + (int64_t)((3 - oz) * 49 + (3 - oy) * 7 + (3 - ox)) * %d + %d;" % (kst, off[r0]))
+        L.append("    const %s* Kg = K + (int64_t)((3 - oz) * 49 + (3 - oy) * 7 + (3 - ox)) * %d + %d;" % (T, kst, off[r0]))
         L.append("    __syncthreads();")
-        L.append("    for (int e = threadIdx.x; e < %d; e += 128) sK[e] = __ldg(Kg + e);" % klen)
+        L.append("    for (int e = threadIdx.x; e < %d; e += bs) sK[e] = __ldg(Kg + e);" % klen)
         L.append("    __syncthreads();")
         L.append("    const int jx = ix + ox, jy = iy + oy, jz = iz + oz;")
         L.append("    if (!act || jx < 0 || jy < 0 || jz < 0 || jx >= side || jy >= side || jz >= side) continue;")
         L.append("    const int64_t s = cell_index(l, jx, jy, jz);")
         for c in range(ncol):
-            L.append("    const float m%d = __ldg(M + (int64_t)%d * ncell + s);" % (c, c))
+            L.append("    const %s m%d = __ldg(M + (int64_t)%d * ncell + s);" % (T, c, c))
         for r in range(r0, r1):
             base = off[r] - off[r0]
             for c in range(pre[r]):
-                L.append("    a%d = fmaf(sK[%d], m%d, a%d);" % (r - r0, base + c, c, r - r0))
+                L.append("    a%d = fma(sK[%d], m%d, a%d);" % (r - r0, base + c, c, r - r0))
         L.append("  }")
         L.append("  if (!act) return;")
         L.append("  const int64_t tg = (int64_t)cls * h3 + t;")
@@ -480,13 +485,15 @@ def emit_grouped_file(p, basis):
         L.append("}")
     L.append("// groups > 1 splits the 216 offset slots of every target over that many")
     L.append("// blocks (small levels); the partial sums are added into a zeroed Lt.")
-    L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
-             " cudaStream_t s, int groups) {" % (p, basis))
+    L.append("// bs: threads (targets) per block, 128 or 32.")
+    L.append("int launch_m2l_grp%s_p%d_b%d(int l, const %s* M, double* Lt, const %s* K, int64_t ncell,"
+             " cudaStream_t s, int groups, int bs) {" % (sfx, p, basis, T, T))
     L.append("  const int hs = (1 << l) >> 1;")
-    L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + 127) / 128;")
+    L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + bs - 1) / bs;")
     L.append("  if (groups > 1 && cudaMemsetAsync(Lt, 0, (size_t)%d * ncell * sizeof(double), s) != cudaSuccess) return -1;" % len(rows))
     for k in range(len(parts)):
-        L.append("  m2l_grp_p%d_b%d_r%d<<<dim3((unsigned)(8 * bpc), (unsigned)groups), 128, 0, s>>>(l, M, Lt, K, ncell);" % (p, basis, k))
+        L.append("  m2l_grp%s_p%d_b%d_r%d<<<dim3((unsigned)(8 * bpc), (unsigned)groups), bs, 0, s>>>(l, M, Lt, K, ncell);"
+                 % (sfx, p, basis, k))
     L.append("  return %d;" % len(parts))
     L.append("}")
     L.append("}  // namespace fmm")
@@ -761,12 +768,14 @@ def emit_list_dispatch():
 
 
 def emit_grouped_dispatch():
-    L = ['// Generated by gen.py: dispatch and layout of the FP32 offset-grouped M2L.',
+    L = ['// Generated by gen.py: dispatch and layout of the FP32 and FP64 offset-grouped M2L.',
          '#include "../fmm_device.cuh"', "namespace fmm {"]
     for p in range(PMAX + 1):
         for b in (0, 1):
             L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
-                     " cudaStream_t s, int groups);" % (p, b))
+                     " cudaStream_t s, int groups, int bs);" % (p, b))
+            L.append("int launch_m2l_grp64_p%d_b%d(int l, const double* M, double* Lt, const double* K,"
+                     " int64_t ncell, cudaStream_t s, int groups, int bs);" % (p, b))
     L.append("// Levels with fewer target blocks than about four per SM split the offsets")
     L.append("// of every target over up to 27 blocks.")
     L.append("int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K,"
@@ -779,7 +788,22 @@ def emit_grouped_dispatch():
     L.append("  const int groups = (int)(g < 1 ? 1 : g > 27 ? 27 : g);")
     for p in range(PMAX + 1):
         for b in (0, 1):
-            L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s, groups);"
+            L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s, groups, 128);"
+                     % (p, b, p, b))
+    L.append("  return -1;")
+    L.append("}")
+    L.append("// The FP64 form stays deterministic: no offset split (no atomic adds);")
+    L.append("// levels with fewer than two 128-target blocks per SM take blocks of 32.")
+    L.append("int launch_m2l_grp64(int p, int basis, int l, const double* M, double* Lt, const double* K,"
+             " int64_t ncell, cudaStream_t s) {")
+    L.append("  static int sms = 0;")
+    L.append("  if (!sms) { int d = 0; cudaGetDevice(&d); cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);"
+             " if (sms <= 0) sms = 1; }")
+    L.append("  const int64_t hs = (int64_t)1 << (l - 1), blocks = 8 * ((hs * hs * hs + 127) / 128);")
+    L.append("  const int bs = blocks >= 2 * (int64_t)sms ? 128 : 32;")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("  if (p == %d && basis == %d) return launch_m2l_grp64_p%d_b%d(l, M, Lt, K, ncell, s, 1, bs);"
                      % (p, b, p, b))
     L.append("  return -1;")
     L.append("}")
@@ -846,6 +870,9 @@ def generate(out=OUT):
             fg = os.path.join(out, "grp_P%d_b%d.cu" % (p, basis))
             write_if_changed(fg, emit_grouped_file(p, basis))
             files.append(fg)
+            fg64 = os.path.join(out, "grp64_P%d_b%d.cu" % (p, basis))
+            write_if_changed(fg64, emit_grouped_file(p, basis, "double"))
+            files.append(fg64)
     for p in range(0, PMAX + 1):
         for basis in (0, 1):
             fs = os.path.join(out, "shift_P%d_b%d.cu" % (p, basis))
@@ -866,8 +893,6 @@ def generate(out=OUT):
     fd = os.path.join(out, "grp_dispatch.cu")
     write_if_changed(fd, emit_grouped_dispatch())
     files.append(fd)
-    if False:
-        pass
     return files
 
 

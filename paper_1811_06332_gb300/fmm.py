@@ -21,12 +21,12 @@ FP64, FP32, GEMM_TF32X3, GEMM_BF16X3 = 0, 1, 2, 3
 
 EXPORTS = [
     "fmm_ncoef", "fmm_create", "fmm_destroy", "fmm_last_error", "fmm_build_tree", "fmm_p2m", "fmm_m2m",
-    "fmm_m2l", "fmm_m2l_levels", "fmm_tc_layout", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate",
-    "fmm_evaluate_host", "fmm_op_dtensor",
+    "fmm_m2l", "fmm_m2l_levels", "fmm_tc_layout", "fmm_tc_gen_layout", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate",
+    "fmm_evaluate_host", "fmm_evaluate_dipoles", "fmm_op_dtensor",
     "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
     "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_sync_status", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
     "fmm_mlp_grad", "fmm_mlp_train", "fmm_mlp_predict", "fmm_set_mlp", "fmm_set_pair_orders",
-    "fmm_plan_pair_orders",
+    "fmm_plan_pair_orders", "fmm_set_tc_shape", "fmm_plan_tuning", "fmm_tune_cache_get", "fmm_tune_cache_put",
 ]
 
 MLP_NF, MLP_NOUT, MLP_NBLOB = 12, 9, 9769
@@ -42,7 +42,7 @@ class Config(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("basis", ctypes.c_int), ("prec", ctypes.c_int),
                 ("adaptive", ctypes.c_int), ("depth", ctypes.c_int), ("max_leaf", ctypes.c_int),
                 ("theta", ctypes.c_double), ("learned_p", ctypes.c_int),
-                ("target_rel_err", ctypes.c_double), ("use_graph", ctypes.c_int)]
+                ("target_rel_err", ctypes.c_double), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 _lib = None
@@ -65,11 +65,13 @@ def lib():
             "fmm_p2m": ([_vp, _vp], _int), "fmm_m2m": ([_vp, _vp], _int),
             "fmm_m2l": ([_vp, _vp], _int), "fmm_m2l_levels": ([_vp, _int, _int, _vp], _int),
             "fmm_tc_layout": ([_int, _int, _vp, _int], _int),
+            "fmm_tc_gen_layout": ([_int, _int, _int, _vp, _int, _vp, _int], _int),
             "fmm_l2l": ([_vp, _vp], _int),
             "fmm_l2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_p2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_evaluate": ([_vp, _i64] + [_vp] * 9, _int),
             "fmm_evaluate_host": ([_vp, _i64] + [_vp] * 9, _int),
+            "fmm_evaluate_dipoles": ([_vp, _i64] + [_vp] * 12, _int),
             "fmm_op_dtensor": ([_int, _int, _int, _i64, _vp, _vp, _vp], _int),
             "fmm_op_p2m": ([_int, _int, _i64] + [_vp] * 8, _int),
             "fmm_op_m2m": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
@@ -89,6 +91,10 @@ def lib():
             "fmm_set_mlp": ([_vp, _vp, _i64], _int),
             "fmm_set_pair_orders": ([_vp, _vp, _i64], _int),
             "fmm_plan_pair_orders": ([_vp, _vp, _i64, _vp], _int),
+            "fmm_set_tc_shape": ([_vp, _int, _int], _int),
+            "fmm_plan_tuning": ([_vp, _vp, _int], _int),
+            "fmm_tune_cache_get": ([ctypes.c_char_p, ctypes.c_char_p, _vp], _int),
+            "fmm_tune_cache_put": ([ctypes.c_char_p, ctypes.c_char_p, _vp, ctypes.c_double], _int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -218,10 +224,10 @@ class Plan:
     """Owns an fmm_plan (uniform octree FMM of App. C)."""
 
     def __init__(self, p, basis=BASIS_SYM, prec=FP64, depth=3, use_graph=False, adaptive=False,
-                 max_leaf=64, theta=0.5, learned_p=False, target_rel_err=1e-4):
+                 max_leaf=64, theta=0.5, learned_p=False, target_rel_err=1e-4, autotune=False):
         cfg = Config(p=p, basis=basis, prec=prec, adaptive=int(adaptive), depth=depth, max_leaf=max_leaf,
                      theta=theta, learned_p=int(learned_p), target_rel_err=target_rel_err,
-                     use_graph=int(use_graph))
+                     use_graph=int(use_graph), autotune=int(autotune))
         h = _vp()
         _check(lib().fmm_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h
@@ -269,6 +275,10 @@ class Plan:
         self._c(lib().fmm_evaluate(self.h, len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), _ptr(pot), _ptr(ax),
                                    _ptr(ay), _ptr(az), _stream(stream)))
 
+    def fmm_evaluate_dipoles(self, x, y, z, q, px, py, pz, pot, ax, ay, az, stream=None):
+        self._c(lib().fmm_evaluate_dipoles(self.h, len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), _ptr(px), _ptr(py),
+                                           _ptr(pz), _ptr(pot), _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
+
     def fmm_evaluate_host(self, x, y, z, q, pot, ax, ay, az, stream=None):
         """Host (CPU) tensors or numpy arrays of float64; synchronous."""
         import numpy as np
@@ -286,6 +296,20 @@ class Plan:
         """Waits for the stream; raises FMMError (FMM_ERR_TIMEOUT) if a bounded
         device wait of the plan's tensor-core kernels gave up since the last check."""
         self._c(lib().fmm_sync_status(self.h, _stream(stream)))
+
+    def set_tc_shape(self, kernel, cw):
+        self._c(lib().fmm_set_tc_shape(self.h, int(kernel), int(cw)))
+
+    def tuning(self):
+        """Tensor-core kernel shape in use and the autotuner's candidates."""
+        import numpy as np
+        v = np.zeros(5 + 4 * 8, dtype=np.int32)
+        n = lib().fmm_plan_tuning(self.h, v.ctypes.data, len(v))
+        if n < 0:
+            _check(n)
+        cand = [dict(zip(("kernel", "cw", "niss", "us"), v[5 + 4 * c:9 + 4 * c].tolist())) for c in range(v[4])]
+        return {"kernel": int(v[0]), "cw": int(v[1]), "niss": int(v[2]),
+                "source": ("default", "autotuned", "cache", "set")[v[3]], "candidates": cand}
 
     def stats(self):
         """Tree and list sizes (fmm_plan_stats); learned_p plans add the

@@ -248,3 +248,93 @@ def test_tensor_core_form_rejects_unsupported(F):
             F.Plan(p=9, basis=1, prec=prec, depth=4)
         with pytest.raises(F.FMMError):
             F.Plan(p=6, basis=0, prec=prec, depth=4)
+
+
+@pytest.mark.parametrize("form,shapes", [("GEMM_BF16X3", [(0, 32), (0, 48), (0, 96), (1, 48), (1, 96)]),
+                                         ("GEMM_TF32X3", [(0, 16), (0, 32), (0, 48)])])
+def test_every_tensor_core_shape_vs_oracle(F, form, shapes):
+    """Every kernel shape the autotuner may pick (the streamed-matrix kernel
+    at each chunk width; for BF16 also the on-chip-matrix kernel) gives the
+    oracle's result within the tensor-core forms' 5e-6, depth 5."""
+    n, depth = 131072, 5
+    x, y, z = inputs.uniform_cube(n, 16)
+    q = inputs.masses_equal(n)
+    s = np.sort(np.unique((inputs.u01(7, 95, 150) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, 8, 1, sample=s)
+    X = [g(a) for a in (x, y, z, q)]
+    plan = F.Plan(p=8, basis=1, prec=getattr(F, form), depth=depth)
+    for kern, cw in shapes:
+        plan.set_tc_shape(kern, cw)
+        t = plan.tuning()
+        assert (t["kernel"], t["cw"], t["source"]) == (kern, cw, "set")
+        pot, acc = plan.evaluate(*X)
+        plan.sync_status()
+        ep, ea, per = errs(pot.cpu().numpy()[s], acc.cpu().numpy()[:, s], pref, aref)
+        assert ep < 5e-6 and ea < 5e-6, (kern, cw, ep, ea)
+    with pytest.raises(F.FMMError):
+        plan.set_tc_shape(1 if form == "GEMM_TF32X3" else 2, 48)
+    plan.close()
+
+
+def test_autotuned_plan_and_its_cache(F, tmp_path, monkeypatch):
+    """autotune: the first M2L times every candidate and keeps the fastest;
+    a second plan of the same configuration reads the choice back from the
+    cache file; both agree with the oracle."""
+    monkeypatch.setenv("FMM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    n, depth = 131072, 5
+    x, y, z = inputs.uniform_cube(n, 17)
+    q = inputs.masses_equal(n)
+    s = np.sort(np.unique((inputs.u01(7, 96, 120) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, 8, 1, sample=s)
+    X = [g(a) for a in (x, y, z, q)]
+    plan = F.Plan(p=8, basis=1, prec=F.GEMM_BF16X3, depth=depth, autotune=True)
+    assert plan.tuning()["source"] == "default"
+    pot, acc = plan.evaluate(*X)
+    plan.sync_status()
+    t = plan.tuning()
+    plan.close()
+    assert t["source"] == "autotuned" and len(t["candidates"]) == 5
+    best = min(t["candidates"], key=lambda c: c["us"])
+    assert (t["kernel"], t["cw"]) == (best["kernel"], best["cw"])
+    ep, ea, _ = errs(pot.cpu().numpy()[s], acc.cpu().numpy()[:, s], pref, aref)
+    assert ep < 5e-6 and ea < 5e-6
+    plan2 = F.Plan(p=8, basis=1, prec=F.GEMM_BF16X3, depth=depth, autotune=True)
+    t2 = plan2.tuning()
+    assert t2["source"] == "cache" and (t2["kernel"], t2["cw"]) == (t["kernel"], t["cw"])
+    pot2, acc2 = plan2.evaluate(*X)
+    torch.cuda.synchronize()
+    # the same shape; the small levels add partial sums with FP64 atomics
+    torch.testing.assert_close(pot2, pot, rtol=1e-12, atol=0)
+    torch.testing.assert_close(acc2, acc, rtol=1e-12, atol=1e-300)
+    plan2.close()
+
+
+@pytest.mark.parametrize("basis,depth,p", [(0, 3, 4), (1, 3, 6), (1, 4, 5), (0, 1, 3)])
+def test_point_dipoles_vs_oracle(F, basis, depth, p):
+    """Charges and point dipoles (App. B, Dipoles) through
+    fmm_evaluate_dipoles (FP64) against the oracle's FMM with dipoles on the
+    same tree (1e-12), and near its direct sum."""
+    n = 5000 + 7 * depth
+    x, y, z = inputs.uniform_cube(n, 70 + depth)
+    q = inputs.masses_open_unit(n, 70 + depth) - 0.5
+    px, py, pz = (inputs.u01(71 + depth, k, n) - 0.5 for k in range(3))
+    X = [g(a) for a in (x, y, z, q, px, py, pz)]
+    out = torch.full((4, n), 9.0, dtype=torch.float64, device=DEV)
+    plan = F.Plan(p=p, basis=basis, prec=F.FP64, depth=depth)
+    plan.fmm_evaluate_dipoles(*X, out[0], out[1], out[2], out[3])
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    pref, aref = oracle.fmm_uniform_dipole(x, y, z, q, px, py, pz, depth, p, basis)
+    ep, ea, per = errs(o[0], o[1:], pref, aref)
+    assert ep < 1e-12 and ea < 1e-12, (ep, ea)
+    # dipole moments zero: the charge-only evaluation
+    zero = torch.zeros(n, dtype=torch.float64, device=DEV)
+    plan.fmm_evaluate_dipoles(*X[:4], zero, zero, zero, out[0], out[1], out[2], out[3])
+    pot, acc = plan.evaluate(*X[:4])
+    torch.cuda.synchronize()
+    # (another P2M kernel: equal up to the summation order)
+    assert (torch.linalg.norm(out[0] - pot) / torch.linalg.norm(pot)).item() < 1e-13
+    assert (torch.linalg.norm(out[1:] - acc) / torch.linalg.norm(acc)).item() < 1e-13
+    plan.close()
+    with pytest.raises(F.FMMError):
+        F.Plan(p=4, basis=basis, prec=F.FP32, depth=3).fmm_evaluate_dipoles(*X, out[0], out[1], out[2], out[3])

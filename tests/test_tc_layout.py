@@ -1,6 +1,6 @@
-"""Host-side layout of the tensor-core M2L kernel (no GPU): for every order
-and operand type the kernel accepts, and every chunk width it can be tuned
-to, the layout the library computes must keep every copy and MMA operand in
+"""Host-side layout of the TF32 form's tensor-core M2L kernel, which streams
+each offset's precomputed matrix (no GPU): for every order the kernel
+accepts, and every chunk width it can be tuned to, the layout the library computes must keep every copy and MMA operand in
 bounds, fit the shared memory, cover the rank triangle |n| + |m| <= p, and
 keep the barrier invariant (the issuer count divides the matrix stages; see
 test_tc_protocol.py)."""
@@ -43,7 +43,7 @@ def test_layout_invariants(F, cw, monkeypatch):
         monkeypatch.delenv("FMM_TC_CHUNK", raising=False)
     else:
         monkeypatch.setenv("FMM_TC_CHUNK", cw)
-    for prec, tf in ((F.GEMM_BF16X3, 0), (F.GEMM_TF32X3, 1)):
+    for prec, tf in ((F.GEMM_TF32X3, 1),):
         cps = 8 if tf else 16                       # multipole columns per K-step (32 bytes of a row)
         for p in range(1, 9):
             d = layout(F, p, prec)
@@ -78,7 +78,8 @@ def test_layout_invariants(F, cw, monkeypatch):
 def test_layout_rejects(F):
     out = (ctypes.c_int * 42)()
     L = F.lib()
-    assert L.fmm_tc_layout(9, F.GEMM_BF16X3, out, 42) == F.ERR_ARG
+    assert L.fmm_tc_layout(9, F.GEMM_TF32X3, out, 42) == F.ERR_ARG
     assert L.fmm_tc_layout(8, F.FP32, out, 42) == F.ERR_ARG
+    assert L.fmm_tc_layout(8, F.GEMM_BF16X3, out, 42) == F.ERR_ARG   # the BF16 form: fmm_tc_gen_layout
     assert L.fmm_tc_layout(0, F.GEMM_TF32X3, out, 42) == F.ERR_ARG
-    assert L.fmm_tc_layout(8, F.GEMM_BF16X3, out, 8) == 8
+    assert L.fmm_tc_layout(8, F.GEMM_TF32X3, out, 8) == 8

@@ -112,3 +112,87 @@ def test_four_issuers_on_two_stages_break_the_parity_waits():
         except AssertionError:
             broken += 1
     assert broken > 0
+
+
+# ---------------------------------------------------------------------------
+# The kernel that builds the offset matrices on chip (csrc/fmm_m2l_tcgen.cu):
+# a producer (slabs into 2 buffers, D vectors into ND stages), NISS issuers
+# and G generator warps.  Generator warps wait for an offset's D vector
+# (dfull, one arrival), release it (dempty, G arrivals), wait for their
+# matrix stage to be free (bempty, one arrival: the issuer's commit) and
+# mark it written (bfull, G arrivals); issuer t % NISS waits for bfull and
+# commits to bempty; slabs as above.
+# ---------------------------------------------------------------------------
+def _simulate_gen(niss, nb, nd, ngen, seed, nslab=24):
+    rnd = random.Random(seed)
+    per_slab = [rnd.randint(5, 9) for _ in range(nslab)]
+    tot = sum(per_slab)
+    sfull, sempty = [_Barrier(1), _Barrier(1)], [_Barrier(niss), _Barrier(niss)]
+    dfull = [_Barrier(1) for _ in range(nd)]
+    dempty = [_Barrier(ngen) for _ in range(nd)]
+    bfull = [_Barrier(ngen) for _ in range(nb)]
+    bempty = [_Barrier(1) for _ in range(nb)]
+    done = _Barrier(niss)
+    prod, t = [], 0
+    for sl, n in enumerate(per_slab):
+        prod.append(("slab", sl))
+        for _ in range(n):
+            prod.append(("dvec", t))
+            t += 1
+    iss = []
+    for w in range(niss):
+        prog, t = [], 0
+        for sl, n in enumerate(per_slab):
+            prog.append(("wslab", sl))
+            for _ in range(n):
+                if t % niss == w:
+                    prog.append(("wmat", t))
+                t += 1
+            prog.append(("cslab", sl))
+        prog.append(("done", 0))
+        iss.append(prog)
+    gen = [[(step, k) for k in range(tot) for step in ("wd", "wb")] for _ in range(ngen)]
+    progs = [prod] + iss + gen
+    pc = [0] * len(progs)
+    pending = []
+    for _ in range(10 ** 7):
+        actors = [a for a in range(len(progs)) if pc[a] < len(progs[a])]
+        if not actors and not pending:
+            assert done.phase == 1
+            return
+        choice = rnd.randrange(len(actors) + (1 if pending else 0))
+        if choice == len(actors):
+            pending.pop(rnd.randrange(len(pending))).arrive()
+            continue
+        a = actors[choice]
+        kind, i = progs[a][pc[a]]
+        if a == 0:
+            if kind == "slab":
+                if sempty[i & 1].parity_wait((i >> 1) - 1):
+                    pending.append(sfull[i & 1]); pc[a] += 1
+            elif dempty[i % nd].parity_wait(i // nd - 1):
+                pending.append(dfull[i % nd]); pc[a] += 1
+        elif a <= niss:
+            if kind == "wslab":
+                if sfull[i & 1].parity_wait(i >> 1):
+                    pc[a] += 1
+            elif kind == "wmat":
+                if bfull[i % nb].parity_wait(i // nb):
+                    pending.append(bempty[i % nb]); pc[a] += 1
+            elif kind == "cslab":
+                pending.append(sempty[i & 1]); pc[a] += 1
+            else:
+                pending.append(done); pc[a] += 1
+        else:
+            if kind == "wd":
+                if dfull[i % nd].parity_wait(i // nd):
+                    dempty[i % nd].arrive(); pc[a] += 1
+            elif bempty[i % nb].parity_wait(i // nb - 1):
+                bfull[i % nb].arrive(); pc[a] += 1
+    raise AssertionError("no progress: deadlock")
+
+
+@pytest.mark.parametrize("niss,nb", [(1, 2), (1, 3), (1, 4), (2, 2), (2, 4)])
+def test_onchip_matrix_protocol_is_safe(niss, nb):
+    for seed in range(60):
+        _simulate_gen(niss, nb, 8, 4, seed, nslab=10)
