@@ -44,6 +44,7 @@ _lib = None
 
 SYM = 0
 TRACELESS = 1
+TG = 2          # fmm_uniform only: symmetric multipoles, traceless locals (the TG variant)
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -98,6 +99,7 @@ def lib():
         L.orc_adaptive_tree.restype = ctypes.c_int64
         L.orc_ncols_labels.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_m2m_fused.argtypes = [ctypes.c_int, _dp, _dp, _dp]
         L.orc_p2m_dipole.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64] + [_dp] * 8
         L.orc_direct_dipole.argtypes = [ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int64, _i64p] + [_dp] * 4
         L.orc_fmm_uniform_dipole.argtypes = [ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int] * 3 + \
@@ -174,6 +176,14 @@ def p2m(p: int, basis: int, x, y, z, q, zc) -> np.ndarray:
     x, y, z, q, zc = (_f64(v) for v in (x, y, z, q, zc))
     out = np.zeros(ncoef(p, basis))
     lib().orc_p2m(p, basis, len(x), _d(x), _d(y), _d(z), _d(q), _d(zc), _d(out))
+    return out
+
+
+def m2m_fused(p: int, M: np.ndarray, delta) -> np.ndarray:
+    """Traceless M2M in the fused form of Eq. Detracer2 (traceless storage)."""
+    M, delta = _f64(M), _f64(delta)
+    out = np.zeros(ncoef(p, TRACELESS))
+    lib().orc_m2m_fused(p, _d(M), _d(delta), _d(out))
     return out
 
 

@@ -316,6 +316,55 @@ void orc_m2m(int p, int basis, const double* Mc, const double delta[3], double* 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Fused traceless M2M (Eq. Detracer2, Sec. 2.1): the shift of Eq. M2M part  */
+/* 2 inserted into the detracer of Eq. M2M and the terms regrouped by the    */
+/* multipole component q.  Read (its printed symbols are partly garbled) as  */
+/* the form that equals D[shift]: with j = n + 2k - 2m - q,                   */
+/*   Mbar'_n = 1/(2n-1)!! sum_{|q| <= |n|} (Mbar_q / q!)                      */
+/*             sum_{m <= floor(n/2)} f_{n,m} sum_{|k| = |m|} (|m|!/k!)        */
+/*             ((j + q)!/j!) (-delta)^j          (terms with j >= 0)          */
+/* whose q = 0 term is Mbar_0 D[(-delta)^n]_n.  Mbar_q runs over every        */
+/* component (dependent ones from the trace condition).  Traceless storage  */
+/* in and out; the independent outputs are added into Mp.                   */
+/* ------------------------------------------------------------------------ */
+void orc_m2m_fused(int p, const double* Mc, const double delta[3], double* Mp) {
+    orc_init();
+    int ns = orc_ncoef_sym(p), nt = orc_ncoef_tl(p);
+    double Ms[NS_MAX];
+    tl_to_sym(p, Mc, Ms);
+    double md[3] = {-delta[0], -delta[1], -delta[2]};
+    for (int t = 0; t < nt; ++t) {
+        const int* n = g_tl[t];
+        int nn = n[0] + n[1] + n[2];
+        double s = 0.0;
+        for (int iq = 0; iq < ns; ++iq) {
+            const int* q = g_sym[iq];
+            if (q[0] + q[1] + q[2] > nn) continue;
+            double inner = 0.0;
+            for (int mx = 0; mx <= n[0] / 2; ++mx)
+                for (int my = 0; my <= n[1] / 2; ++my)
+                    for (int mz = 0; mz <= n[2] / 2; ++mz) {
+                        int m[3] = {mx, my, mz};
+                        int mm = mx + my + mz;
+                        double fm = f_nm(n, m);
+                        for (int kx = mm; kx >= 0; --kx)
+                            for (int ky = mm - kx; ky >= 0; --ky) {
+                                int kz = mm - kx - ky;
+                                int j[3] = {n[0] + 2 * kx - 2 * mx - q[0], n[1] + 2 * ky - 2 * my - q[1],
+                                            n[2] + 2 * kz - 2 * mz - q[2]};
+                                if (j[0] < 0 || j[1] < 0 || j[2] < 0) continue;
+                                double w = fm * g_fact[mm] / mfact(kx, ky, kz) *
+                                           mfact(j[0] + q[0], j[1] + q[1], j[2] + q[2]) / mfact(j[0], j[1], j[2]);
+                                inner += w * ipow(md[0], j[0]) * ipow(md[1], j[1]) * ipow(md[2], j[2]);
+                            }
+                    }
+            s += Ms[iq] / mfact(q[0], q[1], q[2]) * inner;
+        }
+        Mp[t] += s / dfact_odd(nn);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* M2L (Eq. M2L, Sec. 2.1):                                                  */
 /*   L_n(z' = z + r) += sum_{|m| <= p-|n|} (1/m!) M_m(z) D_{n+m}(r)           */
 /* D is the full symmetric D-tensor up to rank p (orc_dtensor).              */
@@ -547,10 +596,16 @@ static int fmm_uniform_impl(int64_t n, const double* x, const double* y, const d
                             int64_t nsample, const int64_t* sample, double* pot, double* ax, double* ay,
                             double* az) {
     orc_init();
-    if (p < 0 || p > ORC_PMAX || depth < 0 || depth > 10) return -1;
+    if (p < 0 || p > ORC_PMAX || depth < 0 || depth > 10 || basis < 0 || basis > 2) return -1;
     int side = 1 << depth;
     int64_t nleaf = (int64_t)side * side * side;
-    int nc = orc_ncoef(p, basis);
+    /* basis 2, the TG variant (Sec. 3): multipoles in full symmetric storage
+       (P2M, M2M without a detracer), M2L from them to a traceless local
+       expansion (D is traceless, so is L; its independent components are
+       kept), L2L and L2P on traceless storage */
+    const int tg = basis == 2;
+    const int bM = tg ? 0 : basis, bL = tg ? 1 : basis;
+    int nc = orc_ncoef(p, bM) > orc_ncoef(p, bL) ? orc_ncoef(p, bM) : orc_ncoef(p, bL);
     uni_t U;
     U.depth = depth; U.p = p; U.basis = basis; U.nc = nc; U.n = n;
     U.x = x; U.y = y; U.z = z; U.q = q;
@@ -609,14 +664,14 @@ static int fmm_uniform_impl(int64_t n, const double* x, const double* y, const d
             int64_t i = U.order[b + a];
             buf[a] = x[i]; buf[cnt + a] = y[i]; buf[2 * cnt + a] = z[i]; buf[3 * cnt + a] = q[i];
         }
-        orc_p2m(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, buf + 3 * cnt, zc, U.M[depth] + c * nc);
+        orc_p2m(p, bM, cnt, buf, buf + cnt, buf + 2 * cnt, buf + 3 * cnt, zc, U.M[depth] + c * nc);
         if (px) {
             double* pb = (double*)malloc(sizeof(double) * 3 * cnt);
             for (int64_t a = 0; a < cnt; ++a) {
                 int64_t i = U.order[b + a];
                 pb[a] = px[i]; pb[cnt + a] = py[i]; pb[2 * cnt + a] = pz[i];
             }
-            orc_p2m_dipole(p, basis, cnt, buf, buf + cnt, buf + 2 * cnt, pb, pb + cnt, pb + 2 * cnt, zc,
+            orc_p2m_dipole(p, bM, cnt, buf, buf + cnt, buf + 2 * cnt, pb, pb + cnt, pb + 2 * cnt, zc,
                            U.M[depth] + c * nc);
             free(pb);
         }
@@ -635,7 +690,7 @@ static int fmm_uniform_impl(int64_t n, const double* x, const double* y, const d
                 double zch[3], d[3];
                 cell_centre(l + 1, cx, cy, cz, zch);
                 d[0] = zch[0] - zp[0]; d[1] = zch[1] - zp[1]; d[2] = zch[2] - zp[2];
-                orc_m2m(p, basis, U.M[l + 1] + cell_id(l + 1, cx, cy, cz) * nc, d, U.M[l] + c * nc);
+                orc_m2m(p, bM, U.M[l + 1] + cell_id(l + 1, cx, cy, cz) * nc, d, U.M[l] + c * nc);
             }
         }
     }
@@ -659,7 +714,14 @@ static int fmm_uniform_impl(int64_t n, const double* x, const double* y, const d
                         double zs[3], r[3];
                         cell_centre(l, jx, jy, jz, zs);
                         r[0] = zt[0] - zs[0]; r[1] = zt[1] - zs[1]; r[2] = zt[2] - zs[2];
-                        orc_m2l(p, basis, U.M[l] + cell_id(l, jx, jy, jz) * nc, r, U.L[l] + c * nc);
+                        if (tg) {
+                            double Ls[NS_MAX];
+                            for (int i = 0; i < NS_MAX; ++i) Ls[i] = 0.0;
+                            orc_m2l(p, 0, U.M[l] + cell_id(l, jx, jy, jz) * nc, r, Ls);
+                            add_out(p, 1, Ls, U.L[l] + c * nc);
+                        } else {
+                            orc_m2l(p, basis, U.M[l] + cell_id(l, jx, jy, jz) * nc, r, U.L[l] + c * nc);
+                        }
                     }
         }
     }
@@ -676,7 +738,7 @@ static int fmm_uniform_impl(int64_t n, const double* x, const double* y, const d
             cell_centre(l, ix, iy, iz, zc);
             cell_centre(l - 1, ix >> 1, iy >> 1, iz >> 1, zp);
             d[0] = zc[0] - zp[0]; d[1] = zc[1] - zp[1]; d[2] = zc[2] - zp[2];
-            orc_l2l(p, basis, U.L[l - 1] + cell_id(l - 1, ix >> 1, iy >> 1, iz >> 1) * nc, d,
+            orc_l2l(p, bL, U.L[l - 1] + cell_id(l - 1, ix >> 1, iy >> 1, iz >> 1) * nc, d,
                     U.L[l] + c * nc);
         }
     }
@@ -689,7 +751,7 @@ static int fmm_uniform_impl(int64_t n, const double* x, const double* y, const d
         double zc[3], rb[3], o[4] = {0.0, 0.0, 0.0, 0.0};
         cell_centre(depth, ix, iy, iz, zc);
         rb[0] = x[i] - zc[0]; rb[1] = y[i] - zc[1]; rb[2] = z[i] - zc[2];
-        if (depth >= 2) orc_l2p(p, basis, U.L[depth] + cell_id(depth, ix, iy, iz) * nc, rb, o);
+        if (depth >= 2) orc_l2p(p, bL, U.L[depth] + cell_id(depth, ix, iy, iz) * nc, rb, o);
         double ph = o[0], gx = o[1], gy = o[2], gz = o[3];
         for (int jz = iz - 1; jz <= iz + 1; ++jz)
             for (int jy = iy - 1; jy <= iy + 1; ++jy)

@@ -70,3 +70,16 @@ def test_ragged_and_empty_leaves():
     pot_ref, acc_ref = oracle.direct(x, y, z, q)
     pot, acc = oracle.fmm_uniform(x, y, z, q, 3, 8, TL)
     assert rel_force_err(acc, acc_ref) < 2e-4
+
+
+@pytest.mark.parametrize("p", [3, 6])
+def test_tg_variant_equals_symmetric_and_traceless(p):
+    """The TG variant (symmetric multipoles, traceless locals; Sec. 3) gives
+    the field of the SYM and FT variants (equal in exact arithmetic)."""
+    n, depth = 2500, 3
+    x, y, z = inputs.uniform_cube(n, 81)
+    q = inputs.masses_open_unit(n, 81)
+    res = [oracle.fmm_uniform(x, y, z, q, depth, p, b) for b in (oracle.SYM, oracle.TRACELESS, oracle.TG)]
+    for pot, acc in res[1:]:
+        assert np.linalg.norm(pot - res[0][0]) <= 1e-13 * np.linalg.norm(res[0][0])
+        assert np.linalg.norm(acc - res[0][1]) <= 1e-13 * np.linalg.norm(res[0][1])

@@ -229,3 +229,22 @@ def test_direct_two_body_and_momentum():
     pt, at = oracle.direct(x, y, z, q, t)
     np.testing.assert_array_equal(pt, pot[t])
     np.testing.assert_array_equal(at, acc[:, t])
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 5, 8])
+def test_fused_m2m_is_exact(p):
+    """Eq. Detracer2 (fused traceless M2M): P2M at a child centre followed by
+    the fused M2M equals P2M at the parent centre, as the M2M of Eq. M2M
+    does (the shift is exact; App. B)."""
+    rng = np.random.default_rng(90 + p)
+    n = 9
+    x, y, z = rng.uniform(-0.2, 0.2, (3, n)) + 0.3
+    q = rng.uniform(0.1, 1.0, n)
+    zc = np.array([0.3, 0.31, 0.29])
+    zp = np.array([0.2, 0.45, 0.1])
+    Mc = oracle.p2m(p, oracle.TRACELESS, x, y, z, q, zc)
+    Mref = oracle.p2m(p, oracle.TRACELESS, x, y, z, q, zp)
+    Mf = oracle.m2m_fused(p, Mc, zc - zp)
+    assert np.abs(Mf - Mref).max() <= 1e-13 * max(np.abs(Mref).max(), 1.0)
+    Mu = oracle.m2m(p, oracle.TRACELESS, Mc, zc - zp)
+    assert np.abs(Mf - Mu).max() <= 1e-13 * max(np.abs(Mu).max(), 1.0)
