@@ -57,7 +57,11 @@ typedef enum {
     FMM_ERR_UNSUPPORTED = -6  /* valid but not implemented combination      */
 } fmm_status;
 
-typedef enum { FMM_BASIS_SYM = 0, FMM_BASIS_TRACELESS = 1 } fmm_basis;
+/* FMM_BASIS_TG (plans only; uniform octree, FMM_FP64): the paper's TG
+ * variant (Sec. 3), multipoles in full symmetric storage (P2M and M2M
+ * without a detracer), M2L from them to traceless local expansions (D is
+ * traceless, so is L), L2L and L2P on traceless storage. */
+typedef enum { FMM_BASIS_SYM = 0, FMM_BASIS_TRACELESS = 1, FMM_BASIS_TG = 2 } fmm_basis;
 
 typedef enum {
     FMM_FP64 = 0,        /* every operator in FP64                                     */
@@ -248,6 +252,20 @@ int fmm_op_m2m(int p, int basis, int prec, int64_t n, const void* Mc, const doub
  * r = z_target - z_source, nonzero.  accumulate = 0 overwrites L. */
 int fmm_op_m2l(int p, int basis, int prec, int64_t n, const void* M, const double* r,
                void* L, int accumulate, void* stream);
+
+/* M2M of traceless multipoles in the fused form of Eq. Detracer2 (Sec. 2.1):
+ * the shift inserted into the detracer and regrouped by multipole
+ * component, evaluated from a table of (coefficient, component, power)
+ * terms built once per order.  Mp[:,i] += shifted Mc[:,i], delta[:,i] =
+ * z_child - z_parent; Mc, Mp: [(p+1)^2][n] doubles in traceless storage
+ * (distinct arrays); delta: [3][n].  Computes what fmm_op_m2m computes for
+ * FMM_BASIS_TRACELESS, FMM_FP64.  The first call for an order on a device
+ * allocates and uploads its table (synchronous). */
+int fmm_op_m2m_fused(int p, int64_t n, const double* Mc, const double* delta, double* Mp,
+                     void* stream);
+/* Number of terms of the fused M2M table of order p (no GPU needed), or
+ * FMM_ERR_ARG. */
+int fmm_m2m_fused_terms(int p);
 
 /* L2L (Eq. L2L, Sec. 2.1): Lc[:,i] += shift of Lp[:,i] by
  * delta[:,i] = z_child - z_parent.  Lp, Lc: [ncoef][n] (distinct arrays) of

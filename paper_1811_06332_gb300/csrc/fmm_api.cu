@@ -82,6 +82,11 @@ struct fmm_plan {
 
 static bool is_tc(int prec) { return prec == FMM_GEMM_BF16X3 || prec == FMM_GEMM_TF32X3; }
 
+// storage basis of the multipoles and of the local expansions (the TG
+// basis: symmetric multipoles, traceless locals; Sec. 3)
+static int bM(const fmm_plan* pl) { return pl->cfg.basis == FMM_BASIS_TG ? 0 : pl->cfg.basis; }
+static int bL(const fmm_plan* pl) { return pl->cfg.basis == FMM_BASIS_TG ? 1 : pl->cfg.basis; }
+
 static void* tc_maps_at(fmm_plan* pl, int l) {
     // 64-byte aligned block of the host-side tensor maps of level l
     uintptr_t b = ((uintptr_t)pl->maps.data() + 63) & ~(uintptr_t)63;
@@ -368,6 +373,26 @@ int fmm_op_m2m(int p, int basis, int prec, int64_t n, const void* Mc, const doub
     return FMM_OK;
 }
 
+int fmm_op_m2m_fused(int p, int64_t n, const double* Mc, const double* delta, double* Mp, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (p < 0 || p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    if (n < 0) FAIL(FMM_ERR_ARG, "n < 0");
+    if (n > 0 && (!Mc || !delta || !Mp)) FAIL(FMM_ERR_ARG, "null array");
+    if (n > 0 && Mc == Mp) FAIL(FMM_ERR_ARG, "Mc and Mp must be distinct");
+    int dev;
+    if (int rc = tables_for_current(pl, &dev)) return rc;
+    const int r = launch_m2m_fused(p, n, Mc, delta, Mp, g_tab[dev], S(stream));
+    if (r == -3) FAIL(FMM_ERR_OOM, "allocating the fused M2M table failed");
+    if (r) FAIL(FMM_ERR_CUDA, "uploading the fused M2M table failed");
+    CKLAUNCH();
+    return FMM_OK;
+}
+
+int fmm_m2m_fused_terms(int p) {
+    if (p < 0 || p > FMM_PMAX) return fail_plan(nullptr, FMM_ERR_ARG, "p=%d outside 0..%d", p, FMM_PMAX);
+    return m2m_fused_terms(p);
+}
+
 int fmm_op_l2l(int p, int basis, int prec, int64_t n, const void* Lp, const double* delta, void* Lc,
                void* stream) {
     fmm_plan* pl = nullptr;
@@ -507,7 +532,10 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     *out = nullptr;
     if (!cfg) FAIL(FMM_ERR_ARG, "cfg is NULL");
     if (cfg->p < 0 || cfg->p > FMM_PMAX) FAIL(FMM_ERR_ARG, "p=%d outside 0..%d", cfg->p, FMM_PMAX);
-    if (cfg->basis != 0 && cfg->basis != 1) FAIL(FMM_ERR_ARG, "unknown basis %d", cfg->basis);
+    if (cfg->basis != 0 && cfg->basis != 1 && cfg->basis != FMM_BASIS_TG)
+        FAIL(FMM_ERR_ARG, "unknown basis %d", cfg->basis);
+    if (cfg->basis == FMM_BASIS_TG && (cfg->adaptive || cfg->prec != FMM_FP64))
+        FAIL(FMM_ERR_UNSUPPORTED, "FMM_BASIS_TG needs a uniform octree and FMM_FP64");
     if (cfg->prec < FMM_FP64 || cfg->prec > FMM_GEMM_BF16X3) FAIL(FMM_ERR_ARG, "unknown precision %d", cfg->prec);
     if (cfg->adaptive) {
         if (cfg->max_leaf < 1) FAIL(FMM_ERR_ARG, "max_leaf=%d must be >= 1", cfg->max_leaf);
@@ -532,7 +560,9 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     }
     pl->depth = cfg->depth;
     pl->nleaf = (int64_t)1 << (3 * cfg->depth);
-    pl->nc = ncoef_of(cfg->p, cfg->basis);
+    // storage per coefficient row: the TG basis keeps symmetric multipoles and
+    // traceless locals (a prefix of the rows of the same arrays)
+    pl->nc = ncoef_of(cfg->p, cfg->basis == FMM_BASIS_TG ? 0 : cfg->basis);
     pl->ns = ns_of(cfg->p);
     int dev;
     if (int rc = tables_for_current(pl, &dev)) { fmm_destroy(pl); return rc; }
@@ -548,9 +578,13 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         return FMM_OK;
     }
     std::vector<double> W, V;
-    build_translation(cfg->p, cfg->basis, W, V);
-    const size_t mb = W.size() * sizeof(double);
-    if (cudaMalloc(&pl->W, mb) != cudaSuccess || cudaMalloc(&pl->V, mb) != cudaSuccess ||
+    build_translation(cfg->p, bM(pl), W, V);
+    if (cfg->basis == FMM_BASIS_TG) {
+        std::vector<double> W1;
+        build_translation(cfg->p, 1, W1, V);   // L2L on traceless locals
+    }
+    const size_t mb = W.size() * sizeof(double), vb = V.size() * sizeof(double);
+    if (cudaMalloc(&pl->W, mb) != cudaSuccess || cudaMalloc(&pl->V, vb) != cudaSuccess ||
         cudaMalloc(&pl->Dtab, (size_t)343 * pl->ns * sizeof(double)) != cudaSuccess) {
         fmm_destroy(pl);
         return fail_plan(nullptr, FMM_ERR_OOM, "allocating operator matrices failed");
@@ -565,7 +599,7 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     }
     double* doffs = nullptr;
     bool ok = cudaMemcpy(pl->W, W.data(), mb, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(pl->V, V.data(), mb, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(pl->V, V.data(), vb, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMalloc(&doffs, offs.size() * sizeof(double)) == cudaSuccess &&
               cudaMemcpy(doffs, offs.data(), offs.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok) {
@@ -735,7 +769,7 @@ int fmm_p2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
     if (pl->ad) { ad_run_p2m(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     const int d = pl->depth;
-    launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, d, pl->nleaf, pl->start, pl->xs,
+    launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, bM(pl), d, pl->nleaf, pl->start, pl->xs,
                     pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32);
     CKLAUNCH();
     return FMM_OK;
@@ -754,7 +788,7 @@ int fmm_m2m(fmm_plan* pl, void* stream) {
         return FMM_OK;
     }
     for (int l = pl->depth - 1; l >= 2; --l)
-        launch_m2m_level(pl->cfg.p, pl->cfg.basis, l, pl->W, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
+        launch_m2m_level(pl->cfg.p, bM(pl), l, pl->W, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
                          Mlev(pl, l), (int64_t)1 << (3 * l), S(stream));
     CKLAUNCH();
     return FMM_OK;
@@ -852,7 +886,7 @@ int fmm_l2l(fmm_plan* pl, void* stream) {
         return FMM_OK;
     }
     for (int l = 2; l < pl->depth; ++l)
-        launch_l2l_level(pl->cfg.p, pl->cfg.basis, l, pl->V, Llev(pl, l), (int64_t)1 << (3 * l), Llev(pl, l + 1),
+        launch_l2l_level(pl->cfg.p, bL(pl), l, pl->V, Llev(pl, l), (int64_t)1 << (3 * l), Llev(pl, l + 1),
                          (int64_t)1 << (3 * (l + 1)), S(stream));
     CKLAUNCH();
     return FMM_OK;
@@ -867,7 +901,7 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
         return FMM_OK;
     }
     if (pl->depth >= 2)
-        launch_l2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, pl->depth, pl->nleaf,
+        launch_l2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, bL(pl), pl->depth, pl->nleaf,
                          pl->start, pl->xs, pl->ys, pl->zs, pl->perm, Llev(pl, pl->depth), g_tab[pl->dev], pot, ax,
                          ay, az, S(stream), pl->pos32);
     else
@@ -956,7 +990,7 @@ int fmm_evaluate_dipoles(fmm_plan* pl, int64_t n, const double* x, const double*
     const int d = pl->depth;
     // P2M of charges and dipoles (the general P2M kernel writes the plan's
     // scaled leaf multipoles; traceless: the reduced representative)
-    launch_p2m(pl->cfg.p, pl->cfg.basis, 1, pl->nleaf, nullptr, pl->start, pl->xs, pl->ys, pl->zs, pl->qs, nullptr, d,
+    launch_p2m(pl->cfg.p, bM(pl), 1, pl->nleaf, nullptr, pl->start, pl->xs, pl->ys, pl->zs, pl->qs, nullptr, d,
                (double)(1 << d), Mlev(pl, d), pl->nleaf, g_tab[pl->dev], s, pxs, pys, pzs);
     CKLAUNCH();
     if ((rc = fmm_m2m(pl, stream))) return rc;

@@ -1,5 +1,8 @@
 // General-shift M2M, L2L, L2P (operator-level entry points, FP64 or FP32
 // storage and arithmetic) and the FP64 direct sum.
+#include <cmath>
+#include <vector>
+
 #include "fmm_internal.h"
 
 namespace fmm {
@@ -217,6 +220,144 @@ int launch_l2p_general(int prec, int p, int basis, int64_t n, const void* L, con
                                                gtab<float>(T.expand, T.expand32), T.offsets());
     count_launch();
     return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Fused traceless M2M (Eq. Detracer2, Sec. 2.1): the shift inserted into the
+// detracer and regrouped by multipole component q; with j = n + 2k - 2m - q
+//   Mbar'_n = sum_q Mbar_q sum_j c_{n,q,j} (-delta)^j,
+//   c_{n,q,j} = 1/((2n-1)!! q!) sum_{m <= floor(n/2), |k| = |m|} f_{n,m} (|m|!/k!) (j+q)!/j!
+// (the regrouping that reproduces D[shift]).  The coefficients are a table of
+// (c, q, j) terms per output row, built once per order on the host; one warp
+// per item, lanes over the output rows, FP64.
+// ---------------------------------------------------------------------------
+struct FusedTerm {
+    double c;
+    uint16_t q;            // symmetric position of the multipole component
+    uint8_t jx, jy, jz, pad;
+};
+
+__global__ void __launch_bounds__(128)
+k_m2m_fused(int p, int64_t n, const double* __restrict__ Mc, const double* __restrict__ delta,
+            double* __restrict__ Mp, const double* __restrict__ expand, DevOffsets off,
+            const int* __restrict__ toff, const FusedTerm* __restrict__ terms) {
+    __shared__ double sX[4][FMM_NS_MAX], sA[4][FMM_NT_MAX];
+    __shared__ double sP[4][3][FMM_PMAX + 1];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 4 + w;
+    if (i >= n) return;
+    const int nt = nt_of(p);
+    for (int t = lane; t < nt; t += 32) sA[w][t] = Mc[(int64_t)t * n + i];
+    __syncwarp();
+    expand_tl_warp_t<double>(p, sA[w], sX[w], expand, off, lane);
+    if (lane < 3) {
+        const double md = -delta[(int64_t)lane * n + i];
+        double v = 1.0;
+        sP[w][lane][0] = 1.0;
+        for (int k = 1; k <= p; ++k) { v *= md; sP[w][lane][k] = v; }
+    }
+    __syncwarp();
+    for (int t = lane; t < nt; t += 32) {
+        double v = 0.0;
+        for (int e = toff[t]; e < toff[t + 1]; ++e) {
+            const FusedTerm T = terms[e];
+            v += T.c * sX[w][T.q] * sP[w][0][T.jx] * sP[w][1][T.jy] * sP[w][2][T.jz];
+        }
+        Mp[(int64_t)t * n + i] += v;
+    }
+}
+
+// Host: the term table of order p (rows in traceless order).
+static void fused_table(int p, std::vector<int>& toff, std::vector<FusedTerm>& terms) {
+    auto fact = [](int k) { double f = 1; for (int i = 2; i <= k; ++i) f *= i; return f; };
+    auto mf = [&](int a, int b, int c) { return fact(a) * fact(b) * fact(c); };
+    auto dfo = [](int k) { double v = 1; for (int i = 2 * k - 1; i > 1; i -= 2) v *= i; return v; };
+    const int nt = nt_of(p), ns = ns_of(p);
+    toff.assign(1, 0);
+    terms.clear();
+    std::vector<double> acc;
+    for (int t = 0; t < nt; ++t) {
+        const unsigned char* nn = fmm_tl_idx[t];
+        const int n[3] = {nn[0], nn[1], nn[2]}, an = n[0] + n[1] + n[2];
+        for (int iq = 0; iq < ns; ++iq) {
+            const unsigned char* qq = fmm_sym_idx[iq];
+            const int q[3] = {qq[0], qq[1], qq[2]};
+            if (q[0] + q[1] + q[2] > an) continue;
+            // accumulate c_{n,q,j} over (m, k) for each j (indexed by j's symmetric position)
+            acc.assign(ns, 0.0);
+            for (int mx = 0; mx <= n[0] / 2; ++mx)
+                for (int my = 0; my <= n[1] / 2; ++my)
+                    for (int mz = 0; mz <= n[2] / 2; ++mz) {
+                        const int mm = mx + my + mz;
+                        double f = dfo(an - mm) * mf(n[0], n[1], n[2]) /
+                                   (std::ldexp(1.0, mm) * mf(mx, my, mz) * mf(n[0] - 2 * mx, n[1] - 2 * my, n[2] - 2 * mz));
+                        if (mm & 1) f = -f;
+                        for (int kx = 0; kx <= mm; ++kx)
+                            for (int ky = 0; ky <= mm - kx; ++ky) {
+                                const int kz = mm - kx - ky;
+                                const int j[3] = {n[0] + 2 * kx - 2 * mx - q[0], n[1] + 2 * ky - 2 * my - q[1],
+                                                  n[2] + 2 * kz - 2 * mz - q[2]};
+                                if (j[0] < 0 || j[1] < 0 || j[2] < 0) continue;
+                                acc[pos_sym(j[0], j[1], j[2])] += f * fact(mm) / mf(kx, ky, kz) *
+                                                                 mf(j[0] + q[0], j[1] + q[1], j[2] + q[2]) /
+                                                                 mf(j[0], j[1], j[2]);
+                            }
+                    }
+            const double sc = 1.0 / (dfo(an) * mf(q[0], q[1], q[2]));
+            for (int ij = 0; ij < ns; ++ij) {
+                if (acc[ij] == 0.0) continue;
+                FusedTerm T;
+                T.c = acc[ij] * sc;
+                T.q = (uint16_t)iq;
+                T.jx = fmm_sym_idx[ij][0];
+                T.jy = fmm_sym_idx[ij][1];
+                T.jz = fmm_sym_idx[ij][2];
+                T.pad = 0;
+                terms.push_back(T);
+            }
+        }
+        toff.push_back((int)terms.size());
+    }
+}
+
+int launch_m2m_fused(int p, int64_t n, const double* Mc, const double* delta, double* Mp, const DevTables& T,
+                     cudaStream_t s) {
+    // term tables per device and order, uploaded once
+    static int* d_off[64][FMM_PMAX + 1];
+    static FusedTerm* d_terms[64][FMM_PMAX + 1];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -2;
+    if (!d_off[dev][p]) {
+        std::vector<int> toff;
+        std::vector<FusedTerm> terms;
+        fused_table(p, toff, terms);
+        int* o = nullptr;
+        FusedTerm* tm = nullptr;
+        if (cudaMalloc(&o, toff.size() * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&tm, (terms.size() + 1) * sizeof(FusedTerm)) != cudaSuccess) {
+            cudaFree(o);
+            return -3;
+        }
+        if (cudaMemcpy(o, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            (!terms.empty() &&
+             cudaMemcpy(tm, terms.data(), terms.size() * sizeof(FusedTerm), cudaMemcpyHostToDevice) != cudaSuccess))
+            return -2;
+        d_off[dev][p] = o;
+        d_terms[dev][p] = tm;
+    }
+    if (n <= 0) return 0;
+    k_m2m_fused<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(p, n, Mc, delta, Mp, T.expand, T.offsets(), d_off[dev][p],
+                                                         d_terms[dev][p]);
+    count_launch();
+    return 0;
+}
+
+// number of (c, q, j) terms of the fused table of order p (host)
+int m2m_fused_terms(int p) {
+    std::vector<int> toff;
+    std::vector<FusedTerm> terms;
+    fused_table(p, toff, terms);
+    return (int)terms.size();
 }
 
 // ---------------------------------------------------------------------------

@@ -90,6 +90,10 @@ int launch_l2l_general(int prec, int p, int basis, int64_t n, const void* Lp, co
                        const DevTables& T, cudaStream_t s);
 int launch_l2p_general(int prec, int p, int basis, int64_t n, const void* L, const double* rb, void* out,
                        const DevTables& T, cudaStream_t s);
+// fused traceless M2M of Eq. Detracer2 (FP64); 0 ok, -2 CUDA error, -3 allocation failure
+int launch_m2m_fused(int p, int64_t n, const double* Mc, const double* delta, double* Mp, const DevTables& T,
+                     cudaStream_t s);
+int m2m_fused_terms(int p);
 int launch_direct(int64_t n, const double* x, const double* y, const double* z, const double* q, int64_t nt,
                   const int64_t* targets, double* pot, double* ax, double* ay, double* az, cudaStream_t s);
 int launch_m2m_level(int p, int basis, int l, const double* W, const double* Mch, int64_t nch, double* Mpa,

@@ -38,11 +38,11 @@ __global__ void k_build_ktab64(int ns, int ksz, int kst, const unsigned char* __
 
 static int packed_size(int p, int basis) {
     int ksz = 0;
-    const int nc = ncoef_of(p, basis);
+    const int nc = ncoef_of(p, basis == 2 ? 1 : basis);
     for (int r = 0; r < nc; ++r) {
         const unsigned char* n = basis ? fmm_tl_idx[r] : fmm_sym_idx[r];
         const int rem = p - n[0] - n[1] - n[2];
-        ksz += basis ? nt_of(rem) : ns_of(rem);
+        ksz += basis == 1 ? nt_of(rem) : ns_of(rem);
     }
     return ksz;
 }
@@ -72,16 +72,17 @@ int launch_build_ktab(int p, int basis, int kst, const unsigned char* ent, const
 }
 
 // Host-side packed entry list in the generator's layout (rows in storage
-// order, each followed by its prefix of columns).
+// order, each followed by its prefix of columns).  basis 2 (the TG
+// variant): traceless rows, full symmetric columns.
 int grouped_entries(int p, int basis, unsigned char* out, int cap) {
-    const int nc = ncoef_of(p, basis);
+    const int nc = ncoef_of(p, basis == 2 ? 1 : basis);
     int e = 0;
     for (int r = 0; r < nc; ++r) {
         const unsigned char* n = basis ? fmm_tl_idx[r] : fmm_sym_idx[r];
         const int rem = p - n[0] - n[1] - n[2];
-        const int pre = basis ? nt_of(rem) : ns_of(rem);
+        const int pre = basis == 1 ? nt_of(rem) : ns_of(rem);
         for (int c = 0; c < pre; ++c) {
-            const unsigned char* m = basis ? fmm_tl_idx[c] : fmm_sym_idx[c];
+            const unsigned char* m = basis == 1 ? fmm_tl_idx[c] : fmm_sym_idx[c];
             if (e >= cap) return -1;
             unsigned char* o = out + 6 * e;
             o[0] = n[0]; o[1] = n[1]; o[2] = n[2]; o[3] = m[0]; o[4] = m[1]; o[5] = m[2];

@@ -393,8 +393,9 @@ def grouped_layout(p, basis):
     storage order, columns m = multipole components of rank <= p - |n|, which
     form a prefix of the storage order.  Returns (rows, prefix length per
     row, packed offset per row, packed size)."""
+    # basis 2 (the TG variant): traceless rows, full symmetric multipole columns
     rows = sym_list(p) if basis == 0 else tl_list(p)
-    pre = [(ns(p - sum(n)) if basis == 0 else nt(p - sum(n))) for n in rows]
+    pre = [(nt(p - sum(n)) if basis == 1 else ns(p - sum(n))) for n in rows]
     off = [0]
     for k in pre:
         off.append(off[-1] + k)
@@ -776,6 +777,8 @@ def emit_grouped_dispatch():
                      " cudaStream_t s, int groups, int bs);" % (p, b))
             L.append("int launch_m2l_grp64_p%d_b%d(int l, const double* M, double* Lt, const double* K,"
                      " int64_t ncell, cudaStream_t s, int groups, int bs);" % (p, b))
+        L.append("int launch_m2l_grp64_p%d_b2(int l, const double* M, double* Lt, const double* K,"
+                 " int64_t ncell, cudaStream_t s, int groups, int bs);" % p)
     L.append("// Levels with fewer target blocks than about four per SM split the offsets")
     L.append("// of every target over up to 27 blocks.")
     L.append("int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K,"
@@ -802,14 +805,14 @@ def emit_grouped_dispatch():
     L.append("  const int64_t hs = (int64_t)1 << (l - 1), blocks = 8 * ((hs * hs * hs + 127) / 128);")
     L.append("  const int bs = blocks >= 2 * (int64_t)sms ? 128 : 32;")
     for p in range(PMAX + 1):
-        for b in (0, 1):
+        for b in (0, 1, 2):
             L.append("  if (p == %d && basis == %d) return launch_m2l_grp64_p%d_b%d(l, M, Lt, K, ncell, s, 1, bs);"
                      % (p, b, p, b))
     L.append("  return -1;")
     L.append("}")
     L.append("int grouped_kstride(int p, int basis) {")
     for p in range(PMAX + 1):
-        for b in (0, 1):
+        for b in (0, 1, 2):
             L.append("  if (p == %d && basis == %d) return %d;" % (p, b, kstride(p, b)))
     L.append("  return -1;")
     L.append("}")
@@ -873,6 +876,9 @@ def generate(out=OUT):
             fg64 = os.path.join(out, "grp64_P%d_b%d.cu" % (p, basis))
             write_if_changed(fg64, emit_grouped_file(p, basis, "double"))
             files.append(fg64)
+        fg2 = os.path.join(out, "grp64_P%d_b2.cu" % p)
+        write_if_changed(fg2, emit_grouped_file(p, 2, "double"))
+        files.append(fg2)
     for p in range(0, PMAX + 1):
         for basis in (0, 1):
             fs = os.path.join(out, "shift_P%d_b%d.cu" % (p, basis))

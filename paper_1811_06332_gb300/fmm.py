@@ -16,14 +16,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STATE, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-BASIS_SYM, BASIS_TRACELESS = 0, 1
+BASIS_SYM, BASIS_TRACELESS, BASIS_TG = 0, 1, 2
 FP64, FP32, GEMM_TF32X3, GEMM_BF16X3 = 0, 1, 2, 3
 
 EXPORTS = [
     "fmm_ncoef", "fmm_create", "fmm_destroy", "fmm_last_error", "fmm_build_tree", "fmm_p2m", "fmm_m2m",
     "fmm_m2l", "fmm_m2l_levels", "fmm_tc_layout", "fmm_tc_gen_layout", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate",
     "fmm_evaluate_host", "fmm_evaluate_dipoles", "fmm_op_dtensor",
-    "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
+    "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2m_fused", "fmm_m2m_fused_terms", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
     "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_sync_status", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
     "fmm_mlp_grad", "fmm_mlp_train", "fmm_mlp_predict", "fmm_set_mlp", "fmm_set_pair_orders",
     "fmm_plan_pair_orders", "fmm_set_tc_shape", "fmm_plan_tuning", "fmm_tune_cache_get", "fmm_tune_cache_put",
@@ -75,6 +75,8 @@ def lib():
             "fmm_op_dtensor": ([_int, _int, _int, _i64, _vp, _vp, _vp], _int),
             "fmm_op_p2m": ([_int, _int, _i64] + [_vp] * 8, _int),
             "fmm_op_m2m": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_op_m2m_fused": ([_int, _i64, _vp, _vp, _vp, _vp], _int),
+            "fmm_m2m_fused_terms": ([_int], _int),
             "fmm_op_m2l": ([_int, _int, _int, _i64, _vp, _vp, _vp, _int, _vp], _int),
             "fmm_op_l2l": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
             "fmm_op_l2p": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
@@ -158,6 +160,11 @@ def fmm_op_m2m(p, basis, Mc, delta, Mp, stream=None):
     """FP64 or FP32 by the dtype of Mc (Mp must match)."""
     _check(lib().fmm_op_m2m(p, basis, _prec_of(Mc), Mc.shape[1], _ptr(Mc), _ptr(delta), _ptr(Mp),
                             _stream(stream)))
+
+
+def fmm_op_m2m_fused(p, Mc, delta, Mp, stream=None):
+    """Fused traceless M2M (Eq. Detracer2), FP64, traceless storage."""
+    _check(lib().fmm_op_m2m_fused(p, Mc.shape[1], _ptr(Mc), _ptr(delta), _ptr(Mp), _stream(stream)))
 
 
 def fmm_op_m2l(p, basis, prec, M, r, L, accumulate=False, stream=None):

@@ -338,3 +338,23 @@ def test_point_dipoles_vs_oracle(F, basis, depth, p):
     plan.close()
     with pytest.raises(F.FMMError):
         F.Plan(p=4, basis=basis, prec=F.FP32, depth=3).fmm_evaluate_dipoles(*X, out[0], out[1], out[2], out[3])
+
+
+@pytest.mark.parametrize("p,depth", [(4, 3), (8, 4)])
+def test_tg_basis_vs_oracle(F, p, depth):
+    """The TG variant (symmetric multipoles, traceless locals) in FP64 against
+    the oracle's TG FMM on the same tree (1e-12), and equal to the symmetric
+    basis up to rounding."""
+    n = 6000
+    x, y, z = inputs.uniform_cube(n, 90 + p)
+    q = inputs.masses_open_unit(n, 90 + p)
+    pot, acc = run(F, x, y, z, q, p, F.BASIS_TG, depth)
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, oracle.TG)
+    ep, ea, per = errs(pot, acc, pref, aref)
+    assert ep < 1e-12 and ea < 1e-12, (ep, ea)
+    ps, as_ = run(F, x, y, z, q, p, F.BASIS_SYM, depth)
+    ep, ea, _ = errs(pot, acc, ps, as_)
+    assert ep < 1e-12 and ea < 1e-12
+    for prec in (F.FP32, F.GEMM_BF16X3):
+        with pytest.raises(F.FMMError):
+            F.Plan(p=p, basis=F.BASIS_TG, prec=prec, depth=depth)

@@ -277,3 +277,31 @@ def test_empty_batches(F):
     F.fmm_op_m2m(4, 0, M, r, M.clone())
     F.fmm_direct(e, e, e, e, e, e, e, e)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 4, 7, 8, 10])
+def test_fused_m2m_vs_oracle(F, p):
+    """Eq. Detracer2 on the GPU (fmm_op_m2m_fused) against the oracle's fused
+    form and its shift-then-detrace M2M, 1e-12 per item and rank."""
+    rng = np.random.default_rng(200 + p)
+    ncell = 131
+    counts = rng.integers(1, 12, ncell)
+    start = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    cen = rng.uniform(-1, 1, (3, ncell))
+    pos = np.repeat(cen, counts, axis=1) + rng.uniform(-0.25, 0.25, (3, int(start[-1])))
+    q = rng.uniform(0.1, 1, int(start[-1]))
+    nc = oracle.ncoef(p, 1)
+    M = np.zeros((nc, ncell))
+    for c in range(ncell):
+        s, e = start[c], start[c + 1]
+        M[:, c] = oracle.p2m(p, 1, pos[0, s:e], pos[1, s:e], pos[2, s:e], q[s:e], cen[:, c])
+    delta = rng.uniform(-0.3, 0.3, (3, ncell))
+    base = inputs.random_coefficients(nc, ncell, 4)
+    ref = base + np.stack([oracle.m2m_fused(p, M[:, c], delta[:, c]) for c in range(ncell)], 1)
+    ref2 = base + np.stack([oracle.m2m(p, 1, M[:, c], delta[:, c]) for c in range(ncell)], 1)
+    Mp = g(base)
+    F.fmm_op_m2m_fused(p, g(M), g(delta), Mp)
+    got = Mp.cpu().numpy()
+    assert rank_err(got, ref, p, 1) < 1e-12
+    assert rank_err(got, ref2, p, 1) < 1e-12
+    assert F.lib().fmm_m2m_fused_terms(p) > 0
