@@ -100,6 +100,14 @@ def lib():
         L.orc_ncols_labels.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_m2m_fused.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+        for name in ("orc_fmm_adaptive_ap", "orc_fmm_adaptive_com"):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                          ctypes.c_int64, _i64p, _dp, _dp, _dp, _dp, _i64p]
+            f.restype = ctypes.c_int
+        L.orc_adaptive_tree_com.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_adaptive_tree_com.restype = ctypes.c_int64
         L.orc_p2m_dipole.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64] + [_dp] * 8
         L.orc_direct_dipole.argtypes = [ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int64, _i64p] + [_dp] * 4
         L.orc_fmm_uniform_dipole.argtypes = [ctypes.c_int64] + [_dp] * 7 + [ctypes.c_int] * 3 + \
@@ -379,19 +387,54 @@ def pair_error(p, src_xyzq, zA, zB, targets):
     return e
 
 
-def adaptive_tree(x, y, z, max_leaf: int, parents=False):
+def adaptive_tree(x, y, z, max_leaf: int, parents=False, com_q=None):
     """Nodes of the adaptive octree: (nn, 4) centre and radius, (nn, 2)
     sorted-position ranges, the sorted order of the particles and, on
-    request, each node's parent (-1 for the root)."""
+    request, each node's parent (-1 for the root).  With com_q (charges)
+    the centres are centres of mass (the AP variant's geometry)."""
     x, y, z = (_f64(v) for v in (x, y, z))
     n = len(x)
     L = lib()
-    nn = L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, 0, None, None, None, None)
+    if com_q is None:
+        call = lambda cap, *a: L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, cap, *a)  # noqa: E731
+    else:
+        qq = _f64(com_q)
+        call = lambda cap, *a: L.orc_adaptive_tree_com(n, _d(x), _d(y), _d(z), _d(qq), max_leaf, cap, *a)  # noqa: E731
+    nn = call(0, None, None, None, None)
     zr = np.zeros((nn, 4))
     rg = np.zeros((nn, 2), dtype=np.int64)
     order = np.zeros(n, dtype=np.int64)
     par = np.zeros(nn, dtype=np.int64)
-    got = L.orc_adaptive_tree(n, _d(x), _d(y), _d(z), max_leaf, nn, zr.ctypes.data, rg.ctypes.data,
-                              order.ctypes.data, par.ctypes.data)
+    got = call(nn, zr.ctypes.data, rg.ctypes.data, order.ctypes.data, par.ctypes.data)
     assert got == nn
     return (zr, rg, order, par) if parents else (zr, rg, order)
+
+
+def _adaptive_variant(fn, x, y, z, q, max_leaf, theta, p, sample):
+    x, y, z, q = (_f64(v) for v in (x, y, z, q))
+    n = len(x)
+    if sample is None:
+        ns, sp, nout = -1, None, n
+    else:
+        sample = np.ascontiguousarray(sample, dtype=np.int64)
+        ns, sp, nout = len(sample), sample.ctypes.data_as(_i64p), len(sample)
+    pot, ax, ay, az = (np.zeros(nout) for _ in range(4))
+    st = np.zeros(5, dtype=np.int64)
+    rc = fn(n, _d(x), _d(y), _d(z), _d(q), max_leaf, float(theta), p, ns, sp, _d(pot), _d(ax), _d(ay), _d(az),
+            st.ctypes.data_as(_i64p))
+    if rc != 0:
+        raise ValueError("adaptive FMM rejected its arguments (%d)" % rc)
+    keys = ("nodes", "m2l_pairs", "p2p_pairs", "leaves", "covered_pairs")
+    return pot, np.stack([ax, ay, az]), dict(zip(keys, st.tolist()))
+
+
+def fmm_adaptive_ap(x, y, z, q, max_leaf: int, theta: float, p: int, sample=None):
+    """The AP variant (Sec. 3): traceless, centre-of-mass centres, dipole 0,
+    gradient only (pot returned as 0)."""
+    return _adaptive_variant(lib().orc_fmm_adaptive_ap, x, y, z, q, max_leaf, theta, p, sample)
+
+
+def fmm_adaptive_com(x, y, z, q, max_leaf: int, theta: float, p: int, sample=None):
+    """The traceless adaptive FMM about centres of mass, dipole kept and the
+    potential evaluated (the FT variant on the AP tree)."""
+    return _adaptive_variant(lib().orc_fmm_adaptive_com, x, y, z, q, max_leaf, theta, p, sample)

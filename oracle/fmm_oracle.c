@@ -886,9 +886,15 @@ static void atree_free(atree_t* T) {
     memset(T, 0, sizeof(*T));
 }
 
-/* Octree, geometry and interaction lists as described above (n > 0). */
-static void atree_build(atree_t* T, int64_t n, const double* x, const double* y, const double* z, int max_leaf,
-                        double theta) {
+/* Octree, geometry and interaction lists as described above (n > 0).
+ * com != 0 (the AP variant, Sec. 3): expansion centres are centres of mass
+ * instead of geometric centres, computed bottom-up in a fixed order -- a
+ * leaf sums q_a x_a and q_a over its particles in sorted order, an inner
+ * cell sums Q_c z_c and Q_c over its children in octant order, z = S/Q --
+ * and a cell whose total charge is 0 keeps its geometric centre.  The
+ * radii and the traversal then use these centres. */
+static void atree_build(atree_t* T, int64_t n, const double* x, const double* y, const double* z, const double* q,
+                        int max_leaf, double theta, int com) {
     memset(T, 0, sizeof(*T));
     T->n = n;
     /* bounding cube */
@@ -953,6 +959,28 @@ static void atree_build(atree_t* T, int64_t n, const double* x, const double* y,
         nd[c].z[0] = lo[0] + (nd[c].ix + 0.5) * h;
         nd[c].z[1] = lo[1] + (nd[c].iy + 0.5) * h;
         nd[c].z[2] = lo[2] + (nd[c].iz + 0.5) * h;
+    }
+    if (com) {
+        double* Q = (double*)calloc(nn, sizeof(double));
+        for (int64_t c = nn - 1; c >= 0; --c) {   /* children follow parents: reverse order is bottom-up */
+            double S[3] = {0.0, 0.0, 0.0}, Qc = 0.0;
+            if (nd[c].nchild == 0) {
+                for (int64_t a = nd[c].b; a < nd[c].e; ++a) {
+                    const int64_t i = kv[a].idx;
+                    Qc += q[i];
+                    S[0] += q[i] * x[i]; S[1] += q[i] * y[i]; S[2] += q[i] * z[i];
+                }
+            } else {
+                for (int k = 0; k < nd[c].nchild; ++k) {
+                    const int64_t ch = nd[c].child0 + k;
+                    Qc += Q[ch];
+                    S[0] += Q[ch] * nd[ch].z[0]; S[1] += Q[ch] * nd[ch].z[1]; S[2] += Q[ch] * nd[ch].z[2];
+                }
+            }
+            Q[c] = Qc;
+            if (Qc != 0.0) { nd[c].z[0] = S[0] / Qc; nd[c].z[1] = S[1] / Qc; nd[c].z[2] = S[2] / Qc; }
+        }
+        free(Q);
     }
     for (int64_t c = nn - 1; c >= 0; --c) {
         double r = 0.0;
@@ -1043,16 +1071,16 @@ static void atree_multipoles(const atree_t* T, const double* x, const double* y,
  * (target, then source): the pair contributes the terms |n| + |m| <= p_k of
  * Eq. M2L (ranks 0..p_k of the stored expansions, which are prefixes of the
  * order-p storage).  Every other operator runs at order p. */
-int orc_fmm_adaptive_orders(int64_t n, const double* x, const double* y, const double* z, const double* q,
-                            int max_leaf, double theta, int p, int basis, const signed char* pair_p,
-                            int64_t npair_p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
-                            double* ay, double* az, int64_t* stats /* [5] or NULL */) {
+static int fmm_adaptive_impl(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                             int max_leaf, double theta, int p, int basis, const signed char* pair_p,
+                             int64_t npair_p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
+                             double* ay, double* az, int64_t* stats, int ap) {
     orc_init();
     if (p < 0 || p > ORC_PMAX || max_leaf < 1 || theta < 0.0 || n < 0) return -1;
     int64_t ntarg = nsample >= 0 ? nsample : n;
     if (n == 0) return 0;
     atree_t T;
-    atree_build(&T, n, x, y, z, max_leaf, theta);
+    atree_build(&T, n, x, y, z, q, max_leaf, theta, ap != 0);
     const int64_t nn = T.nn;
     const anode_t* nd = T.nd;
     const kv_t* kv = T.kv;
@@ -1088,6 +1116,9 @@ int orc_fmm_adaptive_orders(int64_t n, const double* x, const double* y, const d
     double* M = (double*)calloc((size_t)nn * nc, sizeof(double));
     double* L = (double*)calloc((size_t)nn * nc, sizeof(double));
     atree_multipoles(&T, x, y, z, q, p, basis, M);
+    if (ap == 1 && p >= 1)   /* AP: about the centre of mass the dipole vanishes; it is set to exactly 0 */
+        for (int64_t c = 0; c < nn; ++c)
+            for (int t = 1; t <= 3; ++t) M[c * nc + t] = 0.0;
     /* interaction phase: the sorted M2L list is already grouped by target */
     int64_t* cnt = (int64_t*)calloc(nn + 1, sizeof(int64_t));
     for (int64_t k = 0; k < T.m2l.n; ++k) cnt[T.m2l.v[k].a + 1]++;
@@ -1152,11 +1183,20 @@ int orc_fmm_adaptive_orders(int64_t n, const double* x, const double* y, const d
                 gx += q[j] * dx * ir3; gy += q[j] * dy * ir3; gz += q[j] * dz * ir3;
             }
         }
-        pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
+        /* AP: only the gradient is evaluated (Sec. 3); the potential is not */
+        pot[t] = ap == 1 ? 0.0 : -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
     }
     atree_free(&T);
     free(pos_of); free(leaf_of); free(need); free(M); free(L); free(cnt); free(pc); free(psrc);
     return 0;
+}
+
+int orc_fmm_adaptive_orders(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                            int max_leaf, double theta, int p, int basis, const signed char* pair_p,
+                            int64_t npair_p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
+                            double* ay, double* az, int64_t* stats /* [5] or NULL */) {
+    return fmm_adaptive_impl(n, x, y, z, q, max_leaf, theta, p, basis, pair_p, npair_p, nsample, sample, pot, ax, ay,
+                             az, stats, 0);
 }
 
 int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* z, const double* q,
@@ -1164,6 +1204,26 @@ int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* 
                      double* pot, double* ax, double* ay, double* az, int64_t* stats /* [5] or NULL */) {
     return orc_fmm_adaptive_orders(n, x, y, z, q, max_leaf, theta, p, basis, NULL, 0, nsample, sample, pot, ax,
                                    ay, az, stats);
+}
+
+/* The AP variant (Sec. 3, astrophysics): the adaptive FMM in the fully
+ * traceless form with centre-of-mass expansion centres, the dipole of every
+ * multipole set to 0 (it vanishes about the centre of mass), and only the
+ * gradient evaluated (pot is written as 0).  basis must be traceless. */
+int orc_fmm_adaptive_ap(int64_t n, const double* x, const double* y, const double* z, const double* q, int max_leaf,
+                        double theta, int p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
+                        double* ay, double* az, int64_t* stats) {
+    return fmm_adaptive_impl(n, x, y, z, q, max_leaf, theta, p, 1, NULL, 0, nsample, sample, pot, ax, ay, az, stats,
+                             1);
+}
+
+/* The FT variant on the AP tree (centre-of-mass centres, dipole kept and the
+ * potential evaluated), for comparison with the AP variant. */
+int orc_fmm_adaptive_com(int64_t n, const double* x, const double* y, const double* z, const double* q, int max_leaf,
+                         double theta, int p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
+                         double* ay, double* az, int64_t* stats) {
+    return fmm_adaptive_impl(n, x, y, z, q, max_leaf, theta, p, 1, NULL, 0, nsample, sample, pot, ax, ay, az, stats,
+                             2);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1274,12 +1334,13 @@ double orc_pair_error(int p, int64_t na, const double* xa, const double* ya, con
  * [b, e) of sorted positions it holds and its parent (-1 for the root);
  * order[a] = the particle at sorted position a.  Returns the node count
  * (arrays written when cap allows). */
-int64_t orc_adaptive_tree(int64_t n, const double* x, const double* y, const double* z, int max_leaf, int64_t cap,
-                          double* zr, int64_t* range, int64_t* order, int64_t* parent) {
+static int64_t adaptive_tree_impl(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                                  int com, int max_leaf, int64_t cap, double* zr, int64_t* range, int64_t* order,
+                                  int64_t* parent) {
     orc_init();
     if (max_leaf < 1 || n < 1) return -1;
     atree_t T;
-    atree_build(&T, n, x, y, z, max_leaf, 0.0);
+    atree_build(&T, n, x, y, z, q, max_leaf, 0.0, com);
     const int64_t nn = T.nn;
     if (cap >= nn) {
         for (int64_t c = 0; c < nn; ++c) {
@@ -1294,6 +1355,17 @@ int64_t orc_adaptive_tree(int64_t n, const double* x, const double* y, const dou
     return nn;
 }
 
+int64_t orc_adaptive_tree(int64_t n, const double* x, const double* y, const double* z, int max_leaf, int64_t cap,
+                          double* zr, int64_t* range, int64_t* order, int64_t* parent) {
+    return adaptive_tree_impl(n, x, y, z, NULL, 0, max_leaf, cap, zr, range, order, parent);
+}
+
+/* The tree with centre-of-mass centres (the AP variant's geometry). */
+int64_t orc_adaptive_tree_com(int64_t n, const double* x, const double* y, const double* z, const double* q,
+                              int max_leaf, int64_t cap, double* zr, int64_t* range, int64_t* order, int64_t* parent) {
+    return adaptive_tree_impl(n, x, y, z, q, 1, max_leaf, cap, zr, range, order, parent);
+}
+
 int orc_ncols_features(void) { return ORC_NF; }
 int orc_ncols_labels(void) { return ORC_NLAB; }
 
@@ -1304,7 +1376,7 @@ int64_t orc_adaptive_pairs(int64_t n, const double* x, const double* y, const do
     if (max_leaf < 1 || theta < 0.0 || n < 0) return -1;
     if (n == 0) return 0;
     atree_t T;
-    atree_build(&T, n, x, y, z, max_leaf, theta);
+    atree_build(&T, n, x, y, z, q, max_leaf, theta, 0);
     const int64_t np = T.m2l.n;
     if (cap < np || (!tgt && !src && !feat && !lab)) { atree_free(&T); return np; }
     const anode_t* nd = T.nd;
