@@ -100,6 +100,12 @@ def lib():
         L.orc_ncols_labels.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_m2m_fused.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+        L.orc_fmm_btree.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i64p, _dp, _dp, _dp, _dp, _i64p]
+        L.orc_fmm_btree.restype = ctypes.c_int
+        L.orc_btree.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_btree.restype = ctypes.c_int64
         for name in ("orc_fmm_adaptive_ap", "orc_fmm_adaptive_com"):
             f = getattr(L, name)
             f.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -385,6 +391,41 @@ def pair_error(p, src_xyzq, zA, zB, targets):
     if e < 0:
         raise ValueError("orc_pair_error rejected its arguments")
     return e
+
+
+def btree(x, y, z, max_leaf: int):
+    """The binary median-split tree (App. C): (nn, 4) centre and radius,
+    (nn, 2) sorted-position ranges, the sorted order, each node's parent."""
+    x, y, z = (_f64(v) for v in (x, y, z))
+    n = len(x)
+    L = lib()
+    nn = L.orc_btree(n, _d(x), _d(y), _d(z), max_leaf, 0, None, None, None, None)
+    zr = np.zeros((nn, 4))
+    rg = np.zeros((nn, 2), dtype=np.int64)
+    order = np.zeros(n, dtype=np.int64)
+    par = np.zeros(nn, dtype=np.int64)
+    assert L.orc_btree(n, _d(x), _d(y), _d(z), max_leaf, nn, zr.ctypes.data, rg.ctypes.data, order.ctypes.data,
+                       par.ctypes.data) == nn
+    return zr, rg, order, par
+
+
+def fmm_btree(x, y, z, q, max_leaf: int, theta: float, p: int, basis: int, sample=None):
+    """The FMM on the binary median-split tree (App. C)."""
+    x, y, z, q = (_f64(v) for v in (x, y, z, q))
+    n = len(x)
+    if sample is None:
+        ns, sp, nout = -1, None, n
+    else:
+        sample = np.ascontiguousarray(sample, dtype=np.int64)
+        ns, sp, nout = len(sample), sample.ctypes.data_as(_i64p), len(sample)
+    pot, ax, ay, az = (np.zeros(nout) for _ in range(4))
+    st = np.zeros(5, dtype=np.int64)
+    rc = lib().orc_fmm_btree(n, _d(x), _d(y), _d(z), _d(q), max_leaf, float(theta), p, basis, ns, sp, _d(pot),
+                             _d(ax), _d(ay), _d(az), st.ctypes.data_as(_i64p))
+    if rc != 0:
+        raise ValueError("orc_fmm_btree rejected its arguments (%d)" % rc)
+    keys = ("nodes", "m2l_pairs", "p2p_pairs", "leaves", "covered_pairs")
+    return pot, np.stack([ax, ay, az]), dict(zip(keys, st.tolist()))
 
 
 def adaptive_tree(x, y, z, max_leaf: int, parents=False, com_q=None):

@@ -886,6 +886,48 @@ static void atree_free(atree_t* T) {
     memset(T, 0, sizeof(*T));
 }
 
+/* Interaction lists of a built tree (T->nd with centres and radii): the
+ * directed dual traversal described above. */
+static void atree_lists(atree_t* T, double theta) {
+    const anode_t* nd = T->nd;
+    plist_t qa = {0, 0, 0}, qb = {0, 0, 0}, m2l = {0, 0, 0}, p2p = {0, 0, 0};
+    pl_push(&qa, 0, 0);
+    while (qa.n) {
+        qb.n = 0;
+        for (int64_t k = 0; k < qa.n; ++k) {
+            const int64_t A = qa.v[k].a, B = qa.v[k].b;
+            const int la = nd[A].nchild == 0, lb = nd[B].nchild == 0;
+            if (A == B) {
+                if (la) pl_push(&p2p, A, A);
+                else
+                    for (int i = 0; i < nd[A].nchild; ++i)
+                        for (int j = 0; j < nd[A].nchild; ++j) pl_push(&qb, nd[A].child0 + i, nd[A].child0 + j);
+                continue;
+            }
+            /* the MAC of App. C, theta |z_A - z_B| > r_A + r_B, compared squared
+               (both sides are non-negative): theta^2 |z_A - z_B|^2 > (r_A + r_B)^2 */
+            {
+                const double dx = nd[A].z[0] - nd[B].z[0], dy = nd[A].z[1] - nd[B].z[1],
+                             dz = nd[A].z[2] - nd[B].z[2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                const double sr = nd[A].r + nd[B].r;
+                if (theta * theta * d2 > sr * sr) { pl_push(&m2l, A, B); continue; }
+            }
+            if (la && lb) { pl_push(&p2p, A, B); continue; }
+            if (!la && (lb || nd[A].r >= nd[B].r)) {
+                for (int i = 0; i < nd[A].nchild; ++i) pl_push(&qb, nd[A].child0 + i, B);
+            } else {
+                for (int j = 0; j < nd[B].nchild; ++j) pl_push(&qb, A, nd[B].child0 + j);
+            }
+        }
+        plist_t t = qa; qa = qb; qb = t;
+    }
+    free(qa.v); free(qb.v);
+    if (m2l.n > 1) qsort(m2l.v, m2l.n, sizeof(pair_t), pair_cmp);
+    T->m2l = m2l;
+    T->p2p = p2p;
+}
+
 /* Octree, geometry and interaction lists as described above (n > 0).
  * com != 0 (the AP variant, Sec. 3): expansion centres are centres of mass
  * instead of geometric centres, computed bottom-up in a fixed order -- a
@@ -1000,42 +1042,108 @@ static void atree_build(atree_t* T, int64_t n, const double* x, const double* y,
         }
         nd[c].r = r;
     }
-    /* directed dual traversal */
-    plist_t qa = {0, 0, 0}, qb = {0, 0, 0}, m2l = {0, 0, 0}, p2p = {0, 0, 0};
-    pl_push(&qa, 0, 0);
-    while (qa.n) {
-        qb.n = 0;
-        for (int64_t k = 0; k < qa.n; ++k) {
-            const int64_t A = qa.v[k].a, B = qa.v[k].b;
-            const int la = nd[A].nchild == 0, lb = nd[B].nchild == 0;
-            if (A == B) {
-                if (la) pl_push(&p2p, A, A);
-                else
-                    for (int i = 0; i < nd[A].nchild; ++i)
-                        for (int j = 0; j < nd[A].nchild; ++j) pl_push(&qb, nd[A].child0 + i, nd[A].child0 + j);
-                continue;
-            }
-            /* the MAC of App. C, theta |z_A - z_B| > r_A + r_B, compared squared
-               (both sides are non-negative): theta^2 |z_A - z_B|^2 > (r_A + r_B)^2 */
-            {
-                const double dx = nd[A].z[0] - nd[B].z[0], dy = nd[A].z[1] - nd[B].z[1],
-                             dz = nd[A].z[2] - nd[B].z[2];
-                const double d2 = dx * dx + dy * dy + dz * dz;
-                const double sr = nd[A].r + nd[B].r;
-                if (theta * theta * d2 > sr * sr) { pl_push(&m2l, A, B); continue; }
-            }
-            if (la && lb) { pl_push(&p2p, A, B); continue; }
-            if (!la && (lb || nd[A].r >= nd[B].r)) {
-                for (int i = 0; i < nd[A].nchild; ++i) pl_push(&qb, nd[A].child0 + i, B);
-            } else {
-                for (int j = 0; j < nd[B].nchild; ++j) pl_push(&qb, A, nd[B].child0 + j);
+    T->nn = nn; T->kv = kv; T->nd = nd;
+    atree_lists(T, theta);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binary median-split tree (App. C): a cell holding more than max_leaf      */
+/* particles is split across the longest axis of its particles' bounding    */
+/* box (the first of x, y, z on ties) into two children with equal numbers  */
+/* of particles (the lower floor(n/2) by that coordinate, ties in the order  */
+/* the particles already have: a stable sort), children first the lower one. */
+/* Cells are shrink-wrapped: the expansion centre is the centre of the       */
+/* bounding box of the cell's particles, (lo + hi) / 2 per axis; radii as   */
+/* for the octree.  Nodes are numbered level by level (breadth first).       */
+/* ------------------------------------------------------------------------ */
+static const double* g_sort_coord;   /* coordinate array of the stable sort below */
+static void merge_sort_kv(kv_t* v, kv_t* tmp, int64_t n) {
+    if (n < 2) return;
+    const int64_t h = n / 2;
+    merge_sort_kv(v, tmp, h);
+    merge_sort_kv(v + h, tmp, n - h);
+    int64_t i = 0, j = h, k = 0;
+    while (i < h && j < n) {
+        /* stable: take from the left run unless the right one is strictly smaller */
+        if (g_sort_coord[v[j].idx] < g_sort_coord[v[i].idx]) tmp[k++] = v[j++];
+        else tmp[k++] = v[i++];
+    }
+    while (i < h) tmp[k++] = v[i++];
+    while (j < n) tmp[k++] = v[j++];
+    memcpy(v, tmp, sizeof(kv_t) * n);
+}
+
+static void node_bbox(const kv_t* kv, const anode_t* c, const double* x, const double* y, const double* z,
+                      double lo[3], double hi[3]) {
+    const int64_t i0 = kv[c->b].idx;
+    lo[0] = hi[0] = x[i0]; lo[1] = hi[1] = y[i0]; lo[2] = hi[2] = z[i0];
+    for (int64_t a = c->b; a < c->e; ++a) {
+        const int64_t i = kv[a].idx;
+        const double v[3] = {x[i], y[i], z[i]};
+        for (int d = 0; d < 3; ++d) { if (v[d] < lo[d]) lo[d] = v[d]; if (v[d] > hi[d]) hi[d] = v[d]; }
+    }
+}
+
+static void btree_build(atree_t* T, int64_t n, const double* x, const double* y, const double* z, int max_leaf,
+                        double theta) {
+    memset(T, 0, sizeof(*T));
+    T->n = n;
+    kv_t* kv = (kv_t*)malloc(sizeof(kv_t) * n);
+    kv_t* tmp = (kv_t*)malloc(sizeof(kv_t) * n);
+    for (int64_t i = 0; i < n; ++i) { kv[i].key = 0; kv[i].idx = i; }
+    int64_t cap = 1024, nn = 1;
+    anode_t* nd = (anode_t*)malloc(sizeof(anode_t) * cap);
+    memset(&nd[0], 0, sizeof(anode_t));
+    nd[0].b = 0; nd[0].e = n; nd[0].child0 = -1; nd[0].parent = -1;
+    int64_t lvl_b = 0, lvl_e = 1;
+    while (lvl_b < lvl_e) {
+        for (int64_t c = lvl_b; c < lvl_e; ++c) {
+            double lo[3], hi[3];
+            node_bbox(kv, &nd[c], x, y, z, lo, hi);
+            nd[c].z[0] = (lo[0] + hi[0]) * 0.5; nd[c].z[1] = (lo[1] + hi[1]) * 0.5; nd[c].z[2] = (lo[2] + hi[2]) * 0.5;
+            const int64_t cnt = nd[c].e - nd[c].b;
+            if (cnt <= max_leaf) continue;
+            int axis = 0;
+            for (int d = 1; d < 3; ++d) if (hi[d] - lo[d] > hi[axis] - lo[axis]) axis = d;
+            g_sort_coord = axis == 0 ? x : axis == 1 ? y : z;
+            merge_sort_kv(kv + nd[c].b, tmp, cnt);
+            const int64_t mid = nd[c].b + cnt / 2;
+            if (nn + 2 > cap) { cap *= 2; nd = (anode_t*)realloc(nd, sizeof(anode_t) * cap); }
+            nd[c].child0 = nn;
+            nd[c].nchild = 2;
+            for (int k = 0; k < 2; ++k) {
+                anode_t* ch = &nd[nn++];
+                memset(ch, 0, sizeof(anode_t));
+                ch->level = nd[c].level + 1;
+                ch->b = k ? mid : nd[c].b;
+                ch->e = k ? nd[c].e : mid;
+                ch->child0 = -1; ch->nchild = 0; ch->parent = c;
             }
         }
-        plist_t t = qa; qa = qb; qb = t;
+        lvl_b = lvl_e;
+        lvl_e = nn;
     }
-    free(qa.v); free(qb.v);
-    if (m2l.n > 1) qsort(m2l.v, m2l.n, sizeof(pair_t), pair_cmp);
-    T->nn = nn; T->kv = kv; T->nd = nd; T->m2l = m2l; T->p2p = p2p;
+    free(tmp);
+    for (int64_t c = nn - 1; c >= 0; --c) {
+        double r = 0.0;
+        if (nd[c].nchild == 0) {
+            for (int64_t a = nd[c].b; a < nd[c].e; ++a) {
+                const int64_t i = kv[a].idx;
+                const double v[3] = {x[i], y[i], z[i]};
+                const double d = dist3(v, nd[c].z);
+                if (d > r) r = d;
+            }
+        } else {
+            for (int k = 0; k < nd[c].nchild; ++k) {
+                const anode_t* ch = &nd[nd[c].child0 + k];
+                const double d = dist3(ch->z, nd[c].z) + ch->r;
+                if (d > r) r = d;
+            }
+        }
+        nd[c].r = r;
+    }
+    T->nn = nn; T->kv = kv; T->nd = nd;
+    atree_lists(T, theta);
 }
 
 /* Upward pass: P2M at the leaves (Eq. P2M), M2M to the root (Eq. M2M). */
@@ -1074,13 +1182,16 @@ static void atree_multipoles(const atree_t* T, const double* x, const double* y,
 static int fmm_adaptive_impl(int64_t n, const double* x, const double* y, const double* z, const double* q,
                              int max_leaf, double theta, int p, int basis, const signed char* pair_p,
                              int64_t npair_p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
-                             double* ay, double* az, int64_t* stats, int ap) {
+                             double* ay, double* az, int64_t* stats, int ap, int binary) {
     orc_init();
     if (p < 0 || p > ORC_PMAX || max_leaf < 1 || theta < 0.0 || n < 0) return -1;
     int64_t ntarg = nsample >= 0 ? nsample : n;
     if (n == 0) return 0;
     atree_t T;
-    atree_build(&T, n, x, y, z, q, max_leaf, theta, ap != 0);
+    if (binary)
+        btree_build(&T, n, x, y, z, max_leaf, theta);
+    else
+        atree_build(&T, n, x, y, z, q, max_leaf, theta, ap != 0);
     const int64_t nn = T.nn;
     const anode_t* nd = T.nd;
     const kv_t* kv = T.kv;
@@ -1196,7 +1307,7 @@ int orc_fmm_adaptive_orders(int64_t n, const double* x, const double* y, const d
                             int64_t npair_p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
                             double* ay, double* az, int64_t* stats /* [5] or NULL */) {
     return fmm_adaptive_impl(n, x, y, z, q, max_leaf, theta, p, basis, pair_p, npair_p, nsample, sample, pot, ax, ay,
-                             az, stats, 0);
+                             az, stats, 0, 0);
 }
 
 int orc_fmm_adaptive(int64_t n, const double* x, const double* y, const double* z, const double* q,
@@ -1214,7 +1325,17 @@ int orc_fmm_adaptive_ap(int64_t n, const double* x, const double* y, const doubl
                         double theta, int p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
                         double* ay, double* az, int64_t* stats) {
     return fmm_adaptive_impl(n, x, y, z, q, max_leaf, theta, p, 1, NULL, 0, nsample, sample, pot, ax, ay, az, stats,
-                             1);
+                             1, 0);
+}
+
+/* The FMM on the binary median-split tree (App. C): the operators, the
+ * traversal and the lists as for the octree; expansion centres at the
+ * centres of the cells' shrink-wrapped bounding boxes. */
+int orc_fmm_btree(int64_t n, const double* x, const double* y, const double* z, const double* q, int max_leaf,
+                  double theta, int p, int basis, int64_t nsample, const int64_t* sample, double* pot, double* ax,
+                  double* ay, double* az, int64_t* stats) {
+    return fmm_adaptive_impl(n, x, y, z, q, max_leaf, theta, p, basis, NULL, 0, nsample, sample, pot, ax, ay, az,
+                             stats, 0, 1);
 }
 
 /* The FT variant on the AP tree (centre-of-mass centres, dipole kept and the
@@ -1223,7 +1344,7 @@ int orc_fmm_adaptive_com(int64_t n, const double* x, const double* y, const doub
                          double theta, int p, int64_t nsample, const int64_t* sample, double* pot, double* ax,
                          double* ay, double* az, int64_t* stats) {
     return fmm_adaptive_impl(n, x, y, z, q, max_leaf, theta, p, 1, NULL, 0, nsample, sample, pot, ax, ay, az, stats,
-                             2);
+                             2, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1340,7 +1461,10 @@ static int64_t adaptive_tree_impl(int64_t n, const double* x, const double* y, c
     orc_init();
     if (max_leaf < 1 || n < 1) return -1;
     atree_t T;
-    atree_build(&T, n, x, y, z, q, max_leaf, 0.0, com);
+    if (com == 2)
+        btree_build(&T, n, x, y, z, max_leaf, 0.0);
+    else
+        atree_build(&T, n, x, y, z, q, max_leaf, 0.0, com);
     const int64_t nn = T.nn;
     if (cap >= nn) {
         for (int64_t c = 0; c < nn; ++c) {
@@ -1358,6 +1482,12 @@ static int64_t adaptive_tree_impl(int64_t n, const double* x, const double* y, c
 int64_t orc_adaptive_tree(int64_t n, const double* x, const double* y, const double* z, int max_leaf, int64_t cap,
                           double* zr, int64_t* range, int64_t* order, int64_t* parent) {
     return adaptive_tree_impl(n, x, y, z, NULL, 0, max_leaf, cap, zr, range, order, parent);
+}
+
+/* The binary median-split tree (App. C). */
+int64_t orc_btree(int64_t n, const double* x, const double* y, const double* z, int max_leaf, int64_t cap, double* zr,
+                  int64_t* range, int64_t* order, int64_t* parent) {
+    return adaptive_tree_impl(n, x, y, z, NULL, 2, max_leaf, cap, zr, range, order, parent);
 }
 
 /* The tree with centre-of-mass centres (the AP variant's geometry). */
