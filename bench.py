@@ -109,6 +109,13 @@ def m2l_fma_per_pair(p, basis):
     return sum((2 * a + 1) * (p - a + 1) ** 2 for a in range(p + 1))
 
 
+def alu_peak_tflops(bits, mhz):
+    """Nominal FP64 (bits 64) or FP32 (bits 32) FMA peak at the SM clock mhz,
+    counting an FMA as two flops."""
+    per = NOMINAL["fp64_fma_per_clk_sm"] if bits == 64 else NOMINAL["fp32_fma_per_clk_sm"]
+    return NOMINAL["sm_count"] * per * 2 * mhz * 1e6 / 1e12
+
+
 def m2l_alg_fma_per_pair(p, basis):
     """Algorithmic FMAs of one M2L (Eq. M2L with independent local outputs
     and full multipoles): symmetric C(p+6,6); traceless
@@ -511,6 +518,8 @@ def run_m2l_sweep(args):
     zero = torch.zeros((3, n), device=dev, dtype=torch.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ps = [int(v) for v in args.orders.split(",")]
+    pk, _ = peaks()
+    mhz_max = float(pk.get("sm_max_mhz", 2070.0))
     for p in ps:
         for basis in (0, 1):
             nc = F.ncoef(p, basis)
@@ -533,9 +542,17 @@ def run_m2l_sweep(args):
                     times.append(e0.elapsed_time(e1))
                 ms = float(np.median(times))
                 s = 8 if prec == F.FP64 else 4
+                # algorithmic work of one pair: the Eq. M2L FMAs (full
+                # multipoles, independent local outputs); bytes: M in, L out,
+                # the offset r (3 doubles), each once
+                gbs = n * (2 * nc * s + 24) / (ms * 1e-3) / 1e9
+                fma = m2l_alg_fma_per_pair(p, basis)
+                tfl = n * 2 * fma / (ms * 1e-3) / 1e12
+                alu_peak = alu_peak_tflops(64 if prec == F.FP64 else 32, mhz_max)
                 res["fp64" if prec == F.FP64 else "fp32"] = {
-                    "pairs_per_s": n / (ms * 1e-3), "ms": ms,
-                    "GB_per_s": n * (2 * nc * s + 24) / (ms * 1e-3) / 1e9}
+                    "pairs_per_s": n / (ms * 1e-3), "ms": ms, "GB_per_s": gbs,
+                    "hbm_frac": gbs / pk.get("hbm_gbs", 6800.0), "alg_fma_per_pair": fma, "TFLOP_s": tfl,
+                    "alu_frac": tfl / alu_peak, "alu_peak_tflops": alu_peak}
             print(json.dumps({"workload": "m2l per-pair, 2^20 pairs", "p": p,
                               "basis": "sym" if basis == 0 else "traceless", **res,
                               "fp32_vs_fp64": res["fp32"]["pairs_per_s"] / res["fp64"]["pairs_per_s"]}))
@@ -619,6 +636,57 @@ def run_adaptive(args):
             "tree": res["fp32"]["stats"],
             "fp64_form": {"value": v64, "ms_per_step": res["fp64"]["ms_per_step"]} if v64 else None,
             "vs_fp64_form": v32 / v64 if v64 else None}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ap(args):
+    """AP variant (Sec. 3): the batching-form workload (8,388,608 Plummer
+    particles, adaptive octree <= 64 per leaf, MAC theta 0.6, p = 6) in the
+    fully traceless form about centres of mass, dipole 0, gradient only, FP64;
+    beside it the same FP64 traceless FMM about geometric centres.  One step =
+    fmm_evaluate (tree, centres of mass, traversal, operators)."""
+    import torch
+
+    from paper_1811_06332_gb300 import fmm as F
+    from paper_1811_06332_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    n, p, ml, theta = 8388608, 6, 64, 0.6
+    x, y, z = inputs.plummer(n, 4)
+    q = inputs.masses_equal(n)
+    X = [torch.from_numpy(a).to(dev) for a in (x, y, z, q)]
+    out = torch.empty((4, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tsel = torch.from_numpy(np.sort(np.unique((inputs.u01(4, 95, 4096) * n).astype(np.int64)))).to(dev)
+    ref = torch.empty((4, len(tsel)), dtype=torch.float64, device=dev)
+    F.fmm_direct(X[0], X[1], X[2], X[3], ref[0], ref[1], ref[2], ref[3], targets=tsel)
+    res = {}
+    for name, ap in (("ap", True), ("ft_geometric", False)):
+        plan = F.Plan(p=p, basis=F.BASIS_TRACELESS, prec=F.FP64, adaptive=True, max_leaf=ml, theta=theta, ap=ap)
+        times = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(float(k))
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record()
+            plan.fmm_evaluate(*X, out[0], out[1], out[2], out[3])
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        acc = out[1:, tsel]
+        err = float(torch.sqrt(((acc - ref[1:]) ** 2).sum() / (ref[1:] ** 2).sum()).item())
+        res[name] = {"ms_per_step": float(np.mean(times)), "rel_force_err": err, "stats": plan.stats()}
+        plan.close()
+    ms = res["ap"]["ms_per_step"]
+    line = {"metric": METRIC, "value": n / (ms * 1e-3), "unit": "particles/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Plummer sphere, 8,388,608 particles, equal masses, adaptive octree <= 64 per "
+                                   "leaf, MAC theta 0.6, traceless p=6",
+                       "form": "AP variant (centre-of-mass centres, dipole 0, gradient only), FP64",
+                       "l2": "flushed before each step"},
+            "rel_force_err": res["ap"]["rel_force_err"], "ap": res["ap"], "ft_geometric_centres": res["ft_geometric"],
+            "vs_geometric_centres": res["ft_geometric"]["ms_per_step"] / ms}
     print(json.dumps(line))
     return 0
 
@@ -747,7 +815,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="bf16x3", choices=["fp64", "fp32", "bf16x3", "tf32x3"])
-    ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l", "adaptive", "learned"])
+    ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l", "adaptive", "learned", "ap"])
     ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -766,6 +834,8 @@ def main():
         return run_adaptive(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "ap":
+        return run_ap(args)
     return run_gpu(args)
 
 

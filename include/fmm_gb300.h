@@ -109,6 +109,23 @@ typedef struct {
                               the first M2L that reaches a tensor-core level times
                               every candidate shape on the deepest level, keeps the
                               fastest and stores it.  0: the default shape          */
+    int ap;                /* 1: the AP variant of Sec. 3 (astrophysics): adaptive tree,
+                              traceless basis, FMM_FP64; expansion centres at the
+                              centres of mass (summed bottom-up: a leaf over its
+                              particles in sorted order, a cell over its children's
+                              charge-weighted centres; a cell of zero charge keeps its
+                              geometric centre), radii and MAC about them, the dipole
+                              of every multipole set to 0 (it vanishes about the
+                              centre of mass), and only the gradient evaluated: the
+                              accelerations are written, pot is written as 0       */
+    int binary_tree;       /* 1 (adaptive, FMM_FP64, not ap, not learned_p): the binary
+                              median-split tree of App. C instead of the octree: a
+                              cell of more than max_leaf particles is halved across
+                              the longest side of its particles' bounding box (the
+                              lower floor(n/2) by that coordinate, ties in the current
+                              order; the first of x, y, z when sides tie), cells
+                              shrink-wrapped and centred on their bounding boxes;
+                              the same traversal, MAC and operators as the octree  */
 } fmm_config;
 
 typedef struct fmm_plan fmm_plan;

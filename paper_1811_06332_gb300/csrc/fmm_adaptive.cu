@@ -248,6 +248,49 @@ __global__ void k_centres(int nn, const int* __restrict__ lev, const int* __rest
     zc[3 * c + 2] = __dadd_rn(box[2], __dmul_rn((double)iz[c] + 0.5, h));
 }
 
+// Centres of mass of the nodes [lb, lb + n) (one level, children done), the
+// AP variant's expansion centres: a leaf sums q_a x_a and q_a over its
+// particles in sorted order, a cell sums Q_c z_c and Q_c over its children
+// in octant order, z = S / Q; explicitly rounded FP64 in the oracle's order,
+// so both trees have the same centres, radii and lists.  A node of zero
+// total charge keeps its geometric centre.
+__global__ void k_com(int lb, int le, const int* __restrict__ nb, const int* __restrict__ ne,
+                      const int* __restrict__ child0, const int* __restrict__ nchild, const double* __restrict__ xs,
+                      const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
+                      double* __restrict__ Q, double* __restrict__ zc) {
+    const int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= le) return;
+    double q = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    if (nchild[c] == 0) {
+        for (int a = nb[c]; a < ne[c]; ++a) {
+            q = __dadd_rn(q, qs[a]);
+            sx = __dadd_rn(sx, __dmul_rn(qs[a], xs[a]));
+            sy = __dadd_rn(sy, __dmul_rn(qs[a], ys[a]));
+            sz = __dadd_rn(sz, __dmul_rn(qs[a], zs[a]));
+        }
+    } else {
+        for (int k = 0; k < nchild[c]; ++k) {
+            const int ch = child0[c] + k;
+            q = __dadd_rn(q, Q[ch]);
+            sx = __dadd_rn(sx, __dmul_rn(Q[ch], zc[3 * ch]));
+            sy = __dadd_rn(sy, __dmul_rn(Q[ch], zc[3 * ch + 1]));
+            sz = __dadd_rn(sz, __dmul_rn(Q[ch], zc[3 * ch + 2]));
+        }
+    }
+    Q[c] = q;
+    if (q != 0.0) {
+        zc[3 * c] = __ddiv_rn(sx, q);
+        zc[3 * c + 1] = __ddiv_rn(sy, q);
+        zc[3 * c + 2] = __ddiv_rn(sz, q);
+    }
+}
+
+// AP: the dipole (rank-1 components 1..3 of the node-major multipoles) set to 0
+__global__ void k_zero_dipole(int nn, int nc, double* __restrict__ M) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nn) { M[(int64_t)c * nc + 1] = 0.0; M[(int64_t)c * nc + 2] = 0.0; M[(int64_t)c * nc + 3] = 0.0; }
+}
+
 // radii in units of side / 2^22 (the unit of the integer centres), rounded to FP32
 __global__ void k_radf(int nn, const double* __restrict__ rad, const double* __restrict__ box,
                        float* __restrict__ radf) {
@@ -676,6 +719,20 @@ int ad_centres(int nn, const int* lev, const int* ix, const int* iy, const int* 
     count_launch();
     return 0;
 }
+int ad_com(int lb, int le, const int* nb, const int* ne, const int* child0, const int* nchild, const double* xs,
+           const double* ys, const double* zs, const double* qs, double* Q, double* zc, cudaStream_t s) {
+    if (le <= lb) return 0;
+    k_com<<<(le - lb + 255) / 256, 256, 0, s>>>(lb, le, nb, ne, child0, nchild, xs, ys, zs, qs, Q, zc);
+    count_launch();
+    return 0;
+}
+int ad_zero_dipole(int nn, int nc, double* M, cudaStream_t s) {
+    if (nn <= 0 || nc < 4) return 0;
+    k_zero_dipole<<<(nn + 255) / 256, 256, 0, s>>>(nn, nc, M);
+    count_launch();
+    return 0;
+}
+
 int ad_radii(int lb, int le, const int* nb, const int* ne, const int* child0, const int* nchild, const double* zc,
              const double* xs, const double* ys, const double* zs, double* rad, cudaStream_t s) {
     k_radii<<<G256(le - lb)>>>(lb, le, nb, ne, child0, nchild, zc, xs, ys, zs, rad);

@@ -21,6 +21,13 @@ struct AdState {
     int *lev = nullptr, *ix = nullptr, *iy = nullptr, *iz = nullptr, *nb = nullptr, *ne = nullptr;
     int *child0 = nullptr, *nchild = nullptr, *parent = nullptr;
     double *zc = nullptr, *rad = nullptr;
+    int ap = 0;             // AP variant: centre-of-mass centres (Q: total charge per node)
+    int binary = 0;         // binary median-split tree (App. C) instead of the octree
+    int *axis = nullptr, *segstart = nullptr, *segof = nullptr;
+    unsigned char* axis_at = nullptr;
+    size_t cap_axis = 0, cap_segstart = 0, cap_segof = 0, cap_axis_at = 0;
+    double* Q = nullptr;
+    size_t cap_Q = 0;
     float* radf = nullptr;   // radii / (side / 2^22) rounded to FP32 (MAC screen)
     int *bounds = nullptr, *nch = nullptr, *choff = nullptr;
     // traversal
@@ -88,6 +95,17 @@ int ad_bucket_csr(int n, int nn, const uint64_t* key, const int* val, const int*
                   int* bcnt, cudaStream_t s);
 int ad_iota(int n, int* a, cudaStream_t s);
 
+// fmm_btree.cu (binary median-split tree)
+int bt_nodes(int lb, int le, int max_leaf, const int* nb, const int* ne, const int* perm, const double* x,
+             const double* y, const double* z, double* zc, int* axis, int* nsplit, cudaStream_t s);
+int bt_children(int lb, int le, const int* nsplit, const int* off, int* lev, int* nb, int* ne, int* child0,
+                int* nchild, int* parent, cudaStream_t s);
+int bt_reorder_keys(int64_t n, int lb, int le, const int* nb, const int* ne, const int* nchild, const int* axis,
+                    unsigned char* axis_at, const int* perm, const int* segstart, const double* x, const double* y,
+                    const double* z, uint64_t* key, int* val, int* segof, cudaStream_t s);
+int bt_keys2(int64_t n, const int* val, const int* segof, uint64_t* key, cudaStream_t s);
+int bt_segstart(int lb, int le, const int* nb, const int* ne, const int* nchild, int* segstart, cudaStream_t s);
+
 // fmm_adaptive.cu
 void radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,
                 int* scratch, cudaStream_t s);
@@ -102,6 +120,9 @@ int ad_split_write(int lb, int le, const int* bounds, const int* nch, const int*
                    int* iz, int* nb, int* ne, int* child0, int* nchild, int* parent, cudaStream_t s);
 int ad_centres(int nn, const int* lev, const int* ix, const int* iy, const int* iz, const double* box, double* zc,
                cudaStream_t s);
+int ad_com(int lb, int le, const int* nb, const int* ne, const int* child0, const int* nchild, const double* xs,
+           const double* ys, const double* zs, const double* qs, double* Q, double* zc, cudaStream_t s);
+int ad_zero_dipole(int nn, int nc, double* M, cudaStream_t s);
 int ad_radii(int lb, int le, const int* nb, const int* ne, const int* child0, const int* nchild, const double* zc,
              const double* xs, const double* ys, const double* zs, double* rad, cudaStream_t s);
 int ad_trav_count(int nq, const int2* q, double theta, const int* nchild, const double* zc, const double* rad,

@@ -39,7 +39,7 @@ static int grow_bytes(void** p, size_t* cap, size_t need, unsigned* gen) {
 
 void ad_free(AdState* a) {
     if (!a) return;
-    void* ptrs[] = {a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
+    void* ptrs[] = {a->Q, a->axis, a->segstart, a->segof, a->axis_at, a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
                     a->box, a->part, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0, a->nchild, a->parent,
                     a->zc, a->rad, a->radf, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
                     a->oq, a->tmode, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
@@ -70,6 +70,80 @@ static int sort_pairs(AdState* a, int64_t n, int bits, cudaStream_t s) {
     return 0;
 }
 
+// Binary median-split tree (App. C; fmm_btree.cu): nodes level by level,
+// the particles reordered within the cells each level splits, then the
+// sorted particles, the node centres (bounding-box centres) and radii.
+static int build_binary(AdState* a, int64_t n, const double* x, const double* y, const double* z, const double* q,
+                        int max_leaf, cudaStream_t s) {
+    GROW(a->perm, a->cap_perm, n * 4);
+    GROW(a->segstart, a->cap_segstart, n * 4);
+    GROW(a->segof, a->cap_segof, n * 4);
+    GROW(a->axis_at, a->cap_axis_at, n);
+    ad_iota((int)n, a->perm, s);
+    cudaMemsetAsync(a->segstart, 0, n * 4, s);
+    int cap = 1024;
+    auto node_cap = [&](int need) -> int {
+        const size_t nd = (size_t)need;
+        GROW(a->lev, a->cap_lev, nd * 4); GROW(a->nb, a->cap_nb, nd * 4); GROW(a->ne, a->cap_ne, nd * 4);
+        GROW(a->child0, a->cap_child0, nd * 4); GROW(a->nchild, a->cap_nchild, nd * 4);
+        GROW(a->parent, a->cap_parent, nd * 4); GROW(a->axis, a->cap_axis, nd * 4);
+        GROW(a->zc, a->cap_zc, nd * 24);
+        GROW(a->ix, a->cap_ix, nd * 4); GROW(a->iy, a->cap_iy, nd * 4); GROW(a->iz, a->cap_iz, nd * 4);
+        return 0;
+    };
+    if (int r = node_cap(cap)) return r;
+    {
+        const int zero = 0, nn1 = (int)n, m1 = -1;
+        cudaMemcpyAsync(a->lev, &zero, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->nb, &zero, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->ne, &nn1, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->parent, &m1, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->child0, &m1, 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(a->nchild, &zero, 4, cudaMemcpyHostToDevice, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;   // host values must land first
+    }
+    a->lvl.assign(1, 0);
+    int lb = 0, le = 1;
+    while (le > lb) {
+        a->lvl.push_back(le);
+        const int m = le - lb;
+        GROW(a->nch, a->cap_nch, (size_t)(m + 1) * 4);
+        GROW(a->choff, a->cap_choff, (size_t)(m + 1) * 4);
+        bt_nodes(lb, le, max_leaf, a->nb, a->ne, a->perm, x, y, z, a->zc, a->axis, a->nch, s);
+        int tot = 0;
+        if (scan_total(a->nch, a->choff, m, a->scr, &tot, s)) return -2;
+        if (le + tot > cap) {
+            cap = 2 * (le + tot);
+            if (int r = node_cap(cap)) return r;
+        }
+        bt_children(lb, le, a->nch, a->choff, a->lev, a->nb, a->ne, a->child0, a->nchild, a->parent, s);
+        if (tot > 0) {
+            // reorder the particles of the split cells: by the split coordinate,
+            // then (stably) by the start of their cell
+            bt_reorder_keys(n, lb, le, a->nb, a->ne, a->nchild, a->axis, a->axis_at, a->perm, a->segstart, x, y, z,
+                            a->k0, a->v0, a->segof, s);
+            if (int r = sort_pairs(a, n, 64, s)) return r;
+            bt_keys2(n, a->v0, a->segof, a->k0, s);
+            int bits = 1;
+            while ((1ll << bits) < n) ++bits;
+            if (int r = sort_pairs(a, n, bits, s)) return r;
+            cudaMemcpyAsync(a->perm, a->v0, n * 4, cudaMemcpyDeviceToDevice, s);
+            bt_segstart(lb, le, a->nb, a->ne, a->nchild, a->segstart, s);
+        }
+        lb = le;
+        le = le + tot;
+    }
+    a->nn = le;
+    ad_gather(n, a->perm, x, y, z, q, a->xs, a->ys, a->zs, a->qs, s);
+    GROW(a->rad, a->cap_rad, (size_t)a->nn * 8);
+    for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
+        ad_radii(a->lvl[L], a->lvl[L + 1], a->nb, a->ne, a->child0, a->nchild, a->zc, a->xs, a->ys, a->zs, a->rad, s);
+    cudaMemsetAsync(a->ix, 0, (size_t)a->nn * 4, s);
+    cudaMemsetAsync(a->iy, 0, (size_t)a->nn * 4, s);
+    cudaMemsetAsync(a->iz, 0, (size_t)a->nn * 4, s);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
 int ad_build(AdState* a, int64_t n, const double* x, const double* y, const double* z, const double* q,
              int max_leaf, double theta, int nc, int prec, cudaStream_t s) {
     a->n = n;
@@ -87,65 +161,76 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
     GROW(a->counter, a->cap_counter, 64);
     if (n == 0) { a->nn = 0; a->nleaf = 0; a->nm2l = 0; a->np2p = 0; a->ntarg = 0; return 0; }
     ad_bbox(n, x, y, z, a->part, a->box, s);
-    ad_morton(n, x, y, z, a->box, a->k0, a->v0, s);
-    if (int r = sort_pairs(a, n, 63, s)) return r;
-    GROW(a->perm, a->cap_perm, n * 4);
-    cudaMemcpyAsync(a->perm, a->v0, n * 4, cudaMemcpyDeviceToDevice, s);
-    ad_gather(n, a->perm, x, y, z, q, a->xs, a->ys, a->zs, a->qs, s);
-    // sorted keys stay in k0; keep a copy (k0/k1 are reused by later sorts)
-    uint64_t* keys = a->k1;
-    cudaMemcpyAsync(keys, a->k0, n * 8, cudaMemcpyDeviceToDevice, s);
-    // ---------------- tree, level by level ----------------
-    int cap = 1024;
-    auto node_cap = [&](int need) -> int {
-        const size_t nd = (size_t)need;
-        GROW(a->lev, a->cap_lev, nd * 4); GROW(a->ix, a->cap_ix, nd * 4); GROW(a->iy, a->cap_iy, nd * 4);
-        GROW(a->iz, a->cap_iz, nd * 4); GROW(a->nb, a->cap_nb, nd * 4); GROW(a->ne, a->cap_ne, nd * 4);
-        GROW(a->child0, a->cap_child0, nd * 4); GROW(a->nchild, a->cap_nchild, nd * 4);
-        GROW(a->parent, a->cap_parent, nd * 4);
-        return 0;
-    };
-    if (int r = node_cap(cap)) return r;
-    {
-        const int zero = 0, nn1 = (int)n, m1 = -1;
-        cudaMemcpyAsync(a->lev, &zero, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->ix, &zero, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->iy, &zero, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->iz, &zero, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->nb, &zero, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->ne, &nn1, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->parent, &m1, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->child0, &m1, 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(a->nchild, &zero, 4, cudaMemcpyHostToDevice, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) return -2;   // host values must land first
-    }
-    a->lvl.assign(1, 0);
-    int lb = 0, le = 1;
-    while (le > lb) {
-        a->lvl.push_back(le);
-        const int m = le - lb;
-        GROW(a->bounds, a->cap_bounds, (size_t)m * 9 * 4);
-        GROW(a->nch, a->cap_nch, (size_t)(m + 1) * 4);
-        GROW(a->choff, a->cap_choff, (size_t)(m + 1) * 4);
-        ad_split_count(lb, le, max_leaf, a->lev, a->nb, a->ne, keys, a->bounds, a->nch, s);
-        int tot = 0;
-        if (scan_total(a->nch, a->choff, m, a->scr, &tot, s)) return -2;
-        if (le + tot > cap) {
-            cap = 2 * (le + tot);
-            if (int r = node_cap(cap)) return r;
+    if (a->binary) {
+        if (int r = build_binary(a, n, x, y, z, q, max_leaf, s)) return r;
+    } else {
+        ad_morton(n, x, y, z, a->box, a->k0, a->v0, s);
+        if (int r = sort_pairs(a, n, 63, s)) return r;
+        GROW(a->perm, a->cap_perm, n * 4);
+        cudaMemcpyAsync(a->perm, a->v0, n * 4, cudaMemcpyDeviceToDevice, s);
+        ad_gather(n, a->perm, x, y, z, q, a->xs, a->ys, a->zs, a->qs, s);
+        // sorted keys stay in k0; keep a copy (k0/k1 are reused by later sorts)
+        uint64_t* keys = a->k1;
+        cudaMemcpyAsync(keys, a->k0, n * 8, cudaMemcpyDeviceToDevice, s);
+        // ---------------- tree, level by level ----------------
+        int cap = 1024;
+        auto node_cap = [&](int need) -> int {
+            const size_t nd = (size_t)need;
+            GROW(a->lev, a->cap_lev, nd * 4); GROW(a->ix, a->cap_ix, nd * 4); GROW(a->iy, a->cap_iy, nd * 4);
+            GROW(a->iz, a->cap_iz, nd * 4); GROW(a->nb, a->cap_nb, nd * 4); GROW(a->ne, a->cap_ne, nd * 4);
+            GROW(a->child0, a->cap_child0, nd * 4); GROW(a->nchild, a->cap_nchild, nd * 4);
+            GROW(a->parent, a->cap_parent, nd * 4);
+            return 0;
+        };
+        if (int r = node_cap(cap)) return r;
+        {
+            const int zero = 0, nn1 = (int)n, m1 = -1;
+            cudaMemcpyAsync(a->lev, &zero, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->ix, &zero, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->iy, &zero, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->iz, &zero, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->nb, &zero, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->ne, &nn1, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->parent, &m1, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->child0, &m1, 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(a->nchild, &zero, 4, cudaMemcpyHostToDevice, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) return -2;   // host values must land first
         }
-        ad_split_write(lb, le, a->bounds, a->nch, a->choff, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0,
-                       a->nchild, a->parent, s);
-        lb = le;
-        le = le + tot;
+        a->lvl.assign(1, 0);
+        int lb = 0, le = 1;
+        while (le > lb) {
+            a->lvl.push_back(le);
+            const int m = le - lb;
+            GROW(a->bounds, a->cap_bounds, (size_t)m * 9 * 4);
+            GROW(a->nch, a->cap_nch, (size_t)(m + 1) * 4);
+            GROW(a->choff, a->cap_choff, (size_t)(m + 1) * 4);
+            ad_split_count(lb, le, max_leaf, a->lev, a->nb, a->ne, keys, a->bounds, a->nch, s);
+            int tot = 0;
+            if (scan_total(a->nch, a->choff, m, a->scr, &tot, s)) return -2;
+            if (le + tot > cap) {
+                cap = 2 * (le + tot);
+                if (int r = node_cap(cap)) return r;
+            }
+            ad_split_write(lb, le, a->bounds, a->nch, a->choff, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0,
+                           a->nchild, a->parent, s);
+            lb = le;
+            le = le + tot;
+        }
+        a->nn = le;
+        // lvl: level L holds nodes [lvl[L], lvl[L+1]); the last entry is nn
+        GROW(a->zc, a->cap_zc, (size_t)a->nn * 24);
+        GROW(a->rad, a->cap_rad, (size_t)a->nn * 8);
+        ad_centres(a->nn, a->lev, a->ix, a->iy, a->iz, a->box, a->zc, s);
+        if (a->ap) {
+            // AP: centres of mass, bottom-up level by level
+            GROW(a->Q, a->cap_Q, (size_t)a->nn * 8);
+            for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
+                ad_com(a->lvl[L], a->lvl[L + 1], a->nb, a->ne, a->child0, a->nchild, a->xs, a->ys, a->zs, a->qs, a->Q,
+                       a->zc, s);
+        }
+        for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
+            ad_radii(a->lvl[L], a->lvl[L + 1], a->nb, a->ne, a->child0, a->nchild, a->zc, a->xs, a->ys, a->zs, a->rad, s);
     }
-    a->nn = le;
-    // lvl: level L holds nodes [lvl[L], lvl[L+1]); the last entry is nn
-    GROW(a->zc, a->cap_zc, (size_t)a->nn * 24);
-    GROW(a->rad, a->cap_rad, (size_t)a->nn * 8);
-    ad_centres(a->nn, a->lev, a->ix, a->iy, a->iz, a->box, a->zc, s);
-    for (int L = (int)a->lvl.size() - 2; L >= 0; --L)
-        ad_radii(a->lvl[L], a->lvl[L + 1], a->nb, a->ne, a->child0, a->nchild, a->zc, a->xs, a->ys, a->zs, a->rad, s);
     // integer centres (FP32 centre offsets), FP32 radii (MAC screen), cell side
     GROW(a->ic, a->cap_ic, (size_t)a->nn * 16);
     ad_icentre(a->nn, a->lev, a->ix, a->iy, a->iz, a->ic, s);
@@ -165,6 +250,10 @@ int ad_build(AdState* a, int64_t n, const double* x, const double* y, const doub
         const double lo = fmax(fabs(bx[0]), fmax(fabs(bx[1]), fabs(bx[2])));
         const double band = 1e-5 + ldexp(lo / side + 2.0, -27);
         a->mac_band = band < 0.5 ? (float)band : 0.5f;
+        // AP and the binary tree: the integer (octree) centres do not locate
+        // the expansion centres, so the FP32 screen is bypassed and every pair
+        // takes the FP64 rule
+        if (a->ap || a->binary) a->mac_band = 1e30f;
     }
     // ---------------- directed dual traversal ----------------
     int nq = 1, nm = 0, np = 0;

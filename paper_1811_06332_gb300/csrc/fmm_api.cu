@@ -543,6 +543,14 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         if (cfg->prec != FMM_FP64 && cfg->prec != FMM_FP32)
             FAIL(FMM_ERR_UNSUPPORTED, "adaptive trees support FMM_FP64 and FMM_FP32");
     }
+    if (cfg->ap) {
+        if (!cfg->adaptive || cfg->basis != FMM_BASIS_TRACELESS || cfg->prec != FMM_FP64 || cfg->learned_p)
+            FAIL(FMM_ERR_UNSUPPORTED, "the AP variant needs an adaptive tree, FMM_BASIS_TRACELESS and FMM_FP64");
+    }
+    if (cfg->binary_tree) {
+        if (!cfg->adaptive || cfg->prec != FMM_FP64 || cfg->ap || cfg->learned_p)
+            FAIL(FMM_ERR_UNSUPPORTED, "the binary tree needs an adaptive plan in FMM_FP64, without ap or learned_p");
+    }
     if (cfg->learned_p) {
         if (!cfg->adaptive) FAIL(FMM_ERR_UNSUPPORTED, "learned_p needs an adaptive tree");
         if (cfg->basis != FMM_BASIS_SYM) FAIL(FMM_ERR_UNSUPPORTED, "learned_p needs FMM_BASIS_SYM");
@@ -556,6 +564,8 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
     pl->cfg = *cfg;
     if (cfg->adaptive) {
         pl->ad = new AdState();
+        pl->ad->ap = cfg->ap ? 1 : 0;
+        pl->ad->binary = cfg->binary_tree ? 1 : 0;
         pl->depth = 0;
     }
     pl->depth = cfg->depth;
@@ -777,7 +787,13 @@ int fmm_p2m(fmm_plan* pl, void* stream) {
 
 int fmm_m2m(fmm_plan* pl, void* stream) {
     NEED_TREE();
-    if (pl->ad) { ad_run_m2m(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
+    if (pl->ad) {
+        ad_run_m2m(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream));
+        // AP: about the centre of mass the dipole vanishes; it is set to exactly 0
+        if (pl->ad->ap && pl->cfg.p >= 1) ad_zero_dipole(pl->ad->nn, pl->nc, pl->ad->M, S(stream));
+        CKLAUNCH();
+        return FMM_OK;
+    }
     if (pl->W32) {
         for (int l = pl->depth - 1; l >= 2; --l) {
             launch_shift32(pl->cfg.p, pl->cfg.basis, 1, l, pl->W32, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
@@ -897,6 +913,7 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
     if (pl->ad) {
         ad_run_l2p(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], pot, ax, ay, az, S(stream));
+        if (pl->ad->ap) launch_fill(pl->n, pot, 0.0, S(stream));   // AP: the gradient only
         CKLAUNCH();
         return FMM_OK;
     }
@@ -915,6 +932,7 @@ int fmm_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
     if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
     if (pl->ad) {
         ad_run_p2p(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->sms, pot, ax, ay, az, S(stream));
+        if (pl->ad->ap) launch_fill(pl->n, pot, 0.0, S(stream));   // AP: the gradient only
         CKLAUNCH();
         return FMM_OK;
     }

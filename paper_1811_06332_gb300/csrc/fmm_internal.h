@@ -101,6 +101,7 @@ int launch_m2m_level(int p, int basis, int l, const double* W, const double* Mch
 int launch_l2l_level(int p, int basis, int l, const double* V, const double* Lpa, int64_t npa, double* Lch,
                      int64_t nch, cudaStream_t s);
 int launch_zero4(int64_t n, double* a, double* b, double* c, double* d, cudaStream_t s);
+int launch_fill(int64_t n, double* a, double v, cudaStream_t s);
 
 // fmm_leafops.cu (prec 0: double arithmetic, 1: float arithmetic)
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,

@@ -42,7 +42,9 @@ class Config(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("basis", ctypes.c_int), ("prec", ctypes.c_int),
                 ("adaptive", ctypes.c_int), ("depth", ctypes.c_int), ("max_leaf", ctypes.c_int),
                 ("theta", ctypes.c_double), ("learned_p", ctypes.c_int),
-                ("target_rel_err", ctypes.c_double), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("target_rel_err", ctypes.c_double), ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("ap", ctypes.c_int),
+                ("binary_tree", ctypes.c_int)]
 
 
 _lib = None
@@ -231,10 +233,12 @@ class Plan:
     """Owns an fmm_plan (uniform octree FMM of App. C)."""
 
     def __init__(self, p, basis=BASIS_SYM, prec=FP64, depth=3, use_graph=False, adaptive=False,
-                 max_leaf=64, theta=0.5, learned_p=False, target_rel_err=1e-4, autotune=False):
+                 max_leaf=64, theta=0.5, learned_p=False, target_rel_err=1e-4, autotune=False, ap=False,
+                 binary_tree=False):
         cfg = Config(p=p, basis=basis, prec=prec, adaptive=int(adaptive), depth=depth, max_leaf=max_leaf,
                      theta=theta, learned_p=int(learned_p), target_rel_err=target_rel_err,
-                     use_graph=int(use_graph), autotune=int(autotune))
+                     use_graph=int(use_graph), autotune=int(autotune), ap=int(ap),
+                     binary_tree=int(binary_tree))
         h = _vp()
         _check(lib().fmm_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h

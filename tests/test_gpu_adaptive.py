@@ -122,3 +122,65 @@ def test_fp32_high_order_deep_tree(F, p, basis):
     assert np.all(np.isfinite(r32[0])) and np.all(np.isfinite(r32[1]))
     ep, ea = errs(r32[0], r32[1], r64[0], r64[1])
     assert ep < 2e-6 and ea < 2e-5, (ep, ea)
+
+
+@pytest.mark.parametrize("p,max_leaf,theta", [(4, 32, 0.6), (6, 64, 0.5)])
+def test_ap_variant_vs_oracle(F, p, max_leaf, theta):
+    """The AP variant (Sec. 3): centre-of-mass centres, dipole 0, gradient
+    only, against the oracle's AP FMM on the same tree (same lists; 1e-12 on
+    the accelerations)."""
+    n = 8000
+    x, y, z = inputs.plummer(n, 34)
+    q = inputs.masses_open_unit(n, 34)
+    plan = F.Plan(p=p, basis=F.BASIS_TRACELESS, prec=F.FP64, adaptive=True, max_leaf=max_leaf, theta=theta, ap=True)
+    pot, acc = plan.evaluate(g(x), g(y), g(z), g(q))
+    torch.cuda.synchronize()
+    st = plan.stats()
+    plan.close()
+    pref, aref, ost = oracle.fmm_adaptive_ap(x, y, z, q, max_leaf, theta, p)
+    assert (st["cells"], st["leaves"], st["m2l_pairs"], st["p2p_pairs"]) == \
+        (ost["nodes"], ost["leaves"], ost["m2l_pairs"], ost["p2p_pairs"])
+    assert not pot.any()
+    acc = acc.cpu().numpy()
+    assert np.linalg.norm(acc - aref) / np.linalg.norm(aref) < 1e-12
+    for bad in (dict(basis=F.BASIS_SYM), dict(prec=F.FP32), dict(adaptive=False)):
+        kw = dict(p=p, basis=F.BASIS_TRACELESS, prec=F.FP64, adaptive=True, ap=True)
+        kw.update(bad)
+        with pytest.raises(F.FMMError):
+            F.Plan(**kw)
+
+
+@pytest.mark.parametrize("p,basis,max_leaf,theta,dist", [(4, 0, 32, 0.5, "plummer"), (6, 1, 64, 0.6, "plummer"),
+                                                          (5, 1, 16, 0.5, "lattice")])
+def test_binary_tree_vs_oracle(F, p, basis, max_leaf, theta, dist):
+    """The binary median-split tree (App. C) built on the device: the same
+    node, leaf and list counts as the oracle's tree, the fields within 1e-12.
+    The lattice case puts many particles on equal coordinates, so the split
+    order of ties (kept in the current order) decides the tree."""
+    if dist == "plummer":
+        n = 7000
+        x, y, z = inputs.plummer(n, 41)
+    else:
+        k = np.arange(4096)
+        x, y, z = ((k % 16) / 16.0, ((k // 16) % 16) / 16.0 * 0.7, (k // 256) / 16.0 * 1.3)
+        n = 4096
+    q = inputs.masses_open_unit(n, 41)
+    plan = F.Plan(p=p, basis=basis, prec=F.FP64, adaptive=True, max_leaf=max_leaf, theta=theta, binary_tree=True)
+    pot, acc = plan.evaluate(g(x), g(y), g(z), g(q))
+    torch.cuda.synchronize()
+    st = plan.stats()
+    plan.close()
+    pref, aref, ost = oracle.fmm_btree(x, y, z, q, max_leaf, theta, p, basis)
+    assert (st["cells"], st["leaves"], st["m2l_pairs"], st["p2p_pairs"]) == \
+        (ost["nodes"], ost["leaves"], ost["m2l_pairs"], ost["p2p_pairs"])
+    ep, ea = errs(pot.cpu().numpy(), acc.cpu().numpy(), pref, aref)
+    assert ep < 1e-12 and ea < 1e-12, (ep, ea)
+
+
+def test_binary_tree_configs(F):
+    """The binary tree is an FP64 adaptive option; other forms are refused."""
+    for bad in (dict(prec=F.FP32), dict(adaptive=False), dict(ap=True), dict(learned_p=True)):
+        kw = dict(p=4, basis=F.BASIS_TRACELESS, prec=F.FP64, adaptive=True, binary_tree=True)
+        kw.update(bad)
+        with pytest.raises(F.FMMError):
+            F.Plan(**kw)
