@@ -10,7 +10,13 @@ import oracle
 from paper_1811_06332_gb300 import inputs
 
 
-@pytest.mark.parametrize("gen,n,ml", [(inputs.plummer, 5000, 32), (inputs.blobs, 4096, 16)])
+def lattice(n, seed):
+    """Points on a 16 x 16 x 16 lattice (many equal coordinates: ties)."""
+    k = np.arange(n)
+    return (k % 16) / 16.0, ((k // 16) % 16) / 16.0 * 0.7, (k // 256) / 16.0 * 1.3
+
+
+@pytest.mark.parametrize("gen,n,ml", [(inputs.plummer, 5000, 32), (inputs.blobs, 4096, 16), (lattice, 4096, 16)])
 def test_structure_median_splits_and_shrink_wrap(gen, n, ml):
     x, y, z = gen(n, 41)
     P = np.stack([x, y, z], 1)
@@ -37,6 +43,27 @@ def test_structure_median_splits_and_shrink_wrap(gen, n, ml):
         left = P[order[rg[a, 0]:rg[a, 1]], axis]
         right = P[order[rg[b, 0]:rg[b, 1]], axis]
         assert left.max() <= right.min()
+    # the same tree built independently with numpy: breadth-first, each split
+    # a stable sort (ties keep the parent's current order) by the longest
+    # side of the bounding box, lower half first; every node's particle
+    # sequence must match the oracle's final order at its leaves
+    seqs = [np.arange(n)]
+    k = 0
+    while k < len(seqs):
+        sq = seqs[k]
+        if len(sq) > ml:
+            pts = P[sq]
+            ax = int(np.argmax(pts.max(0) - pts.min(0)))
+            srt = sq[np.argsort(pts[:, ax], kind="stable")]
+            h = len(sq) // 2
+            seqs += [srt[:h], srt[h:]]
+        k += 1
+    assert len(seqs) == nn
+    for c in range(nn):
+        if not kids[c]:
+            np.testing.assert_array_equal(order[rg[c, 0]:rg[c, 1]], seqs[c])
+        else:
+            assert sorted(order[rg[c, 0]:rg[c, 1]].tolist()) == sorted(seqs[c].tolist())
 
 
 def test_lists_cover_every_pair_and_theta_zero_is_direct():
