@@ -45,7 +45,15 @@ NOMINAL = {"sm_count": 152, "fp64_fma_per_clk_sm": 2, "fp32_fma_per_clk_sm": 128
 # scaled by the cells of the levels it runs on, with the profile summary it
 # comes from; a form is absent while its kernel has changed since its
 # counters were taken (traffic is then reported as null).
-M2L_TRAFFIC = {}
+# key: (form, tensor-core kernel, chunk width) -- (None, None) for the ALU forms
+M2L_TRAFFIC = {
+    # k_m2l_tc_slab<0, 4>, cw 48: 787.1 MB read + 155.9 MB written at level 6, x 9/8 for levels 5-6
+    ("bf16x3", 0, 48): (1.0609e9, "ncu capture of the level-6 launch scaled by cells to levels 5-6 "
+                                  "(profiles/m2l_tensorcore_bf16x3_level6_uniform4M_p8.md)"),
+    # m2l_grp_p8_b1_r0: 653.9 MB read + 154.4 MB written at level 6, x 299584/262144 for levels 2-6
+    ("fp32", None, None): (9.237e8, "ncu capture of the level-6 launch scaled by cells to levels 2-6 "
+                                    "(profiles/m2l_grouped_fp32_level6_uniform4M_p8.md)"),
+}
 # nominal dense tensor rates (PFLOP/s): a TF32 contraction takes the measured
 # BF16 peak scaled by their ratio
 NOMINAL_TENSOR = {"bf16": 2.25, "tf32": 1.1}
@@ -371,7 +379,8 @@ def run_gpu(args):
     else:
         peak = NOMINAL["sm_count"] * NOMINAL["fp32_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
         peak_note = "FP32 ALU: 152 SMs x 128 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
-    traffic, traffic_src = M2L_TRAFFIC.get(form, (None, "no capture of the current kernel"))
+    tkey = (form, tc["shape"]["kernel"], tc["shape"]["cw"]) if tc is not None else (form, None, None)
+    traffic, traffic_src = M2L_TRAFFIC.get(tkey, (None, "no capture of this kernel and shape"))
     achieved = npairs * afma * 2 / (m2l_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "m2l (levels 2..6, %d pairs per step)" % npairs,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -640,18 +649,45 @@ def run_adaptive(args):
     return 0
 
 
-def run_ap(args):
-    """AP variant (Sec. 3): the batching-form workload (8,388,608 Plummer
-    particles, adaptive octree <= 64 per leaf, MAC theta 0.6, p = 6) in the
-    fully traceless form about centres of mass, dipole 0, gradient only, FP64;
-    beside it the same FP64 traceless FMM about geometric centres.  One step =
-    fmm_evaluate (tree, centres of mass, traversal, operators)."""
+def stage_breakdown(F, plan, X, out, flush):
+    """One pass of the plan's operator sequence through the per-operator
+    entry points (after one untimed pass), with CUDA events between them."""
+    import torch
+    names = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p"]
+    tb = {}
+    for k in range(2):
+        flush.fill_(float(k))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        ev[0].record()
+        plan.fmm_build_tree(*X); ev[1].record()
+        plan.fmm_p2m(); ev[2].record()
+        plan.fmm_m2m(); ev[3].record()
+        plan.fmm_m2l(); ev[4].record()
+        plan.fmm_l2l(); ev[5].record()
+        plan.fmm_l2p(out[0], out[1], out[2], out[3]); ev[6].record()
+        plan.fmm_p2p(out[0], out[1], out[2], out[3]); ev[7].record()
+        torch.cuda.synchronize()
+        tb = {nm: ev[i].elapsed_time(ev[i + 1]) for i, nm in enumerate(names)}
+    return tb
+
+
+def run_variant(args):
+    """Sec. 3 and App. C variants on the batching-form workload (8,388,608
+    Plummer particles, MAC theta 0.6, traceless p = 6, FP64): --workload ap:
+    the AP variant (centre-of-mass centres, dipole 0, gradient only) on the
+    adaptive octree with <= 64 particles per leaf; --workload binary: the
+    binary median-split tree with shrink-wrapped cells, at leaf bounds 64, 32
+    and 16 (a median split leaves 32..64 particles per leaf at bound 64,
+    against 19 on average for the octree), the fastest reported.  Beside
+    each, the same FP64 traceless FMM on the adaptive octree (<= 64 per leaf)
+    about geometric centres.  One step = fmm_evaluate (tree, centres,
+    traversal, operators)."""
     import torch
 
     from paper_1811_06332_gb300 import fmm as F
     from paper_1811_06332_gb300 import inputs
     dev = torch.device("cuda", 0)
-    n, p, ml, theta = 8388608, 6, 64, 0.6
+    n, p, theta = 8388608, 6, 0.6
     x, y, z = inputs.plummer(n, 4)
     q = inputs.masses_equal(n)
     X = [torch.from_numpy(a).to(dev) for a in (x, y, z, q)]
@@ -660,9 +696,15 @@ def run_ap(args):
     tsel = torch.from_numpy(np.sort(np.unique((inputs.u01(4, 95, 4096) * n).astype(np.int64)))).to(dev)
     ref = torch.empty((4, len(tsel)), dtype=torch.float64, device=dev)
     F.fmm_direct(X[0], X[1], X[2], X[3], ref[0], ref[1], ref[2], ref[3], targets=tsel)
+    kind = args.workload
+    runs = [("octree_geometric", 64, {})]
+    if kind == "ap":
+        runs.append(("ap", 64, dict(ap=True)))
+    else:
+        runs += [("binary_leaf%d" % ml, ml, dict(binary_tree=True)) for ml in (64, 32, 16)]
     res = {}
-    for name, ap in (("ap", True), ("ft_geometric", False)):
-        plan = F.Plan(p=p, basis=F.BASIS_TRACELESS, prec=F.FP64, adaptive=True, max_leaf=ml, theta=theta, ap=ap)
+    for name, ml, kw in runs:
+        plan = F.Plan(p=p, basis=F.BASIS_TRACELESS, prec=F.FP64, adaptive=True, max_leaf=ml, theta=theta, **kw)
         times = []
         for k in range(args.warmup + args.steps):
             flush.fill_(float(k))
@@ -675,18 +717,23 @@ def run_ap(args):
                 times.append(e0.elapsed_time(e1))
         acc = out[1:, tsel]
         err = float(torch.sqrt(((acc - ref[1:]) ** 2).sum() / (ref[1:] ** 2).sum()).item())
-        res[name] = {"ms_per_step": float(np.mean(times)), "rel_force_err": err, "stats": plan.stats()}
+        res[name] = {"max_leaf": ml, "ms_per_step": float(np.mean(times)), "rel_force_err": err,
+                     "stage_ms": stage_breakdown(F, plan, X, out, flush), "stats": plan.stats()}
         plan.close()
-    ms = res["ap"]["ms_per_step"]
+    best = min((k for k in res if k != "octree_geometric"), key=lambda k: res[k]["ms_per_step"])
+    ms = res[best]["ms_per_step"]
+    form = {"ap": "AP variant (centre-of-mass centres, dipole 0, gradient only), FP64",
+            "binary": "binary median-split tree, shrink-wrapped cells, FT, FP64"}[kind]
+    tree = {"ap": "adaptive octree <= 64 per leaf",
+            "binary": "binary median-split tree <= %d per leaf" % res[best]["max_leaf"]}[kind]
     line = {"metric": METRIC, "value": n / (ms * 1e-3), "unit": "particles/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Plummer sphere, 8,388,608 particles, equal masses, adaptive octree <= 64 per "
-                                   "leaf, MAC theta 0.6, traceless p=6",
-                       "form": "AP variant (centre-of-mass centres, dipole 0, gradient only), FP64",
-                       "l2": "flushed before each step"},
-            "rel_force_err": res["ap"]["rel_force_err"], "ap": res["ap"], "ft_geometric_centres": res["ft_geometric"],
-            "vs_geometric_centres": res["ft_geometric"]["ms_per_step"] / ms}
+            "config": {"workload": "Plummer sphere, 8,388,608 particles, equal masses, %s, MAC theta 0.6, "
+                                   "traceless p=6" % tree,
+                       "form": form, "l2": "flushed before each step"},
+            "rel_force_err": res[best]["rel_force_err"], "runs": res,
+            "vs_octree_geometric_centres": res["octree_geometric"]["ms_per_step"] / ms}
     print(json.dumps(line))
     return 0
 
@@ -815,7 +862,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="bf16x3", choices=["fp64", "fp32", "bf16x3", "tf32x3"])
-    ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l", "adaptive", "learned", "ap"])
+    ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l", "adaptive", "learned", "ap", "binary"])
     ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -834,8 +881,8 @@ def main():
         return run_adaptive(args)
     if args.workload == "learned":
         return run_learned(args)
-    if args.workload == "ap":
-        return run_ap(args)
+    if args.workload in ("ap", "binary"):
+        return run_variant(args)
     return run_gpu(args)
 
 
