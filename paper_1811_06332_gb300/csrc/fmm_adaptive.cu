@@ -660,8 +660,7 @@ k_p2p_tree(int nwork, const int* __restrict__ work, const int* __restrict__ off,
                         for (int j = grp; j < cnt; j += G) {
                             const T dx = sx[w][j] - xi, dy = sy[w][j] - yi, dz = sz[w][j] - zi;
                             const T r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 == T(0)) continue;   // self pair and coincident pairs
-                            const T ir = fmm_rsqrt(r2);
+                            const T ir = r2 > T(0) ? fmm_rsqrt(r2) : T(0);   // self and coincident pairs: 0
                             const T qir = sq[w][j] * ir, qir3 = qir * ir * ir;
                             ph += qir; gx += qir3 * dx; gy += qir3 * dy; gz += qir3 * dz;
                         }

@@ -7,7 +7,10 @@
 
 namespace fmm {
 
-__device__ __forceinline__ double fmm_rsqrt(double v) { return 1.0 / sqrt(v); }
+// 1/sqrt(v): CUDA's double-precision rsqrt (at most 1 ulp from the exact
+// value; one call in place of a rounded square root and a rounded division,
+// which on this part's FP64 units costs several times the rest of a pair)
+__device__ __forceinline__ double fmm_rsqrt(double v) { return rsqrt(v); }
 __device__ __forceinline__ float fmm_rsqrt(float v) { return rsqrtf(v); }
 
 // Storage positions (App. D multi-indices; App. A compressed order).

@@ -1,5 +1,6 @@
 // General-shift M2M, L2L, L2P (operator-level entry points, FP64 or FP32
 // storage and arithmetic) and the FP64 direct sum.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -361,43 +362,84 @@ int m2m_fused_terms(int p) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 direct sum (Eq. PhiAB), shared-memory tiles of sources.
+// FP64 direct sum (Eq. PhiAB), shared-memory tiles of sources.  A block
+// takes 256 targets and the sources of its slice blockIdx.y of gridDim.y;
+// with one slice it writes the result, with several it writes its partial
+// sums to part[slice][4][nt], which k_direct_sum adds in slice order (the
+// result does not depend on scheduling).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_direct(int64_t n, const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
          const double* __restrict__ q, int64_t nt, const int64_t* __restrict__ targets, double* __restrict__ pot,
-         double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az) {
+         double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az, double* __restrict__ part) {
     __shared__ double sx[256], sy[256], sz[256], sq[256];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = t < nt;
     const int64_t i = act ? (targets ? targets[t] : t) : 0;
     const double xi = act ? x[i] : 0.0, yi = act ? y[i] : 0.0, zi = act ? z[i] : 0.0;
+    // the slice: whole tiles of 256 sources
+    const int64_t ntile = (n + 255) / 256, per = (ntile + gridDim.y - 1) / gridDim.y;
+    const int64_t s0 = (int64_t)blockIdx.y * per * 256, s1 = min(n, s0 + per * 256);
     double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-    for (int64_t b = 0; b < n; b += 256) {
+    for (int64_t b = s0; b < s1; b += 256) {
         const int64_t j = b + threadIdx.x;
         __syncthreads();
-        if (j < n) { sx[threadIdx.x] = x[j]; sy[threadIdx.x] = y[j]; sz[threadIdx.x] = z[j]; sq[threadIdx.x] = q[j]; }
+        if (j < s1) { sx[threadIdx.x] = x[j]; sy[threadIdx.x] = y[j]; sz[threadIdx.x] = z[j]; sq[threadIdx.x] = q[j]; }
         __syncthreads();
-        const int cnt = (int)min((int64_t)256, n - b);
+        const int cnt = (int)min((int64_t)256, s1 - b);
         for (int k = 0; k < cnt; ++k) {
-            if (b + k == i) continue;
             const double dx = sx[k] - xi, dy = sy[k] - yi, dz = sz[k] - zi;
             const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 == 0.0) continue;
-            const double ir = 1.0 / sqrt(r2);
+            // the self pair and coincident pairs contribute 0
+            const double ir = (b + k != i && r2 > 0.0) ? fmm_rsqrt(r2) : 0.0;
             const double qir3 = sq[k] * ir * ir * ir;
             ph += sq[k] * ir;
             gx += qir3 * dx; gy += qir3 * dy; gz += qir3 * dz;
         }
     }
-    if (act) { pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz; }
+    if (!act) return;
+    if (gridDim.y == 1) {
+        pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
+    } else {
+        double* o = part + (int64_t)blockIdx.y * 4 * nt;
+        o[t] = ph; o[nt + t] = gx; o[2 * nt + t] = gy; o[3 * nt + t] = gz;
+    }
+}
+
+__global__ void k_direct_sum(int64_t nt, int nsl, const double* __restrict__ part, double* __restrict__ pot,
+                             double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double ph = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int k = 0; k < nsl; ++k) {
+        const double* o = part + (int64_t)k * 4 * nt;
+        ph += o[t]; gx += o[nt + t]; gy += o[2 * nt + t]; gz += o[3 * nt + t];
+    }
+    pot[t] = -ph; ax[t] = gx; ay[t] = gy; az[t] = gz;
 }
 
 int launch_direct(int64_t n, const double* x, const double* y, const double* z, const double* q, int64_t nt,
                   const int64_t* targets, double* pot, double* ax, double* ay, double* az, cudaStream_t s) {
     if (nt <= 0) return 0;
-    k_direct<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(n, x, y, z, q, nt, targets, pot, ax, ay, az);
+    const int64_t nbx = (nt + 255) / 256, ntile = (n + 255) / 256;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // slices of the sources so that about 4 blocks per SM run
+    int64_t nsl = (4 * (int64_t)sms + nbx - 1) / nbx;
+    nsl = std::max<int64_t>(1, std::min<int64_t>({nsl, 64, ntile}));
+    double* part = nullptr;
+    if (nsl > 1 && cudaMallocAsync((void**)&part, sizeof(double) * 4 * nt * nsl, s) != cudaSuccess) {
+        cudaGetLastError();
+        nsl = 1;   // no scratch: one slice
+    }
+    k_direct<<<dim3((unsigned)nbx, (unsigned)nsl), 256, 0, s>>>(n, x, y, z, q, nt, targets, pot, ax, ay, az, part);
     count_launch();
+    if (nsl > 1) {
+        k_direct_sum<<<(unsigned)nbx, 256, 0, s>>>(nt, (int)nsl, part, pot, ax, ay, az);
+        count_launch();
+        cudaFreeAsync(part, s);
+    }
     return 0;
 }
 

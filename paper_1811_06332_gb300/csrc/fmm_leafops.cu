@@ -357,8 +357,8 @@ k_p2p_leaf2(int depth, int64_t nleaf, const int* __restrict__ start, const doubl
                     for (int k = grp; k < cnt; k += G) {
                         const T dx = sx[w][k] - xi, dy = sy[w][k] - yi, dz = sz[w][k] - zi;
                         const T r2 = dx * dx + dy * dy + dz * dz;
-                        if (sid[w][k] == ti || r2 == T(0)) continue;
-                        const T ir = fmm_rsqrt(r2);
+                        // the self pair and coincident pairs contribute 0
+                        const T ir = (sid[w][k] != ti && r2 > T(0)) ? fmm_rsqrt(r2) : T(0);
                         const T qir = sq[w][k] * ir;
                         const T qir3 = qir * ir * ir;
                         ph += qir;
