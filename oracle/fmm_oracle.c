@@ -1050,8 +1050,10 @@ static void atree_build(atree_t* T, int64_t n, const double* x, const double* y,
 /* Binary median-split tree (App. C): a cell holding more than max_leaf      */
 /* particles is split across the longest axis of its particles' bounding    */
 /* box (the first of x, y, z on ties) into two children with equal numbers  */
-/* of particles (the lower floor(n/2) by that coordinate, ties in the order  */
-/* the particles already have: a stable sort), children first the lower one. */
+/* of particles (the lower floor(n/2) by that coordinate, equal coordinates */
+/* ordered by the particles' original index), the lower child first.  The   */
+/* paper does not say how ties are split; by original index the split of a  */
+/* cell depends only on its set of particles.                               */
 /* Cells are shrink-wrapped: the expansion centre is the centre of the       */
 /* bounding box of the cell's particles, (lo + hi) / 2 per axis; radii as   */
 /* for the octree.  Nodes are numbered level by level (breadth first).       */
@@ -1064,8 +1066,9 @@ static void merge_sort_kv(kv_t* v, kv_t* tmp, int64_t n) {
     merge_sort_kv(v + h, tmp, n - h);
     int64_t i = 0, j = h, k = 0;
     while (i < h && j < n) {
-        /* stable: take from the left run unless the right one is strictly smaller */
-        if (g_sort_coord[v[j].idx] < g_sort_coord[v[i].idx]) tmp[k++] = v[j++];
+        /* order by (coordinate, original index): equal coordinates by index */
+        const double cj = g_sort_coord[v[j].idx], ci = g_sort_coord[v[i].idx];
+        if (cj < ci || (cj == ci && v[j].idx < v[i].idx)) tmp[k++] = v[j++];
         else tmp[k++] = v[i++];
     }
     while (i < h) tmp[k++] = v[i++];

@@ -11,12 +11,14 @@ from paper_1811_06332_gb300 import inputs
 
 
 def lattice(n, seed):
-    """Points on a 16 x 16 x 16 lattice (many equal coordinates: ties)."""
-    k = np.arange(n)
-    return (k % 16) / 16.0, ((k // 16) % 16) / 16.0 * 0.7, (k // 256) / 16.0 * 1.3
+    """Points with every coordinate drawn from 5 values (seeded): most
+    medians fall inside a run of equal coordinates, so the tie rule decides
+    which particles go to which child."""
+    a = np.floor(inputs.u01(seed, 0, 3 * n) * 5).reshape(3, n)
+    return a[0] / 5.0, a[1] / 5.0 * 0.7, a[2] / 5.0 * 1.3
 
 
-@pytest.mark.parametrize("gen,n,ml", [(inputs.plummer, 5000, 32), (inputs.blobs, 4096, 16), (lattice, 4096, 16)])
+@pytest.mark.parametrize("gen,n,ml", [(inputs.plummer, 5000, 32), (inputs.blobs, 4096, 16), (lattice, 3000, 16)])
 def test_structure_median_splits_and_shrink_wrap(gen, n, ml):
     x, y, z = gen(n, 41)
     P = np.stack([x, y, z], 1)
@@ -44,9 +46,9 @@ def test_structure_median_splits_and_shrink_wrap(gen, n, ml):
         right = P[order[rg[b, 0]:rg[b, 1]], axis]
         assert left.max() <= right.min()
     # the same tree built independently with numpy: breadth-first, each split
-    # a stable sort (ties keep the parent's current order) by the longest
-    # side of the bounding box, lower half first; every node's particle
-    # sequence must match the oracle's final order at its leaves
+    # a sort by (coordinate, original index) along the longest side of the
+    # bounding box, lower half first; every leaf's particle sequence must
+    # match the oracle's final order
     seqs = [np.arange(n)]
     k = 0
     while k < len(seqs):
@@ -54,7 +56,7 @@ def test_structure_median_splits_and_shrink_wrap(gen, n, ml):
         if len(sq) > ml:
             pts = P[sq]
             ax = int(np.argmax(pts.max(0) - pts.min(0)))
-            srt = sq[np.argsort(pts[:, ax], kind="stable")]
+            srt = sq[np.lexsort((sq, pts[:, ax]))]
             h = len(sq) // 2
             seqs += [srt[:h], srt[h:]]
         k += 1
