@@ -23,9 +23,13 @@ struct AdState {
     double *zc = nullptr, *rad = nullptr;
     int ap = 0;             // AP variant: centre-of-mass centres (Q: total charge per node)
     int binary = 0;         // binary median-split tree (App. C) instead of the octree
-    int *axis = nullptr, *segstart = nullptr, *segof = nullptr;
-    unsigned char* axis_at = nullptr;
-    size_t cap_axis = 0, cap_segstart = 0, cap_segof = 0, cap_axis_at = 0;
+    // binary tree: split axis per node; per axis a permutation of the
+    // particles sorted by (coordinate, index) within every cell (and its
+    // next-level copy), the side of the split per particle, the node holding
+    // each sorted position, partition flags and their scan
+    int *axis = nullptr, *btP = nullptr, *btnode = nullptr, *btflag = nullptr, *btscan = nullptr;
+    unsigned char* btside = nullptr;
+    size_t cap_axis = 0, cap_btP = 0, cap_btnode = 0, cap_btflag = 0, cap_btscan = 0, cap_btside = 0;
     double* Q = nullptr;
     size_t cap_Q = 0;
     float* radf = nullptr;   // radii / (side / 2^22) rounded to FP32 (MAC screen)
@@ -96,15 +100,18 @@ int ad_bucket_csr(int n, int nn, const uint64_t* key, const int* val, const int*
 int ad_iota(int n, int* a, cudaStream_t s);
 
 // fmm_btree.cu (binary median-split tree)
-int bt_nodes(int lb, int le, int max_leaf, const int* nb, const int* ne, const int* perm, const double* x,
+int bt_axis_keys(int64_t n, const double* c, uint64_t* key, int* val, cudaStream_t s);
+int bt_nodes(int lb, int le, int max_leaf, const int* nb, const int* ne, const int* P, int64_t n, const double* x,
              const double* y, const double* z, double* zc, int* axis, int* nsplit, cudaStream_t s);
 int bt_children(int lb, int le, const int* nsplit, const int* off, int* lev, int* nb, int* ne, int* child0,
                 int* nchild, int* parent, cudaStream_t s);
-int bt_reorder_keys(int64_t n, int lb, int le, const int* nb, const int* ne, const int* nchild, const int* axis,
-                    unsigned char* axis_at, const int* perm, const int* segstart, const double* x, const double* y,
-                    const double* z, uint64_t* key, int* val, int* segof, cudaStream_t s);
-int bt_keys2(int64_t n, const int* val, const int* segof, uint64_t* key, cudaStream_t s);
-int bt_segstart(int lb, int le, const int* nb, const int* ne, const int* nchild, int* segstart, cudaStream_t s);
+int bt_side(int64_t n, int lb, int le, const int* node, const int* nb, const int* ne, const int* nchild,
+            const int* axis, const int* P, unsigned char* side, cudaStream_t s);
+int bt_flags(int64_t n, const int* Pa, const unsigned char* side, int* flag, cudaStream_t s);
+int bt_partition(int64_t n, int lb, int le, const int* node, const int* nb, const int* ne, const int* nchild,
+                 const int* Pa, const int* scan, int* Pn, cudaStream_t s);
+int bt_advance(int64_t n, int lb, int le, int* node, const int* nb, const int* ne, const int* nchild,
+               const int* child0, cudaStream_t s);
 
 // fmm_adaptive.cu
 void radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,

@@ -39,7 +39,7 @@ static int grow_bytes(void** p, size_t* cap, size_t need, unsigned* gen) {
 
 void ad_free(AdState* a) {
     if (!a) return;
-    void* ptrs[] = {a->Q, a->axis, a->segstart, a->segof, a->axis_at, a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
+    void* ptrs[] = {a->Q, a->axis, a->btP, a->btnode, a->btflag, a->btscan, a->btside, a->xs, a->ys, a->zs, a->qs, a->perm, a->k0, a->k1, a->v0, a->v1, a->hist, a->hsum, a->scr,
                     a->box, a->part, a->lev, a->ix, a->iy, a->iz, a->nb, a->ne, a->child0, a->nchild, a->parent,
                     a->zc, a->rad, a->radf, a->bounds, a->nch, a->choff, a->q0, a->q1, a->cm, a->cp, a->cq, a->om, a->op,
                     a->oq, a->tmode, a->m2l, a->p2p, a->moff, a->msrc, a->poff, a->psrc, a->order, a->leaf, a->ic,
@@ -70,17 +70,28 @@ static int sort_pairs(AdState* a, int64_t n, int bits, cudaStream_t s) {
     return 0;
 }
 
-// Binary median-split tree (App. C; fmm_btree.cu): nodes level by level,
-// the particles reordered within the cells each level splits, then the
-// sorted particles, the node centres (bounding-box centres) and radii.
+// Binary median-split tree (App. C; fmm_btree.cu): three permutations
+// sorted by (coordinate, index), then level by level the nodes (bounding
+// boxes from the permutations), their children and a stable partition of
+// each permutation by the side of the split; finally the sorted particles,
+// centres and radii.
 static int build_binary(AdState* a, int64_t n, const double* x, const double* y, const double* z, const double* q,
                         int max_leaf, cudaStream_t s) {
-    GROW(a->perm, a->cap_perm, n * 4);
-    GROW(a->segstart, a->cap_segstart, n * 4);
-    GROW(a->segof, a->cap_segof, n * 4);
-    GROW(a->axis_at, a->cap_axis_at, n);
-    ad_iota((int)n, a->perm, s);
-    cudaMemsetAsync(a->segstart, 0, n * 4, s);
+    GROW(a->btP, a->cap_btP, (size_t)n * 24);          // P_x, P_y, P_z and their next-level copies
+    GROW(a->btnode, a->cap_btnode, (size_t)n * 4);
+    GROW(a->btflag, a->cap_btflag, (size_t)(n + 1) * 4);
+    GROW(a->btscan, a->cap_btscan, (size_t)(n + 1) * 4);
+    GROW(a->btside, a->cap_btside, (size_t)n);
+    int* P = a->btP;
+    int* Pn = a->btP + 3 * n;
+    const double* co[3] = {x, y, z};
+    for (int d = 0; d < 3; ++d) {
+        bt_axis_keys(n, co[d], a->k0, a->v0, s);
+        if (int r = sort_pairs(a, n, 64, s)) return r;
+        cudaMemcpyAsync(P + d * n, a->v0, n * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    cudaMemsetAsync(a->btnode, 0, n * 4, s);
+    cudaMemsetAsync(a->btside, 0, n, s);
     int cap = 1024;
     auto node_cap = [&](int need) -> int {
         const size_t nd = (size_t)need;
@@ -109,7 +120,7 @@ static int build_binary(AdState* a, int64_t n, const double* x, const double* y,
         const int m = le - lb;
         GROW(a->nch, a->cap_nch, (size_t)(m + 1) * 4);
         GROW(a->choff, a->cap_choff, (size_t)(m + 1) * 4);
-        bt_nodes(lb, le, max_leaf, a->nb, a->ne, a->perm, x, y, z, a->zc, a->axis, a->nch, s);
+        bt_nodes(lb, le, max_leaf, a->nb, a->ne, P, n, x, y, z, a->zc, a->axis, a->nch, s);
         int tot = 0;
         if (scan_total(a->nch, a->choff, m, a->scr, &tot, s)) return -2;
         if (le + tot > cap) {
@@ -118,22 +129,22 @@ static int build_binary(AdState* a, int64_t n, const double* x, const double* y,
         }
         bt_children(lb, le, a->nch, a->choff, a->lev, a->nb, a->ne, a->child0, a->nchild, a->parent, s);
         if (tot > 0) {
-            // reorder the particles of the split cells: by the split coordinate,
-            // then (stably) by the start of their cell
-            bt_reorder_keys(n, lb, le, a->nb, a->ne, a->nchild, a->axis, a->axis_at, a->perm, a->segstart, x, y, z,
-                            a->k0, a->v0, a->segof, s);
-            if (int r = sort_pairs(a, n, 64, s)) return r;
-            bt_keys2(n, a->v0, a->segof, a->k0, s);
-            int bits = 1;
-            while ((1ll << bits) < n) ++bits;
-            if (int r = sort_pairs(a, n, bits, s)) return r;
-            cudaMemcpyAsync(a->perm, a->v0, n * 4, cudaMemcpyDeviceToDevice, s);
-            bt_segstart(lb, le, a->nb, a->ne, a->nchild, a->segstart, s);
+            bt_side(n, lb, le, a->btnode, a->nb, a->ne, a->nchild, a->axis, P, a->btside, s);
+            for (int d = 0; d < 3; ++d) {
+                bt_flags(n, P + d * n, a->btside, a->btflag, s);
+                scan_excl_int(a->btflag, a->btscan, n, a->scr, s);
+                bt_partition(n, lb, le, a->btnode, a->nb, a->ne, a->nchild, P + d * n, a->btscan, Pn + d * n, s);
+            }
+            std::swap(P, Pn);
+            bt_advance(n, lb, le, a->btnode, a->nb, a->ne, a->nchild, a->child0, s);
         }
         lb = le;
         le = le + tot;
     }
     a->nn = le;
+    // sorted order: P_x (every cell's particles contiguous, by x inside a leaf)
+    GROW(a->perm, a->cap_perm, n * 4);
+    cudaMemcpyAsync(a->perm, P, n * 4, cudaMemcpyDeviceToDevice, s);
     ad_gather(n, a->perm, x, y, z, q, a->xs, a->ys, a->zs, a->qs, s);
     GROW(a->rad, a->cap_rad, (size_t)a->nn * 8);
     for (int L = (int)a->lvl.size() - 2; L >= 0; --L)

@@ -155,15 +155,16 @@ def test_ap_variant_vs_oracle(F, p, max_leaf, theta):
 def test_binary_tree_vs_oracle(F, p, basis, max_leaf, theta, dist):
     """The binary median-split tree (App. C) built on the device: the same
     node, leaf and list counts as the oracle's tree, the fields within 1e-12.
-    The lattice case puts many particles on equal coordinates, so the split
-    order of ties (kept in the current order) decides the tree."""
+    The lattice case draws every coordinate from 5 values, so most medians
+    fall inside runs of equal coordinates and the tie rule (by original
+    index) decides the tree."""
     if dist == "plummer":
         n = 7000
         x, y, z = inputs.plummer(n, 41)
     else:
-        k = np.arange(4096)
-        x, y, z = ((k % 16) / 16.0, ((k // 16) % 16) / 16.0 * 0.7, (k // 256) / 16.0 * 1.3)
-        n = 4096
+        n = 3000
+        a = np.floor(inputs.u01(41, 0, 3 * n) * 5).reshape(3, n)   # every coordinate one of 5 values
+        x, y, z = a[0] / 5.0, a[1] / 5.0 * 0.7, a[2] / 5.0 * 1.3
     q = inputs.masses_open_unit(n, 41)
     plan = F.Plan(p=p, basis=basis, prec=F.FP64, adaptive=True, max_leaf=max_leaf, theta=theta, binary_tree=True)
     pot, acc = plan.evaluate(g(x), g(y), g(z), g(q))
