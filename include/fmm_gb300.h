@@ -122,8 +122,9 @@ typedef struct {
                               median-split tree of App. C instead of the octree: a
                               cell of more than max_leaf particles is halved across
                               the longest side of its particles' bounding box (the
-                              lower floor(n/2) by that coordinate, ties in the current
-                              order; the first of x, y, z when sides tie), cells
+                              lower floor(n/2) by that coordinate, equal coordinates
+                              by original index; the first of x, y, z when sides
+                              tie), cells
                               shrink-wrapped and centred on their bounding boxes;
                               the same traversal, MAC and operators as the octree  */
 } fmm_config;
@@ -385,8 +386,11 @@ int fmm_tc_gen_layout(int p, int cw, int niss, int* out, int nout, uint32_t* gro
 /* Kernel shape of a tensor-core plan's M2L (Eq. M2L regrouped by offset).
  * kernel 0: each offset's matrix precomputed in global memory and streamed
  * into shared memory (BF16 or TF32 operands); kernel 1: each offset's matrix
- * built in shared memory from the offset's D vector (BF16 operands only).
- * cw: chunk width, the local components per MMA (16, 32, 48 or 96).
+ * built in shared memory from the offset's D vector (BF16 operands only);
+ * kernel 2: the matrix as the A operand (M = 128 local components) and the
+ * target cells of a tile as N (256 cells on levels >= 6, 128 on level 5),
+ * BF16 operands only.  cw: chunk width, the local components per MMA (16,
+ * 32, 48 or 96) for kernels 0 and 1; 256 for kernel 2.
  * fmm_set_tc_shape fixes the shape (rebuilding the plan's offset tables;
  * synchronous); FMM_ERR_ARG for a shape the plan's form has not.
  * fmm_plan_tuning writes to out[0..min(nout, 5 + 4 ncand)): kernel, cw,

@@ -95,11 +95,13 @@ static void* tc_maps_at(fmm_plan* pl, int l) {
 
 // ---------------------------------------------------------------------------
 // tensor-core kernel shape: kernel (0: streamed matrices, 1: matrices built
-// on chip, BF16 only) and chunk width; the autotuner times the candidates on
-// the plan's deepest level and keeps the fastest, cached on disk
+// on chip, BF16 only; 2: the matrix as the A operand and the cells of a tile
+// as N, BF16 only, cw = 256 its N) and chunk width; the autotuner times the
+// candidates on the plan's deepest level and keeps the fastest, cached on disk
 // ---------------------------------------------------------------------------
 static bool tc_shape_valid(int tf, int kern, int cw) {
     if (kern == 0) return cw == 16 || cw == 32 || cw == 48 || cw == 96;
+    if (kern == 2) return !tf && cw == 256;
     return kern == 1 && !tf && (cw == 16 || cw == 32 || cw == 48 || cw == 96);
 }
 
@@ -108,6 +110,9 @@ static int tc_set_shape(fmm_plan* pl, int kern, int cw, cudaStream_t s) {
     if (kern == 0) {
         if (tc_build_mat(pl->cfg.p, tf, cw, pl->Dtab, pl->Kbf, s) != 0) return -2;
         pl->tc_niss = tc_mat_niss(pl->cfg.p, tf, cw);
+    } else if (kern == 2) {
+        if (tct_bytes() > tc_mat_bytes(tf) || tct_build(pl->cfg.p, pl->Dtab, pl->Kbf, s) != 0) return -2;
+        pl->tc_niss = 2;
     } else {
         if (tg_build(pl->cfg.p, cw, 1, pl->Dtab, pl->Kgen, s) != 0) return -2;
         pl->tc_niss = 1;
@@ -140,7 +145,8 @@ static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
     char* hp = (char*)pl->Mbf + pl->mbf_off[l] * es;
     char* lp = hp + tc_m_elems(l) * es;
     return tc_m2l_level(pl->cfg.p, tf, pl->tc_kern, pl->tc_cw, pl->tc_niss, l, pl->Mbuf + pl->lvl_off[l], hp, lp,
-                        tc_maps_at(pl, l), pl->tc_kern ? pl->Kgen : pl->Kbf, pl->Lbuf + pl->lvl_off[l], pl->derr, s);
+                        tc_maps_at(pl, l), pl->tc_kern == 1 ? pl->Kgen : pl->Kbf, pl->Lbuf + pl->lvl_off[l], pl->derr,
+                        s);
 }
 
 // Times every candidate shape on level `l` (one warm-up and one timed
@@ -148,10 +154,10 @@ static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
 // and keeps the fastest.
 static int tc_autotune(fmm_plan* pl, int l, cudaStream_t s) {
     const int tf = pl->cfg.prec == FMM_GEMM_TF32X3;
-    static const int cand_bf16[][2] = {{0, 32}, {0, 48}, {0, 96}, {1, 48}, {1, 96}};
+    static const int cand_bf16[][2] = {{0, 32}, {0, 48}, {0, 96}, {1, 48}, {1, 96}, {2, 256}};
     static const int cand_tf32[][2] = {{0, 16}, {0, 32}, {0, 48}};
     const int (*cand)[2] = tf ? cand_tf32 : cand_bf16;
-    const int nc = tf ? 3 : 5;
+    const int nc = tf ? 3 : 6;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -2;
     int best = -1;

@@ -152,6 +152,13 @@ int tc_default_cw(int tf);
 int tc_mat_niss(int p, int tf, int cw);
 int tc_elem_bytes(int tf);
 size_t tc_m_elems(int l);
+// tensor-core M2L with the matrix as the A operand (fmm_m2l_tct.cu)
+int tct_np(int p);
+size_t tct_bytes();
+int tct_ty(int l);
+void tct_box(int l, unsigned (&box)[5]);
+int tct_build(int p, const double* Dtab, void* B, cudaStream_t s);
+int tct_m2l_level(int p, int l, const void* maps, const void* B, double* Lt, int* err, cudaStream_t s);
 size_t tc_maps_bytes();
 // kern 0: per-offset matrices streamed from global memory (tc_build_mat at
 // chunk width cw; niss follows from the layout); kern 1 (BF16 only): the

@@ -534,7 +534,12 @@ int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps) {
     const cuuint64_t hs = (cuuint64_t)1 << (l - 1);
     if (hs < 16) return -1;
     const cuuint32_t slab[5] = {(cuuint32_t)epc, SL_I, (cuuint32_t)TC_CH, SL_J, 1};
-    return encode_set(&maps->slab, tf, hi, lo, hs, slab) == 0 ? 0 : -1;
+    if (encode_set(&maps->slab, tf, hi, lo, hs, slab) != 0) return -1;
+    if (tf) return 0;
+    unsigned tb[5];
+    tct_box(l, tb);
+    const cuuint32_t tall[5] = {tb[0], tb[1], tb[2], tb[3], tb[4]};
+    return encode_set(&maps->tall, tf, hi, lo, hs, tall) == 0 ? 0 : -1;
 }
 size_t tc_maps_bytes() { return sizeof(TcLevelMaps); }
 
@@ -562,7 +567,7 @@ int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double*
     const int nc = ncoef_of(p, 1);
     if (ncell > ((int64_t)1 << 30)) return -1;   // 32-bit cell indices in k_tc_split_m
     const dim3 g((unsigned)((ncell + 255) / 256), (unsigned)(TC_K * tc_elem_bytes(tf) / 16));
-    if (kern == 1 && tf) return -1;   // the on-chip kernel takes BF16 operands
+    if ((kern == 1 || kern == 2) && tf) return -1;   // the on-chip and swapped kernels take BF16 operands
     // the on-chip kernel's matrices hold D_{n+m} alone: its operand carries 1/m!
     if (tf)
         k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, 0, M, hi, lo);
@@ -574,6 +579,7 @@ int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double*
         if (rc != 0) return rc;
         return cudaGetLastError() == cudaSuccess ? 0 : -2;
     }
+    if (kern == 2) return tct_m2l_level(p, l, maps, B, Lt, err, s);
     const TcChunks ch = tc_chunks(p, tf, cw);
     if (ch.niss != 2 && ch.niss != 4) return -1;
     const int rc = tf ? (ch.niss == 4 ? tc_launch<1, 4>(ch, l, nc, maps, B, Lt, ncell, err, s)

@@ -32,6 +32,7 @@ constexpr int SL_BYTES = SL_I * TC_CH * SL_J * 16;   // 34560: one slab operand 
 
 struct alignas(64) TcLevelMaps {
     TcMaps slab;    // box 10 x 18 x 1 cells, one K-part
+    TcMaps tall;    // BF16 only: box 10 x (TY + 2) x 1 cells, half a K-part (fmm_m2l_tct.cu)
 };
 
 static __device__ __forceinline__ uint32_t smem_u32(const void* p) {

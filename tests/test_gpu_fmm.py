@@ -176,6 +176,29 @@ def test_tensor_core_form_vs_oracle(F, depth, n):
     assert ep < 5e-6 and ea < 5e-6, (ep, ea, per)
 
 
+@pytest.mark.parametrize("depth,n,p", [(6, 262144, 8), (7, 1048576, 8), (6, 262144, 6), (5, 131072, 4)])
+def test_swapped_tensor_core_kernel_vs_oracle(F, depth, n, p):
+    """Kernel shape 2 (the offset's matrix as the A operand, 128 local
+    components; the cells of an 8 x 32 tile as N = 256, 8 x 16 on level 5;
+    two K-parts of 48 multipole components, or one at p <= 5), traceless,
+    against the FP64 oracle on sampled particles: depth 6 and 7 run the
+    256-cell tiles on levels 6 and 7 and the 128-cell tiles on level 5.
+    Bound: 5e-6 on pot and acc, as for the other shapes."""
+    x, y, z = inputs.uniform_cube(n, 31 + depth + p)
+    q = inputs.masses_equal(n)
+    plan = F.Plan(p=p, basis=1, prec=F.GEMM_BF16X3, depth=depth)
+    plan.set_tc_shape(2, 256)
+    pot, acc = plan.evaluate(*[g(a) for a in (x, y, z, q)])
+    plan.sync_status()
+    assert plan.tuning()["kernel"] == 2
+    plan.close()
+    pot, acc = pot.cpu().numpy(), acc.cpu().numpy()
+    s = np.sort(np.unique((inputs.u01(7, 94, 150) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, 1, sample=s)
+    ep, ea, per = errs(pot[s], acc[:, s], pref, aref)
+    assert ep < 5e-6 and ea < 5e-6, (ep, ea, per)
+
+
 @pytest.mark.parametrize("depth,n", [(5, 131072), (6, 262144)])
 def test_tensor_core_tf32_form_vs_oracle(F, depth, n):
     """The same offset-grouped tensor-core M2L with TF32 hi/lo operands
@@ -250,7 +273,7 @@ def test_tensor_core_form_rejects_unsupported(F):
             F.Plan(p=6, basis=0, prec=prec, depth=4)
 
 
-@pytest.mark.parametrize("form,shapes", [("GEMM_BF16X3", [(0, 32), (0, 48), (0, 96), (1, 48), (1, 96)]),
+@pytest.mark.parametrize("form,shapes", [("GEMM_BF16X3", [(0, 32), (0, 48), (0, 96), (1, 48), (1, 96), (2, 256)]),
                                          ("GEMM_TF32X3", [(0, 16), (0, 32), (0, 48)])])
 def test_every_tensor_core_shape_vs_oracle(F, form, shapes):
     """Every kernel shape the autotuner may pick (the streamed-matrix kernel
@@ -293,7 +316,7 @@ def test_autotuned_plan_and_its_cache(F, tmp_path, monkeypatch):
     plan.sync_status()
     t = plan.tuning()
     plan.close()
-    assert t["source"] == "autotuned" and len(t["candidates"]) == 5
+    assert t["source"] == "autotuned" and len(t["candidates"]) == 6
     best = min(t["candidates"], key=lambda c: c["us"])
     assert (t["kernel"], t["cw"]) == (best["kernel"], best["cw"])
     ep, ea, _ = errs(pot.cpu().numpy()[s], acc.cpu().numpy()[:, s], pref, aref)
