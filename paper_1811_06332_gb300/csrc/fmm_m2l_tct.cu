@@ -28,11 +28,13 @@
 // lo.hi), FP32 accumulation in TMEM, the two issuers' accumulators added in
 // FP64 at write-out.
 //
-// Roles: warp 0 lane 0 issues copies; lane 0 of warps 1 and 6 issue
-// tcgen05.mma, each into its own accumulator of N columns, taking the
-// matrix blocks alternately; warps 2..5 drain TMEM (each reads its lane
-// quadrant).  Every wait is bounded and reports a timeout through an error
-// word.
+// Roles: warp 0 lane 0 issues the slab loads and warp 7 lane 0 the matrix
+// copies (separately, so that the next slab is requested as soon as its
+// buffer is free); lane 0 of warps 1 and 6 issue tcgen05.mma, each into its
+// own accumulator of N columns, taking the matrix blocks alternately; warps
+// 2..5 drain TMEM (each reads its lane quadrant) and write L through a
+// shared-memory transpose.  Every wait is bounded and reports a timeout
+// through an error word.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -60,8 +62,10 @@ int tct_np(int p) { return (ncoef_of(p, 1) + 8 * TT_KP - 1) / (8 * TT_KP); }
 size_t tct_bytes() { return (size_t)343 * 2 * TT_BLK; }
 int tct_ty(int l) { return l >= 6 ? 32 : 16; }   // tile rows: the class grid has 2^(l-1) cells per axis
 
+constexpr int TT_THREADS = 256;
+
 template <int TY>
-__global__ void __launch_bounds__(224, 1)
+__global__ void __launch_bounds__(TT_THREADS, 1)
 k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const unsigned char* __restrict__ Kmat,
            double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
     constexpr int N = 8 * TY;
@@ -107,8 +111,9 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- producer ----------------
+    if ((warp == 0 || warp == 7) && lane == 0) {
+        // ---------------- producers: slabs (warp 0), matrices (warp 7) ----------------
+        const bool slabs = warp == 0;
         int sl = 0, bt = 0;
         bool ok = true;
         for (int sc = 0; sc < 8 && ok; ++sc) {
@@ -118,7 +123,9 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
                 const int oz = 2 * dz + sz - cz;
                 for (int pt = 0; pt < np && ok; ++pt) {
                     const int buf = sl & 1;
-                    if (!(ok = mbar_wait(smem_u32(&sempty[buf]), ((uint32_t)(sl >> 1) & 1u) ^ 1u, err, 21))) break;
+                    ++sl;
+                    if (slabs) {
+                    if (!(ok = mbar_wait(smem_u32(&sempty[buf]), ((uint32_t)((sl - 1) >> 1) & 1u) ^ 1u, err, 21))) break;
                     const uint32_t fb = smem_u32(&sfull[buf]);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * SLB)
                                  : "memory");
@@ -134,7 +141,8 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
                         " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(st + SLB)),
                         "l"((uint64_t)&maps.lo[sc]), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(fb)
                         : "memory");
-                    ++sl;
+                    continue;
+                    }
                     for (int dy = -1; dy <= 1 && ok; ++dy) {
                         const int oy = 2 * dy + sy - cy;
                         for (int dx = -1; dx <= 1; ++dx) {
@@ -162,10 +170,12 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
             }
         }
         // drain: every issued copy has landed before the CTA may exit
-        for (int k = sl > 2 ? sl - 2 : 0; k < sl; ++k)
-            mbar_wait(smem_u32(&sfull[k & 1]), (uint32_t)(k >> 1) & 1u, err, 23);
-        for (int k = bt > TT_NST ? bt - TT_NST : 0; k < bt; ++k)
-            mbar_wait(smem_u32(&bfull[k % TT_NST]), (uint32_t)(k / TT_NST) & 1u, err, 23);
+        if (slabs)
+            for (int k = sl > 2 ? sl - 2 : 0; k < sl; ++k)
+                mbar_wait(smem_u32(&sfull[k & 1]), (uint32_t)(k >> 1) & 1u, err, 23);
+        else
+            for (int k = bt > TT_NST ? bt - TT_NST : 0; k < bt; ++k)
+                mbar_wait(smem_u32(&bfull[k % TT_NST]), (uint32_t)(k / TT_NST) & 1u, err, 23);
     } else if ((warp == 1 || warp == 6) && lane == 0) {
         // ---------------- MMA issuers ----------------
         const int w = warp == 1 ? 0 : 1;
@@ -236,9 +246,13 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int q = warp & 3;
         const int n = q * 32 + lane;   // local component of this thread's TMEM lane
+        // a 32 x 33 FP64 tile per warp in the slab buffers (free: every copy
+        // has been consumed by the MMAs behind `done`)
+        double* tile = (double*)smem + (warp - 2) * 32 * 33;
         if (q * 32 < nrows) {
             const int64_t h3 = (int64_t)hs * hs * hs;
             const int64_t tbase = (int64_t)cls * h3 + ((int64_t)tk * hs + TY * tj) * hs + 8 * ti;
+            const int rmax = min(32, nrows - q * 32);   // rows of this quadrant holding local components
 #pragma unroll 1
             for (int cb = 0; cb < N / 32; ++cb) {
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
@@ -246,15 +260,16 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
                 tmem_ld32(ta, v0);
                 tmem_ld32(ta + (uint32_t)N, v1);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (ok && n < nrows) {
-                    double* row = Lt + (int64_t)n * ncell + tbase;
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int col = cb * 32 + e;   // cell (x, y) = (col % 8, col / 8) of the tile
-                        row[(int64_t)(col >> 3) * hs + (col & 7)] =
-                            (double)__uint_as_float(v0[e]) + (double)__uint_as_float(v1[e]);
-                    }
-                }
+                for (int e = 0; e < 32; ++e)
+                    tile[lane * 33 + e] = (double)__uint_as_float(v0[e]) + (double)__uint_as_float(v1[e]);
+                __syncwarp();
+                // lane = cell (x, y) = (col % 8, col / 8) of the tile, col = 32 cb + lane
+                const int col = cb * 32 + lane;
+                const int64_t cell = tbase + (int64_t)(col >> 3) * hs + (col & 7);
+                if (ok)
+                    for (int r = 0; r < rmax; ++r) Lt[(int64_t)(q * 32 + r) * ncell + cell] = tile[r * 33 + lane];
+                __syncwarp();
             }
         }
     }
@@ -324,7 +339,8 @@ static int tct_launch(int l, int np, int nc, const TcMaps& maps, const void* B, 
     if (cudaFuncSetAttribute(k_m2l_tc_t<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -2;
     const int tpc = (hs / 8) * (hs / TY) * hs;
-    k_m2l_tc_t<TY><<<(unsigned)(8 * tpc), 224, smem, s>>>(maps, l, np, nc, (const unsigned char*)B, Lt, ncell, err);
+    k_m2l_tc_t<TY><<<(unsigned)(8 * tpc), TT_THREADS, smem, s>>>(maps, l, np, nc, (const unsigned char*)B, Lt, ncell,
+                                                                 err);
     count_launch();
     return 0;
 }
