@@ -296,7 +296,7 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
 // Operand preparation
 // ---------------------------------------------------------------------------
 // Split of an FP64 value into hi + lo of the operand type.  BF16 rounds to
-// nearest even (the CUDA conversion); TF32 (a 32-bit container whose low 13
+// nearest even (the CUDA conversion, from the value rounded to FP32); TF32 (a 32-bit container whose low 13
 // mantissa bits are zero) rounds the FP32 value to nearest, ties away from
 // zero, on the magnitude bits.  Both parts are exact in the operand type, so
 // the tensor core reads them without further rounding.
@@ -308,17 +308,23 @@ struct TcSplit;
 template <>
 struct TcSplit<0> {
     using T = __nv_bfloat16;
+    // through FP32: one conversion from FP64 (this part's FP64 rate is 1/64
+    // of FP32), then hi = x rounded to BF16 and lo = the rest, whose FP32
+    // difference is exact; hi + lo keeps 16 bits of x, far above the 24 of
+    // the FP32 rounding
     static __device__ __forceinline__ void split(double x, T& h, T& l) {
-        h = __double2bfloat16(x);
-        l = __double2bfloat16(x - (double)__bfloat162float(h));
+        const float xf = (float)x;
+        h = __float2bfloat16_rn(xf);
+        l = __float2bfloat16_rn(xf - __bfloat162float(h));
     }
 };
 template <>
 struct TcSplit<1> {
     using T = uint32_t;
     static __device__ __forceinline__ void split(double x, T& h, T& l) {
-        h = tf32_round((float)x);
-        l = tf32_round((float)(x - (double)__uint_as_float(h)));
+        const float xf = (float)x;   // as for BF16: one conversion, the rest in FP32
+        h = tf32_round(xf);
+        l = tf32_round(xf - __uint_as_float(h));
     }
 };
 
