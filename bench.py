@@ -50,6 +50,9 @@ M2L_TRAFFIC = {
     # k_m2l_tc_slab<0, 4>, cw 48: 787.1 MB read + 155.9 MB written at level 6, x 9/8 for levels 5-6
     ("bf16x3", 0, 48): (1.0609e9, "ncu capture of the level-6 launch scaled by cells to levels 5-6 "
                                   "(profiles/m2l_tensorcore_bf16x3_level6_uniform4M_p8.md)"),
+    # k_m2l_tc_t<32> (kernel 2): 722.5 MB read + 154.8 MB written at level 6, x 9/8 for levels 5-6
+    ("bf16x3", 2, 256): (9.870e8, "ncu capture of the level-6 launch scaled by cells to levels 5-6 "
+                                  "(profiles/m2l_tensorcore_swapped_bf16x3_level6_uniform4M_p8.md)"),
     # m2l_grp_p8_b1_r0: 653.9 MB read + 154.4 MB written at level 6, x 299584/262144 for levels 2-6
     ("fp32", None, None): (9.237e8, "ncu capture of the level-6 launch scaled by cells to levels 2-6 "
                                     "(profiles/m2l_grouped_fp32_level6_uniform4M_p8.md)"),
@@ -370,9 +373,30 @@ def run_gpu(args):
         rk = [a for a in range(P + 1) for _ in range(2 * a + 1)]   # rank of each traceless component
         cols = sum(cw * ks * (((P - rk[r0] + 1) ** 2 + ks - 1) // ks) for r0 in range(0, nc, cw))
         tiles = sum(8 ** (l - 1) // 128 * 8 for l in range(5, DEPTH + 1))
-        # both kernels execute 3 cw columns per K-step and chunk (3 MMAs of N = cw, or the
-        # stacked hi/lo MMA of N = 2 cw and the lo.hi MMA of N = cw)
-        tc = {"executed_flop_per_step": tiles * 189 * 3 * 2 * 128 * cols, "shape": tuning}
+        # kernels 0 and 1 execute 3 cw columns per K-step and chunk (3 MMAs of N = cw, or the
+        # stacked hi/lo MMA of N = 2 cw and the lo.hi MMA of N = cw) for 128 cells per offset
+        ex = tiles * 189 * 3 * 2 * 128 * cols
+        if tuning["kernel"] == 2:
+            # kernel 2: per tile of 8 x TY cells (N) and offset, two K-parts x 3 K-steps x 3
+            # passes of M = 128 x N x 16; offsets of planes outside the grid are skipped
+            ex = 0
+            for l in range(5, DEPTH + 1):
+                hs = 1 << (l - 1)
+                ty = 32 if l >= 6 else 16
+                for c in range(8):
+                    cx, cy, cz = c & 1, (c >> 1) & 1, c >> 2
+                    for tk in range(hs):
+                        offs = 0
+                        for sc in range(8):
+                            sx, sy, sz = sc & 1, (sc >> 1) & 1, sc >> 2
+                            for dz in (-1, 0, 1):
+                                if not 0 <= tk + dz < hs:
+                                    continue
+                                oz = 2 * dz + sz - cz
+                                offs += sum(1 for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                                            if max(abs(2 * dx + sx - cx), abs(2 * dy + sy - cy), abs(oz)) > 1)
+                        ex += (hs // 8) * (hs // ty) * offs * 18 * 2 * 128 * (8 * ty) * 16
+        tc = {"executed_flop_per_step": ex, "shape": tuning}
     if prec == F.FP64:
         peak = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
         peak_note = "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz (nominal units, max clock)" % mhz
@@ -452,8 +476,10 @@ def run_gpu(args):
                                  "frac_of_F_tl_count": a64 / pk64,
                                  "peak_source": "FP64 ALU: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz" % mhz}}
         p64.close()
-    else:
+    elif prec == F.FP64:
         fp64 = {"value": value / world, "m2l_pairs_per_s": npairs / (m2l_ms * 1e-3), "ms_per_step": t_ms}
+    else:
+        fp64 = None   # --no-fp64: not measured
 
     # end to end through the host entry point (pinned host buffers)
     e2e = None
@@ -490,7 +516,7 @@ def run_gpu(args):
         "stage_ms": dict({s: float(per_stage[:, i].mean()) for i, s in enumerate(stages)}, m2l=m2l_ms),
         "m2l_pairs_per_s": world * npairs / (m2l_ms * 1e-3),
         "fp64_form": fp64,
-        "vs_fp64_form": value / world / fp64["value"],
+        "vs_fp64_form": value / world / fp64["value"] if fp64 else None,
         "roofline": roof,
         "roofline_per_op": per_op,
         "cpu_baseline": cpu,
