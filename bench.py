@@ -182,6 +182,18 @@ def roofline_per_op(stage, form, nc, depth, n, npart_pairs, pk, mhz, fp_peak, al
     out["p2p"] = {"bound": "alu", "achieved": ach, "peak": fp_peak, "unit": "TFLOP/s", "frac": ach / fp_peak,
                   "ms": stage["p2p"], "pairs": npart_pairs, "flop_per_pair": P2P_FLOP_PER_PAIR,
                   "pairs_per_s": npart_pairs / (stage["p2p"] * 1e-3)}
+    if "l2p_p2p" in stage:
+        # the fused pass: the near-field flops and the far-field evaluation
+        # (2 (ns(p) + 3 ns(p - 1)) flop per particle)
+        ns = lambda p: (p + 1) * (p + 2) * (p + 3) // 6   # noqa: E731
+        pp = int(round((nc ** 0.5) - 1))
+        l2p_flop = n * 2 * (ns(pp) + 3 * ns(pp - 1))
+        fl = p2p_flop + l2p_flop
+        ach = fl / (stage["l2p_p2p"] * 1e-3) / 1e12
+        out["l2p_p2p"] = {"bound": "alu", "achieved": ach, "peak": fp_peak, "unit": "TFLOP/s", "frac": ach / fp_peak,
+                          "ms": stage["l2p_p2p"], "flop": fl,
+                          "flop_are": "near field (flop_per_pair of p2p) and far-field evaluation per particle",
+                          "note": "one pass; the l2p and p2p entries time the two steps run separately"}
     m2l_ms = stage["m2l_2_4"] + stage["m2l_5_6"]
     ach = alg_m2l_flop / (m2l_ms * 1e-3) / 1e12
     out["m2l"] = {"bound": "alu" if tc_roof is None else "tensor", "achieved": ach,
@@ -302,8 +314,10 @@ def run_gpu(args):
     plan = F.Plan(p=P, basis=BASIS, prec=prec, depth=DEPTH, autotune=tc_form)
 
     # M2L runs as two calls, levels 2..4 and 5..6 (the tensor-core levels of
-    # the tensor-core forms), so that the dominant kernel is timed on its own
-    stages = ["tree", "p2m", "m2m", "m2l_2_4", "m2l_5_6", "l2l", "l2p", "p2p"]
+    # the tensor-core forms), so that the dominant kernel is timed on its own;
+    # the far and near field run as one call (fmm_l2p_p2p: one kernel in the
+    # FP32 and tensor-core forms)
+    stages = ["tree", "p2m", "m2m", "m2l_2_4", "m2l_5_6", "l2l", "l2p_p2p"]
     NST = len(stages)
 
     def step(ev):
@@ -314,8 +328,7 @@ def run_gpu(args):
         plan.fmm_m2l_levels(2, TC_LEVEL - 1); ev[4].record(stream)
         plan.fmm_m2l_levels(TC_LEVEL, DEPTH); ev[5].record(stream)
         plan.fmm_l2l(); ev[6].record(stream)
-        plan.fmm_l2p(out[0], out[1], out[2], out[3]); ev[7].record(stream)
-        plan.fmm_p2p(out[0], out[1], out[2], out[3]); ev[8].record(stream)
+        plan.fmm_l2p_p2p(out[0], out[1], out[2], out[3]); ev[7].record(stream)
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(NST + 1)] for _ in range(args.steps)]
     wev = [torch.cuda.Event(enable_timing=True) for _ in range(NST + 1)]
@@ -340,6 +353,17 @@ def run_gpu(args):
     step_ms = per_stage.sum(1)
     t_ms = max_over_ranks(float(step_ms.mean()), world, dist, dev)
     value = job_rate(N_PART, world, t_ms * 1e-3)
+
+    # breakdown of the far and near field as separate steps (untimed for the
+    # step; the second of two passes recorded), for the per-operator roofline
+    for k in range(2):
+        flush.fill_(3.0 + k)
+        eb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        eb[0].record(stream)
+        plan.fmm_l2p(out[0], out[1], out[2], out[3]); eb[1].record(stream)
+        plan.fmm_p2p(out[0], out[1], out[2], out[3]); eb[2].record(stream)
+        torch.cuda.synchronize()
+    sep = {"l2p": eb[0].elapsed_time(eb[1]), "p2p": eb[1].elapsed_time(eb[2])}
 
     # accuracy: relative force error against an FP64 direct sum on 4096 sampled targets
     torch.cuda.synchronize()
@@ -439,7 +463,7 @@ def run_gpu(args):
                 "m2l_all_levels_ms_per_step": m2l_ms}
 
     stage_mean = {st: float(per_stage[:, i].mean()) for i, st in enumerate(stages)}
-    per_op = roofline_per_op(stage_mean, form, (P + 1) ** 2, DEPTH, N_PART, p2p_pairs_uniform(x, y, z, DEPTH), pk,
+    per_op = roofline_per_op(dict(stage_mean, **sep), form, (P + 1) ** 2, DEPTH, N_PART, p2p_pairs_uniform(x, y, z, DEPTH), pk,
                              mhz, peak if prec == F.FP64 else
                              NOMINAL["sm_count"] * NOMINAL["fp32_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12,
                              npairs * 2 * afma, roof["peak"] if tc is not None else None)
@@ -514,6 +538,7 @@ def run_gpu(args):
                    "particles_per_gpu": N_PART, "m2l_pairs": npairs, "l2": "flushed (256 MiB write) before each step"},
         "rel_force_err": rel_err,
         "stage_ms": dict({s: float(per_stage[:, i].mean()) for i, s in enumerate(stages)}, m2l=m2l_ms),
+        "l2p_p2p_as_two_steps_ms": sep,
         "m2l_pairs_per_s": world * npairs / (m2l_ms * 1e-3),
         "fp64_form": fp64,
         "vs_fp64_form": value / world / fp64["value"] if fp64 else None,

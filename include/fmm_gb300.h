@@ -192,6 +192,12 @@ int fmm_l2p(fmm_plan* plan, double* pot, double* ax, double* ay, double* az, voi
 /* Near field (App. C direct sum over adjacent leaves, self excluded):
  * ADDS into pot, ax, ay, az (device, length n, caller order). */
 int fmm_p2p(fmm_plan* plan, double* pot, double* ax, double* ay, double* az, void* stream);
+/* L2P followed by P2P in one pass: writes (does not add) pot and acc of
+ * every particle with the far field of its leaf's local expansion and the
+ * near field of its adjacent leaves.  The result is that of fmm_l2p then
+ * fmm_p2p; plans of the FP32 and tensor-core forms on a uniform octree run
+ * one kernel (each output written once), the others run the two steps. */
+int fmm_l2p_p2p(fmm_plan* plan, double* pot, double* ax, double* ay, double* az, void* stream);
 
 /* fmm_build_tree + p2m + m2m + m2l + l2l + l2p + p2p on `stream`.
  * All arrays are device arrays of length n in caller order; outputs are
@@ -235,6 +241,15 @@ int fmm_evaluate_host(fmm_plan* plan, int64_t n, const double* x, const double* 
  * their kernels run and cannot see such a timeout; fmm_evaluate_host calls
  * this before it returns.  Synchronous. */
 int fmm_sync_status(fmm_plan* plan, void* stream);
+
+/* Self-test of the bounded waits of the tensor-core kernels (no counterpart
+ * in the paper): one kernel waits, with the kernels' own bounded wait, on
+ * an mbarrier that expects one arrival.  arrive != 0: the kernel arrives
+ * first and the wait completes (FMM_OK).  arrive == 0: nothing arrives, the
+ * wait gives up after `spin` polls, records its code in an error word and
+ * the kernel returns; the call reports FMM_ERR_TIMEOUT and the context stays
+ * usable.  FMM_ERR_ARG for spin < 1.  Synchronous on `stream`. */
+int fmm_selftest_wait(int64_t spin, int arrive, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Operator-level batched entry points (independent items, physical units).

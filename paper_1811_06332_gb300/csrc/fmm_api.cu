@@ -951,6 +951,21 @@ int fmm_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
     return FMM_OK;
 }
 
+int fmm_l2p_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void* stream) {
+    NEED_TREE();
+    if (pl->n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
+    if (!pl->ad && pl->pos32 && pl->depth >= 2) {
+        // the FP32 uniform form: far and near field in one kernel
+        launch_l2p_p2p32(pl->cfg.p, bL(pl), pl->depth, pl->nleaf, pl->start, pl->pos32, pl->perm, Llev(pl, pl->depth),
+                         g_tab[pl->dev], pot, ax, ay, az, S(stream));
+        CKLAUNCH();
+        return FMM_OK;
+    }
+    int rc;
+    if ((rc = fmm_l2p(pl, pot, ax, ay, az, stream))) return rc;
+    return fmm_p2p(pl, pot, ax, ay, az, stream);
+}
+
 int fmm_evaluate(fmm_plan* pl, int64_t n, const double* x, const double* y, const double* z, const double* q,
                  double* pot, double* ax, double* ay, double* az, void* stream) {
     if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
@@ -989,9 +1004,7 @@ int fmm_evaluate(fmm_plan* pl, int64_t n, const double* x, const double* y, cons
     if ((rc = fmm_m2m(pl, stream))) return rc;
     if ((rc = fmm_m2l(pl, stream))) return rc;
     if ((rc = fmm_l2l(pl, stream))) return rc;
-    if ((rc = fmm_l2p(pl, pot, ax, ay, az, stream))) return rc;
-    if ((rc = fmm_p2p(pl, pot, ax, ay, az, stream))) return rc;
-    return FMM_OK;
+    return fmm_l2p_p2p(pl, pot, ax, ay, az, stream);
 }
 
 int fmm_evaluate_dipoles(fmm_plan* pl, int64_t n, const double* x, const double* y, const double* z, const double* q,
@@ -1067,6 +1080,23 @@ int fmm_sync_status(fmm_plan* pl, void* stream) {
     CK(cudaMemset(pl->derr, 0, sizeof(int)));
     FAIL(FMM_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel gave up (code %d); the outputs of the work "
                           "queued since the previous status check are undefined", herr);
+}
+
+int fmm_selftest_wait(int64_t spin, int arrive, void* stream) {
+    fmm_plan* pl = nullptr;
+    if (spin < 1) FAIL(FMM_ERR_ARG, "spin must be >= 1");
+    cudaStream_t s = S(stream);
+    int* derr = nullptr;
+    if (cudaMalloc(&derr, sizeof(int)) != cudaSuccess) FAIL(FMM_ERR_OOM, "allocating the error word failed");
+    int herr = 0;
+    const bool ok = cudaMemsetAsync(derr, 0, sizeof(int), s) == cudaSuccess &&
+                    wait_selftest((long)spin, arrive ? 1 : 0, derr, s) == 0 &&
+                    cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                    cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(derr);
+    if (!ok) FAIL(FMM_ERR_CUDA, "the wait self-test failed to run: %s", cudaGetErrorString(cudaGetLastError()));
+    if (herr) FAIL(FMM_ERR_TIMEOUT, "the bounded wait gave up (code %d)", herr);
+    return FMM_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -139,6 +139,9 @@ namespace fmm {
 int launch_shift32(int p, int basis, int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,
                    int64_t ny, cudaStream_t s);
 int shift32_supported(int p, int basis);
+int launch_l2p_p2p32(int p, int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
+                     const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,
+                     cudaStream_t s);
 int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm, double* pot,
                  double* ax, double* ay, double* az, cudaStream_t s);
 
@@ -152,6 +155,7 @@ int tc_default_cw(int tf);
 int tc_mat_niss(int p, int tf, int cw);
 int tc_elem_bytes(int tf);
 size_t tc_m_elems(int l);
+int wait_selftest(long spin, int arrive, int* err, cudaStream_t s);
 // tensor-core M2L with the matrix as the A operand (fmm_m2l_tct.cu)
 int tct_np(int p);
 size_t tct_bytes();

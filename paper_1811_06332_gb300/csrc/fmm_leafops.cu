@@ -585,6 +585,201 @@ k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* _
     }
 }
 
+// ---------------------------------------------------------------------------
+// Far and near field in one pass (FP32 form, uniform octree): one warp per
+// target leaf evaluates the leaf's local expansion at its particles (the
+// arithmetic of k_l2p_leaf2, one target per lane), then the near field of
+// k_p2p32, and writes each particle's potential and acceleration once, in
+// the operation order of k_l2p_leaf2 followed by k_p2p32 (explicitly
+// rounded, so the result is that sequence's), without the separate write
+// and read-modify-write of the caller-order outputs.
+// ---------------------------------------------------------------------------
+// far field at one point (scaled offset r from the leaf centre): the
+// arithmetic of k_l2p_leaf2; not inlined, so that the expansion is read
+// from shared memory per point instead of being held in registers
+template <int P>
+__device__ __noinline__ float4 l2p_point32(const float* Ln, float rx, float ry, float rz) {
+    float fx[P + 1], fy[P + 1], fz[P + 1];
+    fx[0] = fy[0] = fz[0] = 1.f;
+#pragma unroll
+    for (int q = 1; q <= P; ++q) {
+        fx[q] = fx[q - 1] * rx * float(1.0 / q);
+        fy[q] = fy[q - 1] * ry * float(1.0 / q);
+        fz[q] = fz[q - 1] * rz * float(1.0 / q);
+    }
+    float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    l2p_all<P, float, 0>(Ln, fx, fy, fz, ph, gx, gy, gz);
+    return make_float4(ph, gx, gy, gz);
+}
+
+template <int P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const float4* __restrict__ pos,
+            const int* __restrict__ perm, const double* __restrict__ Lt, const float* __restrict__ expand,
+            DevOffsets off, double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay,
+            double* __restrict__ az) {
+    constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
+    constexpr int NN = nested_col_off<P, float>(P + 1, 0);
+    __shared__ float sA[WARPS][NS];
+    __shared__ __align__(16) float sN[WARPS][NN];
+    __shared__ float4 sF[WARPS][64];   // far field of a block of targets (potential, gradient; scaled units)
+    __shared__ float4 sP[WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * WARPS + w;
+    if (c >= nleaf) return;
+    const int b = start[c], e = start[c + 1];
+    if (b == e) return;
+    // the leaf's local expansion in the nested FP32 layout of k_l2p_leaf2
+    if (basis) {
+        constexpr int NT = (P + 1) * (P + 1);
+        for (int t = lane; t < NT; t += 32) sA[w][t] = float(Lt[(int64_t)t * nleaf + c]);
+        __syncwarp();
+        for (int s = lane; s < NS; s += 32) {
+            const int nx = c_sym_idx[s][0], ny = c_sym_idx[s][1], nz = c_sym_idx[s][2];
+            const int j = nx + ny + nz;
+            const int row = (j - nx) * (j - nx + 1) / 2 + nz;
+            const float* E = expand + off.expand[j] + row * (2 * j + 1);
+            float v = 0.f;
+            for (int t = 0; t < 2 * j + 1; ++t) v += E[t] * sA[w][j * j + t];
+            sN[w][nested_col_off<P, float>(nx, ny) + nz] = v;
+        }
+    } else {
+        for (int s = lane; s < NS; s += 32)
+            sN[w][nested_col_off<P, float>(c_sym_idx[s][0], c_sym_idx[s][1]) + c_sym_idx[s][2]] =
+                float(Lt[(int64_t)s * nleaf + c]);
+    }
+    __syncwarp();
+    const double inv_h = (double)(1 << depth);
+    const float* Ln = sN[w];
+    const int side = 1 << depth;
+    const float h = 1.0f / (float)side;
+    int ix, iy, iz;
+    cell_coords(depth, c, ix, iy, iz);
+    // the 27 neighbour leaves, one per lane (lane 0: the target leaf)
+    int cntS = 0, sbS = 0;
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+    if (lane < 27) {
+        const int d = lane == 0 ? 13 : lane <= 13 ? lane - 1 : lane;
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+        if (jx >= 0 && jy >= 0 && jz >= 0 && jx < side && jy < side && jz < side) {
+            const int64_t S = cell_index(depth, jx, jy, jz);
+            sbS = start[S];
+            cntS = start[S + 1] - sbS;
+            ox = dx * h; oy = dy * h; oz = dz * h;
+        }
+    }
+    int incl = cntS;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
+    const int nself = __shfl_sync(0xffffffffu, cntS, 0);
+    for (int t0 = b; t0 < e; t0 += 64) {
+        const int tn = min(64, e - t0), half = (tn + 1) >> 1;
+        // far field of the block's targets, one per lane
+#pragma unroll 1
+        for (int k = lane; k < tn; k += 32) {
+            const float4 v = pos[t0 + k];
+            sF[w][k] = l2p_point32<P>(Ln, v.x * (float)inv_h, v.y * (float)inv_h, v.z * (float)inv_h);
+        }
+        __syncwarp();
+        int tp = 1;
+        while (tp < half) tp <<= 1;
+        const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
+        const int ta = t0 + tl, tb = t0 + tl + tp;
+        const bool va = tl < tn, vb = tl + tp < tn;
+        const float4 pa = va ? pos[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 pb = vb ? pos[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float fa = 0.f, xa = 0.f, ya = 0.f, za = 0.f, fb = 0.f, xb = 0.f, yb = 0.f, zb = 0.f;
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            {
+                const int g = min(c0 + lane, total - 1);
+                int i = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, incl, i + step - 1);
+                    if (v <= g) i += step;
+                }
+                const int sbi = __shfl_sync(0xffffffffu, sbS, i), exi = __shfl_sync(0xffffffffu, excl, i);
+                const float oxi = __shfl_sync(0xffffffffu, ox, i), oyi = __shfl_sync(0xffffffffu, oy, i),
+                            ozi = __shfl_sync(0xffffffffu, oz, i);
+                __syncwarp();
+                if (c0 + lane < total) {
+                    const float4 v = pos[sbi + (g - exi)];
+                    sP[w][lane] = make_float4(v.x + oxi, v.y + oyi, v.z + ozi, v.w);
+                }
+                __syncwarp();
+            }
+            {
+                const int cnt = min(32, total - c0);
+                if (c0 < nself) {
+                    for (int k = grp; k < cnt; k += G) {
+                        const float4 sv = sP[w][k];
+                        p2p32_pair_guarded(sv, pa, fa, xa, ya, za);
+                        p2p32_pair_guarded(sv, pb, fb, xb, yb, zb);
+                    }
+                } else {
+#pragma unroll 2
+                    for (int k = grp; k < cnt; k += G) {
+                        const float4 sv = sP[w][k];
+                        p2p32_pair(sv, pa, fa, xa, ya, za);
+                        p2p32_pair(sv, pb, fb, xb, yb, zb);
+                    }
+                }
+            }
+        }
+        for (int o = tp; o < 32; o <<= 1) {
+            fa += __shfl_xor_sync(0xffffffffu, fa, o); xa += __shfl_xor_sync(0xffffffffu, xa, o);
+            ya += __shfl_xor_sync(0xffffffffu, ya, o); za += __shfl_xor_sync(0xffffffffu, za, o);
+            fb += __shfl_xor_sync(0xffffffffu, fb, o); xb += __shfl_xor_sync(0xffffffffu, xb, o);
+            yb += __shfl_xor_sync(0xffffffffu, yb, o); zb += __shfl_xor_sync(0xffffffffu, zb, o);
+        }
+        if (grp == 0) {
+            const double h2 = inv_h;
+            if (va) {
+                const int o = perm[ta];
+                const float4 F = sF[w][tl];
+                pot[o] = __dsub_rn(__dmul_rn(-(double)F.x, h2), (double)fa);
+                ax[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.y, h2), h2), (double)xa);
+                ay[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.z, h2), h2), (double)ya);
+                az[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.w, h2), h2), (double)za);
+            }
+            if (vb) {
+                const int o = perm[tb];
+                const float4 F = sF[w][tl + tp];
+                pot[o] = __dsub_rn(__dmul_rn(-(double)F.x, h2), (double)fb);
+                ax[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.y, h2), h2), (double)xb);
+                ay[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.z, h2), h2), (double)yb);
+                az[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.w, h2), h2), (double)zb);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int P>
+static void l2p_p2p32_p(int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
+                        const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,
+                        cudaStream_t s) {
+    constexpr int W = 4;
+    k_l2p_p2p32<P, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(basis, depth, nleaf, start, pos, perm, Lt,
+                                                                          Tb.expand32, Tb.offsets(), pot, ax, ay, az);
+}
+
+int launch_l2p_p2p32(int p, int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
+                     const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,
+                     cudaStream_t s) {
+    if (nleaf <= 0) return 0;
+#define CF(P) l2p_p2p32_p<P>(basis, depth, nleaf, start, pos, perm, Lt, Tb, pot, ax, ay, az, s)
+    FMM_P_SWITCH(p, CF)
+#undef CF
+    count_launch();
+    return 0;
+}
+
 int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm, double* pot,
                  double* ax, double* ay, double* az, cudaStream_t s) {
     if (nleaf <= 0) return 0;

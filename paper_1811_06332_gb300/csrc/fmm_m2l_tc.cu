@@ -401,6 +401,28 @@ __global__ void k_tc_build_b(int p, int nc, const TcChunks ch, const double* __r
     *(uint4*)(bh + ch.pbytes[pt] + boff) = *(const uint4*)vl;
 }
 
+// Self-test of the bounded wait: one mbarrier expecting one arrival; with
+// `arrive` thread 0 arrives before waiting, otherwise nothing ever arrives
+// and the wait gives up after `spin` polls, records code 99 and returns.
+__global__ void k_wait_selftest(long spin, int arrive, int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+        mbar_wait(smem_u32(&bar), 0u, err, 99, spin);
+    }
+}
+
+int wait_selftest(long spin, int arrive, int* err, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(spin, arrive, err);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------

@@ -39,10 +39,11 @@ static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Bounded parity wait on an mbarrier; on giving up it records `code` in the
-// error word and returns false.
-static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-    for (long it = 0; it < TC_SPIN; ++it) {
+// Bounded parity wait on an mbarrier; after `spin` polls it records `code`
+// in the error word and returns false.
+static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
+                                                 long spin = TC_SPIN) {
+    for (long it = 0; it < spin; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -24,7 +24,7 @@ EXPORTS = [
     "fmm_m2l", "fmm_m2l_levels", "fmm_tc_layout", "fmm_tc_gen_layout", "fmm_l2l", "fmm_l2p", "fmm_p2p", "fmm_evaluate",
     "fmm_evaluate_host", "fmm_evaluate_dipoles", "fmm_op_dtensor",
     "fmm_op_p2m", "fmm_op_m2m", "fmm_op_m2m_fused", "fmm_m2m_fused_terms", "fmm_op_m2l", "fmm_op_l2l", "fmm_op_l2p", "fmm_direct",
-    "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_sync_status", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
+    "fmm_kernel_launches", "fmm_evaluate_noalloc", "fmm_sync_status", "fmm_selftest_wait", "fmm_l2p_p2p", "fmm_plan_stats", "fmm_plan_pairs", "fmm_pair_data",
     "fmm_mlp_grad", "fmm_mlp_train", "fmm_mlp_predict", "fmm_set_mlp", "fmm_set_pair_orders",
     "fmm_plan_pair_orders", "fmm_set_tc_shape", "fmm_plan_tuning", "fmm_tune_cache_get", "fmm_tune_cache_put",
 ]
@@ -71,6 +71,7 @@ def lib():
             "fmm_l2l": ([_vp, _vp], _int),
             "fmm_l2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_p2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
+            "fmm_l2p_p2p": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_evaluate": ([_vp, _i64] + [_vp] * 9, _int),
             "fmm_evaluate_host": ([_vp, _i64] + [_vp] * 9, _int),
             "fmm_evaluate_dipoles": ([_vp, _i64] + [_vp] * 12, _int),
@@ -83,6 +84,7 @@ def lib():
             "fmm_op_l2l": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
             "fmm_op_l2p": ([_int, _int, _int, _i64, _vp, _vp, _vp, _vp], _int),
             "fmm_sync_status": ([_vp, _vp], _int),
+            "fmm_selftest_wait": ([ctypes.c_int64, _int, _vp], _int),
             "fmm_direct": ([_i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp], _int),
             "fmm_kernel_launches": ([], _i64),
             "fmm_evaluate_noalloc": ([_int, _int, _int, _i64] + [_vp] * 9, _int),
@@ -220,6 +222,12 @@ def fmm_mlp_predict(blob, feat, pred, stream=None):
     _check(lib().fmm_mlp_predict(b.ctypes.data, feat.shape[0], _ptr(feat), _ptr(pred), _stream(stream)))
 
 
+def fmm_selftest_wait(spin, arrive, stream=None):
+    """Bounded-wait self-test (fmm_selftest_wait): FMM_OK when the barrier is
+    arrived on; raises FMMError (FMM_ERR_TIMEOUT) when the wait gives up."""
+    _check(lib().fmm_selftest_wait(int(spin), int(arrive), _stream(stream)))
+
+
 def fmm_direct(x, y, z, q, pot, ax, ay, az, targets=None, stream=None):
     nt = len(targets) if targets is not None else len(x)
     _check(lib().fmm_direct(len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), nt, _ptr(targets), _ptr(pot),
@@ -281,6 +289,9 @@ class Plan:
 
     def fmm_p2p(self, pot, ax, ay, az, stream=None):
         self._c(lib().fmm_p2p(self.h, _ptr(pot), _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
+
+    def fmm_l2p_p2p(self, pot, ax, ay, az, stream=None):
+        self._c(lib().fmm_l2p_p2p(self.h, _ptr(pot), _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
 
     def fmm_evaluate(self, x, y, z, q, pot, ax, ay, az, stream=None):
         self._c(lib().fmm_evaluate(self.h, len(x), _ptr(x), _ptr(y), _ptr(z), _ptr(q), _ptr(pot), _ptr(ax),

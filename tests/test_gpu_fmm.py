@@ -85,6 +85,31 @@ def test_step_by_step_equals_evaluate(F):
     plan.close()
 
 
+@pytest.mark.parametrize("prec,p,basis,depth,n", [("FP32", 8, 1, 4, 70000), ("FP32", 6, 0, 3, 9000),
+                                                   ("GEMM_BF16X3", 8, 1, 5, 300000), ("FP32", 4, 1, 1, 2000),
+                                                   ("FP64", 5, 1, 3, 6000)])
+def test_fused_far_near_field_equals_the_two_steps(F, prec, p, basis, depth, n):
+    """fmm_l2p_p2p (one kernel for the FP32 and tensor-core forms on a
+    uniform octree; the two steps otherwise) writes exactly what fmm_l2p
+    followed by fmm_p2p writes: the same FP32 arithmetic in the same order
+    and explicitly rounded FP64 combinations.  Ragged leaves (Poisson counts,
+    some empty at depth 5 with 300,000 particles: about 9 per leaf)."""
+    x, y, z = inputs.uniform_cube(n, 70 + depth)
+    q = inputs.masses_open_unit(n, 70 + depth)
+    plan = F.Plan(p=p, basis=basis, prec=getattr(F, prec), depth=depth)
+    t = [g(a) for a in (x, y, z, q)]
+    two = torch.full((4, n), 7.0, device=DEV, dtype=torch.float64)
+    one = torch.full((4, n), -3.0, device=DEV, dtype=torch.float64)
+    plan.fmm_build_tree(*t)
+    plan.fmm_p2m(); plan.fmm_m2m(); plan.fmm_m2l(); plan.fmm_l2l()
+    plan.fmm_l2p(two[0], two[1], two[2], two[3])
+    plan.fmm_p2p(two[0], two[1], two[2], two[3])
+    plan.fmm_l2p_p2p(one[0], one[1], one[2], one[3])
+    plan.sync_status()
+    plan.close()
+    assert torch.equal(one, two)
+
+
 @pytest.mark.parametrize("depth", [0, 1, 2])
 def test_shallow_trees(F, depth):
     n = 1500
