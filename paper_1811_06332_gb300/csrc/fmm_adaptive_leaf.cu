@@ -234,9 +234,10 @@ k_ad_l2p(int basis, int nleaf, const int* __restrict__ leaf, const int* __restri
 
 // ---------------------------------------------------------------------------
 // FP32 P2P over the near-field lists: one warp per target leaf from an
-// atomic work counter (persistent grid).  Up to 64 targets per pass: above
-// 32 each lane keeps two, at or below 16 the targets are spread over lane
-// groups that split the staged sources and are summed by shuffles.
+// atomic work counter (persistent grid).  Targets in blocks of up to 32: tp
+// lanes per target set (4 or 8) hold NT targets each (8, 16, 24 or 32
+// slots), the 32 / tp lane groups split the staged sources and are summed by
+// shuffles, so a shared load of one source serves NT interactions.
 // Sources of up to 32 source leaves are taken together: a warp prefix sum of
 // their counts maps lane g of a chunk to (leaf, particle) by a fixed
 // five-step search, so every staged chunk holds 32 sources (float4: offset
@@ -283,6 +284,90 @@ __device__ __forceinline__ int p2p_stage(float4* ss, int lane, int c0, int total
     return min(32, total - c0);
 }
 
+// Near field of targets [t0, t0 + tn) of leaf c from all its source leaves
+// [k0, k1): lane (grp, tl) holds targets t0 + tl + tp j, j < NT.
+template <int NT>
+__device__ __forceinline__ void ad_p2p_block(int c, int4 ct, int k0, int k1, int t0, int tn, int tp, int lane,
+                                             float4* ss, const int* __restrict__ src, const int* __restrict__ nb,
+                                             const int* __restrict__ ne, const int4* __restrict__ ic, float scale,
+                                             const float4* __restrict__ pos32, const int* __restrict__ perm,
+                                             double* __restrict__ pot, double* __restrict__ ax,
+                                             double* __restrict__ ay, double* __restrict__ az) {
+    const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
+    float4 pt[NT];
+    float ph[NT], gx[NT], gy[NT], gz[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int k = tl + tp * j;
+        pt[j] = k < tn ? pos32[t0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ph[j] = 0.f; gx[j] = 0.f; gy[j] = 0.f; gz[j] = 0.f;
+    }
+    for (int kb = k0; kb < k1; kb += 32) {
+        // metadata of up to 32 source leaves, one per lane
+        const int kk = kb + lane;
+        int cntS = 0, sb = 0;
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (kk < k1) {
+            const int S = src[kk];
+            const int4 cs = ic[S];
+            ox = (float)(cs.x - ct.x) * scale;
+            oy = (float)(cs.y - ct.y) * scale;
+            oz = (float)(cs.z - ct.z) * scale;
+            sb = nb[S];
+            cntS = ne[S] - sb;
+        }
+        int incl = cntS;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
+        // the target leaf's own particles in this batch: [s0, s1) of the concatenation
+        const unsigned selfm = __ballot_sync(0xffffffffu, kk < k1 && src[kk < k1 ? kk : k0] == c);
+        int s0 = total, s1 = total;
+        if (selfm) {
+            const int sl = __ffs(selfm) - 1;
+            s0 = __shfl_sync(0xffffffffu, excl, sl);
+            s1 = __shfl_sync(0xffffffffu, incl, sl);
+        }
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            const int cnt = p2p_stage(ss, lane, c0, total, incl, excl, sb, ox, oy, oz, pos32);
+            if (c0 < s1 && c0 + 32 > s0) {
+                for (int k = grp; k < cnt; k += G) {
+                    const float4 sv = ss[k];
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) p2p_acc<true>(sv, pt[j].x, pt[j].y, pt[j].z, ph[j], gx[j], gy[j], gz[j]);
+                }
+            } else {
+#pragma unroll 2
+                for (int k = grp; k < cnt; k += G) {
+                    const float4 sv = ss[k];
+#pragma unroll
+                    for (int j = 0; j < NT; ++j)
+                        p2p_acc<false>(sv, pt[j].x, pt[j].y, pt[j].z, ph[j], gx[j], gy[j], gz[j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+        for (int o = tp; o < 32; o <<= 1) {
+            ph[j] += __shfl_xor_sync(0xffffffffu, ph[j], o); gx[j] += __shfl_xor_sync(0xffffffffu, gx[j], o);
+            gy[j] += __shfl_xor_sync(0xffffffffu, gy[j], o); gz[j] += __shfl_xor_sync(0xffffffffu, gz[j], o);
+        }
+    if (grp == 0) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const int k = tl + tp * j;
+            if (k < tn) {
+                const int o = perm[t0 + k];
+                pot[o] -= (double)ph[j]; ax[o] += (double)gx[j]; ay[o] += (double)gy[j]; az[o] += (double)gz[j];
+            }
+        }
+    }
+}
+
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_ad_p2p32(int nwork, const int* __restrict__ work, const int* __restrict__ off, const int* __restrict__ src,
@@ -300,88 +385,20 @@ k_ad_p2p32(int nwork, const int* __restrict__ work, const int* __restrict__ off,
         const int4 ct = ic[c];
         const int b = nb[c], e = ne[c];
         const int k0 = off[c], k1 = off[c + 1];
-        for (int t0 = b; t0 < e; t0 += 64) {
-            const int tn = min(64, e - t0);
-            const bool two = tn > 32;
-            int tp = 1;
-            while (tp < tn) tp <<= 1;
-            const int G = two ? 1 : 32 / tp, grp = two ? 0 : lane / tp, tl = two ? lane : lane % tp;
-            const int i0 = t0 + tl, i1 = t0 + 32 + lane;
-            const bool a0 = two ? true : tl < tn, a1 = two && lane < tn - 32;
-            const float4 p0 = a0 ? pos32[i0] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 p1 = a1 ? pos32[i1] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float ph0 = 0.f, gx0 = 0.f, gy0 = 0.f, gz0 = 0.f, ph1 = 0.f, gx1 = 0.f, gy1 = 0.f, gz1 = 0.f;
-            for (int kb = k0; kb < k1; kb += 32) {
-                // metadata of up to 32 source leaves, one per lane
-                const int kk = kb + lane;
-                int cntS = 0, sb = 0;
-                float ox = 0.f, oy = 0.f, oz = 0.f;
-                if (kk < k1) {
-                    const int S = src[kk];
-                    const int4 cs = ic[S];
-                    ox = (float)(cs.x - ct.x) * scale;
-                    oy = (float)(cs.y - ct.y) * scale;
-                    oz = (float)(cs.z - ct.z) * scale;
-                    sb = nb[S];
-                    cntS = ne[S] - sb;
-                }
-                int incl = cntS;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
-                // the target leaf's own particles in this batch: [s0, s1) of the concatenation
-                const unsigned selfm = __ballot_sync(0xffffffffu, kk < k1 && src[kk < k1 ? kk : k0] == c);
-                int s0 = total, s1 = total;
-                if (selfm) {
-                    const int sl = __ffs(selfm) - 1;
-                    s0 = __shfl_sync(0xffffffffu, excl, sl);
-                    s1 = __shfl_sync(0xffffffffu, incl, sl);
-                }
-                for (int c0 = 0; c0 < total; c0 += 32) {
-                    const int cnt = p2p_stage(ss[w], lane, c0, total, incl, excl, sb, ox, oy, oz, pos32);
-                    const bool guard = c0 < s1 && c0 + 32 > s0;
-                    if (two) {
-                        if (guard) {
-                            for (int j = 0; j < cnt; ++j) {
-                                const float4 sv = ss[w][j];
-                                p2p_acc<true>(sv, p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
-                                p2p_acc<true>(sv, p1.x, p1.y, p1.z, ph1, gx1, gy1, gz1);
-                            }
-                        } else {
-                            for (int j = 0; j < cnt; ++j) {
-                                const float4 sv = ss[w][j];
-                                p2p_acc<false>(sv, p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
-                                p2p_acc<false>(sv, p1.x, p1.y, p1.z, ph1, gx1, gy1, gz1);
-                            }
-                        }
-                    } else if (a0) {
-                        if (guard) {
-                            for (int j = grp; j < cnt; j += G)
-                                p2p_acc<true>(ss[w][j], p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
-                        } else {
-                            for (int j = grp; j < cnt; j += G)
-                                p2p_acc<false>(ss[w][j], p0.x, p0.y, p0.z, ph0, gx0, gy0, gz0);
-                        }
-                    }
-                }
-            }
-            if (!two) {
-                for (int o = tp; o < 32; o <<= 1) {
-                    ph0 += __shfl_xor_sync(0xffffffffu, ph0, o); gx0 += __shfl_xor_sync(0xffffffffu, gx0, o);
-                    gy0 += __shfl_xor_sync(0xffffffffu, gy0, o); gz0 += __shfl_xor_sync(0xffffffffu, gz0, o);
-                }
-            }
-            if (a0 && grp == 0) {
-                const int o = perm[i0];
-                pot[o] -= (double)ph0; ax[o] += (double)gx0; ay[o] += (double)gy0; az[o] += (double)gz0;
-            }
-            if (a1) {
-                const int o = perm[i1];
-                pot[o] -= (double)ph1; ax[o] += (double)gx1; ay[o] += (double)gy1; az[o] += (double)gz1;
-            }
+        for (int t0 = b; t0 < e; t0 += 32) {
+            const int tn = min(32, e - t0);
+            if (tn <= 8)
+                ad_p2p_block<2>(c, ct, k0, k1, t0, tn, 4, lane, ss[w], src, nb, ne, ic, scale, pos32, perm, pot, ax,
+                                ay, az);
+            else if (tn <= 16)
+                ad_p2p_block<2>(c, ct, k0, k1, t0, tn, 8, lane, ss[w], src, nb, ne, ic, scale, pos32, perm, pot, ax,
+                                ay, az);
+            else if (tn <= 24)
+                ad_p2p_block<3>(c, ct, k0, k1, t0, tn, 8, lane, ss[w], src, nb, ne, ic, scale, pos32, perm, pot, ax,
+                                ay, az);
+            else
+                ad_p2p_block<4>(c, ct, k0, k1, t0, tn, 8, lane, ss[w], src, nb, ne, ic, scale, pos32, perm, pot, ax,
+                                ay, az);
         }
     }
 }
