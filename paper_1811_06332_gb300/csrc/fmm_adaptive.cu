@@ -154,14 +154,15 @@ __global__ void __launch_bounds__(256) k_rs_scatter(int64_t n, const uint64_t* _
     }
 }
 
-// Sorts (key, val) by key bits [0, bits); buffers alternate, the result is
-// left in (k0, v0).  Scratch: hist (256 * nblk + 1 ints) and scan scratch.
-void radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,
-                int* scratch, cudaStream_t s) {
-    if (n <= 1) return;
+// Sorts (key, val) by key bits [0, bits), 8 bits per pass; buffers
+// alternate.  Returns 1 when the result is in (k1, v1) (an odd number of
+// passes), 0 when it is in (k0, v0).  Scratch: hist (256 * nblk + 1 ints)
+// and scan scratch.
+int radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,
+               int* scratch, cudaStream_t s) {
+    if (n <= 1) return 0;
     const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
-    int passes = (bits + 7) / 8;
-    if (passes & 1) ++passes;   // even number of passes: result back in (k0, v0)
+    const int passes = (bits + 7) / 8;
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = 8 * ps;
         uint64_t* ki = (ps & 1) ? k1 : k0;
@@ -174,6 +175,7 @@ void radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bit
         k_rs_scatter<<<nblk, 256, 0, s>>>(n, ki, vi, ko, vo, shift, nblk, hsum);
         count_launch();
     }
+    return passes & 1;
 }
 
 // ---------------------------------------------------------------------------

@@ -114,7 +114,7 @@ int bt_advance(int64_t n, int lb, int le, int* node, const int* nb, const int* n
                const int* child0, cudaStream_t s);
 
 // fmm_adaptive.cu
-void radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,
+int radix_sort(int64_t n, uint64_t* k0, int* v0, uint64_t* k1, int* v1, int bits, int* hist, int* hsum,
                 int* scratch, cudaStream_t s);
 int ad_bbox(int64_t n, const double* x, const double* y, const double* z, double* part, double* box, cudaStream_t s);
 int ad_morton(int64_t n, const double* x, const double* y, const double* z, const double* box, uint64_t* key,

@@ -61,12 +61,18 @@ static int scan_total(const int* in, int* out, int n, int* scr, int* tot, cudaSt
     return d2h_int(out + n, tot, s);
 }
 
-// sort (key, val) pairs by the low `bits` of key
+// sort (key, val) pairs by the low `bits` of key; the result is in (k0, v0)
+// afterwards (after an odd number of passes the two buffer pairs swap roles)
 static int sort_pairs(AdState* a, int64_t n, int bits, cudaStream_t s) {
     const int64_t nblk = (n + 2047) / 2048;
     GROW(a->hist, a->cap_hist, (256 * nblk + 1) * 4);
     GROW(a->hsum, a->cap_hsum, (256 * nblk + 1) * 4);
-    radix_sort(n, a->k0, a->v0, a->k1, a->v1, bits, a->hist, a->hsum, a->scr, s);
+    if (radix_sort(n, a->k0, a->v0, a->k1, a->v1, bits, a->hist, a->hsum, a->scr, s)) {
+        std::swap(a->k0, a->k1);
+        std::swap(a->cap_k0, a->cap_k1);
+        std::swap(a->v0, a->v1);
+        std::swap(a->cap_v0, a->cap_v1);
+    }
     return 0;
 }
 

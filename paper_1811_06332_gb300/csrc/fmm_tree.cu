@@ -67,12 +67,21 @@ __global__ void __launch_bounds__(1024) k_scan_block(const int* __restrict__ in,
         if (base + k < m) out[base + k] = ex;
         ex += v[k];
     }
-    if (tid == 1023 && bsum) bsum[blockIdx.x] = wsum[31];
+    if (tid == 1023) {
+        if (bsum) bsum[blockIdx.x] = wsum[31];
+        else out[m] = wsum[31];   // one block: its sum is the total
+    }
 }
 
-__global__ void k_scan_add(int* __restrict__ out, int64_t m, const int* __restrict__ bscan) {
+// adds the scanned block sums; the last element's thread also writes the total
+__global__ void k_scan_add(const int* __restrict__ in, int* __restrict__ out, int64_t m,
+                           const int* __restrict__ bscan) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[i] += bscan[i / 4096];
+    if (i < m) {
+        const int v = out[i] + bscan[i / 4096];
+        out[i] = v;
+        if (i == m - 1) out[m] = v + in[i];
+    }
 }
 
 __global__ void k_scan_total(const int* __restrict__ in, int* __restrict__ out, int64_t m) {
@@ -90,11 +99,12 @@ static void scan_excl(const int* in, int* out, int64_t m, int* scratch, cudaStre
         count_launch();
         if (nb > 1) {
             scan_excl(bsum, bscan, nb, bscan + align_up(nb + 1, 64), s);
-            k_scan_add<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(out, m, bscan);
+            k_scan_add<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(in, out, m, bscan);
             count_launch();
         }
+        return;
     }
-    k_scan_total<<<1, 32, 0, s>>>(in, out, m);
+    k_scan_total<<<1, 32, 0, s>>>(in, out, m);   // m == 0: the total is 0
     count_launch();
 }
 
