@@ -97,10 +97,14 @@ typedef struct {
                               the model, K_B the number of M2L pairs of the target
                               and its ancestors (errors of independent pairs add in
                               quadrature at a target)                                  */
-    int use_graph;         /* 1 (adaptive trees, non-default stream): after the first
-                              evaluation, capture the operator sequence P2M..P2P into
-                              a CUDA graph and replay it while the tree keeps its
-                              sizes and buffers                                        */
+    int use_graph;         /* 1 (non-default stream): adaptive trees capture the
+                              operator sequence P2M..P2P of fmm_evaluate into a CUDA
+                              graph after the first evaluation and replay it while
+                              the tree keeps its sizes and buffers; uniform octrees
+                              capture the whole step (tree and operators) at the
+                              second evaluation and replay it while n, the input and
+                              output arrays and the tensor-core kernel shape stay the
+                              same                                                     */
     int autotune;          /* tensor-core forms: 1 takes the kernel shape stored for
                               this GPU, p, basis, form and depth in the tuning cache
                               (the JSON file FMM_TUNE_CACHE, else

@@ -56,6 +56,8 @@ struct fmm_plan {
     void* Kgen = nullptr;                // BF16: group table + FP32 D vectors (on-chip-matrix kernel)
     int tc_kern = 0, tc_cw = 48, tc_niss = 4;   // kernel shape in use
     int tc_source = 0;                   // 0 default, 1 autotuned, 2 from the cache, 3 set by the caller
+    cudaGraphExec_t ugexec = nullptr;    // uniform plans with use_graph: the captured step
+    const void* ugkey[11] = {nullptr};   // what the captured step depends on
     int tc_ncand = 0;
     int tc_cand[8][4];                   // autotuner candidates: kernel, cw, niss, microseconds
     void* Mbf = nullptr;                 // per level >= 4: hi then lo operand tiles
@@ -314,6 +316,7 @@ int fmm_plan_stats(const fmm_plan* pl, int64_t* out, int nout) {
         int64_t cells = 0;
         for (int l = 0; l <= pl->depth; ++l) cells += (int64_t)1 << (3 * l);
         v[0] = cells; v[1] = pl->nleaf; v[6] = pl->depth + 1;
+        v[7] = pl->ugexec ? 1 : 0;
     }
     for (int k = 0; k < nout && k < 19; ++k) out[k] = v[k];
     return FMM_OK;
@@ -698,6 +701,7 @@ void fmm_destroy(fmm_plan* pl) {
     ad_free(pl->ad);
     free_tree(pl);
     cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32); cudaFree(pl->K64);
+    if (pl->ugexec) cudaGraphExecDestroy(pl->ugexec);
     cudaFree(pl->Kbf); cudaFree(pl->Kgen); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
     delete pl;
 }
@@ -971,6 +975,33 @@ int fmm_evaluate(fmm_plan* pl, int64_t n, const double* x, const double* y, cons
     if (!pl) return fail_plan(nullptr, FMM_ERR_ARG, "plan is NULL");
     if (n > 0 && (!pot || !ax || !ay || !az)) FAIL(FMM_ERR_ARG, "null output array");
     int rc;
+    if (!pl->ad && pl->cfg.use_graph && stream && n > 0 && pl->built && n == pl->n &&
+        !(is_tc(pl->cfg.prec) && pl->cfg.autotune && pl->tc_source == 0)) {
+        // uniform plan: the whole step (tree and operators) is captured once
+        // into a CUDA graph and replayed while the particle count, the
+        // arrays and the tensor-core kernel shape stay the same (the first
+        // evaluation, which allocates and autotunes, runs eagerly)
+        const void* key[11] = {x, y, z, q, pot, ax, ay, az, (const void*)(intptr_t)n,
+                               (const void*)(intptr_t)pl->tc_kern, (const void*)(intptr_t)pl->tc_cw};
+        if (!pl->ugexec || memcmp(key, pl->ugkey, sizeof key) != 0) {
+            if (pl->ugexec) { cudaGraphExecDestroy(pl->ugexec); pl->ugexec = nullptr; }
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(S(stream), cudaStreamCaptureModeThreadLocal));
+            const int r1 = fmm_build_tree(pl, n, x, y, z, q, stream) | fmm_p2m(pl, stream) | fmm_m2m(pl, stream) |
+                           fmm_m2l(pl, stream) | fmm_l2l(pl, stream) | fmm_l2p_p2p(pl, pot, ax, ay, az, stream);
+            const cudaError_t ce = cudaStreamEndCapture(S(stream), &g);
+            if (r1 || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                FAIL(FMM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&pl->ugexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) FAIL(FMM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+            memcpy(pl->ugkey, key, sizeof key);
+        }
+        CK(cudaGraphLaunch(pl->ugexec, S(stream)));
+        return FMM_OK;
+    }
     if ((rc = fmm_build_tree(pl, n, x, y, z, q, stream))) return rc;
     if (pl->ad && pl->cfg.use_graph && stream && n > 0 &&
         (pl->ad->m2l_blocks > 0 || (pl->cfg.learned_p && (pl->mlp_set || pl->ad->orders_fixed)))) {

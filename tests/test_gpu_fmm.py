@@ -406,3 +406,49 @@ def test_tg_basis_vs_oracle(F, p, depth):
     for prec in (F.FP32, F.GEMM_BF16X3):
         with pytest.raises(F.FMMError):
             F.Plan(p=p, basis=F.BASIS_TG, prec=prec, depth=depth)
+
+
+@pytest.mark.parametrize("prec,p,depth,n", [("GEMM_BF16X3", 8, 5, 150000), ("FP32", 6, 4, 40000),
+                                            ("FP64", 4, 3, 6000)])
+def test_uniform_graph_replay(F, prec, p, depth, n):
+    """use_graph on a uniform plan: the first evaluation runs eagerly, the
+    second captures the whole step (tree and operators) and later ones
+    replay it; with new particle positions in the same arrays the replayed
+    step equals an eager plan's result (to the rounding of the atomic FP64
+    accumulation of the small levels' grouped M2L, whose order may differ),
+    and new output arrays make it capture again."""
+    x, y, z = inputs.uniform_cube(n, 80 + depth)
+    q = inputs.masses_open_unit(n, 80 + depth)
+    x2, y2, z2 = inputs.uniform_cube(n, 90 + depth)
+    X = [g(a) for a in (x, y, z, q)]
+    stream = torch.cuda.Stream()
+    gp = F.Plan(p=p, basis=1, prec=getattr(F, prec), depth=depth, use_graph=True)
+    ep = F.Plan(p=p, basis=1, prec=getattr(F, prec), depth=depth)
+    if prec == "GEMM_BF16X3":
+        gp.set_tc_shape(2, 256)
+        ep.set_tc_shape(2, 256)
+    out = torch.empty((4, n), device=DEV, dtype=torch.float64)
+    with torch.cuda.stream(stream):
+        for k in range(3):
+            if k == 2:   # new positions, same arrays
+                for t, a in zip(X[:3], (x2, y2, z2)):
+                    t.copy_(torch.from_numpy(a).to(DEV))
+            gp.fmm_evaluate(*X, out[0], out[1], out[2], out[3], stream=stream)
+    stream.synchronize()
+    assert gp.stats()["graph"] == 1
+    ref = torch.empty_like(out)
+    ep.fmm_evaluate(*X, ref[0], ref[1], ref[2], ref[3])
+    torch.cuda.synchronize()
+
+    def close(a, b):
+        d = (a - b).abs().amax(dim=1)
+        return bool((d <= 1e-12 * b.abs().amax(dim=1)).all())
+    assert close(out, ref)
+    out2 = torch.empty_like(out)
+    with torch.cuda.stream(stream):
+        gp.fmm_evaluate(*X, out2[0], out2[1], out2[2], out2[3], stream=stream)
+    stream.synchronize()
+    gp.sync_status()
+    assert close(out2, ref)
+    gp.close()
+    ep.close()
