@@ -613,6 +613,18 @@ def run_m2l_sweep(args):
                     "pairs_per_s": n / (ms * 1e-3), "ms": ms, "GB_per_s": gbs,
                     "hbm_frac": gbs / pk.get("hbm_gbs", 6800.0), "alg_fma_per_pair": fma, "TFLOP_s": tfl,
                     "alu_frac": tfl / alu_peak, "alu_peak_tflops": alu_peak}
+            if not args.no_cpu:
+                # the FP64 oracle's per-pair M2L (D by Eq. Detracer3, the literal
+                # double loop) on the host cores, on the first 2^12 offsets with
+                # seeded coefficients (the time does not depend on their values)
+                import oracle
+                ns_ = 1 << 12
+                Mh = inputs.u01(2, 40 + p, nc * ns_).reshape(nc, ns_)
+                t0 = time.perf_counter()
+                oracle.m2l_batch(p, basis, Mh, r[:, :ns_])
+                dt = time.perf_counter() - t0
+                res["oracle_cpu"] = {"pairs_per_s": ns_ / dt, "cores": oracle.num_threads(),
+                                     "sample": "first 4096 pairs, FP64"}
             print(json.dumps({"workload": "m2l per-pair, 2^20 pairs", "p": p,
                               "basis": "sym" if basis == 0 else "traceless", **res,
                               "fp32_vs_fp64": res["fp32"]["pairs_per_s"] / res["fp64"]["pairs_per_s"]}))
@@ -696,6 +708,79 @@ def run_adaptive(args):
             "tree": res["fp32"]["stats"],
             "fp64_form": {"value": v64, "ms_per_step": res["fp64"]["ms_per_step"]} if v64 else None,
             "vs_fp64_form": v32 / v64 if v64 else None}
+    print(json.dumps(line))
+    return 0
+
+
+def run_small(args):
+    """Small uniform workload: 4,096 particles U[0,1)^3, masses 1 - U[0,1),
+    uniform octree of depth 3, symmetric p = 4, FP64 (launch-bound).  Per
+    step fmm_evaluate with the tree build, and the operators alone (P2M ..
+    P2P after one build); both eager and replayed from a CUDA graph, the
+    median of at least 20 warm replays; the FP64 oracle FMM and the direct
+    sum on the host cores beside them; errors against the direct sum."""
+    import torch
+
+    import oracle
+    from paper_1811_06332_gb300 import fmm as F
+    from paper_1811_06332_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    n, depth, p = 4096, 3, 4
+    x, y, z = inputs.uniform_cube(n, 1)
+    q = inputs.masses_open_unit(n, 1)
+    X = [torch.from_numpy(a).to(dev) for a in (x, y, z, q)]
+    out = torch.empty((4, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream()
+    reps = max(20, args.steps)
+
+    def median_ms(fn):
+        ts = []
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup + reps):
+                e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                stream.synchronize()
+                if k >= args.warmup:
+                    ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    res = {}
+    for name, graph in (("eager", False), ("graph", True)):
+        plan = F.Plan(p=p, basis=F.BASIS_SYM, prec=F.FP64, depth=depth, use_graph=graph)
+        ev = lambda: plan.fmm_evaluate(*X, out[0], out[1], out[2], out[3], stream=stream)   # noqa: E731
+
+        def ops():
+            plan.fmm_p2m(stream=stream); plan.fmm_m2m(stream=stream); plan.fmm_m2l(stream=stream)
+            plan.fmm_l2l(stream=stream); plan.fmm_l2p_p2p(out[0], out[1], out[2], out[3], stream=stream)
+        res[name] = {"with_tree_ms": median_ms(ev)}
+        if not graph:
+            res[name]["operators_only_ms"] = median_ms(ops)
+        res[name]["graph_in_use"] = bool(plan.stats()["graph"])
+        plan.close()
+    torch.cuda.synchronize()
+    pot, acc = out[0].cpu().numpy(), out[1:].cpu().numpy()
+    t0 = time.perf_counter()
+    pd, ad = oracle.direct(x, y, z, q)
+    t_direct = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    po, ao = oracle.fmm_uniform(x, y, z, q, depth, p, 0)
+    t_fmm = time.perf_counter() - t0
+    err = float(np.linalg.norm(acc - ad) / np.linalg.norm(ad))
+    ms = res["graph"]["with_tree_ms"]
+    line = {"metric": METRIC, "value": n / (ms * 1e-3), "unit": "particles/s", "n_gpus": 1, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "uniform cube, 4,096 particles, masses 1 - U[0,1), depth-3 octree, symmetric p=4",
+                       "timing": "median of %d warm steps, not flushed (the working set is ~1 MB)" % reps,
+                       "step": "fmm_evaluate with the tree build, replayed from a CUDA graph"},
+            "rel_force_err": err,
+            "vs_oracle_fmm_rel_err": float(np.linalg.norm(acc - ao) / np.linalg.norm(ao)),
+            "forms": res,
+            "cpu_baseline": {"value": n / t_fmm, "unit": "particles/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": "the whole workload: oracle FMM (FP64)",
+                             "direct_sum_s": t_direct}}
     print(json.dumps(line))
     return 0
 
@@ -913,7 +998,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="bf16x3", choices=["fp64", "fp32", "bf16x3", "tf32x3"])
-    ap.add_argument("--workload", default="fmm", choices=["fmm", "m2l", "adaptive", "learned", "ap", "binary"])
+    ap.add_argument("--workload", default="fmm", choices=["fmm", "small", "m2l", "adaptive", "learned", "ap", "binary"])
     ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -928,6 +1013,8 @@ def main():
     g.build()
     if args.workload == "m2l":
         return run_m2l_sweep(args)
+    if args.workload == "small":
+        return run_small(args)
     if args.workload == "adaptive":
         return run_adaptive(args)
     if args.workload == "learned":

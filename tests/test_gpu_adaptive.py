@@ -151,7 +151,7 @@ def test_ap_variant_vs_oracle(F, p, max_leaf, theta):
 
 
 @pytest.mark.parametrize("p,basis,max_leaf,theta,dist", [(4, 0, 32, 0.5, "plummer"), (6, 1, 64, 0.6, "plummer"),
-                                                          (5, 1, 16, 0.5, "lattice")])
+                                                          (5, 1, 16, 0.5, "lattice"), (4, 1, 16, 0.5, "cube")])
 def test_binary_tree_vs_oracle(F, p, basis, max_leaf, theta, dist):
     """The binary median-split tree (App. C) built on the device: the same
     node, leaf and list counts as the oracle's tree, the fields within 1e-12.
@@ -164,7 +164,10 @@ def test_binary_tree_vs_oracle(F, p, basis, max_leaf, theta, dist):
     else:
         n = 3000
         a = np.floor(inputs.u01(41, 0, 3 * n) * 5).reshape(3, n)   # every coordinate one of 5 values
-        x, y, z = a[0] / 5.0, a[1] / 5.0 * 0.7, a[2] / 5.0 * 1.3
+        if dist == "lattice":
+            x, y, z = a[0] / 5.0, a[1] / 5.0 * 0.7, a[2] / 5.0 * 1.3
+        else:   # equal extents: the rule for tied sides decides the axis
+            x, y, z = a[0] / 5.0, a[1] / 5.0, a[2] / 5.0
     q = inputs.masses_open_unit(n, 41)
     plan = F.Plan(p=p, basis=basis, prec=F.FP64, adaptive=True, max_leaf=max_leaf, theta=theta, binary_tree=True)
     pot, acc = plan.evaluate(g(x), g(y), g(z), g(q))

@@ -18,7 +18,16 @@ def lattice(n, seed):
     return a[0] / 5.0, a[1] / 5.0 * 0.7, a[2] / 5.0 * 1.3
 
 
-@pytest.mark.parametrize("gen,n,ml", [(inputs.plummer, 5000, 32), (inputs.blobs, 4096, 16), (lattice, 3000, 16)])
+def lattice_cube(n, seed):
+    """Every coordinate from the same 5 values: the root's (and many cells')
+    bounding-box sides tie, so the rule for equal sides (the first of x, y,
+    z) decides the split axis."""
+    a = np.floor(inputs.u01(seed, 0, 3 * n) * 5).reshape(3, n)
+    return a[0] / 5.0, a[1] / 5.0, a[2] / 5.0
+
+
+@pytest.mark.parametrize("gen,n,ml", [(inputs.plummer, 5000, 32), (inputs.blobs, 4096, 16), (lattice, 3000, 16),
+                                      (lattice_cube, 3000, 16)])
 def test_structure_median_splits_and_shrink_wrap(gen, n, ml):
     x, y, z = gen(n, 41)
     P = np.stack([x, y, z], 1)
