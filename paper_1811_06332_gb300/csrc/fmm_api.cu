@@ -49,6 +49,8 @@ struct fmm_plan {
     double* Dtab = nullptr;  // 343 x ns     (M2L, integer offsets in cell units)
     float* K32 = nullptr;    // 343 x kstride packed FP32 M2L matrices (FMM_FP32)
     double* K64 = nullptr;   // 343 x kstride packed FP64 M2L matrices (FMM_FP64)
+    double* part64 = nullptr;   // partial sums of the split FP64 grouped M2L on small levels
+    int64_t part64_cap = 0;
     float* M32 = nullptr;    // FP32 copy of the multipoles (FMM_FP32)
     int kst = 0;
     // tensor-core forms (FMM_GEMM_BF16X3, FMM_GEMM_TF32X3)
@@ -679,6 +681,13 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
              cudaMemcpy(dent, ent.data(), ent.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
              (f64 ? cudaMalloc(&pl->K64, (size_t)343 * pl->kst * sizeof(double))
                   : cudaMalloc(&pl->K32, (size_t)343 * pl->kst * sizeof(float))) == cudaSuccess;
+        if (ok && f64) {
+            for (int l = 2; l <= cfg->depth; ++l) {
+                const int64_t e = m2l_grp64_part_elems(cfg->p, cfg->basis, l);
+                if (e > pl->part64_cap) pl->part64_cap = e;
+            }
+            ok = pl->part64_cap == 0 || cudaMalloc(&pl->part64, (size_t)pl->part64_cap * sizeof(double)) == cudaSuccess;
+        }
         if (ok) {
             if (f64)
                 launch_build_ktab64(cfg->p, cfg->basis, pl->kst, dent, pl->Dtab, pl->K64, 0);
@@ -701,6 +710,7 @@ void fmm_destroy(fmm_plan* pl) {
     ad_free(pl->ad);
     free_tree(pl);
     cudaFree(pl->W); cudaFree(pl->V); cudaFree(pl->Dtab); cudaFree(pl->stage); cudaFree(pl->K32); cudaFree(pl->K64);
+    cudaFree(pl->part64);
     if (pl->ugexec) cudaGraphExecDestroy(pl->ugexec);
     cudaFree(pl->Kbf); cudaFree(pl->Kgen); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
     delete pl;
@@ -885,7 +895,7 @@ static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
     }
     for (int l = lo; l <= hi; ++l) {
         const int parts = launch_m2l_grp64(pl->cfg.p, pl->cfg.basis, l, Mlev(pl, l), Llev(pl, l), pl->K64,
-                                           (int64_t)1 << (3 * l), S(stream));
+                                           (int64_t)1 << (3 * l), S(stream), pl->part64, pl->part64_cap);
         for (int k = 0; k < parts; ++k) count_launch();
     }
     CKLAUNCH();

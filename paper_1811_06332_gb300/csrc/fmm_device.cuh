@@ -7,6 +7,9 @@
 
 namespace fmm {
 
+// Lt[i] = sum over g < groups of part[g m + i], in group order (fmm_m2l32.cu)
+int launch_sum_parts(const double* part, double* Lt, int64_t m, int groups, cudaStream_t s);
+
 // 1/sqrt(v): CUDA's double-precision rsqrt (at most 1 ulp from the exact
 // value; one call in place of a rounded square root and a rounded division,
 // which on this part's FP64 units costs several times the rest of a pair)

@@ -126,7 +126,8 @@ int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const fl
 int launch_build_ktab64(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, double* K,
                         cudaStream_t s);
 int launch_m2l_grp64(int p, int basis, int l, const double* M, double* Lt, const double* K, int64_t ncell,
-                     cudaStream_t s);
+                     cudaStream_t s, double* part, int64_t part_cap);
+int64_t m2l_grp64_part_elems(int p, int basis, int l);
 int grouped_kstride(int p, int basis);
 
 // fmm_api.cu: translation matrices of the uniform octree in scaled units

@@ -104,4 +104,19 @@ int launch_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
     return 0;
 }
 
+// Partial sums of the split FP64 grouped M2L, added in group order.
+__global__ void k_sum_parts(const double* __restrict__ part, double* __restrict__ Lt, int64_t m, int groups) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double v = 0.0;
+    for (int g = 0; g < groups; ++g) v += part[(int64_t)g * m + i];
+    Lt[i] = v;
+}
+
+int launch_sum_parts(const double* part, double* Lt, int64_t m, int groups, cudaStream_t s) {
+    if (m <= 0) return 0;
+    k_sum_parts<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(part, Lt, m, groups);
+    return 0;
+}
+
 }  // namespace fmm

@@ -183,7 +183,8 @@ extern "C" int fmm_evaluate_noalloc(int p, int basis, int depth, int64_t n, cons
         launch_m2m_level(p, basis, l, W, Mb + lo[l + 1], (int64_t)1 << (3 * (l + 1)), Mb + lo[l],
                          (int64_t)1 << (3 * l), s);
     for (int l = 2; l <= depth; ++l) {
-        const int parts = launch_m2l_grp64(p, basis, l, Mb + lo[l], Lb + lo[l], K64, (int64_t)1 << (3 * l), s);
+        const int parts = launch_m2l_grp64(p, basis, l, Mb + lo[l], Lb + lo[l], K64, (int64_t)1 << (3 * l), s,
+                                           nullptr, 0);   // no room for partial sums: unsplit
         for (int k = 0; k < parts; ++k) count_launch();
     }
     for (int l = 2; l < depth; ++l)

@@ -442,7 +442,7 @@ def emit_grouped_file(p, basis, T="float"):
         ncol = pre[r0]
         L.append("__global__ void __launch_bounds__(128)")
         L.append("m2l_grp%s_p%d_b%d_r%d(int l, const %s* __restrict__ M, double* __restrict__ Lt,"
-                 " const %s* __restrict__ K, int64_t ncell) {" % (sfx, p, basis, k, T, T))
+                 " const %s* __restrict__ K, int64_t ncell, double* __restrict__ part) {" % (sfx, p, basis, k, T, T))
         L.append("  __shared__ __align__(16) %s sK[%d];" % (T, (klen + 3) // 4 * 4))
         L.append("  const int side = 1 << l, hs = side >> 1, bs = (int)blockDim.x;   // 128 or (FP64 small levels) 32")
         L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + bs - 1) / bs;")
@@ -479,22 +479,28 @@ def emit_grouped_file(p, basis, T="float"):
         L.append("  if (gridDim.y == 1) {")
         for r in range(r0, r1):
             L.append("    Lt[(int64_t)%d * ncell + tg] = (double)a%d;" % (r, r - r0))
+        L.append("  } else if (part) {   // partial sums of this offset group, added in group order afterwards")
+        for r in range(r0, r1):
+            L.append("    part[((int64_t)blockIdx.y * %d + %d) * ncell + tg] = (double)a%d;" % (len(rows), r, r - r0))
         L.append("  } else {")
         for r in range(r0, r1):
             L.append("    atomicAdd(Lt + (int64_t)%d * ncell + tg, (double)a%d);" % (r, r - r0))
         L.append("  }")
         L.append("}")
     L.append("// groups > 1 splits the 216 offset slots of every target over that many")
-    L.append("// blocks (small levels); the partial sums are added into a zeroed Lt.")
-    L.append("// bs: threads (targets) per block, 128 or 32.")
+    L.append("// blocks (small levels).  Without part the partial sums are added into a")
+    L.append("// zeroed Lt with atomics; with part (groups x %d x ncell doubles) they are" % len(rows))
+    L.append("// stored there and added in group order (the result does not depend on")
+    L.append("// scheduling).  bs: threads (targets) per block, 128 or 32.")
     L.append("int launch_m2l_grp%s_p%d_b%d(int l, const %s* M, double* Lt, const %s* K, int64_t ncell,"
-             " cudaStream_t s, int groups, int bs) {" % (sfx, p, basis, T, T))
+             " cudaStream_t s, int groups, int bs, double* part) {" % (sfx, p, basis, T, T))
     L.append("  const int hs = (1 << l) >> 1;")
     L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + bs - 1) / bs;")
-    L.append("  if (groups > 1 && cudaMemsetAsync(Lt, 0, (size_t)%d * ncell * sizeof(double), s) != cudaSuccess) return -1;" % len(rows))
+    L.append("  if (groups > 1 && !part && cudaMemsetAsync(Lt, 0, (size_t)%d * ncell * sizeof(double), s) != cudaSuccess) return -1;" % len(rows))
     for k in range(len(parts)):
-        L.append("  m2l_grp%s_p%d_b%d_r%d<<<dim3((unsigned)(8 * bpc), (unsigned)groups), bs, 0, s>>>(l, M, Lt, K, ncell);"
+        L.append("  m2l_grp%s_p%d_b%d_r%d<<<dim3((unsigned)(8 * bpc), (unsigned)groups), bs, 0, s>>>(l, M, Lt, K, ncell, part);"
                  % (sfx, p, basis, k))
+    L.append("  if (groups > 1 && part) { launch_sum_parts(part, Lt, (int64_t)%d * ncell, groups, s); return %d; }" % (len(rows), len(parts) + 1))
     L.append("  return %d;" % len(parts))
     L.append("}")
     L.append("}  // namespace fmm")
@@ -774,11 +780,11 @@ def emit_grouped_dispatch():
     for p in range(PMAX + 1):
         for b in (0, 1):
             L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
-                     " cudaStream_t s, int groups, int bs);" % (p, b))
+                     " cudaStream_t s, int groups, int bs, double* part);" % (p, b))
             L.append("int launch_m2l_grp64_p%d_b%d(int l, const double* M, double* Lt, const double* K,"
-                     " int64_t ncell, cudaStream_t s, int groups, int bs);" % (p, b))
+                     " int64_t ncell, cudaStream_t s, int groups, int bs, double* part);" % (p, b))
         L.append("int launch_m2l_grp64_p%d_b2(int l, const double* M, double* Lt, const double* K,"
-                 " int64_t ncell, cudaStream_t s, int groups, int bs);" % p)
+                 " int64_t ncell, cudaStream_t s, int groups, int bs, double* part);" % p)
     L.append("// Levels with fewer target blocks than about four per SM split the offsets")
     L.append("// of every target over up to 27 blocks.")
     L.append("int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K,"
@@ -791,22 +797,46 @@ def emit_grouped_dispatch():
     L.append("  const int groups = (int)(g < 1 ? 1 : g > 27 ? 27 : g);")
     for p in range(PMAX + 1):
         for b in (0, 1):
-            L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s, groups, 128);"
+            L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s, groups, 128, nullptr);"
                      % (p, b, p, b))
     L.append("  return -1;")
     L.append("}")
-    L.append("// The FP64 form stays deterministic: no offset split (no atomic adds);")
-    L.append("// levels with fewer than two 128-target blocks per SM take blocks of 32.")
-    L.append("int launch_m2l_grp64(int p, int basis, int l, const double* M, double* Lt, const double* K,"
-             " int64_t ncell, cudaStream_t s) {")
+    L.append("// The FP64 form stays deterministic: levels with fewer than two 128-target")
+    L.append("// blocks per SM take blocks of 32, and levels with fewer target blocks than")
+    L.append("// about four per SM split the offsets over up to 27 groups whose partial sums")
+    L.append("// go to part and are added in group order (no atomic adds); without room in")
+    L.append("// part (part_cap doubles) the level runs unsplit.")
+    L.append("static int grp64_split(int l, int* bs_out) {")
     L.append("  static int sms = 0;")
     L.append("  if (!sms) { int d = 0; cudaGetDevice(&d); cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);"
              " if (sms <= 0) sms = 1; }")
-    L.append("  const int64_t hs = (int64_t)1 << (l - 1), blocks = 8 * ((hs * hs * hs + 127) / 128);")
-    L.append("  const int bs = blocks >= 2 * (int64_t)sms ? 128 : 32;")
+    L.append("  const int64_t hs = (int64_t)1 << (l - 1), h3 = hs * hs * hs, blocks128 = 8 * ((h3 + 127) / 128);")
+    L.append("  const int bs = blocks128 >= 2 * (int64_t)sms ? 128 : 32;")
+    L.append("  const int64_t blocks = 8 * ((h3 + bs - 1) / bs);")
+    L.append("  const int64_t g = (4 * (int64_t)sms + blocks - 1) / blocks;")
+    L.append("  *bs_out = bs;")
+    L.append("  return (int)(g < 1 ? 1 : g > 27 ? 27 : g);")
+    L.append("}")
+    L.append("int grouped_nrows(int p, int basis) {")
     for p in range(PMAX + 1):
         for b in (0, 1, 2):
-            L.append("  if (p == %d && basis == %d) return launch_m2l_grp64_p%d_b%d(l, M, Lt, K, ncell, s, 1, bs);"
+            L.append("  if (p == %d && basis == %d) return %d;" % (p, b, len(grouped_layout(p, b)[0])))
+    L.append("  return -1;")
+    L.append("}")
+    L.append("// doubles of part that level l needs for its split (0: the level runs unsplit)")
+    L.append("int64_t m2l_grp64_part_elems(int p, int basis, int l) {")
+    L.append("  int bs = 0;")
+    L.append("  const int g = grp64_split(l, &bs);")
+    L.append("  return g > 1 ? (int64_t)g * grouped_nrows(p, basis) * ((int64_t)1 << (3 * l)) : 0;")
+    L.append("}")
+    L.append("int launch_m2l_grp64(int p, int basis, int l, const double* M, double* Lt, const double* K,"
+             " int64_t ncell, cudaStream_t s, double* part, int64_t part_cap) {")
+    L.append("  int bs = 0;")
+    L.append("  int groups = grp64_split(l, &bs);")
+    L.append("  if (!part || (int64_t)groups * grouped_nrows(p, basis) * ncell > part_cap) groups = 1;")
+    for p in range(PMAX + 1):
+        for b in (0, 1, 2):
+            L.append("  if (p == %d && basis == %d) return launch_m2l_grp64_p%d_b%d(l, M, Lt, K, ncell, s, groups, bs, part);"
                      % (p, b, p, b))
     L.append("  return -1;")
     L.append("}")
