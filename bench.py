@@ -205,16 +205,77 @@ def roofline_per_op(stage, form, nc, depth, n, npart_pairs, pk, mhz, fp_peak, al
 
 
 class Clocks:
-    """Samples nvidia-smi every 200 ms during the timed region."""
+    """SM clock and clock-event reasons of the GPU during the timed region.
+
+    Read through NVML (ctypes on libnvidia-ml, read-only queries) on a thread
+    every 2 ms, so that a timed region of a few tens of milliseconds still
+    gets samples; the thread is running before the region starts.  Without
+    NVML, nvidia-smi every 200 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of the NVML API
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index):
+    def __init__(self, index, device=None):
         self.index = index
+        self.device = device
         self.proc = None
+        self.rows = []
+        self.nvml = None
+
+    def _nvml_open(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(self.device if self.device is not None else 0).uuid)
+            u = u if u.startswith("GPU-") else "GPU-" + u
+            ok = lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+            return None
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) != 0:
+            return None
+        self.max_mhz = float(mx.value)
+        return lib, h, reasons
+
+    def _poll(self):
+        import ctypes
+        lib, h, reasons = self.nvml
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while True:
+            a = lib.nvmlDeviceGetClockInfo(h, ctypes.c_int(1), ctypes.byref(clk))
+            b = reasons(h, ctypes.byref(rs))
+            if a == 0 and b == 0:
+                self.rows.append((float(clk.value), int(rs.value)))
+            if self.stop.wait(0.002):
+                break
 
     def __enter__(self):
+        import threading
+        try:
+            self.nvml = self._nvml_open()
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 1.0:
+                time.sleep(0.001)
+            self.rows.clear()
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -225,6 +286,9 @@ class Clocks:
 
     def __exit__(self, *a):
         self.out = ""
+        if self.nvml is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -234,6 +298,14 @@ class Clocks:
                 self.out, _ = self.proc.communicate()
 
     def summary(self):
+        if self.nvml is not None:
+            if not self.rows:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"], "samples": 0,
+                        "sampler": "nvml, 2 ms"}
+            reasons = sorted({n for _, r in self.rows for bit, n in self.BITS.items() if r & bit})
+            return {"sm_mhz": float(np.median([c for c, _ in self.rows])), "sm_max_mhz": self.max_mhz,
+                    "sm_min_mhz": min(c for c, _ in self.rows), "reasons": reasons, "samples": len(self.rows),
+                    "sampler": "nvml, 2 ms"}
         rows = [r.split(", ") for r in getattr(self, "out", "").strip().splitlines() if r.count(",") >= 8]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
@@ -242,7 +314,7 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "sampler": "nvidia-smi, 200 ms"}
 
 
 # ---------------------------------------------------------------------------
@@ -341,7 +413,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = F.kernel_launches()
-    with Clocks(local) as clk:
+    with Clocks(local, dev) as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
             step(evs[k])
@@ -401,9 +473,11 @@ def run_gpu(args):
         # kernels 0 and 1 execute 3 cw columns per K-step and chunk (3 MMAs of N = cw, or the
         # stacked hi/lo MMA of N = 2 cw and the lo.hi MMA of N = cw) for 128 cells per offset
         ex = tiles * 189 * 3 * 2 * 128 * cols
-        if tuning["kernel"] == 2:
+        if tuning["kernel"] in (2, 3):
             # kernel 2: per tile of 8 x TY cells (N) and offset, two K-parts x 3 K-steps x 3
-            # passes of M = 128 x N x 16; offsets of planes outside the grid are skipped
+            # passes of M = 128 x N x 16; offsets of planes outside the grid are skipped;
+            # kernel 3: the first K-part only (the columns >= 48 on the CUDA cores)
+            nkp = 2 if tuning["kernel"] == 2 else 1
             ex = 0
             for l in range(5, DEPTH + 1):
                 hs = 1 << (l - 1)
@@ -420,7 +494,7 @@ def run_gpu(args):
                                 oz = 2 * dz + sz - cz
                                 offs += sum(1 for dy in (-1, 0, 1) for dx in (-1, 0, 1)
                                             if max(abs(2 * dx + sx - cx), abs(2 * dy + sy - cy), abs(oz)) > 1)
-                        ex += (hs // 8) * (hs // ty) * offs * 18 * 2 * 128 * (8 * ty) * 16
+                        ex += (hs // 8) * (hs // ty) * offs * nkp * 9 * 2 * 128 * (8 * ty) * 16
         tc = {"executed_flop_per_step": ex, "shape": tuning}
     if prec == F.FP64:
         peak = NOMINAL["sm_count"] * NOMINAL["fp64_fma_per_clk_sm"] * 2 * mhz * 1e6 / 1e12
@@ -664,15 +738,20 @@ def run_adaptive(args):
         steps = args.steps if form == "fp32" else 1
         times, tb = [], []
         with torch.cuda.stream(stream):
-            for k in range(args.warmup + steps):
+            def one(k):
                 flush.fill_(float(k))
                 e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
                 e0.record(stream)
                 plan.fmm_evaluate(*X, out[0], out[1], out[2], out[3], stream=stream)   # tree + operators
                 e1.record(stream)
                 stream.synchronize()
-                if k >= args.warmup:
-                    times.append(e0.elapsed_time(e1))
+                return e0.elapsed_time(e1)
+            for k in range(args.warmup):
+                one(k)
+            with Clocks(0, dev) as clk:
+                for k in range(steps):
+                    times.append(one(args.warmup + k))
+            res.setdefault("clocks_" + form, clk.summary())
             # breakdown: the same sequence through the per-operator entry
             # points (no graph), twice, the second pass recorded
             names = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p"]
@@ -713,7 +792,7 @@ def run_adaptive(args):
             "stage_ms": res["fp32"]["stage_ms"],
             "tree": res["fp32"]["stats"],
             "fp64_form": {"value": v64, "ms_per_step": res["fp64"]["ms_per_step"]} if v64 else None,
-            "vs_fp64_form": v32 / v64 if v64 else None}
+            "vs_fp64_form": v32 / v64 if v64 else None, "clocks": res["clocks_fp32"]}
     print(json.dumps(line))
     return 0
 

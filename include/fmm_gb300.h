@@ -408,8 +408,12 @@ int fmm_tc_gen_layout(int p, int cw, int niss, int* out, int nout, uint32_t* gro
  * built in shared memory from the offset's D vector (BF16 operands only);
  * kernel 2: the matrix as the A operand (M = 128 local components) and the
  * target cells of a tile as N (256 cells on levels >= 6, 128 on level 5),
- * BF16 operands only.  cw: chunk width, the local components per MMA (16,
- * 32, 48 or 96) for kernels 0 and 1; 256 for kernel 2.
+ * BF16 operands only; kernel 3: kernel 2 with the multipole columns 0..47
+ * on the tensor cores, then the columns >= 48 (which reach only the local
+ * rows of rank <= p - 6) as FP32 products on the CUDA cores, added to L
+ * (p = 6..8; the same as kernel 2 below p = 6).
+ * cw: chunk width, the local components per MMA (16, 32, 48 or 96) for
+ * kernels 0 and 1; 256 for kernels 2 and 3.
  * fmm_set_tc_shape fixes the shape (rebuilding the plan's offset tables;
  * synchronous); FMM_ERR_ARG for a shape the plan's form has not.
  * fmm_plan_tuning writes to out[0..min(nout, 5 + 4 ncand)): kernel, cw,

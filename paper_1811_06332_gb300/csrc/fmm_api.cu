@@ -57,6 +57,9 @@ struct fmm_plan {
     void* Kbf = nullptr;                 // 343 x {hi, lo} preformatted matrices (streamed-matrix kernel)
     void* Kgen = nullptr;                // BF16: group table + FP32 D vectors (on-chip-matrix kernel)
     int tc_kern = 0, tc_cw = 48, tc_niss = 4;   // kernel shape in use
+    // kernel 3: the multipole columns >= 48 on the CUDA cores
+    float* Mrest = nullptr;              // 8^depth x rest_cstride(p): columns >= 48, cell-major FP32
+    float* Krest = nullptr;              // 343 x rest_kstride(p) matrix entries of those columns
     int tc_source = 0;                   // 0 default, 1 autotuned, 2 from the cache, 3 set by the caller
     cudaGraphExec_t ugexec = nullptr;    // uniform plans with use_graph: the captured step
     const void* ugkey[11] = {nullptr};   // what the captured step depends on
@@ -105,7 +108,7 @@ static void* tc_maps_at(fmm_plan* pl, int l) {
 // ---------------------------------------------------------------------------
 static bool tc_shape_valid(int tf, int kern, int cw) {
     if (kern == 0) return cw == 16 || cw == 32 || cw == 48 || cw == 96;
-    if (kern == 2) return !tf && cw == 256;
+    if (kern == 2 || kern == 3) return !tf && cw == 256;
     return kern == 1 && !tf && (cw == 16 || cw == 32 || cw == 48 || cw == 96);
 }
 
@@ -114,9 +117,17 @@ static int tc_set_shape(fmm_plan* pl, int kern, int cw, cudaStream_t s) {
     if (kern == 0) {
         if (tc_build_mat(pl->cfg.p, tf, cw, pl->Dtab, pl->Kbf, s) != 0) return -2;
         pl->tc_niss = tc_mat_niss(pl->cfg.p, tf, cw);
-    } else if (kern == 2) {
+    } else if (kern == 2 || kern == 3) {
         if (tct_bytes() > tc_mat_bytes(tf) || tct_build(pl->cfg.p, pl->Dtab, pl->Kbf, s) != 0) return -2;
         pl->tc_niss = 2;
+        if (kern == 3 && rest_rows(pl->cfg.p) > 0 && !pl->Mrest) {
+            const int p = pl->cfg.p;
+            const size_t nmax = (size_t)1 << (3 * pl->depth);
+            if (cudaMalloc(&pl->Mrest, (size_t)rest_cstride(p) * nmax * sizeof(float)) != cudaSuccess ||
+                cudaMalloc(&pl->Krest, (size_t)343 * rest_kstride(p) * sizeof(float)) != cudaSuccess ||
+                build_krest(p, pl->Dtab, pl->Krest, s) != 0)
+                return -2;
+        }
     } else {
         if (tg_build(pl->cfg.p, cw, 1, pl->Dtab, pl->Kgen, s) != 0) return -2;
         pl->tc_niss = 1;
@@ -148,9 +159,17 @@ static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
     const int tf = pl->cfg.prec == FMM_GEMM_TF32X3, es = tc_elem_bytes(tf);
     char* hp = (char*)pl->Mbf + pl->mbf_off[l] * es;
     char* lp = hp + tc_m_elems(l) * es;
-    return tc_m2l_level(pl->cfg.p, tf, pl->tc_kern, pl->tc_cw, pl->tc_niss, l, pl->Mbuf + pl->lvl_off[l], hp, lp,
-                        tc_maps_at(pl, l), pl->tc_kern == 1 ? pl->Kgen : pl->Kbf, pl->Lbuf + pl->lvl_off[l], pl->derr,
-                        s);
+    const int p = pl->cfg.p;
+    const int rc = tc_m2l_level(p, tf, pl->tc_kern, pl->tc_cw, pl->tc_niss, l, pl->Mbuf + pl->lvl_off[l], hp, lp,
+                                tc_maps_at(pl, l), pl->tc_kern == 1 ? pl->Kgen : pl->Kbf, pl->Lbuf + pl->lvl_off[l],
+                                pl->derr, s);
+    // kernel 3: the multipole columns >= 48 (a cell-major FP32 copy of
+    // them, then their products) on the CUDA cores, added to L
+    if (rc == 0 && pl->tc_kern == 3 && rest_rows(p) > 0 &&
+        (launch_rest_pack(p, l, pl->Mbuf + pl->lvl_off[l], pl->Mrest, s) != 0 ||
+         launch_m2l_rest(p, l, pl->Mrest, pl->Krest, pl->Lbuf + pl->lvl_off[l], s) != 0))
+        return -2;
+    return rc;
 }
 
 // Times every candidate shape on level `l` (one warm-up and one timed
@@ -158,10 +177,10 @@ static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
 // and keeps the fastest.
 static int tc_autotune(fmm_plan* pl, int l, cudaStream_t s) {
     const int tf = pl->cfg.prec == FMM_GEMM_TF32X3;
-    static const int cand_bf16[][2] = {{0, 32}, {0, 48}, {0, 96}, {1, 48}, {1, 96}, {2, 256}};
+    static const int cand_bf16[][2] = {{0, 32}, {0, 48}, {0, 96}, {1, 48}, {1, 96}, {2, 256}, {3, 256}};
     static const int cand_tf32[][2] = {{0, 16}, {0, 32}, {0, 48}};
     const int (*cand)[2] = tf ? cand_tf32 : cand_bf16;
-    const int nc = tf ? 3 : 6;
+    const int nc = tf ? 3 : 7;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -2;
     int best = -1;
@@ -713,6 +732,7 @@ void fmm_destroy(fmm_plan* pl) {
     cudaFree(pl->part64);
     if (pl->ugexec) cudaGraphExecDestroy(pl->ugexec);
     cudaFree(pl->Kbf); cudaFree(pl->Kgen); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
+    cudaFree(pl->Mrest); cudaFree(pl->Krest);
     delete pl;
 }
 

@@ -163,7 +163,17 @@ size_t tct_bytes();
 int tct_ty(int l);
 void tct_box(int l, unsigned (&box)[5]);
 int tct_build(int p, const double* Dtab, void* B, cudaStream_t s);
-int tct_m2l_level(int p, int l, const void* maps, const void* B, double* Lt, int* err, cudaStream_t s);
+int tct_m2l_level(int p, int l, int first_part_only, const void* maps, const void* B, double* Lt, int* err,
+                  cudaStream_t s);
+// tables of the multipole columns >= 48 that kernel shape 3 contracts on the
+// CUDA cores (fmm_m2l_rest.cu): rows of rank <= p - 6
+int rest_rows(int p);
+int rest_kstride(int p);   // floats per offset of the matrix table
+int rest_cstride(int p);   // floats per cell of the multipole copy
+int build_krest(int p, const double* Dtab, float* Krest, cudaStream_t s);
+int launch_rest_pack(int p, int l, const double* M, float* Mrest, cudaStream_t s);
+// Lt (level l, after the tensor-core kernel) += those products
+int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s);
 size_t tc_maps_bytes();
 // kern 0: per-offset matrices streamed from global memory (tc_build_mat at
 // chunk width cw; niss follows from the layout); kern 1 (BF16 only): the

@@ -594,8 +594,9 @@ int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double*
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const int nc = ncoef_of(p, 1);
     if (ncell > ((int64_t)1 << 30)) return -1;   // 32-bit cell indices in k_tc_split_m
-    const dim3 g((unsigned)((ncell + 255) / 256), (unsigned)(TC_K * tc_elem_bytes(tf) / 16));
-    if ((kern == 1 || kern == 2) && tf) return -1;   // the on-chip and swapped kernels take BF16 operands
+    // kernel 3 reads the first K-part (16-byte chunks 0..5) only
+    const dim3 g((unsigned)((ncell + 255) / 256), (unsigned)(kern == 3 ? 6 : TC_K * tc_elem_bytes(tf) / 16));
+    if ((kern >= 1) && tf) return -1;   // the on-chip and swapped kernels take BF16 operands
     // the on-chip kernel's matrices hold D_{n+m} alone: its operand carries 1/m!
     if (tf)
         k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, 0, M, hi, lo);
@@ -607,7 +608,7 @@ int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double*
         if (rc != 0) return rc;
         return cudaGetLastError() == cudaSuccess ? 0 : -2;
     }
-    if (kern == 2) return tct_m2l_level(p, l, maps, B, Lt, err, s);
+    if (kern == 2 || kern == 3) return tct_m2l_level(p, l, kern == 3, maps, B, Lt, err, s);
     const TcChunks ch = tc_chunks(p, tf, cw);
     if (ch.niss != 2 && ch.niss != 4) return -1;
     const int rc = tf ? (ch.niss == 4 ? tc_launch<1, 4>(ch, l, nc, maps, B, Lt, ncell, err, s)

@@ -28,6 +28,11 @@
 // lo.hi), FP32 accumulation in TMEM, the two issuers' accumulators added in
 // FP64 at write-out.
 //
+// Kernel shape 3 runs the first K-part only: the columns >= 48 reach only
+// the local rows of rank <= p - 6 (9 of the 128 rows at p = 8), so the second
+// K-part's tiles would be mostly padding; those products (86 per pair at
+// p = 8) run afterwards as FP32 FMAs on the CUDA cores (fmm_m2l_rest.cu).
+//
 // Roles: warp 0 lane 0 issues the slab loads and warp 7 lane 0 the matrix
 // copies (separately, so that the next slab is requested as soon as its
 // buffer is free); lane 0 of warps 1 and 6 issue tcgen05.mma, each into its
@@ -66,8 +71,8 @@ constexpr int TT_THREADS = 256;
 
 template <int TY>
 __global__ void __launch_bounds__(TT_THREADS, 1)
-k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const unsigned char* __restrict__ Kmat,
-           double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
+k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int npt, int nrows,
+           const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
     constexpr int N = 8 * TY;
     constexpr int SLB = tt_slab_bytes(TY);
     extern __shared__ unsigned char smem_raw[];
@@ -121,7 +126,7 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
             for (int dz = -1; dz <= 1 && ok; ++dz) {
                 if (tk + dz < 0 || tk + dz >= hs) continue;   // plane outside the grid: no sources
                 const int oz = 2 * dz + sz - cz;
-                for (int pt = 0; pt < np && ok; ++pt) {
+                for (int pt = 0; pt < npt && ok; ++pt) {
                     const int buf = sl & 1;
                     ++sl;
                     if (slabs) {
@@ -188,7 +193,7 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int nrows, const 
             for (int dz = -1; dz <= 1 && ok; ++dz) {
                 if (tk + dz < 0 || tk + dz >= hs) continue;
                 const int oz = 2 * dz + sz - cz;
-                for (int pt = 0; pt < np && ok; ++pt) {
+                for (int pt = 0; pt < npt && ok; ++pt) {
                     const int buf = sl & 1;
                     if (!(ok = mbar_wait(smem_u32(&sfull[buf]), (uint32_t)(sl >> 1) & 1u, err, 24))) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -332,22 +337,25 @@ void tct_box(int l, unsigned (&box)[5]) {
 }
 
 template <int TY>
-static int tct_launch(int l, int np, int nc, const TcMaps& maps, const void* B, double* Lt, int64_t ncell, int* err,
-                      cudaStream_t s) {
+static int tct_launch(int l, int np, int npt, int nc, const TcMaps& maps, const void* B, double* Lt, int64_t ncell,
+                      int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
     const int smem = tt_smem(TY);
     if (cudaFuncSetAttribute(k_m2l_tc_t<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -2;
     const int tpc = (hs / 8) * (hs / TY) * hs;
-    k_m2l_tc_t<TY><<<(unsigned)(8 * tpc), TT_THREADS, smem, s>>>(maps, l, np, nc, (const unsigned char*)B, Lt, ncell,
-                                                                 err);
+    k_m2l_tc_t<TY><<<(unsigned)(8 * tpc), TT_THREADS, smem, s>>>(maps, l, np, npt, nc, (const unsigned char*)B, Lt,
+                                                                 ncell, err);
     count_launch();
     return 0;
 }
 
 // M2L of tensor-core level l (>= 5) with this kernel; the hi/lo operand
-// tiles of the level must be in place (k_tc_split_m).
-int tct_m2l_level(int p, int l, const void* maps, const void* B, double* Lt, int* err, cudaStream_t s) {
+// tiles of the level must be in place (k_tc_split_m).  first_part_only:
+// only the multipole columns 0..47 (the first K-part) on the tensor cores;
+// the columns >= 48 are left to k_m2l_rest (kernel shape 3).
+int tct_m2l_level(int p, int l, int first_part_only, const void* maps, const void* B, double* Lt, int* err,
+                  cudaStream_t s) {
     const int hs = 1 << (l - 1);
     const int ty = tct_ty(l);
     if (hs < 16 || hs % ty != 0) return -1;
@@ -356,8 +364,9 @@ int tct_m2l_level(int p, int l, const void* maps, const void* B, double* Lt, int
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const TcMaps& m = ((const TcLevelMaps*)maps)->tall;
     const int nc = ncoef_of(p, 1);
-    const int rc = ty == 32 ? tct_launch<32>(l, np, nc, m, B, Lt, ncell, err, s)
-                            : tct_launch<16>(l, np, nc, m, B, Lt, ncell, err, s);
+    const int npt = first_part_only ? 1 : np;
+    const int rc = ty == 32 ? tct_launch<32>(l, np, npt, nc, m, B, Lt, ncell, err, s)
+                            : tct_launch<16>(l, np, npt, nc, m, B, Lt, ncell, err, s);
     if (rc != 0) return rc;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

@@ -224,6 +224,38 @@ def test_swapped_tensor_core_kernel_vs_oracle(F, depth, n, p):
     assert ep < 5e-6 and ea < 5e-6, (ep, ea, per)
 
 
+@pytest.mark.parametrize("depth,n,p", [(6, 262144, 8), (7, 1048576, 8), (6, 262144, 7), (6, 262144, 6),
+                                       (5, 131072, 5)])
+def test_split_tensor_core_kernel_vs_oracle(F, depth, n, p):
+    """Kernel shape 3: the swapped kernel on the first K-part (multipole
+    columns 0..47) while the columns >= 48, which reach only the local rows
+    of rank <= p - 6, run as FP32 products on the CUDA cores on a second
+    stream and are added to L after both (p = 6..8; at p = 5 there are no
+    such columns and it is kernel 2).  Against the FP64 oracle on sampled
+    particles, bound 5e-6 as for the other shapes; and equal to kernel 2
+    within 1e-5 of the largest value (the two differ only in the rounding
+    of those few products)."""
+    x, y, z = inputs.uniform_cube(n, 41 + depth + p)
+    q = inputs.masses_equal(n)
+    X = [g(a) for a in (x, y, z, q)]
+    plan = F.Plan(p=p, basis=1, prec=F.GEMM_BF16X3, depth=depth)
+    plan.set_tc_shape(3, 256)
+    pot, acc = plan.evaluate(*X)
+    plan.sync_status()
+    assert plan.tuning()["kernel"] == 3
+    plan.set_tc_shape(2, 256)
+    pot2, acc2 = plan.evaluate(*X)
+    plan.sync_status()
+    plan.close()
+    for a, b in ((pot, pot2), (acc, acc2)):
+        assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max())
+    pot, acc = pot.cpu().numpy(), acc.cpu().numpy()
+    s = np.sort(np.unique((inputs.u01(7, 97, 150) * n).astype(np.int64)))
+    pref, aref = oracle.fmm_uniform(x, y, z, q, depth, p, 1, sample=s)
+    ep, ea, per = errs(pot[s], acc[:, s], pref, aref)
+    assert ep < 5e-6 and ea < 5e-6, (ep, ea, per)
+
+
 @pytest.mark.parametrize("depth,n", [(5, 131072), (6, 262144)])
 def test_tensor_core_tf32_form_vs_oracle(F, depth, n):
     """The same offset-grouped tensor-core M2L with TF32 hi/lo operands
@@ -298,7 +330,8 @@ def test_tensor_core_form_rejects_unsupported(F):
             F.Plan(p=6, basis=0, prec=prec, depth=4)
 
 
-@pytest.mark.parametrize("form,shapes", [("GEMM_BF16X3", [(0, 32), (0, 48), (0, 96), (1, 48), (1, 96), (2, 256)]),
+@pytest.mark.parametrize("form,shapes", [("GEMM_BF16X3", [(0, 32), (0, 48), (0, 96), (1, 48), (1, 96), (2, 256),
+                                                          (3, 256)]),
                                          ("GEMM_TF32X3", [(0, 16), (0, 32), (0, 48)])])
 def test_every_tensor_core_shape_vs_oracle(F, form, shapes):
     """Every kernel shape the autotuner may pick (the streamed-matrix kernel
@@ -341,7 +374,7 @@ def test_autotuned_plan_and_its_cache(F, tmp_path, monkeypatch):
     plan.sync_status()
     t = plan.tuning()
     plan.close()
-    assert t["source"] == "autotuned" and len(t["candidates"]) == 6
+    assert t["source"] == "autotuned" and len(t["candidates"]) == 7
     best = min(t["candidates"], key=lambda c: c["us"])
     assert (t["kernel"], t["cw"]) == (best["kernel"], best["cw"])
     ep, ea, _ = errs(pot.cpu().numpy()[s], acc.cpu().numpy()[:, s], pref, aref)
@@ -408,9 +441,9 @@ def test_tg_basis_vs_oracle(F, p, depth):
             F.Plan(p=p, basis=F.BASIS_TG, prec=prec, depth=depth)
 
 
-@pytest.mark.parametrize("prec,p,depth,n", [("GEMM_BF16X3", 8, 5, 150000), ("FP32", 6, 4, 40000),
-                                            ("FP64", 4, 3, 6000)])
-def test_uniform_graph_replay(F, prec, p, depth, n):
+@pytest.mark.parametrize("prec,p,depth,n,kern", [("GEMM_BF16X3", 8, 5, 150000, 2), ("GEMM_BF16X3", 8, 5, 150000, 3),
+                                                 ("FP32", 6, 4, 40000, None), ("FP64", 4, 3, 6000, None)])
+def test_uniform_graph_replay(F, prec, p, depth, n, kern):
     """use_graph on a uniform plan: the first evaluation runs eagerly, the
     second captures the whole step (tree and operators) and later ones
     replay it; with new particle positions in the same arrays the replayed
@@ -424,9 +457,9 @@ def test_uniform_graph_replay(F, prec, p, depth, n):
     stream = torch.cuda.Stream()
     gp = F.Plan(p=p, basis=1, prec=getattr(F, prec), depth=depth, use_graph=True)
     ep = F.Plan(p=p, basis=1, prec=getattr(F, prec), depth=depth)
-    if prec == "GEMM_BF16X3":
-        gp.set_tc_shape(2, 256)
-        ep.set_tc_shape(2, 256)
+    if kern is not None:   # kernel 3 forks the CUDA-core columns onto a second stream inside the graph
+        gp.set_tc_shape(kern, 256)
+        ep.set_tc_shape(kern, 256)
     out = torch.empty((4, n), device=DEV, dtype=torch.float64)
     with torch.cuda.stream(stream):
         for k in range(3):
