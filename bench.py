@@ -53,6 +53,10 @@ M2L_TRAFFIC = {
     # k_m2l_tc_t<32> (kernel 2): 722.5 MB read + 154.8 MB written at level 6, x 9/8 for levels 5-6
     ("bf16x3", 2, 256): (9.870e8, "ncu capture of the level-6 launch scaled by cells to levels 5-6 "
                                   "(profiles/m2l_tensorcore_swapped_bf16x3_level6_uniform4M_p8.md)"),
+    # kernel 3: k_m2l_tc_t<32> first K-part 160.9 MB read + 137.5 MB written, k_m2l_rest<8> 56.8 + 1.5 MB,
+    # at level 6, x 9/8 for levels 5-6 (the operand split and the FP32 copy of the columns >= 48 not included)
+    ("bf16x3", 3, 256): (4.0125e8, "ncu capture of the level-6 tensor-core and CUDA-core launches scaled by cells "
+                                   "to levels 5-6 (profiles/m2l_tensorcore_split_bf16x3_level6_uniform_p8.md)"),
     # m2l_grp_p8_b1_r0: 653.9 MB read + 154.4 MB written at level 6, x 299584/262144 for levels 2-6
     ("fp32", None, None): (9.237e8, "ncu capture of the level-6 launch scaled by cells to levels 2-6 "
                                     "(profiles/m2l_grouped_fp32_level6_uniform4M_p8.md)"),
@@ -384,7 +388,10 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     tc_form = prec in (F.GEMM_BF16X3, F.GEMM_TF32X3)
-    plan = F.Plan(p=P, basis=BASIS, prec=prec, depth=DEPTH, autotune=tc_form)
+    # use_graph: fmm_evaluate (the host entry point below) replays the whole
+    # step from a CUDA graph; the per-operator calls of the timed region run
+    # eagerly, so that each stage is timed on its own
+    plan = F.Plan(p=P, basis=BASIS, prec=prec, depth=DEPTH, autotune=tc_form, use_graph=True)
 
     # M2L runs as two calls, levels 2..4 and 5..6 (the tensor-core levels of
     # the tensor-core forms), so that the dominant kernel is timed on its own;
@@ -585,21 +592,47 @@ def run_gpu(args):
     else:
         fp64 = None   # --no-fp64: not measured
 
+    # the same step as one fmm_evaluate replayed from a CUDA graph (device
+    # arrays, L2 flushed before each step): the per-operator sequence above
+    # without its ~145 separate launches and the stage events
+    gr = None
+    gs = torch.cuda.Stream()   # a capturable (non-default) stream
+    torch.cuda.synchronize()
+    with torch.cuda.stream(gs):
+        for _ in range(2):   # capture, then a first replay
+            plan.fmm_evaluate(*X, out[0], out[1], out[2], out[3], stream=gs)
+        gts = []
+        for k in range(args.steps):
+            flush.fill_(3.0 + k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(gs)
+            plan.fmm_evaluate(*X, out[0], out[1], out[2], out[3], stream=gs)
+            e1.record(gs)
+            torch.cuda.synchronize()
+            gts.append(e0.elapsed_time(e1))
+    plan.sync_status()
+    gms = max_over_ranks(float(np.mean(gts)), world, dist, dev)
+    gr = {"value": job_rate(N_PART, world, gms * 1e-3), "ms_per_step": gms, "graph": plan.stats().get("graph"),
+          "api": "fmm_evaluate (use_graph plan)"}
+
     # end to end through the host entry point (pinned host buffers)
     e2e = None
     if not args.no_e2e:
         hx = [torch.from_numpy(a).pin_memory() for a in (x, y, z, q)]
         ho = torch.empty((4, N_PART), dtype=torch.float64).pin_memory()
-        plan.fmm_evaluate_host(*hx, ho[0], ho[1], ho[2], ho[3])
+        es = torch.cuda.Stream()
+        for _ in range(2):   # the first call captures the step, the second replays it
+            plan.fmm_evaluate_host(*hx, ho[0], ho[1], ho[2], ho[3], stream=es)
         tms = []
         for _ in range(max(1, min(args.steps, 5))):
             t0 = time.perf_counter()
-            plan.fmm_evaluate_host(*hx, ho[0], ho[1], ho[2], ho[3])
+            plan.fmm_evaluate_host(*hx, ho[0], ho[1], ho[2], ho[3], stream=es)
             tms.append(time.perf_counter() - t0)
         e2e = {"value": job_rate(N_PART, world, max_over_ranks(float(np.mean(tms)), world, dist, dev)),
                "unit": "particles/s",
                "h2d_bytes_per_step": 4 * 8 * N_PART, "d2h_bytes_per_step": 4 * 8 * N_PART,
-               "host_api": "fmm_evaluate_host"}
+               "host_api": "fmm_evaluate_host (pinned host arrays; the step replayed from a CUDA graph)",
+               "graph": plan.stats().get("graph")}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -627,6 +660,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
+        "graph_replay": gr,
         "clocks": clk.summary(),
         "peaks_source": pk_kind,
     }
@@ -892,6 +926,47 @@ def stage_breakdown(F, plan, X, out, flush):
     return tb
 
 
+def run_tclevel(args):
+    """One tensor-core M2L level alone, per kernel shape: a 262,144-particle
+    uniform cube (the M2L work of a level does not depend on the particle
+    count), traceless p = 8, BF16x3, an octree of --depth levels; each shape
+    times fmm_m2l_levels(l, l) on the deepest level (median of --steps after
+    --warmup calls).  For kernel-level profiling on a small device footprint."""
+    import torch
+
+    from paper_1811_06332_gb300 import fmm as F
+    from paper_1811_06332_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    n, depth = 262144, args.depth
+    x, y, z = inputs.uniform_cube(n, SEED)
+    q = inputs.masses_equal(n)
+    X = [torch.from_numpy(a).to(dev) for a in (x, y, z, q)]
+    plan = F.Plan(p=P, basis=BASIS, prec=F.GEMM_BF16X3, depth=depth)
+    plan.fmm_build_tree(*X)
+    plan.fmm_p2m()
+    plan.fmm_m2m()
+    res = {}
+    for shape in args.tc_shapes.split(","):
+        kern, cw = (int(v) for v in shape.split(":"))
+        plan.set_tc_shape(kern, cw)
+        ts = []
+        for k in range(args.warmup + args.steps):
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record()
+            plan.fmm_m2l_levels(depth, depth)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        res["%d:%d" % (kern, cw)] = float(np.median(ts))
+    plan.sync_status()
+    plan.close()
+    print(json.dumps({"workload": "tensor-core M2L, level %d of a depth-%d uniform octree, traceless p=%d, bf16x3"
+                      % (depth, depth, P), "ms_per_level_by_shape": res, "steps": args.steps,
+                      "warmup": args.warmup}))
+    return 0
+
+
 def run_variant(args):
     """Sec. 3 and App. C variants on the batching-form workload (8,388,608
     Plummer particles, MAC theta 0.6, traceless p = 6, FP64): --workload ap:
@@ -1083,7 +1158,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="bf16x3", choices=["fp64", "fp32", "bf16x3", "tf32x3"])
-    ap.add_argument("--workload", default="fmm", choices=["fmm", "small", "m2l", "adaptive", "learned", "ap", "binary"])
+    ap.add_argument("--workload", default="fmm",
+                    choices=["fmm", "small", "m2l", "adaptive", "learned", "ap", "binary", "tclevel"])
+    ap.add_argument("--tc-shapes", default="0:48,2:256,3:256", help="tclevel: kernel:cw list")
+    ap.add_argument("--depth", type=int, default=6, help="tclevel: octree depth (the level timed)")
     ap.add_argument("--orders", default="2,3,4,5,6,7,8,9,10")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -1106,6 +1184,8 @@ def main():
         return run_learned(args)
     if args.workload in ("ap", "binary"):
         return run_variant(args)
+    if args.workload == "tclevel":
+        return run_tclevel(args)
     return run_gpu(args)
 
 
