@@ -52,6 +52,7 @@ struct fmm_plan {
     double* part64 = nullptr;   // partial sums of the split FP64 grouped M2L on small levels
     int64_t part64_cap = 0;
     float* M32 = nullptr;    // FP32 copy of the multipoles (FMM_FP32)
+    float* msym32 = nullptr; // FP32 traceless forms: the leaves' symmetric moments, leaf-major (P2M)
     int kst = 0;
     // tensor-core forms (FMM_GEMM_BF16X3, FMM_GEMM_TF32X3)
     void* Kbf = nullptr;                 // 343 x {hi, lo} preformatted matrices (streamed-matrix kernel)
@@ -473,7 +474,8 @@ static void free_tree(fmm_plan* pl) {
     cudaFree(pl->xs); cudaFree(pl->ys); cudaFree(pl->zs); cudaFree(pl->qs);
     cudaFree(pl->perm); cudaFree(pl->start); cudaFree(pl->scratch);
     cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32); cudaFree(pl->Mbf); cudaFree(pl->pos32);
-    cudaFree(pl->dip);
+    cudaFree(pl->dip); cudaFree(pl->msym32);
+    pl->msym32 = nullptr;
     pl->dip = nullptr;
     pl->pos32 = nullptr;
     pl->M32 = nullptr;
@@ -771,7 +773,9 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             cudaMalloc(&pl->scratch, pl->scratch_bytes) != cudaSuccess ||
             cudaMalloc(&pl->Mbuf, tot * 8) != cudaSuccess || cudaMalloc(&pl->Lbuf, tot * 8) != cudaSuccess ||
             (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess) ||
-            (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->pos32, nn * 16) != cudaSuccess)) {
+            (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->pos32, nn * 16) != cudaSuccess) ||
+            (pl->cfg.prec != FMM_FP64 && bM(pl) == FMM_BASIS_TRACELESS &&
+             cudaMalloc(&pl->msym32, (size_t)pl->nleaf * ((ns_of(pl->cfg.p) + 3) / 4 * 4) * 4) != cudaSuccess)) {
             cudaGetLastError();
             free_tree(pl);
             FAIL(FMM_ERR_OOM, "allocating tree storage for n=%lld failed", (long long)n);
@@ -820,7 +824,7 @@ int fmm_p2m(fmm_plan* pl, void* stream) {
     if (pl->ad) { ad_run_p2m(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     const int d = pl->depth;
     launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, bM(pl), d, pl->nleaf, pl->start, pl->xs,
-                    pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32);
+                    pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32, pl->msym32);
     CKLAUNCH();
     return FMM_OK;
 }

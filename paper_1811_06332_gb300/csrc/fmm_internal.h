@@ -106,7 +106,7 @@ int launch_fill(int64_t n, double* a, double v, cudaStream_t s);
 // fmm_leafops.cu (prec 0: double arithmetic, 1: float arithmetic)
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                     const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
-                    cudaStream_t s, const float4* pos32 = nullptr);
+                    cudaStream_t s, const float4* pos32 = nullptr, float* msym = nullptr);
 int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                      const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
                      double* pot, double* ax, double* ay, double* az, cudaStream_t s,

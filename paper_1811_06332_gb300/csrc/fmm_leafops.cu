@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
            const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
            double* __restrict__ M, const T* __restrict__ reduce, DevOffsets off,
-           const float4* __restrict__ pos32) {
+           const float4* __restrict__ pos32, float* __restrict__ msym) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
     // powers per axis; FP32 rows padded to 16 bytes for vector loads (FP64 rows
@@ -157,6 +157,14 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
     __syncwarp();
     if (!basis) {
         for (int s = lane; s < NS; s += 32) M[(int64_t)s * nleaf + c] = (double)sA[w][s];
+        return;
+    }
+    if (msym) {
+        // the symmetric moments, leaf-major (NS padded to 4 per leaf), for
+        // k_p2m_reduce: one thread per leaf there instead of this warp's
+        // rank-imbalanced rows
+        constexpr int NSP = (NS + 3) / 4 * 4;
+        for (int s = lane; s < NSP; s += 32) msym[c * NSP + s] = s < NS ? float(sA[w][s]) : 0.f;
         return;
     }
     // reduced representative, in the arithmetic type (FP32 tables for the FP32 form)
@@ -390,14 +398,72 @@ const double* tab_of<double>(const double* d, const float*) { return d; }
 template <>
 const float* tab_of<float>(const double*, const float* f) { return f; }
 
+// rank J of k_p2m_reduce (RO: offset of its rows in the map, S0: of its
+// moments), then the next rank; every bound is a compile-time constant
+template <int P, int J, int RO, int S0>
+__device__ __forceinline__ void p2m_reduce_rank(const float* sR, const float* a, double* M, int64_t nleaf,
+                                                int64_t c) {
+    if constexpr (J <= P) {
+        constexpr int cols = (J + 1) * (J + 2) / 2;
+        float m[cols];
+#pragma unroll
+        for (int k = 0; k < cols; ++k) m[k] = a[S0 + k];
+#pragma unroll 1
+        for (int u = 0; u < 2 * J + 1; ++u) {
+            const float* R = sR + RO + u * cols;
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < cols; ++k) v = fmaf(R[k], m[k], v);
+            M[(int64_t)(J * J + u) * nleaf + c] = (double)v;
+        }
+        p2m_reduce_rank<P, J + 1, RO + (2 * J + 1) * cols, S0 + cols>(sR, a, M, nleaf, c);
+    }
+}
+
+// Reduced traceless representative of the leaves' symmetric moments (FP32
+// form), one thread per leaf: row t of rank j is the dot product of the
+// exact map's row with the rank-j moments, summed in the order of the
+// warp-per-leaf form (so the result is the same bit for bit); the map sits in
+// shared memory and every thread of a warp reads the same entry.
+template <int P>
+__global__ void __launch_bounds__(128)
+k_p2m_reduce(int64_t nleaf, const float* __restrict__ msym, const float* __restrict__ reduce, DevOffsets off,
+             double* __restrict__ M) {
+    constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6, NSP = (NS + 3) / 4 * 4;
+    constexpr int RT = [] {
+        int t = 0;
+        for (int j = 0; j <= P; ++j) t += (2 * j + 1) * (j + 1) * (j + 2) / 2;
+        return t;
+    }();
+    __shared__ float sR[RT];
+    {
+        int o = 0;
+        for (int j = 0; j <= P; ++j) {
+            const int sz = (2 * j + 1) * (j + 1) * (j + 2) / 2;
+            for (int i = threadIdx.x; i < sz; i += blockDim.x) sR[o + i] = reduce[off.reduce[j] + i];
+            o += sz;
+        }
+    }
+    __syncthreads();
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nleaf) return;
+    p2m_reduce_rank<P, 0, 0, 0>(sR, msym + c * NSP, M, nleaf, c);
+}
+
 template <int P, typename T>
 static void p2m_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
                        const double* zs, const double* qs, double* M, const DevTables& Tb, cudaStream_t s,
-                       const float4* pos32) {
+                       const float4* pos32, float* msym) {
     constexpr int W = 4;
+    const bool split = sizeof(T) == 4 && basis && msym;
     k_p2m_leaf<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(basis, depth, nleaf, start, xs, ys, zs,
                                                                            qs, M, tab_of<T>(Tb.reduce, Tb.reduce32),
-                                                                           Tb.offsets(), pos32);
+                                                                           Tb.offsets(), pos32,
+                                                                           split ? msym : nullptr);
+    if (split) {
+        k_p2m_reduce<P><<<(unsigned)((nleaf + 127) / 128), 128, 0, s>>>(nleaf, msym, Tb.reduce32, Tb.offsets(), M);
+        count_launch();
+    }
 }
 template <int P, typename T>
 static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
@@ -417,10 +483,10 @@ static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, co
 
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                     const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
-                    cudaStream_t s, const float4* pos32) {
+                    cudaStream_t s, const float4* pos32, float* msym) {
     if (nleaf <= 0) return 0;
-#define C64(P) p2m_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, nullptr)
-#define C32(P) p2m_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, pos32)
+#define C64(P) p2m_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, nullptr, nullptr)
+#define C32(P) p2m_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, pos32, msym)
     if (prec == 0) { FMM_P_SWITCH(p, C64) } else { FMM_P_SWITCH(p, C32) }
 #undef C64
 #undef C32
