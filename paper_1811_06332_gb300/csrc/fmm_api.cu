@@ -74,6 +74,7 @@ struct fmm_plan {
     float4* pos32 = nullptr;
     float* W32 = nullptr;
     float* V32 = nullptr;
+    float* part32 = nullptr;   // per-child FP32 M2M contributions: 8 x nc x 8^(depth-1)
     // point dipoles in sorted order (fmm_evaluate_dipoles)
     double* dip = nullptr;
     // host-call staging
@@ -670,7 +671,9 @@ int fmm_create(const fmm_config* cfg, fmm_plan** out) {
         }
         ok = cudaMalloc(&pl->W32, w32.size() * 4) == cudaSuccess && cudaMalloc(&pl->V32, v32.size() * 4) == cudaSuccess &&
              cudaMemcpy(pl->W32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(pl->V32, v32.data(), v32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+             cudaMemcpy(pl->V32, v32.data(), v32.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             (cfg->adaptive || cfg->depth < 3 ||
+              cudaMalloc(&pl->part32, (size_t)8 * nc * ((size_t)1 << (3 * (cfg->depth - 1))) * 4) == cudaSuccess);
     }
     if (ok && is_tc(cfg->prec)) {
         const int tf = cfg->prec == FMM_GEMM_TF32X3;
@@ -734,6 +737,7 @@ void fmm_destroy(fmm_plan* pl) {
     cudaFree(pl->part64);
     if (pl->ugexec) cudaGraphExecDestroy(pl->ugexec);
     cudaFree(pl->Kbf); cudaFree(pl->Kgen); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
+    cudaFree(pl->part32);
     cudaFree(pl->Mrest); cudaFree(pl->Krest);
     delete pl;
 }
@@ -840,9 +844,10 @@ int fmm_m2m(fmm_plan* pl, void* stream) {
     }
     if (pl->W32) {
         for (int l = pl->depth - 1; l >= 2; --l) {
-            launch_shift32(pl->cfg.p, pl->cfg.basis, 1, l, pl->W32, Mlev(pl, l + 1), (int64_t)1 << (3 * (l + 1)),
-                           Mlev(pl, l), (int64_t)1 << (3 * l), S(stream));
-            count_launch();
+            const int nl = launch_shift32(pl->cfg.p, pl->cfg.basis, 1, l, pl->W32, Mlev(pl, l + 1),
+                                          (int64_t)1 << (3 * (l + 1)), Mlev(pl, l), (int64_t)1 << (3 * l), S(stream),
+                                          pl->part32);
+            for (int k = 0; k < nl; ++k) count_launch();
         }
         CKLAUNCH();
         return FMM_OK;
@@ -938,9 +943,9 @@ int fmm_l2l(fmm_plan* pl, void* stream) {
     if (pl->ad) { ad_run_l2l(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     if (pl->V32) {
         for (int l = 2; l < pl->depth; ++l) {
-            launch_shift32(pl->cfg.p, pl->cfg.basis, 0, l, pl->V32, Llev(pl, l), (int64_t)1 << (3 * l),
-                           Llev(pl, l + 1), (int64_t)1 << (3 * (l + 1)), S(stream));
-            count_launch();
+            const int nl = launch_shift32(pl->cfg.p, pl->cfg.basis, 0, l, pl->V32, Llev(pl, l), (int64_t)1 << (3 * l),
+                                          Llev(pl, l + 1), (int64_t)1 << (3 * (l + 1)), S(stream));
+            for (int k = 0; k < nl; ++k) count_launch();
         }
         CKLAUNCH();
         return FMM_OK;

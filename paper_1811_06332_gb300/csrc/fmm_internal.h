@@ -137,8 +137,10 @@ extern "C" __attribute__((visibility("hidden"))) void build_translation(int p, i
 namespace fmm {
 
 // generated shift_*.cu: FP32 level shifts (m2m = 1: M2M, 0: L2L)
+// part (M2M): 8 x nc x ny floats for the per-child form, or nullptr.
+// Returns the number of kernels launched, -1 without a kernel for (p, basis).
 int launch_shift32(int p, int basis, int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,
-                   int64_t ny, cudaStream_t s);
+                   int64_t ny, cudaStream_t s, float* part = nullptr);
 int shift32_supported(int p, int basis);
 int launch_l2p_p2p32(int p, int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
                      const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,

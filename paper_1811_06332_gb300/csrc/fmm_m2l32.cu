@@ -104,6 +104,26 @@ int launch_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
     return 0;
 }
 
+// M2M of one level from the per-child FP32 contributions (m2m32c):
+// Mpa(r, P) = sum over the child classes c = 0..7, in that order, of
+// part[(c nc + r) npa + P].
+__global__ void k_m2m32_sum(int nc, int64_t npa, const float* __restrict__ part, double* __restrict__ Mpa) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nc * npa) return;
+    const int64_t r = i / npa, P = i - r * npa;
+    float v = part[r * npa + P];
+#pragma unroll
+    for (int c = 1; c < 8; ++c) v += part[((int64_t)c * nc + r) * npa + P];
+    Mpa[i] = (double)v;
+}
+
+int launch_m2m32_sum(int nc, int64_t npa, const float* part, double* Mpa, cudaStream_t s) {
+    const int64_t n = (int64_t)nc * npa;
+    if (n <= 0) return 0;
+    k_m2m32_sum<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nc, npa, part, Mpa);
+    return 0;
+}
+
 // Partial sums of the split FP64 grouped M2L, added in group order.
 __global__ void k_sum_parts(const double* __restrict__ part, double* __restrict__ Lt, int64_t m, int groups) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -570,6 +570,32 @@ def emit_shift_file(p, basis):
         for r in range(nc):
             L.append("  Mpa[(int64_t)%d * npa + P] = (double)a%d;" % (r, r))
         L.append("}")
+        # ---- M2M, one child class per block row: the eight children of a
+        # parent on eight threads (blockIdx.y = child class), their FP32
+        # contributions summed afterwards in child order (m2m32_sum) ----
+        L.append("__global__ void __launch_bounds__(128)")
+        L.append("m2m32c_p%d_b%d(int l, const float* __restrict__ W, const double* __restrict__ Mch, int64_t nch,"
+                 " float* __restrict__ part, int64_t npa) {" % (p, basis))
+        L.append("  __shared__ float sW[%d];" % sz)
+        L.append("  const int c = (int)blockIdx.y;")
+        L.append("  for (int e = threadIdx.x; e < %d; e += 128) sW[e] = W[c * %d + e];" % (sz, sz))
+        L.append("  __syncthreads();")
+        L.append("  const int64_t P = (int64_t)blockIdx.x * 128 + threadIdx.x;")
+        L.append("  if (P >= npa) return;")
+        L.append("  int ix, iy, iz;")
+        L.append("  cell_coords(l, P, ix, iy, iz);")
+        L.append("  const int64_t ch = c * ((int64_t)1 << (3 * l)) + lin_index(l, ix, iy, iz);")
+        for k in range(nc):
+            L.append("  const float x%d = (float)Mch[(int64_t)%d * nch + ch];" % (k, k))
+        for r in range(nc):
+            c0, c1 = rng[r]
+            L.append("  {")
+            L.append("    float a = 0.f;")
+            for k in range(c0, c1):
+                L.append("    a = fmaf(sW[%d], x%d, a);" % (off[r] + k - c0, k))
+            L.append("    part[((int64_t)c * %d + %d) * npa + P] = a;" % (nc, r))
+            L.append("  }")
+        L.append("}")
         # ---- L2L ----
         rows, rng, off, sz = shift_layout(p, basis, True)
         L.append("__global__ void __launch_bounds__(128)")
@@ -587,24 +613,37 @@ def emit_shift_file(p, basis):
         L.append("  const int64_t P = cell_index(l, px, py, pz), C = c * blk + lin;")
         for k in range(nc):
             L.append("  const float x%d = (float)Lpa[(int64_t)%d * npa + P];" % (k, k))
-        for r in range(nc):
-            c0, c1 = rng[r]
-            terms = " + ".join([])
+        # rows in blocks of 16: the block's old values are loaded before its
+        # sums, so that the read-modify-writes of a block are one round trip
+        # rather than one per row
+        for r0 in range(0, nc, 16):
+            r1 = min(nc, r0 + 16)
             L.append("  {")
-            L.append("    float a = 0.f;")
-            for k in range(c0, c1):
-                L.append("    a = fmaf(sV[%d], x%d, a);" % (off[r] + k - c0, k))
-            L.append("    Lch[(int64_t)%d * nch + C] += (double)a;" % r)
+            for r in range(r0, r1):
+                L.append("    const double o%d = Lch[(int64_t)%d * nch + C];" % (r, r))
+            for r in range(r0, r1):
+                c0, c1 = rng[r]
+                L.append("    float a%d = 0.f;" % r)
+                for k in range(c0, c1):
+                    L.append("    a%d = fmaf(sV[%d], x%d, a%d);" % (r, off[r] + k - c0, k, r))
+            for r in range(r0, r1):
+                L.append("    Lch[(int64_t)%d * nch + C] = o%d + (double)a%d;" % (r, r, r))
             L.append("  }")
         L.append("}")
     L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,"
-             " int64_t ny, cudaStream_t s) {" % (p, basis))
+             " int64_t ny, cudaStream_t s, float* part) {" % (p, basis))
     if shift32_ok(p, basis):
+        L.append("  if (m2m && part) {")
+        L.append("    m2m32c_p%d_b%d<<<dim3((unsigned)((ny + 127) / 128), 8), 128, 0, s>>>(l, A, X, nx, part, ny);"
+                 % (p, basis))
+        L.append("    launch_m2m32_sum(%d, ny, part, Y, s);" % nc)
+        L.append("    return 2;")
+        L.append("  }")
         L.append("  if (m2m) m2m32_p%d_b%d<<<(unsigned)((ny + 127) / 128), 128, 0, s>>>(l, A, X, nx, Y, ny);"
                  % (p, basis))
         L.append("  else l2l32_p%d_b%d<<<(unsigned)(8 * ((((int64_t)1 << (3 * l)) + 127) / 128)), 128, 0, s>>>"
                  "(l, A, X, nx, Y, ny);" % (p, basis))
-        L.append("  return 0;")
+        L.append("  return 1;")
     else:
         L.append("  return -1;")
     L.append("}")
@@ -618,12 +657,14 @@ def emit_shift_dispatch():
     for p in range(PMAX + 1):
         for b in (0, 1):
             L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx,"
-                     " double* Y, int64_t ny, cudaStream_t s);" % (p, b))
+                     " double* Y, int64_t ny, cudaStream_t s, float* part);" % (p, b))
+    L.append("// part: 8 x nc x ny floats for the per-child M2M (m2m32c + m2m32_sum), or")
+    L.append("// nullptr for the one-thread-per-parent M2M.  Returns the launches made.")
     L.append("int launch_shift32(int p, int basis, int m2m, int l, const float* A, const double* X, int64_t nx,"
-             " double* Y, int64_t ny, cudaStream_t s) {")
+             " double* Y, int64_t ny, cudaStream_t s, float* part) {")
     for p in range(PMAX + 1):
         for b in (0, 1):
-            L.append("  if (p == %d && basis == %d) return launch_shift32_p%d_b%d(m2m, l, A, X, nx, Y, ny, s);"
+            L.append("  if (p == %d && basis == %d) return launch_shift32_p%d_b%d(m2m, l, A, X, nx, Y, ny, s, part);"
                      % (p, b, p, b))
     L.append("  return -1;")
     L.append("}")
