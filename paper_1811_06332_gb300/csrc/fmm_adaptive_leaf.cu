@@ -252,7 +252,7 @@ __device__ __forceinline__ void p2p_acc(const float4 s, float xi, float yi, floa
                                         float& gy, float& gz) {
     const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir = GUARD ? (r2 > 0.f ? rsqrtf(r2) : 0.f) : rsqrtf(r2);
+    const float ir = GUARD ? (r2 > 0.f ? fmm_rsqrt(r2) : 0.f) : fmm_rsqrt(r2);
     const float qir = s.w * ir, qir3 = qir * ir * ir;
     ph += qir;
     gx = fmaf(qir3, dx, gx);

@@ -16,7 +16,16 @@ int launch_m2m32_sum(int nc, int64_t npa, const float* part, double* Mpa, cudaSt
 // value; one call in place of a rounded square root and a rounded division,
 // which on this part's FP64 units costs several times the rest of a pair)
 __device__ __forceinline__ double fmm_rsqrt(double v) { return rsqrt(v); }
-__device__ __forceinline__ float fmm_rsqrt(float v) { return rsqrtf(v); }
+// FP32: the PTX approximate reciprocal square root with subnormal inputs
+// flushed to zero (one special-function instruction).  Its arguments are
+// squared distances of FP32 offsets within a few cells, which for distinct
+// points lie far above the subnormal range; exact zeros are excluded by the
+// callers.
+__device__ __forceinline__ float fmm_rsqrt(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 
 // Storage positions (App. D multi-indices; App. A compressed order).
 __host__ __device__ __forceinline__ int ns_of(int p) { return p < 0 ? 0 : (p + 1) * (p + 2) * (p + 3) / 6; }

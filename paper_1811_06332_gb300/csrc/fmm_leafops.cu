@@ -534,7 +534,7 @@ int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const
 __device__ __forceinline__ void p2p32_pair(const float4 sv, const float4 p, float& f, float& x, float& y, float& z) {
     const float rx = sv.x - p.x, ry = sv.y - p.y, rz = sv.z - p.z;
     const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float ir = rsqrtf(r2);
+    const float ir = fmm_rsqrt(r2);
     const float qir = sv.w * ir, qir3 = qir * ir * ir;
     f += qir; x = fmaf(qir3, rx, x); y = fmaf(qir3, ry, y); z = fmaf(qir3, rz, z);
 }
@@ -542,7 +542,7 @@ __device__ __forceinline__ void p2p32_pair_guarded(const float4 sv, const float4
                                                    float& z) {
     const float rx = sv.x - p.x, ry = sv.y - p.y, rz = sv.z - p.z;
     const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float ir = r2 > 0.f ? fmm_rsqrt(r2) : 0.f;
     const float qir = sv.w * ir, qir3 = qir * ir * ir;
     f += qir; x = fmaf(qir3, rx, x); y = fmaf(qir3, ry, y); z = fmaf(qir3, rz, z);
 }
