@@ -405,9 +405,17 @@ __device__ __forceinline__ void p2m_reduce_rank(const float* sR, const float* a,
                                                 int64_t c) {
     if constexpr (J <= P) {
         constexpr int cols = (J + 1) * (J + 2) / 2;
+        // the rank's moments by 16-byte loads of the aligned span around them
+        constexpr int A0 = S0 / 4 * 4, A1 = (S0 + cols + 3) / 4 * 4;
+        float v[A1 - A0];
+#pragma unroll
+        for (int k = 0; k < A1 - A0; k += 4) {
+            const float4 q = *(const float4*)(a + A0 + k);
+            v[k] = q.x; v[k + 1] = q.y; v[k + 2] = q.z; v[k + 3] = q.w;
+        }
         float m[cols];
 #pragma unroll
-        for (int k = 0; k < cols; ++k) m[k] = a[S0 + k];
+        for (int k = 0; k < cols; ++k) m[k] = v[S0 - A0 + k];
 #pragma unroll 1
         for (int u = 0; u < 2 * J + 1; ++u) {
             const float* R = sR + RO + u * cols;

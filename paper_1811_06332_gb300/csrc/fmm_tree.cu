@@ -143,16 +143,23 @@ __global__ void k_gather(int64_t n, const int* __restrict__ order, const double*
     if (i >= n) return;
     const int o = order[i];
     const double xo = x[o], yo = y[o], zo = z[o], qo = q[o];
-    xs[i] = xo; ys[i] = yo; zs[i] = zo; qs[i] = qo;
     perm[i] = o;
     if (pos32) {
-        // FP32 position relative to the centre of the particle's own leaf
-        int ix, iy, iz;
-        cell_coords(depth, key[o], ix, iy, iz);
-        const double h = 1.0 / (double)(1 << depth);
+        // FP32 forms: only the FP32 position relative to the centre of the
+        // particle's own leaf (its cell recomputed as k_leaf_key computes it,
+        // instead of a second random read of the key); their operators read
+        // no sorted FP64 coordinates
+        const int side = 1 << depth;
+        const double fs = (double)side;
+        const int ix = min(max((int)floor(xo * fs), 0), side - 1);
+        const int iy = min(max((int)floor(yo * fs), 0), side - 1);
+        const int iz = min(max((int)floor(zo * fs), 0), side - 1);
+        const double h = 1.0 / (double)side;
         pos32[i] = make_float4((float)(xo - (ix + 0.5) * h), (float)(yo - (iy + 0.5) * h),
                                (float)(zo - (iz + 0.5) * h), (float)qo);
+        return;
     }
+    xs[i] = xo; ys[i] = yo; zs[i] = zo; qs[i] = qo;
 }
 
 int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,
