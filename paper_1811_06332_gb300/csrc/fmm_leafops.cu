@@ -73,10 +73,18 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * WARPS + w;
     if (c >= nleaf) return;
-    int ix, iy, iz;
-    cell_coords(depth, c, ix, iy, iz);
-    const double inv_h = (double)(1 << depth), h = 1.0 / inv_h;
-    const double cx = (ix + 0.5) * h, cy = (iy + 0.5) * h, cz = (iz + 0.5) * h;
+    // the leaf centre in FP64 only for the FP64 coordinates; the FP32 path
+    // scales by the exact power of two in FP32 (an FP64 operation costs a
+    // warp 16 cycles of this part's narrow FP64 pipe)
+    const float inv_hf = (float)(1 << depth);
+    double inv_h = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+    if (!pos32) {
+        int ix, iy, iz;
+        cell_coords(depth, c, ix, iy, iz);
+        inv_h = (double)(1 << depth);
+        const double h = 1.0 / inv_h;
+        cx = (ix + 0.5) * h; cy = (iy + 0.5) * h; cz = (iz + 0.5) * h;
+    }
     const int b = start[c], e = start[c + 1];
     // columns of this lane: col = lane + 32*k -> (nx, ny)
     constexpr int KC = (NCOL + 31) / 32;
@@ -99,9 +107,9 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
         if (a < e) {
             if (pos32) {   // FP32 offsets from the leaf centre
                 const float4 v = pos32[a];
-                sx[w][lane] = T(-v.x * (float)inv_h);
-                sy[w][lane] = T(-v.y * (float)inv_h);
-                sz[w][lane] = T(-v.z * (float)inv_h);
+                sx[w][lane] = T(-v.x * inv_hf);
+                sy[w][lane] = T(-v.y * inv_hf);
+                sz[w][lane] = T(-v.z * inv_hf);
                 sq[w][lane] = T(v.w);
             } else {
                 sx[w][lane] = T((cx - xs[a]) * inv_h);   // -(x_a - z)/h
@@ -278,10 +286,15 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
     }
     __syncwarp();
     if (!valid || b == e) return;
-    int ix, iy, iz;
-    cell_coords(depth, c, ix, iy, iz);
-    const double inv_h = (double)(1 << depth), hc = 1.0 / inv_h;
-    const double cx = (ix + 0.5) * hc, cy = (iy + 0.5) * hc, cz = (iz + 0.5) * hc;
+    const float inv_hf = (float)(1 << depth);   // exact
+    const double inv_h = (double)(1 << depth);
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    if (!pos32) {
+        int ix, iy, iz;
+        cell_coords(depth, c, ix, iy, iz);
+        const double hc = 1.0 / inv_h;
+        cx = (ix + 0.5) * hc; cy = (iy + 0.5) * hc; cz = (iz + 0.5) * hc;
+    }
     const T* Ln = sN[w][h];
     for (int a0 = b; a0 < e; a0 += 16) {
         const int a = a0 + hl;
@@ -289,7 +302,7 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
         T rx, ry, rz;
         if (pos32) {
             const float4 v = pos32[a];
-            rx = T(v.x * (float)inv_h); ry = T(v.y * (float)inv_h); rz = T(v.z * (float)inv_h);
+            rx = T(v.x * inv_hf); ry = T(v.y * inv_hf); rz = T(v.z * inv_hf);
         } else {
             rx = T((xs[a] - cx) * inv_h); ry = T((ys[a] - cy) * inv_h); rz = T((zs[a] - cz) * inv_h);
         }
@@ -304,10 +317,19 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
         T ph = 0, gx = 0, gy = 0, gz = 0;
         l2p_all<P, T, 0>(Ln, fx, fy, fz, ph, gx, gy, gz);
         const int o = perm[a];
-        pot[o] = -(double)ph * inv_h;
-        ax[o] = (double)gx * inv_h * inv_h;
-        ay[o] = (double)gy * inv_h * inv_h;
-        az[o] = (double)gz * inv_h * inv_h;
+        if constexpr (sizeof(T) == 4) {
+            // scaling by powers of two, exact in FP32 (outside FP32's
+            // subnormal range), then one conversion each
+            pot[o] = (double)(-ph * inv_hf);
+            ax[o] = (double)(gx * inv_hf * inv_hf);
+            ay[o] = (double)(gy * inv_hf * inv_hf);
+            az[o] = (double)(gz * inv_hf * inv_hf);
+        } else {
+            pot[o] = -(double)ph * inv_h;
+            ax[o] = (double)gx * inv_h * inv_h;
+            ay[o] = (double)gy * inv_h * inv_h;
+            az[o] = (double)gz * inv_h * inv_h;
+        }
     }
 }
 
@@ -723,7 +745,7 @@ k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
                 float(Lt[(int64_t)s * nleaf + c]);
     }
     __syncwarp();
-    const double inv_h = (double)(1 << depth);
+    const float inv_hf = (float)(1 << depth);   // exact
     const float* Ln = sN[w];
     const int side = 1 << depth;
     const float h = 1.0f / (float)side;
@@ -757,7 +779,7 @@ k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
 #pragma unroll 1
         for (int k = lane; k < tn; k += 32) {
             const float4 v = pos[t0 + k];
-            sF[w][k] = l2p_point32<P>(Ln, v.x * (float)inv_h, v.y * (float)inv_h, v.z * (float)inv_h);
+            sF[w][k] = l2p_point32<P>(Ln, v.x * inv_hf, v.y * inv_hf, v.z * inv_hf);
         }
         __syncwarp();
         int tp = 1;
@@ -812,22 +834,23 @@ k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
             yb += __shfl_xor_sync(0xffffffffu, yb, o); zb += __shfl_xor_sync(0xffffffffu, zb, o);
         }
         if (grp == 0) {
-            const double h2 = inv_h;
+            // the far field scaled as k_l2p_leaf2 scales it (exact powers of two
+            // in FP32), plus the near field in FP64 as k_p2p32 adds it
             if (va) {
                 const int o = perm[ta];
                 const float4 F = sF[w][tl];
-                pot[o] = __dsub_rn(__dmul_rn(-(double)F.x, h2), (double)fa);
-                ax[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.y, h2), h2), (double)xa);
-                ay[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.z, h2), h2), (double)ya);
-                az[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.w, h2), h2), (double)za);
+                pot[o] = __dsub_rn((double)(-F.x * inv_hf), (double)fa);
+                ax[o] = __dadd_rn((double)(F.y * inv_hf * inv_hf), (double)xa);
+                ay[o] = __dadd_rn((double)(F.z * inv_hf * inv_hf), (double)ya);
+                az[o] = __dadd_rn((double)(F.w * inv_hf * inv_hf), (double)za);
             }
             if (vb) {
                 const int o = perm[tb];
                 const float4 F = sF[w][tl + tp];
-                pot[o] = __dsub_rn(__dmul_rn(-(double)F.x, h2), (double)fb);
-                ax[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.y, h2), h2), (double)xb);
-                ay[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.z, h2), h2), (double)yb);
-                az[o] = __dadd_rn(__dmul_rn(__dmul_rn((double)F.w, h2), h2), (double)zb);
+                pot[o] = __dsub_rn((double)(-F.x * inv_hf), (double)fb);
+                ax[o] = __dadd_rn((double)(F.y * inv_hf * inv_hf), (double)xb);
+                ay[o] = __dadd_rn((double)(F.z * inv_hf * inv_hf), (double)yb);
+                az[o] = __dadd_rn((double)(F.w * inv_hf * inv_hf), (double)zb);
             }
         }
         __syncwarp();
