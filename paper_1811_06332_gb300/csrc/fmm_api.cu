@@ -91,6 +91,11 @@ struct fmm_plan {
 
 static bool is_tc(int prec) { return prec == FMM_GEMM_BF16X3 || prec == FMM_GEMM_TF32X3; }
 
+// Uniform FP32 and tensor-core plans on the per-child FP32 M2M: P2M and M2M
+// keep M32 (the FP32 copy of the multipoles) current at every level, so the
+// M2M and M2L kernels read it instead of converting the FP64 expansions again.
+static bool m32_current(const fmm_plan* pl) { return !pl->ad && pl->M32 && pl->W32 && pl->part32; }
+
 // storage basis of the multipoles and of the local expansions (the TG
 // basis: symmetric multipoles, traceless locals; Sec. 3)
 static int bM(const fmm_plan* pl) { return pl->cfg.basis == FMM_BASIS_TG ? 0 : pl->cfg.basis; }
@@ -162,13 +167,14 @@ static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
     char* hp = (char*)pl->Mbf + pl->mbf_off[l] * es;
     char* lp = hp + tc_m_elems(l) * es;
     const int p = pl->cfg.p;
+    const float* m32 = m32_current(pl) ? pl->M32 + pl->lvl_off[l] : nullptr;
     const int rc = tc_m2l_level(p, tf, pl->tc_kern, pl->tc_cw, pl->tc_niss, l, pl->Mbuf + pl->lvl_off[l], hp, lp,
                                 tc_maps_at(pl, l), pl->tc_kern == 1 ? pl->Kgen : pl->Kbf, pl->Lbuf + pl->lvl_off[l],
-                                pl->derr, s);
+                                pl->derr, s, m32);
     // kernel 3: the multipole columns >= 48 (a cell-major FP32 copy of
     // them, then their products) on the CUDA cores, added to L
     if (rc == 0 && pl->tc_kern == 3 && rest_rows(p) > 0 &&
-        (launch_rest_pack(p, l, pl->Mbuf + pl->lvl_off[l], pl->Mrest, s) != 0 ||
+        (launch_rest_pack(p, l, pl->Mbuf + pl->lvl_off[l], pl->Mrest, s, m32) != 0 ||
          launch_m2l_rest(p, l, pl->Mrest, pl->Krest, pl->Lbuf + pl->lvl_off[l], s) != 0))
         return -2;
     return rc;
@@ -828,7 +834,8 @@ int fmm_p2m(fmm_plan* pl, void* stream) {
     if (pl->ad) { ad_run_p2m(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     const int d = pl->depth;
     launch_p2m_leaf(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, bM(pl), d, pl->nleaf, pl->start, pl->xs,
-                    pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32, pl->msym32);
+                    pl->ys, pl->zs, pl->qs, Mlev(pl, d), g_tab[pl->dev], S(stream), pl->pos32, pl->msym32,
+                    m32_current(pl) ? pl->M32 + pl->lvl_off[d] : nullptr);
     CKLAUNCH();
     return FMM_OK;
 }
@@ -844,9 +851,11 @@ int fmm_m2m(fmm_plan* pl, void* stream) {
     }
     if (pl->W32) {
         for (int l = pl->depth - 1; l >= 2; --l) {
+            const bool c32 = m32_current(pl);
             const int nl = launch_shift32(pl->cfg.p, pl->cfg.basis, 1, l, pl->W32, Mlev(pl, l + 1),
                                           (int64_t)1 << (3 * (l + 1)), Mlev(pl, l), (int64_t)1 << (3 * l), S(stream),
-                                          pl->part32);
+                                          pl->part32, c32 ? pl->M32 + pl->lvl_off[l + 1] : nullptr,
+                                          c32 ? pl->M32 + pl->lvl_off[l] : nullptr);
             for (int k = 0; k < nl; ++k) count_launch();
         }
         CKLAUNCH();
@@ -894,7 +903,7 @@ static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
         const int lt = hi < tc_first_level() - 1 ? hi : tc_first_level() - 1;
         if (lo <= lt) {
             const int64_t b = pl->lvl_off[lo], e = pl->lvl_off[lt] + ((int64_t)pl->nc << (3 * lt));
-            launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
+            if (!m32_current(pl)) launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
             for (int l = lo; l <= lt; ++l) {
                 const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
                                                  pl->K32, (int64_t)1 << (3 * l), S(stream));
@@ -913,7 +922,7 @@ static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
     }
     if (pl->cfg.prec == FMM_FP32) {
         const int64_t b = pl->lvl_off[lo], e = pl->lvl_off[hi] + ((int64_t)pl->nc << (3 * hi));
-        launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
+        if (!m32_current(pl)) launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
         for (int l = lo; l <= hi; ++l) {
             const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
                                              pl->K32, (int64_t)1 << (3 * l), S(stream));

@@ -106,7 +106,7 @@ int launch_fill(int64_t n, double* a, double v, cudaStream_t s);
 // fmm_leafops.cu (prec 0: double arithmetic, 1: float arithmetic)
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                     const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
-                    cudaStream_t s, const float4* pos32 = nullptr, float* msym = nullptr);
+                    cudaStream_t s, const float4* pos32 = nullptr, float* msym = nullptr, float* M32 = nullptr);
 int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                      const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
                      double* pot, double* ax, double* ay, double* az, cudaStream_t s,
@@ -137,10 +137,12 @@ extern "C" __attribute__((visibility("hidden"))) void build_translation(int p, i
 namespace fmm {
 
 // generated shift_*.cu: FP32 level shifts (m2m = 1: M2M, 0: L2L)
-// part (M2M): 8 x nc x ny floats for the per-child form, or nullptr.
+// part (M2M): 8 x nc x ny floats for the per-child form (with the FP32
+// copies X32 of the children and Y32 of the parents), or nullptr.
 // Returns the number of kernels launched, -1 without a kernel for (p, basis).
 int launch_shift32(int p, int basis, int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,
-                   int64_t ny, cudaStream_t s, float* part = nullptr);
+                   int64_t ny, cudaStream_t s, float* part = nullptr, const float* X32 = nullptr,
+                   float* Y32 = nullptr);
 int shift32_supported(int p, int basis);
 int launch_l2p_p2p32(int p, int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
                      const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,
@@ -173,7 +175,7 @@ int rest_rows(int p);
 int rest_kstride(int p);   // floats per offset of the matrix table
 int rest_cstride(int p);   // floats per cell of the multipole copy
 int build_krest(int p, const double* Dtab, float* Krest, cudaStream_t s);
-int launch_rest_pack(int p, int l, const double* M, float* Mrest, cudaStream_t s);
+int launch_rest_pack(int p, int l, const double* M, float* Mrest, cudaStream_t s, const float* M32 = nullptr);
 // Lt (level l, after the tensor-core kernel) += those products
 int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s);
 size_t tc_maps_bytes();
@@ -183,7 +185,8 @@ size_t tc_maps_bytes();
 int tc_build_mat(int p, int tf, int cw, const double* Dtab, void* B, cudaStream_t s);
 int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps);
 int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double* M, void* hi, void* lo,
-                 const void* maps, const void* B, double* Lt, int* err, cudaStream_t s);
+                 const void* maps, const void* B, double* Lt, int* err, cudaStream_t s,
+                 const float* M32 = nullptr);
 // fmm_m2l_tcgen.cu (BF16 hi/lo form, offset matrices built on chip)
 int tg_supported(int p);
 size_t tg_b_bytes();

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const double* __restrict__ xs,
            const double* __restrict__ ys, const double* __restrict__ zs, const double* __restrict__ qs,
            double* __restrict__ M, const T* __restrict__ reduce, DevOffsets off,
-           const float4* __restrict__ pos32, float* __restrict__ msym) {
+           const float4* __restrict__ pos32, float* __restrict__ msym, float* __restrict__ M32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NCOL = (P + 1) * (P + 2) / 2;
     // powers per axis; FP32 rows padded to 16 bytes for vector loads (FP64 rows
@@ -164,7 +164,10 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
     }
     __syncwarp();
     if (!basis) {
-        for (int s = lane; s < NS; s += 32) M[(int64_t)s * nleaf + c] = (double)sA[w][s];
+        for (int s = lane; s < NS; s += 32) {
+            M[(int64_t)s * nleaf + c] = (double)sA[w][s];
+            if (M32) M32[(int64_t)s * nleaf + c] = float(sA[w][s]);
+        }
         return;
     }
     if (msym) {
@@ -185,6 +188,7 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
         T v = T(0);
         for (int s = 0; s < cols; ++s) v += R[s] * As[s];
         M[(int64_t)t * nleaf + c] = (double)v;
+        if (M32) M32[(int64_t)t * nleaf + c] = float(v);
     }
 }
 
@@ -423,8 +427,8 @@ const float* tab_of<float>(const double*, const float* f) { return f; }
 // rank J of k_p2m_reduce (RO: offset of its rows in the map, S0: of its
 // moments), then the next rank; every bound is a compile-time constant
 template <int P, int J, int RO, int S0>
-__device__ __forceinline__ void p2m_reduce_rank(const float* sR, const float* a, double* M, int64_t nleaf,
-                                                int64_t c) {
+__device__ __forceinline__ void p2m_reduce_rank(const float* sR, const float* a, double* M, float* M32,
+                                                int64_t nleaf, int64_t c) {
     if constexpr (J <= P) {
         constexpr int cols = (J + 1) * (J + 2) / 2;
         // the rank's moments by 16-byte loads of the aligned span around them
@@ -445,8 +449,9 @@ __device__ __forceinline__ void p2m_reduce_rank(const float* sR, const float* a,
 #pragma unroll
             for (int k = 0; k < cols; ++k) v = fmaf(R[k], m[k], v);
             M[(int64_t)(J * J + u) * nleaf + c] = (double)v;
+            if (M32) M32[(int64_t)(J * J + u) * nleaf + c] = v;
         }
-        p2m_reduce_rank<P, J + 1, RO + (2 * J + 1) * cols, S0 + cols>(sR, a, M, nleaf, c);
+        p2m_reduce_rank<P, J + 1, RO + (2 * J + 1) * cols, S0 + cols>(sR, a, M, M32, nleaf, c);
     }
 }
 
@@ -458,7 +463,7 @@ __device__ __forceinline__ void p2m_reduce_rank(const float* sR, const float* a,
 template <int P>
 __global__ void __launch_bounds__(128)
 k_p2m_reduce(int64_t nleaf, const float* __restrict__ msym, const float* __restrict__ reduce, DevOffsets off,
-             double* __restrict__ M) {
+             double* __restrict__ M, float* __restrict__ M32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6, NSP = (NS + 3) / 4 * 4;
     constexpr int RT = [] {
         int t = 0;
@@ -477,21 +482,22 @@ k_p2m_reduce(int64_t nleaf, const float* __restrict__ msym, const float* __restr
     __syncthreads();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nleaf) return;
-    p2m_reduce_rank<P, 0, 0, 0>(sR, msym + c * NSP, M, nleaf, c);
+    p2m_reduce_rank<P, 0, 0, 0>(sR, msym + c * NSP, M, M32, nleaf, c);
 }
 
 template <int P, typename T>
 static void p2m_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
                        const double* zs, const double* qs, double* M, const DevTables& Tb, cudaStream_t s,
-                       const float4* pos32, float* msym) {
+                       const float4* pos32, float* msym, float* M32) {
     constexpr int W = 4;
     const bool split = sizeof(T) == 4 && basis && msym;
     k_p2m_leaf<P, T, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(basis, depth, nleaf, start, xs, ys, zs,
                                                                            qs, M, tab_of<T>(Tb.reduce, Tb.reduce32),
                                                                            Tb.offsets(), pos32,
-                                                                           split ? msym : nullptr);
+                                                                           split ? msym : nullptr, M32);
     if (split) {
-        k_p2m_reduce<P><<<(unsigned)((nleaf + 127) / 128), 128, 0, s>>>(nleaf, msym, Tb.reduce32, Tb.offsets(), M);
+        k_p2m_reduce<P><<<(unsigned)((nleaf + 127) / 128), 128, 0, s>>>(nleaf, msym, Tb.reduce32, Tb.offsets(), M,
+                                                                        M32);
         count_launch();
     }
 }
@@ -513,10 +519,10 @@ static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, co
 
 int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                     const double* ys, const double* zs, const double* qs, double* M, const DevTables& Tb,
-                    cudaStream_t s, const float4* pos32, float* msym) {
+                    cudaStream_t s, const float4* pos32, float* msym, float* M32) {
     if (nleaf <= 0) return 0;
-#define C64(P) p2m_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, nullptr, nullptr)
-#define C32(P) p2m_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, pos32, msym)
+#define C64(P) p2m_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, nullptr, nullptr, nullptr)
+#define C32(P) p2m_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, qs, M, Tb, s, pos32, msym, M32)
     if (prec == 0) { FMM_P_SWITCH(p, C64) } else { FMM_P_SWITCH(p, C32) }
 #undef C64
 #undef C32

@@ -106,8 +106,9 @@ int launch_to_f32(int64_t n, const double* a, float* b, cudaStream_t s) {
 
 // M2M of one level from the per-child FP32 contributions (m2m32c):
 // Mpa(r, P) = sum over the child classes c = 0..7, in that order, of
-// part[(c nc + r) npa + P].
-__global__ void k_m2m32_sum(int nc, int64_t npa, const float* __restrict__ part, double* __restrict__ Mpa) {
+// part[(c nc + r) npa + P]; written in FP64 and to the FP32 copy Mpa32.
+__global__ void k_m2m32_sum(int nc, int64_t npa, const float* __restrict__ part, double* __restrict__ Mpa,
+                            float* __restrict__ Mpa32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)nc * npa) return;
     const int64_t r = i / npa, P = i - r * npa;
@@ -115,12 +116,13 @@ __global__ void k_m2m32_sum(int nc, int64_t npa, const float* __restrict__ part,
 #pragma unroll
     for (int c = 1; c < 8; ++c) v += part[((int64_t)c * nc + r) * npa + P];
     Mpa[i] = (double)v;
+    Mpa32[i] = v;
 }
 
-int launch_m2m32_sum(int nc, int64_t npa, const float* part, double* Mpa, cudaStream_t s) {
+int launch_m2m32_sum(int nc, int64_t npa, const float* part, double* Mpa, float* Mpa32, cudaStream_t s) {
     const int64_t n = (int64_t)nc * npa;
     if (n <= 0) return 0;
-    k_m2m32_sum<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nc, npa, part, Mpa);
+    k_m2m32_sum<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nc, npa, part, Mpa, Mpa32);
     return 0;
 }
 

@@ -13,7 +13,8 @@
 // tensor-core kernel and adds them to L, reading
 //   Mrest  the columns >= 48 of a level's multipoles, cell-major FP32, one
 //          16-byte aligned record of rest_cstride(p) floats per cell
-//          (k_rest_pack, once per level and step), and
+//          (k_rest_pack, once per level and step, from the plan's FP32 copy
+//          of the multipoles when it has one), and
 //   Krest  per offset, the rows of rank <= p - 6 one after the other, each
 //          with its entries of columns >= 48 padded to a multiple of 4
 //          (k_build_krest, once per plan).
@@ -114,14 +115,17 @@ k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ K
 // Mrest of level l from the FP64 coefficient-major multipoles M: a block
 // transposes 64 cells through shared memory
 template <int P>
-__global__ void __launch_bounds__(256) k_rest_pack(int64_t ncell, const double* __restrict__ M, float* __restrict__ Mrest) {
+__global__ void __launch_bounds__(256) k_rest_pack(int64_t ncell, const double* __restrict__ M, float* __restrict__ Mrest,
+                                                   const float* __restrict__ M32) {
     constexpr int NCOL = (P + 1) * (P + 1) - RS_K0;
     constexpr int CS = rs_cstride(P);
     __shared__ float tile[64][CS + 1];
     const int64_t c0 = (int64_t)blockIdx.x * 64;
     const int cl = threadIdx.x & 63;
     for (int c = threadIdx.x >> 6; c < NCOL; c += 4)
-        tile[cl][c] = c0 + cl < ncell ? (float)M[(int64_t)(RS_K0 + c) * ncell + c0 + cl] : 0.f;
+        tile[cl][c] = c0 + cl >= ncell ? 0.f
+                      : M32 ? M32[(int64_t)(RS_K0 + c) * ncell + c0 + cl]
+                            : (float)M[(int64_t)(RS_K0 + c) * ncell + c0 + cl];
     __syncthreads();
     for (int e = threadIdx.x; e < 64 * CS; e += 256) {
         const int cell = e / CS, c = e % CS;
@@ -182,11 +186,11 @@ int build_krest(int p, const double* Dtab, float* Krest, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-int launch_rest_pack(int p, int l, const double* M, float* Mrest, cudaStream_t s) {
+int launch_rest_pack(int p, int l, const double* M, float* Mrest, cudaStream_t s, const float* M32) {
     if (!rest_rows(p)) return -1;
     const int64_t ncell = (int64_t)8 << (3 * (l - 1));
     const unsigned g = (unsigned)((ncell + 63) / 64);
-#define RS_K(P) (k_rest_pack<P><<<g, 256, 0, s>>>(ncell, M, Mrest), 0)
+#define RS_K(P) (k_rest_pack<P><<<g, 256, 0, s>>>(ncell, M, Mrest, M32), 0)
     RS_P_SWITCH(p, RS_K);
 #undef RS_K
     count_launch();

@@ -312,8 +312,8 @@ struct TcSplit<0> {
     // of FP32), then hi = x rounded to BF16 and lo = the rest, whose FP32
     // difference is exact; hi + lo keeps 16 bits of x, far above the 24 of
     // the FP32 rounding
-    static __device__ __forceinline__ void split(double x, T& h, T& l) {
-        const float xf = (float)x;
+    static __device__ __forceinline__ void split(double x, T& h, T& l) { split32((float)x, h, l); }
+    static __device__ __forceinline__ void split32(float xf, T& h, T& l) {
         h = __float2bfloat16_rn(xf);
         l = __float2bfloat16_rn(xf - __bfloat162float(h));
     }
@@ -321,8 +321,9 @@ struct TcSplit<0> {
 template <>
 struct TcSplit<1> {
     using T = uint32_t;
-    static __device__ __forceinline__ void split(double x, T& h, T& l) {
-        const float xf = (float)x;   // as for BF16: one conversion, the rest in FP32
+    // as for BF16: one conversion, the rest in FP32
+    static __device__ __forceinline__ void split(double x, T& h, T& l) { split32((float)x, h, l); }
+    static __device__ __forceinline__ void split32(float xf, T& h, T& l) {
         h = tf32_round(xf);
         l = tf32_round(xf - __uint_as_float(h));
     }
@@ -335,9 +336,12 @@ struct TcSplit<1> {
 // kernel whose offset matrices hold D_{n+m} without the 1/m! weight).  One
 // thread per (cell, chunk): blockIdx.y is the chunk, the cell index splits
 // into class and (i, j, k) by shifts (the class grid side is a power of 2).
+// M32 (when given, and without scale): the plan's FP32 copy of the same
+// multipoles, read instead of M (the split starts from the FP32 value either
+// way, so the operands are the same).
 template <int TF>
 __global__ void k_tc_split_m(int l, int nc, int scale, const double* __restrict__ M, void* __restrict__ hi_,
-                             void* __restrict__ lo_) {
+                             void* __restrict__ lo_, const float* __restrict__ M32) {
     using T = typename TcSplit<TF>::T;
     constexpr int EPC = 16 / (int)sizeof(T);        // elements per 16-byte chunk
     constexpr int NCH = TC_K / EPC;                 // chunks per row
@@ -351,6 +355,10 @@ __global__ void k_tc_split_m(int l, int nc, int scale, const double* __restrict_
 #pragma unroll
     for (int e = 0; e < EPC; ++e) {
         const int m = EPC * c + e;
+        if (M32) {
+            TcSplit<TF>::split32(m < nc ? M32[(int64_t)m * ncell + idx] : 0.f, vh[e], vl[e]);
+            continue;
+        }
         double x = m < nc ? M[(int64_t)m * ncell + idx] : 0.0;
         if (scale && m < nc) x *= c_invfact[c_tl_idx[m][0]] * c_invfact[c_tl_idx[m][1]] * c_invfact[c_tl_idx[m][2]];
         TcSplit<TF>::split(x, vh[e], vl[e]);
@@ -588,7 +596,8 @@ static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const 
 }
 
 int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double* M, void* hi, void* lo,
-                 const void* maps, const void* B, double* Lt, int* err, cudaStream_t s) {
+                 const void* maps, const void* B, double* Lt, int* err, cudaStream_t s,
+                 const float* M32) {
     const int hs = 1 << (l - 1);
     if (hs < 16) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
@@ -599,9 +608,9 @@ int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double*
     if ((kern >= 1) && tf) return -1;   // the on-chip and swapped kernels take BF16 operands
     // the on-chip kernel's matrices hold D_{n+m} alone: its operand carries 1/m!
     if (tf)
-        k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, 0, M, hi, lo);
+        k_tc_split_m<1><<<g, 256, 0, s>>>(l, nc, 0, M, hi, lo, M32);
     else
-        k_tc_split_m<0><<<g, 256, 0, s>>>(l, nc, kern == 1, M, hi, lo);
+        k_tc_split_m<0><<<g, 256, 0, s>>>(l, nc, kern == 1, M, hi, lo, kern == 1 ? nullptr : M32);
     count_launch();
     if (kern == 1) {
         const int rc = tg_m2l_level(p, cw, niss, l, maps, B, Lt, err, s);

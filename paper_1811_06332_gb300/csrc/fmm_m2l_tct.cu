@@ -26,7 +26,8 @@
 // no local component and are never read.
 // Split precision: x = hi + lo in BF16, three MMAs per K-step (hi.hi, hi.lo,
 // lo.hi), FP32 accumulation in TMEM, the two issuers' accumulators added in
-// FP64 at write-out.
+// FP32 and converted once at write-out (FP64 operations are the narrow pipe
+// of this part).
 //
 // Kernel shape 3 runs the first K-part only: the columns >= 48 reach only
 // the local rows of rank <= p - 6 (9 of the 128 rows at p = 8), so the second
@@ -251,9 +252,9 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int npt, int nrow
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int q = warp & 3;
         const int n = q * 32 + lane;   // local component of this thread's TMEM lane
-        // a 32 x 33 FP64 tile per warp in the slab buffers (free: every copy
+        // a 32 x 33 FP32 tile per warp in the slab buffers (free: every copy
         // has been consumed by the MMAs behind `done`)
-        double* tile = (double*)smem + (warp - 2) * 32 * 33;
+        float* tile = (float*)smem + (warp - 2) * 32 * 33;
         if (q * 32 < nrows) {
             const int64_t h3 = (int64_t)hs * hs * hs;
             const int64_t tbase = (int64_t)cls * h3 + ((int64_t)tk * hs + TY * tj) * hs + 8 * ti;
@@ -267,13 +268,13 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int npt, int nrow
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int e = 0; e < 32; ++e)
-                    tile[lane * 33 + e] = (double)__uint_as_float(v0[e]) + (double)__uint_as_float(v1[e]);
+                    tile[lane * 33 + e] = __uint_as_float(v0[e]) + __uint_as_float(v1[e]);
                 __syncwarp();
                 // lane = cell (x, y) = (col % 8, col / 8) of the tile, col = 32 cb + lane
                 const int col = cb * 32 + lane;
                 const int64_t cell = tbase + (int64_t)(col >> 3) * hs + (col & 7);
                 if (ok)
-                    for (int r = 0; r < rmax; ++r) Lt[(int64_t)(q * 32 + r) * ncell + cell] = tile[r * 33 + lane];
+                    for (int r = 0; r < rmax; ++r) Lt[(int64_t)(q * 32 + r) * ncell + cell] = (double)tile[r * 33 + lane];
                 __syncwarp();
             }
         }

@@ -574,7 +574,7 @@ def emit_shift_file(p, basis):
         # parent on eight threads (blockIdx.y = child class), their FP32
         # contributions summed afterwards in child order (m2m32_sum) ----
         L.append("__global__ void __launch_bounds__(128)")
-        L.append("m2m32c_p%d_b%d(int l, const float* __restrict__ W, const double* __restrict__ Mch, int64_t nch,"
+        L.append("m2m32c_p%d_b%d(int l, const float* __restrict__ W, const float* __restrict__ Mch, int64_t nch,"
                  " float* __restrict__ part, int64_t npa) {" % (p, basis))
         L.append("  __shared__ float sW[%d];" % sz)
         L.append("  const int c = (int)blockIdx.y;")
@@ -586,7 +586,7 @@ def emit_shift_file(p, basis):
         L.append("  cell_coords(l, P, ix, iy, iz);")
         L.append("  const int64_t ch = c * ((int64_t)1 << (3 * l)) + lin_index(l, ix, iy, iz);")
         for k in range(nc):
-            L.append("  const float x%d = (float)Mch[(int64_t)%d * nch + ch];" % (k, k))
+            L.append("  const float x%d = Mch[(int64_t)%d * nch + ch];" % (k, k))
         for r in range(nc):
             c0, c1 = rng[r]
             L.append("  {")
@@ -631,12 +631,12 @@ def emit_shift_file(p, basis):
             L.append("  }")
         L.append("}")
     L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,"
-             " int64_t ny, cudaStream_t s, float* part) {" % (p, basis))
+             " int64_t ny, cudaStream_t s, float* part, const float* X32, float* Y32) {" % (p, basis))
     if shift32_ok(p, basis):
-        L.append("  if (m2m && part) {")
-        L.append("    m2m32c_p%d_b%d<<<dim3((unsigned)((ny + 127) / 128), 8), 128, 0, s>>>(l, A, X, nx, part, ny);"
+        L.append("  if (m2m && part && X32 && Y32) {")
+        L.append("    m2m32c_p%d_b%d<<<dim3((unsigned)((ny + 127) / 128), 8), 128, 0, s>>>(l, A, X32, nx, part, ny);"
                  % (p, basis))
-        L.append("    launch_m2m32_sum(%d, ny, part, Y, s);" % nc)
+        L.append("    launch_m2m32_sum(%d, ny, part, Y, Y32, s);" % nc)
         L.append("    return 2;")
         L.append("  }")
         L.append("  if (m2m) m2m32_p%d_b%d<<<(unsigned)((ny + 127) / 128), 128, 0, s>>>(l, A, X, nx, Y, ny);"
@@ -657,15 +657,16 @@ def emit_shift_dispatch():
     for p in range(PMAX + 1):
         for b in (0, 1):
             L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx,"
-                     " double* Y, int64_t ny, cudaStream_t s, float* part);" % (p, b))
-    L.append("// part: 8 x nc x ny floats for the per-child M2M (m2m32c + m2m32_sum), or")
-    L.append("// nullptr for the one-thread-per-parent M2M.  Returns the launches made.")
+                     " double* Y, int64_t ny, cudaStream_t s, float* part, const float* X32, float* Y32);" % (p, b))
+    L.append("// part: 8 x nc x ny floats for the per-child M2M (m2m32c + m2m32_sum), which")
+    L.append("// reads the children's FP32 copy X32 and writes both Y and its FP32 copy Y32;")
+    L.append("// without them the one-thread-per-parent M2M.  Returns the launches made.")
     L.append("int launch_shift32(int p, int basis, int m2m, int l, const float* A, const double* X, int64_t nx,"
-             " double* Y, int64_t ny, cudaStream_t s, float* part) {")
+             " double* Y, int64_t ny, cudaStream_t s, float* part, const float* X32, float* Y32) {")
     for p in range(PMAX + 1):
         for b in (0, 1):
-            L.append("  if (p == %d && basis == %d) return launch_shift32_p%d_b%d(m2m, l, A, X, nx, Y, ny, s, part);"
-                     % (p, b, p, b))
+            L.append("  if (p == %d && basis == %d)" % (p, b))
+            L.append("    return launch_shift32_p%d_b%d(m2m, l, A, X, nx, Y, ny, s, part, X32, Y32);" % (p, b))
     L.append("  return -1;")
     L.append("}")
     # packed entry lists (row, column) for host-side packing
