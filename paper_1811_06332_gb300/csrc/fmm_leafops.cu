@@ -559,8 +559,9 @@ int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const
 
 // ---------------------------------------------------------------------------
 // FP32 P2P on positions relative to leaf centres: one warp per target leaf,
-// two targets per lane (each staged source is used twice from registers),
-// lane groups split the sources, one 16-byte shared load per source.  The
+// its targets in blocks of up to 32 with 2, 3 or 4 targets per lane (each
+// staged source is used that many times from registers), lane groups split
+// the sources, one 16-byte shared load per source.  The
 // target leaf itself comes first among the 27 neighbour leaves: only the
 // chunks that hold its particles can contain the self pair or coincident
 // pairs (r^2 == 0 exactly, dropped by a select as the direct sum skips
@@ -582,6 +583,147 @@ __device__ __forceinline__ void p2p32_pair_guarded(const float4 sv, const float4
     const float qir = sv.w * ir, qir3 = qir * ir * ir;
     f += qir; x = fmaf(qir3, rx, x); y = fmaf(qir3, ry, y); z = fmaf(qir3, rz, z);
 }
+// The near field of one block of up to 32 targets [t0, t0 + tn) of a leaf:
+// NT targets per lane on lane groups of tp lanes (tp * NT >= tn), the
+// 32 / tp groups splitting each staged chunk of 32 sources, the groups'
+// sums added by shuffles.  The 27 neighbour leaves' sources are addressed
+// through the warp's prefix sums (incl, excl, sbS, offsets ox..oz per lane);
+// the chunks holding the target leaf's own particles ([0, nself)) take the
+// r^2 == 0 select.  FUSED: each output written once as the far field sF
+// (scaled by exact powers of two) plus the near field; otherwise the near
+// field added to the outputs.
+template <int NT, bool FUSED>
+__device__ __forceinline__ void p2p32_block(int t0, int tn, int tp, int lane, float4* __restrict__ sP,
+                                            const float4* __restrict__ sF, int total, int incl, int excl, int sbS,
+                                            float ox, float oy, float oz, int nself, const float4* __restrict__ pos,
+                                            const int* __restrict__ perm, float inv_hf, double* __restrict__ pot,
+                                            double* __restrict__ ax, double* __restrict__ ay,
+                                            double* __restrict__ az) {
+    const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
+    float4 pt[NT];
+    float f[NT], gx[NT], gy[NT], gz[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int k = tl + tp * j;
+        pt[j] = k < tn ? pos[t0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        f[j] = gx[j] = gy[j] = gz[j] = 0.f;
+    }
+    for (int c0 = 0; c0 < total; c0 += 32) {
+        {
+            const int g = min(c0 + lane, total - 1);
+            int i = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, i + step - 1);
+                if (v <= g) i += step;
+            }
+            const int sbi = __shfl_sync(0xffffffffu, sbS, i), exi = __shfl_sync(0xffffffffu, excl, i);
+            const float oxi = __shfl_sync(0xffffffffu, ox, i), oyi = __shfl_sync(0xffffffffu, oy, i),
+                        ozi = __shfl_sync(0xffffffffu, oz, i);
+            __syncwarp();
+            if (c0 + lane < total) {
+                const float4 v = pos[sbi + (g - exi)];
+                sP[lane] = make_float4(v.x + oxi, v.y + oyi, v.z + ozi, v.w);
+            }
+            __syncwarp();
+        }
+        const int cnt = min(32, total - c0);
+        if (c0 < nself) {
+            for (int k = grp; k < cnt; k += G) {
+                const float4 sv = sP[k];
+#pragma unroll
+                for (int j = 0; j < NT; ++j) p2p32_pair_guarded(sv, pt[j], f[j], gx[j], gy[j], gz[j]);
+            }
+        } else {
+#pragma unroll 2
+            for (int k = grp; k < cnt; k += G) {
+                const float4 sv = sP[k];
+#pragma unroll
+                for (int j = 0; j < NT; ++j) p2p32_pair(sv, pt[j], f[j], gx[j], gy[j], gz[j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+        for (int o = tp; o < 32; o <<= 1) {
+            f[j] += __shfl_xor_sync(0xffffffffu, f[j], o); gx[j] += __shfl_xor_sync(0xffffffffu, gx[j], o);
+            gy[j] += __shfl_xor_sync(0xffffffffu, gy[j], o); gz[j] += __shfl_xor_sync(0xffffffffu, gz[j], o);
+        }
+    if (grp == 0) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const int k = tl + tp * j;
+            if (k >= tn) continue;
+            const int o = perm[t0 + k];
+            if constexpr (FUSED) {
+                // the far field scaled as k_l2p_leaf2 scales it, plus the near
+                // field in FP64 as the two-step form adds it
+                const float4 F = sF[k];
+                pot[o] = __dsub_rn((double)(-F.x * inv_hf), (double)f[j]);
+                ax[o] = __dadd_rn((double)(F.y * inv_hf * inv_hf), (double)gx[j]);
+                ay[o] = __dadd_rn((double)(F.z * inv_hf * inv_hf), (double)gy[j]);
+                az[o] = __dadd_rn((double)(F.w * inv_hf * inv_hf), (double)gz[j]);
+            } else {
+                pot[o] -= (double)f[j]; ax[o] += (double)gx[j]; ay[o] += (double)gy[j]; az[o] += (double)gz[j];
+            }
+        }
+    }
+}
+
+// the block schedule for tn targets: 2 per lane on 4 lanes up to 8 targets,
+// on 8 lanes up to 16; 3 and 4 per lane on 8 lanes up to 24 and 32
+template <bool FUSED>
+__device__ __forceinline__ void p2p32_block_any(int t0, int tn, int lane, float4* sP, const float4* sF, int total,
+                                                int incl, int excl, int sbS, float ox, float oy, float oz, int nself,
+                                                const float4* pos, const int* perm, float inv_hf, double* pot,
+                                                double* ax, double* ay, double* az) {
+    if (tn <= 8)
+        p2p32_block<2, FUSED>(t0, tn, 4, lane, sP, sF, total, incl, excl, sbS, ox, oy, oz, nself, pos, perm, inv_hf,
+                              pot, ax, ay, az);
+    else if (tn <= 16)
+        p2p32_block<2, FUSED>(t0, tn, 8, lane, sP, sF, total, incl, excl, sbS, ox, oy, oz, nself, pos, perm, inv_hf,
+                              pot, ax, ay, az);
+    else if (tn <= 24)
+        p2p32_block<3, FUSED>(t0, tn, 8, lane, sP, sF, total, incl, excl, sbS, ox, oy, oz, nself, pos, perm, inv_hf,
+                              pot, ax, ay, az);
+    else
+        p2p32_block<4, FUSED>(t0, tn, 8, lane, sP, sF, total, incl, excl, sbS, ox, oy, oz, nself, pos, perm, inv_hf,
+                              pot, ax, ay, az);
+}
+
+// sources of the 27 neighbour leaves of leaf c, one leaf per lane (lane 0:
+// the leaf itself, so its particles come first): start, count and the
+// offset of the leaf's centre; incl/excl: the warp's prefix sums of the counts
+__device__ __forceinline__ void p2p32_neighbours(int depth, int64_t c, int lane, const int* __restrict__ start,
+                                                 int& sbS, int& cntS, float& ox, float& oy, float& oz, int& incl,
+                                                 int& excl, int& total, int& nself) {
+    const int side = 1 << depth;
+    const float h = 1.0f / (float)side;
+    int ix, iy, iz;
+    cell_coords(depth, c, ix, iy, iz);
+    cntS = 0; sbS = 0; ox = oy = oz = 0.f;
+    if (lane < 27) {
+        const int d = lane == 0 ? 13 : lane <= 13 ? lane - 1 : lane;
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+        if (jx >= 0 && jy >= 0 && jz >= 0 && jx < side && jy < side && jz < side) {
+            const int64_t S = cell_index(depth, jx, jy, jz);
+            sbS = start[S];
+            cntS = start[S + 1] - sbS;
+            ox = dx * h; oy = dy * h; oz = dz * h;
+        }
+    }
+    incl = cntS;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    excl = incl - cntS;
+    nself = __shfl_sync(0xffffffffu, cntS, 0);
+}
+
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* __restrict__ pos,
@@ -593,105 +735,20 @@ k_p2p32(int depth, int64_t nleaf, const int* __restrict__ start, const float4* _
     if (c >= nleaf) return;
     const int b = start[c], e = start[c + 1];
     if (b == e) return;
-    const int side = 1 << depth;
-    const float h = 1.0f / (float)side;
-    int ix, iy, iz;
-    cell_coords(depth, c, ix, iy, iz);
-    for (int t0 = b; t0 < e; t0 += 64) {
-        const int tn = min(64, e - t0), half = (tn + 1) >> 1;
-        int tp = 1;
-        while (tp < half) tp <<= 1;
-        const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
-        const int ta = t0 + tl, tb = t0 + tl + tp;
-        const bool va = tl < tn, vb = tl + tp < tn;
-        const float4 pa = va ? pos[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 pb = vb ? pos[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float fa = 0.f, xa = 0.f, ya = 0.f, za = 0.f, fb = 0.f, xb = 0.f, yb = 0.f, zb = 0.f;
-        // the 27 neighbour leaves, one per lane: start, count, centre offset
-        int cntS = 0, sbS = 0;
-        float ox = 0.f, oy = 0.f, oz = 0.f;
-        if (lane < 27) {
-            // lane 0: the target leaf (neighbour 13); lanes 1..26: the others in order
-            const int d = lane == 0 ? 13 : lane <= 13 ? lane - 1 : lane;
-            const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-            const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
-            if (jx >= 0 && jy >= 0 && jz >= 0 && jx < side && jy < side && jz < side) {
-                const int64_t S = cell_index(depth, jx, jy, jz);
-                sbS = start[S];
-                cntS = start[S + 1] - sbS;
-                ox = dx * h; oy = dy * h; oz = dz * h;
-            }
-        }
-        int incl = cntS;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
-        const int nself = __shfl_sync(0xffffffffu, cntS, 0);   // sources of the target leaf: [0, nself)
-        // full 32-wide chunks of the concatenated neighbour sources
-        for (int c0 = 0; c0 < total; c0 += 32) {
-            {
-                const int g = min(c0 + lane, total - 1);
-                int i = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int v = __shfl_sync(0xffffffffu, incl, i + step - 1);
-                    if (v <= g) i += step;
-                }
-                const int sbi = __shfl_sync(0xffffffffu, sbS, i), exi = __shfl_sync(0xffffffffu, excl, i);
-                const float oxi = __shfl_sync(0xffffffffu, ox, i), oyi = __shfl_sync(0xffffffffu, oy, i),
-                            ozi = __shfl_sync(0xffffffffu, oz, i);
-                __syncwarp();
-                if (c0 + lane < total) {
-                    const float4 v = pos[sbi + (g - exi)];
-                    sP[w][lane] = make_float4(v.x + oxi, v.y + oyi, v.z + ozi, v.w);
-                }
-                __syncwarp();
-            }
-            {
-                const int cnt = min(32, total - c0);
-                if (c0 < nself) {
-                    for (int k = grp; k < cnt; k += G) {
-                        const float4 sv = sP[w][k];
-                        p2p32_pair_guarded(sv, pa, fa, xa, ya, za);
-                        p2p32_pair_guarded(sv, pb, fb, xb, yb, zb);
-                    }
-                } else {
-#pragma unroll 2
-                    for (int k = grp; k < cnt; k += G) {
-                        const float4 sv = sP[w][k];
-                        p2p32_pair(sv, pa, fa, xa, ya, za);
-                        p2p32_pair(sv, pb, fb, xb, yb, zb);
-                    }
-                }
-            }
-        }
-        for (int o = tp; o < 32; o <<= 1) {
-            fa += __shfl_xor_sync(0xffffffffu, fa, o); xa += __shfl_xor_sync(0xffffffffu, xa, o);
-            ya += __shfl_xor_sync(0xffffffffu, ya, o); za += __shfl_xor_sync(0xffffffffu, za, o);
-            fb += __shfl_xor_sync(0xffffffffu, fb, o); xb += __shfl_xor_sync(0xffffffffu, xb, o);
-            yb += __shfl_xor_sync(0xffffffffu, yb, o); zb += __shfl_xor_sync(0xffffffffu, zb, o);
-        }
-        if (grp == 0) {
-            if (va) {
-                const int o = perm[ta];
-                pot[o] -= (double)fa; ax[o] += (double)xa; ay[o] += (double)ya; az[o] += (double)za;
-            }
-            if (vb) {
-                const int o = perm[tb];
-                pot[o] -= (double)fb; ax[o] += (double)xb; ay[o] += (double)yb; az[o] += (double)zb;
-            }
-        }
-    }
+    int sbS, cntS, incl, excl, total, nself;
+    float ox, oy, oz;
+    p2p32_neighbours(depth, c, lane, start, sbS, cntS, ox, oy, oz, incl, excl, total, nself);
+    for (int t0 = b; t0 < e; t0 += 32)
+        p2p32_block_any<false>(t0, min(32, e - t0), lane, sP[w], nullptr, total, incl, excl, sbS, ox, oy, oz, nself,
+                               pos, perm, 0.f, pot, ax, ay, az);
 }
 
 // ---------------------------------------------------------------------------
 // Far and near field in one pass (FP32 form, uniform octree): one warp per
 // target leaf evaluates the leaf's local expansion at its particles (the
 // arithmetic of k_l2p_leaf2, one target per lane), then the near field of
-// k_p2p32, and writes each particle's potential and acceleration once, in
+// k_p2p32 (the same block schedule, p2p32_block), and writes each particle's
+// potential and acceleration once, in
 // the operation order of k_l2p_leaf2 followed by k_p2p32 (explicitly
 // rounded, so the result is that sequence's), without the separate write
 // and read-modify-write of the caller-order outputs.
@@ -714,8 +771,10 @@ __device__ __noinline__ float4 l2p_point32(const float* Ln, float rx, float ry, 
     return make_float4(ph, gx, gy, gz);
 }
 
+// at most 64 registers (8 blocks of 4 warps per SM): with more, the 3- and
+// 4-target blocks cost the pass more in occupancy than they save
 template <int P, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
 k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const float4* __restrict__ pos,
             const int* __restrict__ perm, const double* __restrict__ Lt, const float* __restrict__ expand,
             DevOffsets off, double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay,
@@ -724,7 +783,7 @@ k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
     constexpr int NN = nested_col_off<P, float>(P + 1, 0);
     __shared__ float sA[WARPS][NS];
     __shared__ __align__(16) float sN[WARPS][NN];
-    __shared__ float4 sF[WARPS][64];   // far field of a block of targets (potential, gradient; scaled units)
+    __shared__ float4 sF[WARPS][32];   // far field of a block of targets (potential, gradient; scaled units)
     __shared__ float4 sP[WARPS][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * WARPS + w;
@@ -753,112 +812,19 @@ k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
     __syncwarp();
     const float inv_hf = (float)(1 << depth);   // exact
     const float* Ln = sN[w];
-    const int side = 1 << depth;
-    const float h = 1.0f / (float)side;
-    int ix, iy, iz;
-    cell_coords(depth, c, ix, iy, iz);
-    // the 27 neighbour leaves, one per lane (lane 0: the target leaf)
-    int cntS = 0, sbS = 0;
-    float ox = 0.f, oy = 0.f, oz = 0.f;
-    if (lane < 27) {
-        const int d = lane == 0 ? 13 : lane <= 13 ? lane - 1 : lane;
-        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-        const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
-        if (jx >= 0 && jy >= 0 && jz >= 0 && jx < side && jy < side && jz < side) {
-            const int64_t S = cell_index(depth, jx, jy, jz);
-            sbS = start[S];
-            cntS = start[S + 1] - sbS;
-            ox = dx * h; oy = dy * h; oz = dz * h;
-        }
-    }
-    int incl = cntS;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - cntS;
-    const int nself = __shfl_sync(0xffffffffu, cntS, 0);
-    for (int t0 = b; t0 < e; t0 += 64) {
-        const int tn = min(64, e - t0), half = (tn + 1) >> 1;
+    int sbS, cntS, incl, excl, total, nself;
+    float ox, oy, oz;
+    p2p32_neighbours(depth, c, lane, start, sbS, cntS, ox, oy, oz, incl, excl, total, nself);
+    for (int t0 = b; t0 < e; t0 += 32) {
+        const int tn = min(32, e - t0);
         // far field of the block's targets, one per lane
-#pragma unroll 1
-        for (int k = lane; k < tn; k += 32) {
-            const float4 v = pos[t0 + k];
-            sF[w][k] = l2p_point32<P>(Ln, v.x * inv_hf, v.y * inv_hf, v.z * inv_hf);
+        if (lane < tn) {
+            const float4 v = pos[t0 + lane];
+            sF[w][lane] = l2p_point32<P>(Ln, v.x * inv_hf, v.y * inv_hf, v.z * inv_hf);
         }
         __syncwarp();
-        int tp = 1;
-        while (tp < half) tp <<= 1;
-        const int G = 32 / tp, grp = lane / tp, tl = lane % tp;
-        const int ta = t0 + tl, tb = t0 + tl + tp;
-        const bool va = tl < tn, vb = tl + tp < tn;
-        const float4 pa = va ? pos[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 pb = vb ? pos[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float fa = 0.f, xa = 0.f, ya = 0.f, za = 0.f, fb = 0.f, xb = 0.f, yb = 0.f, zb = 0.f;
-        for (int c0 = 0; c0 < total; c0 += 32) {
-            {
-                const int g = min(c0 + lane, total - 1);
-                int i = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int v = __shfl_sync(0xffffffffu, incl, i + step - 1);
-                    if (v <= g) i += step;
-                }
-                const int sbi = __shfl_sync(0xffffffffu, sbS, i), exi = __shfl_sync(0xffffffffu, excl, i);
-                const float oxi = __shfl_sync(0xffffffffu, ox, i), oyi = __shfl_sync(0xffffffffu, oy, i),
-                            ozi = __shfl_sync(0xffffffffu, oz, i);
-                __syncwarp();
-                if (c0 + lane < total) {
-                    const float4 v = pos[sbi + (g - exi)];
-                    sP[w][lane] = make_float4(v.x + oxi, v.y + oyi, v.z + ozi, v.w);
-                }
-                __syncwarp();
-            }
-            {
-                const int cnt = min(32, total - c0);
-                if (c0 < nself) {
-                    for (int k = grp; k < cnt; k += G) {
-                        const float4 sv = sP[w][k];
-                        p2p32_pair_guarded(sv, pa, fa, xa, ya, za);
-                        p2p32_pair_guarded(sv, pb, fb, xb, yb, zb);
-                    }
-                } else {
-#pragma unroll 2
-                    for (int k = grp; k < cnt; k += G) {
-                        const float4 sv = sP[w][k];
-                        p2p32_pair(sv, pa, fa, xa, ya, za);
-                        p2p32_pair(sv, pb, fb, xb, yb, zb);
-                    }
-                }
-            }
-        }
-        for (int o = tp; o < 32; o <<= 1) {
-            fa += __shfl_xor_sync(0xffffffffu, fa, o); xa += __shfl_xor_sync(0xffffffffu, xa, o);
-            ya += __shfl_xor_sync(0xffffffffu, ya, o); za += __shfl_xor_sync(0xffffffffu, za, o);
-            fb += __shfl_xor_sync(0xffffffffu, fb, o); xb += __shfl_xor_sync(0xffffffffu, xb, o);
-            yb += __shfl_xor_sync(0xffffffffu, yb, o); zb += __shfl_xor_sync(0xffffffffu, zb, o);
-        }
-        if (grp == 0) {
-            // the far field scaled as k_l2p_leaf2 scales it (exact powers of two
-            // in FP32), plus the near field in FP64 as k_p2p32 adds it
-            if (va) {
-                const int o = perm[ta];
-                const float4 F = sF[w][tl];
-                pot[o] = __dsub_rn((double)(-F.x * inv_hf), (double)fa);
-                ax[o] = __dadd_rn((double)(F.y * inv_hf * inv_hf), (double)xa);
-                ay[o] = __dadd_rn((double)(F.z * inv_hf * inv_hf), (double)ya);
-                az[o] = __dadd_rn((double)(F.w * inv_hf * inv_hf), (double)za);
-            }
-            if (vb) {
-                const int o = perm[tb];
-                const float4 F = sF[w][tl + tp];
-                pot[o] = __dsub_rn((double)(-F.x * inv_hf), (double)fb);
-                ax[o] = __dadd_rn((double)(F.y * inv_hf * inv_hf), (double)xb);
-                ay[o] = __dadd_rn((double)(F.z * inv_hf * inv_hf), (double)yb);
-                az[o] = __dadd_rn((double)(F.w * inv_hf * inv_hf), (double)zb);
-            }
-        }
+        p2p32_block_any<true>(t0, tn, lane, sP[w], sF[w], total, incl, excl, sbS, ox, oy, oz, nself, pos, perm,
+                              inv_hf, pot, ax, ay, az);
         __syncwarp();
     }
 }
