@@ -53,6 +53,9 @@ struct fmm_plan {
     int64_t part64_cap = 0;
     float* M32 = nullptr;    // FP32 copy of the multipoles (FMM_FP32)
     float* msym32 = nullptr; // FP32 traceless forms: the leaves' symmetric moments, leaf-major (P2M)
+    float* L32 = nullptr;    // uniform FP32 and tensor-core forms with FP32 shifts: the local expansions in FP32
+    float* lpart = nullptr;  // their split small levels' M2L partial sums (FP32)
+    int64_t lpart_cap = 0;
     int kst = 0;
     // tensor-core forms (FMM_GEMM_BF16X3, FMM_GEMM_TF32X3)
     void* Kbf = nullptr;                 // 343 x {hi, lo} preformatted matrices (streamed-matrix kernel)
@@ -95,6 +98,13 @@ static bool is_tc(int prec) { return prec == FMM_GEMM_BF16X3 || prec == FMM_GEMM
 // keep M32 (the FP32 copy of the multipoles) current at every level, so the
 // M2M and M2L kernels read it instead of converting the FP64 expansions again.
 static bool m32_current(const fmm_plan* pl) { return !pl->ad && pl->M32 && pl->W32 && pl->part32; }
+
+// Uniform FP32 and tensor-core plans with the FP32 level shifts keep their
+// local expansions in FP32 only (L32): M2L writes them, L2L updates them and
+// L2P reads them without a conversion to or from FP64 (an FP64 operation
+// holds this part's narrow FP64 pipe for 16 cycles per warp).  L32 is
+// allocated exactly when these conditions hold.
+static float* L32lev(fmm_plan* pl, int l) { return pl->L32 ? pl->L32 + pl->lvl_off[l] : nullptr; }
 
 // storage basis of the multipoles and of the local expansions (the TG
 // basis: symmetric multipoles, traceless locals; Sec. 3)
@@ -170,12 +180,12 @@ static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
     const float* m32 = m32_current(pl) ? pl->M32 + pl->lvl_off[l] : nullptr;
     const int rc = tc_m2l_level(p, tf, pl->tc_kern, pl->tc_cw, pl->tc_niss, l, pl->Mbuf + pl->lvl_off[l], hp, lp,
                                 tc_maps_at(pl, l), pl->tc_kern == 1 ? pl->Kgen : pl->Kbf, pl->Lbuf + pl->lvl_off[l],
-                                pl->derr, s, m32);
+                                pl->derr, s, m32, L32lev(pl, l));
     // kernel 3: the multipole columns >= 48 (a cell-major FP32 copy of
     // them, then their products) on the CUDA cores, added to L
     if (rc == 0 && pl->tc_kern == 3 && rest_rows(p) > 0 &&
         (launch_rest_pack(p, l, pl->Mbuf + pl->lvl_off[l], pl->Mrest, s, m32) != 0 ||
-         launch_m2l_rest(p, l, pl->Mrest, pl->Krest, pl->Lbuf + pl->lvl_off[l], s) != 0))
+         launch_m2l_rest(p, l, pl->Mrest, pl->Krest, pl->Lbuf + pl->lvl_off[l], s, L32lev(pl, l)) != 0))
         return -2;
     return rc;
 }
@@ -481,8 +491,11 @@ static void free_tree(fmm_plan* pl) {
     cudaFree(pl->xs); cudaFree(pl->ys); cudaFree(pl->zs); cudaFree(pl->qs);
     cudaFree(pl->perm); cudaFree(pl->start); cudaFree(pl->scratch);
     cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32); cudaFree(pl->Mbf); cudaFree(pl->pos32);
-    cudaFree(pl->dip); cudaFree(pl->msym32);
+    cudaFree(pl->dip); cudaFree(pl->msym32); cudaFree(pl->L32); cudaFree(pl->lpart);
     pl->msym32 = nullptr;
+    pl->L32 = nullptr;
+    pl->lpart = nullptr;
+    pl->lpart_cap = 0;
     pl->dip = nullptr;
     pl->pos32 = nullptr;
     pl->M32 = nullptr;
@@ -785,7 +798,20 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess) ||
             (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->pos32, nn * 16) != cudaSuccess) ||
             (pl->cfg.prec != FMM_FP64 && bM(pl) == FMM_BASIS_TRACELESS &&
-             cudaMalloc(&pl->msym32, (size_t)pl->nleaf * ((ns_of(pl->cfg.p) + 3) / 4 * 4) * 4) != cudaSuccess)) {
+             cudaMalloc(&pl->msym32, (size_t)pl->nleaf * ((ns_of(pl->cfg.p) + 3) / 4 * 4) * 4) != cudaSuccess) ||
+            (pl->cfg.prec != FMM_FP64 && pl->V32 && cudaMalloc(&pl->L32, tot * 4) != cudaSuccess)) {
+            cudaGetLastError();
+            free_tree(pl);
+            FAIL(FMM_ERR_OOM, "allocating tree storage for n=%lld failed", (long long)n);
+        }
+        if (pl->L32) {
+            pl->lpart_cap = 0;
+            for (int l = 2; l <= pl->depth; ++l) {
+                const int64_t e = m2l_grpf_part_elems(pl->cfg.p, pl->cfg.basis, l);
+                if (e > pl->lpart_cap) pl->lpart_cap = e;
+            }
+        }
+        if (pl->lpart_cap > 0 && cudaMalloc(&pl->lpart, (size_t)pl->lpart_cap * 4) != cudaSuccess) {
             cudaGetLastError();
             free_tree(pl);
             FAIL(FMM_ERR_OOM, "allocating tree storage for n=%lld failed", (long long)n);
@@ -905,8 +931,11 @@ static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
             const int64_t b = pl->lvl_off[lo], e = pl->lvl_off[lt] + ((int64_t)pl->nc << (3 * lt));
             if (!m32_current(pl)) launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
             for (int l = lo; l <= lt; ++l) {
-                const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
-                                                 pl->K32, (int64_t)1 << (3 * l), S(stream));
+                const int parts =
+                    pl->L32 ? launch_m2l_grpf(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], L32lev(pl, l),
+                                              pl->K32, (int64_t)1 << (3 * l), S(stream), pl->lpart, pl->lpart_cap)
+                            : launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
+                                             pl->K32, (int64_t)1 << (3 * l), S(stream));
                 for (int k = 0; k < parts; ++k) count_launch();
             }
         }
@@ -924,8 +953,11 @@ static int m2l_uniform(fmm_plan* pl, int lo, int hi, void* stream) {
         const int64_t b = pl->lvl_off[lo], e = pl->lvl_off[hi] + ((int64_t)pl->nc << (3 * hi));
         if (!m32_current(pl)) launch_to_f32(e - b, pl->Mbuf + b, pl->M32 + b, S(stream));
         for (int l = lo; l <= hi; ++l) {
-            const int parts = launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
-                                             pl->K32, (int64_t)1 << (3 * l), S(stream));
+            const int parts =
+                pl->L32 ? launch_m2l_grpf(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], L32lev(pl, l),
+                                          pl->K32, (int64_t)1 << (3 * l), S(stream), pl->lpart, pl->lpart_cap)
+                        : launch_m2l_grp(pl->cfg.p, pl->cfg.basis, l, pl->M32 + pl->lvl_off[l], Llev(pl, l),
+                                         pl->K32, (int64_t)1 << (3 * l), S(stream));
             for (int k = 0; k < parts; ++k) count_launch();
         }
         CKLAUNCH();
@@ -952,8 +984,12 @@ int fmm_l2l(fmm_plan* pl, void* stream) {
     if (pl->ad) { ad_run_l2l(pl->ad, pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, pl->cfg.basis, g_tab[pl->dev], S(stream)); CKLAUNCH(); return FMM_OK; }
     if (pl->V32) {
         for (int l = 2; l < pl->depth; ++l) {
-            const int nl = launch_shift32(pl->cfg.p, pl->cfg.basis, 0, l, pl->V32, Llev(pl, l), (int64_t)1 << (3 * l),
-                                          Llev(pl, l + 1), (int64_t)1 << (3 * (l + 1)), S(stream));
+            const int nl = pl->L32 ? launch_l2l32f(pl->cfg.p, pl->cfg.basis, l, pl->V32, L32lev(pl, l),
+                                                   (int64_t)1 << (3 * l), L32lev(pl, l + 1),
+                                                   (int64_t)1 << (3 * (l + 1)), S(stream))
+                                   : launch_shift32(pl->cfg.p, pl->cfg.basis, 0, l, pl->V32, Llev(pl, l),
+                                                    (int64_t)1 << (3 * l), Llev(pl, l + 1),
+                                                    (int64_t)1 << (3 * (l + 1)), S(stream));
             for (int k = 0; k < nl; ++k) count_launch();
         }
         CKLAUNCH();
@@ -978,7 +1014,7 @@ int fmm_l2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, void*
     if (pl->depth >= 2)
         launch_l2p_leaf2(pl->cfg.prec == FMM_FP64 ? 0 : 1, pl->cfg.p, bL(pl), pl->depth, pl->nleaf,
                          pl->start, pl->xs, pl->ys, pl->zs, pl->perm, Llev(pl, pl->depth), g_tab[pl->dev], pot, ax,
-                         ay, az, S(stream), pl->pos32);
+                         ay, az, S(stream), pl->pos32, L32lev(pl, pl->depth));
     else
         launch_zero4(pl->n, pot, ax, ay, az, S(stream));
     CKLAUNCH();
@@ -1009,7 +1045,7 @@ int fmm_l2p_p2p(fmm_plan* pl, double* pot, double* ax, double* ay, double* az, v
     if (!pl->ad && pl->pos32 && pl->depth >= 2) {
         // the FP32 uniform form: far and near field in one kernel
         launch_l2p_p2p32(pl->cfg.p, bL(pl), pl->depth, pl->nleaf, pl->start, pl->pos32, pl->perm, Llev(pl, pl->depth),
-                         g_tab[pl->dev], pot, ax, ay, az, S(stream));
+                         g_tab[pl->dev], pot, ax, ay, az, S(stream), L32lev(pl, pl->depth));
         CKLAUNCH();
         return FMM_OK;
     }

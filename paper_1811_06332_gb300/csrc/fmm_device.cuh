@@ -9,6 +9,7 @@ namespace fmm {
 
 // Lt[i] = sum over g < groups of part[g m + i], in group order (fmm_m2l32.cu)
 int launch_sum_parts(const double* part, double* Lt, int64_t m, int groups, cudaStream_t s);
+int launch_sum_parts(const float* part, float* Lt, int64_t m, int groups, cudaStream_t s);
 // Mpa(r, P) = sum over c = 0..7 of part[(c nc + r) npa + P], also to the FP32
 // copy Mpa32 (fmm_m2l32.cu)
 int launch_m2m32_sum(int nc, int64_t npa, const float* part, double* Mpa, float* Mpa32, cudaStream_t s);

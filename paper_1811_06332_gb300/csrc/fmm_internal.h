@@ -110,7 +110,8 @@ int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const 
 int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                      const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
                      double* pot, double* ax, double* ay, double* az, cudaStream_t s,
-                     const float4* pos32 = nullptr);
+                     const float4* pos32 = nullptr,
+                     const float* Lt32 = nullptr);
 int launch_p2p_leaf2(int prec, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
                      const double* zs, const double* qs, const int* perm, double* pot, double* ax, double* ay,
                      double* az, cudaStream_t s);
@@ -122,6 +123,10 @@ int grouped_entries(int p, int basis, unsigned char* out, int cap);
 int launch_to_f32(int64_t n, const double* a, float* b, cudaStream_t s);
 int launch_m2l_grp(int p, int basis, int l, const float* M, double* Lt, const float* K, int64_t ncell,
                    cudaStream_t s);
+// the same with FP32 locals (uniform FP32 and tensor-core plans)
+int launch_m2l_grpf(int p, int basis, int l, const float* M, float* Lt, const float* K, int64_t ncell,
+                    cudaStream_t s, float* part, int64_t part_cap);
+int64_t m2l_grpf_part_elems(int p, int basis, int l);   // floats of part for level l (0: unsplit)
 // FP64 form of the grouped M2L (packed FP64 matrices)
 int launch_build_ktab64(int p, int basis, int kst, const unsigned char* ent, const double* Dtab, double* K,
                         cudaStream_t s);
@@ -144,9 +149,12 @@ int launch_shift32(int p, int basis, int m2m, int l, const float* A, const doubl
                    int64_t ny, cudaStream_t s, float* part = nullptr, const float* X32 = nullptr,
                    float* Y32 = nullptr);
 int shift32_supported(int p, int basis);
+// L2L on FP32 locals (generated l2l32f); the launches made, -1 without a kernel
+int launch_l2l32f(int p, int basis, int l, const float* V, const float* X, int64_t nx, float* Y, int64_t ny,
+                  cudaStream_t s);
 int launch_l2p_p2p32(int p, int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
                      const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,
-                     cudaStream_t s);
+                     cudaStream_t s, const float* Lt32 = nullptr);
 int launch_p2p32(int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm, double* pot,
                  double* ax, double* ay, double* az, cudaStream_t s);
 
@@ -168,7 +176,7 @@ int tct_ty(int l);
 void tct_box(int l, unsigned (&box)[5]);
 int tct_build(int p, const double* Dtab, void* B, cudaStream_t s);
 int tct_m2l_level(int p, int l, int first_part_only, const void* maps, const void* B, double* Lt, int* err,
-                  cudaStream_t s);
+                  cudaStream_t s, float* Lt32 = nullptr);
 // tables of the multipole columns >= 48 that kernel shape 3 contracts on the
 // CUDA cores (fmm_m2l_rest.cu): rows of rank <= p - 6
 int rest_rows(int p);
@@ -177,7 +185,8 @@ int rest_cstride(int p);   // floats per cell of the multipole copy
 int build_krest(int p, const double* Dtab, float* Krest, cudaStream_t s);
 int launch_rest_pack(int p, int l, const double* M, float* Mrest, cudaStream_t s, const float* M32 = nullptr);
 // Lt (level l, after the tensor-core kernel) += those products
-int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s);
+int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s,
+                    float* Lt32 = nullptr);
 size_t tc_maps_bytes();
 // kern 0: per-offset matrices streamed from global memory (tc_build_mat at
 // chunk width cw; niss follows from the layout); kern 1 (BF16 only): the
@@ -186,13 +195,13 @@ int tc_build_mat(int p, int tf, int cw, const double* Dtab, void* B, cudaStream_
 int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps);
 int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double* M, void* hi, void* lo,
                  const void* maps, const void* B, double* Lt, int* err, cudaStream_t s,
-                 const float* M32 = nullptr);
+                 const float* M32 = nullptr, float* Lt32 = nullptr);
 // fmm_m2l_tcgen.cu (BF16 hi/lo form, offset matrices built on chip)
 int tg_supported(int p);
 size_t tg_b_bytes();
 int tg_build(int p, int cw, int niss, const double* Dtab, void* B, cudaStream_t s);
 int tg_m2l_level(int p, int cw, int niss, int l, const void* maps, const void* B, double* Lt, int* err,
-                 cudaStream_t s);
+                 cudaStream_t s, float* Lt32 = nullptr);
 int tg_layout_host(int p, int cw, int niss, int* out, int nout, uint32_t* groups, int gcap);
 int tg_default_cw();
 int tg_default_niss();

@@ -257,7 +257,7 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
             const double* __restrict__ ys, const double* __restrict__ zs, const int* __restrict__ perm,
             const double* __restrict__ Lt, const T* __restrict__ expand, DevOffsets off,
             double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay, double* __restrict__ az,
-            const float4* __restrict__ pos32) {
+            const float4* __restrict__ pos32, const float* __restrict__ Lt32) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
     constexpr int NN = nested_col_off<P, T>(P + 1, 0);   // nested layout size (a multiple of 16 bytes)
     __shared__ T sA[WARPS][2][NS];
@@ -270,7 +270,7 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
     if (basis) {
         constexpr int NT = (P + 1) * (P + 1);
         for (int t = hl; t < NT; t += 16)
-            if (valid) sA[w][h][t] = T(Lt[(int64_t)t * nleaf + c]);
+            if (valid) sA[w][h][t] = Lt32 ? T(Lt32[(int64_t)t * nleaf + c]) : T(Lt[(int64_t)t * nleaf + c]);
         __syncwarp();
         for (int s = hl; s < NS; s += 16) {
             if (!valid) continue;
@@ -286,7 +286,7 @@ k_l2p_leaf2(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
         for (int s = hl; s < NS; s += 16)
             if (valid)
                 sN[w][h][nested_col_off<P, T>(c_sym_idx[s][0], c_sym_idx[s][1]) + c_sym_idx[s][2]] =
-                    T(Lt[(int64_t)s * nleaf + c]);
+                    Lt32 ? T(Lt32[(int64_t)s * nleaf + c]) : T(Lt[(int64_t)s * nleaf + c]);
     }
     __syncwarp();
     if (!valid || b == e) return;
@@ -504,11 +504,11 @@ static void p2m_leaf_p(int basis, int depth, int64_t nleaf, const int* start, co
 template <int P, typename T>
 static void l2p_leaf_p(int basis, int depth, int64_t nleaf, const int* start, const double* xs, const double* ys,
                        const double* zs, const int* perm, const double* Lt, const DevTables& Tb, double* pot,
-                       double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32) {
+                       double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32, const float* Lt32) {
     constexpr int W = 4;
     k_l2p_leaf2<P, T, W><<<(unsigned)((nleaf + 2 * W - 1) / (2 * W)), W * 32, 0, s>>>(
         basis, depth, nleaf, start, xs, ys, zs, perm, Lt, tab_of<T>(Tb.expand, Tb.expand32), Tb.offsets(), pot, ax,
-        ay, az, pos32);
+        ay, az, pos32, Lt32);
 }
 
 #define FMM_P_SWITCH(P_, CALL) \
@@ -532,10 +532,13 @@ int launch_p2m_leaf(int prec, int p, int basis, int depth, int64_t nleaf, const 
 
 int launch_l2p_leaf2(int prec, int p, int basis, int depth, int64_t nleaf, const int* start, const double* xs,
                      const double* ys, const double* zs, const int* perm, const double* Lt, const DevTables& Tb,
-                     double* pot, double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32) {
+                     double* pot, double* ax, double* ay, double* az, cudaStream_t s, const float4* pos32,
+                     const float* Lt32) {
     if (nleaf <= 0) return 0;
-#define C64(P) l2p_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s, nullptr)
-#define C32(P) l2p_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s, pos32)
+#define C64(P) l2p_leaf_p<P, double>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s, nullptr, \
+                                     nullptr)
+#define C32(P) l2p_leaf_p<P, float>(basis, depth, nleaf, start, xs, ys, zs, perm, Lt, Tb, pot, ax, ay, az, s, pos32, \
+                                    Lt32)
     if (prec == 0) { FMM_P_SWITCH(p, C64) } else { FMM_P_SWITCH(p, C32) }
 #undef C64
 #undef C32
@@ -773,10 +776,10 @@ __device__ __noinline__ float4 l2p_point32(const float* Ln, float rx, float ry, 
 
 // at most 64 registers (8 blocks of 4 warps per SM): with more, the 3- and
 // 4-target blocks cost the pass more in occupancy than they save
-template <int P, int WARPS>
+template <int P, int WARPS, typename LT>   // LT: the type of the stored locals
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
 k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, const float4* __restrict__ pos,
-            const int* __restrict__ perm, const double* __restrict__ Lt, const float* __restrict__ expand,
+            const int* __restrict__ perm, const LT* __restrict__ Lt, const float* __restrict__ expand,
             DevOffsets off, double* __restrict__ pot, double* __restrict__ ax, double* __restrict__ ay,
             double* __restrict__ az) {
     constexpr int NS = (P + 1) * (P + 2) * (P + 3) / 6;
@@ -832,17 +835,22 @@ k_l2p_p2p32(int basis, int depth, int64_t nleaf, const int* __restrict__ start, 
 template <int P>
 static void l2p_p2p32_p(int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
                         const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,
-                        cudaStream_t s) {
+                        cudaStream_t s, const float* Lt32) {
     constexpr int W = 4;
-    k_l2p_p2p32<P, W><<<(unsigned)((nleaf + W - 1) / W), W * 32, 0, s>>>(basis, depth, nleaf, start, pos, perm, Lt,
-                                                                          Tb.expand32, Tb.offsets(), pot, ax, ay, az);
+    const unsigned g = (unsigned)((nleaf + W - 1) / W);
+    if (Lt32)
+        k_l2p_p2p32<P, W, float><<<g, W * 32, 0, s>>>(basis, depth, nleaf, start, pos, perm, Lt32, Tb.expand32,
+                                                       Tb.offsets(), pot, ax, ay, az);
+    else
+        k_l2p_p2p32<P, W, double><<<g, W * 32, 0, s>>>(basis, depth, nleaf, start, pos, perm, Lt, Tb.expand32,
+                                                        Tb.offsets(), pot, ax, ay, az);
 }
 
 int launch_l2p_p2p32(int p, int basis, int depth, int64_t nleaf, const int* start, const float4* pos, const int* perm,
                      const double* Lt, const DevTables& Tb, double* pot, double* ax, double* ay, double* az,
-                     cudaStream_t s) {
+                     cudaStream_t s, const float* Lt32) {
     if (nleaf <= 0) return 0;
-#define CF(P) l2p_p2p32_p<P>(basis, depth, nleaf, start, pos, perm, Lt, Tb, pot, ax, ay, az, s)
+#define CF(P) l2p_p2p32_p<P>(basis, depth, nleaf, start, pos, perm, Lt, Tb, pot, ax, ay, az, s, Lt32)
     FMM_P_SWITCH(p, CF)
 #undef CF
     count_launch();

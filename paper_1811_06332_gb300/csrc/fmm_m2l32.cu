@@ -141,4 +141,19 @@ int launch_sum_parts(const double* part, double* Lt, int64_t m, int groups, cuda
     return 0;
 }
 
+// The same for FP32 locals: the groups' FP32 partial sums added in group order.
+__global__ void k_sum_parts32(const float* __restrict__ part, float* __restrict__ Lt, int64_t m, int groups) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    float v = 0.f;
+    for (int g = 0; g < groups; ++g) v += part[(int64_t)g * m + i];
+    Lt[i] = v;
+}
+
+int launch_sum_parts(const float* part, float* Lt, int64_t m, int groups, cudaStream_t s) {
+    if (m <= 0) return 0;
+    k_sum_parts32<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(part, Lt, m, groups);
+    return 0;
+}
+
 }  // namespace fmm

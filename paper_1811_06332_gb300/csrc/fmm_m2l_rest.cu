@@ -35,7 +35,7 @@ namespace fmm {
 template <int P>
 __global__ void __launch_bounds__(64)
 k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ Krest, double* __restrict__ Lt,
-           int64_t ncell) {
+           int64_t ncell, float* __restrict__ Lt32) {
     constexpr int NR = rs_rows(P);
     constexpr int CS = rs_cstride(P);
     constexpr int KS = rs_kstride(P);
@@ -105,10 +105,15 @@ k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ K
     const int64_t tg = cls * h3 + ((int64_t)tk * hs + RS_TY * tj + y) * hs + RS_TX * ti + x;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        Lt[(int64_t)r * ncell + tg] +=
-            (double)(__uint_as_float((uint32_t)aa[r]) + __uint_as_float((uint32_t)(aa[r] >> 32)));
-        Lt[(int64_t)r * ncell + tg + 8 * hs] +=
-            (double)(__uint_as_float((uint32_t)ab[r]) + __uint_as_float((uint32_t)(ab[r] >> 32)));
+        const float va = __uint_as_float((uint32_t)aa[r]) + __uint_as_float((uint32_t)(aa[r] >> 32));
+        const float vb = __uint_as_float((uint32_t)ab[r]) + __uint_as_float((uint32_t)(ab[r] >> 32));
+        if (Lt32) {
+            Lt32[(int64_t)r * ncell + tg] += va;
+            Lt32[(int64_t)r * ncell + tg + 8 * hs] += vb;
+        } else {
+            Lt[(int64_t)r * ncell + tg] += (double)va;
+            Lt[(int64_t)r * ncell + tg + 8 * hs] += (double)vb;
+        }
     }
 }
 
@@ -162,14 +167,14 @@ int rest_cstride(int p) { return rest_rows(p) ? rs_cstride(p) : 0; }
 
 #define RS_P_SWITCH(p, F) (p == 6 ? F(6) : p == 7 ? F(7) : F(8))
 
-int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s) {
+int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s, float* Lt32) {
     const int hs = 1 << (l - 1);
     if (hs < RS_TY || rest_rows(p) == 0) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const unsigned g = (unsigned)(8 * (int64_t)(hs / RS_TX) * (hs / RS_TY) * hs);
     const float4* m4 = (const float4*)Mrest;
     const float4* k4 = (const float4*)Krest;
-#define RS_L(P) (k_m2l_rest<P><<<g, 64, 0, s>>>(l, m4, k4, Lt, ncell), 0)
+#define RS_L(P) (k_m2l_rest<P><<<g, 64, 0, s>>>(l, m4, k4, Lt, ncell, Lt32), 0)
     RS_P_SWITCH(p, RS_L);
 #undef RS_L
     count_launch();

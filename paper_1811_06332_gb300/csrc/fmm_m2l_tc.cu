@@ -77,7 +77,8 @@ constexpr int sl_threads() { return 32 * (5 + NISS); }
 template <int TF, int NISS>
 __global__ void __launch_bounds__(sl_threads<NISS>(), 1)
 k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int nrows,
-              const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
+              const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err,
+              float* __restrict__ Lt32) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* bring = smem + 4 * SL_BYTES;
@@ -278,7 +279,10 @@ k_m2l_tc_slab(const __grid_constant__ TcMaps maps, const TcChunks ch, int l, int
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
                     const int n = cb * 32 + e;
-                    if (n < nrows) Lt[(int64_t)n * ncell + tg] = acc[e];
+                    if (n < nrows) {
+                        if (Lt32) Lt32[(int64_t)n * ncell + tg] = (float)acc[e];
+                        else Lt[(int64_t)n * ncell + tg] = acc[e];
+                    }
                 }
             }
         }
@@ -580,7 +584,8 @@ int tc_encode_maps(int l, int tf, void* hi, void* lo, void* out_maps) {
 size_t tc_maps_bytes() { return sizeof(TcLevelMaps); }
 
 template <int TF, int NISS>
-static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const void* B, double* Lt, int64_t ncell,
+static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const void* B, double* Lt, float* Lt32,
+                     int64_t ncell,
                      int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
     const TcLevelMaps* m = (const TcLevelMaps*)maps;
@@ -590,14 +595,14 @@ static int tc_launch(const TcChunks& ch, int l, int nc, const void* maps, const 
         return -2;
     const int tpc = (hs / 8) * (hs / 16) * hs;
     k_m2l_tc_slab<TF, NISS><<<(unsigned)(8 * tpc), sl_threads<NISS>(), smem, s>>>(
-        m->slab, ch, l, nc, (const unsigned char*)B, Lt, ncell, err);
+        m->slab, ch, l, nc, (const unsigned char*)B, Lt, ncell, err, Lt32);
     count_launch();
     return 0;
 }
 
 int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double* M, void* hi, void* lo,
                  const void* maps, const void* B, double* Lt, int* err, cudaStream_t s,
-                 const float* M32) {
+                 const float* M32, float* Lt32) {
     const int hs = 1 << (l - 1);
     if (hs < 16) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
@@ -613,17 +618,17 @@ int tc_m2l_level(int p, int tf, int kern, int cw, int niss, int l, const double*
         k_tc_split_m<0><<<g, 256, 0, s>>>(l, nc, kern == 1, M, hi, lo, kern == 1 ? nullptr : M32);
     count_launch();
     if (kern == 1) {
-        const int rc = tg_m2l_level(p, cw, niss, l, maps, B, Lt, err, s);
+        const int rc = tg_m2l_level(p, cw, niss, l, maps, B, Lt, err, s, Lt32);
         if (rc != 0) return rc;
         return cudaGetLastError() == cudaSuccess ? 0 : -2;
     }
-    if (kern == 2 || kern == 3) return tct_m2l_level(p, l, kern == 3, maps, B, Lt, err, s);
+    if (kern == 2 || kern == 3) return tct_m2l_level(p, l, kern == 3, maps, B, Lt, err, s, Lt32);
     const TcChunks ch = tc_chunks(p, tf, cw);
     if (ch.niss != 2 && ch.niss != 4) return -1;
-    const int rc = tf ? (ch.niss == 4 ? tc_launch<1, 4>(ch, l, nc, maps, B, Lt, ncell, err, s)
-                                      : tc_launch<1, 2>(ch, l, nc, maps, B, Lt, ncell, err, s))
-                      : (ch.niss == 4 ? tc_launch<0, 4>(ch, l, nc, maps, B, Lt, ncell, err, s)
-                                      : tc_launch<0, 2>(ch, l, nc, maps, B, Lt, ncell, err, s));
+    const int rc = tf ? (ch.niss == 4 ? tc_launch<1, 4>(ch, l, nc, maps, B, Lt, Lt32, ncell, err, s)
+                                      : tc_launch<1, 2>(ch, l, nc, maps, B, Lt, Lt32, ncell, err, s))
+                      : (ch.niss == 4 ? tc_launch<0, 4>(ch, l, nc, maps, B, Lt, Lt32, ncell, err, s)
+                                      : tc_launch<0, 2>(ch, l, nc, maps, B, Lt, Lt32, ncell, err, s));
     if (rc != 0) return rc;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

@@ -63,7 +63,7 @@ template <int NISS>
 __global__ void __launch_bounds__(tg_threads<NISS>(), 1)
 k_m2l_tc_gen(const __grid_constant__ TcMaps maps, const TgLayout lay, int l, int nrows,
              const float* __restrict__ D32, const uint4* __restrict__ groups, double* __restrict__ Lt,
-             int64_t ncell, int* __restrict__ err) {
+             int64_t ncell, int* __restrict__ err, float* __restrict__ Lt32) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* bring = smem + 4 * SL_BYTES;
@@ -351,7 +351,10 @@ k_m2l_tc_gen(const __grid_constant__ TcMaps maps, const TgLayout lay, int l, int
                     if (write) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e)
-                            if (n0 + e < nrows) Lt[(int64_t)(n0 + e) * ncell + tg] = acc[e];
+                            if (n0 + e < nrows) {
+                                if (Lt32) Lt32[(int64_t)(n0 + e) * ncell + tg] = (float)acc[e];
+                                else Lt[(int64_t)(n0 + e) * ncell + tg] = acc[e];
+                            }
                     }
                 }
             }
@@ -493,7 +496,8 @@ int tg_build(int p, int cw, int niss, const double* Dtab, void* B, cudaStream_t 
 }
 
 template <int NISS>
-static int tg_launch(const TgLayout& L, int l, int nc, const void* maps, const void* B, double* Lt, int64_t ncell,
+static int tg_launch(const TgLayout& L, int l, int nc, const void* maps, const void* B, double* Lt, float* Lt32,
+                     int64_t ncell,
                      int* err, cudaStream_t s) {
     const int hs = 1 << (l - 1);
     const TcLevelMaps* m = (const TcLevelMaps*)maps;
@@ -503,7 +507,7 @@ static int tg_launch(const TgLayout& L, int l, int nc, const void* maps, const v
     const uint4* groups = (const uint4*)B;
     const float* D32 = (const float*)((const unsigned char*)B + (size_t)TG_GEN_THREADS * 16);
     k_m2l_tc_gen<NISS><<<(unsigned)(8 * tpc), tg_threads<NISS>(), L.smem, s>>>(m->slab, L, l, nc, D32, groups, Lt,
-                                                                               ncell, err);
+                                                                               ncell, err, Lt32);
     count_launch();
     return 0;
 }
@@ -512,15 +516,15 @@ static int tg_launch(const TgLayout& L, int l, int nc, const void* maps, const v
 // on-chip matrices; hi/lo BF16 operands of the level already split (scaled
 // by 1/m!) into the slab layout.
 int tg_m2l_level(int p, int cw, int niss, int l, const void* maps, const void* B, double* Lt, int* err,
-                 cudaStream_t s) {
+                 cudaStream_t s, float* Lt32) {
     const int hs = 1 << (l - 1);
     if (hs < 16 || !tg_supported(p)) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
     const TgLayout L = tg_layout(p, cw, niss);
     if (L.nb < 2) return -1;
     const int nc = ncoef_of(p, 1);
-    return niss == 2 ? tg_launch<2>(L, l, nc, maps, B, Lt, ncell, err, s)
-                     : tg_launch<1>(L, l, nc, maps, B, Lt, ncell, err, s);
+    return niss == 2 ? tg_launch<2>(L, l, nc, maps, B, Lt, Lt32, ncell, err, s)
+                     : tg_launch<1>(L, l, nc, maps, B, Lt, Lt32, ncell, err, s);
 }
 
 int tg_default_cw() { return tg_cw_default(); }

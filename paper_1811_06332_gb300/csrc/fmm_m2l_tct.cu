@@ -73,7 +73,8 @@ constexpr int TT_THREADS = 256;
 template <int TY>
 __global__ void __launch_bounds__(TT_THREADS, 1)
 k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int npt, int nrows,
-           const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err) {
+           const unsigned char* __restrict__ Kmat, double* __restrict__ Lt, int64_t ncell, int* __restrict__ err,
+           float* __restrict__ Lt32) {
     constexpr int N = 8 * TY;
     constexpr int SLB = tt_slab_bytes(TY);
     extern __shared__ unsigned char smem_raw[];
@@ -274,7 +275,10 @@ k_m2l_tc_t(const __grid_constant__ TcMaps maps, int l, int np, int npt, int nrow
                 const int col = cb * 32 + lane;
                 const int64_t cell = tbase + (int64_t)(col >> 3) * hs + (col & 7);
                 if (ok)
-                    for (int r = 0; r < rmax; ++r) Lt[(int64_t)(q * 32 + r) * ncell + cell] = (double)tile[r * 33 + lane];
+                    for (int r = 0; r < rmax; ++r) {
+                        if (Lt32) Lt32[(int64_t)(q * 32 + r) * ncell + cell] = tile[r * 33 + lane];
+                        else Lt[(int64_t)(q * 32 + r) * ncell + cell] = (double)tile[r * 33 + lane];
+                    }
                 __syncwarp();
             }
         }
@@ -339,14 +343,14 @@ void tct_box(int l, unsigned (&box)[5]) {
 
 template <int TY>
 static int tct_launch(int l, int np, int npt, int nc, const TcMaps& maps, const void* B, double* Lt, int64_t ncell,
-                      int* err, cudaStream_t s) {
+                      int* err, cudaStream_t s, float* Lt32) {
     const int hs = 1 << (l - 1);
     const int smem = tt_smem(TY);
     if (cudaFuncSetAttribute(k_m2l_tc_t<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -2;
     const int tpc = (hs / 8) * (hs / TY) * hs;
     k_m2l_tc_t<TY><<<(unsigned)(8 * tpc), TT_THREADS, smem, s>>>(maps, l, np, npt, nc, (const unsigned char*)B, Lt,
-                                                                 ncell, err);
+                                                                 ncell, err, Lt32);
     count_launch();
     return 0;
 }
@@ -356,7 +360,7 @@ static int tct_launch(int l, int np, int npt, int nc, const TcMaps& maps, const 
 // only the multipole columns 0..47 (the first K-part) on the tensor cores;
 // the columns >= 48 are left to k_m2l_rest (kernel shape 3).
 int tct_m2l_level(int p, int l, int first_part_only, const void* maps, const void* B, double* Lt, int* err,
-                  cudaStream_t s) {
+                  cudaStream_t s, float* Lt32) {
     const int hs = 1 << (l - 1);
     const int ty = tct_ty(l);
     if (hs < 16 || hs % ty != 0) return -1;
@@ -366,8 +370,8 @@ int tct_m2l_level(int p, int l, int first_part_only, const void* maps, const voi
     const TcMaps& m = ((const TcLevelMaps*)maps)->tall;
     const int nc = ncoef_of(p, 1);
     const int npt = first_part_only ? 1 : np;
-    const int rc = ty == 32 ? tct_launch<32>(l, np, npt, nc, m, B, Lt, ncell, err, s)
-                            : tct_launch<16>(l, np, npt, nc, m, B, Lt, ncell, err, s);
+    const int rc = ty == 32 ? tct_launch<32>(l, np, npt, nc, m, B, Lt, ncell, err, s, Lt32)
+                            : tct_launch<16>(l, np, npt, nc, m, B, Lt, ncell, err, s, Lt32);
     if (rc != 0) return rc;
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }

@@ -440,9 +440,10 @@ def emit_grouped_file(p, basis, T="float"):
     for k, (r0, r1) in enumerate(parts):
         klen = off[r1] - off[r0]
         ncol = pre[r0]
+        L.append("template <typename OT>   // the type of the stored locals")
         L.append("__global__ void __launch_bounds__(128)")
-        L.append("m2l_grp%s_p%d_b%d_r%d(int l, const %s* __restrict__ M, double* __restrict__ Lt,"
-                 " const %s* __restrict__ K, int64_t ncell, double* __restrict__ part) {" % (sfx, p, basis, k, T, T))
+        L.append("m2l_grp%s_p%d_b%d_r%d(int l, const %s* __restrict__ M, OT* __restrict__ Lt,"
+                 " const %s* __restrict__ K, int64_t ncell, OT* __restrict__ part) {" % (sfx, p, basis, k, T, T))
         L.append("  __shared__ __align__(16) %s sK[%d];" % (T, (klen + 3) // 4 * 4))
         L.append("  const int side = 1 << l, hs = side >> 1, bs = (int)blockDim.x;   // 128 or (FP64 small levels) 32")
         L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + bs - 1) / bs;")
@@ -478,13 +479,13 @@ def emit_grouped_file(p, basis, T="float"):
         L.append("  const int64_t tg = (int64_t)cls * h3 + t;")
         L.append("  if (gridDim.y == 1) {")
         for r in range(r0, r1):
-            L.append("    Lt[(int64_t)%d * ncell + tg] = (double)a%d;" % (r, r - r0))
+            L.append("    Lt[(int64_t)%d * ncell + tg] = (OT)a%d;" % (r, r - r0))
         L.append("  } else if (part) {   // partial sums of this offset group, added in group order afterwards")
         for r in range(r0, r1):
-            L.append("    part[((int64_t)blockIdx.y * %d + %d) * ncell + tg] = (double)a%d;" % (len(rows), r, r - r0))
+            L.append("    part[((int64_t)blockIdx.y * %d + %d) * ncell + tg] = (OT)a%d;" % (len(rows), r, r - r0))
         L.append("  } else {")
         for r in range(r0, r1):
-            L.append("    atomicAdd(Lt + (int64_t)%d * ncell + tg, (double)a%d);" % (r, r - r0))
+            L.append("    atomicAdd(Lt + (int64_t)%d * ncell + tg, (OT)a%d);" % (r, r - r0))
         L.append("  }")
         L.append("}")
     L.append("// groups > 1 splits the 216 offset slots of every target over that many")
@@ -492,17 +493,28 @@ def emit_grouped_file(p, basis, T="float"):
     L.append("// zeroed Lt with atomics; with part (groups x %d x ncell doubles) they are" % len(rows))
     L.append("// stored there and added in group order (the result does not depend on")
     L.append("// scheduling).  bs: threads (targets) per block, 128 or 32.")
-    L.append("int launch_m2l_grp%s_p%d_b%d(int l, const %s* M, double* Lt, const %s* K, int64_t ncell,"
-             " cudaStream_t s, int groups, int bs, double* part) {" % (sfx, p, basis, T, T))
+    L.append("template <typename OT>")
+    L.append("static int launch_m2l_grp%s_t_p%d_b%d(int l, const %s* M, OT* Lt, const %s* K, int64_t ncell,"
+             " cudaStream_t s, int groups, int bs, OT* part) {" % (sfx, p, basis, T, T))
     L.append("  const int hs = (1 << l) >> 1;")
     L.append("  const int64_t h3 = (int64_t)hs * hs * hs, bpc = (h3 + bs - 1) / bs;")
-    L.append("  if (groups > 1 && !part && cudaMemsetAsync(Lt, 0, (size_t)%d * ncell * sizeof(double), s) != cudaSuccess) return -1;" % len(rows))
+    L.append("  if (groups > 1 && !part && cudaMemsetAsync(Lt, 0, (size_t)%d * ncell * sizeof(OT), s) != cudaSuccess) return -1;" % len(rows))
     for k in range(len(parts)):
-        L.append("  m2l_grp%s_p%d_b%d_r%d<<<dim3((unsigned)(8 * bpc), (unsigned)groups), bs, 0, s>>>(l, M, Lt, K, ncell, part);"
+        L.append("  m2l_grp%s_p%d_b%d_r%d<OT><<<dim3((unsigned)(8 * bpc), (unsigned)groups), bs, 0, s>>>(l, M, Lt, K, ncell, part);"
                  % (sfx, p, basis, k))
     L.append("  if (groups > 1 && part) { launch_sum_parts(part, Lt, (int64_t)%d * ncell, groups, s); return %d; }" % (len(rows), len(parts) + 1))
     L.append("  return %d;" % len(parts))
     L.append("}")
+    L.append("int launch_m2l_grp%s_p%d_b%d(int l, const %s* M, double* Lt, const %s* K, int64_t ncell,"
+             " cudaStream_t s, int groups, int bs, double* part) {" % (sfx, p, basis, T, T))
+    L.append("  return launch_m2l_grp%s_t_p%d_b%d<double>(l, M, Lt, K, ncell, s, groups, bs, part);" % (sfx, p, basis))
+    L.append("}")
+    if not f64:
+        L.append("// FP32 locals (uniform FP32 and tensor-core plans)")
+        L.append("int launch_m2l_grpf_p%d_b%d(int l, const float* M, float* Lt, const float* K, int64_t ncell,"
+                 " cudaStream_t s, int groups, int bs, float* part) {" % (p, basis))
+        L.append("  return launch_m2l_grp_t_p%d_b%d<float>(l, M, Lt, K, ncell, s, groups, bs, part);" % (p, basis))
+        L.append("}")
     L.append("}  // namespace fmm")
     return "\n".join(L) + "\n"
 
@@ -630,6 +642,46 @@ def emit_shift_file(p, basis):
                 L.append("    Lch[(int64_t)%d * nch + C] = o%d + (double)a%d;" % (r, r, r))
             L.append("  }")
         L.append("}")
+        # ---- L2L on FP32 locals (uniform FP32 and tensor-core plans): the
+        # same sums, read-modify-writes in FP32 ----
+        L.append("__global__ void __launch_bounds__(128)")
+        L.append("l2l32f_p%d_b%d(int l, const float* __restrict__ V, const float* __restrict__ Lpa, int64_t npa,"
+                 " float* __restrict__ Lch, int64_t nch) {" % (p, basis))
+        L.append("  __shared__ float sV[%d];" % sz)
+        L.append("  const int64_t blk = (int64_t)1 << (3 * l), bpc = (blk + 127) / 128;")
+        L.append("  const int c = (int)(blockIdx.x / bpc);")
+        L.append("  const int64_t lin = (int64_t)(blockIdx.x % bpc) * 128 + threadIdx.x;")
+        L.append("  for (int e = threadIdx.x; e < %d; e += 128) sV[e] = V[c * %d + e];" % (sz, sz))
+        L.append("  __syncthreads();")
+        L.append("  if (lin >= blk) return;")
+        L.append("  const int s = 1 << l;")
+        L.append("  const int px = (int)(lin % s), py = (int)((lin / s) % s), pz = (int)(lin / ((int64_t)s * s));")
+        L.append("  const int64_t P = cell_index(l, px, py, pz), C = c * blk + lin;")
+        for k in range(nc):
+            L.append("  const float x%d = Lpa[(int64_t)%d * npa + P];" % (k, k))
+        for r0 in range(0, nc, 16):
+            r1 = min(nc, r0 + 16)
+            L.append("  {")
+            for r in range(r0, r1):
+                L.append("    const float o%d = Lch[(int64_t)%d * nch + C];" % (r, r))
+            for r in range(r0, r1):
+                c0, c1 = rng[r]
+                L.append("    float a%d = 0.f;" % r)
+                for k in range(c0, c1):
+                    L.append("    a%d = fmaf(sV[%d], x%d, a%d);" % (r, off[r] + k - c0, k, r))
+            for r in range(r0, r1):
+                L.append("    Lch[(int64_t)%d * nch + C] = o%d + a%d;" % (r, r, r))
+            L.append("  }")
+        L.append("}")
+    L.append("int launch_l2l32f_p%d_b%d(int l, const float* V, const float* X, int64_t nx, float* Y, int64_t ny,"
+             " cudaStream_t s) {" % (p, basis))
+    if shift32_ok(p, basis):
+        L.append("  l2l32f_p%d_b%d<<<(unsigned)(8 * ((((int64_t)1 << (3 * l)) + 127) / 128)), 128, 0, s>>>"
+                 "(l, V, X, nx, Y, ny);" % (p, basis))
+        L.append("  return 1;")
+    else:
+        L.append("  return -1;")
+    L.append("}")
     L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx, double* Y,"
              " int64_t ny, cudaStream_t s, float* part, const float* X32, float* Y32) {" % (p, basis))
     if shift32_ok(p, basis):
@@ -658,6 +710,19 @@ def emit_shift_dispatch():
         for b in (0, 1):
             L.append("int launch_shift32_p%d_b%d(int m2m, int l, const float* A, const double* X, int64_t nx,"
                      " double* Y, int64_t ny, cudaStream_t s, float* part, const float* X32, float* Y32);" % (p, b))
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("int launch_l2l32f_p%d_b%d(int l, const float* V, const float* X, int64_t nx, float* Y,"
+                     " int64_t ny, cudaStream_t s);" % (p, b))
+    L.append("// L2L on FP32 locals; returns the launches made, -1 without a kernel")
+    L.append("int launch_l2l32f(int p, int basis, int l, const float* V, const float* X, int64_t nx, float* Y,"
+             " int64_t ny, cudaStream_t s) {")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("  if (p == %d && basis == %d) return launch_l2l32f_p%d_b%d(l, V, X, nx, Y, ny, s);"
+                     % (p, b, p, b))
+    L.append("  return -1;")
+    L.append("}")
     L.append("// part: 8 x nc x ny floats for the per-child M2M (m2m32c + m2m32_sum), which")
     L.append("// reads the children's FP32 copy X32 and writes both Y and its FP32 copy Y32;")
     L.append("// without them the one-thread-per-parent M2M.  Returns the launches made.")
@@ -823,6 +888,8 @@ def emit_grouped_dispatch():
         for b in (0, 1):
             L.append("int launch_m2l_grp_p%d_b%d(int l, const float* M, double* Lt, const float* K, int64_t ncell,"
                      " cudaStream_t s, int groups, int bs, double* part);" % (p, b))
+            L.append("int launch_m2l_grpf_p%d_b%d(int l, const float* M, float* Lt, const float* K, int64_t ncell,"
+                     " cudaStream_t s, int groups, int bs, float* part);" % (p, b))
             L.append("int launch_m2l_grp64_p%d_b%d(int l, const double* M, double* Lt, const double* K,"
                      " int64_t ncell, cudaStream_t s, int groups, int bs, double* part);" % (p, b))
         L.append("int launch_m2l_grp64_p%d_b2(int l, const double* M, double* Lt, const double* K,"
@@ -840,6 +907,32 @@ def emit_grouped_dispatch():
     for p in range(PMAX + 1):
         for b in (0, 1):
             L.append("  if (p == %d && basis == %d) return launch_m2l_grp_p%d_b%d(l, M, Lt, K, ncell, s, groups, 128, nullptr);"
+                     % (p, b, p, b))
+    L.append("  return -1;")
+    L.append("}")
+    L.append("int grouped_nrows(int p, int basis);")
+    L.append("// The same with FP32 locals, deterministic: the split small levels write")
+    L.append("// their groups' partial sums to part and add them in group order (no atomic")
+    L.append("// adds); without room in part (part_cap floats) a level runs unsplit.")
+    L.append("static int grpf_split(int l) {")
+    L.append("  static int sms = 0;")
+    L.append("  if (!sms) { int d = 0; cudaGetDevice(&d); cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);"
+             " if (sms <= 0) sms = 1; }")
+    L.append("  const int64_t hs = (int64_t)1 << (l - 1), blocks = 8 * ((hs * hs * hs + 127) / 128);")
+    L.append("  const int64_t g = (4 * (int64_t)sms + blocks - 1) / blocks;")
+    L.append("  return (int)(g < 1 ? 1 : g > 27 ? 27 : g);")
+    L.append("}")
+    L.append("int64_t m2l_grpf_part_elems(int p, int basis, int l) {")
+    L.append("  const int g = grpf_split(l);")
+    L.append("  return g > 1 ? (int64_t)g * grouped_nrows(p, basis) * ((int64_t)1 << (3 * l)) : 0;")
+    L.append("}")
+    L.append("int launch_m2l_grpf(int p, int basis, int l, const float* M, float* Lt, const float* K,"
+             " int64_t ncell, cudaStream_t s, float* part, int64_t part_cap) {")
+    L.append("  int groups = grpf_split(l);")
+    L.append("  if (!part || (int64_t)groups * grouped_nrows(p, basis) * ncell > part_cap) groups = 1;")
+    for p in range(PMAX + 1):
+        for b in (0, 1):
+            L.append("  if (p == %d && basis == %d) return launch_m2l_grpf_p%d_b%d(l, M, Lt, K, ncell, s, groups, 128, part);"
                      % (p, b, p, b))
     L.append("  return -1;")
     L.append("}")
