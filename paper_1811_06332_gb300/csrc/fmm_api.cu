@@ -75,6 +75,7 @@ struct fmm_plan {
     int* derr = nullptr;                 // device error word (bounded waits)
     // FP32 forms: positions relative to leaf centres, packed FP32 shifts
     float4* pos32 = nullptr;
+    float4* pos32c = nullptr;   // the same in caller order (tree build scratch)
     float* W32 = nullptr;
     float* V32 = nullptr;
     float* part32 = nullptr;   // per-child FP32 M2M contributions: 8 x nc x 8^(depth-1)
@@ -491,7 +492,8 @@ static void free_tree(fmm_plan* pl) {
     cudaFree(pl->xs); cudaFree(pl->ys); cudaFree(pl->zs); cudaFree(pl->qs);
     cudaFree(pl->perm); cudaFree(pl->start); cudaFree(pl->scratch);
     cudaFree(pl->Mbuf); cudaFree(pl->Lbuf); cudaFree(pl->M32); cudaFree(pl->Mbf); cudaFree(pl->pos32);
-    cudaFree(pl->dip); cudaFree(pl->msym32); cudaFree(pl->L32); cudaFree(pl->lpart);
+    cudaFree(pl->dip); cudaFree(pl->msym32); cudaFree(pl->L32); cudaFree(pl->lpart); cudaFree(pl->pos32c);
+    pl->pos32c = nullptr;
     pl->msym32 = nullptr;
     pl->L32 = nullptr;
     pl->lpart = nullptr;
@@ -797,6 +799,7 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
             cudaMalloc(&pl->Mbuf, tot * 8) != cudaSuccess || cudaMalloc(&pl->Lbuf, tot * 8) != cudaSuccess ||
             (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->M32, tot * 4) != cudaSuccess) ||
             (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->pos32, nn * 16) != cudaSuccess) ||
+            (pl->cfg.prec != FMM_FP64 && cudaMalloc(&pl->pos32c, nn * 16) != cudaSuccess) ||
             (pl->cfg.prec != FMM_FP64 && bM(pl) == FMM_BASIS_TRACELESS &&
              cudaMalloc(&pl->msym32, (size_t)pl->nleaf * ((ns_of(pl->cfg.p) + 3) / 4 * 4) * 4) != cudaSuccess) ||
             (pl->cfg.prec != FMM_FP64 && pl->V32 && cudaMalloc(&pl->L32, tot * 4) != cudaSuccess)) {
@@ -841,7 +844,7 @@ int fmm_build_tree(fmm_plan* pl, int64_t n, const double* x, const double* y, co
         pl->n = n;
     }
     if (launch_uniform_tree(n, pl->depth, x, y, z, q, pl->xs, pl->ys, pl->zs, pl->qs, pl->perm, pl->start,
-                            pl->scratch, S(stream), pl->pos32) != 0)
+                            pl->scratch, S(stream), pl->pos32, pl->pos32c) != 0)
         FAIL(FMM_ERR_CUDA, "tree build failed: %s", cudaGetErrorString(cudaGetLastError()));
     CKLAUNCH();
     pl->built = true;

@@ -216,6 +216,6 @@ size_t tree_scratch_bytes(int64_t n, int64_t nleaf);
 void scan_excl_int(const int* in, int* out, int64_t m, int* scratch, cudaStream_t s);
 int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,
                         double* xs, double* ys, double* zs, double* qs, int* perm, int* start, void* scratch,
-                        cudaStream_t s, float4* pos32 = nullptr);
+                        cudaStream_t s, float4* pos32 = nullptr, float4* pos32c = nullptr);
 
 }  // namespace fmm

@@ -20,18 +20,28 @@ size_t tree_scratch_bytes(int64_t n, int64_t nleaf) {
 }
 
 __global__ void k_leaf_key(int64_t n, int depth, const double* __restrict__ x, const double* __restrict__ y,
-                           const double* __restrict__ z, int* __restrict__ key, int* __restrict__ count) {
+                           const double* __restrict__ z, int* __restrict__ key, int* __restrict__ count,
+                           const double* __restrict__ q, float4* __restrict__ pc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int side = 1 << depth;
     const double fs = (double)side;
-    int ix = (int)floor(x[i] * fs), iy = (int)floor(y[i] * fs), iz = (int)floor(z[i] * fs);
+    const double xi = x[i], yi = y[i], zi = z[i];
+    int ix = (int)floor(xi * fs), iy = (int)floor(yi * fs), iz = (int)floor(zi * fs);
     ix = min(max(ix, 0), side - 1);
     iy = min(max(iy, 0), side - 1);
     iz = min(max(iz, 0), side - 1);
     const int k = (int)cell_index(depth, ix, iy, iz);
     key[i] = k;
     atomicAdd(&count[k], 1);
+    if (pc) {
+        // FP32 forms: the position relative to the centre of its leaf, in
+        // caller order (coalesced here; the gather then moves one 16-byte
+        // record per particle)
+        const double h = 1.0 / fs;
+        pc[i] = make_float4((float)(xi - (ix + 0.5) * h), (float)(yi - (iy + 0.5) * h), (float)(zi - (iz + 0.5) * h),
+                            (float)q[i]);
+    }
 }
 
 // Exclusive scan of int32, 4096 elements per block (1024 threads x 4).
@@ -137,34 +147,25 @@ __global__ void k_leaf_sort(int64_t nleaf, const int* __restrict__ start, int* _
 __global__ void k_gather(int64_t n, const int* __restrict__ order, const double* __restrict__ x,
                          const double* __restrict__ y, const double* __restrict__ z, const double* __restrict__ q,
                          double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ zs,
-                         double* __restrict__ qs, int* __restrict__ perm, int depth, const int* __restrict__ key,
+                         double* __restrict__ qs, int* __restrict__ perm, const float4* __restrict__ pc,
                          float4* __restrict__ pos32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int o = order[i];
-    const double xo = x[o], yo = y[o], zo = z[o], qo = q[o];
     perm[i] = o;
     if (pos32) {
-        // FP32 forms: only the FP32 position relative to the centre of the
-        // particle's own leaf (its cell recomputed as k_leaf_key computes it,
-        // instead of a second random read of the key); their operators read
-        // no sorted FP64 coordinates
-        const int side = 1 << depth;
-        const double fs = (double)side;
-        const int ix = min(max((int)floor(xo * fs), 0), side - 1);
-        const int iy = min(max((int)floor(yo * fs), 0), side - 1);
-        const int iz = min(max((int)floor(zo * fs), 0), side - 1);
-        const double h = 1.0 / (double)side;
-        pos32[i] = make_float4((float)(xo - (ix + 0.5) * h), (float)(yo - (iy + 0.5) * h),
-                               (float)(zo - (iz + 0.5) * h), (float)qo);
+        // FP32 forms: only the FP32 leaf-relative positions (computed by
+        // k_leaf_key); their operators read no sorted FP64 coordinates
+        pos32[i] = pc[o];
         return;
     }
-    xs[i] = xo; ys[i] = yo; zs[i] = zo; qs[i] = qo;
+    xs[i] = x[o]; ys[i] = y[o]; zs[i] = z[o]; qs[i] = q[o];
 }
 
 int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, const double* z, const double* q,
                         double* xs, double* ys, double* zs, double* qs, int* perm, int* start, void* scratch,
-                        cudaStream_t s, float4* pos32) {
+                        cudaStream_t s, float4* pos32, float4* pos32c) {
+    if (pos32 && !pos32c) return -1;
     const int64_t nleaf = (int64_t)1 << (3 * depth);
     char* p = (char*)scratch;
     int* key = (int*)p;   p += align_up(n * 4, 256);
@@ -173,7 +174,7 @@ int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, 
     int* sc = (int*)p;
     if (cudaMemsetAsync(fill, 0, nleaf * sizeof(int), s) != cudaSuccess) return -2;
     if (n > 0) {
-        k_leaf_key<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, depth, x, y, z, key, fill);
+        k_leaf_key<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, depth, x, y, z, key, fill, q, pos32 ? pos32c : nullptr);
         count_launch();
     }
     scan_excl(fill, start, nleaf, sc, s);
@@ -185,8 +186,7 @@ int launch_uniform_tree(int64_t n, int depth, const double* x, const double* y, 
     k_leaf_sort<<<(unsigned)((nleaf + 255) / 256), 256, 0, s>>>(nleaf, start, order);
     count_launch();
     if (n > 0) {
-        k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, order, x, y, z, q, xs, ys, zs, qs, perm, depth, key,
-                                                             pos32);
+        k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, order, x, y, z, q, xs, ys, zs, qs, perm, pos32c, pos32);
         count_launch();
     }
     return 0;
