@@ -53,9 +53,9 @@ M2L_TRAFFIC = {
     # k_m2l_tc_t<32> (kernel 2): 722.5 MB read + 154.8 MB written at level 6, x 9/8 for levels 5-6
     ("bf16x3", 2, 256): (9.870e8, "ncu capture of the level-6 launch scaled by cells to levels 5-6 "
                                   "(profiles/m2l_tensorcore_swapped_bf16x3_level6_uniform4M_p8.md)"),
-    # kernel 3: k_m2l_tc_t<32> first K-part 160.1 MB read + 137.5 MB written, k_m2l_rest<8> 56.8 + 1.8 MB,
-    # at level 6, x 9/8 for levels 5-6 (the operand split and the FP32 copy of the columns >= 48 not included)
-    ("bf16x3", 3, 256): (4.008e8, "ncu capture of the level-6 tensor-core and CUDA-core launches scaled by cells "
+    # kernel 3: k_m2l_tc_t<32> first K-part 113.9 MB read + 62.9 MB written (FP32 locals), k_m2l_rest<8>
+    # 47.3 + 0.5 MB, at level 6, x 9/8 for levels 5-6 (the operand split and the column pack not included)
+    ("bf16x3", 3, 256): (2.528e8, "ncu capture of the level-6 tensor-core and CUDA-core launches scaled by cells "
                                    "to levels 5-6 (profiles/m2l_tensorcore_split_bf16x3_level6_uniform_p8.md)"),
     # m2l_grp_p8_b1_r0: 653.9 MB read + 154.4 MB written at level 6, x 299584/262144 for levels 2-6
     ("fp32", None, None): (9.237e8, "ncu capture of the level-6 launch scaled by cells to levels 2-6 "
