@@ -64,6 +64,8 @@ struct fmm_plan {
     // kernel 3: the multipole columns >= 48 on the CUDA cores
     float* Mrest = nullptr;              // 8^depth x rest_cstride(p): columns >= 48, cell-major FP32
     float* Krest = nullptr;              // 343 x rest_kstride(p) matrix entries of those columns
+    float* Rpart = nullptr;              // level 5's source-class group sums of those products
+    int64_t rpart_cap = 0;               // floats in Rpart
     int tc_source = 0;                   // 0 default, 1 autotuned, 2 from the cache, 3 set by the caller
     cudaGraphExec_t ugexec = nullptr;    // uniform plans with use_graph: the captured step
     const void* ugkey[11] = {nullptr};   // what the captured step depends on
@@ -145,6 +147,12 @@ static int tc_set_shape(fmm_plan* pl, int kern, int cw, cudaStream_t s) {
                 cudaMalloc(&pl->Krest, (size_t)343 * rest_kstride(p) * sizeof(float)) != cudaSuccess ||
                 build_krest(p, pl->Dtab, pl->Krest, s) != 0)
                 return -2;
+            // level 5 (16^3 cells per class) splits its source classes
+            if (pl->depth >= 5) {
+                const int64_t cap = (int64_t)rest_nsplit(5) * rest_rows(p) * ((int64_t)1 << 15);
+                if (cudaMalloc(&pl->Rpart, (size_t)cap * sizeof(float)) != cudaSuccess) return -2;
+                pl->rpart_cap = cap;
+            }
         }
     } else {
         if (tg_build(pl->cfg.p, cw, 1, pl->Dtab, pl->Kgen, s) != 0) return -2;
@@ -186,7 +194,8 @@ static int tc_level_call(fmm_plan* pl, int l, cudaStream_t s) {
     // them, then their products) on the CUDA cores, added to L
     if (rc == 0 && pl->tc_kern == 3 && rest_rows(p) > 0 &&
         (launch_rest_pack(p, l, pl->Mbuf + pl->lvl_off[l], pl->Mrest, s, m32) != 0 ||
-         launch_m2l_rest(p, l, pl->Mrest, pl->Krest, pl->Lbuf + pl->lvl_off[l], s, L32lev(pl, l)) != 0))
+         launch_m2l_rest(p, l, pl->Mrest, pl->Krest, pl->Lbuf + pl->lvl_off[l], s, L32lev(pl, l), pl->Rpart,
+                         pl->rpart_cap) != 0))
         return -2;
     return rc;
 }
@@ -759,7 +768,7 @@ void fmm_destroy(fmm_plan* pl) {
     if (pl->ugexec) cudaGraphExecDestroy(pl->ugexec);
     cudaFree(pl->Kbf); cudaFree(pl->Kgen); cudaFree(pl->derr); cudaFree(pl->W32); cudaFree(pl->V32); cudaFree(pl->mlp_dev);
     cudaFree(pl->part32);
-    cudaFree(pl->Mrest); cudaFree(pl->Krest);
+    cudaFree(pl->Mrest); cudaFree(pl->Krest); cudaFree(pl->Rpart);
     delete pl;
 }
 

@@ -184,9 +184,13 @@ int rest_kstride(int p);   // floats per offset of the matrix table
 int rest_cstride(int p);   // floats per cell of the multipole copy
 int build_krest(int p, const double* Dtab, float* Krest, cudaStream_t s);
 int launch_rest_pack(int p, int l, const double* M, float* Mrest, cudaStream_t s, const float* M32 = nullptr);
-// Lt (level l, after the tensor-core kernel) += those products
+// Lt (level l, after the tensor-core kernel) += those products.  Levels
+// where rest_nsplit(l) > 1 split the source classes over that many blocks
+// per tile when part holds rest_nsplit(l) * rest_rows(p) * 8^l floats
+// (part_cap), summed in order by a second kernel; else one block per tile.
+int rest_nsplit(int l);
 int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s,
-                    float* Lt32 = nullptr);
+                    float* Lt32 = nullptr, float* part = nullptr, int64_t part_cap = 0);
 size_t tc_maps_bytes();
 // kern 0: per-offset matrices streamed from global memory (tc_build_mat at
 // chunk width cw; niss follows from the layout); kern 1 (BF16 only): the

@@ -30,12 +30,15 @@ namespace fmm {
 // records and the nine (dx, dy) offsets' entries to shared memory, then every
 // thread accumulates its targets' rows over the offsets that are not near
 // neighbours (packed FP32x2 FMAs over column pairs, each entry load serving
-// both targets), and finally adds them to the FP64 locals the tensor-core
-// kernel wrote.
+// both targets), and finally adds them to the locals the tensor-core kernel
+// wrote.  With nsplit > 1 (small levels, where one block per tile leaves
+// most schedulers idle) the eight source classes are split into nsplit
+// consecutive groups, one block per tile and group; each block writes its
+// sums to part[group] and k_rest_sum adds the groups in order.
 template <int P>
 __global__ void __launch_bounds__(64)
-k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ Krest, double* __restrict__ Lt,
-           int64_t ncell, float* __restrict__ Lt32) {
+k_m2l_rest(int l, int nsplit, const float4* __restrict__ Mrest, const float4* __restrict__ Krest,
+           double* __restrict__ Lt, int64_t ncell, float* __restrict__ Lt32, float* __restrict__ part) {
     constexpr int NR = rs_rows(P);
     constexpr int CS = rs_cstride(P);
     constexpr int KS = rs_kstride(P);
@@ -47,8 +50,11 @@ k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ K
     const int64_t h3 = (int64_t)hs * hs * hs;
     const int ntx = hs / RS_TX, nty = hs / RS_TY;
     const int64_t tpc = (int64_t)ntx * nty * hs;
-    const int cls = (int)(blockIdx.x / tpc);
-    const int64_t t = blockIdx.x % tpc;
+    const int grp = (int)(blockIdx.x / (8 * tpc));   // source-class group
+    const int64_t bt = blockIdx.x % (8 * tpc);
+    const int cls = (int)(bt / tpc);
+    const int64_t t = bt % tpc;
+    const int sc0 = grp * (8 / nsplit), sc1 = sc0 + 8 / nsplit;
     const int ti = (int)(t % ntx), tj = (int)((t / ntx) % nty), tk = (int)(t / ((int64_t)ntx * nty));
     const int cx = cls & 1, cy = (cls >> 1) & 1, cz = cls >> 2;
     const int x = threadIdx.x & 7, y = threadIdx.x >> 3;   // targets (x, y) and (x, y + 8)
@@ -56,7 +62,7 @@ k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ K
 #pragma unroll
     for (int r = 0; r < NR; ++r) aa[r] = ab[r] = 0ull;
 #pragma unroll 1
-    for (int sc = 0; sc < 8; ++sc) {
+    for (int sc = sc0; sc < sc1; ++sc) {
         const int sx = sc & 1, sy = (sc >> 1) & 1, sz = sc >> 2;
 #pragma unroll 1
         for (int dz = -1; dz <= 1; ++dz) {
@@ -107,7 +113,11 @@ k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ K
     for (int r = 0; r < NR; ++r) {
         const float va = __uint_as_float((uint32_t)aa[r]) + __uint_as_float((uint32_t)(aa[r] >> 32));
         const float vb = __uint_as_float((uint32_t)ab[r]) + __uint_as_float((uint32_t)(ab[r] >> 32));
-        if (Lt32) {
+        if (nsplit > 1) {
+            float* pr = part + ((int64_t)grp * NR + r) * ncell;
+            pr[tg] = va;
+            pr[tg + 8 * hs] = vb;
+        } else if (Lt32) {
             Lt32[(int64_t)r * ncell + tg] += va;
             Lt32[(int64_t)r * ncell + tg + 8 * hs] += vb;
         } else {
@@ -115,6 +125,20 @@ k_m2l_rest(int l, const float4* __restrict__ Mrest, const float4* __restrict__ K
             Lt[(int64_t)r * ncell + tg + 8 * hs] += (double)vb;
         }
     }
+}
+
+// L[r][cell] += the nsplit groups' sums part[g][r][cell], added in group
+// order (rows r < nr of a level's coefficient-major locals)
+__global__ void __launch_bounds__(256) k_rest_sum(int64_t nel, int nsplit, const float* __restrict__ part,
+                                                  double* __restrict__ Lt, float* __restrict__ Lt32) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nel) return;
+    float v = part[e];
+    for (int g = 1; g < nsplit; ++g) v += part[(int64_t)g * nel + e];
+    if (Lt32)
+        Lt32[e] += v;
+    else
+        Lt[e] += (double)v;
 }
 
 // Mrest of level l from the FP64 coefficient-major multipoles M: a block
@@ -167,17 +191,31 @@ int rest_cstride(int p) { return rest_rows(p) ? rs_cstride(p) : 0; }
 
 #define RS_P_SWITCH(p, F) (p == 6 ? F(6) : p == 7 ? F(7) : F(8))
 
-int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s, float* Lt32) {
+int rest_nsplit(int l) {
+    const int64_t hs = (int64_t)1 << (l - 1);
+    return 8 * (hs / RS_TX) * (hs / RS_TY) * hs < 1024 ? 4 : 1;
+}
+
+int launch_m2l_rest(int p, int l, const float* Mrest, const float* Krest, double* Lt, cudaStream_t s, float* Lt32,
+                    float* part, int64_t part_cap) {
     const int hs = 1 << (l - 1);
     if (hs < RS_TY || rest_rows(p) == 0) return -1;
     const int64_t ncell = (int64_t)8 * hs * hs * hs;
-    const unsigned g = (unsigned)(8 * (int64_t)(hs / RS_TX) * (hs / RS_TY) * hs);
+    const int nr = rest_rows(p);
+    int nsplit = rest_nsplit(l);
+    if (!part || part_cap < (int64_t)nsplit * nr * ncell) nsplit = 1;
+    const unsigned g = (unsigned)(8 * (int64_t)(hs / RS_TX) * (hs / RS_TY) * hs * nsplit);
     const float4* m4 = (const float4*)Mrest;
     const float4* k4 = (const float4*)Krest;
-#define RS_L(P) (k_m2l_rest<P><<<g, 64, 0, s>>>(l, m4, k4, Lt, ncell, Lt32), 0)
+#define RS_L(P) (k_m2l_rest<P><<<g, 64, 0, s>>>(l, nsplit, m4, k4, Lt, ncell, Lt32, part), 0)
     RS_P_SWITCH(p, RS_L);
 #undef RS_L
     count_launch();
+    if (nsplit > 1) {
+        const int64_t nel = (int64_t)nr * ncell;
+        k_rest_sum<<<(unsigned)((nel + 255) / 256), 256, 0, s>>>(nel, nsplit, part, Lt, Lt32);
+        count_launch();
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -87,13 +87,17 @@ def test_step_by_step_equals_evaluate(F):
 
 @pytest.mark.parametrize("prec,p,basis,depth,n", [("FP32", 8, 1, 4, 70000), ("FP32", 6, 0, 3, 9000),
                                                    ("GEMM_BF16X3", 8, 1, 5, 300000), ("FP32", 4, 1, 1, 2000),
+                                                   ("FP32", 8, 1, 2, 2500), ("FP32", 5, 1, 2, 9000),
                                                    ("FP64", 5, 1, 3, 6000)])
 def test_fused_far_near_field_equals_the_two_steps(F, prec, p, basis, depth, n):
     """fmm_l2p_p2p (one kernel for the FP32 and tensor-core forms on a
     uniform octree; the two steps otherwise) writes exactly what fmm_l2p
     followed by fmm_p2p writes: the same FP32 arithmetic in the same order
     and explicitly rounded FP64 combinations.  Ragged leaves (Poisson counts,
-    some empty at depth 5 with 300,000 particles: about 9 per leaf)."""
+    some empty at depth 5 with 300,000 particles: about 9 per leaf; about 17
+    and 39 per leaf at depths 4 and 2; 140 per leaf at depth 2, several
+    blocks of 32 targets per leaf).  At depths 0 and 1 (no far field)
+    fmm_l2p_p2p runs the two steps."""
     x, y, z = inputs.uniform_cube(n, 70 + depth)
     q = inputs.masses_open_unit(n, 70 + depth)
     plan = F.Plan(p=p, basis=basis, prec=getattr(F, prec), depth=depth)
@@ -229,9 +233,10 @@ def test_swapped_tensor_core_kernel_vs_oracle(F, depth, n, p):
 def test_split_tensor_core_kernel_vs_oracle(F, depth, n, p):
     """Kernel shape 3: the swapped kernel on the first K-part (multipole
     columns 0..47) while the columns >= 48, which reach only the local rows
-    of rank <= p - 6, run as FP32 products on the CUDA cores on a second
-    stream and are added to L after both (p = 6..8; at p = 5 there are no
-    such columns and it is kernel 2).  Against the FP64 oracle on sampled
+    of rank <= p - 6, run as FP32 products on the CUDA cores after the
+    tensor-core kernel and are added to L (level 5 with its source classes
+    split over four blocks per tile, the groups added in order; p = 6..8; at
+    p = 5 there are no such columns and it is kernel 2).  Against the FP64 oracle on sampled
     particles, bound 5e-6 as for the other shapes; and equal to kernel 2
     within 1e-5 of the largest value (the two differ only in the rounding
     of those few products)."""
