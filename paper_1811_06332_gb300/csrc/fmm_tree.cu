@@ -2,6 +2,7 @@
 // workloads): leaf of a particle from its coordinates, a counting sort of the
 // particles into leaves (stable by original index), and the leaf ranges.
 #include "fmm_internal.h"
+#include "fmm_fixpoint.h"
 
 namespace fmm {
 
@@ -25,12 +26,21 @@ __global__ void k_leaf_key(int64_t n, int depth, const double* __restrict__ x, c
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int side = 1 << depth;
-    const double fs = (double)side;
     const double xi = x[i], yi = y[i], zi = z[i];
-    int ix = (int)floor(xi * fs), iy = (int)floor(yi * fs), iz = (int)floor(zi * fs);
-    ix = min(max(ix, 0), side - 1);
-    iy = min(max(iy, 0), side - 1);
-    iz = min(max(iz, 0), side - 1);
+    // inside the unit cube: leaf and offset in integer fixed point
+    // (fmm_fixpoint.h); else (a point on or outside the boundary) in FP64,
+    // clamped to the boundary leaves
+    int64_t X, Y, Z;
+    const bool fix = fix62(xi, X) && fix62(yi, Y) && fix62(zi, Z);
+    int ix, iy, iz;
+    if (fix) {
+        ix = fix62_leaf(X, depth); iy = fix62_leaf(Y, depth); iz = fix62_leaf(Z, depth);
+    } else {
+        const double fs = (double)side;
+        ix = min(max((int)floor(xi * fs), 0), side - 1);
+        iy = min(max((int)floor(yi * fs), 0), side - 1);
+        iz = min(max((int)floor(zi * fs), 0), side - 1);
+    }
     const int k = (int)cell_index(depth, ix, iy, iz);
     key[i] = k;
     atomicAdd(&count[k], 1);
@@ -38,9 +48,14 @@ __global__ void k_leaf_key(int64_t n, int depth, const double* __restrict__ x, c
         // FP32 forms: the position relative to the centre of its leaf, in
         // caller order (coalesced here; the gather then moves one 16-byte
         // record per particle)
-        const double h = 1.0 / fs;
-        pc[i] = make_float4((float)(xi - (ix + 0.5) * h), (float)(yi - (iy + 0.5) * h), (float)(zi - (iz + 0.5) * h),
-                            (float)q[i]);
+        if (fix) {
+            pc[i] = make_float4(fix62_offset(X, ix, depth), fix62_offset(Y, iy, depth), fix62_offset(Z, iz, depth),
+                                (float)q[i]);
+        } else {
+            const double h = 1.0 / (double)side;
+            pc[i] = make_float4((float)(xi - (ix + 0.5) * h), (float)(yi - (iy + 0.5) * h),
+                                (float)(zi - (iz + 0.5) * h), (float)q[i]);
+        }
     }
 }
 
