@@ -53,10 +53,11 @@ M2L_TRAFFIC = {
     # k_m2l_tc_t<32> (kernel 2): 722.5 MB read + 154.8 MB written at level 6, x 9/8 for levels 5-6
     ("bf16x3", 2, 256): (9.870e8, "ncu capture of the level-6 launch scaled by cells to levels 5-6 "
                                   "(profiles/m2l_tensorcore_swapped_bf16x3_level6_uniform4M_p8.md)"),
-    # kernel 3: k_m2l_tc_t<32> first K-part 113.9 MB read + 62.9 MB written (FP32 locals), k_m2l_rest<8>
-    # 47.3 + 0.5 MB, at level 6, x 9/8 for levels 5-6 (the operand split and the column pack not included)
-    ("bf16x3", 3, 256): (2.528e8, "ncu capture of the level-6 tensor-core and CUDA-core launches scaled by cells "
-                                   "to levels 5-6 (profiles/m2l_tensorcore_split_bf16x3_level6_uniform_p8.md)"),
+    # kernel 3, every launch of levels 6 and 5 (operand split, k_m2l_tc_t first K-part, column pack,
+    # k_m2l_rest, level 5's group sum): 310.9 MB at level 6 + 33.3 MB at level 5, read + written
+    ("bf16x3", 3, 256): (3.442e8, "ncu capture of every launch of the tensor-core levels 6 and 5 (operand split, "
+                                   "tensor-core kernel, column pack, CUDA-core columns, group sum) "
+                                   "(profiles/m2l_tensorcore_split_bf16x3_level6_uniform_p8.md)"),
     # m2l_grp_p8_b1_r0: 653.9 MB read + 154.4 MB written at level 6, x 299584/262144 for levels 2-6
     ("fp32", None, None): (9.237e8, "ncu capture of the level-6 launch scaled by cells to levels 2-6 "
                                     "(profiles/m2l_grouped_fp32_level6_uniform4M_p8.md)"),
