@@ -142,12 +142,16 @@ k_p2m_leaf(int basis, int depth, int64_t nleaf, const int* __restrict__ start, c
 #pragma unroll
             for (int k = 0; k < KC; ++k) {
                 if (lane + 32 * k < NCOL) {
-                    // q x^nx y^ny, then the column's z powers: one product per component
+                    // q x^nx y^ny, then the column's z powers: one product per
+                    // component.  FP32: all P + 1 z powers, unconditionally (the
+                    // sums past the column's rank are never stored; a product costs
+                    // less than the per-lane test that would skip it); FP64 skips
+                    // them, its FMAs being the costly part
                     const T wgt = qa * sPw[w][i][0][cnx[k]] * sPw[w][i][1][cny[k]];
                     const int rem = P - cnx[k] - cny[k];
 #pragma unroll
                     for (int j = 0; j <= P; ++j)
-                        if (j <= rem) acc[k][j] = fma(wgt, zp[j], acc[k][j]);
+                        if (sizeof(T) == 4 || j <= rem) acc[k][j] = fma(wgt, zp[j], acc[k][j]);
                 }
             }
         }
