@@ -462,7 +462,7 @@ def test_uniform_graph_replay(F, prec, p, depth, n, kern):
     stream = torch.cuda.Stream()
     gp = F.Plan(p=p, basis=1, prec=getattr(F, prec), depth=depth, use_graph=True)
     ep = F.Plan(p=p, basis=1, prec=getattr(F, prec), depth=depth)
-    if kern is not None:   # kernel 3 forks the CUDA-core columns onto a second stream inside the graph
+    if kern is not None:   # kernel 3: the CUDA-core columns' launches (and level 5's group sum) in the graph
         gp.set_tc_shape(kern, 256)
         ep.set_tc_shape(kern, 256)
     out = torch.empty((4, n), device=DEV, dtype=torch.float64)
